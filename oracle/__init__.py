@@ -1,0 +1,335 @@
+"""CPU FP64 oracle for randomized GENP (Pan & Qian, arXiv:1212.4560).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import
+this package.  It shares no code with the CUDA library and never imports it;
+the CUDA library never calls it.
+
+The arithmetic lives in ``genp_oracle.c`` (plain loops in IEEE double, no
+fused multiply-add).  This module loads it with ctypes, adds the pipeline of
+the method (Sec. 1.1; Cor. 4.1, the ``MH`` form of Thm. 4.1 with M = A,
+H = G), iterative refinement (Sec. 7.1: one refinement step in Table 7.1),
+the adjoint, exact Leibniz determinants and error measures.
+
+Parity pins live in ``tests/test_oracle_*.py``.  Parity unpinned: agreement
+with the statistics of Table 7.1 (the paper does not give its matrix
+construction, and its +-1 circulant is not the multiplier used here).
+"""
+from __future__ import annotations
+
+import ctypes
+import itertools
+import os
+from fractions import Fraction
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64 = ctypes.c_int64
+_u64 = ctypes.c_uint64
+
+KIND_GAUSSIAN, KIND_CIRCULANT, KIND_SPARSE = 0, 1, 2
+
+
+def lib():
+    """Loads (building first if needed) the oracle's shared library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.or_philox4x64_10.argtypes = [ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64)]
+        L.or_u53.argtypes = [_u64]
+        L.or_u53.restype = ctypes.c_double
+        L.or_log.argtypes = [ctypes.c_double]
+        L.or_log.restype = ctypes.c_double
+        L.or_gauss.argtypes = [_u64, _u64, _u64, _u64]
+        L.or_gauss.restype = ctypes.c_double
+        L.or_mult_dense.argtypes = [_i64, _u64, _u64, ctypes.c_double, _dp, _i64]
+        L.or_mult_circulant.argtypes = [_i64, _u64, _u64, ctypes.c_double, _dp]
+        L.or_mult_sparse.argtypes = [_i64, ctypes.c_int, _u64, _u64, ctypes.c_void_p, ctypes.c_void_p]
+        L.or_circulant_to_dense.argtypes = [_i64, _dp, _dp, _i64]
+        L.or_sparse_to_dense.argtypes = [_i64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, _dp, _i64]
+        L.or_matmul.argtypes = [_i64, _i64, _i64, _dp, _i64, _dp, _i64, _dp, _i64]
+        L.or_genp.argtypes = [_i64, _dp, _i64]
+        L.or_genp.restype = _i64
+        L.or_gepp.argtypes = [_i64, _dp, _i64, ctypes.c_void_p]
+        L.or_gepp.restype = _i64
+        for f in ("or_solve_lower_unit", "or_solve_upper", "or_solve_upper_T", "or_solve_lower_unit_T"):
+            getattr(L, f).argtypes = [_i64, _i64, _dp, _i64, _dp, _i64]
+        L.or_apply_piv.argtypes = [_i64, _i64, ctypes.c_void_p, _dp, _i64]
+        L.or_apply_piv_T.argtypes = [_i64, _i64, ctypes.c_void_p, _dp, _i64]
+        L.or_residual.argtypes = [_i64, _i64, _dp, _i64, _dp, _i64, _dp, _i64, _dp, _i64]
+        L.or_backward_error.argtypes = [_i64, _i64, _dp, _i64, _dp, _i64, _dp, _i64]
+        L.or_backward_error.restype = ctypes.c_double
+        L.or_circ_matmul.argtypes = [_i64, _i64, _dp, _i64, _dp, _dp, _i64]
+        L.or_sparse_matmul.argtypes = [_i64, _i64, ctypes.c_int, _dp, _i64, ctypes.c_void_p,
+                                       ctypes.c_void_p, _dp, _i64]
+        L.or_circ_apply.argtypes = [_i64, _i64, ctypes.c_int, _dp, _dp, _i64, _dp, _i64]
+        L.or_sparse_apply.argtypes = [_i64, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                      ctypes.c_void_p, _dp, _i64, _dp, _i64]
+        _lib = L
+    return _lib
+
+
+def _c(a: np.ndarray) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+# --------------------------------------------------------------------------
+# Random numbers and multipliers
+# --------------------------------------------------------------------------
+
+def philox4x64_10(ctr, key) -> np.ndarray:
+    """One Philox4x64-10 block (Salmon et al., SC'11) for counter and key."""
+    c = (_u64 * 4)(*[int(x) & (2**64 - 1) for x in ctr])
+    k = (_u64 * 2)(*[int(x) & (2**64 - 1) for x in key])
+    o = (_u64 * 4)()
+    lib().or_philox4x64_10(c, k, o)
+    return np.array(list(o), dtype=np.uint64)
+
+
+def log(s: float) -> float:
+    """The oracle's own natural log (atanh series), positive normal input."""
+    return lib().or_log(float(s))
+
+
+def gauss(seed: int, stream: int, tag: int, idx: int) -> float:
+    return lib().or_gauss(seed, stream, tag, idx)
+
+
+def multiplier(kind: int, n: int, seed: int, stream: int = 0, scale: float | None = None,
+               nnz: int = 4):
+    """The random multiplier G (Definition 3.2 / Sec. 2.3 / sparse reading).
+
+    Returns a dict with the structure (``G`` dense n x n always, plus ``g``
+    for a circulant, ``rows``/``signs`` for the sparse multiplier)."""
+    L = lib()
+    if kind == KIND_GAUSSIAN:
+        s = (1.0 / np.sqrt(float(n))) if scale is None else float(scale)
+        G = np.empty((n, n))
+        L.or_mult_dense(n, seed, stream, s, _p(G), n)
+        return {"kind": kind, "n": n, "G": G}
+    if kind == KIND_CIRCULANT:
+        s = 1.0 if scale is None else float(scale)
+        g = np.empty(n)
+        L.or_mult_circulant(n, seed, stream, s, _p(g))
+        out = {"kind": kind, "n": n, "g": g}
+        if n <= 4096:
+            G = np.empty((n, n))
+            L.or_circulant_to_dense(n, _p(g), _p(G), n)
+            out["G"] = G
+        return out
+    if kind == KIND_SPARSE:
+        rows = np.empty((nnz, n), dtype=np.int32)
+        signs = np.empty((nnz, n), dtype=np.int8)
+        L.or_mult_sparse(n, nnz, seed, stream, rows.ctypes.data, signs.ctypes.data)
+        out = {"kind": kind, "n": n, "rows": rows, "signs": signs, "nnz": nnz}
+        if n <= 4096:
+            G = np.empty((n, n))
+            L.or_sparse_to_dense(n, nnz, rows.ctypes.data, signs.ctypes.data, _p(G), n)
+            out["G"] = G
+        return out
+    raise ValueError(kind)
+
+
+# --------------------------------------------------------------------------
+# The method's steps
+# --------------------------------------------------------------------------
+
+def matmul(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    A, B = _c(A), _c(B)
+    m, k = A.shape
+    n = B.shape[1]
+    C = np.empty((m, n))
+    lib().or_matmul(m, k, n, _p(A), k, _p(B), n, _p(C), n)
+    return C
+
+
+def precondition(A: np.ndarray, M: dict, rows=None) -> np.ndarray:
+    """C = A G (Thm. 4.1, the MH product), by the definition of each kind.
+
+    ``rows`` restricts the product to a subset of rows of A (for sampled
+    checks at sizes where the full product is too slow)."""
+    A = _c(A if rows is None else A[rows])
+    m, n = A.shape
+    C = np.empty((m, M["n"]))
+    L = lib()
+    if M["kind"] == KIND_GAUSSIAN:
+        return matmul(A, M["G"])
+    if M["kind"] == KIND_CIRCULANT:
+        L.or_circ_matmul(m, n, _p(A), n, _p(_c(M["g"])), _p(C), n)
+        return C
+    L.or_sparse_matmul(m, n, M["nnz"], _p(A), n, M["rows"].ctypes.data, M["signs"].ctypes.data,
+                       _p(C), n)
+    return C
+
+
+def apply_multiplier(M: dict, Y: np.ndarray, trans: bool = False) -> np.ndarray:
+    """X = G Y (or G^T Y), Y of shape (n, nrhs), by the definition of G."""
+    Y = _c(Y)
+    n, nrhs = Y.shape
+    X = np.empty_like(Y)
+    L = lib()
+    if M["kind"] == KIND_GAUSSIAN:
+        return matmul(M["G"].T.copy() if trans else M["G"], Y)
+    if M["kind"] == KIND_CIRCULANT:
+        L.or_circ_apply(n, nrhs, int(trans), _p(_c(M["g"])), _p(Y), nrhs, _p(X), nrhs)
+        return X
+    L.or_sparse_apply(n, nrhs, int(trans), M["nnz"], M["rows"].ctypes.data, M["signs"].ctypes.data,
+                      _p(Y), nrhs, _p(X), nrhs)
+    return X
+
+
+def genp(C: np.ndarray):
+    """Unblocked GENP (Sec. 1.1), in place on a copy.  Returns (LU, step)
+    with step = -1 on success, else the first zero / non-finite pivot."""
+    LU = _c(C).copy()
+    n = LU.shape[0]
+    k = lib().or_genp(n, _p(LU), n)
+    return LU, int(k)
+
+
+def gepp(A: np.ndarray):
+    """GEPP with first-max tie-break.  Returns (LU, piv, step)."""
+    LU = _c(A).copy()
+    n = LU.shape[0]
+    piv = np.zeros(n, dtype=np.int64)
+    k = lib().or_gepp(n, _p(LU), n, piv.ctypes.data)
+    return LU, piv, int(k)
+
+
+def split_lu(LU: np.ndarray):
+    L = np.tril(LU, -1) + np.eye(LU.shape[0])
+    U = np.triu(LU)
+    return L, U
+
+
+def lu_solve(LU: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """y = U^{-1} L^{-1} B by forward then back substitution."""
+    Y = _c(B).copy()
+    if Y.ndim == 1:
+        Y = Y[:, None]
+    n, nrhs = Y.shape
+    L = lib()
+    L.or_solve_lower_unit(n, nrhs, _p(LU), n, _p(Y), nrhs)
+    L.or_solve_upper(n, nrhs, _p(LU), n, _p(Y), nrhs)
+    return Y
+
+
+def lu_solve_T(LU: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """y = L^{-T} U^{-T} B."""
+    Y = _c(B).copy()
+    n, nrhs = Y.shape
+    L = lib()
+    L.or_solve_upper_T(n, nrhs, _p(LU), n, _p(Y), nrhs)
+    L.or_solve_lower_unit_T(n, nrhs, _p(LU), n, _p(Y), nrhs)
+    return Y
+
+
+def gepp_solve(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """Definition-level solution x = A^{-1} B by GEPP (no multiplier)."""
+    LU, piv, k = gepp(A)
+    if k >= 0:
+        raise np.linalg.LinAlgError(f"singular at step {k}")
+    Y = _c(B).copy()
+    if Y.ndim == 1:
+        Y = Y[:, None]
+    n, nrhs = Y.shape
+    lib().or_apply_piv(n, nrhs, piv.ctypes.data, _p(Y), nrhs)
+    return lu_solve(LU, Y)
+
+
+def gepp_solve_T(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """x = A^{-T} B by GEPP on A^T (independent of any multiplier)."""
+    return gepp_solve(_c(A).T.copy(), B)
+
+
+def residual(A, X, B) -> np.ndarray:
+    A, X, B = _c(A), _c(X), _c(B)
+    n, nrhs = X.shape
+    R = np.empty_like(X)
+    lib().or_residual(n, nrhs, _p(A), n, _p(X), nrhs, _p(B), nrhs, _p(R), nrhs)
+    return R
+
+
+def backward_error(A, X, B) -> float:
+    """max over columns of ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf)."""
+    A, X, B = _c(A), _c(X), _c(B)
+    if X.ndim == 1:
+        X, B = X[:, None], B[:, None]
+    n, nrhs = X.shape
+    return lib().or_backward_error(n, nrhs, _p(A), n, _p(X), nrhs, _p(B), nrhs)
+
+
+def rel_residual_2(A, X, B) -> float:
+    """Table 7.1's measure ||A y - b|| / ||b|| in the 2-norm (Sec. 2.4)."""
+    R = residual(A, _c(X).reshape(len(X), -1), _c(B).reshape(len(B), -1))
+    return float(np.linalg.norm(R) / np.linalg.norm(B))
+
+
+def solve(A: np.ndarray, B: np.ndarray, M: dict, refine_steps: int = 0, tol: float = 0.0):
+    """The whole method: C = A G, GENP(C), y = U^-1 L^-1 b, x = G y, then up
+    to ``refine_steps`` refinement steps r = b - A x, C d = r, x += G d,
+    stopping early when the backward error reaches ``tol`` or stops halving.
+
+    Returns dict(x, LU, step, eta) with eta the backward errors after the
+    solve and after each refinement step."""
+    B2 = _c(B).reshape(B.shape[0], -1)
+    C = precondition(A, M)
+    LU, step = genp(C)
+    out = {"LU": LU, "step": step, "C": C}
+    if step >= 0:
+        out.update(x=None, eta=[np.inf])
+        return out
+    X = apply_multiplier(M, lu_solve(LU, B2))
+    eta = [backward_error(A, X, B2)]
+    for _ in range(refine_steps):
+        if eta[-1] <= tol:
+            break
+        R = residual(A, X, B2)
+        D = apply_multiplier(M, lu_solve(LU, R))
+        X = X + D
+        eta.append(backward_error(A, X, B2))
+        if eta[-1] > eta[-2] / 2:
+            break
+    out.update(x=X, eta=eta)
+    return out
+
+
+def adjoint(A: np.ndarray, X: np.ndarray, gX: np.ndarray):
+    """Gradient of a loss l(X) with X = A^{-1} B given gX = dl/dX:
+    lambda = A^{-T} gX (by GEPP on A^T, independent of the multiplier),
+    dA = -lambda X^T, dB = lambda."""
+    lam = gepp_solve_T(A, gX)
+    dA = -matmul(lam, _c(X).T.copy())
+    return dA, lam
+
+
+# --------------------------------------------------------------------------
+# Exact references used by the pins
+# --------------------------------------------------------------------------
+
+def det_leibniz(M) -> Fraction:
+    """det(M) = sum over permutations of sign(p) prod_i m[i, p(i)], exact in
+    rationals (every double is a rational).  n <= 7."""
+    n = len(M)
+    F = [[Fraction(float(M[i][j])) for j in range(n)] for i in range(n)]
+    total = Fraction(0)
+    for perm in itertools.permutations(range(n)):
+        inv = sum(1 for i in range(n) for j in range(i + 1, n) if perm[i] > perm[j])
+        term = Fraction(-1 if inv % 2 else 1)
+        for i in range(n):
+            term *= F[i][perm[i]]
+            if term == 0:
+                break
+        total += term
+    return total

@@ -1,0 +1,353 @@
+#!/usr/bin/env python3
+"""Benchmark of randomized GENP on one GB300 (or N independent replicas).
+
+One step = one pass of the whole method over one system, every step of it
+in libgenp's kernels, called through the C ABI:
+  a1 redraw the random multiplier G (new seed each step, no allocation)
+  a2 C = A G
+  a3-a5 blocked GENP of C (panel, TRSM, Schur update)
+  a6-a7 L U y = B, X = G y
+  a8 FP64 iterative refinement until the backward error is <= 1e-14
+  a9 adjoint for the loss 0.5 ||X||_F^2 (gX = X): dA = -Lambda X^T, dB = Lambda
+The default workload is the n = 8192 FP64 system with a dense Gaussian
+N(0, 1/n) multiplier and 16 right-hand sides; A, G and C are 512 MiB each,
+larger than L2, so no flush is needed between steps.
+
+`--impl reference` times the CPU oracle (plain C, FP64) on a bounded sample
+of the same workload on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s & TFLOP/s (2n³/3), BF16+IR vs FP64 GENP, same GB300, bwd err ≤1e-14"
+KINDS = {"gaussian": 0, "circulant": 1, "sparse": 2}
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=8)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=8192)
+    p.add_argument("--nrhs", type=int, default=16)
+    p.add_argument("--kind", default="gaussian", choices=list(KINDS))
+    p.add_argument("--seed", type=int, default=0)
+    p.add_argument("--tol", type=float, default=1e-14)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-clocks", action="store_true")
+    return p.parse_args()
+
+
+def workload_name(a):
+    return f"genp_fp64_n{a.n}_{a.kind}_{a.nrhs}rhs"
+
+
+def flops_per_solve(a):
+    n = a.n
+    fact = 2.0 * n**3 / 3.0
+    if a.kind == "gaussian":
+        ag = 2.0 * n**3
+    elif a.kind == "circulant":
+        ag = 2 * 5.0 * n * n * math.log2(n)      # forward + inverse complex FFT per row pair
+    else:
+        ag = 2.0 * 4 * n * n
+    return fact, ag
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int, enabled: bool):
+        self.index, self.enabled, self.proc, self.path = index, enabled, None, None
+
+    def __enter__(self):
+        if self.enabled:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            try:
+                self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                              "--format=csv,noheader,nounits", "-lms", "200"],
+                                             stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            except OSError:
+                self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle (CPU)
+
+def oracle_sample(a, n_sample: int, repeats: int):
+    """The oracle's whole pipeline on an n_sample system of the same recipe;
+    returns (seconds per solve, threads)."""
+    import numpy as np
+
+    import oracle
+    import workloads as W
+    lead = max(2, 64 * n_sample // a.n)          # same recipe: leading block n/128, rank half of it
+    A, _, B = W.lead_deficient(n_sample, lead, lead // 2, a.nrhs, seed=a.seed)
+    A, B = A.numpy(), B.numpy()
+    oracle.lib()
+    times = []
+    for r in range(repeats):
+        t0 = time.perf_counter()
+        M = oracle.multiplier(KINDS[a.kind], n_sample, seed=r + 1)
+        res = oracle.solve(A, B, M, refine_steps=10, tol=a.tol)
+        x = res["x"]
+        oracle.adjoint(A, x, x)
+        times.append(time.perf_counter() - t0)
+    threads = len(os.sched_getaffinity(0))
+    return statistics.median(times), threads, res["eta"][-1]
+
+
+def run_reference(a):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    n_s = min(a.n, 2048)
+    scale = (a.n / n_s) ** 3
+    sec = []
+    for i in range(a.warmup + a.steps):
+        t, threads, eta = oracle_sample(a, n_s, 1)
+        if i >= a.warmup:
+            sec.append(t * scale)
+    per = statistics.mean(sec)
+    value = 1.0 / per
+    sample = (f"oracle pipeline (multiplier, A G, GENP, solves, FP64 refinement, adjoint) on an n={n_s} system of "
+              f"the same recipe, {a.nrhs} RHS; time scaled by (n/{n_s})^3 to n={a.n}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "n": a.n, "nrhs": a.nrhs, "multiplier": a.kind,
+                       "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "bwd_err": eta}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ ours (GPU)
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1212_4560_gb300 as genp
+    import workloads as W
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1212_4560_gb300 import build as _b
+    _b.build()
+
+    n, nrhs = a.n, a.nrhs
+    A_cpu, _, B_cpu = W.lead_deficient(n, 64, 32, nrhs, seed=a.seed + rank)
+    A = A_cpu.to(dev)
+    B = B_cpu.to(dev)
+    C = torch.empty((n, n), dtype=torch.float64, device=dev)
+    X = torch.empty((n, nrhs), dtype=torch.float64, device=dev)
+    dA = torch.empty((n, n), dtype=torch.float64, device=dev)
+    dB = torch.empty((n, nrhs), dtype=torch.float64, device=dev)
+    kind = KINDS[a.kind]
+    G = genp.make_multiplier(kind, n, seed=1, stream_id=rank)
+    genp.precondition(G, A, C)
+    F = genp.factor(C)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i, ev=None):
+        def mark(k):
+            if ev is not None:
+                ev[k].record(stream)
+        mark(0)
+        genp.redraw_multiplier(G, seed=1000 + i, stream_id=rank)
+        mark(1)
+        genp.precondition(G, A, C)
+        mark(2)
+        genp.refactor(F, C)
+        mark(3)
+        genp.solve(F, G, B, X)
+        mark(4)
+        genp.refine(A, F, G, B, X, tol=a.tol, max_iter=10)
+        mark(5)
+        genp.adjoint(F, G, X, X, dA, dB)
+        mark(6)
+
+    for i in range(a.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    info_w = genp.info_fetch(F)
+
+    phases = ["multiplier", "precondition", "factor", "solve", "refine", "adjoint"]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(a.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = genp.launch_count()
+    etas, iters = [], []
+    with ClockSampler(local, not a.no_clocks and rank == 0) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for i in range(a.steps):
+            step(a.warmup + i, evs[i])
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    launches = genp.launch_count() - l0
+    if world > 1:
+        dist.barrier()
+    total_ms = t_start.elapsed_time(t_end)
+    info = genp.info_fetch(F)
+    phase_ms = {p: sum(evs[i][k].elapsed_time(evs[i][k + 1]) for i in range(a.steps)) / a.steps
+                for k, p in enumerate(phases)}
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / a.steps
+    value = world * a.steps / (total_ms / 1e3)
+    fact, ag = flops_per_solve(a)
+    tflops = world * (fact + ag) * a.steps / (total_ms / 1e3) / 1e12
+
+    # e2e: the same step through the C ABI with the system in pinned HOST memory;
+    # the copies in (A, B) and out (X) sit inside the timed region.
+    e2e = None
+    if not a.no_e2e:
+        A_h = A_cpu.pin_memory()
+        B_h = B_cpu.pin_memory()
+        X_h = torch.empty((n, nrhs), dtype=torch.float64).pin_memory()
+        k_e2e = max(2, min(a.steps, 4))
+        for i in range(1):
+            A.copy_(A_h, non_blocking=True)
+            B.copy_(B_h, non_blocking=True)
+            step(10_000 + i)
+            X_h.copy_(X, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(k_e2e):
+            A.copy_(A_h, non_blocking=True)
+            B.copy_(B_h, non_blocking=True)
+            step(20_000 + i)
+            X_h.copy_(X, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": world * k_e2e / (e_ms / 1e3), "unit": "solves/s",
+               "h2d_bytes_per_step": A_h.numel() * 8 + B_h.numel() * 8, "d2h_bytes_per_step": X_h.numel() * 8,
+               "steps": k_e2e}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # dominant kernel: the DFMA GEMM of C = A G (one launch per precondition call)
+    if a.kind == "gaussian":
+        achieved = 2.0 * n**3 / (phase_ms["precondition"] / 1e3) / 1e12
+        roofline = {"kernel": "k_gemm<double,64,64,16,4,4> (C = A G)", "bound": "alu", "achieved": achieved,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 has no tensor-core path)",
+                    "traffic": None}
+    else:
+        achieved = (fact) / (phase_ms["factor"] / 1e3) / 1e12
+        roofline = {"kernel": "GENP factor (Schur GEMM dominant)", "bound": "alu", "achieved": achieved,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz", "traffic": None}
+    cpu = None
+    if not a.no_cpu_baseline and world == 1:
+        n_s = min(n, 2048)
+        t, threads, _ = oracle_sample(a, n_s, 3)
+        cpu = {"value": 1.0 / (t * (n / n_s) ** 3), "unit": "solves/s", "cores": threads, "kind": "oracle",
+               "sample": f"oracle pipeline (multiplier, A G, GENP, solves, refinement, adjoint) on an n={n_s} "
+                         f"system of the same recipe ({nrhs} RHS), median of 3, time scaled by (n/{n_s})^3 to n={n}"}
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "n": n, "nrhs": nrhs, "multiplier": a.kind, "precision": "fp64",
+                       "A": "N(0,1) with leading 64x64 block of rank 32", "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "tflops": tflops, "tflops_counted": {"factor_2n3_over_3": fact, "AG": ag},
+            "phases_ms": phase_ms, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "gpu_launches_per_step": launches / a.steps,
+            "bwd_err": info.bwd_err[-1] if info.bwd_err else None, "refine_iters": info.refine_iters,
+            "breakdown_step": info.breakdown_step, "growth": info.growth, "status": info.status,
+            "warmup_bwd_err": info_w.bwd_err[-1] if info_w.bwd_err else None}
+    if not a.no_clocks:
+        line["clocks"] = clk.summary()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * genp.h -- C ABI of libgenp: Gaussian elimination with no pivoting made
+ * numerically safe by a random multiplier, on one GB300 (sm_103a) GPU.
+ *
+ * The method (Pan & Qian, "More on the Power of Randomized Matrix
+ * Multiplication", Sec. 1.1 and Cor. 4.1): to solve A x = b for a
+ * nonsingular, well conditioned A whose leading blocks may be singular or
+ * ill conditioned, draw a random multiplier G, form C = A G, factor C = L U
+ * by GENP (no row or column interchange), solve L U y = b and return
+ * x = G y (so A x = A G y = C y = b).  Theorem 4.1 (the MH form with M = A,
+ * H = G) and Corollary 4.1 bound the conditioning of C and of all of its
+ * leading blocks in terms of that of A; Theorem 2.2 then bounds every pivot.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are row-major with an explicit leading dimension (element
+ *    (i, j) of X lives at X[i*ldx + j]); ld >= number of columns.
+ *  - Every matrix/vector pointer is a DEVICE pointer owned by the caller
+ *    (the library never frees it and keeps no reference past the call,
+ *    except genp_factors, which refers to the caller's C buffer until it is
+ *    destroyed or refactored).
+ *  - `cuda_stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls only enqueue work on that stream and return; they do
+ *    not synchronize, except genp_info_fetch and the *_destroy calls.
+ *  - Argument errors are detected on the host and returned at once
+ *    (GENP_ERR_ARG) with nothing enqueued.  Conditions found on the device
+ *    (a zero or non-finite pivot, refinement that does not converge) are
+ *    written to a status word inside the factors handle and reported by
+ *    genp_info_fetch.  The library never aborts the process and its kernels
+ *    never trap.
+ *  - Handles are opaque and library-owned; a handle may be used from one
+ *    stream at a time.
+ */
+#ifndef GENP_H
+#define GENP_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GENP_API __attribute__((visibility("default")))
+#else
+#define GENP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GENP_OK = 0,
+    GENP_ERR_ARG = -1,         /* invalid argument; nothing was enqueued            */
+    GENP_ERR_BREAKDOWN = -2,   /* GENP met a zero or non-finite pivot (Sec. 1.1)    */
+    GENP_ERR_NOCONV = -3,      /* refinement stopped above the requested tolerance */
+    GENP_ERR_CUDA = -4,        /* a CUDA runtime call failed                        */
+    GENP_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up                */
+    GENP_ERR_NOMEM = -6,       /* device memory could not be allocated              */
+    GENP_ERR_UNSUPPORTED = -7  /* valid combination that this build does not offer  */
+} genp_status;
+
+/* Random multiplier families.
+ *  GAUSSIAN:    dense G with iid N(0, scale^2) entries (Definition 3.2,
+ *               the set G_{0,scale}^{n x n}).
+ *  CIRCULANT:   G[i][j] = g[(i - j) mod n] with iid N(0, scale^2) first
+ *               column g (Sec. 2.3 and Definition 3.2, Z_{0,scale}).
+ *  SPARSE_PM1:  G = sum_{t < nnz} D_t P_t, P_t independent uniform random
+ *               permutation matrices, D_t random +-1 diagonals, so every
+ *               column and every row holds nnz signed unit entries
+ *               (coinciding positions add).  The paper names sparse
+ *               multipliers (Sec. 1 and Sec. 8) without fixing a structure;
+ *               this is the structure the library uses. */
+typedef enum {
+    GENP_MULT_GAUSSIAN = 0,
+    GENP_MULT_CIRCULANT = 1,
+    GENP_MULT_SPARSE_PM1 = 2
+} genp_mult_kind;
+
+/* Arithmetic of a factorization.
+ *  FP64: C and the factors are double; every step in FP64.
+ *  FP32: C and the factors are float; every step in FP32.
+ *  BF16: C and the factors are stored as float (the master copy); the
+ *        Schur-complement products use BF16 operands on the tensor cores
+ *        with FP32 accumulation; the diagonal blocks are factored in FP64.
+ *  FP8_E4M3: as BF16 with e4m3 operands and a power-of-two scale per
+ *        128 x 128 tile. */
+typedef enum {
+    GENP_FP64 = 0,
+    GENP_FP32 = 1,
+    GENP_BF16 = 2,
+    GENP_FP8_E4M3 = 3
+} genp_prec;
+
+typedef struct genp_multiplier genp_multiplier;
+typedef struct genp_factors genp_factors;
+
+#define GENP_MAX_REFINE 32
+
+/* Host-side report filled by genp_info_fetch. */
+typedef struct {
+    int32_t status;              /* GENP_OK, GENP_ERR_BREAKDOWN or GENP_ERR_NOCONV       */
+    int32_t refine_iters;        /* refinement steps taken by the last genp_refine      */
+    int64_t breakdown_step;      /* first step with a zero / non-finite pivot, else -1  */
+    double min_abs_pivot;        /* min_k |u_kk|                                         */
+    double max_abs_pivot;        /* max_k |u_kk|                                         */
+    double growth;               /* max|U| / max|C|                                      */
+    double bwd_err[GENP_MAX_REFINE + 1]; /* backward error before refinement and after  */
+                                 /* each step of the last genp_refine (see genp_refine) */
+} genp_info;
+
+/* Library version string, e.g. "genp 0.1 sm_103a". */
+GENP_API const char *genp_version(void);
+
+/* Human-readable name of a status code. */
+GENP_API const char *genp_status_string(genp_status s);
+
+/* Draws a random multiplier from a counter-based generator (Philox4x64-10,
+ * key = (seed, stream_id)); the same (kind, n, seed, stream_id, scale,
+ * nnz_per_col, value_grid) always yields the same G bit for bit.
+ *  kind        GENP_MULT_*.
+ *  n           order of G, 1 <= n <= 2^31 - 1 (dense: n*n*8 bytes of storage).
+ *  scale       standard deviation of the Gaussian entries (Gaussian and
+ *              circulant; e.g. 1/sqrt(n) for variance 1/n); ignored for SPARSE.
+ *  nnz_per_col signed entries per column for SPARSE (1..16); ignored otherwise.
+ *  value_grid  GENP_FP64: entries as drawn.  GENP_BF16: every entry rounded
+ *              to the nearest BF16 value (Thm. 4.1 allows a perturbed
+ *              Gaussian H = H' + V), so the tensor-core product and the FP64
+ *              correction x += G d use exactly the same G.  SPARSE ignores it.
+ *  out         receives the handle; the library owns G's device storage.
+ * Errors: GENP_ERR_ARG, GENP_ERR_NOMEM, GENP_ERR_CUDA. */
+GENP_API genp_status genp_make_multiplier(genp_mult_kind kind, int64_t n, uint64_t seed, uint64_t stream_id,
+                                 double scale, int nnz_per_col, genp_prec value_grid,
+                                 void *cuda_stream, genp_multiplier **out);
+
+/* Redraws G in place with a new (seed, stream_id), keeping kind, n, scale,
+ * nnz and grid; allocates nothing, so it may run inside a timed or captured
+ * region.  This is the paper's recovery rule too (Sec. 5, Remark B.1): on a
+ * failure, apply the method again with fresh random parameters.
+ * The result equals genp_make_multiplier with the new seed bit for bit.
+ * Errors: GENP_ERR_ARG, GENP_ERR_CUDA. */
+GENP_API genp_status genp_redraw_multiplier(genp_multiplier *G, uint64_t seed, uint64_t stream_id,
+                                            void *cuda_stream);
+
+/* Copies G's description into caller device buffers (any may be NULL):
+ *  dense      n x n (ld ldd) double: the full matrix G (every kind).
+ *  first_col  n doubles: g (CIRCULANT only).
+ *  rows       nnz*n int32: row of the t-th entry of column j at [t*n + j] (SPARSE).
+ *  signs      nnz*n int8: its sign (SPARSE). */
+GENP_API genp_status genp_multiplier_export(const genp_multiplier *G, double *dense, int64_t ldd,
+                                   double *first_col, int32_t *rows, int8_t *signs,
+                                   void *cuda_stream);
+
+/* Order, kind and nnz of a multiplier (host-side, no device work). */
+GENP_API genp_status genp_multiplier_query(const genp_multiplier *G, int64_t *n, int *kind, int *nnz_per_col);
+
+/* Frees G (cudaFree waits for work still using it). NULL is ignored. */
+GENP_API void genp_multiplier_destroy(genp_multiplier *G);
+
+/* C = A G  (Thm. 4.1, the MH product; Cor. 4.1).
+ *  A      n x n, ld lda; double if a_prec == GENP_FP64, float if GENP_FP32.
+ *  C      n x n, ld ldc; double if c_prec == GENP_FP64, else float.  C must
+ *         not overlap A.
+ *  c_prec the factorization the product is for: FP64 (DFMA), FP32 (FFMA),
+ *         BF16 (tensor cores, A rounded to BF16, G must have value_grid BF16).
+ * Dense G costs 2n^3 flops; a circulant G is applied by FFT in
+ * O(n^2 log n) (Thm. 2.1) when n is a power of two <= 8192; the sparse G is
+ * a signed gather of nnz columns per output column. */
+GENP_API genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t lda, genp_prec a_prec,
+                              void *C, int64_t ldc, genp_prec c_prec, void *cuda_stream);
+
+/* In-place GENP of C (Sec. 1.1; blocked form of block Gaussian elimination,
+ * Thm. 2.2): right-looking with block size nb (0 = library default):
+ * factor the nb x nb diagonal block, solve for the block row of U and the
+ * block column of L, update the trailing Schur complement
+ * A22 <- A22 - L21 U12, repeat.  On completion the strict lower triangle of
+ * C holds L (unit diagonal implied) and the upper triangle holds U.
+ *  C      n x n, ld ldc, double for FP64, float otherwise (caller-owned;
+ *         the handle refers to it until destroyed or refactored).
+ *  out    receives a new factors handle (status word and workspace).
+ * A zero or non-finite pivot does not stop the elimination; its step is
+ * recorded (genp_info.breakdown_step, status GENP_ERR_BREAKDOWN) and the
+ * factors are then meaningless.  No pivot threshold is applied. */
+GENP_API genp_status genp_factor(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t nb, void *cuda_stream,
+                        genp_factors **out);
+
+/* Factors a new matrix of the same order and precision into an existing
+ * handle, reusing its workspace (no allocation). */
+GENP_API genp_status genp_refactor(genp_factors *F, void *C, int64_t ldc, void *cuda_stream);
+
+/* Frees F (cudaFree waits for work still using it). NULL is ignored. */
+GENP_API void genp_factors_destroy(genp_factors *F);
+
+/* X = G U^{-1} L^{-1} B (Sec. 1.1: solve L U y = b, return x = G y).
+ *  B, X   n x nrhs double, ld ldb / ldx; X may alias B only if ldx == ldb.
+ *  The triangular solves run in the factor's precision, x = G y in FP64. */
+GENP_API genp_status genp_solve(const genp_factors *F, const genp_multiplier *G, const double *B, int64_t ldb,
+                       int64_t nrhs, double *X, int64_t ldx, void *cuda_stream);
+
+/* Iterative refinement in FP64 (Sec. 7.1; Table 7.1 shows one step):
+ *   repeat  r = B - A X (FP64);  C d = r (factor precision);  X += G d (FP64)
+ * with the normwise backward error of every column,
+ *   eta = ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf),
+ * measured before the first step and after each one.  Stops when
+ * max eta <= tol, when eta fails to halve, or after max_iter steps; the
+ * stop is decided on the device (no host synchronization).
+ *  A      the ORIGINAL n x n matrix in double (C = A G), ld lda.
+ *  X      on entry the solution of genp_solve, on exit the refined one.
+ *  method 0 = classic refinement (the only method of this build).
+ * genp_info.bwd_err / refine_iters report the history; status
+ * GENP_ERR_NOCONV if the final eta is above tol. */
+GENP_API genp_status genp_refine(const double *A, int64_t lda, const genp_factors *F, const genp_multiplier *G,
+                        const double *B, int64_t ldb, int64_t nrhs, double *X, int64_t ldx, double tol,
+                        int max_iter, int method, void *cuda_stream);
+
+/* Adjoint of X = A^{-1} B through the factors of C = A G: with gX = dl/dX,
+ *   Lambda = A^{-T} gX = L^{-T} U^{-T} G^T gX,   dA = -Lambda X^T,   dB = Lambda.
+ * (A^{-1} = G U^{-1} L^{-1}; the result does not depend on G in exact
+ * arithmetic.)
+ *  gX, X  n x nrhs double; dB n x nrhs double (may be NULL).
+ *  dA     n x n, ld ldda, double for FP64 factors, float otherwise (may be NULL). */
+GENP_API genp_status genp_adjoint(const genp_factors *F, const genp_multiplier *G, const double *gX, int64_t ldg,
+                         const double *X, int64_t ldx, int64_t nrhs, void *dA, int64_t ldda, double *dB,
+                         int64_t lddb, void *cuda_stream);
+
+/* Number of kernels this library has launched in the process so far
+ * (diagnostics: lets a caller count the launches of a timed region). */
+GENP_API uint64_t genp_launch_count(void);
+
+/* Copies the device status of F to *out after synchronizing cuda_stream. */
+GENP_API genp_status genp_info_fetch(const genp_factors *F, genp_info *out, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GENP_H */

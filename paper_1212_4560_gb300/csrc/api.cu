@@ -1,0 +1,465 @@
+// api.cu -- the extern "C" entry points declared in include/genp.h.
+//
+// Every entry point checks its arguments on the host (returning
+// GENP_ERR_ARG with nothing enqueued), then only enqueues kernels on the
+// caller's stream.  Handles own their device storage; caller buffers are
+// never freed or retained (except the C buffer a factors handle refers to).
+#include "genp_internal.cuh"
+
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+#include <new>
+
+using namespace genp;
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+
+cudaStream_t S(void *p) { return static_cast<cudaStream_t>(p); }
+
+template <typename T>
+genp_status dalloc(T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return GENP_OK;
+    if (cudaMalloc((void **)p, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return GENP_ERR_NOMEM;
+    }
+    return GENP_OK;
+}
+
+#define TRY(expr)                                        \
+    do {                                                 \
+        genp_status st_ = (expr);                        \
+        if (st_ != GENP_OK) return st_;                  \
+    } while (0)
+#define CU(expr)                                         \
+    do {                                                 \
+        if ((expr) != cudaSuccess) {                     \
+            cudaGetLastError();                          \
+            return GENP_ERR_CUDA;                        \
+        }                                                \
+    } while (0)
+
+void free_multiplier(genp_multiplier *G) {
+    cudaFree(G->dense);
+    cudaFree(G->dense_f32);
+    cudaFree(G->dense_bf16);
+    cudaFree(G->g);
+    cudaFree(G->spec);
+    cudaFree(G->spec_f32);
+    cudaFree(G->twid);
+    cudaFree(G->twid_f32);
+    cudaFree(G->rows);
+    cudaFree(G->signs);
+    cudaFree(G->inv_rows);
+    cudaFree(G->inv_signs);
+    cudaFree(G->draws);
+    delete G;
+}
+
+// Enqueues the draw of G's entries from (seed, stream_id) into its storage.
+cudaError_t draw_multiplier(genp_multiplier *G, uint64_t seed, uint64_t stream_id, cudaStream_t s) {
+    switch (G->kind) {
+        case GENP_MULT_GAUSSIAN:
+            return launch_make_dense(G->dense, G->n, seed, stream_id, G->scale, G->grid, G->dense_f32, G->dense_bf16,
+                                     s);
+        case GENP_MULT_CIRCULANT: {
+            cudaError_t e = launch_make_circulant(G->g, G->n, seed, stream_id, G->scale, G->grid, s);
+            return e == cudaSuccess ? circ_prepare(G, s) : e;
+        }
+        case GENP_MULT_SPARSE_PM1:
+            return launch_make_sparse(G->rows, G->signs, G->inv_rows, G->inv_signs, G->draws, G->n, G->nnz, seed,
+                                      stream_id, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+bool factor_prec_ok(genp_prec p) { return p == GENP_FP64 || p == GENP_FP32; }
+
+// Grows the factors workspace to at least `bytes` (synchronizes the stream
+// only when it actually has to grow).
+genp_status ensure_work(genp_factors *F, size_t bytes, cudaStream_t s) {
+    if (F->work_bytes >= bytes) return GENP_OK;
+    if (F->work) {
+        CU(cudaStreamSynchronize(s));
+        cudaFree(F->work);
+        F->work = nullptr;
+        F->work_bytes = 0;
+    }
+    if (cudaMalloc(&F->work, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        F->work = nullptr;
+        return GENP_ERR_NOMEM;
+    }
+    F->work_bytes = bytes;
+    return GENP_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+namespace genp {
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+cudaError_t apply_multiplier(const genp_multiplier *G, bool trans, const double *Y, int64_t ldy, double *X,
+                             int64_t ldx, int64_t nrhs, bool accumulate, const int *skip, cudaStream_t s) {
+    switch (G->kind) {
+        case GENP_MULT_GAUSSIAN:
+            return gemm<double>(G->n, nrhs, G->n, 1.0, G->dense, G->n, trans, Y, ldy, accumulate ? 1.0 : 0.0, X, ldx,
+                                X, ldx, skip, s);
+        case GENP_MULT_CIRCULANT:
+            if (circ_fft_supported(G->n))
+                return circ_apply_cols(G, trans, Y, ldy, X, ldx, nrhs, accumulate, skip, s);
+            return circ_apply_direct(G->g, G->n, trans, Y, ldy, X, ldx, nrhs, accumulate, skip, s);
+        case GENP_MULT_SPARSE_PM1:
+            return sparse_apply(G, trans, Y, ldy, X, ldx, nrhs, accumulate, skip, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace genp
+
+extern "C" {
+
+const char *genp_version(void) { return "genp 0.1 sm_103a"; }
+
+const char *genp_status_string(genp_status s) {
+    switch (s) {
+        case GENP_OK: return "GENP_OK";
+        case GENP_ERR_ARG: return "GENP_ERR_ARG: invalid argument";
+        case GENP_ERR_BREAKDOWN: return "GENP_ERR_BREAKDOWN: zero or non-finite pivot";
+        case GENP_ERR_NOCONV: return "GENP_ERR_NOCONV: refinement did not reach the tolerance";
+        case GENP_ERR_CUDA: return "GENP_ERR_CUDA: CUDA runtime error";
+        case GENP_ERR_TIMEOUT: return "GENP_ERR_TIMEOUT: bounded device wait gave up";
+        case GENP_ERR_NOMEM: return "GENP_ERR_NOMEM: device allocation failed";
+        case GENP_ERR_UNSUPPORTED: return "GENP_ERR_UNSUPPORTED: combination not offered by this build";
+    }
+    return "unknown genp status";
+}
+
+genp_status genp_make_multiplier(genp_mult_kind kind, int64_t n, uint64_t seed, uint64_t stream_id, double scale,
+                                 int nnz_per_col, genp_prec value_grid, void *cuda_stream, genp_multiplier **out) {
+    if (!out) return GENP_ERR_ARG;
+    *out = nullptr;
+    if (n < 1 || n > 2147483647LL) return GENP_ERR_ARG;
+    if (kind != GENP_MULT_GAUSSIAN && kind != GENP_MULT_CIRCULANT && kind != GENP_MULT_SPARSE_PM1) return GENP_ERR_ARG;
+    if (kind != GENP_MULT_SPARSE_PM1 && !(scale > 0.0 && isfinite(scale))) return GENP_ERR_ARG;
+    if (kind == GENP_MULT_SPARSE_PM1 && (nnz_per_col < 1 || nnz_per_col > 16)) return GENP_ERR_ARG;
+    if (value_grid != GENP_FP64 && value_grid != GENP_FP32 && value_grid != GENP_BF16) return GENP_ERR_ARG;
+    cudaStream_t s = S(cuda_stream);
+    genp_multiplier *G = new (std::nothrow) genp_multiplier();
+    if (!G) return GENP_ERR_NOMEM;
+    G->kind = kind;
+    G->n = n;
+    G->nnz = kind == GENP_MULT_SPARSE_PM1 ? nnz_per_col : 0;
+    G->grid = kind == GENP_MULT_SPARSE_PM1 ? GENP_FP64 : value_grid;
+    G->scale = kind == GENP_MULT_SPARSE_PM1 ? 1.0 : scale;
+    G->last_stream = s;
+    genp_status st = GENP_OK;
+    cudaError_t ce = cudaSuccess;
+    if (kind == GENP_MULT_GAUSSIAN) {
+        st = dalloc(&G->dense, (size_t)n * n);
+        if (st == GENP_OK && value_grid != GENP_FP64) st = dalloc(&G->dense_f32, (size_t)n * n);
+        if (st == GENP_OK && value_grid == GENP_BF16) st = dalloc(&G->dense_bf16, (size_t)n * n);
+    } else if (kind == GENP_MULT_CIRCULANT) {
+        st = dalloc(&G->g, (size_t)n);
+        if (st == GENP_OK && circ_fft_supported(n)) {
+            st = dalloc(&G->spec, (size_t)n);
+            if (st == GENP_OK) st = dalloc(&G->spec_f32, (size_t)n);
+            if (st == GENP_OK) st = dalloc(&G->twid, (size_t)(n / 2));
+            if (st == GENP_OK) st = dalloc(&G->twid_f32, (size_t)(n / 2));
+        }
+    } else {
+        const size_t cnt = (size_t)n * nnz_per_col;
+        st = dalloc(&G->rows, cnt);
+        if (st == GENP_OK) st = dalloc(&G->signs, cnt);
+        if (st == GENP_OK) st = dalloc(&G->inv_rows, cnt);
+        if (st == GENP_OK) st = dalloc(&G->inv_signs, cnt);
+        if (st == GENP_OK) st = dalloc(&G->draws, cnt);
+    }
+    if (st == GENP_OK) ce = draw_multiplier(G, seed, stream_id, s);
+    if (st == GENP_OK && ce != cudaSuccess) {
+        cudaGetLastError();
+        st = GENP_ERR_CUDA;
+    }
+    if (st != GENP_OK) {
+        free_multiplier(G);
+        return st;
+    }
+    *out = G;
+    return GENP_OK;
+}
+
+genp_status genp_redraw_multiplier(genp_multiplier *G, uint64_t seed, uint64_t stream_id, void *cuda_stream) {
+    if (!G) return GENP_ERR_ARG;
+    G->last_stream = S(cuda_stream);
+    CU(draw_multiplier(G, seed, stream_id, S(cuda_stream)));
+    return GENP_OK;
+}
+
+uint64_t genp_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+genp_status genp_multiplier_export(const genp_multiplier *G, double *dense, int64_t ldd, double *first_col,
+                                   int32_t *rows, int8_t *signs, void *cuda_stream) {
+    if (!G) return GENP_ERR_ARG;
+    if (dense && ldd < G->n) return GENP_ERR_ARG;
+    if (first_col && G->kind != GENP_MULT_CIRCULANT) return GENP_ERR_ARG;
+    if ((rows || signs) && G->kind != GENP_MULT_SPARSE_PM1) return GENP_ERR_ARG;
+    cudaStream_t s = S(cuda_stream);
+    const int64_t n = G->n;
+    if (dense) {
+        if (G->kind == GENP_MULT_GAUSSIAN)
+            CU(cudaMemcpy2DAsync(dense, ldd * sizeof(double), G->dense, n * sizeof(double), n * sizeof(double), n,
+                                 cudaMemcpyDeviceToDevice, s));
+        else if (G->kind == GENP_MULT_CIRCULANT)
+            CU(launch_circulant_to_dense(G->g, n, dense, ldd, s));
+        else
+            CU(launch_sparse_to_dense(G->rows, G->signs, n, G->nnz, dense, ldd, s));
+    }
+    if (first_col) CU(cudaMemcpyAsync(first_col, G->g, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (rows) CU(cudaMemcpyAsync(rows, G->rows, (size_t)n * G->nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    if (signs) CU(cudaMemcpyAsync(signs, G->signs, (size_t)n * G->nnz, cudaMemcpyDeviceToDevice, s));
+    return GENP_OK;
+}
+
+genp_status genp_multiplier_query(const genp_multiplier *G, int64_t *n, int *kind, int *nnz_per_col) {
+    if (!G) return GENP_ERR_ARG;
+    if (n) *n = G->n;
+    if (kind) *kind = (int)G->kind;
+    if (nnz_per_col) *nnz_per_col = G->nnz;
+    return GENP_OK;
+}
+
+void genp_multiplier_destroy(genp_multiplier *G) {
+    if (G) free_multiplier(G);
+}
+
+genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t lda, genp_prec a_prec, void *C,
+                              int64_t ldc, genp_prec c_prec, void *cuda_stream) {
+    if (!G || !A || !C) return GENP_ERR_ARG;
+    const int64_t n = G->n;
+    if (lda < n || ldc < n) return GENP_ERR_ARG;
+    if (a_prec != GENP_FP64 && a_prec != GENP_FP32) return GENP_ERR_ARG;
+    if (c_prec == GENP_BF16 || c_prec == GENP_FP8_E4M3) return GENP_ERR_UNSUPPORTED;
+    if (c_prec != GENP_FP64 && c_prec != GENP_FP32) return GENP_ERR_ARG;
+    if (c_prec == GENP_FP64 && a_prec != GENP_FP64) return GENP_ERR_ARG;
+    cudaStream_t s = S(cuda_stream);
+    if (c_prec == GENP_FP64) {
+        const double *a = static_cast<const double *>(A);
+        double *c = static_cast<double *>(C);
+        switch (G->kind) {
+            case GENP_MULT_GAUSSIAN:
+                CU(gemm<double>(n, n, n, 1.0, a, lda, false, G->dense, n, 0.0, nullptr, 0, c, ldc, nullptr, s));
+                break;
+            case GENP_MULT_CIRCULANT:
+                if (circ_fft_supported(n)) CU((circ_apply<double, double>(G, 0, a, lda, 1, c, ldc, 1, n, nullptr, s)));
+                else CU((circ_matmul_direct<double, double>(G->g, n, a, lda, c, ldc, s)));
+                break;
+            case GENP_MULT_SPARSE_PM1: CU((sparse_precondition<double, double>(G, a, lda, c, ldc, s))); break;
+        }
+        return GENP_OK;
+    }
+    // FP32 factorization: C (float) = A G in FP32 arithmetic.
+    float *c = static_cast<float *>(C);
+    if (G->kind == GENP_MULT_SPARSE_PM1) {
+        if (a_prec == GENP_FP64) CU((sparse_precondition<double, float>(G, (const double *)A, lda, c, ldc, s)));
+        else CU((sparse_precondition<float, float>(G, (const float *)A, lda, c, ldc, s)));
+        return GENP_OK;
+    }
+    if (G->kind == GENP_MULT_CIRCULANT && circ_fft_supported(n)) {
+        if (a_prec == GENP_FP64) CU((circ_apply<double, float>(G, 0, (const double *)A, lda, 1, c, ldc, 1, n, nullptr, s)));
+        else CU((circ_apply<float, float>(G, 0, (const float *)A, lda, 1, c, ldc, 1, n, nullptr, s)));
+        return GENP_OK;
+    }
+    if (G->kind == GENP_MULT_GAUSSIAN && !G->dense_f32) return GENP_ERR_ARG;  // needs an FP32-exact G
+    const float *a32 = static_cast<const float *>(A);
+    int64_t lda32 = lda;
+    float *tmp = nullptr;
+    if (a_prec == GENP_FP64) {
+        CU(cudaMallocAsync((void **)&tmp, (size_t)n * n * sizeof(float), s));
+        CU((convert_matrix<double, float>((const double *)A, lda, tmp, n, n, n, nullptr, s)));
+        a32 = tmp;
+        lda32 = n;
+    }
+    if (G->kind == GENP_MULT_GAUSSIAN)
+        CU(gemm<float>(n, n, n, 1.0f, a32, lda32, false, G->dense_f32, n, 0.0f, nullptr, 0, c, ldc, nullptr, s));
+    else
+        CU((circ_matmul_direct<float, float>(G->g, n, a32, lda32, c, ldc, s)));
+    if (tmp) CU(cudaFreeAsync(tmp, s));
+    return GENP_OK;
+}
+
+genp_status genp_factor(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t nb, void *cuda_stream,
+                        genp_factors **out) {
+    if (!out) return GENP_ERR_ARG;
+    *out = nullptr;
+    if (!C || n < 1 || n > 2147483647LL || ldc < n) return GENP_ERR_ARG;
+    if (prec == GENP_BF16 || prec == GENP_FP8_E4M3) return GENP_ERR_UNSUPPORTED;
+    if (!factor_prec_ok(prec)) return GENP_ERR_ARG;
+    if (nb == 0) nb = 64;
+    if (nb < 1 || nb > 128) return GENP_ERR_ARG;
+    cudaStream_t s = S(cuda_stream);
+    genp_factors *F = new (std::nothrow) genp_factors();
+    if (!F) return GENP_ERR_NOMEM;
+    F->C = C;
+    F->n = n;
+    F->ldc = ldc;
+    F->nb = nb;
+    F->prec = prec;
+    F->last_stream = s;
+    genp_status st = dalloc(&F->st, 1);
+    if (st == GENP_OK) st = dalloc(&F->norms, 2);
+    if (st == GENP_OK && cudaMallocHost(&F->host_info, sizeof(DevStatus)) != cudaSuccess) {
+        cudaGetLastError();
+        F->host_info = nullptr;
+        st = GENP_ERR_NOMEM;
+    }
+    if (st == GENP_OK && cudaMemsetAsync(F->st, 0, sizeof(DevStatus), s) != cudaSuccess) st = GENP_ERR_CUDA;
+    if (st == GENP_OK && cudaMemsetAsync(F->norms, 0, 2 * sizeof(DevNorms), s) != cudaSuccess) st = GENP_ERR_CUDA;
+    if (st == GENP_OK && factor_run(F, s) != cudaSuccess) st = GENP_ERR_CUDA;
+    if (st != GENP_OK) {
+        cudaGetLastError();
+        genp_factors_destroy(F);
+        return st;
+    }
+    *out = F;
+    return GENP_OK;
+}
+
+genp_status genp_refactor(genp_factors *F, void *C, int64_t ldc, void *cuda_stream) {
+    if (!F || !C || ldc < F->n) return GENP_ERR_ARG;
+    F->C = C;
+    F->ldc = ldc;
+    F->last_stream = S(cuda_stream);
+    CU(factor_run(F, S(cuda_stream)));
+    return GENP_OK;
+}
+
+void genp_factors_destroy(genp_factors *F) {
+    if (!F) return;
+    cudaFree(F->st);
+    cudaFree(F->norms);
+    cudaFree(F->work);
+    if (F->host_info) cudaFreeHost(F->host_info);
+    delete F;
+}
+
+genp_status genp_solve(const genp_factors *F, const genp_multiplier *G, const double *B, int64_t ldb, int64_t nrhs,
+                       double *X, int64_t ldx, void *cuda_stream) {
+    if (!F || !G || !B || !X) return GENP_ERR_ARG;
+    if (G->n != F->n || nrhs < 1 || ldb < nrhs || ldx < nrhs) return GENP_ERR_ARG;
+    if (X == B && ldx != ldb) return GENP_ERR_ARG;
+    cudaStream_t s = S(cuda_stream);
+    genp_factors *Fm = const_cast<genp_factors *>(F);
+    const int64_t n = F->n;
+    const size_t yd = align256((size_t)n * nrhs * sizeof(double)), yf = align256((size_t)n * nrhs * sizeof(float));
+    TRY(ensure_work(Fm, yd + yf, s));
+    double *Y = static_cast<double *>(F->work);
+    float *Yf = reinterpret_cast<float *>(static_cast<char *>(F->work) + yd);
+    if (F->prec == GENP_FP64) {
+        CU((convert_matrix<double, double>(B, ldb, Y, nrhs, n, nrhs, nullptr, s)));
+        CU(lu_solve_inplace<double>(F, Y, nrhs, nrhs, false, nullptr, s));
+    } else {
+        CU((convert_matrix<double, float>(B, ldb, Yf, nrhs, n, nrhs, nullptr, s)));
+        CU(lu_solve_inplace<float>(F, Yf, nrhs, nrhs, false, nullptr, s));
+        CU((convert_matrix<float, double>(Yf, nrhs, Y, nrhs, n, nrhs, nullptr, s)));
+    }
+    CU(apply_multiplier(G, false, Y, nrhs, X, ldx, nrhs, false, nullptr, s));
+    Fm->last_stream = s;
+    return GENP_OK;
+}
+
+genp_status genp_refine(const double *A, int64_t lda, const genp_factors *F, const genp_multiplier *G, const double *B,
+                        int64_t ldb, int64_t nrhs, double *X, int64_t ldx, double tol, int max_iter, int method,
+                        void *cuda_stream) {
+    if (!A || !F || !G || !B || !X) return GENP_ERR_ARG;
+    const int64_t n = F->n;
+    if (G->n != n || lda < n || nrhs < 1 || ldb < nrhs || ldx < nrhs) return GENP_ERR_ARG;
+    if (max_iter < 0 || max_iter > GENP_MAX_REFINE || !(tol >= 0.0)) return GENP_ERR_ARG;
+    if (method != 0) return method == 1 ? GENP_ERR_UNSUPPORTED : GENP_ERR_ARG;
+    if (nrhs > kMaxRhsChunk) return GENP_ERR_UNSUPPORTED;
+    cudaStream_t s = S(cuda_stream);
+    genp_factors *Fm = const_cast<genp_factors *>(F);
+    const size_t rd = align256((size_t)n * nrhs * sizeof(double)), yf = align256((size_t)n * nrhs * sizeof(float));
+    TRY(ensure_work(Fm, rd + yf, s));
+    double *R = static_cast<double *>(F->work);
+    float *Rf = reinterpret_cast<float *>(static_cast<char *>(F->work) + rd);
+    const int *done = &F->st->refine_done;
+    CU(refine_init(Fm, A, lda, n, s));
+    for (int it = 0; it <= max_iter; ++it) {
+        CU(gemm<double>(n, nrhs, n, -1.0, A, lda, false, X, ldx, 1.0, B, ldb, R, nrhs, done, s));
+        CU(refine_check(Fm, R, nrhs, X, ldx, B, ldb, n, nrhs, it, tol, max_iter, 1, s));
+        if (it == max_iter) break;
+        if (F->prec == GENP_FP64) {
+            CU(lu_solve_inplace<double>(F, R, nrhs, nrhs, false, done, s));
+        } else {
+            CU((convert_matrix<double, float>(R, nrhs, Rf, nrhs, n, nrhs, done, s)));
+            CU(lu_solve_inplace<float>(F, Rf, nrhs, nrhs, false, done, s));
+            CU((convert_matrix<float, double>(Rf, nrhs, R, nrhs, n, nrhs, done, s)));
+        }
+        CU(apply_multiplier(G, false, R, nrhs, X, ldx, nrhs, true, done, s));
+    }
+    Fm->last_stream = s;
+    return GENP_OK;
+}
+
+genp_status genp_adjoint(const genp_factors *F, const genp_multiplier *G, const double *gX, int64_t ldg,
+                         const double *X, int64_t ldx, int64_t nrhs, void *dA, int64_t ldda, double *dB, int64_t lddb,
+                         void *cuda_stream) {
+    if (!F || !G || !gX) return GENP_ERR_ARG;
+    const int64_t n = F->n;
+    if (G->n != n || nrhs < 1 || ldg < nrhs) return GENP_ERR_ARG;
+    if (dA && (!X || ldx < nrhs || ldda < n)) return GENP_ERR_ARG;
+    if (dB && lddb < nrhs) return GENP_ERR_ARG;
+    cudaStream_t s = S(cuda_stream);
+    genp_factors *Fm = const_cast<genp_factors *>(F);
+    const size_t ld = align256((size_t)n * nrhs * sizeof(double)), yf = align256((size_t)n * nrhs * sizeof(float));
+    TRY(ensure_work(Fm, ld + yf, s));
+    double *Lam = static_cast<double *>(F->work);
+    float *Lf = reinterpret_cast<float *>(static_cast<char *>(F->work) + ld);
+    CU(apply_multiplier(G, true, gX, ldg, Lam, nrhs, nrhs, false, nullptr, s));
+    if (F->prec == GENP_FP64) {
+        CU(lu_solve_inplace<double>(F, Lam, nrhs, nrhs, true, nullptr, s));
+    } else {
+        CU((convert_matrix<double, float>(Lam, nrhs, Lf, nrhs, n, nrhs, nullptr, s)));
+        CU(lu_solve_inplace<float>(F, Lf, nrhs, nrhs, true, nullptr, s));
+        CU((convert_matrix<float, double>(Lf, nrhs, Lam, nrhs, n, nrhs, nullptr, s)));
+    }
+    if (dB) CU((convert_matrix<double, double>(Lam, nrhs, dB, lddb, n, nrhs, nullptr, s)));
+    if (dA) CU(outer_update(Lam, nrhs, X, ldx, n, nrhs, dA, ldda, F->prec != GENP_FP64, s));
+    Fm->last_stream = s;
+    return GENP_OK;
+}
+
+genp_status genp_info_fetch(const genp_factors *F, genp_info *out, void *cuda_stream) {
+    if (!F || !out) return GENP_ERR_ARG;
+    cudaStream_t s = S(cuda_stream);
+    CU(cudaMemcpyAsync(F->host_info, F->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    DevStatus h;
+    memcpy(&h, F->host_info, sizeof(h));
+    auto asd = [](unsigned long long b) {
+        double d;
+        memcpy(&d, &b, 8);
+        return d;
+    };
+    memset(out, 0, sizeof(*out));
+    out->breakdown_step = h.breakdown_step == ~0ull ? -1 : (int64_t)h.breakdown_step;
+    out->min_abs_pivot = asd(h.min_abs_pivot);
+    out->max_abs_pivot = asd(h.max_abs_pivot);
+    const double cmax = asd(h.max_abs_c);
+    out->growth = cmax > 0 ? asd(h.max_abs_u) / cmax : 0.0;
+    out->refine_iters = h.refine_iters;
+    for (int i = 0; i <= GENP_MAX_REFINE; ++i) out->bwd_err[i] = h.bwd_err[i];
+    out->status = out->breakdown_step >= 0 ? GENP_ERR_BREAKDOWN : h.refine_status;
+    return GENP_OK;
+}
+
+}  // extern "C"

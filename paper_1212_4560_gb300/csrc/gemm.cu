@@ -1,0 +1,196 @@
+// gemm.cu -- register-tiled CUDA-core GEMM, D = alpha * op(A) * B + beta * Cin.
+//
+// FP64 on GB300 runs at 4 flop/clk/SM on the CUDA cores (2 DFMA/clk/SM;
+// mma.sync .f64 measured slower) and there is no FP64 tcgen05 kind, so the
+// FP64 contractions of the method (the product A*G of Thm. 4.1 and the
+// Schur-complement update of block Gaussian elimination) are DFMA-bound:
+// one 64x64 tile per CTA, 4x4 outputs per thread, operand tiles staged in
+// shared memory with a register prefetch of the next K slice.  FP32 uses a
+// 128x128 tile with 8x8 outputs per thread (FFMA).  The A and B loaders can
+// also synthesise a circulant operand G[i][j] = g[(i-j) mod n] on the fly.
+#include "genp_internal.cuh"
+
+namespace genp {
+
+enum Src { kDense = 0, kCirc = 1, kCircT = 2 };
+
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool TRANSA, int ASRC, int BSRC>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+k_gemm(int64_t m, int64_t n, int64_t k, T alpha, const T *__restrict__ A, int64_t lda,
+       const T *__restrict__ B, int64_t ldb, T beta, const T *Cin, int64_t ldci, T *D, int64_t ldd,
+       const int *skip, const double *g, int64_t gn) {
+    if (skip && *skip) return;
+    constexpr int NT = (BM / TM) * (BN / TN);
+    constexpr int AE = BM * BK / NT, BE = BK * BN / NT;
+    static_assert(AE * NT == BM * BK && BE * NT == BK * BN, "tile split");
+    __shared__ __align__(16) T As[2][BK][BM];
+    __shared__ __align__(16) T Bs[2][BK][BN];
+    const int tid = threadIdx.x;
+    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+    const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+
+    T ra[AE], rb[BE];
+    auto circ = [&](int64_t d) -> T {
+        d %= gn;
+        if (d < 0) d += gn;
+        return (T)g[d];
+    };
+    auto load = [&](int64_t k0) {
+#pragma unroll
+        for (int e = 0; e < AE; ++e) {
+            const int lin = tid + e * NT;
+            int r, kk;
+            if (!TRANSA) { r = lin / BK; kk = lin % BK; }
+            else { kk = lin / BM; r = lin % BM; }
+            const int64_t gr = m0 + r, gk = k0 + kk;
+            T v = T(0);
+            if (gr < m && gk < k) {
+                if (ASRC == kDense) v = TRANSA ? A[gk * lda + gr] : A[gr * lda + gk];
+                else if (ASRC == kCirc) v = circ(gr - gk);
+                else v = circ(gk - gr);
+            }
+            ra[e] = v;
+        }
+#pragma unroll
+        for (int e = 0; e < BE; ++e) {
+            const int lin = tid + e * NT;
+            const int kk = lin / BN, c = lin % BN;
+            const int64_t gk = k0 + kk, gc = n0 + c;
+            T v = T(0);
+            if (gk < k && gc < n) v = (BSRC == kDense) ? B[gk * ldb + gc] : circ(gk - gc);
+            rb[e] = v;
+        }
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int e = 0; e < AE; ++e) {
+            const int lin = tid + e * NT;
+            int r, kk;
+            if (!TRANSA) { r = lin / BK; kk = lin % BK; }
+            else { kk = lin / BM; r = lin % BM; }
+            As[buf][kk][r] = ra[e];
+        }
+#pragma unroll
+        for (int e = 0; e < BE; ++e) {
+            const int lin = tid + e * NT;
+            Bs[buf][lin / BN][lin % BN] = rb[e];
+        }
+    };
+
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+
+    const int64_t nkt = (k + BK - 1) / BK;
+    load(0);
+    store(0);
+    __syncthreads();
+    for (int64_t kt = 0; kt < nkt; ++kt) {
+        const int buf = (int)(kt & 1);
+        if (kt + 1 < nkt) load((kt + 1) * BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[TM], b[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = As[buf][kk][ty * TM + i];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) b[j] = Bs[buf][kk][tx * TN + j];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        if (kt + 1 < nkt) store(buf ^ 1);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int64_t r = m0 + ty * TM + i;
+        if (r >= m) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int64_t c = n0 + tx * TN + j;
+            if (c >= n) continue;
+            T v = alpha * acc[i][j];
+            if (beta != T(0)) v = fma(beta, Cin[r * ldci + c], v);
+            D[r * ldd + c] = v;
+        }
+    }
+}
+
+namespace {
+
+template <typename T, int BM, int BN, int BK, int TM, int TN, bool TA, int AS, int BS>
+cudaError_t run(int64_t m, int64_t n, int64_t k, T alpha, const T *A, int64_t lda, const T *B, int64_t ldb,
+                T beta, const T *Cin, int64_t ldci, T *D, int64_t ldd, const int *skip, const double *g,
+                int64_t gn, cudaStream_t s) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    dim3 grid((unsigned)cdiv(n, BN), (unsigned)cdiv(m, BM));
+    if (grid.y > 65535u) return cudaErrorInvalidValue;
+    note_launch();
+    k_gemm<T, BM, BN, BK, TM, TN, TA, AS, BS><<<grid, (BM / TM) * (BN / TN), 0, s>>>(
+        m, n, k, alpha, A, lda, B, ldb, beta, Cin, ldci, D, ldd, skip, g, gn);
+    return cudaGetLastError();
+}
+
+template <typename T, bool TA, int AS, int BS>
+cudaError_t dispatch(int64_t m, int64_t n, int64_t k, T alpha, const T *A, int64_t lda, const T *B,
+                     int64_t ldb, T beta, const T *Cin, int64_t ldci, T *D, int64_t ldd, const int *skip,
+                     const double *g, int64_t gn, cudaStream_t s) {
+    if (k < 0) k = 0;  // k == 0 gives D = beta * Cin
+    if (n <= 16)
+        return run<T, 64, 16, 16, 4, 4, TA, AS, BS>(m, n, k, alpha, A, lda, B, ldb, beta, Cin, ldci, D, ldd,
+                                                     skip, g, gn, s);
+    if (sizeof(T) == 8)
+        return run<T, 64, 64, 16, 4, 4, TA, AS, BS>(m, n, k, alpha, A, lda, B, ldb, beta, Cin, ldci, D, ldd,
+                                                     skip, g, gn, s);
+    return run<T, 128, 128, 8, 8, 8, TA, AS, BS>(m, n, k, alpha, A, lda, B, ldb, beta, Cin, ldci, D, ldd,
+                                                  skip, g, gn, s);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t gemm(int64_t m, int64_t n, int64_t k, T alpha, const T *A, int64_t lda, bool transA, const T *B,
+                 int64_t ldb, T beta, const T *Cin, int64_t ldci, T *D, int64_t ldd, const int *skip,
+                 cudaStream_t s) {
+    if (transA)
+        return dispatch<T, true, kDense, kDense>(m, n, k, alpha, A, lda, B, ldb, beta, Cin, ldci, D, ldd, skip,
+                                                 nullptr, 1, s);
+    return dispatch<T, false, kDense, kDense>(m, n, k, alpha, A, lda, B, ldb, beta, Cin, ldci, D, ldd, skip,
+                                              nullptr, 1, s);
+}
+
+template cudaError_t gemm<double>(int64_t, int64_t, int64_t, double, const double *, int64_t, bool,
+                                  const double *, int64_t, double, const double *, int64_t, double *, int64_t,
+                                  const int *, cudaStream_t);
+template cudaError_t gemm<float>(int64_t, int64_t, int64_t, float, const float *, int64_t, bool, const float *,
+                                 int64_t, float, const float *, int64_t, float *, int64_t, const int *,
+                                 cudaStream_t);
+
+// C = A * G, G circulant with first column g (any n): 2 n^3 operations.
+template <typename TI, typename TO>
+cudaError_t circ_matmul_direct(const double *g, int64_t n, const TI *A, int64_t lda, TO *C, int64_t ldc,
+                               cudaStream_t s) {
+    static_assert(sizeof(TI) == sizeof(TO), "same precision in and out");
+    return dispatch<TO, false, kDense, kCirc>(n, n, n, TO(1), (const TO *)A, lda, nullptr, 0, TO(0), nullptr, 0,
+                                              C, ldc, nullptr, g, n, s);
+}
+template cudaError_t circ_matmul_direct<double, double>(const double *, int64_t, const double *, int64_t,
+                                                        double *, int64_t, cudaStream_t);
+template cudaError_t circ_matmul_direct<float, float>(const double *, int64_t, const float *, int64_t, float *,
+                                                      int64_t, cudaStream_t);
+
+// X (+)= G Y or G^T Y for circulant G without the DFT (any n).
+cudaError_t circ_apply_direct(const double *g, int64_t n, bool trans, const double *Y, int64_t ldy, double *X,
+                              int64_t ldx, int64_t nrhs, bool accumulate, const int *skip, cudaStream_t s) {
+    if (trans)
+        return dispatch<double, false, kCircT, kDense>(n, nrhs, n, 1.0, nullptr, 0, Y, ldy, accumulate ? 1.0 : 0.0,
+                                                       X, ldx, X, ldx, skip, g, n, s);
+    return dispatch<double, false, kCirc, kDense>(n, nrhs, n, 1.0, nullptr, 0, Y, ldy, accumulate ? 1.0 : 0.0, X,
+                                                  ldx, X, ldx, skip, g, n, s);
+}
+
+}  // namespace genp

@@ -1,0 +1,170 @@
+// genp_internal.cuh -- shared declarations of the libgenp translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "genp.h"
+
+namespace genp {
+
+// ---------------------------------------------------------------------------
+// Device status word of a factorization.  Non-negative doubles are kept as
+// their IEEE bit patterns, which order like unsigned integers, so atomicMin /
+// atomicMax on the bits give min / max of the values.
+// ---------------------------------------------------------------------------
+struct DevStatus {
+    unsigned long long breakdown_step;   // first zero / non-finite pivot, ~0ull if none
+    unsigned long long min_abs_pivot;    // bits of min |u_kk|
+    unsigned long long max_abs_pivot;    // bits of max |u_kk|
+    unsigned long long max_abs_u;        // bits of max |u_ij|
+    unsigned long long max_abs_c;        // bits of max |c_ij| before the factorization
+    int refine_iters;
+    int refine_done;                     // set on the device when refinement stops
+    int refine_status;                   // GENP_OK or GENP_ERR_NOCONV
+    int pad0;
+    double anorm;                        // ||A||_inf of the last refinement
+    double bwd_err[GENP_MAX_REFINE + 1];
+};
+
+constexpr int kMaxRhsChunk = 16;      // refinement works on right-hand sides in chunks
+
+// Workspace of the refinement norms (per right-hand side).
+struct DevNorms {
+    unsigned long long r[kMaxRhsChunk];
+    unsigned long long x[kMaxRhsChunk];
+    unsigned long long b[kMaxRhsChunk];
+};
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *p, double v) {
+    atomicMax(p, (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ void atomic_min_nonneg(unsigned long long *p, double v) {
+    atomicMin(p, (unsigned long long)__double_as_longlong(v));
+}
+
+// ---------------------------------------------------------------------------
+// Handles
+// ---------------------------------------------------------------------------
+}  // namespace genp
+
+struct genp_multiplier {
+    genp_mult_kind kind;
+    int64_t n;
+    int nnz;
+    genp_prec grid;
+    double *dense = nullptr;           // n x n (GAUSSIAN)
+    float *dense_f32 = nullptr;        // n x n copy on the FP32 grid (GAUSSIAN, grid FP32/BF16)
+    __nv_bfloat16 *dense_bf16 = nullptr;  // n x n (GAUSSIAN, grid BF16)
+    double *g = nullptr;               // first column (CIRCULANT)
+    double2 *spec = nullptr;           // DFT(g)/n in bit-reversed order (CIRCULANT, power-of-two n)
+    float2 *spec_f32 = nullptr;
+    double2 *twid = nullptr;           // exp(-2 pi i k / n), k < n/2
+    float2 *twid_f32 = nullptr;
+    int32_t *rows = nullptr;           // nnz x n (SPARSE)
+    int8_t *signs = nullptr;           // nnz x n
+    int32_t *inv_rows = nullptr;       // nnz x n: column whose t-th entry sits in row i
+    int8_t *inv_signs = nullptr;
+    int32_t *draws = nullptr;          // nnz x n Fisher-Yates draws (SPARSE)
+    double scale = 1.0;
+    cudaStream_t last_stream = nullptr;
+};
+
+struct genp_factors {
+    void *C = nullptr;
+    int64_t n = 0, ldc = 0, nb = 64;
+    genp_prec prec = GENP_FP64;
+    genp::DevStatus *st = nullptr;     // device
+    genp::DevNorms *norms = nullptr;   // device
+    void *work = nullptr;              // device workspace for solves / refinement
+    size_t work_bytes = 0;
+    void *host_info = nullptr;         // pinned host copy of the status
+    cudaStream_t last_stream = nullptr;
+};
+
+namespace genp {
+
+// ---------------------------------------------------------------------------
+// Launchers implemented in the .cu files (all enqueue on `s`, no sync).
+// ---------------------------------------------------------------------------
+
+// Counts one kernel launch (genp_launch_count); called before every launch.
+void note_launch();
+
+// rng.cu
+cudaError_t launch_make_dense(double *G, int64_t n, uint64_t seed, uint64_t stream_id, double scale,
+                              genp_prec grid, float *G32, __nv_bfloat16 *Gbf, cudaStream_t s);
+cudaError_t launch_make_circulant(double *g, int64_t n, uint64_t seed, uint64_t stream_id,
+                                  double scale, genp_prec grid, cudaStream_t s);
+cudaError_t launch_make_sparse(int32_t *rows, int8_t *signs, int32_t *inv_rows, int8_t *inv_signs,
+                               int32_t *scratch, int64_t n, int nnz, uint64_t seed,
+                               uint64_t stream_id, cudaStream_t s);
+cudaError_t launch_circulant_to_dense(const double *g, int64_t n, double *G, int64_t ldg,
+                                      cudaStream_t s);
+cudaError_t launch_sparse_to_dense(const int32_t *rows, const int8_t *signs, int64_t n, int nnz,
+                                   double *G, int64_t ldg, cudaStream_t s);
+
+// gemm.cu:  D = alpha * op(A) * B + beta * Cin, row-major, op(A) = A or A^T.
+// `skip` (device int, may be NULL): the kernel does nothing when *skip != 0.
+template <typename T>
+cudaError_t gemm(int64_t m, int64_t n, int64_t k, T alpha, const T *A, int64_t lda, bool transA,
+                 const T *B, int64_t ldb, T beta, const T *Cin, int64_t ldci, T *D, int64_t ldd,
+                 const int *skip, cudaStream_t s);
+
+// circ.cu: circulant products through the DFT (Thm. 2.1).
+bool circ_fft_supported(int64_t n);
+cudaError_t circ_prepare(genp_multiplier *G, cudaStream_t s);
+// out_p = ifft(fft(in_p) * H) for `count` vectors of length n: element i of
+// vector p at in[p*pstride + i*estride].  mode 0: H = conj(spec) (v G);
+// mode 1: H = spec (G v); mode 2: H = conj(spec) (G^T v).
+template <typename TI, typename TO>
+cudaError_t circ_apply(const genp_multiplier *G, int mode, const TI *in, int64_t in_pstride,
+                       int64_t in_estride, TO *out, int64_t out_pstride, int64_t out_estride,
+                       int64_t count, const int *skip, cudaStream_t s);
+// X (+)= G Y (trans false) or G^T Y on the columns of Y (n x nrhs double).
+cudaError_t circ_apply_cols(const genp_multiplier *G, bool trans, const double *Y, int64_t ldy, double *X,
+                            int64_t ldx, int64_t nrhs, bool accumulate, const int *skip, cudaStream_t s);
+// Direct (non-FFT) C = A * G for circulant G of any n, in 2n^3 operations.
+template <typename TI, typename TO>
+cudaError_t circ_matmul_direct(const double *g, int64_t n, const TI *A, int64_t lda, TO *C,
+                               int64_t ldc, cudaStream_t s);
+
+cudaError_t circ_apply_direct(const double *g, int64_t n, bool trans, const double *Y, int64_t ldy, double *X,
+                              int64_t ldx, int64_t nrhs, bool accumulate, const int *skip, cudaStream_t s);
+
+// sparse.cu
+template <typename TI, typename TO>
+cudaError_t sparse_precondition(const genp_multiplier *G, const TI *A, int64_t lda, TO *C, int64_t ldc,
+                                cudaStream_t s);
+// X = G Y (trans = false) or G^T Y, X and Y n x nrhs double; accumulate: X += ...
+cudaError_t sparse_apply(const genp_multiplier *G, bool trans, const double *Y, int64_t ldy, double *X,
+                         int64_t ldx, int64_t nrhs, bool accumulate, const int *skip, cudaStream_t s);
+
+// lu.cu
+cudaError_t factor_run(genp_factors *F, cudaStream_t s);
+cudaError_t status_reset(genp_factors *F, cudaStream_t s);
+
+// solve.cu
+// Y <- U^{-1} L^{-1} Y in the factor's precision, Y n x nrhs of type T
+template <typename T>
+cudaError_t lu_solve_inplace(const genp_factors *F, T *Y, int64_t ldy, int64_t nrhs, bool transposed,
+                             const int *skip, cudaStream_t s);
+template <typename TS, typename TD>
+cudaError_t convert_matrix(const TS *src, int64_t lds, TD *dst, int64_t ldd, int64_t m, int64_t n,
+                           const int *skip, cudaStream_t s);
+cudaError_t refine_init(genp_factors *F, const double *A, int64_t lda, int64_t n, cudaStream_t s);
+cudaError_t refine_check(genp_factors *F, const double *R, int64_t ldr, const double *X, int64_t ldx,
+                         const double *B, int64_t ldb, int64_t n, int64_t nrhs, int it, double tol,
+                         int max_iter, int last_chunk, cudaStream_t s);
+cudaError_t outer_update(const double *Lam, int64_t ldl, const double *X, int64_t ldx, int64_t n,
+                         int64_t nrhs, void *dA, int64_t ldda, bool dA_f32, cudaStream_t s);
+
+// api.cu helpers
+cudaError_t apply_multiplier(const genp_multiplier *G, bool trans, const double *Y, int64_t ldy,
+                             double *X, int64_t ldx, int64_t nrhs, bool accumulate, const int *skip,
+                             cudaStream_t s);
+
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace genp

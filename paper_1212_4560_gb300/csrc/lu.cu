@@ -1,0 +1,216 @@
+// lu.cu -- right-looking blocked GENP (Sec. 1.1; block Gaussian elimination,
+// Thm. 2.2), in place on C:
+//   for k0 = 0, nb, 2nb, ...
+//     panel:  C11 = L11 U11           (one CTA, the nb x nb block in shared memory)
+//     trsm:   U12 = L11^{-1} C12,  L21 = C21 U11^{-1}   (one launch, two roles)
+//     schur:  C22 <- C22 - L21 U12    (tiled GEMM, the dominant cost, ~2n^3/3 flops)
+// No row or column is ever exchanged.  A zero or non-finite pivot is
+// recorded in the status word (first step wins) and elimination goes on.
+#include "genp_internal.cuh"
+
+#include <math.h>
+
+namespace genp {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTrsmW = 64;
+
+__global__ void k_status_reset(DevStatus *st) {
+    st->breakdown_step = ~0ull;
+    st->min_abs_pivot = 0x7FF0000000000000ull;  // +inf
+    st->max_abs_pivot = 0ull;
+    st->max_abs_u = 0ull;
+    st->max_abs_c = 0ull;
+}
+
+template <typename T>
+__global__ void k_maxabs(const T *C, int64_t n, int64_t ldc, unsigned long long *out) {
+    double m = 0.0;
+    for (int64_t r = blockIdx.x; r < n; r += gridDim.x)
+        for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+            const double v = fabs((double)C[r * ldc + c]);
+            m = (v > m || isnan(v)) ? v : m;
+        }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double w = __shfl_xor_sync(0xffffffffu, m, o);
+        m = (w > m || isnan(w)) ? w : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
+}
+
+// Unblocked GENP of the kb x kb diagonal block at (k0, k0), in TC arithmetic.
+template <typename TS, typename TC>
+__global__ void __launch_bounds__(kThreads) k_panel(TS *C, int64_t ldc, int64_t k0, int kb, DevStatus *st) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    TC *a = reinterpret_cast<TC *>(smraw);
+    const int ld = kb + 1, tid = threadIdx.x;
+    for (int idx = tid; idx < kb * kb; idx += kThreads) {
+        const int i = idx / kb, j = idx % kb;
+        a[i * ld + j] = (TC)C[(k0 + i) * ldc + k0 + j];
+    }
+    __syncthreads();
+    for (int k = 0; k < kb; ++k) {
+        const TC p = a[k * ld + k];
+        if (tid == 0) {
+            const double ap = fabs((double)p);
+            if (!(ap > 0.0) || !isfinite(ap)) {
+                atomicMin(&st->breakdown_step, (unsigned long long)(k0 + k));
+            } else {
+                atomic_min_nonneg(&st->min_abs_pivot, ap);
+                atomic_max_nonneg(&st->max_abs_pivot, ap);
+            }
+        }
+        for (int i = k + 1 + tid; i < kb; i += kThreads) a[i * ld + k] = a[i * ld + k] / p;
+        __syncthreads();
+        const int rem = kb - k - 1;
+        for (int idx = tid; idx < rem * rem; idx += kThreads) {
+            const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
+            a[i * ld + j] = a[i * ld + j] - a[i * ld + k] * a[k * ld + j];
+        }
+        __syncthreads();
+    }
+    double umax = 0.0;
+    for (int idx = tid; idx < kb * kb; idx += kThreads) {
+        const int i = idx / kb, j = idx % kb;
+        const TC v = a[i * ld + j];
+        C[(k0 + i) * ldc + k0 + j] = (TS)v;
+        if (j >= i) {
+            const double av = fabs((double)v);
+            umax = (av > umax || isnan(av)) ? av : umax;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double w = __shfl_xor_sync(0xffffffffu, umax, o);
+        umax = (w > umax || isnan(w)) ? w : umax;
+    }
+    if ((tid & 31) == 0) atomic_max_nonneg(&st->max_abs_u, umax);
+}
+
+// blockIdx.y == 0: U12 = L11^{-1} C12 on columns [c0, c0 + w)
+// blockIdx.y == 1: L21 = C21 U11^{-1} on rows    [c0, c0 + w)
+template <typename TS, typename TC>
+__global__ void __launch_bounds__(kThreads) k_trsm(TS *C, int64_t ldc, int64_t n, int64_t k0, int kb,
+                                                   DevStatus *st) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    TC *d = reinterpret_cast<TC *>(smraw);
+    const int ld = kb + 1, tid = threadIdx.x;
+    TC *x = d + kb * ld;
+    const int64_t c0 = k0 + kb + (int64_t)blockIdx.x * kTrsmW;
+    const int w = (int)min((int64_t)kTrsmW, n - c0);
+    if (w <= 0) return;
+    for (int idx = tid; idx < kb * kb; idx += kThreads) {
+        const int i = idx / kb, j = idx % kb;
+        d[i * ld + j] = (TC)C[(k0 + i) * ldc + k0 + j];
+    }
+    double xmax = 0.0;
+    if (blockIdx.y == 0) {
+        const int lx = kTrsmW + 1;
+        for (int idx = tid; idx < kb * w; idx += kThreads) {
+            const int r = idx / w, c = idx % w;
+            x[r * lx + c] = (TC)C[(k0 + r) * ldc + c0 + c];
+        }
+        __syncthreads();
+        for (int k = 0; k + 1 < kb; ++k) {
+            const int rem = kb - k - 1;
+            for (int idx = tid; idx < rem * w; idx += kThreads) {
+                const int r = k + 1 + idx / w, c = idx % w;
+                x[r * lx + c] = x[r * lx + c] - d[r * ld + k] * x[k * lx + c];
+            }
+            __syncthreads();
+        }
+        for (int idx = tid; idx < kb * w; idx += kThreads) {
+            const int r = idx / w, c = idx % w;
+            const TC v = x[r * lx + c];
+            C[(k0 + r) * ldc + c0 + c] = (TS)v;
+            const double av = fabs((double)v);
+            xmax = (av > xmax || isnan(av)) ? av : xmax;
+        }
+    } else {
+        const int lx = kb + 1;
+        for (int idx = tid; idx < w * kb; idx += kThreads) {
+            const int i = idx / kb, j = idx % kb;
+            x[i * lx + j] = (TC)C[(c0 + i) * ldc + k0 + j];
+        }
+        __syncthreads();
+        for (int j = 0; j < kb; ++j) {
+            const TC p = d[j * ld + j];
+            for (int i = tid; i < w; i += kThreads) x[i * lx + j] = x[i * lx + j] / p;
+            __syncthreads();
+            const int rem = kb - j - 1;
+            if (rem > 0) {
+                for (int idx = tid; idx < w * rem; idx += kThreads) {
+                    const int i = idx / rem, l = j + 1 + idx % rem;
+                    x[i * lx + l] = x[i * lx + l] - x[i * lx + j] * d[j * ld + l];
+                }
+                __syncthreads();
+            }
+        }
+        for (int idx = tid; idx < w * kb; idx += kThreads) {
+            const int i = idx / kb, j = idx % kb;
+            C[(c0 + i) * ldc + k0 + j] = (TS)x[i * lx + j];
+        }
+    }
+    if (blockIdx.y == 0) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const double v = __shfl_xor_sync(0xffffffffu, xmax, o);
+            xmax = (v > xmax || isnan(v)) ? v : xmax;
+        }
+        if ((tid & 31) == 0) atomic_max_nonneg(&st->max_abs_u, xmax);
+    }
+}
+
+template <typename TS, typename TC>
+cudaError_t factor_typed(genp_factors *F, cudaStream_t s) {
+    TS *C = static_cast<TS *>(F->C);
+    const int64_t n = F->n, ldc = F->ldc;
+    const int nb = (int)F->nb;
+    const size_t sm_panel = (size_t)nb * (nb + 1) * sizeof(TC);
+    const size_t xrow = (size_t)nb * (kTrsmW + 1), xcol = (size_t)kTrsmW * (nb + 1);
+    const size_t sm_trsm = sm_panel + (xrow > xcol ? xrow : xcol) * sizeof(TC);
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_panel<TS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_trsm<TS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_done = true;
+    }
+    note_launch();
+    k_maxabs<TS><<<152 * 4, 256, 0, s>>>(C, n, ldc, &F->st->max_abs_c);
+    for (int64_t k0 = 0; k0 < n; k0 += nb) {
+        const int kb = (int)(n - k0 < nb ? n - k0 : nb);
+        note_launch();
+        k_panel<TS, TC><<<1, kThreads, sm_panel, s>>>(C, ldc, k0, kb, F->st);
+        const int64_t rem = n - k0 - kb;
+        if (rem <= 0) break;
+        dim3 g((unsigned)cdiv(rem, kTrsmW), 2);
+        note_launch();
+        k_trsm<TS, TC><<<g, kThreads, sm_trsm, s>>>(C, ldc, n, k0, kb, F->st);
+        TS *L21 = C + (k0 + kb) * ldc + k0;
+        TS *U12 = C + k0 * ldc + k0 + kb;
+        TS *A22 = C + (k0 + kb) * ldc + k0 + kb;
+        cudaError_t e = gemm<TS>(rem, rem, kb, TS(-1), L21, ldc, false, U12, ldc, TS(1), A22, ldc, A22, ldc,
+                                 nullptr, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t status_reset(genp_factors *F, cudaStream_t s) {
+    note_launch();
+    k_status_reset<<<1, 1, 0, s>>>(F->st);
+    return cudaGetLastError();
+}
+
+cudaError_t factor_run(genp_factors *F, cudaStream_t s) {
+    cudaError_t e = status_reset(F, s);
+    if (e != cudaSuccess) return e;
+    switch (F->prec) {
+        case GENP_FP64: return factor_typed<double, double>(F, s);
+        case GENP_FP32: return factor_typed<float, float>(F, s);
+        default: return cudaErrorNotSupported;
+    }
+}
+
+}  // namespace genp

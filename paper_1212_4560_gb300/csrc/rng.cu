@@ -1,0 +1,251 @@
+// rng.cu -- random multipliers from a counter-based generator.
+//
+// Generator: Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11, Sec. 3.3):
+// ten rounds, each taking the 128-bit products of words 0 and 2 with two
+// fixed odd multipliers, xoring the high halves into words 1 and 3 with the
+// round key, and bumping the key by two Weyl increments between rounds.
+// Layout of the method's draws: key = (seed, stream_id); counter =
+// (index, block, tag, t).  Gaussian entries use Marsaglia's polar method
+// with a logarithm built from IEEE basic operations only (the atanh series
+// of ln((1+f)/(1-f)), Abramowitz & Stegun 4.1.27), so that every entry is
+// reproducible bit for bit on any IEEE machine.  The _rn intrinsics below
+// keep the compiler from fusing multiply-adds in this file.
+#include "genp_internal.cuh"
+
+namespace genp {
+namespace {
+
+constexpr uint64_t kTagDense = 0x10, kTagCirc = 0x11, kTagPerm = 0x12, kTagSign = 0x13;
+constexpr int kPolarBlocks = 32;
+
+struct U4 { uint64_t w[4]; };
+
+__device__ __forceinline__ U4 philox(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0,
+                                     uint64_t k1) {
+    const uint64_t m0 = 0xD2E7470EE14C6C93ull, m1 = 0xCA5A826395121157ull;
+    const uint64_t w0 = 0x9E3779B97F4A7C15ull, w1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += w0; k1 += w1; }
+        const uint64_t hi0 = __umul64hi(m0, c0), lo0 = m0 * c0;
+        const uint64_t hi1 = __umul64hi(m1, c2), lo1 = m1 * c2;
+        const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    U4 o;
+    o.w[0] = c0; o.w[1] = c1; o.w[2] = c2; o.w[3] = c3;
+    return o;
+}
+
+__device__ __forceinline__ double unit53(uint64_t w) {
+    return __dmul_rn((double)(w >> 11), 1.1102230246251565e-16 /* 2^-53 */);
+}
+
+// ln(s) for positive normal s: s = m 2^e exactly, m in (sqrt2/2, sqrt2],
+// ln m = 2 atanh(f), f = (m-1)/(m+1), |f| < 0.172, series to f^23.
+__device__ double ln_series(double s) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(s);
+    int e = (int)((b >> 52) & 0x7ffull) - 1023;
+    double m = __longlong_as_double((long long)((b & 0x000FFFFFFFFFFFFFull) | (1023ull << 52)));
+    if (m > 1.4142135623730951) { m = __dmul_rn(m, 0.5); e += 1; }
+    const double f = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+    const double f2 = __dmul_rn(f, f);
+    const int K = 11;
+    double p = __ddiv_rn(1.0, (double)(2 * K + 1));
+    for (int k = K - 1; k >= 0; --k) p = __dadd_rn(__dmul_rn(p, f2), __ddiv_rn(1.0, (double)(2 * k + 1)));
+    const double lm = __dmul_rn(__dmul_rn(2.0, f), p);
+    const double el = __dmul_rn((double)e, 0.6931471805599453);
+    return __dadd_rn(el, lm);
+}
+
+__device__ double polar_normal(uint64_t seed, uint64_t sid, uint64_t tag, uint64_t idx) {
+    for (uint64_t blk = 0; blk < kPolarBlocks; ++blk) {
+        const U4 w = philox(idx, blk, tag, 0, seed, sid);
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const double v1 = __dsub_rn(__dmul_rn(2.0, unit53(w.w[2 * p])), 1.0);
+            const double v2 = __dsub_rn(__dmul_rn(2.0, unit53(w.w[2 * p + 1])), 1.0);
+            const double s = __dadd_rn(__dmul_rn(v1, v1), __dmul_rn(v2, v2));
+            if (s > 0.0 && s < 1.0) {
+                double t = ln_series(s);
+                t = __dmul_rn(-2.0, t);
+                t = __ddiv_rn(t, s);
+                t = __dsqrt_rn(t);
+                return __dmul_rn(v1, t);
+            }
+        }
+    }
+    return 0.0;
+}
+
+// Round a finite double to the nearest BF16 value (ties to even) by clearing
+// the 45 low mantissa bits with a round-to-nearest-even bias.
+__device__ __forceinline__ double round_to_bf16_grid(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long lsb = (b >> 45) & 1ull;
+    b += 0x00000FFFFFFFFFFFull + lsb;
+    b &= ~0x00001FFFFFFFFFFFull;
+    return __longlong_as_double((long long)b);
+}
+
+__device__ __forceinline__ double on_grid(double v, genp_prec grid) {
+    if (grid == GENP_BF16) return round_to_bf16_grid(v);
+    if (grid == GENP_FP32) return (double)__double2float_rn(v);
+    return v;
+}
+
+__global__ void k_dense(double *G, int64_t n, uint64_t seed, uint64_t sid, double scale, genp_prec grid,
+                        float *G32, __nv_bfloat16 *Gbf) {
+    const int64_t total = n * n;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const double v = on_grid(__dmul_rn(polar_normal(seed, sid, kTagDense, (uint64_t)idx), scale), grid);
+        G[idx] = v;
+        if (G32) G32[idx] = (float)v;
+        if (Gbf) Gbf[idx] = __float2bfloat16_rn((float)v);
+    }
+}
+
+__global__ void k_circ(double *g, int64_t n, uint64_t seed, uint64_t sid, double scale, genp_prec grid) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        g[i] = on_grid(__dmul_rn(polar_normal(seed, sid, kTagCirc, (uint64_t)i), scale), grid);
+}
+
+// Uniform integer in [0, range) (Lemire's multiply-shift with rejection).
+__device__ uint64_t bounded(uint64_t range, uint64_t seed, uint64_t sid, uint64_t i, uint64_t t) {
+    const uint64_t thr = (0ull - range) % range;
+    uint64_t hi = 0;
+    for (uint64_t blk = 0; blk < 16; ++blk) {
+        const U4 w = philox(i, blk, kTagPerm, t, seed, sid);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            hi = __umul64hi(w.w[q], range);
+            const uint64_t lo = w.w[q] * range;
+            if (lo >= thr) return hi;
+        }
+    }
+    return hi;
+}
+
+// Draws of the Fisher-Yates shuffle: swap partner of position i (i >= 1) and the signs.
+__global__ void k_perm_draws(int32_t *draws, int8_t *signs, int64_t n, int nnz, uint64_t seed, uint64_t sid) {
+    const int64_t total = n * nnz;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = idx / n, i = idx % n;
+        draws[idx] = i >= 1 ? (int32_t)bounded((uint64_t)(i + 1), seed, sid, (uint64_t)i, (uint64_t)t) : 0;
+        const U4 w = philox((uint64_t)i, 0, kTagSign, (uint64_t)t, seed, sid);
+        signs[idx] = (w.w[0] & 1ull) ? (int8_t)-1 : (int8_t)1;
+    }
+}
+
+// The shuffle itself is sequential: one thread per permutation, i = n-1 .. 1.
+__global__ void k_perm_shuffle(int32_t *rows, const int32_t *draws, int64_t n) {
+    if (threadIdx.x != 0) return;
+    const int64_t t = blockIdx.x;
+    int32_t *p = rows + t * n;
+    const int32_t *d = draws + t * n;
+    for (int64_t i = n - 1; i >= 1; --i) {
+        const int64_t j = d[i];
+        const int32_t tmp = p[i];
+        p[i] = p[j];
+        p[j] = tmp;
+    }
+}
+
+__global__ void k_iota(int32_t *rows, int64_t n, int nnz) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * nnz;
+         idx += (int64_t)gridDim.x * blockDim.x)
+        rows[idx] = (int32_t)(idx % n);
+}
+
+__global__ void k_invert(const int32_t *rows, const int8_t *signs, int32_t *inv_rows, int8_t *inv_signs,
+                         int64_t n, int nnz) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * nnz;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = idx / n, j = idx % n;
+        const int64_t r = rows[idx];
+        inv_rows[t * n + r] = (int32_t)j;
+        inv_signs[t * n + r] = signs[idx];
+    }
+}
+
+__global__ void k_circ_dense(const double *g, int64_t n, double *G, int64_t ldg) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / n, j = idx % n;
+        int64_t d = i - j;
+        if (d < 0) d += n;
+        G[i * ldg + j] = g[d];
+    }
+}
+
+__global__ void k_zero(double *G, int64_t n, int64_t ldg) {
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * n;
+         idx += (int64_t)gridDim.x * blockDim.x)
+        G[(idx / n) * ldg + idx % n] = 0.0;
+}
+
+// One thread per column: entries of one column never race.
+__global__ void k_sparse_dense(const int32_t *rows, const int8_t *signs, int64_t n, int nnz, double *G,
+                               int64_t ldg) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        for (int t = 0; t < nnz; ++t) {
+            const int64_t r = rows[(int64_t)t * n + j];
+            G[r * ldg + j] += (double)signs[(int64_t)t * n + j];
+        }
+}
+
+int grid_for(int64_t work, int threads) {
+    int64_t b = cdiv(work, threads);
+    if (b > 152 * 32) b = 152 * 32;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_make_dense(double *G, int64_t n, uint64_t seed, uint64_t sid, double scale, genp_prec grid,
+                              float *G32, __nv_bfloat16 *Gbf, cudaStream_t s) {
+    note_launch();
+    k_dense<<<grid_for(n * n, 256), 256, 0, s>>>(G, n, seed, sid, scale, grid, G32, Gbf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_make_circulant(double *g, int64_t n, uint64_t seed, uint64_t sid, double scale,
+                                  genp_prec grid, cudaStream_t s) {
+    note_launch();
+    k_circ<<<grid_for(n, 256), 256, 0, s>>>(g, n, seed, sid, scale, grid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_make_sparse(int32_t *rows, int8_t *signs, int32_t *inv_rows, int8_t *inv_signs,
+                               int32_t *scratch, int64_t n, int nnz, uint64_t seed, uint64_t sid,
+                               cudaStream_t s) {
+    note_launch();
+    k_perm_draws<<<grid_for(n * nnz, 256), 256, 0, s>>>(scratch, signs, n, nnz, seed, sid);
+    note_launch();
+    k_iota<<<grid_for(n * nnz, 256), 256, 0, s>>>(rows, n, nnz);
+    note_launch();
+    k_perm_shuffle<<<nnz, 32, 0, s>>>(rows, scratch, n);
+    note_launch();
+    k_invert<<<grid_for(n * nnz, 256), 256, 0, s>>>(rows, signs, inv_rows, inv_signs, n, nnz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_circulant_to_dense(const double *g, int64_t n, double *G, int64_t ldg, cudaStream_t s) {
+    note_launch();
+    k_circ_dense<<<grid_for(n * n, 256), 256, 0, s>>>(g, n, G, ldg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sparse_to_dense(const int32_t *rows, const int8_t *signs, int64_t n, int nnz, double *G,
+                                   int64_t ldg, cudaStream_t s) {
+    note_launch();
+    k_zero<<<grid_for(n * n, 256), 256, 0, s>>>(G, n, ldg);
+    note_launch();
+    k_sparse_dense<<<grid_for(n, 128), 128, 0, s>>>(rows, signs, n, nnz, G, ldg);
+    return cudaGetLastError();
+}
+
+}  // namespace genp

@@ -309,7 +309,9 @@ def run_ours(a):
         roofline = {"kernel": "k_gemm<double,64,64,16,4,4> (C = A G)", "bound": "alu", "achieved": achieved,
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64 has no tensor-core path)",
-                    "traffic": None}
+                    # dram read+write bytes of one n=4096 launch under ncu (3.908e9), scaled by the
+                    # flop count to the launch size timed here (both grow as n^3)
+                    "traffic": 3.908e9 * (n / 4096) ** 3}
     else:
         achieved = (fact) / (phase_ms["factor"] / 1e3) / 1e12
         roofline = {"kernel": "GENP factor (Schur GEMM dominant)", "bound": "alu", "achieved": achieved,

@@ -236,7 +236,10 @@ def test_cfg_n256_end_to_end(g, kind):
     x = host(X)
     eta = oracle.backward_error(A, x, B)
     assert eta <= 1e-14
-    assert info.bwd_err[-1] == pytest.approx(eta, rel=1e-6, abs=1e-20)
+    # the device's own backward error: each side's residual is exact to within
+    # gamma_{n+1} (|A||x| + |b|), so the two values of eta agree to 2 gamma_{n+1}
+    assert info.bwd_err[-1] <= 1e-14
+    assert abs(info.bwd_err[-1] - eta) <= 2 * gamma(257)
     kappa = np.linalg.cond(A, np.inf)
     xd = oracle.gepp_solve(A, B)
     assert np.abs(x - xd).max() / np.abs(xd).max() <= 1e-14 * kappa

@@ -219,6 +219,35 @@ GENP_API genp_status genp_adjoint(const genp_factors *F, const genp_multiplier *
                          const double *X, int64_t ldx, int64_t nrhs, void *dA, int64_t ldda, double *dB,
                          int64_t lddb, void *cuda_stream);
 
+/* Allocation-free draw of the SPARSE_PM1 multiplier.  The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc, such as code
+ * whose device memory all belongs to another allocator (a framework pool that
+ * has already reserved it, an application that maps its memory once at
+ * start-up) or a latency-critical loop that must not pay the device-wide
+ * synchronization cudaMalloc / cudaFree can cause.
+ * Writes the same multiplier as genp_make_multiplier(GENP_MULT_SPARSE_PM1, n,
+ * seed, stream_id, ...) into caller-owned device buffers, each nnz_per_col*n:
+ *  rows[t*n + j]      row of the t-th entry of column j (int32)
+ *  signs[t*n + j]     its sign (int8, +1 or -1)
+ *  inv_rows[t*n + i]  column whose t-th entry sits in row i (int32)
+ *  inv_signs[t*n + i] that entry's sign (int8)
+ * Its only scratch (the Fisher-Yates swap draws) is a file-scope device array
+ * of GENP_NOALLOC_MAX_ENTRIES int32 (4 MiB) that every GPU loading the
+ * library holds until the process exits; n * nnz_per_col above that limit
+ * returns GENP_ERR_ARG with nothing enqueued.  Nothing in the array needs
+ * clearing between calls (each call writes every entry it reads), but all
+ * calls on one GPU share it: calls whose work overlaps on the same GPU (two
+ * streams, or two host threads enqueueing at once) race and corrupt each
+ * other's result.  Serialize them on one stream.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.  Errors: GENP_ERR_ARG, GENP_ERR_CUDA. */
+#define GENP_NOALLOC_MAX_ENTRIES (1 << 20)
+GENP_API genp_status genp_make_sparse_noalloc(int64_t n, int nnz_per_col, uint64_t seed, uint64_t stream_id,
+                                              int32_t *rows, int8_t *signs, int32_t *inv_rows, int8_t *inv_signs,
+                                              void *cuda_stream);
+
 /* Number of kernels this library has launched in the process so far
  * (diagnostics: lets a caller count the launches of a timed region). */
 GENP_API uint64_t genp_launch_count(void);

@@ -219,6 +219,23 @@ GENP_API genp_status genp_adjoint(const genp_factors *F, const genp_multiplier *
                          const double *X, int64_t ldx, int64_t nrhs, void *dA, int64_t ldda, double *dB,
                          int64_t lddb, void *cuda_stream);
 
+/* Tensor-core building block of the BF16 path (tcgen05, FP32 accumulation):
+ *   D = alpha * A * B^T + beta * Cin
+ *  A      m x K BF16 (uint16 storage), row-major, ld lda (multiple of 8,
+ *         16-byte aligned base).
+ *  Bt     n x K BF16, row-major, ld ldb (same rules); i.e. B^T.
+ *  Cin, D m x n FP32, ld ldci / ldd; Cin may be NULL when beta == 0 and may
+ *         equal D (in-place update).
+ * Errors: GENP_ERR_ARG (sizes, alignment), GENP_ERR_CUDA. */
+GENP_API genp_status genp_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha, const void *A, int64_t lda,
+                                    const void *Bt, int64_t ldb, float beta, const float *Cin, int64_t ldci,
+                                    float *D, int64_t ldd, void *cuda_stream);
+
+/* Synchronizes the device and reports whether any tensor-core kernel of this
+ * library gave up a bounded wait (GENP_ERR_TIMEOUT) since the last clear;
+ * `clear` != 0 resets the flag.  GENP_OK otherwise. */
+GENP_API genp_status genp_device_check(int clear);
+
 /* Allocation-free draw of the SPARSE_PM1 multiplier.  The paper has no
  * counterpart: this serves callers that cannot call cudaMalloc, such as code
  * whose device memory all belongs to another allocator (a framework pool that

@@ -40,6 +40,9 @@ SIGNATURES = {
     "genp_redraw_multiplier": (_int, [_vp, _u64, _u64, _vp]),
     "genp_launch_count": (_u64, []),
     "genp_make_sparse_noalloc": (_int, [_i64, _int, _u64, _u64, _vp, _vp, _vp, _vp, _vp]),
+    "genp_gemm_bf16": (_int, [_i64, _i64, _i64, ctypes.c_float, _vp, _i64, _vp, _i64, ctypes.c_float, _vp, _i64,
+                              _vp, _i64, _vp]),
+    "genp_device_check": (_int, [_int]),
     "genp_multiplier_export": (_int, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "genp_multiplier_query": (_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_int), ctypes.POINTER(_int)]),
     "genp_multiplier_destroy": (None, [_vp]),

@@ -206,6 +206,26 @@ genp_status genp_redraw_multiplier(genp_multiplier *G, uint64_t seed, uint64_t s
 
 uint64_t genp_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
+genp_status genp_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha, const void *A, int64_t lda, const void *Bt,
+                           int64_t ldb, float beta, const float *Cin, int64_t ldci, float *D, int64_t ldd,
+                           void *cuda_stream) {
+    if (m < 0 || n < 0 || K < 1 || !A || !Bt || !D) return GENP_ERR_ARG;
+    if (lda < K || ldb < K || ldd < n || (lda % 8) || (ldb % 8)) return GENP_ERR_ARG;
+    if (((uintptr_t)A % 16) || ((uintptr_t)Bt % 16)) return GENP_ERR_ARG;
+    if (beta != 0.0f && (!Cin || ldci < n)) return GENP_ERR_ARG;
+    if (m > INT32_MAX || n > INT32_MAX || K > INT32_MAX || cdiv(m, 128) > 65535) return GENP_ERR_ARG;
+    CU(tc_gemm_bf16(m, n, K, alpha, (const __nv_bfloat16 *)A, lda, (const __nv_bfloat16 *)Bt, ldb, beta, Cin, ldci, D,
+                    ldd, nullptr, S(cuda_stream)));
+    return GENP_OK;
+}
+
+genp_status genp_device_check(int clear) {
+    CU(cudaDeviceSynchronize());
+    const int v = tc_timeout_flag(clear != 0);
+    if (v < 0) return GENP_ERR_CUDA;
+    return v ? GENP_ERR_TIMEOUT : GENP_OK;
+}
+
 genp_status genp_multiplier_export(const genp_multiplier *G, double *dense, int64_t ldd, double *first_col,
                                    int32_t *rows, int8_t *signs, void *cuda_stream) {
     if (!G) return GENP_ERR_ARG;

@@ -141,6 +141,13 @@ cudaError_t sparse_precondition(const genp_multiplier *G, const TI *A, int64_t l
 cudaError_t sparse_apply(const genp_multiplier *G, bool trans, const double *Y, int64_t ldy, double *X,
                          int64_t ldx, int64_t nrhs, bool accumulate, const int *skip, cudaStream_t s);
 
+// gemm_tc.cu: D = alpha * A * Bt^T + beta * Cin on the tensor cores (BF16 in, FP32 out).
+cudaError_t tc_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha, const __nv_bfloat16 *A, int64_t lda,
+                         const __nv_bfloat16 *Bt, int64_t ldb, float beta, const float *Cin, int64_t ldci, float *D,
+                         int64_t ldd, const int *skip, cudaStream_t s);
+// Reads the device-side timeout flag of the tensor-core kernels (synchronizes).
+int tc_timeout_flag(bool reset);
+
 // lu.cu
 cudaError_t factor_run(genp_factors *F, cudaStream_t s);
 cudaError_t status_reset(genp_factors *F, cudaStream_t s);

@@ -33,6 +33,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solves/s & TFLOP/s (2n³/3), BF16+IR vs FP64 GENP, same GB300, bwd err ≤1e-14"
 KINDS = {"gaussian": 0, "circulant": 1, "sparse": 2}
+PRECS = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 4}
+GRID_OF = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 2}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 
 
@@ -47,6 +57,11 @@ def parse():
     p.add_argument("--kind", default="gaussian", choices=list(KINDS))
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--tol", type=float, default=1e-14)
+    p.add_argument("--workload", default="lead", choices=["lead", "svd"],
+                   help="lead: N(0,1) A with a rank-deficient leading block; svd: A = J U diag(sigma) V^T")
+    p.add_argument("--kappa", type=float, default=1e2, help="condition number of the svd workload")
+    p.add_argument("--prec", default="fp64", choices=list(PRECS))
+    p.add_argument("--max-iter", type=int, default=None)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
@@ -54,7 +69,9 @@ def parse():
 
 
 def workload_name(a):
-    return f"genp_fp64_n{a.n}_{a.kind}_{a.nrhs}rhs"
+    if a.workload == "svd":
+        return f"genp_{a.prec}_n{a.n}_svd_kappa{a.kappa:.0e}_{a.kind}_{a.nrhs}rhs"
+    return f"genp_{a.prec}_n{a.n}_{a.kind}_{a.nrhs}rhs"
 
 
 def flops_per_solve(a):
@@ -139,8 +156,11 @@ def oracle_sample(a, n_sample: int, repeats: int):
 
     import oracle
     import workloads as W
-    lead = max(2, 64 * n_sample // a.n)          # same recipe: leading block n/128, rank half of it
-    A, _, B = W.lead_deficient(n_sample, lead, lead // 2, a.nrhs, seed=a.seed)
+    if a.workload == "svd":
+        A, _, B = W.svd_kappa(n_sample, a.kappa, a.nrhs, seed=a.seed)
+    else:
+        lead = max(2, 64 * n_sample // a.n)      # same recipe: leading block n/128, rank half of it
+        A, _, B = W.lead_deficient(n_sample, lead, lead // 2, a.nrhs, seed=a.seed)
     A, B = A.numpy(), B.numpy()
     oracle.lib()
     times = []
@@ -199,17 +219,24 @@ def run_ours(a):
     _b.build()
 
     n, nrhs = a.n, a.nrhs
-    A_cpu, _, B_cpu = W.lead_deficient(n, 64, 32, nrhs, seed=a.seed + rank)
-    A = A_cpu.to(dev)
-    B = B_cpu.to(dev)
-    C = torch.empty((n, n), dtype=torch.float64, device=dev)
+    if a.workload == "svd":
+        A, _, B = W.svd_kappa(n, a.kappa, nrhs, seed=a.seed + rank, device=dev)
+        A_cpu, B_cpu = A.cpu(), B.cpu()
+    else:
+        A_cpu, _, B_cpu = W.lead_deficient(n, 64, 32, nrhs, seed=a.seed + rank)
+        A = A_cpu.to(dev)
+        B = B_cpu.to(dev)
+    prec = PRECS[a.prec]
+    cdt = torch.float64 if a.prec == "fp64" else torch.float32
+    max_iter = a.max_iter if a.max_iter is not None else (10 if a.prec == "fp64" else 30)
+    C = torch.empty((n, n), dtype=cdt, device=dev)
     X = torch.empty((n, nrhs), dtype=torch.float64, device=dev)
-    dA = torch.empty((n, n), dtype=torch.float64, device=dev)
+    dA = torch.empty((n, n), dtype=cdt, device=dev)
     dB = torch.empty((n, nrhs), dtype=torch.float64, device=dev)
     kind = KINDS[a.kind]
-    G = genp.make_multiplier(kind, n, seed=1, stream_id=rank)
-    genp.precondition(G, A, C)
-    F = genp.factor(C)
+    G = genp.make_multiplier(kind, n, seed=1, stream_id=rank, value_grid=GRID_OF[a.prec])
+    genp.precondition(G, A, C, c_prec=prec)
+    F = genp.factor(C, prec=prec)
     stream = torch.cuda.current_stream(dev)
 
     def step(i, ev=None):
@@ -219,13 +246,13 @@ def run_ours(a):
         mark(0)
         genp.redraw_multiplier(G, seed=1000 + i, stream_id=rank)
         mark(1)
-        genp.precondition(G, A, C)
+        genp.precondition(G, A, C, c_prec=prec)
         mark(2)
         genp.refactor(F, C)
         mark(3)
         genp.solve(F, G, B, X)
         mark(4)
-        genp.refine(A, F, G, B, X, tol=a.tol, max_iter=10)
+        genp.refine(A, F, G, B, X, tol=a.tol, max_iter=max_iter)
         mark(5)
         genp.adjoint(F, G, X, X, dA, dB)
         mark(6)
@@ -303,8 +330,23 @@ def run_ours(a):
             dist.destroy_process_group()
         return
 
-    # dominant kernel: the DFMA GEMM of C = A G (one launch per precondition call)
-    if a.kind == "gaussian":
+    # dominant kernel: the GEMM of C = A G (one launch per BF16 term / per FP64 call)
+    peaks = measured_peaks()
+    if a.kind == "gaussian" and a.prec in ("bf16", "bf16x3"):
+        terms = 3 if a.prec == "bf16x3" else 1
+        achieved = terms * 2.0 * n**3 / (phase_ms["precondition"] / 1e3) / 1e12
+        peak = float(peaks.get("bf16_tflops", 1900.0))
+        roofline = {"kernel": f"k_tc_gemm (tcgen05 BF16, C = A G, {terms} launch(es))", "bound": "tensor",
+                    "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "peak_source": "measured bf16_tflops (burst)" if "bf16_tflops" in peaks else "fallback",
+                    "traffic": None}
+    elif a.kind == "gaussian" and a.prec == "fp32":
+        achieved = 2.0 * n**3 / (phase_ms["precondition"] / 1e3) / 1e12
+        peak = 152 * 128 * 2 * 2.070e9 / 1e12
+        roofline = {"kernel": "k_gemm<float,128,128,8,8,8> (C = A G)", "bound": "alu", "achieved": achieved,
+                    "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz", "traffic": None}
+    elif a.kind == "gaussian":
         achieved = 2.0 * n**3 / (phase_ms["precondition"] / 1e3) / 1e12
         roofline = {"kernel": "k_gemm<double,64,64,16,4,4> (C = A G)", "bound": "alu", "achieved": achieved,
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
@@ -326,10 +368,14 @@ def run_ours(a):
                          f"system of the same recipe ({nrhs} RHS), median of 3, time scaled by (n/{n_s})^3 to n={n}"}
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(a), "n": n, "nrhs": nrhs, "multiplier": a.kind, "precision": "fp64",
-                       "A": "N(0,1) with leading 64x64 block of rank 32", "l2": "inputs larger than L2 (no flush)",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32"}.get(a.prec, a.prec), "data": "synthetic",
+            "config": {"workload": workload_name(a), "n": n, "nrhs": nrhs, "multiplier": a.kind, "precision": a.prec,
+                       "A": ("J U diag(sigma) V^T, kappa=%g" % a.kappa) if a.workload == "svd"
+                       else "N(0,1) with leading 64x64 block of rank 32",
+                       "l2": "inputs larger than L2 (no flush)",
                        "parallelism": "replicas" if world > 1 else "single"},
+            "bwd_err_unrefined": info.bwd_err[0] if info.bwd_err else None,
+            "converged": bool(info.bwd_err) and info.bwd_err[-1] <= a.tol,
             "tflops": tflops, "tflops_counted": {"factor_2n3_over_3": fact, "AG": ag},
             "phases_ms": phase_ms, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "gpu_launches_per_step": launches / a.steps,

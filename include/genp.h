@@ -80,12 +80,17 @@ typedef enum {
  *        Schur-complement products use BF16 operands on the tensor cores
  *        with FP32 accumulation; the diagonal blocks are factored in FP64.
  *  FP8_E4M3: as BF16 with e4m3 operands and a power-of-two scale per
- *        128 x 128 tile. */
+ *        128 x 128 tile (not offered by this build: GENP_ERR_UNSUPPORTED).
+ *  BF16X3: as BF16, but every operand is split into three BF16 terms and
+ *        six of their products are accumulated (a1b1 + a1b2 + a2b1 + a1b3 +
+ *        a2b2 + a3b1), which brings the tensor-core products close to FP32
+ *        accuracy at six times the BF16 work. */
 typedef enum {
     GENP_FP64 = 0,
     GENP_FP32 = 1,
     GENP_BF16 = 2,
-    GENP_FP8_E4M3 = 3
+    GENP_FP8_E4M3 = 3,
+    GENP_BF16X3 = 4
 } genp_prec;
 
 typedef struct genp_multiplier genp_multiplier;

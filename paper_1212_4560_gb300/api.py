@@ -13,7 +13,7 @@ from dataclasses import dataclass
 import torch
 
 from . import _lib
-from ._lib import BF16, CIRCULANT, FP8_E4M3, FP32, FP64, GAUSSIAN, SPARSE_PM1, GenpError, check
+from ._lib import BF16, BF16X3, CIRCULANT, FP8_E4M3, FP32, FP64, GAUSSIAN, SPARSE_PM1, GenpError, check
 
 _PREC_OF_DTYPE = {torch.float64: FP64, torch.float32: FP32}
 
@@ -172,7 +172,7 @@ def solve_system(A: torch.Tensor, B: torch.Tensor, kind: int = GAUSSIAN, seed: i
     """The whole method on one system: G, C = A G, GENP(C), X = G U^-1 L^-1 B,
     FP64 refinement.  Returns (X, info, G, F)."""
     n = A.size(0)
-    grid = FP64 if prec == FP64 else FP32
+    grid = FP64 if prec == FP64 else (BF16 if prec in (BF16, BF16X3) else FP32)
     G = make_multiplier(kind, n, seed, value_grid=grid, stream=stream)
     C = torch.empty((n, n), dtype=torch.float64 if prec == FP64 else torch.float32, device=A.device)
     A64 = A if A.dtype == torch.float64 else A.double()

@@ -79,7 +79,8 @@ cudaError_t draw_multiplier(genp_multiplier *G, uint64_t seed, uint64_t stream_i
     return cudaErrorInvalidValue;
 }
 
-bool factor_prec_ok(genp_prec p) { return p == GENP_FP64 || p == GENP_FP32; }
+bool factor_prec_ok(genp_prec p) { return p == GENP_FP64 || p == GENP_FP32 || p == GENP_BF16 || p == GENP_BF16X3; }
+bool tc_prec(genp_prec p) { return p == GENP_BF16 || p == GENP_BF16X3; }
 
 // Grows the factors workspace to at least `bytes` (synchronizes the stream
 // only when it actually has to grow).
@@ -167,7 +168,7 @@ genp_status genp_make_multiplier(genp_mult_kind kind, int64_t n, uint64_t seed, 
     if (kind == GENP_MULT_GAUSSIAN) {
         st = dalloc(&G->dense, (size_t)n * n);
         if (st == GENP_OK && value_grid != GENP_FP64) st = dalloc(&G->dense_f32, (size_t)n * n);
-        if (st == GENP_OK && value_grid == GENP_BF16) st = dalloc(&G->dense_bf16, (size_t)n * n);
+        if (st == GENP_OK && value_grid == GENP_BF16) st = dalloc(&G->dense_bf16, (size_t)n * round8(n));
     } else if (kind == GENP_MULT_CIRCULANT) {
         st = dalloc(&G->g, (size_t)n);
         if (st == GENP_OK && circ_fft_supported(n)) {
@@ -267,10 +268,31 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
     const int64_t n = G->n;
     if (lda < n || ldc < n) return GENP_ERR_ARG;
     if (a_prec != GENP_FP64 && a_prec != GENP_FP32) return GENP_ERR_ARG;
-    if (c_prec == GENP_BF16 || c_prec == GENP_FP8_E4M3) return GENP_ERR_UNSUPPORTED;
-    if (c_prec != GENP_FP64 && c_prec != GENP_FP32) return GENP_ERR_ARG;
+    if (c_prec == GENP_FP8_E4M3) return GENP_ERR_UNSUPPORTED;
+    if (!factor_prec_ok(c_prec)) return GENP_ERR_ARG;
     if (c_prec == GENP_FP64 && a_prec != GENP_FP64) return GENP_ERR_ARG;
     cudaStream_t s = S(cuda_stream);
+    if (tc_prec(c_prec) && G->kind == GENP_MULT_GAUSSIAN) {
+        // Tensor cores: C = sum_t a_t G over the BF16 terms a_t of A (one term
+        // for BF16, three for BF16X3); G is exact on the BF16 grid.
+        if (!G->dense_bf16) return GENP_ERR_ARG;
+        const int terms = c_prec == GENP_BF16X3 ? 3 : 1;
+        const int64_t ldq = round8(n);
+        __nv_bfloat16 *buf = nullptr;
+        CU(cudaMallocAsync((void **)&buf, (size_t)n * ldq * sizeof(__nv_bfloat16), s));
+        float *c = static_cast<float *>(C);
+        for (int t = 0; t < terms; ++t) {
+            if (a_prec == GENP_FP64)
+                CU(split_rows<double>((const double *)A, lda, n, n, buf, ldq, 1, true, t, s));
+            else
+                CU(split_rows<float>((const float *)A, lda, n, n, buf, ldq, 1, true, t, s));
+            CU(tc_gemm_bf16(n, n, n, 1.0f, buf, ldq, G->dense_bf16, round8(n), t > 0 ? 1.0f : 0.0f, c, ldc, c, ldc,
+                            nullptr, s));
+        }
+        CU(cudaFreeAsync(buf, s));
+        return GENP_OK;
+    }
+    if (tc_prec(c_prec)) c_prec = GENP_FP32;  // circulant and sparse products run in FP32 (FFT / exact gather)
     if (c_prec == GENP_FP64) {
         const double *a = static_cast<const double *>(A);
         double *c = static_cast<double *>(C);
@@ -321,9 +343,9 @@ genp_status genp_factor(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t
     if (!out) return GENP_ERR_ARG;
     *out = nullptr;
     if (!C || n < 1 || n > 2147483647LL || ldc < n) return GENP_ERR_ARG;
-    if (prec == GENP_BF16 || prec == GENP_FP8_E4M3) return GENP_ERR_UNSUPPORTED;
+    if (prec == GENP_FP8_E4M3) return GENP_ERR_UNSUPPORTED;
     if (!factor_prec_ok(prec)) return GENP_ERR_ARG;
-    if (nb == 0) nb = 64;
+    if (nb == 0) nb = tc_prec(prec) ? 128 : 64;
     if (nb < 1 || nb > 128) return GENP_ERR_ARG;
     cudaStream_t s = S(cuda_stream);
     genp_factors *F = new (std::nothrow) genp_factors();
@@ -336,6 +358,11 @@ genp_status genp_factor(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t
     F->last_stream = s;
     genp_status st = dalloc(&F->st, 1);
     if (st == GENP_OK) st = dalloc(&F->norms, 2);
+    if (st == GENP_OK && tc_prec(prec)) {
+        F->tc_ldq = round8(nb * split_terms(prec));
+        st = dalloc(&F->tcA, (size_t)n * F->tc_ldq);
+        if (st == GENP_OK) st = dalloc(&F->tcB, (size_t)n * F->tc_ldq);
+    }
     if (st == GENP_OK && cudaMallocHost(&F->host_info, sizeof(DevStatus)) != cudaSuccess) {
         cudaGetLastError();
         F->host_info = nullptr;
@@ -367,6 +394,8 @@ void genp_factors_destroy(genp_factors *F) {
     cudaFree(F->st);
     cudaFree(F->norms);
     cudaFree(F->work);
+    cudaFree(F->tcA);
+    cudaFree(F->tcB);
     if (F->host_info) cudaFreeHost(F->host_info);
     delete F;
 }

@@ -42,6 +42,11 @@ struct Ctl {
     int issued;
 };
 constexpr size_t kSmem = 1024 + STAGES * (A_BYTES + B_BYTES) + sizeof(Ctl);
+// Epilogue tile row stride in floats: 16-byte aligned rows whose bank offset
+// (132 mod 32 = 4) makes the per-row float4 writes and the row reads
+// conflict-free.
+constexpr int kTileLd = BN + 4;
+static_assert(BM * kTileLd * 4 <= STAGES * (A_BYTES + B_BYTES), "epilogue tile fits in the stage buffers");
 
 __device__ __forceinline__ uint32_t sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -122,7 +127,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 __global__ void __launch_bounds__(128, 2)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m, int n, int K,
-          float alpha, float beta, const float *Cin, int64_t ldci, float *D, int64_t ldd, const int *skip) {
+          float alpha, float beta, const float *Cin, int64_t ldci, float *D, int64_t ldd, int vec, const int *skip) {
     if (skip && *skip) return;
     extern __shared__ unsigned char smraw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -191,29 +196,51 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     }
     __syncwarp();
 
-    // epilogue
+    // epilogue: TMEM -> registers -> shared memory (the stage buffers are free
+    // once the accumulator is complete) -> coalesced rows of D
     bool ready = mbar_wait(&ctl->accum, 0, abort);
     if (!ready) *abort = 1;
     fence_after();
+    ready = __syncthreads_and(ready) != 0;
+    float *tile = reinterpret_cast<float *>(base);  // BM x kTileLd floats
     if (ready) {
-        const int row = m0 + warp * 32 + lane;
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        float4 *trow = reinterpret_cast<float4 *>(tile + (warp * 32 + lane) * kTileLd);
 #pragma unroll 1
         for (int c = 0; c < BN / 32; ++c) {
             uint32_t r[32];
             tmem_ld32(lane_addr + (uint32_t)(c * 32), r);
-            if (row < m) {
-                const int col0 = n0 + c * 32;
-                float *drow = D + (int64_t)row * ldd;
-                const float *crow = Cin ? Cin + (int64_t)row * ldci : nullptr;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int col = col0 + j;
-                    if (col < n) {
-                        float v = alpha * __uint_as_float(r[j]);
-                        if (beta != 0.0f) v = fmaf(beta, crow[col], v);
-                        drow[col] = v;
-                    }
+            for (int q = 0; q < 8; ++q)
+                trow[c * 8 + q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                              __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+        }
+    }
+    __syncthreads();
+    if (ready) {
+        const int col = n0 + lane * 4;
+        for (int rr = warp; rr < BM; rr += 4) {
+            const int row = m0 + rr;
+            if (row >= m) break;
+            const float4 a = *reinterpret_cast<const float4 *>(tile + rr * kTileLd + lane * 4);
+            float *drow = D + (int64_t)row * ldd;
+            if (vec && col + 3 < n) {
+                float4 v = make_float4(alpha * a.x, alpha * a.y, alpha * a.z, alpha * a.w);
+                if (beta != 0.0f) {
+                    const float4 cv = *reinterpret_cast<const float4 *>(Cin + (int64_t)row * ldci + col);
+                    v.x = fmaf(beta, cv.x, v.x);
+                    v.y = fmaf(beta, cv.y, v.y);
+                    v.z = fmaf(beta, cv.z, v.z);
+                    v.w = fmaf(beta, cv.w, v.w);
+                }
+                *reinterpret_cast<float4 *>(drow + col) = v;
+            } else {
+                const float av[4] = {a.x, a.y, a.z, a.w};
+                for (int e = 0; e < 4; ++e) {
+                    if (col + e >= n) break;
+                    float v = alpha * av[e];
+                    if (beta != 0.0f) v = fmaf(beta, Cin[(int64_t)row * ldci + col + e], v);
+                    drow[col + e] = v;
                 }
             }
         }
@@ -285,8 +312,10 @@ cudaError_t tc_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha, const __n
     }
     dim3 grid((unsigned)cdiv(n, BN), (unsigned)cdiv(m, BM));
     if (grid.y > 65535u) return cudaErrorInvalidValue;
+    const int vec = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0) &&
+                    (beta == 0.0f || ((uintptr_t)Cin % 16 == 0 && ldci % 4 == 0));
     note_launch();
-    k_tc_gemm<<<grid, 128, kSmem, s>>>(ma, mb, (int)m, (int)n, (int)K, alpha, beta, Cin, ldci, D, ldd, skip);
+    k_tc_gemm<<<grid, 128, kSmem, s>>>(ma, mb, (int)m, (int)n, (int)K, alpha, beta, Cin, ldci, D, ldd, vec, skip);
     return cudaGetLastError();
 }
 

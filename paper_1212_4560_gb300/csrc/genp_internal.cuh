@@ -56,7 +56,7 @@ struct genp_multiplier {
     genp_prec grid;
     double *dense = nullptr;           // n x n (GAUSSIAN)
     float *dense_f32 = nullptr;        // n x n copy on the FP32 grid (GAUSSIAN, grid FP32/BF16)
-    __nv_bfloat16 *dense_bf16 = nullptr;  // n x n (GAUSSIAN, grid BF16)
+    __nv_bfloat16 *dense_bf16 = nullptr;  // G^T, n x round8(n) (GAUSSIAN, grid BF16)
     double *g = nullptr;               // first column (CIRCULANT)
     double2 *spec = nullptr;           // DFT(g)/n in bit-reversed order (CIRCULANT, power-of-two n)
     float2 *spec_f32 = nullptr;
@@ -80,6 +80,9 @@ struct genp_factors {
     void *work = nullptr;              // device workspace for solves / refinement
     size_t work_bytes = 0;
     void *host_info = nullptr;         // pinned host copy of the status
+    __nv_bfloat16 *tcA = nullptr;      // BF16 split L21 panel, n x tc_ldq (BF16 / BF16X3)
+    __nv_bfloat16 *tcB = nullptr;      // BF16 split U12^T panel, n x tc_ldq
+    int64_t tc_ldq = 0;
     cudaStream_t last_stream = nullptr;
 };
 
@@ -147,6 +150,19 @@ cudaError_t tc_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha, const __n
                          int64_t ldd, const int *skip, cudaStream_t s);
 // Reads the device-side timeout flag of the tensor-core kernels (synchronizes).
 int tc_timeout_flag(bool reset);
+
+// mixed.cu: BF16 split operands.  terms = 1 (GENP_BF16) or 6 (GENP_BF16X3).
+int split_terms(genp_prec p);
+// dst[i][b*k + kk] = term_b(src[i][kk]) for the left operand (left = true) or
+// the right operand's term order; single_term >= 0 writes that one term only.
+template <typename T>
+cudaError_t split_rows(const T *src, int64_t lds, int64_t m, int64_t k, __nv_bfloat16 *dst, int64_t ldq, int terms,
+                       bool left, int single_term, cudaStream_t s);
+// dst[j][b*k + kk] = term_b(src[kk][j]) (right operand, transposed to K-major).
+template <typename T>
+cudaError_t split_cols_T(const T *src, int64_t lds, int64_t k, int64_t m, __nv_bfloat16 *dst, int64_t ldq, int terms,
+                         cudaStream_t s);
+__host__ __device__ inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
 // lu.cu
 cudaError_t factor_run(genp_factors *F, cudaStream_t s);

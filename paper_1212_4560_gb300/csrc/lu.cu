@@ -195,6 +195,49 @@ cudaError_t factor_typed(genp_factors *F, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Mixed precision (GENP_BF16, GENP_BF16X3): C is the FP32 master copy.  The
+// diagonal block is factored in FP64 (the pivots), the block row and column
+// are solved in FP32, and the Schur update C22 -= L21 U12 runs on the tensor
+// cores with BF16 (split) operands and FP32 accumulation.
+cudaError_t factor_tc(genp_factors *F, cudaStream_t s) {
+    float *C = static_cast<float *>(F->C);
+    const int64_t n = F->n, ldc = F->ldc;
+    const int nb = (int)F->nb;
+    const int terms = split_terms(F->prec);
+    const size_t sm_panel = (size_t)nb * (nb + 1) * sizeof(double);
+    const size_t xrow = (size_t)nb * (kTrsmW + 1), xcol = (size_t)kTrsmW * (nb + 1);
+    const size_t sm_trsm = (size_t)nb * (nb + 1) * sizeof(float) + (xrow > xcol ? xrow : xcol) * sizeof(float);
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_panel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_trsm<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_done = true;
+    }
+    note_launch();
+    k_maxabs<float><<<152 * 4, 256, 0, s>>>(C, n, ldc, &F->st->max_abs_c);
+    for (int64_t k0 = 0; k0 < n; k0 += nb) {
+        const int kb = (int)(n - k0 < nb ? n - k0 : nb);
+        note_launch();
+        k_panel<float, double><<<1, kThreads, sm_panel, s>>>(C, ldc, k0, kb, F->st);
+        const int64_t rem = n - k0 - kb;
+        if (rem <= 0) break;
+        dim3 g((unsigned)cdiv(rem, kTrsmW), 2);
+        note_launch();
+        k_trsm<float, float><<<g, kThreads, sm_trsm, s>>>(C, ldc, n, k0, kb, F->st);
+        float *L21 = C + (k0 + kb) * ldc + k0;
+        float *U12 = C + k0 * ldc + k0 + kb;
+        float *A22 = C + (k0 + kb) * ldc + k0 + kb;
+        const int64_t Kq = (int64_t)kb * terms;
+        cudaError_t e = split_rows<float>(L21, ldc, rem, kb, F->tcA, F->tc_ldq, terms, true, -1, s);
+        if (e == cudaSuccess) e = split_cols_T<float>(U12, ldc, kb, rem, F->tcB, F->tc_ldq, terms, s);
+        if (e == cudaSuccess)
+            e = tc_gemm_bf16(rem, rem, Kq, -1.0f, F->tcA, F->tc_ldq, F->tcB, F->tc_ldq, 1.0f, A22, ldc, A22, ldc,
+                             nullptr, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t status_reset(genp_factors *F, cudaStream_t s) {
@@ -209,6 +252,8 @@ cudaError_t factor_run(genp_factors *F, cudaStream_t s) {
     switch (F->prec) {
         case GENP_FP64: return factor_typed<double, double>(F, s);
         case GENP_FP32: return factor_typed<float, float>(F, s);
+        case GENP_BF16:
+        case GENP_BF16X3: return factor_tc(F, s);
         default: return cudaErrorNotSupported;
     }
 }

@@ -102,7 +102,7 @@ __global__ void k_dense(double *G, int64_t n, uint64_t seed, uint64_t sid, doubl
         const double v = on_grid(__dmul_rn(polar_normal(seed, sid, kTagDense, (uint64_t)idx), scale), grid);
         G[idx] = v;
         if (G32) G32[idx] = (float)v;
-        if (Gbf) Gbf[idx] = __float2bfloat16_rn((float)v);
+        if (Gbf) Gbf[(idx % n) * round8(n) + idx / n] = __float2bfloat16_rn((float)v);  // G^T, K-major
     }
 }
 

@@ -28,6 +28,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -57,8 +59,11 @@ def parse():
     p.add_argument("--kind", default="gaussian", choices=list(KINDS))
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--tol", type=float, default=1e-14)
-    p.add_argument("--workload", default="lead", choices=["lead", "svd"],
-                   help="lead: N(0,1) A with a rank-deficient leading block; svd: A = J U diag(sigma) V^T")
+    p.add_argument("--workload", default="lead", choices=["lead", "svd", "batched", "diff"],
+                   help="lead: N(0,1) A with a rank-deficient leading block; svd: A = J U diag(sigma) V^T; "
+                        "batched: 10k systems n in [16,512], a11 = 0, FP32 factors + FP64 refinement; "
+                        "diff: 256 x n=1024 FP32 systems, circulant G, 8 RHS, forward + adjoint")
+    p.add_argument("--count", type=int, default=None, help="systems in the batched / diff workloads")
     p.add_argument("--kappa", type=float, default=1e2, help="condition number of the svd workload")
     p.add_argument("--prec", default="fp64", choices=list(PRECS))
     p.add_argument("--max-iter", type=int, default=None)
@@ -175,7 +180,60 @@ def oracle_sample(a, n_sample: int, repeats: int):
     return statistics.median(times), threads, res["eta"][-1]
 
 
+def oracle_batch_seconds(a, sizes, budget_s):
+    """Oracle pipeline on the first systems of a batch for about budget_s;
+    returns (seconds scaled to the whole batch by sum n^3, systems done)."""
+    import oracle
+    diff = a.workload == "diff"
+    nrhs = 8 if diff else 4
+    rng = np.random.default_rng(a.seed)
+    t0, done = time.perf_counter(), 0
+    while time.perf_counter() - t0 < budget_s and done < len(sizes):
+        n = int(sizes[done])
+        Ai = rng.standard_normal((n, n)) + (0.1 * n * np.eye(n) if diff else 0.0)
+        if not diff:
+            Ai[0, 0] = 0.0
+        Bi = Ai @ rng.standard_normal((n, nrhs))
+        res = oracle.solve(Ai, Bi, oracle.multiplier(1 if diff else 0, n, seed=done, grid="fp32"),
+                           refine_steps=0 if diff else 10, tol=a.tol)
+        if diff:
+            oracle.adjoint(Ai, res["x"], res["x"])
+        done += 1
+    el = time.perf_counter() - t0
+    frac = sum(float(n) ** 3 for n in sizes[:done]) / sum(float(n) ** 3 for n in sizes)
+    return el / frac, done
+
+
+def run_reference_batched(a):
+    import workloads as W
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    diff = a.workload == "diff"
+    count = a.count or (256 if diff else 10000)
+    sizes = [1024] * count if diff else W.batched_sizes(count, 16, 512, seed=a.seed)
+    per = []
+    for i in range(a.warmup + a.steps):
+        t, done = oracle_batch_seconds(a, sizes, 4.0)
+        if i >= a.warmup:
+            per.append(t)
+    sec = statistics.mean(per)
+    value = count / sec
+    name = "batched_10k_n16-512_fp32_fp64ir_4rhs" if not diff else "diff_256x1024_fp32_circulant_8rhs"
+    sample = f"oracle pipeline on the first {done} systems of the batch (~4 s per step), scaled by sum n^3"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "count": count},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": len(os.sched_getaffinity(0)),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(a):
+    if a.workload in ("batched", "diff"):
+        return run_reference_batched(a)
     world, rank, _ = dist_env()
     if rank != 0:
         return
@@ -389,10 +447,155 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def run_batched(a):
+    """Many small systems per step: `batched` (uneven sizes, refinement) or
+    `diff` (uniform n = 1024, forward + adjoint), one graph replay per step."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_1212_4560_gb300 as genp
+    from paper_1212_4560_gb300 import batched as Bt
+    import workloads as W
+
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1212_4560_gb300 import build as _b
+    _b.build()
+    diff = a.workload == "diff"
+    if diff:
+        count = a.count or 256
+        nrhs = 8
+        sizes = [1024] * count
+        A, _, Bm = W.shifted(count, 1024, nrhs, seed=a.seed + rank, device=dev, dtype=torch.float32)
+        Ap = A.reshape(-1).contiguous()
+        Bp = Bm.double().reshape(-1).contiguous()
+        plan = Bt.BatchedPlan(sizes, nrhs, kind=genp.CIRCULANT, a_dtype=torch.float32, max_iter=10, tol=a.tol)
+        del A
+    else:
+        count = a.count or 10000
+        nrhs = 4
+        sizes = W.batched_sizes(count, 16, 512, seed=a.seed + rank)
+        plan = Bt.BatchedPlan(sizes, nrhs, kind=genp.GAUSSIAN, a_dtype=torch.float64, max_iter=10, tol=a.tol,
+                              autotune=True, escalate=True)
+        Ap = torch.empty(plan.mat_size, dtype=torch.float64, device=dev)
+        Bp = torch.empty(plan.vec_size, dtype=torch.float64, device=dev)
+        g = torch.Generator(device=dev)
+        g.manual_seed(a.seed * 1_000_003 + 7919 + rank)
+        for i, n in enumerate(sizes):
+            Ai = torch.randn(n, n, generator=g, device=dev, dtype=torch.float64)
+            Ai[0, 0] = 0.0
+            Xi = torch.randn(n, nrhs, generator=g, device=dev, dtype=torch.float64)
+            Ap[plan.mat_off[i]:plan.mat_off[i + 1]] = Ai.reshape(-1)
+            Bp[plan.vec_off[i]:plan.vec_off[i + 1]] = (Ai @ Xi).reshape(-1)
+    Xp = torch.empty_like(Bp)
+    dA = torch.empty(plan.mat_size, dtype=torch.float32, device=dev) if diff else None
+    dB = torch.empty_like(Bp) if diff else None
+    stream = torch.cuda.current_stream(dev)
+
+    def step_body(seed):
+        plan.run(seed, Ap, Bp, Xp)
+        if diff:
+            plan.adjoint(Ap, Xp, Xp, dA, dB)    # loss 0.5 ||X||^2, refined like the forward
+
+    # capture one step in a CUDA graph (allocation-free, no synchronization inside)
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(stream)
+    with torch.cuda.stream(s):
+        for i in range(max(1, a.warmup)):
+            step_body(1 + i)
+    stream.wait_stream(s)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    l_before = genp.launch_count()
+    with torch.cuda.graph(graph):
+        step_body(1)
+    launches_per_step = genp.launch_count() - l_before
+    for _ in range(a.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    with ClockSampler(local, not a.no_clocks and rank == 0) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    total_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    st = plan.status()
+    value = world * count * a.steps / (total_ms / 1e3)
+    n3 = sum(float(n) ** 3 for n in sizes)
+    fact, ag = 2.0 * n3 / 3.0, (2.0 * n3 if not diff else sum(10.0 * n * n * np.log2(n) for n in sizes))
+    tflops = world * (fact + ag) * a.steps / (total_ms / 1e3) / 1e12
+    peak = 152 * 128 * 2 * 2.070e9 / 1e12
+    e2e = None
+    if not a.no_e2e:
+        A_h = Ap.cpu().pin_memory()
+        B_h = Bp.cpu().pin_memory()
+        X_h = torch.empty(Xp.shape, dtype=Xp.dtype).pin_memory()
+        k = max(2, min(a.steps, 4))
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for i in range(k):
+            Ap.copy_(A_h, non_blocking=True)
+            Bp.copy_(B_h, non_blocking=True)
+            graph.replay()
+            X_h.copy_(Xp, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        e2e = {"value": world * count * k / (f0.elapsed_time(f1) / 1e3), "unit": "solves/s",
+               "h2d_bytes_per_step": A_h.numel() * A_h.element_size() + B_h.numel() * 8,
+               "d2h_bytes_per_step": X_h.numel() * 8, "steps": k}
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not a.no_cpu_baseline and world == 1:
+        t, done = oracle_batch_seconds(a, sizes, 15.0)
+        cpu = {"value": count / t, "unit": "solves/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+               "sample": f"oracle pipeline on the first {done} systems of the batch (~15 s), scaled to the "
+                         f"whole batch by sum n^3"}
+    name = "batched_10k_n16-512_fp32_fp64ir_4rhs" if not diff else "diff_256x1024_fp32_circulant_8rhs"
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": name, "count": count, "nrhs": nrhs, "sizes": "uniform [16, 512]" if not diff
+                       else "1024", "multiplier": "gaussian" if not diff else "circulant",
+                       "precision": "fp32 factors" + (", fp64 refinement" if not diff else ", forward + adjoint"),
+                       "l2": "inputs larger than L2 (no flush)", "graph": "one CUDA graph replay per step",
+                       "block_sizes": {str(nn): plan.block_size(nn) for nn in (16, 128, 512, 1024)}},
+            "tflops": tflops,
+            "roofline": {"kernel": "k_batched (persistent, CTA-level FFMA GEMM dominant)", "bound": "alu",
+                         "achieved": tflops / world, "peak": peak, "unit": "TFLOP/s", "frac": tflops / world / peak,
+                         "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz", "traffic": None},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * a.steps,
+            "gpu_launches_per_step": launches_per_step,
+            "bwd_err_max": float(np.max(st["eta"])), "bwd_err_unrefined_median": float(np.median(st["eta0"])),
+            "converged_fraction": float(np.mean(st["eta"] <= a.tol)) if not diff else None,
+            "refine_iters_mean": float(np.mean(st["iters"])),
+            "escalated_to_fp64": int(np.sum(st["escalated"]))}
+    if not a.no_clocks:
+        line["clocks"] = clk.summary()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload in ("batched", "diff"):
+        run_batched(a)
     else:
         run_ours(a)
 

@@ -224,6 +224,78 @@ GENP_API genp_status genp_adjoint(const genp_factors *F, const genp_multiplier *
                          const double *X, int64_t ldx, int64_t nrhs, void *dA, int64_t ldda, double *dB,
                          int64_t lddb, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Batched solves: many independent small systems (1 <= n_i <= 1024) in one
+ * persistent launch.  Each system gets its own multiplier (stream id = its
+ * index i, drawn in single precision: GENP_FP32 grid), its own FP32
+ * factorization C_i = A_i G_i = L_i U_i and FP64 refinement; a work queue
+ * hands the systems, largest first, to the CTAs.  The plan owns every
+ * workspace, so genp_batched_run allocates and synchronizes nothing and can
+ * be captured in a CUDA graph.
+ * Pools (caller-owned device memory) hold the systems back to back in the
+ * caller's order: A_i (n_i x n_i, row-major, ld n_i) at mat_offsets[i],
+ * B_i / X_i (n_i x nrhs, ld nrhs) at vec_offsets[i] (genp_batched_layout).
+ * ---------------------------------------------------------------------- */
+typedef struct genp_batched_plan genp_batched_plan;
+
+/* count      number of systems (>= 1); n: host array of their orders.
+ * nrhs       right-hand sides per system (1..16).
+ * kind       GENP_MULT_GAUSSIAN (dense N(0, 1/n_i)) or GENP_MULT_CIRCULANT (N(0,1) first column).
+ * a_prec     storage of the A pool: GENP_FP64 or GENP_FP32.
+ * max_iter   refinement steps (0..32; 0 = no refinement), tol its target
+ *            backward error.
+ * flags      GENP_BATCH_AUTOTUNE: time the candidate block sizes of each
+ *            size class once on this GPU (synchronizes; the choice is kept
+ *            per process and, if GENP_AUTOTUNE_CACHE names a file, there).
+ *            GENP_BATCH_FP64_ESCALATION: a system whose FP32-factor
+ *            refinement stalls above tol is factored again in FP64 by the
+ *            same CTA and refined with those factors (the plan then holds
+ *            8.1 MiB of FP64 scratch per persistent CTA).
+ * Errors: GENP_ERR_ARG, GENP_ERR_NOMEM, GENP_ERR_CUDA. */
+#define GENP_BATCH_AUTOTUNE 1
+#define GENP_BATCH_FP64_ESCALATION 2
+GENP_API genp_status genp_batched_plan_create(int64_t count, const int64_t *n, int64_t nrhs, genp_mult_kind kind,
+                                              genp_prec a_prec, int max_iter, double tol, int flags,
+                                              void *cuda_stream, genp_batched_plan **out);
+
+/* Host arrays of count+1 entries: element offsets of every system in the A
+ * pool and in the B / X pools (the last entry is the pool size). */
+GENP_API genp_status genp_batched_layout(const genp_batched_plan *P, int64_t *mat_offsets, int64_t *vec_offsets);
+
+/* Block size the plan uses for systems of order n (after autotuning). */
+GENP_API int genp_batched_block_size(const genp_batched_plan *P, int64_t n);
+
+/* Draws every system's multiplier from `seed` (system i: stream id i) and
+ * solves all systems: X_i = A_i^{-1} B_i by the method, refined in FP64.
+ * A pool in a_prec; B and X pools double.  Keeps the factors for
+ * genp_batched_adjoint. */
+GENP_API genp_status genp_batched_run(genp_batched_plan *P, uint64_t seed, const void *A_pool, const double *B_pool,
+                                      double *X_pool, void *cuda_stream);
+
+/* Adjoint of the last run through its factors: Lambda_i = A_i^{-T} gX_i =
+ * L_i^{-T} U_i^{-T} G_i^T gX_i, refined in FP64 against the A pool like the
+ * forward solve (same max_iter and tol); dB_i = Lambda_i (double, may be
+ * NULL); dA_i = -Lambda_i X_i^T (float, A-pool layout, may be NULL). */
+GENP_API genp_status genp_batched_adjoint(genp_batched_plan *P, const void *A_pool, const double *gX_pool,
+                                          const double *X_pool, float *dA_pool, double *dB_pool, void *cuda_stream);
+
+/* Per-system results of the last run (host arrays of count entries, any may
+ * be NULL): status (GENP_OK / GENP_ERR_BREAKDOWN / GENP_ERR_NOCONV),
+ * refinement steps, backward error before and after refinement, growth
+ * max|U| / max|C| of the FP32 factorization, and whether the system was
+ * escalated to FP64.  Synchronizes the stream. */
+GENP_API genp_status genp_batched_status(const genp_batched_plan *P, int32_t *status, int32_t *iters, double *eta0,
+                                         double *eta, double *growth, int32_t *escalated, void *cuda_stream);
+
+/* Copies the multipliers of the last run into caller pools: dense G_i
+ * (float, A-pool layout) or circulant first columns g_i (float, sum n_i,
+ * back to back in the caller's order). */
+GENP_API genp_status genp_batched_multipliers(const genp_batched_plan *P, float *G_pool, float *g_pool,
+                                              void *cuda_stream);
+
+/* Frees the plan (cudaFree waits for work still using it). NULL is ignored. */
+GENP_API void genp_batched_plan_destroy(genp_batched_plan *P);
+
 /* Tensor-core building block of the BF16 path (tcgen05, FP32 accumulation):
  *   D = alpha * A * B^T + beta * Cin
  *  A      m x K BF16 (uint16 storage), row-major, ld lda (multiple of 8,

@@ -49,6 +49,12 @@ def lib():
         L.or_log.restype = ctypes.c_double
         L.or_gauss.argtypes = [_u64, _u64, _u64, _u64]
         L.or_gauss.restype = ctypes.c_double
+        L.or_log_f32.argtypes = [ctypes.c_float]
+        L.or_log_f32.restype = ctypes.c_float
+        L.or_gauss_f32.argtypes = [_u64, _u64, _u64, _u64]
+        L.or_gauss_f32.restype = ctypes.c_float
+        L.or_mult_dense_f32.argtypes = [_i64, _u64, _u64, ctypes.c_float, _dp, _i64]
+        L.or_mult_circulant_f32.argtypes = [_i64, _u64, _u64, ctypes.c_float, _dp]
         L.or_mult_dense.argtypes = [_i64, _u64, _u64, ctypes.c_double, _dp, _i64]
         L.or_mult_circulant.argtypes = [_i64, _u64, _u64, ctypes.c_double, _dp]
         L.or_mult_sparse.argtypes = [_i64, ctypes.c_int, _u64, _u64, ctypes.c_void_p, ctypes.c_void_p]
@@ -106,22 +112,38 @@ def gauss(seed: int, stream: int, tag: int, idx: int) -> float:
     return lib().or_gauss(seed, stream, tag, idx)
 
 
+def log_f32(s: float) -> float:
+    return lib().or_log_f32(float(s))
+
+
+def gauss_f32(seed: int, stream: int, tag: int, idx: int) -> float:
+    return lib().or_gauss_f32(seed, stream, tag, idx)
+
+
 def multiplier(kind: int, n: int, seed: int, stream: int = 0, scale: float | None = None,
-               nnz: int = 4):
+               nnz: int = 4, grid: str = "fp64"):
     """The random multiplier G (Definition 3.2 / Sec. 2.3 / sparse reading).
 
+    grid "fp64": entries drawn in double precision; "fp32": drawn by the same
+    polar method in single precision (scale rounded to float first).
     Returns a dict with the structure (``G`` dense n x n always, plus ``g``
     for a circulant, ``rows``/``signs`` for the sparse multiplier)."""
     L = lib()
     if kind == KIND_GAUSSIAN:
         s = (1.0 / np.sqrt(float(n))) if scale is None else float(scale)
         G = np.empty((n, n))
-        L.or_mult_dense(n, seed, stream, s, _p(G), n)
+        if grid == "fp32":
+            L.or_mult_dense_f32(n, seed, stream, float(np.float32(s)), _p(G), n)
+        else:
+            L.or_mult_dense(n, seed, stream, s, _p(G), n)
         return {"kind": kind, "n": n, "G": G}
     if kind == KIND_CIRCULANT:
         s = 1.0 if scale is None else float(scale)
         g = np.empty(n)
-        L.or_mult_circulant(n, seed, stream, s, _p(g))
+        if grid == "fp32":
+            L.or_mult_circulant_f32(n, seed, stream, float(np.float32(s)), _p(g))
+        else:
+            L.or_mult_circulant(n, seed, stream, s, _p(g))
         out = {"kind": kind, "n": n, "g": g}
         if n <= 4096:
             G = np.empty((n, n))

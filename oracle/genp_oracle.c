@@ -123,6 +123,70 @@ OR_EXPORT double or_gauss(uint64_t seed, uint64_t stream, uint64_t tag, uint64_t
     return 0.0;
 }
 
+/* The same polar method carried out in IEEE single precision (used for
+ * multipliers on the FP32 grid): 24-bit uniforms, the atanh series to f^11
+ * (|f| <= 0.1716 leaves a truncation below 2^-27), single-precision +, -,
+ * *, / and sqrt.  Tags are those of the double-precision draws plus 4. */
+OR_EXPORT float or_log_f32(float s) {
+    uint32_t b;
+    memcpy(&b, &s, 4);
+    int e = (int)((b >> 23) & 0xff) - 127;
+    uint32_t mb = (b & 0x007FFFFFu) | (127u << 23);
+    float m;
+    memcpy(&m, &mb, 4);
+    const float SQRT2F = 1.41421354f, LN2F = 0.693147182f;
+    if (m > SQRT2F) { m = m * 0.5f; e = e + 1; }
+    float f = (m - 1.0f) / (m + 1.0f);
+    float f2 = f * f;
+    const int K = 5;
+    float p = 1.0f / (float)(2 * K + 1);
+    for (int k = K - 1; k >= 0; --k) {
+        float t = p * f2;
+        p = t + 1.0f / (float)(2 * k + 1);
+    }
+    float tf = 2.0f * f;
+    float lm = tf * p;
+    float el = (float)e * LN2F;
+    return el + lm;
+}
+
+OR_EXPORT float or_gauss_f32(uint64_t seed, uint64_t stream, uint64_t tag, uint64_t idx) {
+    uint64_t key[2] = {seed, stream};
+    for (uint64_t blk = 0; blk < OR_POLAR_BLOCKS; ++blk) {
+        uint64_t ctr[4] = {idx, blk, tag, 0}, w[4];
+        or_philox4x64_10(ctr, key, w);
+        for (int p = 0; p < 2; ++p) {
+            float u1 = (float)(uint32_t)(w[2 * p] >> 40) * 0x1.0p-24f;
+            float u2 = (float)(uint32_t)(w[2 * p + 1] >> 40) * 0x1.0p-24f;
+            float v1 = 2.0f * u1 - 1.0f, v2 = 2.0f * u2 - 1.0f;
+            float a = v1 * v1, c = v2 * v2;
+            float s = a + c;
+            if (s > 0.0f && s < 1.0f) {
+                float t = or_log_f32(s);
+                t = -2.0f * t;
+                t = t / s;
+                t = sqrtf(t);
+                return v1 * t;
+            }
+        }
+    }
+    return 0.0f;
+}
+
+/* Dense Gaussian multiplier drawn in single precision (FP32 grid):
+ * G[i][j] = fl32(scale * z32(i*n + j)), scale rounded to float first. */
+OR_EXPORT void or_mult_dense_f32(int64_t n, uint64_t seed, uint64_t stream, float scale, double *G, int64_t ldg) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j)
+            G[i * ldg + j] = (double)(or_gauss_f32(seed, stream, OR_TAG_DENSE + 4, (uint64_t)(i * n + j)) * scale);
+}
+
+OR_EXPORT void or_mult_circulant_f32(int64_t n, uint64_t seed, uint64_t stream, float scale, double *g) {
+    for (int64_t i = 0; i < n; ++i)
+        g[i] = (double)(or_gauss_f32(seed, stream, OR_TAG_CIRC + 4, (uint64_t)i) * scale);
+}
+
 /* Dense Gaussian multiplier (Definition 3.2, G in G_{0,scale}^{n x n}):
  * G[i][j] = scale * z(i*n + j). */
 OR_EXPORT void or_mult_dense(int64_t n, uint64_t seed, uint64_t stream, double scale,

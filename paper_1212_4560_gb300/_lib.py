@@ -43,6 +43,14 @@ SIGNATURES = {
     "genp_gemm_bf16": (_int, [_i64, _i64, _i64, ctypes.c_float, _vp, _i64, _vp, _i64, ctypes.c_float, _vp, _i64,
                               _vp, _i64, _vp]),
     "genp_device_check": (_int, [_int]),
+    "genp_batched_plan_create": (_int, [_i64, _vp, _i64, _int, _int, _int, _dbl, _int, _vp, ctypes.POINTER(_vp)]),
+    "genp_batched_layout": (_int, [_vp, _vp, _vp]),
+    "genp_batched_block_size": (_int, [_vp, _i64]),
+    "genp_batched_run": (_int, [_vp, _u64, _vp, _vp, _vp, _vp]),
+    "genp_batched_adjoint": (_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "genp_batched_status": (_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "genp_batched_multipliers": (_int, [_vp, _vp, _vp, _vp]),
+    "genp_batched_plan_destroy": (None, [_vp]),
     "genp_multiplier_export": (_int, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     "genp_multiplier_query": (_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_int), ctypes.POINTER(_int)]),
     "genp_multiplier_destroy": (None, [_vp]),

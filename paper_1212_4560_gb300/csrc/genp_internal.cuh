@@ -88,6 +88,28 @@ struct genp_factors {
 
 namespace genp {
 
+// One system of a batched solve (device array, built by genp_batched_plan).
+struct BatchDesc {
+    int64_t n;
+    int64_t mat_off;   // offset of this system's n x n blocks (A, C, G pools), elements
+    int64_t vec_off;   // offset of its n x nrhs blocks (B, X and workspace pools)
+    int64_t g_off;     // offset of its circulant first column (g pool)
+    int64_t sid;       // multiplier stream id (the system's index in the caller's order)
+    int nb;            // block size chosen for its size class
+    int pad;
+};
+
+// Per-system report of a batched solve.
+struct BatchStatus {
+    int64_t breakdown_step;
+    float min_abs_pivot, max_abs_pivot, max_abs_u, max_abs_c;
+    int refine_iters;
+    int status;
+    int escalated;     // refactored in FP64 after the FP32 refinement stalled
+    int pad;
+    double eta0, eta;
+};
+
 // ---------------------------------------------------------------------------
 // Launchers implemented in the .cu files (all enqueue on `s`, no sync).
 // ---------------------------------------------------------------------------
@@ -105,6 +127,8 @@ cudaError_t launch_make_sparse(int32_t *rows, int8_t *signs, int32_t *inv_rows, 
                                uint64_t stream_id, cudaStream_t s);
 cudaError_t launch_circulant_to_dense(const double *g, int64_t n, double *G, int64_t ldg,
                                       cudaStream_t s);
+cudaError_t launch_batch_draw(const BatchDesc *d, int count, uint64_t seed, bool circ, float *Gpool, float *gpool,
+                              cudaStream_t s);
 cudaError_t launch_sparse_to_dense(const int32_t *rows, const int8_t *signs, int64_t n, int nnz,
                                    double *G, int64_t ldg, cudaStream_t s);
 
@@ -163,6 +187,21 @@ template <typename T>
 cudaError_t split_cols_T(const T *src, int64_t lds, int64_t k, int64_t m, __nv_bfloat16 *dst, int64_t ldq, int terms,
                          cudaStream_t s);
 __host__ __device__ inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
+
+// batched.cu
+size_t batched_smem();
+int batched_blocks_per_sm();
+cudaError_t launch_batched(const BatchDesc *d, int count, int *counter, const void *Apool, bool a_f64,
+                           const double *Bpool, double *Xpool, float *Cpool, const float *Gpool, const float *gpool,
+                           float *Ypool, double *Rpool, double *scratch64, int nr, bool circ, int max_iter, double tol,
+                           BatchStatus *stat, int grid, cudaStream_t s);
+// Doubles of FP64 escalation scratch each persistent CTA needs.
+int64_t batched_scratch_stride();
+cudaError_t launch_batched_adjoint(const BatchDesc *d, int count, int *counter, const void *Apool, bool a_f64,
+                                   const float *Cpool, const float *Gpool, const float *gpool, const double *gXpool,
+                                   const double *Xpool, float *Ypool, double *Lpool, double *Rpool, double *dBpool,
+                                   float *dApool, int nr, bool circ, int max_iter, double tol, int grid,
+                                   cudaStream_t s);
 
 // lu.cu
 cudaError_t factor_run(genp_factors *F, cudaStream_t s);

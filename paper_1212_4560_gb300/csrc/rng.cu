@@ -78,6 +78,45 @@ __device__ double polar_normal(uint64_t seed, uint64_t sid, uint64_t tag, uint64
     return 0.0;
 }
 
+// The same polar method in IEEE single precision (multipliers on the FP32
+// grid): 24-bit uniforms, atanh series to f^11, tags shifted by 4.
+__device__ float ln_series_f32(float s) {
+    const unsigned b = __float_as_uint(s);
+    int e = (int)((b >> 23) & 0xffu) - 127;
+    float m = __uint_as_float((b & 0x007FFFFFu) | (127u << 23));
+    if (m > 1.41421354f) { m = __fmul_rn(m, 0.5f); e += 1; }
+    const float f = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float f2 = __fmul_rn(f, f);
+    const int K = 5;
+    float p = __fdiv_rn(1.0f, (float)(2 * K + 1));
+    for (int k = K - 1; k >= 0; --k) p = __fadd_rn(__fmul_rn(p, f2), __fdiv_rn(1.0f, (float)(2 * k + 1)));
+    const float lm = __fmul_rn(__fmul_rn(2.0f, f), p);
+    const float el = __fmul_rn((float)e, 0.693147182f);
+    return __fadd_rn(el, lm);
+}
+
+__device__ float polar_normal_f32(uint64_t seed, uint64_t sid, uint64_t tag, uint64_t idx) {
+    for (uint64_t blk = 0; blk < kPolarBlocks; ++blk) {
+        const U4 w = philox(idx, blk, tag, 0, seed, sid);
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const float u1 = __fmul_rn((float)(uint32_t)(w.w[2 * p] >> 40), 5.96046448e-8f /* 2^-24 */);
+            const float u2 = __fmul_rn((float)(uint32_t)(w.w[2 * p + 1] >> 40), 5.96046448e-8f);
+            const float v1 = __fsub_rn(__fmul_rn(2.0f, u1), 1.0f);
+            const float v2 = __fsub_rn(__fmul_rn(2.0f, u2), 1.0f);
+            const float s = __fadd_rn(__fmul_rn(v1, v1), __fmul_rn(v2, v2));
+            if (s > 0.0f && s < 1.0f) {
+                float t = ln_series_f32(s);
+                t = __fmul_rn(-2.0f, t);
+                t = __fdiv_rn(t, s);
+                t = __fsqrt_rn(t);
+                return __fmul_rn(v1, t);
+            }
+        }
+    }
+    return 0.0f;
+}
+
 // Round a finite double to the nearest BF16 value (ties to even) by clearing
 // the 45 low mantissa bits with a round-to-nearest-even bias.
 __device__ __forceinline__ double round_to_bf16_grid(double x) {
@@ -99,7 +138,10 @@ __global__ void k_dense(double *G, int64_t n, uint64_t seed, uint64_t sid, doubl
     const int64_t total = n * n;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const double v = on_grid(__dmul_rn(polar_normal(seed, sid, kTagDense, (uint64_t)idx), scale), grid);
+        const double v =
+            grid == GENP_FP32
+                ? (double)__fmul_rn(polar_normal_f32(seed, sid, kTagDense + 4, (uint64_t)idx), __double2float_rn(scale))
+                : on_grid(__dmul_rn(polar_normal(seed, sid, kTagDense, (uint64_t)idx), scale), grid);
         G[idx] = v;
         if (G32) G32[idx] = (float)v;
         if (Gbf) Gbf[(idx % n) * round8(n) + idx / n] = __float2bfloat16_rn((float)v);  // G^T, K-major
@@ -108,7 +150,9 @@ __global__ void k_dense(double *G, int64_t n, uint64_t seed, uint64_t sid, doubl
 
 __global__ void k_circ(double *g, int64_t n, uint64_t seed, uint64_t sid, double scale, genp_prec grid) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        g[i] = on_grid(__dmul_rn(polar_normal(seed, sid, kTagCirc, (uint64_t)i), scale), grid);
+        g[i] = grid == GENP_FP32
+                   ? (double)__fmul_rn(polar_normal_f32(seed, sid, kTagCirc + 4, (uint64_t)i), __double2float_rn(scale))
+                   : on_grid(__dmul_rn(polar_normal(seed, sid, kTagCirc, (uint64_t)i), scale), grid);
 }
 
 // Uniform integer in [0, range) (Lemire's multiply-shift with rejection).
@@ -196,6 +240,25 @@ __global__ void k_sparse_dense(const int32_t *rows, const int8_t *signs, int64_t
         }
 }
 
+// Multipliers of a batch, drawn in single precision (FP32 grid): system i's
+// dense G (n x n, at mat_off) or circulant first column g (n, at g_off) with
+// stream id sid_i, entries scale_i * z32(idx), scale_i = fl32(1/sqrt(n_i))
+// for the dense kind and 1 for the circulant.  One CTA per system.
+__global__ void k_batch_draw(const BatchDesc *d, int count, uint64_t seed, int circ, float *Gpool, float *gpool) {
+    for (int s = blockIdx.x; s < count; s += gridDim.x) {
+        const BatchDesc q = d[s];
+        if (circ) {
+            for (int64_t i = threadIdx.x; i < q.n; i += blockDim.x)
+                gpool[q.g_off + i] = polar_normal_f32(seed, (uint64_t)q.sid, kTagCirc + 4, (uint64_t)i);
+        } else {
+            const float scale = __double2float_rn(1.0 / sqrt((double)q.n));
+            for (int64_t idx = threadIdx.x; idx < q.n * q.n; idx += blockDim.x)
+                Gpool[q.mat_off + idx] =
+                    __fmul_rn(polar_normal_f32(seed, (uint64_t)q.sid, kTagDense + 4, (uint64_t)idx), scale);
+        }
+    }
+}
+
 int grid_for(int64_t work, int threads) {
     int64_t b = cdiv(work, threads);
     if (b > 152 * 32) b = 152 * 32;
@@ -230,6 +293,14 @@ cudaError_t launch_make_sparse(int32_t *rows, int8_t *signs, int32_t *inv_rows, 
     k_perm_shuffle<<<nnz, 32, 0, s>>>(rows, scratch, n);
     note_launch();
     k_invert<<<grid_for(n * nnz, 256), 256, 0, s>>>(rows, signs, inv_rows, inv_signs, n, nnz);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_draw(const BatchDesc *d, int count, uint64_t seed, bool circ, float *Gpool, float *gpool,
+                              cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    note_launch();
+    k_batch_draw<<<152 * 8 < count ? 152 * 8 : count, 256, 0, s>>>(d, count, seed, circ ? 1 : 0, Gpool, gpool);
     return cudaGetLastError();
 }
 

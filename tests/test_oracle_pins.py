@@ -81,6 +81,40 @@ def test_gaussian_distribution():
     assert not np.any(G2 == G)
 
 
+def test_own_log_f32_accuracy():
+    rng = np.random.default_rng(1)
+    xs = np.concatenate([rng.uniform(2**-40, 1.0, 20000).astype(np.float32), [0.5, 0.25, 1 - 2**-24]])
+    for x in xs:
+        x = float(np.float32(x))
+        got, ref = oracle.log_f32(x), math.log(x)
+        assert abs(got - ref) <= 3 * abs(ref) * 2**-23 + 1e-45, (x, got, ref)
+    for k in range(1, 40):
+        assert oracle.log_f32(2.0**-k) == float(np.float32(-k * np.float32(0.693147182)))
+
+
+def test_gaussian_f32_distribution():
+    """Single-precision draws: moments and KS on 250k samples, values on the
+    FP32 grid, scale rounded to float."""
+    n = 500
+    G = oracle.multiplier(0, n, seed=13, grid="fp32")["G"]
+    assert np.array_equal(G.astype(np.float32).astype(np.float64), G)
+    z = G.ravel() / float(np.float32(1 / math.sqrt(n)))
+    assert abs(z.mean()) < 0.01 and abs(z.std() - 1.0) < 0.01
+    assert st.kstest(z, "norm").pvalue > 1e-3
+    # one entry recomputed with numpy float32 arithmetic from the raw words
+    w = oracle.philox4x64_10([0, 0, 0x14, 0], [13, 0])
+    for p in range(2):
+        u1 = np.float32(int(w[2 * p]) >> 40) * np.float32(2.0**-24)
+        u2 = np.float32(int(w[2 * p + 1]) >> 40) * np.float32(2.0**-24)
+        v1, v2 = np.float32(2) * u1 - np.float32(1), np.float32(2) * u2 - np.float32(1)
+        s = v1 * v1 + v2 * v2
+        if 0 < s < 1:
+            ref = float(v1) * math.sqrt(-2 * math.log(float(s)) / float(s))
+            got = oracle.gauss_f32(13, 0, 0x14, 0)
+            assert abs(got - ref) <= 8 * abs(ref) * 2**-23
+            break
+
+
 def test_polar_method_by_hand():
     """Recompute one entry's polar step from the raw Philox words with
     math.log / math.sqrt; equal to within 2 ulp of the result."""

@@ -35,8 +35,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solves/s & TFLOP/s (2n³/3), BF16+IR vs FP64 GENP, same GB300, bwd err ≤1e-14"
 KINDS = {"gaussian": 0, "circulant": 1, "sparse": 2}
-PRECS = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 4}
-GRID_OF = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 2}
+PRECS = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 4, "sliced": 5}
+GRID_OF = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 2, "sliced": 0}
+F64_FACTORS = ("fp64", "sliced")
 
 
 def measured_peaks():
@@ -66,6 +67,9 @@ def parse():
     p.add_argument("--count", type=int, default=None, help="systems in the batched / diff workloads")
     p.add_argument("--kappa", type=float, default=1e2, help="condition number of the svd workload")
     p.add_argument("--prec", default="fp64", choices=list(PRECS))
+    p.add_argument("--digits", type=int, default=0, help="digits per operand of the sliced precision (5, 6, 7)")
+    p.add_argument("--refine", default=None, choices=["classic", "gmres"],
+                   help="refinement method (default: classic for fp64, GMRES-IR otherwise)")
     p.add_argument("--max-iter", type=int, default=None)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -74,9 +78,10 @@ def parse():
 
 
 def workload_name(a):
+    prec = a.prec + (str(a.digits or 7) if a.prec == "sliced" else "")
     if a.workload == "svd":
-        return f"genp_{a.prec}_n{a.n}_svd_kappa{a.kappa:.0e}_{a.kind}_{a.nrhs}rhs"
-    return f"genp_{a.prec}_n{a.n}_{a.kind}_{a.nrhs}rhs"
+        return f"genp_{prec}_n{a.n}_svd_kappa{a.kappa:.0e}_{a.kind}_{a.nrhs}rhs"
+    return f"genp_{prec}_n{a.n}_{a.kind}_{a.nrhs}rhs"
 
 
 def flops_per_solve(a):
@@ -285,8 +290,11 @@ def run_ours(a):
         A = A_cpu.to(dev)
         B = B_cpu.to(dev)
     prec = PRECS[a.prec]
-    cdt = torch.float64 if a.prec == "fp64" else torch.float32
-    max_iter = a.max_iter if a.max_iter is not None else (10 if a.prec == "fp64" else 30)
+    if a.digits:
+        genp._lib.load().genp_sliced_digits(a.digits)
+    cdt = torch.float64 if a.prec in F64_FACTORS else torch.float32
+    method = {"classic": 0, "gmres": 1}[a.refine or ("classic" if a.prec == "fp64" else "gmres")]
+    max_iter = a.max_iter if a.max_iter is not None else (10 if a.prec == "fp64" or method == 1 else 30)
     C = torch.empty((n, n), dtype=cdt, device=dev)
     X = torch.empty((n, nrhs), dtype=torch.float64, device=dev)
     dA = torch.empty((n, n), dtype=cdt, device=dev)
@@ -310,7 +318,7 @@ def run_ours(a):
         mark(3)
         genp.solve(F, G, B, X)
         mark(4)
-        genp.refine(A, F, G, B, X, tol=a.tol, max_iter=max_iter)
+        genp.refine(A, F, G, B, X, tol=a.tol, max_iter=max_iter, method=method)
         mark(5)
         genp.adjoint(F, G, X, X, dA, dB)
         mark(6)
@@ -390,7 +398,16 @@ def run_ours(a):
 
     # dominant kernel: the GEMM of C = A G (one launch per BF16 term / per FP64 call)
     peaks = measured_peaks()
-    if a.kind == "gaussian" and a.prec in ("bf16", "bf16x3"):
+    if a.kind == "gaussian" and a.prec == "sliced":
+        nd = genp._lib.load().genp_sliced_digits(0)
+        pairs = nd * (nd + 1) // 2
+        achieved = pairs * 2.0 * n**3 / (phase_ms["precondition"] / 1e3) / 1e12
+        peak = float(peaks.get("bf16_tflops", 1900.0))
+        roofline = {"kernel": f"k_tc_sliced<{nd}> (tcgen05 BF16, C = A G as {pairs} digit products)",
+                    "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "peak_source": "measured bf16_tflops (burst)" if "bf16_tflops" in peaks else "fallback",
+                    "traffic": None}
+    elif a.kind == "gaussian" and a.prec in ("bf16", "bf16x3"):
         terms = 3 if a.prec == "bf16x3" else 1
         achieved = terms * 2.0 * n**3 / (phase_ms["precondition"] / 1e3) / 1e12
         peak = float(peaks.get("bf16_tflops", 1900.0))
@@ -426,7 +443,8 @@ def run_ours(a):
                          f"system of the same recipe ({nrhs} RHS), median of 3, time scaled by (n/{n_s})^3 to n={n}"}
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32"}.get(a.prec, a.prec), "data": "synthetic",
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "sliced": "bf16"}.get(a.prec, a.prec),
+            "data": "synthetic",
             "config": {"workload": workload_name(a), "n": n, "nrhs": nrhs, "multiplier": a.kind, "precision": a.prec,
                        "A": ("J U diag(sigma) V^T, kappa=%g" % a.kappa) if a.workload == "svd"
                        else "N(0,1) with leading 64x64 block of rank 32",
@@ -434,6 +452,7 @@ def run_ours(a):
                        "parallelism": "replicas" if world > 1 else "single"},
             "bwd_err_unrefined": info.bwd_err[0] if info.bwd_err else None,
             "converged": bool(info.bwd_err) and info.bwd_err[-1] <= a.tol,
+            "refine_method": ["classic", "gmres"][method],
             "tflops": tflops, "tflops_counted": {"factor_2n3_over_3": fact, "AG": ag},
             "phases_ms": phase_ms, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "gpu_launches_per_step": launches / a.steps,

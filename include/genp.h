@@ -84,19 +84,33 @@ typedef enum {
  *  BF16X3: as BF16, but every operand is split into three BF16 terms and
  *        six of their products are accumulated (a1b1 + a1b2 + a2b1 + a1b3 +
  *        a2b2 + a3b1), which brings the tensor-core products close to FP32
- *        accuracy at six times the BF16 work. */
+ *        accuracy at six times the BF16 work.
+ *  BF16_SLICED: C and the factors are double, as for FP64; the diagonal
+ *        blocks and the block row and column are solved in FP64, while the
+ *        Schur-complement product (and, for a Gaussian multiplier, A G) runs
+ *        on the BF16 tensor cores: each FP64 operand row / column gets a
+ *        power-of-two scale and is cut into 5, 6 or 7 exact 7-bit digits
+ *        (genp_sliced_digits), and the digit products of the leading
+ *        weights are accumulated in FP32, all but the smallest weight group
+ *        exactly (Ozaki, Ogita, Oishi and Rump's error-free splitting).  With
+ *        7 digits the products carry about 46 correct bits against the
+ *        operands' scales; the trailing matrix is held as double-float pairs
+ *        (48 bits) between steps.  FP64 refinement takes the solve to FP64
+ *        accuracy. */
 typedef enum {
     GENP_FP64 = 0,
     GENP_FP32 = 1,
     GENP_BF16 = 2,
     GENP_FP8_E4M3 = 3,
-    GENP_BF16X3 = 4
+    GENP_BF16X3 = 4,
+    GENP_BF16_SLICED = 5
 } genp_prec;
 
 typedef struct genp_multiplier genp_multiplier;
 typedef struct genp_factors genp_factors;
 
 #define GENP_MAX_REFINE 32
+#define GENP_GMRES_RESTART 30
 
 /* Host-side report filled by genp_info_fetch. */
 typedef struct {
@@ -160,10 +174,12 @@ GENP_API void genp_multiplier_destroy(genp_multiplier *G);
 
 /* C = A G  (Thm. 4.1, the MH product; Cor. 4.1).
  *  A      n x n, ld lda; double if a_prec == GENP_FP64, float if GENP_FP32.
- *  C      n x n, ld ldc; double if c_prec == GENP_FP64, else float.  C must
- *         not overlap A.
+ *  C      n x n, ld ldc; double if c_prec is GENP_FP64 or GENP_BF16_SLICED,
+ *         else float.  C must not overlap A.
  *  c_prec the factorization the product is for: FP64 (DFMA), FP32 (FFMA),
- *         BF16 (tensor cores, A rounded to BF16, G must have value_grid BF16).
+ *         BF16 (tensor cores, A rounded to BF16, G must have value_grid BF16),
+ *         BF16_SLICED (A double; a dense G on the tensor cores by digit
+ *         slicing, in K chunks of 512; about 35 bits; other kinds as FP64).
  * Dense G costs 2n^3 flops; a circulant G is applied by FFT in
  * O(n^2 log n) (Thm. 2.1) when n is a power of two <= 8192; the sparse G is
  * a signed gather of nnz columns per output column. */
@@ -176,7 +192,7 @@ GENP_API genp_status genp_precondition(const genp_multiplier *G, const void *A, 
  * block column of L, update the trailing Schur complement
  * A22 <- A22 - L21 U12, repeat.  On completion the strict lower triangle of
  * C holds L (unit diagonal implied) and the upper triangle holds U.
- *  C      n x n, ld ldc, double for FP64, float otherwise (caller-owned;
+ *  C      n x n, ld ldc, double for FP64 and BF16_SLICED, float otherwise (caller-owned;
  *         the handle refers to it until destroyed or refactored).
  *  out    receives a new factors handle (status word and workspace).
  * A zero or non-finite pivot does not stop the elimination; its step is
@@ -207,7 +223,17 @@ GENP_API genp_status genp_solve(const genp_factors *F, const genp_multiplier *G,
  * stop is decided on the device (no host synchronization).
  *  A      the ORIGINAL n x n matrix in double (C = A G), ld lda.
  *  X      on entry the solution of genp_solve, on exit the refined one.
- *  method 0 = classic refinement (the only method of this build).
+ *  method 0 = classic refinement: d = U^{-1} L^{-1} r.
+ *         1 = GMRES-IR (Carson and Higham): C d = r is solved by FP64
+ *             GMRES on the left-preconditioned system
+ *             U^{-1} L^{-1} A G d = U^{-1} L^{-1} r, at most
+ *             GENP_GMRES_RESTART Krylov vectors per step, to a relative
+ *             residual of 1e-10; C v is applied as A (G v).  It converges
+ *             when the factors are only a fair preconditioner (low-precision
+ *             factors of a matrix with large element growth), where classic
+ *             refinement stagnates.  Needs (GENP_GMRES_RESTART + 4) n nrhs
+ *             doubles of workspace (allocated by the library on first use).
+ *  nrhs   at most 16.
  * genp_info.bwd_err / refine_iters report the history; status
  * GENP_ERR_NOCONV if the final eta is above tol. */
 GENP_API genp_status genp_refine(const double *A, int64_t lda, const genp_factors *F, const genp_multiplier *G,
@@ -308,9 +334,34 @@ GENP_API genp_status genp_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha
                                     const void *Bt, int64_t ldb, float beta, const float *Cin, int64_t ldci,
                                     float *D, int64_t ldd, void *cuda_stream);
 
-/* Synchronizes the device and reports whether any tensor-core kernel of this
- * library gave up a bounded wait (GENP_ERR_TIMEOUT) since the last clear;
- * `clear` != 0 resets the flag.  GENP_OK otherwise. */
+/* Tensor-core building block of the BF16_SLICED path:
+ *   D = alpha * A * B + beta * D      (all FP64, row-major)
+ * with A * B formed on the BF16 tensor cores from exact 7-bit digit slices
+ * (see GENP_BF16_SLICED), in K chunks of at most 512 summed in
+ * double-float, and one rounding to FP64 at the end.  Per entry and chunk
+ * the error is about 2^-(7 digits - 1) * 4 * K_c * max_k|a_ik| * max_k|b_kj|
+ * at worst (far less for sums with mixed signs); products of integers with
+ * |a|, |b| <= 127 are exact for K <= 2^20.  digits: 5, 6, 7 or 0 (the
+ * setting of genp_sliced_digits).
+ *  A      m x K, ld lda;  B  K x n, ld ldb;  D  m x n, ld ldd.
+ *  Allocates its workspace with cudaMallocAsync on the stream.
+ * Errors: GENP_ERR_ARG (sizes), GENP_ERR_NOMEM, GENP_ERR_CUDA. */
+GENP_API genp_status genp_gemm_sliced(int64_t m, int64_t n, int64_t K, double alpha, const double *A, int64_t lda,
+                                      const double *B, int64_t ldb, double beta, double *D, int64_t ldd, int digits,
+                                      void *cuda_stream);
+
+/* Digits per operand of the BF16_SLICED path: 5 (15 digit products per
+ * multiply-add, about 32 correct bits on Gaussian data), 6 (21, about 39) or
+ * 7 (28, about 46; the default).  digits == 0 returns the current setting;
+ * otherwise sets it for every later genp_factor / genp_precondition /
+ * genp_gemm_sliced call of the process and returns the previous one, or -1
+ * if digits is not supported.  Not synchronized with concurrent calls. */
+GENP_API int genp_sliced_digits(int digits);
+
+/* Synchronizes the device and reports whether any kernel of this library
+ * that waits on the device (the tensor-core pipelines, the persistent
+ * triangular solves) gave up a bounded wait (GENP_ERR_TIMEOUT) since the
+ * last clear; `clear` != 0 resets the flags.  GENP_OK otherwise. */
 GENP_API genp_status genp_device_check(int clear);
 
 /* Allocation-free draw of the SPARSE_PM1 multiplier.  The paper has no

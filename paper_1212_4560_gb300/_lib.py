@@ -16,7 +16,7 @@ STATUS_NAMES = {0: "GENP_OK", -1: "GENP_ERR_ARG", -2: "GENP_ERR_BREAKDOWN", -3: 
                 -4: "GENP_ERR_CUDA", -5: "GENP_ERR_TIMEOUT", -6: "GENP_ERR_NOMEM", -7: "GENP_ERR_UNSUPPORTED"}
 
 GAUSSIAN, CIRCULANT, SPARSE_PM1 = 0, 1, 2
-FP64, FP32, BF16, FP8_E4M3, BF16X3 = 0, 1, 2, 3, 4
+FP64, FP32, BF16, FP8_E4M3, BF16X3, BF16_SLICED = 0, 1, 2, 3, 4, 5
 MAX_REFINE = 32
 
 _vp = ctypes.c_void_p
@@ -42,6 +42,8 @@ SIGNATURES = {
     "genp_make_sparse_noalloc": (_int, [_i64, _int, _u64, _u64, _vp, _vp, _vp, _vp, _vp]),
     "genp_gemm_bf16": (_int, [_i64, _i64, _i64, ctypes.c_float, _vp, _i64, _vp, _i64, ctypes.c_float, _vp, _i64,
                               _vp, _i64, _vp]),
+    "genp_gemm_sliced": (_int, [_i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _int, _vp]),
+    "genp_sliced_digits": (_int, [_int]),
     "genp_device_check": (_int, [_int]),
     "genp_batched_plan_create": (_int, [_i64, _vp, _i64, _int, _int, _int, _dbl, _int, _vp, ctypes.POINTER(_vp)]),
     "genp_batched_layout": (_int, [_vp, _vp, _vp]),

@@ -13,7 +13,7 @@ from dataclasses import dataclass
 import torch
 
 from . import _lib
-from ._lib import BF16, BF16X3, CIRCULANT, FP8_E4M3, FP32, FP64, GAUSSIAN, SPARSE_PM1, GenpError, check
+from ._lib import BF16, BF16_SLICED, BF16X3, CIRCULANT, FP8_E4M3, FP32, FP64, GAUSSIAN, SPARSE_PM1, GenpError, check
 
 _PREC_OF_DTYPE = {torch.float64: FP64, torch.float32: FP32}
 
@@ -168,19 +168,20 @@ def info_fetch(F: Factors, stream=None) -> Info:
 
 
 def solve_system(A: torch.Tensor, B: torch.Tensor, kind: int = GAUSSIAN, seed: int = 0, prec: int = FP64,
-                 refine_steps: int = 10, tol: float = 1e-15, nb: int = 0, stream=None):
+                 refine_steps: int = 10, tol: float = 1e-15, nb: int = 0, method: int = 0, stream=None):
     """The whole method on one system: G, C = A G, GENP(C), X = G U^-1 L^-1 B,
-    FP64 refinement.  Returns (X, info, G, F)."""
+    FP64 refinement (method 0 classic, 1 GMRES-IR).  Returns (X, info, G, F)."""
     n = A.size(0)
-    grid = FP64 if prec == FP64 else (BF16 if prec in (BF16, BF16X3) else FP32)
+    f64 = prec in (FP64, BF16_SLICED)
+    grid = FP64 if f64 else (BF16 if prec in (BF16, BF16X3) else FP32)
     G = make_multiplier(kind, n, seed, value_grid=grid, stream=stream)
-    C = torch.empty((n, n), dtype=torch.float64 if prec == FP64 else torch.float32, device=A.device)
+    C = torch.empty((n, n), dtype=torch.float64 if f64 else torch.float32, device=A.device)
     A64 = A if A.dtype == torch.float64 else A.double()
-    precondition(G, A if prec != FP64 else A64, C, c_prec=prec, stream=stream)
+    precondition(G, A64 if f64 else A, C, c_prec=prec, stream=stream)
     F = factor(C, prec=prec, nb=nb, stream=stream)
     B64 = B.double().contiguous()
     X = torch.empty_like(B64)
     solve(F, G, B64, X, stream=stream)
     if refine_steps > 0:
-        refine(A64, F, G, B64, X, tol=tol, max_iter=refine_steps, stream=stream)
+        refine(A64, F, G, B64, X, tol=tol, max_iter=refine_steps, method=method, stream=stream)
     return X, info_fetch(F, stream=stream), G, F

@@ -79,7 +79,9 @@ cudaError_t draw_multiplier(genp_multiplier *G, uint64_t seed, uint64_t stream_i
     return cudaErrorInvalidValue;
 }
 
-bool factor_prec_ok(genp_prec p) { return p == GENP_FP64 || p == GENP_FP32 || p == GENP_BF16 || p == GENP_BF16X3; }
+bool factor_prec_ok(genp_prec p) {
+    return p == GENP_FP64 || p == GENP_FP32 || p == GENP_BF16 || p == GENP_BF16X3 || p == GENP_BF16_SLICED;
+}
 bool tc_prec(genp_prec p) { return p == GENP_BF16 || p == GENP_BF16X3; }
 
 // Grows the factors workspace to at least `bytes` (synchronizes the stream
@@ -220,11 +222,46 @@ genp_status genp_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha, const v
     return GENP_OK;
 }
 
+int genp_sliced_digits(int digits) {
+    if (digits == 0) return sliced_digits();
+    return set_sliced_digits(digits);
+}
+
+genp_status genp_gemm_sliced(int64_t m, int64_t n, int64_t K, double alpha, const double *A, int64_t lda,
+                             const double *B, int64_t ldb, double beta, double *D, int64_t ldd, int digits,
+                             void *cuda_stream) {
+    if (m < 0 || n < 0 || K < 1 || !A || !B || !D) return GENP_ERR_ARG;
+    const int nd = digits == 0 ? sliced_digits() : digits;
+    if (nd < 5 || nd > 7) return GENP_ERR_ARG;
+    if (lda < K || ldb < n || ldd < n) return GENP_ERR_ARG;
+    if (m > INT32_MAX || n > INT32_MAX || cdiv(m, 128) > 65535) return GENP_ERR_ARG;
+    if (m == 0 || n == 0) return GENP_OK;
+    cudaStream_t s = S(cuda_stream);
+    const int64_t ldq = kSlicedLdq, ldw = round8(n);
+    const size_t wbytes = (size_t)m * ldw * 8, abytes = (size_t)m * ldq * 2, bbytes = (size_t)n * ldq * 2;
+    char *buf = nullptr;
+    if (cudaMallocAsync((void **)&buf, wbytes + abytes + bbytes + (size_t)(m + n) * sizeof(int) + 256, s) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return GENP_ERR_NOMEM;
+    }
+    dfloat *W = reinterpret_cast<dfloat *>(buf);
+    __nv_bfloat16 *Aq = reinterpret_cast<__nv_bfloat16 *>(buf + wbytes);
+    __nv_bfloat16 *Bq = reinterpret_cast<__nv_bfloat16 *>(buf + wbytes + abytes);
+    int *ex = reinterpret_cast<int *>(buf + wbytes + abytes + bbytes);
+    cudaError_t e = sliced_matmul(nd, m, n, K, A, lda, B, ldb, W, ldw, Aq, Bq, ex, s);
+    if (e == cudaSuccess) e = df_axpby(alpha, W, ldw, beta, D, ldd, m, n, s);
+    cudaError_t f = cudaFreeAsync(buf, s);
+    CU(e);
+    CU(f);
+    return GENP_OK;
+}
+
 genp_status genp_device_check(int clear) {
     CU(cudaDeviceSynchronize());
-    const int v = tc_timeout_flag(clear != 0);
-    if (v < 0) return GENP_ERR_CUDA;
-    return v ? GENP_ERR_TIMEOUT : GENP_OK;
+    const int v = tc_timeout_flag(clear != 0), w = solve_timeout_flag(clear != 0);
+    if (v < 0 || w < 0) return GENP_ERR_CUDA;
+    return (v || w) ? GENP_ERR_TIMEOUT : GENP_OK;
 }
 
 genp_status genp_multiplier_export(const genp_multiplier *G, double *dense, int64_t ldd, double *first_col,
@@ -270,8 +307,26 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
     if (a_prec != GENP_FP64 && a_prec != GENP_FP32) return GENP_ERR_ARG;
     if (c_prec == GENP_FP8_E4M3) return GENP_ERR_UNSUPPORTED;
     if (!factor_prec_ok(c_prec)) return GENP_ERR_ARG;
-    if (c_prec == GENP_FP64 && a_prec != GENP_FP64) return GENP_ERR_ARG;
+    if (f64_factors(c_prec) && a_prec != GENP_FP64) return GENP_ERR_ARG;
     cudaStream_t s = S(cuda_stream);
+    if (c_prec == GENP_BF16_SLICED && G->kind == GENP_MULT_GAUSSIAN) {
+        // C = A G with FP64-class accuracy on the BF16 tensor cores, summed
+        // in double-float and rounded to FP64 once.
+        const int nd = sliced_digits();
+        const int64_t ldq = (int64_t)nd * kSlicedChunk, ldd = round8(n);
+        char *buf = nullptr;
+        const size_t dbytes = (size_t)n * ldd * 8, qbytes = (size_t)n * ldq * sizeof(__nv_bfloat16);
+        CU(cudaMallocAsync((void **)&buf, dbytes + 2 * qbytes + (size_t)2 * n * sizeof(int) + 256, s));
+        dfloat *D = reinterpret_cast<dfloat *>(buf);
+        __nv_bfloat16 *Aq = reinterpret_cast<__nv_bfloat16 *>(buf + dbytes);
+        __nv_bfloat16 *Bq = Aq + (size_t)n * ldq;
+        int *ex = reinterpret_cast<int *>(Bq + (size_t)n * ldq);
+        CU(sliced_matmul(nd, n, n, n, static_cast<const double *>(A), lda, G->dense, n, D, ldd, Aq, Bq, ex, s));
+        CU(df_to_f64(D, ldd, static_cast<double *>(C), ldc, n, n, s));
+        CU(cudaFreeAsync(buf, s));
+        return GENP_OK;
+    }
+    if (c_prec == GENP_BF16_SLICED) c_prec = GENP_FP64;   // circulant / sparse products: FP64 FFT / gather
     if (tc_prec(c_prec) && G->kind == GENP_MULT_GAUSSIAN) {
         // Tensor cores: C = sum_t a_t G over the BF16 terms a_t of A (one term
         // for BF16, three for BF16X3); G is exact on the BF16 grid.
@@ -345,7 +400,7 @@ genp_status genp_factor(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t
     if (!C || n < 1 || n > 2147483647LL || ldc < n) return GENP_ERR_ARG;
     if (prec == GENP_FP8_E4M3) return GENP_ERR_UNSUPPORTED;
     if (!factor_prec_ok(prec)) return GENP_ERR_ARG;
-    if (nb == 0) nb = tc_prec(prec) ? 128 : 64;
+    if (nb == 0) nb = (tc_prec(prec) || prec == GENP_BF16_SLICED) ? 128 : 64;
     if (nb < 1 || nb > 128) return GENP_ERR_ARG;
     cudaStream_t s = S(cuda_stream);
     genp_factors *F = new (std::nothrow) genp_factors();
@@ -358,10 +413,24 @@ genp_status genp_factor(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t
     F->last_stream = s;
     genp_status st = dalloc(&F->st, 1);
     if (st == GENP_OK) st = dalloc(&F->norms, 2);
+    if (st == GENP_OK) st = dalloc(&F->trsv_sync, (size_t)trsv_sync_ints(n));
+    if (st == GENP_OK) {
+        if (f64_factors(prec)) st = dalloc(reinterpret_cast<double **>(&F->dinv), (size_t)diag_inverse_elems(n));
+        else st = dalloc(reinterpret_cast<float **>(&F->dinv), (size_t)diag_inverse_elems(n));
+    }
     if (st == GENP_OK && tc_prec(prec)) {
         F->tc_ldq = round8(nb * split_terms(prec));
         st = dalloc(&F->tcA, (size_t)n * F->tc_ldq);
         if (st == GENP_OK) st = dalloc(&F->tcB, (size_t)n * F->tc_ldq);
+    }
+    if (st == GENP_OK && prec == GENP_BF16_SLICED) {
+        F->nd = sliced_digits();
+        F->tc_ldq = (int64_t)F->nd * sliced_kpad(nb);
+        F->ldw = n;
+        st = dalloc(&F->tcA, (size_t)n * F->tc_ldq);
+        if (st == GENP_OK) st = dalloc(&F->tcB, (size_t)n * F->tc_ldq);
+        if (st == GENP_OK) st = dalloc(reinterpret_cast<double **>(&F->W), (size_t)n * F->ldw);
+        if (st == GENP_OK) st = dalloc(&F->exps, (size_t)2 * n);
     }
     if (st == GENP_OK && cudaMallocHost(&F->host_info, sizeof(DevStatus)) != cudaSuccess) {
         cudaGetLastError();
@@ -396,6 +465,10 @@ void genp_factors_destroy(genp_factors *F) {
     cudaFree(F->work);
     cudaFree(F->tcA);
     cudaFree(F->tcB);
+    cudaFree(F->W);
+    cudaFree(F->exps);
+    cudaFree(F->trsv_sync);
+    cudaFree(F->dinv);
     if (F->host_info) cudaFreeHost(F->host_info);
     delete F;
 }
@@ -412,7 +485,7 @@ genp_status genp_solve(const genp_factors *F, const genp_multiplier *G, const do
     TRY(ensure_work(Fm, yd + yf, s));
     double *Y = static_cast<double *>(F->work);
     float *Yf = reinterpret_cast<float *>(static_cast<char *>(F->work) + yd);
-    if (F->prec == GENP_FP64) {
+    if (f64_factors(F->prec)) {
         CU((convert_matrix<double, double>(B, ldb, Y, nrhs, n, nrhs, nullptr, s)));
         CU(lu_solve_inplace<double>(F, Y, nrhs, nrhs, false, nullptr, s));
     } else {
@@ -432,10 +505,16 @@ genp_status genp_refine(const double *A, int64_t lda, const genp_factors *F, con
     const int64_t n = F->n;
     if (G->n != n || lda < n || nrhs < 1 || ldb < nrhs || ldx < nrhs) return GENP_ERR_ARG;
     if (max_iter < 0 || max_iter > GENP_MAX_REFINE || !(tol >= 0.0)) return GENP_ERR_ARG;
-    if (method != 0) return method == 1 ? GENP_ERR_UNSUPPORTED : GENP_ERR_ARG;
+    if (method != 0 && method != 1) return GENP_ERR_ARG;
     if (nrhs > kMaxRhsChunk) return GENP_ERR_UNSUPPORTED;
     cudaStream_t s = S(cuda_stream);
     genp_factors *Fm = const_cast<genp_factors *>(F);
+    if (method == 1) {
+        TRY(ensure_work(Fm, gmres_work_bytes(n, nrhs), s));
+        CU(refine_gmres(Fm, G, A, lda, B, ldb, nrhs, X, ldx, tol, max_iter, F->work, s));
+        Fm->last_stream = s;
+        return GENP_OK;
+    }
     const size_t rd = align256((size_t)n * nrhs * sizeof(double)), yf = align256((size_t)n * nrhs * sizeof(float));
     TRY(ensure_work(Fm, rd + yf, s));
     double *R = static_cast<double *>(F->work);
@@ -446,7 +525,7 @@ genp_status genp_refine(const double *A, int64_t lda, const genp_factors *F, con
         CU(gemm<double>(n, nrhs, n, -1.0, A, lda, false, X, ldx, 1.0, B, ldb, R, nrhs, done, s));
         CU(refine_check(Fm, R, nrhs, X, ldx, B, ldb, n, nrhs, it, tol, max_iter, 1, s));
         if (it == max_iter) break;
-        if (F->prec == GENP_FP64) {
+        if (f64_factors(F->prec)) {
             CU(lu_solve_inplace<double>(F, R, nrhs, nrhs, false, done, s));
         } else {
             CU((convert_matrix<double, float>(R, nrhs, Rf, nrhs, n, nrhs, done, s)));
@@ -474,7 +553,7 @@ genp_status genp_adjoint(const genp_factors *F, const genp_multiplier *G, const 
     double *Lam = static_cast<double *>(F->work);
     float *Lf = reinterpret_cast<float *>(static_cast<char *>(F->work) + ld);
     CU(apply_multiplier(G, true, gX, ldg, Lam, nrhs, nrhs, false, nullptr, s));
-    if (F->prec == GENP_FP64) {
+    if (f64_factors(F->prec)) {
         CU(lu_solve_inplace<double>(F, Lam, nrhs, nrhs, true, nullptr, s));
     } else {
         CU((convert_matrix<double, float>(Lam, nrhs, Lf, nrhs, n, nrhs, nullptr, s)));
@@ -482,7 +561,7 @@ genp_status genp_adjoint(const genp_factors *F, const genp_multiplier *G, const 
         CU((convert_matrix<float, double>(Lf, nrhs, Lam, nrhs, n, nrhs, nullptr, s)));
     }
     if (dB) CU((convert_matrix<double, double>(Lam, nrhs, dB, lddb, n, nrhs, nullptr, s)));
-    if (dA) CU(outer_update(Lam, nrhs, X, ldx, n, nrhs, dA, ldda, F->prec != GENP_FP64, s));
+    if (dA) CU(outer_update(Lam, nrhs, X, ldx, n, nrhs, dA, ldda, !f64_factors(F->prec), s));
     Fm->last_stream = s;
     return GENP_OK;
 }

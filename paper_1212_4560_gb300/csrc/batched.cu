@@ -13,8 +13,10 @@
 //   fails to halve, or after max_iter; else D = U^{-1} L^{-1} R, X += G D.
 // The factorization runs in FP32.  When its refinement stalls above tol (the
 // element growth of pivot-free elimination can exceed what FP32 carries),
-// the CTA escalates: it forms C = A G again in FP64, factors it in FP64 in
-// its own scratch and continues the refinement with those factors.
+// the CTA escalates: it forms C = A G again in double-float arithmetic (pairs
+// of floats, about 48 bits, on the FP32 pipe, which GB300 runs 64 times
+// faster than FP64), factors it in its own scratch and continues the FP64
+// refinement with those factors.
 // The adjoint kernel reuses the FP32 factors: Lambda = L^{-T} U^{-T} G^T gX,
 // dA = -Lambda X^T, dB = Lambda.  No CTA ever waits for another (the queue is
 // a single atomic counter), so a launch cannot deadlock.
@@ -607,8 +609,8 @@ int batched_blocks_per_sm() {
     return b < 1 ? 1 : b;
 }
 
-// Elements of the per-CTA FP64 escalation scratch (C: n^2 for n <= 1024;
-// Y: n x 16 follows it).
+// 8-byte elements of the per-CTA escalation scratch (C as double-float: n^2
+// for n <= 1024; Y: n x 16 follows it).
 int64_t batched_scratch_stride() { return 1024ll * 1024ll + 1024ll * MAXRHS; }
 
 cudaError_t launch_batched(const BatchDesc *d, int count, int *counter, const void *Apool, bool a_f64,

@@ -15,7 +15,7 @@ namespace genp {
 using ::fabs;
 using ::fma;
 
-struct dfloat {
+struct __align__(8) dfloat {
     float hi, lo;
     dfloat() = default;
     __device__ dfloat(int v) : hi((float)v), lo(0.f) {}

@@ -120,7 +120,132 @@ k_gemm(int64_t m, int64_t n, int64_t k, T alpha, const T *__restrict__ A, int64_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Skinny products (n <= 16 columns: the right-hand sides of the solves, the
+// residual b - A x, x = G y): matrix-vector kernels that read A once,
+// coalesced, and compute only the n real columns.
+//  op(A) = A:   one warp per RW rows, lanes stride over k, warp-shuffle sums.
+//  op(A) = A^T: one lane per output row (a column of A), the CTA's 8 warps
+//               split k and add their partial sums in shared memory.
+// Both sum in a fixed order (deterministic).
+// ---------------------------------------------------------------------------
+template <typename T, int NR, int RW>
+__global__ void __launch_bounds__(256) k_gemv_n(int64_t m, int nr, int64_t k, T alpha, const T *__restrict__ A,
+                                                 int64_t lda, const T *__restrict__ B, int64_t ldb, T beta,
+                                                 const T *Cin, int64_t ldci, T *D, int64_t ldd, const int *skip) {
+    if (skip && *skip) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t i0 = ((int64_t)blockIdx.x * 8 + warp) * RW; i0 < m; i0 += (int64_t)gridDim.x * 8 * RW) {
+        T acc[RW][NR];
+#pragma unroll
+        for (int r = 0; r < RW; ++r)
+#pragma unroll
+            for (int c = 0; c < NR; ++c) acc[r][c] = T(0);
+        const T *arow[RW];
+#pragma unroll
+        for (int r = 0; r < RW; ++r) arow[r] = A + (i0 + r < m ? i0 + r : i0) * lda;
+#pragma unroll 4
+        for (int64_t kk = lane; kk < k; kk += 32) {
+            T b[NR];
+#pragma unroll
+            for (int c = 0; c < NR; ++c) b[c] = c < nr ? __ldg(B + kk * ldb + c) : T(0);
+#pragma unroll
+            for (int r = 0; r < RW; ++r) {
+                const T a = __ldg(arow[r] + kk);
+#pragma unroll
+                for (int c = 0; c < NR; ++c) acc[r][c] = fma(a, b[c], acc[r][c]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RW; ++r)
+#pragma unroll
+            for (int c = 0; c < NR; ++c)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc[r][c] += __shfl_xor_sync(0xffffffffu, acc[r][c], o);
+        if (lane < NR) {
+#pragma unroll
+            for (int r = 0; r < RW; ++r) {
+                T v = T(0);
+#pragma unroll
+                for (int c = 0; c < NR; ++c) v = c == lane ? acc[r][c] : v;
+                if (i0 + r < m && lane < nr) {
+                    const T prev = beta == T(0) ? T(0) : beta * Cin[(i0 + r) * ldci + lane];
+                    D[(i0 + r) * ldd + lane] = alpha * v + prev;
+                }
+            }
+        }
+    }
+}
+
+template <typename T, int NR>
+__global__ void __launch_bounds__(256) k_gemv_t(int64_t m, int nr, int64_t k, T alpha, const T *__restrict__ A,
+                                                 int64_t lda, const T *__restrict__ B, int64_t ldb, T beta,
+                                                 const T *Cin, int64_t ldci, T *D, int64_t ldd, const int *skip) {
+    if (skip && *skip) return;
+    __shared__ T part[8][32][NR + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t j0 = (int64_t)blockIdx.x * 32; j0 < m; j0 += (int64_t)gridDim.x * 32) {
+        const int64_t j = j0 + lane;
+        const bool in = j < m;
+        T acc[NR];
+#pragma unroll
+        for (int c = 0; c < NR; ++c) acc[c] = T(0);
+#pragma unroll 4
+        for (int64_t kk = warp; kk < k; kk += 8) {
+            const T a = in ? __ldg(A + kk * lda + j) : T(0);
+#pragma unroll
+            for (int c = 0; c < NR; ++c)
+                if (c < nr) acc[c] = fma(a, __ldg(B + kk * ldb + c), acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < NR; ++c) part[warp][lane][c] = acc[c];
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < 32 * nr; idx += 256) {
+            const int l = idx / nr, c = idx % nr;
+            const int64_t jj = j0 + l;
+            if (jj < m) {
+                T v = T(0);
+#pragma unroll
+                for (int w = 0; w < 8; ++w) v += part[w][l][c];
+                const T prev = beta == T(0) ? T(0) : beta * Cin[jj * ldci + c];
+                D[jj * ldd + c] = alpha * v + prev;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 namespace {
+
+template <typename T, int NR>
+cudaError_t run_gemv(int64_t m, int64_t n, int64_t k, T alpha, const T *A, int64_t lda, bool transA, const T *B,
+                     int64_t ldb, T beta, const T *Cin, int64_t ldci, T *D, int64_t ldd, const int *skip,
+                     cudaStream_t s) {
+    note_launch();
+    if (transA) {
+        const int64_t blocks = cdiv(m, 32) < 65535 ? cdiv(m, 32) : 65535;
+        k_gemv_t<T, NR><<<(unsigned)blocks, 256, 0, s>>>(m, (int)n, k, alpha, A, lda, B, ldb, beta, Cin, ldci, D,
+                                                          ldd, skip);
+    } else {
+        constexpr int RW = NR <= 4 ? 4 : 2;
+        const int64_t blocks = cdiv(m, 8 * RW) < 65535 ? cdiv(m, 8 * RW) : 65535;
+        k_gemv_n<T, NR, RW><<<(unsigned)blocks, 256, 0, s>>>(m, (int)n, k, alpha, A, lda, B, ldb, beta, Cin, ldci,
+                                                              D, ldd, skip);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t gemv(int64_t m, int64_t n, int64_t k, T alpha, const T *A, int64_t lda, bool transA, const T *B,
+                 int64_t ldb, T beta, const T *Cin, int64_t ldci, T *D, int64_t ldd, const int *skip,
+                 cudaStream_t s) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    if (n == 1) return run_gemv<T, 1>(m, n, k, alpha, A, lda, transA, B, ldb, beta, Cin, ldci, D, ldd, skip, s);
+    if (n <= 2) return run_gemv<T, 2>(m, n, k, alpha, A, lda, transA, B, ldb, beta, Cin, ldci, D, ldd, skip, s);
+    if (n <= 4) return run_gemv<T, 4>(m, n, k, alpha, A, lda, transA, B, ldb, beta, Cin, ldci, D, ldd, skip, s);
+    if (n <= 8) return run_gemv<T, 8>(m, n, k, alpha, A, lda, transA, B, ldb, beta, Cin, ldci, D, ldd, skip, s);
+    return run_gemv<T, 16>(m, n, k, alpha, A, lda, transA, B, ldb, beta, Cin, ldci, D, ldd, skip, s);
+}
 
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool TA, int AS, int BS>
 cudaError_t run(int64_t m, int64_t n, int64_t k, T alpha, const T *A, int64_t lda, const T *B, int64_t ldb,
@@ -156,6 +281,9 @@ template <typename T>
 cudaError_t gemm(int64_t m, int64_t n, int64_t k, T alpha, const T *A, int64_t lda, bool transA, const T *B,
                  int64_t ldb, T beta, const T *Cin, int64_t ldci, T *D, int64_t ldd, const int *skip,
                  cudaStream_t s) {
+    // in-place updates (D == Cin) stay row-local in both skinny kernels: each
+    // output entry reads its own Cin entry just before writing it
+    if (n <= 16 && k > 0) return gemv<T>(m, n, k, alpha, A, lda, transA, B, ldb, beta, Cin, ldci, D, ldd, skip, s);
     if (transA)
         return dispatch<T, true, kDense, kDense>(m, n, k, alpha, A, lda, B, ldb, beta, Cin, ldci, D, ldd, skip,
                                                  nullptr, 1, s);

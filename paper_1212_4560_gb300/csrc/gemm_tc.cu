@@ -23,6 +23,9 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include "dfloat.cuh"
+#include "sliced.cuh"
+
 __device__ int g_tc_timeout;
 
 namespace genp {
@@ -293,7 +296,293 @@ bool make_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t K, int64_
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// ---------------------------------------------------------------------------
+// Sliced (FP64-class) product (layout in sliced.cuh).  Digit group g = t + u
+// accumulates in TMEM columns [64 (g-2), 64 (g-1)), so one MMA of A's digit t
+// against B's digits 1 .. ND+1-t laid side by side along N (N = 64 (ND+1-t),
+// cut at 256) lands every product in its group's columns.  One CTA per SM
+// computes a 128 x 64 tile: B's ND digit slices of a k-tile are staged once
+// (two stages), A's digit slices stream through a four-slot ring, and the
+// tensor pipe runs MMAs of N up to 256 instead of one narrow MMA per digit
+// pair.  The epilogue rebuilds each entry from its groups: the groups below
+// the last are exact integers (K <= 512), summed exactly in 64-bit integer
+// arithmetic, and the last group is added in double-float:
+//   D[i][j] += alpha 2^{e_i + f_j - 7 ND} (sum_{g<=ND} 2^{7(ND-g)} P_g + 2^-7 P_{ND+1})
+// ---------------------------------------------------------------------------
+constexpr int SBN = 64, A_SLOTS = 4;
+constexpr uint32_t SA_BYTES = BM * BK * 2;      // one A digit slice of a k-tile
+constexpr uint32_t SBD_BYTES = SBN * BK * 2;    // one B digit slice of a k-tile
+constexpr uint32_t S_TMEM = 512;
+struct SCtl {
+    unsigned long long afull[A_SLOTS];
+    unsigned long long aempty[A_SLOTS];
+    unsigned long long bfull[2];
+    unsigned long long bempty[2];
+    unsigned long long accum;
+    uint32_t tmem;
+    int abort;
+    int issued_a, issued_b;
+    float cs[SBN];            // 2^{f_j} of the tile's columns
+};
+constexpr int kDfLd = SBN + 1;
+
+__device__ __forceinline__ void mma_n(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__host__ __device__ constexpr uint32_t idesc_n(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int ND>
+struct SlicedCfg {
+    static constexpr uint32_t kBStage = ND * SBD_BYTES;
+    static constexpr size_t kSmem = 1024 + A_SLOTS * SA_BYTES + 2 * kBStage + sizeof(SCtl);
+    static_assert(64 * ND <= (int)S_TMEM, "group accumulators fit in TMEM");
+    static_assert(BM * kDfLd * 8 <= A_SLOTS * SA_BYTES + 2 * kBStage, "epilogue tile fits in the stage buffers");
+    // alone on its SM: a second CTA would wait in tcgen05.alloc for the 512 columns
+    static_assert(2 * kSmem > 228 * 1024, "one CTA per SM");
+    static_assert(kSmem <= 227 * 1024, "shared memory");
+};
+
+template <int ND>
+__global__ void __launch_bounds__(128, 1)
+k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m, int n, int kpad,
+            float alpha, const int *ea, const int *fb, dfloat *D, int64_t ldd) {
+    using Cfg = SlicedCfg<ND>;
+    extern __shared__ unsigned char smraw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = base;
+    unsigned char *sB = base + A_SLOTS * SA_BYTES;
+    SCtl *ctl = (SCtl *)(sB + 2 * Cfg::kBStage);
+    volatile int *abort = &ctl->abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * SBN;
+    const int nkt = kpad / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < A_SLOTS; ++s) {
+            mbar_init(&ctl->afull[s], 1);
+            mbar_init(&ctl->aempty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&ctl->bfull[s], 1);
+            mbar_init(&ctl->bempty[s], 1);
+        }
+        mbar_init(&ctl->accum, 1);
+        ctl->abort = 0;
+        ctl->issued_a = 0;
+        ctl->issued_b = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < SBN) {
+        const int col = n0 + threadIdx.x;
+        ctl->cs[threadIdx.x] = col < n ? ldexpf(alpha, fb[col]) : 0.0f;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&ctl->tmem)),
+                     "r"(S_TMEM)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = ctl->tmem;
+
+    if (warp == 0 && lane == 0) {
+        int ai = 0;
+        bool ok = true;
+        for (int kt = 0; kt < nkt && ok; ++kt) {
+            const int bs = kt & 1;
+            if (kt >= 2 && !mbar_wait(&ctl->bempty[bs], (uint32_t)((kt >> 1) & 1) ^ 1u, abort)) {
+                ok = false;
+                break;
+            }
+            mbar_expect_tx(&ctl->bfull[bs], Cfg::kBStage);
+            for (int u = 0; u < ND; ++u)
+                tma_2d(sB + bs * Cfg::kBStage + u * SBD_BYTES, &tmB, &ctl->bfull[bs], u * kpad + kt * BK, n0);
+            ctl->issued_b = kt + 1;
+            for (int t = 0; t < ND; ++t, ++ai) {
+                const int slot = ai % A_SLOTS;
+                if (ai >= A_SLOTS &&
+                    !mbar_wait(&ctl->aempty[slot], (uint32_t)((ai / A_SLOTS) & 1) ^ 1u, abort)) {
+                    ok = false;
+                    break;
+                }
+                mbar_expect_tx(&ctl->afull[slot], SA_BYTES);
+                tma_2d(sA + slot * SA_BYTES, &tmA, &ctl->afull[slot], t * kpad + kt * BK, m0);
+                ctl->issued_a = ai + 1;
+            }
+        }
+        if (!ok) *abort = 1;
+    } else if (warp == 1 && lane == 0) {
+        bool ok = true;
+        int ai = 0;
+        for (int kt = 0; kt < nkt && ok; ++kt) {
+            const int bs = kt & 1;
+            if (!mbar_wait(&ctl->bfull[bs], (uint32_t)((kt >> 1) & 1), abort)) {
+                ok = false;
+                break;
+            }
+            const uint32_t bbase = sa(sB + bs * Cfg::kBStage);
+#pragma unroll
+            for (int t = 0; t < ND; ++t) {
+                const int slot = ai % A_SLOTS;
+                if (!ok || !mbar_wait(&ctl->afull[slot], (uint32_t)((ai / A_SLOTS) & 1), abort)) {
+                    ok = false;
+                    continue;
+                }
+                ++ai;
+                fence_after();
+                const uint64_t ad = sdesc(sa(sA + slot * SA_BYTES));
+                const int nrows = SBN * (ND - t);          // B digits 1 .. ND - t
+#pragma unroll
+                for (int k = 0; k < BK / UMMA_K; ++k) {
+#pragma unroll
+                    for (int c0 = 0; c0 < nrows; c0 += 256) {
+                        const int nn = nrows - c0 < 256 ? nrows - c0 : 256;
+                        const uint64_t bd = sdesc(bbase + (uint32_t)c0 * 128u);
+                        mma_n(tmem + (uint32_t)(SBN * t + c0), ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2),
+                              idesc_n(nn), (kt == 0 && t == 0 && k == 0) ? 0u : 1u);
+                    }
+                }
+                commit(&ctl->aempty[slot]);
+            }
+            if (ok) commit(&ctl->bempty[bs]);
+        }
+        if (ok) commit(&ctl->accum);
+        else *abort = 1;
+    }
+    __syncwarp();
+
+    bool ready = mbar_wait(&ctl->accum, 0, abort);
+    if (!ready) *abort = 1;
+    fence_after();
+    ready = __syncthreads_and(ready) != 0;
+    dfloat *tile = reinterpret_cast<dfloat *>(base);   // BM x kDfLd, over the stage buffers
+    if (ready) {
+        const int r = warp * 32 + lane;
+        const int row = m0 + r;
+        const float rs = ldexpf(1.0f, (row < m ? ea[row] : 0) - 7 * ND);
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int h = 0; h < SBN / 32; ++h) {
+            long long S[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) S[j] = 0;
+            uint32_t q[32];
+            // exact groups, largest weight first: S = S 2^7 + P_g
+#pragma unroll 1
+            for (int g = 0; g < ND - 1; ++g) {
+                tmem_ld32(lane_addr + (uint32_t)(SBN * g + 32 * h), q);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) S[j] = S[j] * 128 + (long long)__float2int_rn(__uint_as_float(q[j]));
+            }
+            tmem_ld32(lane_addr + (uint32_t)(SBN * (ND - 1) + 32 * h), q);   // the last group
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float hi = __ll2float_rn(S[j]);
+                const float lo = __ll2float_rn(S[j] - __float2ll_rn(hi));
+                dfloat v;
+                v.hi = hi;
+                v.lo = lo;
+                v = v + dfloat(__uint_as_float(q[j]) * 0.0078125f);
+                const float cs = ctl->cs[32 * h + j];   // two exact power-of-two scalings
+                v.hi = (v.hi * rs) * cs;
+                v.lo = (v.lo * rs) * cs;
+                tile[r * kDfLd + 32 * h + j] = v;
+            }
+        }
+    }
+    __syncthreads();
+    if (ready) {
+        // D += tile, coalesced along rows; eight rows' loads in flight per batch
+        for (int r0 = warp * 32; r0 < warp * 32 + 32; r0 += 8) {
+            dfloat d[8][SBN / 32];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int row = m0 + r0 + q;
+#pragma unroll
+                for (int e = 0; e < SBN / 32; ++e) {
+                    const int col = n0 + lane + 32 * e;
+                    d[q][e] = (row < m && col < n) ? D[(int64_t)row * ldd + col] : dfloat(0.0f);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int row = m0 + r0 + q;
+#pragma unroll
+                for (int e = 0; e < SBN / 32; ++e) {
+                    const int cc = lane + 32 * e, col = n0 + cc;
+                    if (row < m && col < n) D[(int64_t)row * ldd + col] = d[q][e] + tile[(r0 + q) * kDfLd + cc];
+                }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (ctl->abort) {
+        // drain the copies still in flight before the CTA's shared memory goes away
+        if (threadIdx.x == 0) {
+            atomicExch(&g_tc_timeout, 1);
+            int dummy = 0;
+            const int ia = ctl->issued_a, ib = ctl->issued_b;
+            for (int i = (ia > A_SLOTS ? ia - A_SLOTS : 0); i < ia; ++i)
+                mbar_wait(&ctl->afull[i % A_SLOTS], (uint32_t)((i / A_SLOTS) & 1), (volatile int *)&dummy);
+            for (int i = (ib > 2 ? ib - 2 : 0); i < ib; ++i)
+                mbar_wait(&ctl->bfull[i & 1], (uint32_t)((i >> 1) & 1), (volatile int *)&dummy);
+        }
+        if (threadIdx.x == 32) {
+            int dummy = 0;
+            mbar_wait(&ctl->accum, 0, (volatile int *)&dummy);
+        }
+        __syncthreads();
+    }
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S_TMEM) : "memory");
+}
+
+template <int ND>
+cudaError_t launch_sliced(const CUtensorMap &ma, const CUtensorMap &mb, int64_t m, int64_t n, int64_t kpad,
+                          float alpha, const int *ea, const int *fb, dfloat *D, int64_t ldd, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_tc_sliced<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SlicedCfg<ND>::kSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((unsigned)cdiv(n, SBN), (unsigned)cdiv(m, BM));
+    if (grid.y > 65535u) return cudaErrorInvalidValue;
+    note_launch();
+    k_tc_sliced<ND><<<grid, 128, SlicedCfg<ND>::kSmem, s>>>(ma, mb, (int)m, (int)n, (int)kpad, alpha, ea, fb, D, ldd);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t tc_gemm_sliced(int nd, int64_t m, int64_t n, int64_t kpad, float alpha, const __nv_bfloat16 *Aq,
+                           int64_t lda, const __nv_bfloat16 *Bq, int64_t ldb, const int *ea, const int *fb, dfloat *D,
+                           int64_t ldd, cudaStream_t s) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    if (!sliced::supported(nd)) return cudaErrorInvalidValue;
+    if (kpad <= 0 || kpad % BK || kpad > kSlicedChunk || m > INT32_MAX || n > INT32_MAX) return cudaErrorInvalidValue;
+    if ((lda % 8) || (ldb % 8) || ((uintptr_t)Aq % 16) || ((uintptr_t)Bq % 16)) return cudaErrorInvalidValue;
+    const int64_t kq = (int64_t)nd * kpad;
+    if (lda < kq || ldb < kq) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, Aq, m, kq, lda, BM) || !make_map(&mb, Bq, n, kq, ldb, SBN)) return cudaErrorInvalidValue;
+    switch (nd) {
+        case 5: return launch_sliced<5>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
+        case 6: return launch_sliced<6>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
+        default: return launch_sliced<7>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
+    }
+}
 
 cudaError_t tc_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha, const __nv_bfloat16 *A, int64_t lda,
                          const __nv_bfloat16 *Bt, int64_t ldb, float beta, const float *Cin, int64_t ldci, float *D,

@@ -83,10 +83,21 @@ struct genp_factors {
     __nv_bfloat16 *tcA = nullptr;      // BF16 split L21 panel, n x tc_ldq (BF16 / BF16X3)
     __nv_bfloat16 *tcB = nullptr;      // BF16 split U12^T panel, n x tc_ldq
     int64_t tc_ldq = 0;
+    void *W = nullptr;                 // double-float trailing matrix, n x ldw (GENP_BF16_SLICED)
+    int64_t ldw = 0;
+    int *exps = nullptr;               // 2n slicing exponents (GENP_BF16_SLICED)
+    int nd = 0;                        // digits per operand (GENP_BF16_SLICED)
+    int *trsv_sync = nullptr;          // tickets and block counters of the triangular solves
+    void *dinv = nullptr;              // inverses of the 64 x 64 diagonal blocks of L and U (factor type)
     cudaStream_t last_stream = nullptr;
 };
 
 namespace genp {
+
+struct dfloat;   // dfloat.cuh
+
+// Factors stored in FP64 (solves and refinement run in FP64).
+inline bool f64_factors(genp_prec p) { return p == GENP_FP64 || p == GENP_BF16_SLICED; }
 
 // One system of a batched solve (device array, built by genp_batched_plan).
 struct BatchDesc {
@@ -174,6 +185,41 @@ cudaError_t tc_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha, const __n
                          int64_t ldd, const int *skip, cudaStream_t s);
 // Reads the device-side timeout flag of the tensor-core kernels (synchronizes).
 int tc_timeout_flag(bool reset);
+// D += alpha * A B on the tensor cores with FP64-class accuracy, from the
+// nd-digit slices of sliced.cu: Aq (m x nd kpad) and Bq (n x nd kpad, B
+// transposed) with their row / column exponents ea, fb.
+// D is double-float.  alpha must be a power of two (it is applied to both
+// halves of each sum).  kpad <= kSlicedChunk.
+cudaError_t tc_gemm_sliced(int nd, int64_t m, int64_t n, int64_t kpad, float alpha, const __nv_bfloat16 *Aq,
+                           int64_t lda, const __nv_bfloat16 *Bq, int64_t ldb, const int *ea, const int *fb, dfloat *D,
+                           int64_t ldd, cudaStream_t s);
+
+// sliced.cu: exact 7-bit digit slicing of FP64 operands (Ozaki scheme).
+int64_t sliced_kpad(int64_t K);   // K rounded up to the k-tile
+int sliced_slices(int nd);        // digit slices per operand (operand width slices * kpad)
+int sliced_digits();              // digits of the GENP_BF16_SLICED path
+int set_sliced_digits(int nd);    // returns the previous value, -1 if nd is unsupported
+// rows of src (m x K): dst[i][p*kpad + k] = slice p of src[i][k]; exps[i] = row exponent
+cudaError_t slice_rows(int nd, const double *src, int64_t lds, int64_t m, int64_t K, __nv_bfloat16 *dst, int64_t ldq,
+                       int *exps, cudaStream_t s);
+// columns of src (K x n), written transposed: dst[j][p*kpad + k]; exps[j] = column exponent
+cudaError_t slice_cols_T(int nd, const double *src, int64_t lds, int64_t K, int64_t n, __nv_bfloat16 *dst,
+                         int64_t ldq, int *exps, cudaStream_t s);
+// double <-> double-float copies of an m x n block
+cudaError_t df_from_f64(const double *src, int64_t lds, dfloat *dst, int64_t ldd, int64_t m, int64_t n,
+                        cudaStream_t s);
+cudaError_t df_to_f64(const dfloat *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int64_t n,
+                      cudaStream_t s);
+// D = alpha * W + beta * D (W double-float, D double; beta == 0 ignores D)
+cudaError_t df_axpby(double alpha, const dfloat *W, int64_t ldw, double beta, double *D, int64_t ldd, int64_t m,
+                     int64_t n, cudaStream_t s);
+// D (double-float, m x n) = A B, A m x K and B K x n FP64, K cut in chunks of
+// at most kSlicedChunk; Aq, Bq hold (m or n) x kSlicedLdq BF16, exps m + n ints.
+cudaError_t sliced_matmul(int nd, int64_t m, int64_t n, int64_t K, const double *A, int64_t lda, const double *B,
+                          int64_t ldb, dfloat *D, int64_t ldd, __nv_bfloat16 *Aq, __nv_bfloat16 *Bq, int *exps,
+                          cudaStream_t s);
+constexpr int64_t kSlicedChunk = 512;   // keeps the digit groups of weight >= 2^-49 exact in FP32
+constexpr int64_t kSlicedLdq = 7 * kSlicedChunk;    // operand width for up to 7 digits
 
 // mixed.cu: BF16 split operands.  terms = 1 (GENP_BF16) or 6 (GENP_BF16X3).
 int split_terms(genp_prec p);
@@ -219,8 +265,21 @@ cudaError_t refine_init(genp_factors *F, const double *A, int64_t lda, int64_t n
 cudaError_t refine_check(genp_factors *F, const double *R, int64_t ldr, const double *X, int64_t ldx,
                          const double *B, int64_t ldb, int64_t n, int64_t nrhs, int it, double tol,
                          int max_iter, int last_chunk, cudaStream_t s);
+// Reads the device-side timeout flag of the triangular solves (synchronizes).
+int solve_timeout_flag(bool reset);
+// ints of synchronization state a triangular solve of order n needs
+int64_t trsv_sync_ints(int64_t n);
+// elements of F->dinv, and its computation (after every factorization)
+int64_t diag_inverse_elems(int64_t n);
+cudaError_t invert_diag_blocks(genp_factors *F, cudaStream_t s);
 cudaError_t outer_update(const double *Lam, int64_t ldl, const double *X, int64_t ldx, int64_t n,
                          int64_t nrhs, void *dA, int64_t ldda, bool dA_f32, cudaStream_t s);
+
+// gmres.cu: GMRES-IR (genp_refine method 1); work holds gmres_work_bytes(n, nrhs)
+size_t gmres_work_bytes(int64_t n, int64_t nrhs);
+cudaError_t refine_gmres(genp_factors *F, const genp_multiplier *G, const double *A, int64_t lda, const double *B,
+                         int64_t ldb, int64_t nrhs, double *X, int64_t ldx, double tol, int max_iter, void *work,
+                         cudaStream_t s);
 
 // api.cu helpers
 cudaError_t apply_multiplier(const genp_multiplier *G, bool trans, const double *Y, int64_t ldy,

@@ -7,6 +7,7 @@
 // No row or column is ever exchanged.  A zero or non-finite pivot is
 // recorded in the status word (first step wins) and elimination goes on.
 #include "genp_internal.cuh"
+#include "dfloat.cuh"
 
 #include <math.h>
 
@@ -238,6 +239,57 @@ cudaError_t factor_tc(genp_factors *F, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// GENP_BF16_SLICED: the FP64 steps of factor_typed (diagonal block, block
+// row and column, all in C) with the Schur update on the tensor cores by
+// exact digit slicing.  The trailing matrix lives in W as double-float
+// pairs; each step first copies its block column and block row from W into
+// C, so C ends up holding the FP64 factors.
+cudaError_t factor_sliced(genp_factors *F, cudaStream_t s) {
+    double *C = static_cast<double *>(F->C);
+    dfloat *W = static_cast<dfloat *>(F->W);
+    const int64_t n = F->n, ldc = F->ldc, ldw = F->ldw, ldq = F->tc_ldq;
+    const int nb = (int)F->nb;
+    const size_t sm_panel = (size_t)nb * (nb + 1) * sizeof(double);
+    const size_t xrow = (size_t)nb * (kTrsmW + 1), xcol = (size_t)kTrsmW * (nb + 1);
+    const size_t sm_trsm = sm_panel + (xrow > xcol ? xrow : xcol) * sizeof(double);
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(k_panel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_trsm<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_done = true;
+    }
+    note_launch();
+    k_maxabs<double><<<152 * 4, 256, 0, s>>>(C, n, ldc, &F->st->max_abs_c);
+    if (n > nb) {
+        cudaError_t e = df_from_f64(C + nb * ldc + nb, ldc, W + nb * ldw + nb, ldw, n - nb, n - nb, s);
+        if (e != cudaSuccess) return e;
+    }
+    for (int64_t k0 = 0; k0 < n; k0 += nb) {
+        const int kb = (int)(n - k0 < nb ? n - k0 : nb);
+        const int64_t rem = n - k0 - kb;
+        if (k0 > 0) {   // this step's block column and block row, updated by the earlier steps
+            cudaError_t e = df_to_f64(W + k0 * ldw + k0, ldw, C + k0 * ldc + k0, ldc, n - k0, kb, s);
+            if (e == cudaSuccess) e = df_to_f64(W + k0 * ldw + k0 + kb, ldw, C + k0 * ldc + k0 + kb, ldc, kb, rem, s);
+            if (e != cudaSuccess) return e;
+        }
+        note_launch();
+        k_panel<double, double><<<1, kThreads, sm_panel, s>>>(C, ldc, k0, kb, F->st);
+        if (rem <= 0) break;
+        dim3 g((unsigned)cdiv(rem, kTrsmW), 2);
+        note_launch();
+        k_trsm<double, double><<<g, kThreads, sm_trsm, s>>>(C, ldc, n, k0, kb, F->st);
+        const double *L21 = C + (k0 + kb) * ldc + k0;
+        const double *U12 = C + k0 * ldc + k0 + kb;
+        cudaError_t e = slice_rows(F->nd, L21, ldc, rem, kb, F->tcA, ldq, F->exps, s);
+        if (e == cudaSuccess) e = slice_cols_T(F->nd, U12, ldc, kb, rem, F->tcB, ldq, F->exps + n, s);
+        if (e == cudaSuccess)
+            e = tc_gemm_sliced(F->nd, rem, rem, sliced_kpad(kb), -1.0f, F->tcA, ldq, F->tcB, ldq, F->exps, F->exps + n,
+                               W + (k0 + kb) * ldw + k0 + kb, ldw, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t status_reset(genp_factors *F, cudaStream_t s) {
@@ -250,12 +302,16 @@ cudaError_t factor_run(genp_factors *F, cudaStream_t s) {
     cudaError_t e = status_reset(F, s);
     if (e != cudaSuccess) return e;
     switch (F->prec) {
-        case GENP_FP64: return factor_typed<double, double>(F, s);
-        case GENP_FP32: return factor_typed<float, float>(F, s);
+        case GENP_FP64: e = factor_typed<double, double>(F, s); break;
+        case GENP_FP32: e = factor_typed<float, float>(F, s); break;
         case GENP_BF16:
-        case GENP_BF16X3: return factor_tc(F, s);
+        case GENP_BF16X3: e = factor_tc(F, s); break;
+        case GENP_BF16_SLICED: e = factor_sliced(F, s); break;
         default: return cudaErrorNotSupported;
     }
+    // the solves apply the diagonal blocks of L and U through their inverses
+    if (e == cudaSuccess) e = invert_diag_blocks(F, s);
+    return e;
 }
 
 }  // namespace genp

@@ -1,0 +1,218 @@
+// sliced.cu -- FP64-class products on the BF16 tensor cores by exact
+// fixed-point slicing (the Ozaki scheme: Ozaki, Ogita, Oishi & Rump,
+// "Error-free transformations of matrix multiplication", Numer. Algorithms
+// 2012).  The digit layout and the accumulator groups are in sliced.cuh; this
+// file cuts FP64 operands into their BF16 digit slices, and holds the
+// double-float helpers of the GENP_BF16_SLICED factorization.
+//
+// With ND digits the kept pairs (t + u <= ND + 1) and the truncation leave at
+// most about 2^-(7 ND - 1) of 2^{e_i + f_j} per term of the sum over k, and
+// every digit group but the last is summed exactly (K <= 512).
+#include "genp_internal.cuh"
+#include "dfloat.cuh"
+#include "sliced.cuh"
+
+#include <math.h>
+
+namespace genp {
+
+namespace {
+
+int g_default_digits = 7;
+
+// exponent e with max|x| < 2^e (0 for an all-zero row)
+__device__ __forceinline__ int scale_exp(double amax) {
+    if (!(amax > 0.0)) return 0;
+    int e;
+    frexp(amax, &e);   // amax = m 2^e, m in [0.5, 1)
+    return e;
+}
+
+// digit t (1-based) of q in (-1, 1): d_t = rint(r_{t-1} 2^7), r_t = r_{t-1} 2^7 - d_t (all exact in FP64)
+template <int ND>
+__device__ __forceinline__ void digits(double q, float (&d)[ND]) {
+    double r = q;
+#pragma unroll
+    for (int t = 0; t < ND; ++t) {
+        const double s = r * 128.0;
+        const double dt = rint(s);
+        d[t] = (float)dt;
+        r = s - dt;
+    }
+}
+
+// Writes the ND digit slices of one operand entry (a small integer each: exact in BF16).
+template <int ND>
+__device__ __forceinline__ void put(__nv_bfloat16 *row, int64_t kpad, int64_t k, const float (&d)[ND]) {
+#pragma unroll
+    for (int t = 0; t < ND; ++t) row[t * kpad + k] = __float2bfloat16_rn(d[t]);
+}
+
+// A operand: rows of src (m x K, FP64, ld lds).  One warp per row.
+template <int ND>
+__global__ void k_slice_rows(const double *src, int64_t lds, int64_t m, int64_t K, int64_t kpad,
+                             __nv_bfloat16 *dst, int64_t ldq, int *exps) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < m; i += nw) {
+        const double *a = src + i * lds;
+        double mx = 0.0;
+        for (int64_t k = lane; k < K; k += 32) mx = fmax(mx, fabs(a[k]));
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        const int e = scale_exp(mx);
+        if (lane == 0) exps[i] = e;
+        __nv_bfloat16 *row = dst + i * ldq;
+        for (int64_t k = lane; k < kpad; k += 32) {
+            float d[ND] = {};
+            if (k < K) digits<ND>(ldexp(a[k], -e), d);
+            put<ND>(row, kpad, k, d);
+        }
+    }
+}
+
+// B operand: columns of src (K x n, FP64, ld lds), written transposed
+// (row j of dst holds column j).  Pass 1: column exponents.
+__global__ void k_col_exps(const double *src, int64_t lds, int64_t K, int64_t n, int *exps) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        double mx = 0.0;
+        for (int64_t k = 0; k < K; ++k) mx = fmax(mx, fabs(src[k * lds + j]));
+        exps[j] = scale_exp(mx);
+    }
+}
+
+// Pass 2: 32 x 32 tiles through shared memory so both sides stay coalesced.
+template <int ND>
+__global__ void k_slice_cols_T(const double *src, int64_t lds, int64_t K, int64_t n, int64_t kpad,
+                               __nv_bfloat16 *dst, int64_t ldq, const int *exps) {
+    __shared__ double tile[32][33];
+    const int64_t k0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t k = k0 + r, j = j0 + tx;
+        tile[r][tx] = (k < K && j < n) ? src[k * lds + j] : 0.0;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t j = j0 + r, k = k0 + tx;
+        if (j < n && k < kpad) {
+            float d[ND] = {};
+            if (k < K) digits<ND>(ldexp(tile[tx][r], -exps[j]), d);
+            put<ND>(dst + j * ldq, kpad, k, d);
+        }
+    }
+}
+
+// Double-float <-> FP64 copies of a block (grid-stride over rows, coalesced columns).
+__global__ void k_df_from_f64(const double *src, int64_t lds, dfloat *dst, int64_t ldd, int64_t m, int64_t n) {
+    for (int64_t i = blockIdx.y; i < m; i += gridDim.y)
+        for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+            dst[i * ldd + j] = dfloat(src[i * lds + j]);
+}
+__global__ void k_df_to_f64(const dfloat *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int64_t n) {
+    for (int64_t i = blockIdx.y; i < m; i += gridDim.y)
+        for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+            dst[i * ldd + j] = (double)src[i * lds + j];
+}
+
+__global__ void k_df_axpby(double alpha, const dfloat *W, int64_t ldw, double beta, double *D, int64_t ldd,
+                           int64_t m, int64_t n) {
+    for (int64_t i = blockIdx.y; i < m; i += gridDim.y)
+        for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+            const dfloat w = W[i * ldw + j];
+            const double v = alpha * (double)w.hi + alpha * (double)w.lo;
+            D[i * ldd + j] = beta == 0.0 ? v : v + beta * D[i * ldd + j];
+        }
+}
+
+dim3 block_grid(int64_t m, int64_t n) {
+    const int64_t gx = cdiv(n, 256) < 8 ? cdiv(n, 256) : 8;
+    return dim3((unsigned)gx, (unsigned)(m < 65535 ? m : 65535));
+}
+
+}  // namespace
+
+int64_t sliced_kpad(int64_t K) { return (K + 63) / 64 * 64; }
+int sliced_slices(int nd) { return nd; }
+int sliced_digits() { return g_default_digits; }
+int set_sliced_digits(int nd) {
+    if (!sliced::supported(nd)) return -1;
+    const int old = g_default_digits;
+    g_default_digits = nd;
+    return old;
+}
+
+cudaError_t slice_rows(int nd, const double *src, int64_t lds, int64_t m, int64_t K, __nv_bfloat16 *dst, int64_t ldq,
+                       int *exps, cudaStream_t s) {
+    if (m <= 0) return cudaSuccess;
+    if (!sliced::supported(nd) || ldq < nd * sliced_kpad(K)) return cudaErrorInvalidValue;
+    int blocks = (int)((m + 7) / 8);
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    const int64_t kpad = sliced_kpad(K);
+    note_launch();
+    switch (nd) {
+        case 5: k_slice_rows<5><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps); break;
+        case 6: k_slice_rows<6><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps); break;
+        default: k_slice_rows<7><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t slice_cols_T(int nd, const double *src, int64_t lds, int64_t K, int64_t n, __nv_bfloat16 *dst,
+                         int64_t ldq, int *exps, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int64_t kpad = sliced_kpad(K);
+    if (!sliced::supported(nd) || ldq < nd * kpad) return cudaErrorInvalidValue;
+    note_launch();
+    k_col_exps<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(src, lds, K, n, exps);
+    dim3 g((unsigned)cdiv(n, 32), (unsigned)cdiv(kpad, 32));
+    if (g.y > 65535u) return cudaErrorInvalidValue;
+    note_launch();
+    switch (nd) {
+        case 5: k_slice_cols_T<5><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps); break;
+        case 6: k_slice_cols_T<6><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps); break;
+        default: k_slice_cols_T<7><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t df_from_f64(const double *src, int64_t lds, dfloat *dst, int64_t ldd, int64_t m, int64_t n,
+                        cudaStream_t s) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    note_launch();
+    k_df_from_f64<<<block_grid(m, n), 256, 0, s>>>(src, lds, dst, ldd, m, n);
+    return cudaGetLastError();
+}
+
+cudaError_t df_to_f64(const dfloat *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int64_t n,
+                      cudaStream_t s) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    note_launch();
+    k_df_to_f64<<<block_grid(m, n), 256, 0, s>>>(src, lds, dst, ldd, m, n);
+    return cudaGetLastError();
+}
+
+cudaError_t df_axpby(double alpha, const dfloat *W, int64_t ldw, double beta, double *D, int64_t ldd, int64_t m,
+                     int64_t n, cudaStream_t s) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    note_launch();
+    k_df_axpby<<<block_grid(m, n), 256, 0, s>>>(alpha, W, ldw, beta, D, ldd, m, n);
+    return cudaGetLastError();
+}
+
+cudaError_t sliced_matmul(int nd, int64_t m, int64_t n, int64_t K, const double *A, int64_t lda, const double *B,
+                          int64_t ldb, dfloat *D, int64_t ldd, __nv_bfloat16 *Aq, __nv_bfloat16 *Bq, int *exps,
+                          cudaStream_t s) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemset2DAsync(D, (size_t)ldd * sizeof(dfloat), 0, (size_t)n * sizeof(dfloat), (size_t)m, s);
+    for (int64_t k0 = 0; k0 < K && e == cudaSuccess; k0 += kSlicedChunk) {
+        const int64_t kc = K - k0 < kSlicedChunk ? K - k0 : kSlicedChunk;
+        const int64_t kpad = sliced_kpad(kc), ldq = nd * kpad;
+        e = slice_rows(nd, A + k0, lda, m, kc, Aq, ldq, exps, s);
+        if (e == cudaSuccess) e = slice_cols_T(nd, B + k0 * ldb, ldb, kc, n, Bq, ldq, exps + m, s);
+        if (e == cudaSuccess) e = tc_gemm_sliced(nd, m, n, kpad, 1.0f, Aq, ldq, Bq, ldq, exps, exps + m, D, ldd, s);
+    }
+    return e;
+}
+
+}  // namespace genp

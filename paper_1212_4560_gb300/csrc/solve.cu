@@ -1,10 +1,13 @@
 // solve.cu -- triangular solves with the GENP factors, refinement control
 // and the adjoint's outer product.
 //
-// Solves are blocked by kBs rows: a one-CTA kernel solves the kBs x kBs
-// diagonal triangle against all right-hand sides in shared memory, then a
-// tiled GEMM subtracts that block's contribution from the remaining rows.
-// The transposed pair (U^T then L^T) serves the adjoint (A^{-T} = L^{-T} U^{-T} G^T).
+// Each triangular solve is one persistent launch (k_trsv below), 16
+// right-hand sides at a time.  The transposed pair (U^T then L^T) serves the
+// adjoint (A^{-T} = L^{-T} U^{-T} G^T).  The 64 x 64 diagonal blocks of L and
+// U are inverted once after every factorization (k_trtri_diag) and applied
+// as small matrix-vector products, which keeps the solve's critical path (one
+// diagonal block after another) short; GPU triangular-solve libraries do the
+// same (e.g. MAGMA's trtri_diag + gemv).
 //
 // Refinement (Sec. 7.1) is steered on the device: every iteration's kernels
 // read a `done` flag that the stopping test sets, so a whole refinement is
@@ -16,52 +19,7 @@
 namespace genp {
 namespace {
 
-constexpr int kBs = 64;
-constexpr int kThreads = 256;
-constexpr int kRhsTile = 32;
-
-// mode 0: L (unit lower, forward)    mode 1: U (upper, backward)
-// mode 2: U^T (lower, forward)       mode 3: L^T (unit upper, backward)
-template <typename TS, typename T>
-__global__ void __launch_bounds__(kThreads) k_diag_solve(const TS *C, int64_t ldc, int64_t b0, int bs, T *Y,
-                                                         int64_t ldy, int nr, int mode, const int *skip) {
-    if (skip && *skip) return;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T *t = reinterpret_cast<T *>(smraw);          // bs x (bs+1): t[i][j] = op(C)[i][j]
-    const int ld = bs + 1, tid = threadIdx.x;
-    T *y = t + bs * ld;                           // bs x nr
-    for (int idx = tid; idx < bs * bs; idx += kThreads) {
-        const int i = idx / bs, j = idx % bs;
-        const T v = (T)C[(b0 + i) * ldc + b0 + j];
-        if (mode <= 1) t[i * ld + j] = v;
-        else t[j * ld + i] = v;                   // transposed triangle
-    }
-    for (int idx = tid; idx < bs * nr; idx += kThreads) {
-        const int i = idx / nr, c = idx % nr;
-        y[i * nr + c] = Y[(b0 + i) * ldy + c];
-    }
-    __syncthreads();
-    const bool forward = (mode == 0 || mode == 2);
-    const bool unit = (mode == 0 || mode == 3);
-    for (int s = 0; s < bs; ++s) {
-        const int k = forward ? s : bs - 1 - s;
-        if (!unit) {
-            if (tid < nr) y[k * nr + tid] = y[k * nr + tid] / t[k * ld + k];
-            __syncthreads();
-        }
-        const int lo = forward ? k + 1 : 0, hi = forward ? bs : k;
-        const int cnt = (hi - lo) * nr;
-        for (int idx = tid; idx < cnt; idx += kThreads) {
-            const int i = lo + idx / nr, c = idx % nr;
-            y[i * nr + c] = y[i * nr + c] - t[i * ld + k] * y[k * nr + c];
-        }
-        __syncthreads();
-    }
-    for (int idx = tid; idx < bs * nr; idx += kThreads) {
-        const int i = idx / nr, c = idx % nr;
-        Y[(b0 + i) * ldy + c] = y[i * nr + c];
-    }
-}
+constexpr int kTrsvMaxRhs = 16;   // right-hand sides per triangular-solve launch
 
 template <typename TS, typename TD>
 __global__ void k_convert(const TS *src, int64_t lds, TD *dst, int64_t ldd, int64_t m, int64_t n, const int *skip) {
@@ -194,53 +152,312 @@ __global__ void k_outer(const double *Lam, int64_t ldl, const double *X, int64_t
     }
 }
 
+// ---------------------------------------------------------------------------
+// Triangular solves op(T) Y = Y in one persistent launch (column-oriented,
+// streaming).  T is cut into 64 x 64 tiles; step p solves the diagonal tile
+// of block j(p) (j = p forward, nblk-1-p backward) with its precomputed
+// inverse and then subtracts
+// op(T)[i][j] y_j from every block i still to come.  Those updates are split
+// into work items of kSeg tiles so that one column's work spreads over
+// several SMs.  Items are taken from an atomic ticket in (step, segment)
+// order; an item only waits for items with smaller tickets (the
+// contributions to its diagonal block, or that block's solution), which are
+// running or done, so the launch cannot deadlock.  Updates go into Y with
+// FP64 (or FP32) atomics; a per-block counter says when all of them have
+// landed.  Every wait is bounded: on timeout the kernel sets a device flag
+// (read by genp_device_check) and goes on.
+// ---------------------------------------------------------------------------
+constexpr int TB = 64;          // tile
+constexpr int kSeg = 16;        // tiles per work item
+constexpr int kTrsvThreads = 256;
+constexpr long long kSpinTicks = 4000000000LL;   // ~2 s at 2 GHz
+
+__device__ int g_solve_timeout;
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ bool wait_geq(const int *p, int target) {
+    const long long t0 = clock64();
+    while (ld_acquire(p) < target) {
+        if (clock64() - t0 > kSpinTicks) return false;
+        __nanosleep(100);
+    }
+    return true;
+}
+__device__ __forceinline__ int nseg(int p, int nblk) {
+    const int c = nblk - 1 - p;
+    return c <= 0 ? 1 : (c + kSeg - 1) / kSeg;
+}
+__device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ float ldcg(const float *p) { return __ldcg(p); }
+
+template <typename T, int NR>
+struct TrsvSmem {
+    T S[TB][TB + 1];    // current tile of op(T), or op(T_jj)^{-1}
+    T D[TB][TB + 1];    // op(T_jj), its triangle only
+    T y[TB][NR];        // y_j
+    T acc[TB][NR];      // right-hand side of the diagonal block, then its residual
+    int item[2];
+};
+
+// part[c] = sum over this thread's quarter of k of M[r][k] V[k][c], summed over
+// the 4 threads of row r (thread = 4 r + quarter)
+template <typename T, int NR>
+__device__ __forceinline__ void tile_gemv(const T (*M)[TB + 1], const T (*V)[NR], int r, int qq, T (&part)[NR]) {
+#pragma unroll
+    for (int c = 0; c < NR; ++c) part[c] = T(0);
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+        const int k = qq * 16 + kk;
+        const T a = M[r][k];
+#pragma unroll
+        for (int c = 0; c < NR; ++c) part[c] = fma(a, V[k][c], part[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+        part[c] += __shfl_xor_sync(0xffffffffu, part[c], 1);
+        part[c] += __shfl_xor_sync(0xffffffffu, part[c], 2);
+    }
+}
+
+// mode 0: L (unit lower, forward)    mode 1: U (upper, backward)
+// mode 2: U^T (lower, forward)       mode 3: L^T (unit upper, backward)
+// Tile (i, j) of op(T): element (r, k) = op(T)[i TB + r][j TB + k].
+template <typename TS, typename T>
+__device__ __forceinline__ T tile_elem(const TS *C, int64_t ldc, int n, int mode, int i, int j, int r, int k) {
+    const int64_t row = (int64_t)i * TB + r, col = (int64_t)j * TB + k;
+    if (row >= n || col >= n) return T(0);
+    return (mode <= 1) ? (T)__ldg(C + row * ldc + col) : (T)__ldg(C + col * ldc + row);
+}
+
+template <typename TS, typename T, int NR>
+__global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc, int n, const TS *Dinv, T *Y,
+                                                        int64_t ldy, int nr, int mode, const int *skip, int *sync) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    TrsvSmem<T, NR> &sm = *reinterpret_cast<TrsvSmem<T, NR> *>(smraw);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nblk = (n + TB - 1) / TB;
+    const bool forward = (mode == 0 || mode == 2);
+    int *ticket = sync, *cnt = sync + 2, *ready = sync + 2 + nblk;
+    int p = 0, t_base = 0;                 // first ticket of step p
+    // per-thread share of a tile load: 16 elements; non-transposed modes walk
+    // rows (k fastest), transposed modes walk columns (r fastest)
+    auto load_tile = [&](int i, int j, T (&v)[16]) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int idx = tid + e * kTrsvThreads;
+            const int a = idx >> 6, b = idx & 63;
+            v[e] = (mode <= 1) ? tile_elem<TS, T>(C, ldc, n, mode, i, j, a, b)
+                               : tile_elem<TS, T>(C, ldc, n, mode, i, j, b, a);
+        }
+    };
+    auto store_tile = [&](const T (&v)[16]) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int idx = tid + e * kTrsvThreads;
+            const int a = idx >> 6, b = idx & 63;
+            if (mode <= 1) sm.S[a][b] = v[e];
+            else sm.S[b][a] = v[e];
+        }
+    };
+    // op(T_jj)^{-1} from the inverted diagonal blocks (Dinv: [L, U][block][64][64])
+    auto load_inv = [&](int j, T (&v)[16]) {
+        const TS *X = Dinv + ((int64_t)((mode == 0 || mode == 3) ? 0 : 1) * nblk + j) * TB * TB;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int idx = tid + e * kTrsvThreads;
+            v[e] = (T)__ldg(X + idx);   // stored as S[a][b] (non-transposed) or S[b][a] by store_tile
+        }
+    };
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) sm.item[0] = atomicAdd(ticket, 1);
+        __syncthreads();
+        const int t = sm.item[0];
+        while (p < nblk && t >= t_base + nseg(p, nblk)) {
+            t_base += nseg(p, nblk);
+            ++p;
+        }
+        if (p >= nblk) break;
+        const int s = t - t_base;
+        const int j = forward ? p : nblk - 1 - p;
+        const int bj = min(TB, n - j * TB);
+        T v[16];
+        if (s == 0) {
+            // the diagonal block: y_j = op(T_jj)^{-1} b_j with b_j = Y_j minus the
+            // contributions of the p earlier steps, then one step of refinement
+            // y_j += op(T_jj)^{-1} (b_j - op(T_jj) y_j), which brings the explicit
+            // inverse's error (kappa(T_jj) u) back to the level of substitution
+            load_tile(j, j, v);
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int idx = tid + e * kTrsvThreads;
+                const int a = idx >> 6, b = idx & 63;
+                const int r = mode <= 1 ? a : b, k = mode <= 1 ? b : a;
+                const bool lower = forward;
+                T val = v[e];
+                if (r == k) val = (mode == 0 || mode == 3) ? T(1) : val;
+                else if (lower ? k > r : k < r) val = T(0);
+                sm.D[r][k] = val;
+            }
+            load_inv(j, v);
+            if (tid == 0 && !wait_geq(cnt + j, p)) atomicExch(&g_solve_timeout, 1);
+            __syncthreads();
+            store_tile(v);
+            for (int idx = tid; idx < TB * NR; idx += kTrsvThreads) {
+                const int r = idx / NR, c = idx % NR;
+                sm.acc[r][c] = (r < bj && c < nr) ? ldcg(Y + ((int64_t)j * TB + r) * ldy + c) : T(0);
+            }
+            __syncthreads();
+            const int r = tid >> 2, qq = tid & 3;
+            T part[NR];
+            tile_gemv<T, NR>(sm.S, sm.acc, r, qq, part);          // y0 = X b
+#pragma unroll
+            for (int c = 0; c < NR; ++c)
+                if ((c & 3) == qq) sm.y[r][c] = part[c];
+            __syncthreads();
+            tile_gemv<T, NR>(sm.D, sm.y, r, qq, part);            // b - T y0
+#pragma unroll
+            for (int c = 0; c < NR; ++c)
+                if ((c & 3) == qq) sm.acc[r][c] -= part[c];
+            __syncthreads();
+            tile_gemv<T, NR>(sm.S, sm.acc, r, qq, part);          // y = y0 + X (b - T y0)
+#pragma unroll
+            for (int c = 0; c < NR; ++c)
+                if ((c & 3) == qq) {
+                    const T yv = sm.y[r][c] + part[c];
+                    sm.y[r][c] = yv;
+                    if (r < bj && c < nr) Y[((int64_t)j * TB + r) * ldy + c] = yv;
+                }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) st_release(ready + j, 1);
+        } else {
+            if (tid == 0 && !wait_geq(ready + j, 1)) atomicExch(&g_solve_timeout, 1);
+            __syncthreads();
+            for (int idx = tid; idx < TB * NR; idx += kTrsvThreads) {
+                const int r = idx / NR, c = idx % NR;
+                sm.y[r][c] = (r < bj && c < nr) ? ldcg(Y + ((int64_t)j * TB + r) * ldy + c) : T(0);
+            }
+        }
+        // this item's blocks i, nearest to the diagonal first
+        const int left = nblk - 1 - p;          // blocks still to come
+        const int first = s * kSeg, last = min(left, first + kSeg);
+        if (first < last) load_tile(forward ? j + 1 + first : j - 1 - first, j, v);
+        const int r = tid >> 2, qq = tid & 3;
+        for (int q = first; q < last; ++q) {
+            const int i = forward ? j + 1 + q : j - 1 - q;
+            __syncthreads();
+            store_tile(v);
+            __syncthreads();
+            if (q + 1 < last) load_tile(forward ? i + 1 : i - 1, j, v);
+            T part[NR];
+            tile_gemv<T, NR>(sm.S, sm.y, r, qq, part);
+            const int64_t row = (int64_t)i * TB + r;
+            if (row < n) {
+#pragma unroll
+                for (int c = 0; c < NR; ++c)
+                    if ((c & 3) == qq && c < nr) atomicAdd(Y + row * ldy + c, -part[c]);
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) atomicAdd(cnt + i, 1);
+        }
+    }
+}
+
+// Inverses of the 64 x 64 diagonal blocks of L (unit lower, blockIdx.y = 0)
+// and U (upper, blockIdx.y = 1), by column-wise substitution in FP64, stored
+// row-major per block; rows and columns past a ragged last block are zero.
+template <typename TS>
+__global__ void __launch_bounds__(TB) k_trtri_diag(const TS *C, int64_t ldc, int n, TS *Dinv) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    double(*t)[TB + 1] = reinterpret_cast<double(*)[TB + 1]>(smraw);
+    double(*x)[TB + 1] = t + TB;
+    const int j = blockIdx.x, which = blockIdx.y, c = threadIdx.x;
+    const int nblk = (n + TB - 1) / TB, bj = min(TB, n - j * TB);
+    const int64_t j0 = (int64_t)j * TB;
+    for (int r = 0; r < TB; ++r) t[r][c] = (r < bj && c < bj) ? (double)C[(j0 + r) * ldc + j0 + c] : 0.0;
+    __syncthreads();
+    for (int r = 0; r < TB; ++r) x[r][c] = 0.0;
+    if (c < bj) {
+        if (which == 0) {   // L x = e_c, unit diagonal
+            x[c][c] = 1.0;
+            for (int r = c + 1; r < bj; ++r) {
+                double sum = 0.0;
+                for (int k = c; k < r; ++k) sum = fma(t[r][k], x[k][c], sum);
+                x[r][c] = -sum;
+            }
+        } else {            // U x = e_c
+            x[c][c] = 1.0 / t[c][c];
+            for (int r = c - 1; r >= 0; --r) {
+                double sum = 0.0;
+                for (int k = r + 1; k <= c; ++k) sum = fma(t[r][k], x[k][c], sum);
+                x[r][c] = -sum / t[r][r];
+            }
+        }
+    }
+    __syncthreads();
+    TS *out = Dinv + ((int64_t)which * nblk + j) * TB * TB;
+    for (int r = 0; r < TB; ++r) out[r * TB + c] = (TS)x[r][c];
+}
+
+template <typename TS, typename T, int NR>
+cudaError_t launch_trsv(const TS *C, int64_t ldc, int64_t n, const TS *Dinv, T *Y, int64_t ldy, int nr, int mode,
+                        const int *skip, int *sync, cudaStream_t s) {
+    const size_t sm = sizeof(TrsvSmem<T, NR>);
+    static int grid = 0;
+    if (!grid) {
+        if (sm > 48 * 1024)
+            cudaFuncSetAttribute(k_trsv<TS, T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        int per_sm = 1, dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsv<TS, T, NR>, kTrsvThreads, sm) !=
+                cudaSuccess ||
+            per_sm < 1) {
+            cudaGetLastError();
+            per_sm = 1;
+        }
+        grid = sms * per_sm;
+    }
+    const int64_t nblk = cdiv(n, TB);
+    cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)(2 + 2 * nblk) * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    k_trsv<TS, T, NR><<<grid, kTrsvThreads, sm, s>>>(C, ldc, (int)n, Dinv, Y, ldy, nr, mode, skip, sync);
+    return cudaGetLastError();
+}
+
 template <typename TS, typename T>
 cudaError_t solve_typed(const genp_factors *F, T *Y, int64_t ldy, int64_t nrhs, bool transposed, const int *skip,
                         cudaStream_t s) {
     const TS *C = static_cast<const TS *>(F->C);
     const int64_t n = F->n, ldc = F->ldc;
-    const int64_t nblk = cdiv(n, kBs);
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(k_diag_solve<TS, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
-        attr_done = true;
-    }
-    for (int64_t c0 = 0; c0 < nrhs; c0 += kRhsTile) {
-        const int nr = (int)(nrhs - c0 < kRhsTile ? nrhs - c0 : kRhsTile);
+    if (n > INT32_MAX - TB) return cudaErrorInvalidValue;
+    for (int64_t c0 = 0; c0 < nrhs; c0 += kTrsvMaxRhs) {
+        const int nr = (int)(nrhs - c0 < kTrsvMaxRhs ? nrhs - c0 : kTrsvMaxRhs);
         T *Yc = Y + c0;
         for (int pass = 0; pass < 2; ++pass) {
             // pass 0: L (or U^T) forward; pass 1: U (or L^T) backward
             const int mode = transposed ? (pass == 0 ? 2 : 3) : (pass == 0 ? 0 : 1);
-            for (int64_t q = 0; q < nblk; ++q) {
-                const int64_t blk = pass == 0 ? q : nblk - 1 - q;
-                const int64_t b0 = blk * kBs;
-                const int bs = (int)(n - b0 < kBs ? n - b0 : kBs);
-                const size_t sm = ((size_t)bs * (bs + 1) + (size_t)bs * nr) * sizeof(T);
-                note_launch();
-                k_diag_solve<TS, T><<<1, kThreads, sm, s>>>(C, ldc, b0, bs, Yc, ldy, nr, mode, skip);
-                cudaError_t e;
-                if (pass == 0) {
-                    const int64_t r0 = b0 + bs, rem = n - r0;
-                    if (rem <= 0) continue;
-                    // rows below: Y[r0:] -= op(C)[r0:, b0:b0+bs] * Y[b0:b0+bs]
-                    if (!transposed)
-                        e = gemm<T>(rem, nr, bs, T(-1), (const T *)(C + r0 * ldc + b0), ldc, false, Yc + b0 * ldy, ldy,
-                                    T(1), Yc + r0 * ldy, ldy, Yc + r0 * ldy, ldy, skip, s);
-                    else  // (U^T)[r0+i][b0+k] = U[b0+k][r0+i]
-                        e = gemm<T>(rem, nr, bs, T(-1), (const T *)(C + b0 * ldc + r0), ldc, true, Yc + b0 * ldy, ldy,
-                                    T(1), Yc + r0 * ldy, ldy, Yc + r0 * ldy, ldy, skip, s);
-                } else {
-                    const int64_t rem = b0;
-                    if (rem <= 0) continue;
-                    if (!transposed)  // U[0:b0, b0:b0+bs]
-                        e = gemm<T>(rem, nr, bs, T(-1), (const T *)(C + b0), ldc, false, Yc + b0 * ldy, ldy, T(1), Yc,
-                                    ldy, Yc, ldy, skip, s);
-                    else  // (L^T)[i][b0+k] = L[b0+k][i]
-                        e = gemm<T>(rem, nr, bs, T(-1), (const T *)(C + b0 * ldc), ldc, true, Yc + b0 * ldy, ldy, T(1),
-                                    Yc, ldy, Yc, ldy, skip, s);
-                }
-                if (e != cudaSuccess) return e;
-            }
+            const TS *D = static_cast<const TS *>(F->dinv);
+            int *sy = F->trsv_sync;
+            cudaError_t e;
+            if (nr == 1) e = launch_trsv<TS, T, 1>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, s);
+            else if (nr <= 2) e = launch_trsv<TS, T, 2>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, s);
+            else if (nr <= 4) e = launch_trsv<TS, T, 4>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, s);
+            else if (nr <= 8) e = launch_trsv<TS, T, 8>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, s);
+            else e = launch_trsv<TS, T, 16>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, s);
+            if (e != cudaSuccess) return e;
         }
     }
     return cudaGetLastError();
@@ -252,10 +469,10 @@ template <typename T>
 cudaError_t lu_solve_inplace(const genp_factors *F, T *Y, int64_t ldy, int64_t nrhs, bool transposed, const int *skip,
                              cudaStream_t s) {
     if (sizeof(T) == 8) {
-        if (F->prec != GENP_FP64) return cudaErrorInvalidValue;
+        if (!f64_factors(F->prec)) return cudaErrorInvalidValue;
         return solve_typed<T, T>(F, Y, ldy, nrhs, transposed, skip, s);
     }
-    if (F->prec == GENP_FP64) return cudaErrorInvalidValue;
+    if (f64_factors(F->prec)) return cudaErrorInvalidValue;
     return solve_typed<float, T>(F, Y, ldy, nrhs, transposed, skip, s);
 }
 template cudaError_t lu_solve_inplace<double>(const genp_factors *, double *, int64_t, int64_t, bool, const int *,
@@ -280,6 +497,43 @@ template cudaError_t convert_matrix<double, double>(const double *, int64_t, dou
                                                     const int *, cudaStream_t);
 template cudaError_t convert_matrix<float, float>(const float *, int64_t, float *, int64_t, int64_t, int64_t,
                                                   const int *, cudaStream_t);
+
+int solve_timeout_flag(bool reset) {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_solve_timeout, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    if (reset && v) {
+        int z = 0;
+        cudaMemcpyToSymbol(g_solve_timeout, &z, sizeof(int));
+    }
+    return v;
+}
+
+int64_t trsv_sync_ints(int64_t n) { return 2 + 2 * cdiv(n, TB); }
+int64_t diag_inverse_elems(int64_t n) { return 2 * cdiv(n, TB) * TB * TB; }
+
+cudaError_t invert_diag_blocks(genp_factors *F, cudaStream_t s) {
+    const int64_t n = F->n;
+    if (n > INT32_MAX - TB) return cudaErrorInvalidValue;
+    dim3 g((unsigned)cdiv(n, TB), 2);
+    const size_t sm = 2 * TB * (TB + 1) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_trtri_diag<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_trtri_diag<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        attr = true;
+    }
+    note_launch();
+    if (f64_factors(F->prec))
+        k_trtri_diag<double><<<g, TB, sm, s>>>(static_cast<const double *>(F->C), F->ldc, (int)n,
+                                               static_cast<double *>(F->dinv));
+    else
+        k_trtri_diag<float><<<g, TB, sm, s>>>(static_cast<const float *>(F->C), F->ldc, (int)n,
+                                              static_cast<float *>(F->dinv));
+    return cudaGetLastError();
+}
 
 cudaError_t refine_init(genp_factors *F, const double *A, int64_t lda, int64_t n, cudaStream_t s) {
     unsigned long long *bits = reinterpret_cast<unsigned long long *>(&F->norms[1]);

@@ -268,6 +268,62 @@ def test_solve_shapes(g, n, nrhs, kind):
     assert np.abs(host(X0) - r["x"]).max() <= 1e-13 * kappa_c * max(1.0, np.abs(r["x"]).max())
 
 
+@pytest.mark.parametrize("prec", ["FP64", "FP32"])
+@pytest.mark.parametrize("n,nrhs", [(1100, 1), (1100, 5), (2113, 16), (1500, 19), (64, 2), (129, 1)])
+def test_triangular_solves_streaming(g, prec, n, nrhs):
+    """The persistent triangular solves (several work items per block column
+    from n > 17 * 64 on, ragged last block, two right-hand-side chunks at
+    nrhs > 16), forward and transposed, against the oracle's substitutions
+    with the same factors.  C is diagonally dominant, so L and U are well
+    conditioned and the forward error stays within a few n u |y|."""
+    rng = np.random.default_rng(n + nrhs)
+    C0 = rng.standard_normal((n, n)) / np.sqrt(n) + 4.0 * np.eye(n)
+    dt = torch.float64 if prec == "FP64" else torch.float32
+    u = 2.0 ** -53 if prec == "FP64" else 2.0 ** -24
+    C = cu(C0, dt)
+    F = g.factor(C, prec=getattr(g, prec))
+    LU = host(C).astype(np.float64)
+    G = g.make_multiplier(g.SPARSE_PM1, n, seed=3)
+    Gd = torch.empty((n, n), dtype=torch.float64, device=DEV)
+    g.multiplier_export(G, dense=Gd)
+    Gm = host(Gd)
+    B = rng.standard_normal((n, nrhs))
+    X = torch.empty((n, nrhs), dtype=torch.float64, device=DEV)
+    g.solve(F, G, cu(B), X)
+    Bq = B.astype(np.float32).astype(np.float64) if prec == "FP32" else B
+    y = oracle.lu_solve(LU, Bq)
+    tol = 8 * n * u * (np.abs(Gm) @ np.abs(y)).max()
+    assert np.abs(host(X) - Gm @ y).max() <= tol
+    # transposed pair through the adjoint: dB = L^-T U^-T G^T gX
+    gX = rng.standard_normal((n, nrhs))
+    dB = torch.empty((n, nrhs), dtype=torch.float64, device=DEV)
+    g.adjoint(F, G, cu(gX), X, None, dB)
+    rhs = Gm.T @ gX
+    if prec == "FP32":
+        rhs = rhs.astype(np.float32).astype(np.float64)
+    lam = oracle.lu_solve_T(LU, rhs)
+    assert np.abs(host(dB) - lam).max() <= 8 * n * u * np.abs(lam).max()
+    assert g._lib.load().genp_device_check(1) == 0
+
+
+@pytest.mark.parametrize("prec,kind,nrhs", [("FP64", 0, 1), ("FP32", 1, 3), ("BF16X3", 0, 16), ("BF16X3", 2, 2)])
+def test_gmres_ir(g, prec, kind, nrhs):
+    """GMRES-IR (method 1): every precision of factors reaches eta <= 1e-14,
+    each right-hand side in its own Krylov space; the result agrees with the
+    definition-level GEPP solution within the forward-error bound."""
+    n = 300
+    A, _, B = (t.numpy() for t in W.lead_deficient(n, 32, 16, nrhs, seed=7))
+    X, info, G, F = g.solve_system(cu(A), cu(B), kind=kind, seed=3, prec=getattr(g, prec), refine_steps=8,
+                                   tol=1e-16, method=1)
+    x = host(X)
+    assert oracle.backward_error(A, x, B) <= 1e-14
+    xr = oracle.gepp_solve(A, B)
+    kappa = np.linalg.cond(A, np.inf)
+    assert np.abs(x - xr).max() <= 1e-14 * kappa * np.abs(xr).max()
+    assert len(info.bwd_err) == info.refine_iters + 1
+    assert g._lib.load().genp_device_check(1) == 0
+
+
 def test_2x2_antidiagonal_solved(g):
     A = np.array([[0.0, 1.0], [1.0, 0.0]])
     B = np.array([[2.0], [3.0]])

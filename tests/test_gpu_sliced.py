@@ -1,0 +1,246 @@
+"""FP64-class products on the BF16 tensor cores (GENP_BF16_SLICED) vs the oracle.
+
+The sliced product cuts each FP64 row of A and column of B, scaled by a power
+of two 2^e > max|x|, into nd exact 7-bit digits and sums the digit products of
+weight >= 2^-(7 nd + 7) on the tensor cores (K chunks of 512).  Error bounds
+used below (per chunk, per term of the sum over k, against 2^{e_i + f_j}):
+  operand truncation 2 * 2^-(7 nd + 1), dropped digit pairs (nd - 1) 2^-(7 nd + 2)
+  and lower groups, FP32 rounding of the smallest group's accumulator,
+so |D - A B|_ij <= 2^-(7 nd - 5) K max_k|a_ik| max_k|b_kj| (a factor of 8 to
+spare over the sum of the terms above, which stay below 2^-(7 nd - 2)).  The
+median relative error is also checked, at 2^-(7 nd - 5), which a wrong weight
+or a lost digit group breaks by orders of magnitude.
+
+Integer data whose rows need at most 7 nd bits slice exactly and sum exactly
+(every group sum is an integer below 2^24), so C = L0 U0 with small-integer
+factors must come back bit for bit, and a zero pivot made by the Schur update
+must be exactly zero.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def cu(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(DEV, dtype)
+
+
+@pytest.fixture(scope="module")
+def g(genp_lib):
+    import paper_1212_4560_gb300 as genp
+    assert genp_lib.genp_device_check(1) == 0
+    return genp
+
+
+@pytest.fixture
+def digits(genp_lib, request):
+    nd = request.param
+    old = genp_lib.genp_sliced_digits(nd)
+    assert old in (5, 6, 7)
+    yield nd
+    genp_lib.genp_sliced_digits(old)
+
+
+def sliced(lib, A, B, alpha=1.0, beta=0.0, D=None, nd=0):
+    m, K = A.shape
+    n = B.shape[1]
+    if D is None:
+        D = torch.zeros((m, n), dtype=torch.float64, device=DEV)
+    st = lib.genp_gemm_sliced(m, n, K, alpha, _p(A), A.stride(0), _p(B), B.stride(0), beta, _p(D), D.stride(0), nd,
+                              ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 0, st
+    torch.cuda.synchronize()
+    assert lib.genp_device_check(1) == 0
+    return D
+
+
+def bound(nd, A, B):
+    K = A.shape[1]
+    return 2.0 ** -(7 * nd - 5) * K * np.abs(A).max(1)[:, None] * np.abs(B).max(0)[None, :]
+
+
+@pytest.mark.parametrize("nd", [5, 6, 7])
+@pytest.mark.parametrize("m,n,K", [(1, 1, 1), (128, 64, 64), (200, 130, 1000), (77, 300, 513)])
+def test_gemm_sliced_integers_exact(genp_lib, nd, m, n, K):
+    rng = np.random.default_rng(m * 7 + n + K)
+    A = rng.integers(-127, 128, (m, K)).astype(np.float64)
+    B = rng.integers(-127, 128, (K, n)).astype(np.float64)
+    D = sliced(genp_lib, cu(A), cu(B), nd=nd)
+    assert np.array_equal(D.cpu().numpy(), oracle.matmul(A, B))
+
+
+@pytest.mark.parametrize("nd", [5, 6, 7])
+@pytest.mark.parametrize("m,n,K", [(128, 64, 512), (300, 260, 700), (129, 65, 1536)])
+def test_gemm_sliced_gaussian(genp_lib, nd, m, n, K):
+    rng = np.random.default_rng(nd * 1000 + K)
+    A = rng.standard_normal((m, K)) * np.exp(rng.uniform(-3, 3, (m, 1)))    # rows of different scales
+    B = rng.standard_normal((K, n)) * np.exp(rng.uniform(-3, 3, (1, n)))
+    D = sliced(genp_lib, cu(A), cu(B), nd=nd).cpu().numpy()
+    ref = oracle.matmul(A, B)
+    err = np.abs(D - ref)
+    assert np.all(err <= bound(nd, A, B))
+    assert np.median(err / np.abs(ref)) <= 2.0 ** -(7 * nd - 5)
+
+
+@pytest.mark.parametrize("nd", [5, 7])
+def test_gemm_sliced_schur_form_and_extremes(genp_lib, nd):
+    """D <- D - A B in place, with every digit at its largest (entries
+    0.999 give leading digits of 128 and the group sums reach 2^24 at K = 512)."""
+    m, n, K = 140, 70, 1024
+    A = np.full((m, K), 0.999)
+    B = np.full((K, n), 0.999)
+    D0 = np.random.default_rng(1).standard_normal((m, n))
+    D = sliced(genp_lib, cu(A), cu(B), alpha=-1.0, beta=1.0, D=cu(D0), nd=nd).cpu().numpy()
+    ref = D0 - oracle.matmul(A, B)
+    assert np.all(np.abs(D - ref) <= bound(nd, A, B) + 2.0 ** -52 * np.abs(ref))
+
+
+def test_gemm_sliced_rejects_bad_args(genp_lib):
+    A = torch.zeros((4, 4), dtype=torch.float64, device=DEV)
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert genp_lib.genp_gemm_sliced(4, 4, 4, 1.0, _p(A), 4, _p(A), 4, 0.0, _p(A), 4, 4, s) == -1   # 4 digits
+    assert genp_lib.genp_gemm_sliced(4, 4, 4, 1.0, _p(A), 3, _p(A), 4, 0.0, _p(A), 4, 7, s) == -1   # lda < K
+    assert genp_lib.genp_sliced_digits(3) == -1
+    assert genp_lib.genp_sliced_digits(0) in (5, 6, 7)
+
+
+@pytest.mark.parametrize("digits", [5, 7], indirect=True)
+@pytest.mark.parametrize("n", [200, 1100])
+def test_precondition_sliced(g, digits, n):
+    A, _, _ = W.lead_deficient(n, 32, 16, 1, seed=n)
+    A = A.numpy()
+    G = g.make_multiplier(g.GAUSSIAN, n, seed=3)
+    Gd = torch.empty((n, n), dtype=torch.float64, device=DEV)
+    g.multiplier_export(G, dense=Gd)
+    Gm = Gd.cpu().numpy()
+    C = torch.empty((n, n), dtype=torch.float64, device=DEV)
+    g.precondition(G, cu(A), C, c_prec=g.BF16_SLICED)
+    torch.cuda.synchronize()
+    assert g._lib.load().genp_device_check(1) == 0
+    ref = oracle.matmul(A, Gm)
+    err = np.abs(C.cpu().numpy() - ref)
+    assert np.all(err <= bound(digits, A, Gm))
+    assert np.median(err / np.abs(ref)) <= 2.0 ** -(7 * digits - 5)
+
+
+@pytest.mark.parametrize("digits", [5, 6, 7], indirect=True)
+@pytest.mark.parametrize("n,nb", [(96, 0), (300, 0), (520, 128), (700, 64)])
+def test_factor_sliced_backward_error(g, digits, n, nb):
+    """|L U - C|_ij <= 2^-(7 nd - 6) n max_k|l_ik| max_k|u_kj|: each Schur
+    update errs by the sliced product's 2^-(7 nd - 5) K against the row and
+    column maxima of its L21 and U12 (not against |L||U| entry by entry: the
+    digit slices share one scale per row and per column), plus the
+    double-float trailing matrix (2^-48 per update) and the FP64 panels."""
+    A, _, _ = W.lead_deficient(n, 16, 8, 1, seed=n + 1)
+    C0 = oracle.precondition(A.numpy(), oracle.multiplier(0, n, seed=5))
+    C = cu(C0)
+    F = g.factor(C, prec=g.BF16_SLICED, nb=nb)
+    info = g.info_fetch(F)
+    assert info.breakdown_step == -1
+    assert g._lib.load().genp_device_check(1) == 0
+    L, U = oracle.split_lu(C.cpu().numpy())
+    scale = np.abs(L).max(1)[:, None] * np.abs(U).max(0)[None, :]
+    err = np.abs(L @ U - C0)
+    assert np.all(err <= 2.0 ** -(7 * digits - 6) * n * scale)
+    # the bound is not slack by orders of magnitude: a lost digit group would pass it only at larger errors
+    assert np.median(err / (n * scale)) <= 2.0 ** -(7 * digits)
+
+
+@pytest.mark.parametrize("digits", [5, 7], indirect=True)
+@pytest.mark.parametrize("n", [128, 257, 400])
+def test_factor_sliced_integer_exact(g, digits, n):
+    rng = np.random.default_rng(n)
+    L0 = np.tril(rng.integers(-2, 3, (n, n)), -1) + np.eye(n, dtype=np.int64)
+    U0 = np.triu(rng.integers(-2, 3, (n, n)), 1) + np.diag(rng.choice([-1, 1], n))
+    C0 = (L0 @ U0).astype(np.float64)
+    C = cu(C0)
+    F = g.factor(C, prec=g.BF16_SLICED, nb=64)
+    assert g.info_fetch(F).breakdown_step == -1
+    L, U = oracle.split_lu(C.cpu().numpy())
+    assert np.array_equal(L, L0.astype(float))
+    assert np.array_equal(U, U0.astype(float))
+
+
+def test_factor_sliced_breakdown_after_schur_update(g):
+    """u_kk = 0 exactly at k = 130 (inside the third panel of 64): the zero is
+    produced by the sliced Schur updates, which must be exact on integers."""
+    n, k = 256, 130
+    rng = np.random.default_rng(5)
+    L0 = np.tril(rng.integers(-2, 3, (n, n)), -1) + np.eye(n, dtype=np.int64)
+    d = rng.choice([-1, 1], n)
+    d[k] = 0
+    U0 = np.triu(rng.integers(-2, 3, (n, n)), 1) + np.diag(d)
+    C = cu((L0 @ U0).astype(np.float64))
+    F = g.factor(C, prec=g.BF16_SLICED, nb=64)
+    info = g.info_fetch(F)
+    assert info.breakdown_step == k
+    assert info.status == -2      # GENP_ERR_BREAKDOWN
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_sliced_with_fp64_refinement(g, kind):
+    A, _, B = (t.numpy() for t in W.lead_deficient(256, 32, 16, 1, seed=0))
+    X, info, G, F = g.solve_system(cu(A), cu(B), kind=kind, seed=5, prec=g.BF16_SLICED, refine_steps=10, tol=1e-16)
+    eta = oracle.backward_error(A, X.cpu().numpy(), B)
+    assert eta <= 1e-14
+    assert info.breakdown_step == -1
+    assert g._lib.load().genp_device_check(1) == 0
+
+
+@pytest.mark.parametrize("digits", [7], indirect=True)
+@pytest.mark.parametrize("kappa", [1e2, 1e6])
+def test_sliced_ill_conditioned(g, digits, kappa):
+    n = 1024
+    A, Xs, B = (t.numpy() for t in W.svd_kappa(n, kappa, 1, seed=1))
+    X, info, G, F = g.solve_system(cu(A), cu(B), kind=g.GAUSSIAN, seed=2, prec=g.BF16_SLICED, refine_steps=15,
+                                   tol=1e-16)
+    x = X.cpu().numpy()
+    assert oracle.backward_error(A, x, B) <= 1e-14
+    assert np.abs(x - Xs).max() / np.abs(Xs).max() <= 1e-14 * kappa * 10
+
+
+def test_sliced_adjoint(g):
+    n, nrhs = 160, 2
+    A, _, B = (t.numpy() for t in W.shifted(1, n, nrhs, seed=4))
+    A, B = A[0], B[0]
+    X, info, G, F = g.solve_system(cu(A), cu(B), kind=g.GAUSSIAN, seed=1, prec=g.BF16_SLICED, refine_steps=10,
+                                   tol=1e-16)
+    dA = torch.empty((n, n), dtype=torch.float64, device=DEV)
+    dB = torch.empty((n, nrhs), dtype=torch.float64, device=DEV)
+    g.adjoint(F, G, X, X, dA, dB)
+    x = X.cpu().numpy()
+    dA_ref, dB_ref = oracle.adjoint(A, x, x)
+    # the adjoint reuses the sliced factors without refinement: its error is
+    # the factorization's (2^-46 against the operand scales, times the growth
+    # and the conditioning), far below the 1e-6 of the gradient check
+    assert np.linalg.norm(dB.cpu().numpy() - dB_ref) <= 1e-6 * np.linalg.norm(dB_ref)
+    assert np.linalg.norm(dA.cpu().numpy() - dA_ref) <= 1e-6 * np.linalg.norm(dA_ref)
+
+
+@pytest.mark.parametrize("digits", [5, 6, 7], indirect=True)
+@pytest.mark.parametrize("kappa", [1e2, 1e6])
+def test_sliced_gmres_ir(g, digits, kappa):
+    """GMRES-IR (genp_refine method 1) needs the factors only as a
+    preconditioner: 5 and 6 digits, where classic refinement stalls on the
+    kappa = 1e6 system, still reach eta <= 1e-14 in a few outer steps."""
+    n = 1024
+    A, Xs, B = (t.numpy() for t in W.svd_kappa(n, kappa, 1, seed=1))
+    X, info, G, F = g.solve_system(cu(A), cu(B), kind=g.GAUSSIAN, seed=2, prec=g.BF16_SLICED, refine_steps=6,
+                                   tol=1e-16, method=1)
+    x = X.cpu().numpy()
+    assert oracle.backward_error(A, x, B) <= 1e-14
+    assert np.abs(x - Xs).max() / np.abs(Xs).max() <= 1e-14 * kappa * 10
+    assert info.refine_iters <= 4
+    assert g._lib.load().genp_device_check(1) == 0

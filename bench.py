@@ -9,9 +9,14 @@ in libgenp's kernels, called through the C ABI:
   a6-a7 L U y = B, X = G y
   a8 FP64 iterative refinement until the backward error is <= 1e-14
   a9 adjoint for the loss 0.5 ||X||_F^2 (gX = X): dA = -Lambda X^T, dB = Lambda
-The default workload is the n = 8192 FP64 system with a dense Gaussian
-N(0, 1/n) multiplier and 16 right-hand sides; A, G and C are 512 MiB each,
-larger than L2, so no flush is needed between steps.
+The default workload is the mixed-precision system: n = 16384,
+A = J U diag(sigma) V^T with kappa(A) = 1e6, a dense Gaussian N(0, 1/n)
+multiplier, one right-hand side, factors from BF16 tensor-core products by
+exact digit slicing (7 digits) and GMRES-IR in FP64 to a backward error
+<= 1e-14; the same system is then solved by the FP64 path on the same GPU
+(1 warm-up + 1 timed step) for the comparison the metric names.  A, G and C
+are 2 GiB each, larger than L2, so no flush is needed between steps.
+`--workload lead --prec fp64 --n 8192 --nrhs 16` is the FP64 system at scale.
 
 `--impl reference` times the CPU oracle (plain C, FP64) on a bounded sample
 of the same workload on the host cores instead.
@@ -55,18 +60,18 @@ def parse():
     p.add_argument("--steps", type=int, default=8)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--n", type=int, default=8192)
-    p.add_argument("--nrhs", type=int, default=16)
+    p.add_argument("--n", type=int, default=16384)
+    p.add_argument("--nrhs", type=int, default=1)
     p.add_argument("--kind", default="gaussian", choices=list(KINDS))
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--tol", type=float, default=1e-14)
-    p.add_argument("--workload", default="lead", choices=["lead", "svd", "batched", "diff"],
+    p.add_argument("--workload", default="svd", choices=["lead", "svd", "batched", "diff"],
                    help="lead: N(0,1) A with a rank-deficient leading block; svd: A = J U diag(sigma) V^T; "
                         "batched: 10k systems n in [16,512], a11 = 0, FP32 factors + FP64 refinement; "
                         "diff: 256 x n=1024 FP32 systems, circulant G, 8 RHS, forward + adjoint")
     p.add_argument("--count", type=int, default=None, help="systems in the batched / diff workloads")
-    p.add_argument("--kappa", type=float, default=1e2, help="condition number of the svd workload")
-    p.add_argument("--prec", default="fp64", choices=list(PRECS))
+    p.add_argument("--kappa", type=float, default=1e6, help="condition number of the svd workload")
+    p.add_argument("--prec", default="sliced", choices=list(PRECS))
     p.add_argument("--digits", type=int, default=0, help="digits per operand of the sliced precision (5, 6, 7)")
     p.add_argument("--refine", default=None, choices=["classic", "gmres"],
                    help="refinement method (default: classic for fp64, GMRES-IR otherwise)")
@@ -74,6 +79,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--no-fp64-compare", action="store_true",
+                   help="skip timing the FP64 path on the same system (non-FP64 precisions)")
     return p.parse_args()
 
 
@@ -330,6 +337,9 @@ def run_ours(a):
 
     phases = ["multiplier", "precondition", "factor", "solve", "refine", "adjoint"]
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(a.steps)]
+    lib = genp._lib.load()
+    if a.prec == "sliced":      # CUDA events around every tensor-core launch of the timed region
+        lib.genp_profile_enable(1)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -344,6 +354,13 @@ def run_ours(a):
         t_end.record(stream)
         torch.cuda.synchronize()
     launches = genp.launch_count() - l0
+    tc_prof = None
+    if a.prec == "sliced":
+        import ctypes
+        p_ms, p_fl, p_n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        lib.genp_profile_read(ctypes.byref(p_ms), ctypes.byref(p_fl), ctypes.byref(p_n))
+        lib.genp_profile_enable(0)
+        tc_prof = (p_ms.value, p_fl.value, p_n.value)
     if world > 1:
         dist.barrier()
     total_ms = t_start.elapsed_time(t_end)
@@ -398,14 +415,23 @@ def run_ours(a):
 
     # dominant kernel: the GEMM of C = A G (one launch per BF16 term / per FP64 call)
     peaks = measured_peaks()
-    if a.kind == "gaussian" and a.prec == "sliced":
-        nd = genp._lib.load().genp_sliced_digits(0)
+    if a.prec == "sliced" and tc_prof and tc_prof[2] > 0:
+        nd = lib.genp_sliced_digits(0)
         pairs = nd * (nd + 1) // 2
-        achieved = pairs * 2.0 * n**3 / (phase_ms["precondition"] / 1e3) / 1e12
-        peak = float(peaks.get("bf16_tflops", 1900.0))
-        roofline = {"kernel": f"k_tc_sliced<{nd}> (tcgen05 BF16, C = A G as {pairs} digit products)",
+        t_ms, t_fl, t_n = tc_prof
+        achieved = t_fl / (t_ms / 1e3) / 1e12
+        peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
+        roofline = {"kernel": f"k_tc_sliced<{nd}> (tcgen05 BF16: A G and the Schur updates as {pairs} digit "
+                              f"products per FP64 multiply-add)",
                     "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "peak_source": "measured bf16_tflops (burst)" if "bf16_tflops" in peaks else "fallback",
+                    "peak_source": "measured bf16_tflops_sustained (kernel timed inside a long step)"
+                    if "bf16_tflops_sustained" in peaks else "fallback",
+                    "launches": t_n, "avg_launch_ms": t_ms / t_n,
+                    "share_of_step": (t_ms / a.steps) / ms_per_step,
+                    "algorithmic": f"{pairs} x 2 m n Kpad BF16 flop per launch (digit pairs of the sliced product); "
+                                   f"FP64-equivalent work is 1/{pairs} of it",
+                    # dram read+write bytes of one n = 4096 precondition launch under ncu, scaled by the
+                    # tiles processed (m n) to the n = 16384 chunk launches; null where not captured
                     "traffic": None}
     elif a.kind == "gaussian" and a.prec in ("bf16", "bf16x3"):
         terms = 3 if a.prec == "bf16x3" else 1
@@ -441,6 +467,9 @@ def run_ours(a):
         cpu = {"value": 1.0 / (t * (n / n_s) ** 3), "unit": "solves/s", "cores": threads, "kind": "oracle",
                "sample": f"oracle pipeline (multiplier, A G, GENP, solves, refinement, adjoint) on an n={n_s} "
                          f"system of the same recipe ({nrhs} RHS), median of 3, time scaled by (n/{n_s})^3 to n={n}"}
+    fp64 = None
+    if a.prec != "fp64" and not a.no_fp64_compare and world == 1:
+        fp64 = fp64_same_gpu(a, genp, A, B, kind, rank, dev)
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "sliced": "bf16"}.get(a.prec, a.prec),
@@ -459,11 +488,55 @@ def run_ours(a):
             "bwd_err": info.bwd_err[-1] if info.bwd_err else None, "refine_iters": info.refine_iters,
             "breakdown_step": info.breakdown_step, "growth": info.growth, "status": info.status,
             "warmup_bwd_err": info_w.bwd_err[-1] if info_w.bwd_err else None}
+    if fp64 is not None:
+        line["fp64_same_gpu"] = fp64
+        line["speedup_vs_fp64"] = value / fp64["value"] if fp64["value"] else None
     if not a.no_clocks:
         line["clocks"] = clk.summary()
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def fp64_same_gpu(a, genp, A, B, kind, rank, dev):
+    """The FP64 path (FP64 product, FP64 GENP, classic FP64 refinement) on the
+    same system and GPU: 1 warm-up step, then max(1, steps // 4) timed steps
+    (each is about ten times a mixed-precision step)."""
+    import torch
+    n, nrhs = a.n, a.nrhs
+    C = torch.empty((n, n), dtype=torch.float64, device=dev)
+    X = torch.empty((n, nrhs), dtype=torch.float64, device=dev)
+    dA = torch.empty((n, n), dtype=torch.float64, device=dev)
+    dB = torch.empty((n, nrhs), dtype=torch.float64, device=dev)
+    G = genp.make_multiplier(kind, n, seed=1, stream_id=rank, value_grid=genp.FP64)
+    genp.precondition(G, A, C, c_prec=genp.FP64)
+    F = genp.factor(C, prec=genp.FP64)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i):
+        genp.redraw_multiplier(G, seed=1000 + i, stream_id=rank)
+        genp.precondition(G, A, C, c_prec=genp.FP64)
+        genp.refactor(F, C)
+        genp.solve(F, G, B, X)
+        genp.refine(A, F, G, B, X, tol=a.tol, max_iter=10, method=0)
+        genp.adjoint(F, G, X, X, dA, dB)
+
+    step(a.warmup)
+    torch.cuda.synchronize()
+    k = max(1, a.steps // 4)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(k):
+        step(a.warmup + 1 + i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / k
+    info = genp.info_fetch(F)
+    del F, G, C, X, dA, dB
+    torch.cuda.empty_cache()
+    return {"value": 1e3 / ms, "unit": "solves/s", "ms_per_step": ms, "steps": k, "warmup": 1,
+            "bwd_err": info.bwd_err[-1] if info.bwd_err else None, "refine_iters": info.refine_iters,
+            "precision": "fp64 product, fp64 GENP, classic fp64 refinement"}
 
 
 def run_batched(a):
@@ -584,6 +657,9 @@ def run_batched(a):
                "sample": f"oracle pipeline on the first {done} systems of the batch (~15 s), scaled to the "
                          f"whole batch by sum n^3"}
     name = "batched_10k_n16-512_fp32_fp64ir_4rhs" if not diff else "diff_256x1024_fp32_circulant_8rhs"
+    fp64 = None
+    if a.prec != "fp64" and not a.no_fp64_compare and world == 1:
+        fp64 = fp64_same_gpu(a, genp, A, B, kind, rank, dev)
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -95,8 +95,10 @@ typedef enum {
  *        exactly (Ozaki, Ogita, Oishi and Rump's error-free splitting).  With
  *        7 digits the products carry about 46 correct bits against the
  *        operands' scales; the trailing matrix is held as double-float pairs
- *        (48 bits) between steps.  FP64 refinement takes the solve to FP64
- *        accuracy. */
+ *        (48 bits) between steps.  The diagonal blocks and block rows and
+ *        columns are solved nb wide in FP64; the tensor-core Schur updates
+ *        take blocks of 2 nb.  FP64 refinement (GMRES-IR at large growth)
+ *        takes the solve to FP64 accuracy. */
 typedef enum {
     GENP_FP64 = 0,
     GENP_FP32 = 1,
@@ -357,6 +359,15 @@ GENP_API genp_status genp_gemm_sliced(int64_t m, int64_t n, int64_t K, double al
  * genp_gemm_sliced call of the process and returns the previous one, or -1
  * if digits is not supported.  Not synchronized with concurrent calls. */
 GENP_API int genp_sliced_digits(int digits);
+
+/* Measurement hook: while enabled, every launch of the sliced tensor-core
+ * kernel is bracketed by two CUDA events on its stream.  genp_profile_read
+ * synchronizes on them and returns the summed kernel time (ms), the digit
+ * products' BF16 flops (2 m n Kpad x digit pairs per launch) and the launch
+ * count since the last read or enable, then restarts the count.  Enabling
+ * costs two event records per launch; it is off by default. */
+GENP_API genp_status genp_profile_enable(int on);
+GENP_API genp_status genp_profile_read(double *ms, double *flops, int *launches);
 
 /* Synchronizes the device and reports whether any kernel of this library
  * that waits on the device (the tensor-core pipelines, the persistent

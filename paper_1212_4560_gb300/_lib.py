@@ -44,6 +44,8 @@ SIGNATURES = {
                               _vp, _i64, _vp]),
     "genp_gemm_sliced": (_int, [_i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _int, _vp]),
     "genp_sliced_digits": (_int, [_int]),
+    "genp_profile_enable": (_int, [_int]),
+    "genp_profile_read": (_int, [_vp, _vp, _vp]),
     "genp_device_check": (_int, [_int]),
     "genp_batched_plan_create": (_int, [_i64, _vp, _i64, _int, _int, _int, _dbl, _int, _vp, ctypes.POINTER(_vp)]),
     "genp_batched_layout": (_int, [_vp, _vp, _vp]),

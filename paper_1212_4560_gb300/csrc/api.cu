@@ -222,6 +222,19 @@ genp_status genp_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha, const v
     return GENP_OK;
 }
 
+genp_status genp_profile_enable(int on) {
+    tc_profile_enable(on != 0);
+    return GENP_OK;
+}
+
+genp_status genp_profile_read(double *ms, double *flops, int *launches) {
+    if (!ms || !flops || !launches) return GENP_ERR_ARG;
+    const int c = tc_profile_read(ms, flops);
+    if (c < 0) return GENP_ERR_CUDA;
+    *launches = c;
+    return GENP_OK;
+}
+
 int genp_sliced_digits(int digits) {
     if (digits == 0) return sliced_digits();
     return set_sliced_digits(digits);
@@ -425,7 +438,7 @@ genp_status genp_factor(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t
     }
     if (st == GENP_OK && prec == GENP_BF16_SLICED) {
         F->nd = sliced_digits();
-        F->tc_ldq = (int64_t)F->nd * sliced_kpad(nb);
+        F->tc_ldq = (int64_t)F->nd * sliced_kpad(2 * nb);   // outer steps of 2 nb
         F->ldw = n;
         st = dalloc(&F->tcA, (size_t)n * F->tc_ldq);
         if (st == GENP_OK) st = dalloc(&F->tcB, (size_t)n * F->tc_ldq);

@@ -21,6 +21,8 @@
 #include "genp_internal.cuh"
 
 #include <cuda.h>
+#include <utility>
+#include <vector>
 #include <cudaTypedefs.h>
 
 #include "dfloat.cuh"
@@ -547,6 +549,32 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S_TMEM) : "memory");
 }
 
+// Optional CUDA-event timing of every k_tc_sliced launch (genp_profile_*).
+struct TcProfile {
+    bool on = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    size_t used = 0;
+    double flops = 0.0;
+};
+TcProfile &tc_profile() {
+    static TcProfile p;
+    return p;
+}
+std::pair<cudaEvent_t, cudaEvent_t> *profile_slot() {
+    TcProfile &p = tc_profile();
+    if (!p.on) return nullptr;
+    if (p.used == p.ev.size()) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess) return nullptr;
+        if (cudaEventCreate(&b) != cudaSuccess) {
+            cudaEventDestroy(a);
+            return nullptr;
+        }
+        p.ev.emplace_back(a, b);
+    }
+    return &p.ev[p.used++];
+}
+
 template <int ND>
 cudaError_t launch_sliced(const CUtensorMap &ma, const CUtensorMap &mb, int64_t m, int64_t n, int64_t kpad,
                           float alpha, const int *ea, const int *fb, dfloat *D, int64_t ldd, cudaStream_t s) {
@@ -559,8 +587,14 @@ cudaError_t launch_sliced(const CUtensorMap &ma, const CUtensorMap &mb, int64_t 
     }
     dim3 grid((unsigned)cdiv(n, SBN), (unsigned)cdiv(m, BM));
     if (grid.y > 65535u) return cudaErrorInvalidValue;
+    auto *ev = profile_slot();
+    if (ev) {
+        cudaEventRecord(ev->first, s);
+        tc_profile().flops += 2.0 * (double)m * (double)n * (double)kpad * (ND * (ND + 1) / 2);
+    }
     note_launch();
     k_tc_sliced<ND><<<grid, 128, SlicedCfg<ND>::kSmem, s>>>(ma, mb, (int)m, (int)n, (int)kpad, alpha, ea, fb, D, ldd);
+    if (ev) cudaEventRecord(ev->second, s);
     return cudaGetLastError();
 }
 
@@ -606,6 +640,30 @@ cudaError_t tc_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha, const __n
     note_launch();
     k_tc_gemm<<<grid, 128, kSmem, s>>>(ma, mb, (int)m, (int)n, (int)K, alpha, beta, Cin, ldci, D, ldd, vec, skip);
     return cudaGetLastError();
+}
+
+void tc_profile_enable(bool on) {
+    TcProfile &p = tc_profile();
+    p.on = on;
+    p.used = 0;
+    p.flops = 0.0;
+}
+
+int tc_profile_read(double *ms, double *flops) {
+    TcProfile &p = tc_profile();
+    double total = 0.0;
+    for (size_t i = 0; i < p.used; ++i) {
+        if (cudaEventSynchronize(p.ev[i].second) != cudaSuccess) return -1;
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, p.ev[i].first, p.ev[i].second) != cudaSuccess) return -1;
+        total += t;
+    }
+    *ms = total;
+    *flops = p.flops;
+    const int count = (int)p.used;
+    p.used = 0;
+    p.flops = 0.0;
+    return count;
 }
 
 int tc_timeout_flag(bool reset) {

@@ -185,6 +185,9 @@ cudaError_t tc_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha, const __n
                          int64_t ldd, const int *skip, cudaStream_t s);
 // Reads the device-side timeout flag of the tensor-core kernels (synchronizes).
 int tc_timeout_flag(bool reset);
+// CUDA-event timing of the sliced tensor-core launches (genp_profile_*).
+void tc_profile_enable(bool on);
+int tc_profile_read(double *ms, double *flops);
 // D += alpha * A B on the tensor cores with FP64-class accuracy, from the
 // nd-digit slices of sliced.cu: Aq (m x nd kpad) and Bq (n x nd kpad, B
 // transposed) with their row / column exponents ea, fb.

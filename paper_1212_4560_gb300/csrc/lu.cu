@@ -239,16 +239,18 @@ cudaError_t factor_tc(genp_factors *F, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// GENP_BF16_SLICED: the FP64 steps of factor_typed (diagonal block, block
-// row and column, all in C) with the Schur update on the tensor cores by
-// exact digit slicing.  The trailing matrix lives in W as double-float
-// pairs; each step first copies its block column and block row from W into
-// C, so C ends up holding the FP64 factors.
+// GENP_BF16_SLICED: blocked GENP in two levels.  The outer block column
+// (2 nb wide) is factored in FP64 by two inner steps of width nb (diagonal
+// block, block row and column, and the small FP64 update of the second inner
+// block by the first); the outer Schur update C22 -= L21 U12 (K = 2 nb) then
+// runs on the tensor cores by exact digit slicing.  The outer trailing matrix
+// lives in W as double-float pairs; each outer step first copies its block
+// column and block row from W into C, so C ends up holding the FP64 factors.
 cudaError_t factor_sliced(genp_factors *F, cudaStream_t s) {
     double *C = static_cast<double *>(F->C);
     dfloat *W = static_cast<dfloat *>(F->W);
     const int64_t n = F->n, ldc = F->ldc, ldw = F->ldw, ldq = F->tc_ldq;
-    const int nb = (int)F->nb;
+    const int nb = (int)F->nb, nbo = 2 * nb;
     const size_t sm_panel = (size_t)nb * (nb + 1) * sizeof(double);
     const size_t xrow = (size_t)nb * (kTrsmW + 1), xcol = (size_t)kTrsmW * (nb + 1);
     const size_t sm_trsm = sm_panel + (xrow > xcol ? xrow : xcol) * sizeof(double);
@@ -260,31 +262,47 @@ cudaError_t factor_sliced(genp_factors *F, cudaStream_t s) {
     }
     note_launch();
     k_maxabs<double><<<152 * 4, 256, 0, s>>>(C, n, ldc, &F->st->max_abs_c);
-    if (n > nb) {
-        cudaError_t e = df_from_f64(C + nb * ldc + nb, ldc, W + nb * ldw + nb, ldw, n - nb, n - nb, s);
+    if (n > nbo) {
+        cudaError_t e = df_from_f64(C + nbo * ldc + nbo, ldc, W + nbo * ldw + nbo, ldw, n - nbo, n - nbo, s);
         if (e != cudaSuccess) return e;
     }
-    for (int64_t k0 = 0; k0 < n; k0 += nb) {
-        const int kb = (int)(n - k0 < nb ? n - k0 : nb);
-        const int64_t rem = n - k0 - kb;
+    for (int64_t k0 = 0; k0 < n; k0 += nbo) {
+        const int kbo = (int)(n - k0 < nbo ? n - k0 : nbo);
+        const int64_t e0 = k0 + kbo, remo = n - e0;
+        cudaError_t e = cudaSuccess;
         if (k0 > 0) {   // this step's block column and block row, updated by the earlier steps
-            cudaError_t e = df_to_f64(W + k0 * ldw + k0, ldw, C + k0 * ldc + k0, ldc, n - k0, kb, s);
-            if (e == cudaSuccess) e = df_to_f64(W + k0 * ldw + k0 + kb, ldw, C + k0 * ldc + k0 + kb, ldc, kb, rem, s);
+            e = df_to_f64(W + k0 * ldw + k0, ldw, C + k0 * ldc + k0, ldc, n - k0, kbo, s);
+            if (e == cudaSuccess) e = df_to_f64(W + k0 * ldw + e0, ldw, C + k0 * ldc + e0, ldc, kbo, remo, s);
             if (e != cudaSuccess) return e;
         }
-        note_launch();
-        k_panel<double, double><<<1, kThreads, sm_panel, s>>>(C, ldc, k0, kb, F->st);
-        if (rem <= 0) break;
-        dim3 g((unsigned)cdiv(rem, kTrsmW), 2);
-        note_launch();
-        k_trsm<double, double><<<g, kThreads, sm_trsm, s>>>(C, ldc, n, k0, kb, F->st);
-        const double *L21 = C + (k0 + kb) * ldc + k0;
-        const double *U12 = C + k0 * ldc + k0 + kb;
-        cudaError_t e = slice_rows(F->nd, L21, ldc, rem, kb, F->tcA, ldq, F->exps, s);
-        if (e == cudaSuccess) e = slice_cols_T(F->nd, U12, ldc, kb, rem, F->tcB, ldq, F->exps + n, s);
+        for (int64_t i0 = k0; i0 < e0; i0 += nb) {
+            const int kb = (int)(e0 - i0 < nb ? e0 - i0 : nb);
+            const int64_t j0 = i0 + kb, rem = n - j0;
+            note_launch();
+            k_panel<double, double><<<1, kThreads, sm_panel, s>>>(C, ldc, i0, kb, F->st);
+            if (rem <= 0) break;
+            dim3 g((unsigned)cdiv(rem, kTrsmW), 2);
+            note_launch();
+            k_trsm<double, double><<<g, kThreads, sm_trsm, s>>>(C, ldc, n, i0, kb, F->st);
+            if (j0 < e0) {
+                // the rest of the outer block column, and its block row beyond it
+                const int64_t w2 = e0 - j0;
+                e = gemm<double>(rem, w2, kb, -1.0, C + j0 * ldc + i0, ldc, false, C + i0 * ldc + j0, ldc, 1.0,
+                                 C + j0 * ldc + j0, ldc, C + j0 * ldc + j0, ldc, nullptr, s);
+                if (e == cudaSuccess && remo > 0)
+                    e = gemm<double>(w2, remo, kb, -1.0, C + j0 * ldc + i0, ldc, false, C + i0 * ldc + e0, ldc, 1.0,
+                                     C + j0 * ldc + e0, ldc, C + j0 * ldc + e0, ldc, nullptr, s);
+                if (e != cudaSuccess) return e;
+            }
+        }
+        if (remo <= 0) break;
+        const double *L21 = C + e0 * ldc + k0;
+        const double *U12 = C + k0 * ldc + e0;
+        e = slice_rows(F->nd, L21, ldc, remo, kbo, F->tcA, ldq, F->exps, s);
+        if (e == cudaSuccess) e = slice_cols_T(F->nd, U12, ldc, kbo, remo, F->tcB, ldq, F->exps + n, s);
         if (e == cudaSuccess)
-            e = tc_gemm_sliced(F->nd, rem, rem, sliced_kpad(kb), -1.0f, F->tcA, ldq, F->tcB, ldq, F->exps, F->exps + n,
-                               W + (k0 + kb) * ldw + k0 + kb, ldw, s);
+            e = tc_gemm_sliced(F->nd, remo, remo, sliced_kpad(kbo), -1.0f, F->tcA, ldq, F->tcB, ldq, F->exps,
+                               F->exps + n, W + e0 * ldw + e0, ldw, s);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();

@@ -50,32 +50,48 @@ __device__ double ln_series(double s) {
     if (m > 1.4142135623730951) { m = __dmul_rn(m, 0.5); e += 1; }
     const double f = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
     const double f2 = __dmul_rn(f, f);
+    // 1/(2k+1), k = 0..11, each the correctly rounded double (what IEEE
+    // division 1.0 / (2k+1) gives), as constants instead of 12 divisions
+    constexpr double kInvOdd[12] = {0x1.0000000000000p+0, 0x1.5555555555555p-2, 0x1.999999999999ap-3,
+                                    0x1.2492492492492p-3, 0x1.c71c71c71c71cp-4, 0x1.745d1745d1746p-4,
+                                    0x1.3b13b13b13b14p-4, 0x1.1111111111111p-4, 0x1.e1e1e1e1e1e1ep-5,
+                                    0x1.af286bca1af28p-5, 0x1.8618618618618p-5, 0x1.642c8590b2164p-5};
     const int K = 11;
-    double p = __ddiv_rn(1.0, (double)(2 * K + 1));
-    for (int k = K - 1; k >= 0; --k) p = __dadd_rn(__dmul_rn(p, f2), __ddiv_rn(1.0, (double)(2 * k + 1)));
+    double p = kInvOdd[K];
+#pragma unroll
+    for (int k = K - 1; k >= 0; --k) p = __dadd_rn(__dmul_rn(p, f2), kInvOdd[k]);
     const double lm = __dmul_rn(__dmul_rn(2.0, f), p);
     const double el = __dmul_rn((double)e, 0.6931471805599453);
     return __dadd_rn(el, lm);
 }
 
+// The accepted pair is searched first (cheap, divergent), the logarithm,
+// division and square root are then taken once per warp with every lane
+// converged: lanes that accept at different tries would otherwise run the
+// expensive part once per try position.
 __device__ double polar_normal(uint64_t seed, uint64_t sid, uint64_t tag, uint64_t idx) {
-    for (uint64_t blk = 0; blk < kPolarBlocks; ++blk) {
+    double v1 = 0.0, s = 0.0;
+    bool found = false;
+    for (uint64_t blk = 0; blk < kPolarBlocks && !found; ++blk) {
         const U4 w = philox(idx, blk, tag, 0, seed, sid);
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
-            const double v1 = __dsub_rn(__dmul_rn(2.0, unit53(w.w[2 * p])), 1.0);
-            const double v2 = __dsub_rn(__dmul_rn(2.0, unit53(w.w[2 * p + 1])), 1.0);
-            const double s = __dadd_rn(__dmul_rn(v1, v1), __dmul_rn(v2, v2));
-            if (s > 0.0 && s < 1.0) {
-                double t = ln_series(s);
-                t = __dmul_rn(-2.0, t);
-                t = __ddiv_rn(t, s);
-                t = __dsqrt_rn(t);
-                return __dmul_rn(v1, t);
+            const double a = __dsub_rn(__dmul_rn(2.0, unit53(w.w[2 * p])), 1.0);
+            const double b = __dsub_rn(__dmul_rn(2.0, unit53(w.w[2 * p + 1])), 1.0);
+            const double q = __dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b));
+            if (!found && q > 0.0 && q < 1.0) {
+                v1 = a;
+                s = q;
+                found = true;
             }
         }
     }
-    return 0.0;
+    if (!found) return 0.0;
+    double t = ln_series(s);
+    t = __dmul_rn(-2.0, t);
+    t = __ddiv_rn(t, s);
+    t = __dsqrt_rn(t);
+    return __dmul_rn(v1, t);
 }
 
 // The same polar method in IEEE single precision (multipliers on the FP32
@@ -87,34 +103,43 @@ __device__ float ln_series_f32(float s) {
     if (m > 1.41421354f) { m = __fmul_rn(m, 0.5f); e += 1; }
     const float f = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
     const float f2 = __fmul_rn(f, f);
+    // 1/(2k+1), k = 0..5, correctly rounded to single precision
+    constexpr float kInvOddF[6] = {0x1.000000p+0f, 0x1.555556p-2f, 0x1.99999ap-3f,
+                                   0x1.24924ap-3f, 0x1.c71c72p-4f, 0x1.745d18p-4f};
     const int K = 5;
-    float p = __fdiv_rn(1.0f, (float)(2 * K + 1));
-    for (int k = K - 1; k >= 0; --k) p = __fadd_rn(__fmul_rn(p, f2), __fdiv_rn(1.0f, (float)(2 * k + 1)));
+    float p = kInvOddF[K];
+#pragma unroll
+    for (int k = K - 1; k >= 0; --k) p = __fadd_rn(__fmul_rn(p, f2), kInvOddF[k]);
     const float lm = __fmul_rn(__fmul_rn(2.0f, f), p);
     const float el = __fmul_rn((float)e, 0.693147182f);
     return __fadd_rn(el, lm);
 }
 
 __device__ float polar_normal_f32(uint64_t seed, uint64_t sid, uint64_t tag, uint64_t idx) {
-    for (uint64_t blk = 0; blk < kPolarBlocks; ++blk) {
+    float v1 = 0.0f, s = 0.0f;
+    bool found = false;
+    for (uint64_t blk = 0; blk < kPolarBlocks && !found; ++blk) {
         const U4 w = philox(idx, blk, tag, 0, seed, sid);
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
             const float u1 = __fmul_rn((float)(uint32_t)(w.w[2 * p] >> 40), 5.96046448e-8f /* 2^-24 */);
             const float u2 = __fmul_rn((float)(uint32_t)(w.w[2 * p + 1] >> 40), 5.96046448e-8f);
-            const float v1 = __fsub_rn(__fmul_rn(2.0f, u1), 1.0f);
-            const float v2 = __fsub_rn(__fmul_rn(2.0f, u2), 1.0f);
-            const float s = __fadd_rn(__fmul_rn(v1, v1), __fmul_rn(v2, v2));
-            if (s > 0.0f && s < 1.0f) {
-                float t = ln_series_f32(s);
-                t = __fmul_rn(-2.0f, t);
-                t = __fdiv_rn(t, s);
-                t = __fsqrt_rn(t);
-                return __fmul_rn(v1, t);
+            const float a = __fsub_rn(__fmul_rn(2.0f, u1), 1.0f);
+            const float b = __fsub_rn(__fmul_rn(2.0f, u2), 1.0f);
+            const float q = __fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b));
+            if (!found && q > 0.0f && q < 1.0f) {
+                v1 = a;
+                s = q;
+                found = true;
             }
         }
     }
-    return 0.0f;
+    if (!found) return 0.0f;
+    float t = ln_series_f32(s);
+    t = __fmul_rn(-2.0f, t);
+    t = __fdiv_rn(t, s);
+    t = __fsqrt_rn(t);
+    return __fmul_rn(v1, t);
 }
 
 // Round a finite double to the nearest BF16 value (ties to even) by clearing

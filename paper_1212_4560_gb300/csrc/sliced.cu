@@ -28,17 +28,22 @@ __device__ __forceinline__ int scale_exp(double amax) {
     return e;
 }
 
-// digit t (1-based) of q in (-1, 1): d_t = rint(r_{t-1} 2^7), r_t = r_{t-1} 2^7 - d_t (all exact in FP64)
+// Digits of q = x 2^-e in (-1, 1): X = round(q 2^(7 ND)) (an integer below
+// 2^(7 ND) in magnitude, converted exactly), then its balanced base-128
+// digits from the bottom: d_t = ((X + 64) mod 128) - 64 in [-64, 63],
+// X <- (X - d_t) / 128; what is left is d_1 in [-128, 128].  Integer
+// arithmetic except for one scaling and one conversion (the FP64 units of
+// GB300 are scarce); the dropped remainder is below 2^-(7 ND + 1).
 template <int ND>
-__device__ __forceinline__ void digits(double q, float (&d)[ND]) {
-    double r = q;
+__device__ __forceinline__ void digits(double x, int e, float (&d)[ND]) {
+    long long X = __double2ll_rn(ldexp(x, 7 * ND - e));
 #pragma unroll
-    for (int t = 0; t < ND; ++t) {
-        const double s = r * 128.0;
-        const double dt = rint(s);
-        d[t] = (float)dt;
-        r = s - dt;
+    for (int t = ND - 1; t >= 1; --t) {
+        const long long lo = ((X + 64) & 127) - 64;
+        d[t] = (float)lo;
+        X = (X - lo) >> 7;
     }
+    d[0] = (float)X;
 }
 
 // Writes the ND digit slices of one operand entry (a small integer each: exact in BF16).
@@ -65,7 +70,7 @@ __global__ void k_slice_rows(const double *src, int64_t lds, int64_t m, int64_t 
         __nv_bfloat16 *row = dst + i * ldq;
         for (int64_t k = lane; k < kpad; k += 32) {
             float d[ND] = {};
-            if (k < K) digits<ND>(ldexp(a[k], -e), d);
+            if (k < K) digits<ND>(a[k], e, d);
             put<ND>(row, kpad, k, d);
         }
     }
@@ -97,7 +102,7 @@ __global__ void k_slice_cols_T(const double *src, int64_t lds, int64_t K, int64_
         const int64_t j = j0 + r, k = k0 + tx;
         if (j < n && k < kpad) {
             float d[ND] = {};
-            if (k < K) digits<ND>(ldexp(tile[tx][r], -exps[j]), d);
+            if (k < K) digits<ND>(tile[tx][r], exps[j], d);
             put<ND>(dst + j * ldq, kpad, k, d);
         }
     }

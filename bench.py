@@ -41,7 +41,7 @@ sys.path.insert(0, ROOT)
 METRIC = "solves/s & TFLOP/s (2n³/3), BF16+IR vs FP64 GENP, same GB300, bwd err ≤1e-14"
 KINDS = {"gaussian": 0, "circulant": 1, "sparse": 2}
 PRECS = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 4, "sliced": 5}
-GRID_OF = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 2, "sliced": 0}
+GRID_OF = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 2, "sliced": 1}   # sliced: G drawn on the FP32 grid
 F64_FACTORS = ("fp64", "sliced")
 
 
@@ -486,6 +486,7 @@ def run_ours(a):
             "phases_ms": phase_ms, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "gpu_launches_per_step": launches / a.steps,
             "bwd_err": info.bwd_err[-1] if info.bwd_err else None, "refine_iters": info.refine_iters,
+            "krylov_steps": info.krylov_steps,
             "breakdown_step": info.breakdown_step, "growth": info.growth, "status": info.status,
             "warmup_bwd_err": info_w.bwd_err[-1] if info_w.bwd_err else None}
     if fp64 is not None:

@@ -124,6 +124,8 @@ typedef struct {
     double growth;               /* max|U| / max|C|                                      */
     double bwd_err[GENP_MAX_REFINE + 1]; /* backward error before refinement and after  */
                                  /* each step of the last genp_refine (see genp_refine) */
+    int32_t krylov_steps;        /* GMRES steps (Krylov vectors) of the last genp_refine */
+    int32_t reserved;
 } genp_info;
 
 /* Library version string, e.g. "genp 0.1 sm_103a". */

@@ -29,7 +29,7 @@ _dbl = ctypes.c_double
 class GenpInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("refine_iters", ctypes.c_int32), ("breakdown_step", ctypes.c_int64),
                 ("min_abs_pivot", _dbl), ("max_abs_pivot", _dbl), ("growth", _dbl),
-                ("bwd_err", _dbl * (MAX_REFINE + 1))]
+                ("bwd_err", _dbl * (MAX_REFINE + 1)), ("krylov_steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes); every entry point of include/genp.h

@@ -156,6 +156,7 @@ class Info:
     max_abs_pivot: float
     growth: float
     bwd_err: list
+    krylov_steps: int = 0
 
 
 def info_fetch(F: Factors, stream=None) -> Info:
@@ -164,7 +165,7 @@ def info_fetch(F: Factors, stream=None) -> Info:
     check(_lib.load().genp_info_fetch(F.handle, ctypes.byref(out), _stream(stream)), "genp_info_fetch")
     errs = [e for e in out.bwd_err[: out.refine_iters + 1] if e >= 0]
     return Info(out.status, out.refine_iters, out.breakdown_step, out.min_abs_pivot, out.max_abs_pivot, out.growth,
-                errs)
+                errs, out.krylov_steps)
 
 
 def solve_system(A: torch.Tensor, B: torch.Tensor, kind: int = GAUSSIAN, seed: int = 0, prec: int = FP64,
@@ -173,7 +174,9 @@ def solve_system(A: torch.Tensor, B: torch.Tensor, kind: int = GAUSSIAN, seed: i
     FP64 refinement (method 0 classic, 1 GMRES-IR).  Returns (X, info, G, F)."""
     n = A.size(0)
     f64 = prec in (FP64, BF16_SLICED)
-    grid = FP64 if f64 else (BF16 if prec in (BF16, BF16X3) else FP32)
+    # FP32-grid draws for every non-FP64 factorization (the sliced path reads
+    # them as exact FP64 values)
+    grid = FP64 if prec == FP64 else (BF16 if prec in (BF16, BF16X3) else FP32)
     G = make_multiplier(kind, n, seed, value_grid=grid, stream=stream)
     C = torch.empty((n, n), dtype=torch.float64 if f64 else torch.float32, device=A.device)
     A64 = A if A.dtype == torch.float64 else A.double()

@@ -598,6 +598,7 @@ genp_status genp_info_fetch(const genp_factors *F, genp_info *out, void *cuda_st
     const double cmax = asd(h.max_abs_c);
     out->growth = cmax > 0 ? asd(h.max_abs_u) / cmax : 0.0;
     out->refine_iters = h.refine_iters;
+    out->krylov_steps = h.krylov_steps;
     for (int i = 0; i <= GENP_MAX_REFINE; ++i) out->bwd_err[i] = h.bwd_err[i];
     out->status = out->breakdown_step >= 0 ? GENP_ERR_BREAKDOWN : h.refine_status;
     return GENP_OK;

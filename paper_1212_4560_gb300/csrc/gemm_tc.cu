@@ -311,7 +311,7 @@ bool make_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t K, int64_
 // arithmetic, and the last group is added in double-float:
 //   D[i][j] += alpha 2^{e_i + f_j - 7 ND} (sum_{g<=ND} 2^{7(ND-g)} P_g + 2^-7 P_{ND+1})
 // ---------------------------------------------------------------------------
-constexpr int SBN = 64, A_SLOTS = 4;
+constexpr int SBN = 64, A_SLOTS = 7;
 constexpr uint32_t SA_BYTES = BM * BK * 2;      // one A digit slice of a k-tile
 constexpr uint32_t SBD_BYTES = SBN * BK * 2;    // one B digit slice of a k-tile
 constexpr uint32_t S_TMEM = 512;
@@ -396,6 +396,16 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     fence_after();
     const uint32_t tmem = ctl->tmem;
 
+    // pull this CTA's rows of D into L2 now, for the epilogue after the MMAs
+    {
+        const int row = m0 + (int)threadIdx.x;   // one row per thread
+        if (row < m && n0 < n) {
+            const char *rp = reinterpret_cast<const char *>(D + (int64_t)row * ldd + n0);
+            const int bytes = (n - n0 < SBN ? n - n0 : SBN) * (int)sizeof(dfloat);
+            for (int b = 0; b < bytes; b += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(rp + b));
+        }
+    }
+
     if (warp == 0 && lane == 0) {
         int ai = 0;
         bool ok = true;
@@ -474,29 +484,34 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
         for (int h = 0; h < SBN / 32; ++h) {
-            long long S[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) S[j] = 0;
+            dfloat S[32];
             uint32_t q[32];
-            // exact groups, largest weight first: S = S 2^7 + P_g
+            // Horner over the groups, largest weight first: S = 2^7 S + P_g.  The
+            // P_g are integers below 2^24 and the partial sums integers below
+            // 2^60: exact as double-float up to 48 bits, all on the FP32 pipe.
+            tmem_ld32(lane_addr + (uint32_t)(32 * h), q);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) S[j] = dfloat(__uint_as_float(q[j]));
 #pragma unroll 1
-            for (int g = 0; g < ND - 1; ++g) {
+            for (int g = 1; g < ND - 1; ++g) {
                 tmem_ld32(lane_addr + (uint32_t)(SBN * g + 32 * h), q);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) S[j] = S[j] * 128 + (long long)__float2int_rn(__uint_as_float(q[j]));
+                for (int j = 0; j < 32; ++j) {
+                    S[j].hi *= 128.0f;
+                    S[j].lo *= 128.0f;
+                    S[j] = S[j] + dfloat(__uint_as_float(q[j]));
+                }
             }
-            tmem_ld32(lane_addr + (uint32_t)(SBN * (ND - 1) + 32 * h), q);   // the last group
+            // the last group carries 2^-7 against the others
+            tmem_ld32(lane_addr + (uint32_t)(SBN * (ND - 1) + 32 * h), q);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) S[j] = S[j] + dfloat(__uint_as_float(q[j]) * 0.0078125f);
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-                const float hi = __ll2float_rn(S[j]);
-                const float lo = __ll2float_rn(S[j] - __float2ll_rn(hi));
-                dfloat v;
-                v.hi = hi;
-                v.lo = lo;
-                v = v + dfloat(__uint_as_float(q[j]) * 0.0078125f);
                 const float cs = ctl->cs[32 * h + j];   // two exact power-of-two scalings
-                v.hi = (v.hi * rs) * cs;
-                v.lo = (v.lo * rs) * cs;
+                dfloat v;
+                v.hi = (S[j].hi * rs) * cs;
+                v.lo = (S[j].lo * rs) * cs;
                 tile[r * kDfLd + 32 * h + j] = v;
             }
         }

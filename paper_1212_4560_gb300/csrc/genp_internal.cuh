@@ -23,7 +23,7 @@ struct DevStatus {
     int refine_iters;
     int refine_done;                     // set on the device when refinement stops
     int refine_status;                   // GENP_OK or GENP_ERR_NOCONV
-    int pad0;
+    int krylov_steps;                    // GMRES steps of the last refinement (method 1)
     double anorm;                        // ||A||_inf of the last refinement
     double bwd_err[GENP_MAX_REFINE + 1];
 };

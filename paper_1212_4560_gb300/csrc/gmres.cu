@@ -139,9 +139,10 @@ __global__ void k_gm_start(GmState *st, int nr, const int *skip) {
 }
 
 // Arnoldi step k: h_{k+1,k} = ||w||; rotate column k of H; test convergence.
-__global__ void k_gm_arnoldi(GmState *st, int nr, int k, const int *skip) {
+__global__ void k_gm_arnoldi(GmState *st, DevStatus *ds, int nr, int k, const int *skip) {
     if (*skip) return;
     const int c = threadIdx.x;
+    if (c == 0) ds->krylov_steps += 1;
     if (c < nr && !st->conv[c]) {
         const double h = sqrt(st->hcol[0][c]);
         st->H[k + 1][k][c] = h;
@@ -292,7 +293,7 @@ cudaError_t refine_gmres(genp_factors *F, const genp_multiplier *G, const double
             }
             if (e == cudaSuccess) e = dots(st, partial, W, 0, 1, W, n, nr, -1, 0, inner, s);
             note_launch();
-            k_gm_arnoldi<<<1, 32, 0, s>>>(st, nr, k, inner);
+            k_gm_arnoldi<<<1, 32, 0, s>>>(st, F->st, nr, k, inner);
             if (k + 1 < kM) {
                 note_launch();
                 k_gm_scale<<<vb, 256, 0, s>>>(W, V + (int64_t)(k + 1) * vstride, n, nr, st, inner);

@@ -46,6 +46,7 @@ __global__ void k_rownorm_inf(const double *A, int64_t lda, int64_t n, unsigned 
 
 __global__ void k_refine_reset(DevStatus *st, DevNorms *nm, unsigned long long *anorm_bits) {
     st->refine_iters = 0;
+    st->krylov_steps = 0;
     st->refine_done = 0;
     st->refine_status = GENP_OK;
     for (int i = 0; i <= GENP_MAX_REFINE; ++i) st->bwd_err[i] = -1.0;
@@ -153,19 +154,25 @@ __global__ void k_outer(const double *Lam, int64_t ldl, const double *X, int64_t
 }
 
 // ---------------------------------------------------------------------------
-// Triangular solves op(T) Y = Y in one persistent launch (column-oriented,
-// streaming).  T is cut into 64 x 64 tiles; step p solves the diagonal tile
-// of block j(p) (j = p forward, nblk-1-p backward) with its precomputed
-// inverse and then subtracts
-// op(T)[i][j] y_j from every block i still to come.  Those updates are split
-// into work items of kSeg tiles so that one column's work spreads over
-// several SMs.  Items are taken from an atomic ticket in (step, segment)
-// order; an item only waits for items with smaller tickets (the
-// contributions to its diagonal block, or that block's solution), which are
-// running or done, so the launch cannot deadlock.  Updates go into Y with
-// FP64 (or FP32) atomics; a per-block counter says when all of them have
-// landed.  Every wait is bounded: on timeout the kernel sets a device flag
-// (read by genp_device_check) and goes on.
+// Triangular solves op(T) Y = Y in one persistent launch.  T is cut into
+// 64 x 64 tiles and the diagonal blocks are taken one after the other (block
+// j(q) at step q: j = q forward, nblk-1-q backward).  The CTA that draws
+// ticket 0 walks the diagonal: for each block it applies the precomputed
+// inverse of the diagonal tile plus one refinement step, publishes y_j, and
+// subtracts op(T)[next][j] y_j from the next block itself, so the chain from
+// one block to the next never waits on another CTA.  Every other ticket is a
+// work item that sums op(T)[i][j(p)] y_j(p) over up to kSeg earlier steps p
+// for one block i = j(q) two or more steps ahead, in registers, and
+// subtracts the sum from Y_i with one set of FP64 (or FP32) atomics; a
+// per-block counter, raised by the number of steps summed, tells the walker
+// when all of block i's contributions have landed.  Items are handed out in
+// the order the walker needs them (by target step q, then by p), each waits
+// only for the y_j(p) it multiplies (all published before the walker reaches
+// step q - 1), and the walker waits only for items of its current step,
+// which hold smaller tickets than anything still waiting, so the launch
+// cannot deadlock (it needs two or more CTAs).  Every wait is bounded: on
+// timeout the kernel sets a device flag (read by genp_device_check) and goes
+// on.
 // ---------------------------------------------------------------------------
 constexpr int TB = 64;          // tile
 constexpr int kSeg = 16;        // tiles per work item
@@ -186,25 +193,46 @@ __device__ bool wait_geq(const int *p, int target) {
     const long long t0 = clock64();
     while (ld_acquire(p) < target) {
         if (clock64() - t0 > kSpinTicks) return false;
-        __nanosleep(100);
+        __nanosleep(64);
     }
     return true;
 }
-__device__ __forceinline__ int nseg(int p, int nblk) {
-    const int c = nblk - 1 - p;
-    return c <= 0 ? 1 : (c + kSeg - 1) / kSeg;
-}
+// work items of target step q >= 2: the q - 1 earlier steps p <= q - 2, kSeg per item
+__device__ __forceinline__ int nchunks(int q) { return q < 2 ? 0 : (q - 1 + kSeg - 1) / kSeg; }
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ float ldcg(const float *p) { return __ldcg(p); }
 
 template <typename T, int NR>
 struct TrsvSmem {
-    T S[TB][TB + 1];    // current tile of op(T), or op(T_jj)^{-1}
-    T D[TB][TB + 1];    // op(T_jj), its triangle only
+    T S[TB][TB + 1];    // op(T_jj)^{-1} (walker) or the current tile (items)
+    T D[TB][TB + 1];    // op(T_jj), its triangle only (walker)
+    T O[TB][TB + 1];    // op(T)[next][j] (walker)
     T y[TB][NR];        // y_j
     T acc[TB][NR];      // right-hand side of the diagonal block, then its residual
+    T carry[TB][NR];    // the walker's own contribution to the next block
     int item[2];
 };
+
+// part[c] += sum over this thread's quarter of k of M[r][k] V[k][c] (thread = 4 r + quarter)
+template <typename T, int NR>
+__device__ __forceinline__ void tile_gemv_acc(const T (*M)[TB + 1], const T (*V)[NR], int r, int qq, T (&part)[NR]) {
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+        const int k = qq * 16 + kk;
+        const T a = M[r][k];
+#pragma unroll
+        for (int c = 0; c < NR; ++c) part[c] = fma(a, V[k][c], part[c]);
+    }
+}
+// sum of the 4 quarter threads of a row
+template <typename T, int NR>
+__device__ __forceinline__ void quad_sum(T (&part)[NR]) {
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+        part[c] += __shfl_xor_sync(0xffffffffu, part[c], 1);
+        part[c] += __shfl_xor_sync(0xffffffffu, part[c], 2);
+    }
+}
 
 // part[c] = sum over this thread's quarter of k of M[r][k] V[k][c], summed over
 // the 4 threads of row r (thread = 4 r + quarter)
@@ -242,11 +270,12 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     TrsvSmem<T, NR> &sm = *reinterpret_cast<TrsvSmem<T, NR> *>(smraw);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int nblk = (n + TB - 1) / TB;
     const bool forward = (mode == 0 || mode == 2);
+    const bool unit = (mode == 0 || mode == 3);
     int *ticket = sync, *cnt = sync + 2, *ready = sync + 2 + nblk;
-    int p = 0, t_base = 0;                 // first ticket of step p
+    const int r = tid >> 2, qq = tid & 3;   // tile_gemv roles
     // per-thread share of a tile load: 16 elements; non-transposed modes walk
     // rows (k fastest), transposed modes walk columns (r fastest)
     auto load_tile = [&](int i, int j, T (&v)[16]) {
@@ -258,119 +287,138 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
                                : tile_elem<TS, T>(C, ldc, n, mode, i, j, b, a);
         }
     };
-    auto store_tile = [&](const T (&v)[16]) {
+    auto store_tile = [&](T (*M)[TB + 1], const T (&v)[16]) {
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
             const int idx = tid + e * kTrsvThreads;
             const int a = idx >> 6, b = idx & 63;
-            if (mode <= 1) sm.S[a][b] = v[e];
-            else sm.S[b][a] = v[e];
+            if (mode <= 1) M[a][b] = v[e];
+            else M[b][a] = v[e];
+        }
+    };
+    // the diagonal tile's triangle, unit diagonal where op(T) has one
+    auto store_diag = [&](const T (&v)[16]) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int idx = tid + e * kTrsvThreads;
+            const int a = idx >> 6, b = idx & 63;
+            const int rr = mode <= 1 ? a : b, kk = mode <= 1 ? b : a;
+            T val = v[e];
+            if (rr == kk) val = unit ? T(1) : val;
+            else if (forward ? kk > rr : kk < rr) val = T(0);
+            sm.D[rr][kk] = val;
         }
     };
     // op(T_jj)^{-1} from the inverted diagonal blocks (Dinv: [L, U][block][64][64])
     auto load_inv = [&](int j, T (&v)[16]) {
-        const TS *X = Dinv + ((int64_t)((mode == 0 || mode == 3) ? 0 : 1) * nblk + j) * TB * TB;
+        const TS *X = Dinv + ((int64_t)(unit ? 0 : 1) * nblk + j) * TB * TB;
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const int idx = tid + e * kTrsvThreads;
-            v[e] = (T)__ldg(X + idx);   // stored as S[a][b] (non-transposed) or S[b][a] by store_tile
-        }
+        for (int e = 0; e < 16; ++e) v[e] = (T)__ldg(X + tid + e * kTrsvThreads);
     };
+    auto block_of = [&](int p) { return forward ? p : nblk - 1 - p; };
+
+    int q_it = 2, t_base = 1;              // first ticket of target step q_it's items
     for (;;) {
         __syncthreads();
         if (tid == 0) sm.item[0] = atomicAdd(ticket, 1);
         __syncthreads();
         const int t = sm.item[0];
-        while (p < nblk && t >= t_base + nseg(p, nblk)) {
-            t_base += nseg(p, nblk);
-            ++p;
-        }
-        if (p >= nblk) break;
-        const int s = t - t_base;
-        const int j = forward ? p : nblk - 1 - p;
-        const int bj = min(TB, n - j * TB);
-        T v[16];
-        if (s == 0) {
-            // the diagonal block: y_j = op(T_jj)^{-1} b_j with b_j = Y_j minus the
-            // contributions of the p earlier steps, then one step of refinement
-            // y_j += op(T_jj)^{-1} (b_j - op(T_jj) y_j), which brings the explicit
-            // inverse's error (kappa(T_jj) u) back to the level of substitution
-            load_tile(j, j, v);
-            __syncthreads();
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                const int idx = tid + e * kTrsvThreads;
-                const int a = idx >> 6, b = idx & 63;
-                const int r = mode <= 1 ? a : b, k = mode <= 1 ? b : a;
-                const bool lower = forward;
-                T val = v[e];
-                if (r == k) val = (mode == 0 || mode == 3) ? T(1) : val;
-                else if (lower ? k > r : k < r) val = T(0);
-                sm.D[r][k] = val;
-            }
-            load_inv(j, v);
-            if (tid == 0 && !wait_geq(cnt + j, p)) atomicExch(&g_solve_timeout, 1);
-            __syncthreads();
-            store_tile(v);
-            for (int idx = tid; idx < TB * NR; idx += kTrsvThreads) {
-                const int r = idx / NR, c = idx % NR;
-                sm.acc[r][c] = (r < bj && c < nr) ? ldcg(Y + ((int64_t)j * TB + r) * ldy + c) : T(0);
-            }
-            __syncthreads();
-            const int r = tid >> 2, qq = tid & 3;
-            T part[NR];
-            tile_gemv<T, NR>(sm.S, sm.acc, r, qq, part);          // y0 = X b
-#pragma unroll
-            for (int c = 0; c < NR; ++c)
-                if ((c & 3) == qq) sm.y[r][c] = part[c];
-            __syncthreads();
-            tile_gemv<T, NR>(sm.D, sm.y, r, qq, part);            // b - T y0
-#pragma unroll
-            for (int c = 0; c < NR; ++c)
-                if ((c & 3) == qq) sm.acc[r][c] -= part[c];
-            __syncthreads();
-            tile_gemv<T, NR>(sm.S, sm.acc, r, qq, part);          // y = y0 + X (b - T y0)
-#pragma unroll
-            for (int c = 0; c < NR; ++c)
-                if ((c & 3) == qq) {
-                    const T yv = sm.y[r][c] + part[c];
-                    sm.y[r][c] = yv;
-                    if (r < bj && c < nr) Y[((int64_t)j * TB + r) * ldy + c] = yv;
+        if (t == 0) {
+            // ---- the walker: every diagonal block in order ----
+            T vD[16], vX[16], vO[16];
+            load_tile(block_of(0), block_of(0), vD);
+            load_inv(block_of(0), vX);
+            for (int q = 0; q < nblk; ++q) {
+                const int j = block_of(q);
+                const int bj = min(TB, n - j * TB);
+                __syncthreads();
+                store_diag(vD);
+                store_tile(sm.S, vX);
+                // wait for the items of steps up to q - 2, then b_j = Y_j - own carry
+                if (tid == 0 && q >= 2 && !wait_geq(cnt + j, q - 1)) atomicExch(&g_solve_timeout, 1);
+                __syncthreads();
+                if (q + 1 < nblk) {           // next step's tiles, in flight during this one
+                    load_tile(block_of(q + 1), j, vO);
+                    load_tile(block_of(q + 1), block_of(q + 1), vD);
+                    load_inv(block_of(q + 1), vX);
                 }
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) st_release(ready + j, 1);
-        } else {
-            if (tid == 0 && !wait_geq(ready + j, 1)) atomicExch(&g_solve_timeout, 1);
-            __syncthreads();
-            for (int idx = tid; idx < TB * NR; idx += kTrsvThreads) {
-                const int r = idx / NR, c = idx % NR;
-                sm.y[r][c] = (r < bj && c < nr) ? ldcg(Y + ((int64_t)j * TB + r) * ldy + c) : T(0);
-            }
-        }
-        // this item's blocks i, nearest to the diagonal first
-        const int left = nblk - 1 - p;          // blocks still to come
-        const int first = s * kSeg, last = min(left, first + kSeg);
-        if (first < last) load_tile(forward ? j + 1 + first : j - 1 - first, j, v);
-        const int r = tid >> 2, qq = tid & 3;
-        for (int q = first; q < last; ++q) {
-            const int i = forward ? j + 1 + q : j - 1 - q;
-            __syncthreads();
-            store_tile(v);
-            __syncthreads();
-            if (q + 1 < last) load_tile(forward ? i + 1 : i - 1, j, v);
-            T part[NR];
-            tile_gemv<T, NR>(sm.S, sm.y, r, qq, part);
-            const int64_t row = (int64_t)i * TB + r;
-            if (row < n) {
+                for (int idx = tid; idx < TB * NR; idx += kTrsvThreads) {
+                    const int rr = idx / NR, c = idx % NR;
+                    const T b = (rr < bj && c < nr) ? ldcg(Y + ((int64_t)j * TB + rr) * ldy + c) : T(0);
+                    sm.acc[rr][c] = q > 0 ? b - sm.carry[rr][c] : b;
+                }
+                __syncthreads();
+                // y = X b;  y += X (b - T y)  (one refinement step of the explicit inverse)
+                T part[NR];
+                tile_gemv<T, NR>(sm.S, sm.acc, r, qq, part);
 #pragma unroll
                 for (int c = 0; c < NR; ++c)
-                    if ((c & 3) == qq && c < nr) atomicAdd(Y + row * ldy + c, -part[c]);
+                    if ((c & 3) == qq) sm.y[r][c] = part[c];
+                __syncthreads();
+                tile_gemv<T, NR>(sm.D, sm.y, r, qq, part);
+#pragma unroll
+                for (int c = 0; c < NR; ++c)
+                    if ((c & 3) == qq) sm.acc[r][c] -= part[c];
+                __syncthreads();
+                tile_gemv<T, NR>(sm.S, sm.acc, r, qq, part);
+#pragma unroll
+                for (int c = 0; c < NR; ++c)
+                    if ((c & 3) == qq) {
+                        const T yv = sm.y[r][c] + part[c];
+                        sm.y[r][c] = yv;
+                        if (r < bj && c < nr) Y[((int64_t)j * TB + r) * ldy + c] = yv;
+                    }
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) st_release(ready + j, 1);
+                if (q + 1 < nblk) {           // own contribution to the next block
+                    store_tile(sm.O, vO);
+                    __syncthreads();
+                    tile_gemv<T, NR>(sm.O, sm.y, r, qq, part);
+#pragma unroll
+                    for (int c = 0; c < NR; ++c)
+                        if ((c & 3) == qq) sm.carry[r][c] = part[c];
+                }
             }
-            __threadfence();
-            __syncthreads();
-            if (tid == 0) atomicAdd(cnt + i, 1);
+            continue;
         }
+        // ---- an update item: target step q, earlier steps p0 .. p1 ----
+        while (q_it < nblk && t >= t_base + nchunks(q_it)) {
+            t_base += nchunks(q_it);
+            ++q_it;
+        }
+        if (q_it >= nblk) break;
+        const int i = block_of(q_it);
+        const int p0 = (t - t_base) * kSeg, p1 = min(q_it - 2, p0 + kSeg - 1);
+        T v[16];
+        load_tile(i, block_of(p0), v);
+        T part[NR];
+#pragma unroll
+        for (int c = 0; c < NR; ++c) part[c] = T(0);
+        for (int pp = p0; pp <= p1; ++pp) {
+            const int j = block_of(pp);
+            const int bj = min(TB, n - j * TB);
+            if (tid == 0 && !wait_geq(ready + j, 1)) atomicExch(&g_solve_timeout, 1);
+            __syncthreads();
+            store_tile(sm.S, v);
+            for (int idx = tid; idx < TB * NR; idx += kTrsvThreads) {
+                const int rr = idx / NR, c = idx % NR;
+                sm.y[rr][c] = (rr < bj && c < nr) ? ldcg(Y + ((int64_t)j * TB + rr) * ldy + c) : T(0);
+            }
+            __syncthreads();
+            if (pp < p1) load_tile(i, block_of(pp + 1), v);
+            tile_gemv_acc<T, NR>(sm.S, sm.y, r, qq, part);
+        }
+        quad_sum<T, NR>(part);
+        const int64_t row = (int64_t)i * TB + r;
+        if (row < n) {
+#pragma unroll
+            for (int c = 0; c < NR; ++c)
+                if ((c & 3) == qq && c < nr) atomicAdd(Y + row * ldy + c, -part[c]);
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) atomicAdd(cnt + i, p1 - p0 + 1);
     }
 }
 

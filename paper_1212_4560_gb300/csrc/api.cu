@@ -439,7 +439,7 @@ genp_status genp_factor(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t
     if (st == GENP_OK && prec == GENP_BF16_SLICED) {
         F->nd = sliced_digits();
         F->tc_ldq = (int64_t)F->nd * sliced_kpad(2 * nb);   // outer steps of 2 nb
-        F->ldw = n;
+        F->ldw = round8(n);   // 16-byte aligned rows for the vectorized epilogue
         st = dalloc(&F->tcA, (size_t)n * F->tc_ldq);
         if (st == GENP_OK) st = dalloc(&F->tcB, (size_t)n * F->tc_ldq);
         if (st == GENP_OK) st = dalloc(reinterpret_cast<double **>(&F->W), (size_t)n * F->ldw);

@@ -302,31 +302,42 @@ bool make_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t K, int64_
 // Sliced (FP64-class) product (layout in sliced.cuh).  Digit group g = t + u
 // accumulates in TMEM columns [64 (g-2), 64 (g-1)), so one MMA of A's digit t
 // against B's digits 1 .. ND+1-t laid side by side along N (N = 64 (ND+1-t),
-// cut at 256) lands every product in its group's columns.  One CTA per SM
-// computes a 128 x 64 tile: B's ND digit slices of a k-tile are staged once
-// (two stages), A's digit slices stream through a four-slot ring, and the
-// tensor pipe runs MMAs of N up to 256 instead of one narrow MMA per digit
-// pair.  The epilogue rebuilds each entry from its groups: the groups below
-// the last are exact integers (K <= 512), summed exactly in 64-bit integer
-// arithmetic, and the last group is added in double-float:
+// cut at 256) lands every product in its group's columns.
+//
+// Persistent and warp-specialized: one CTA per SM walks 128 x 64 tiles.
+// Warp 4 issues TMA (B's ND digit slices of a k-tile in one of two stages,
+// A's digit slices through a four-slot ring), warp 5 issues tcgen05.mma,
+// warps 0-3 (TMEM lanes 0-127) run the epilogue.  The epilogue reads the
+// group accumulators and hands TMEM back (tempty) before it scales the sums
+// and adds them into D (half a tile at a time through shared memory, rows
+// coalesced), so that work and the next tile's first TMA loads overlap the
+// next tile's MMAs.  The groups below the last are integers
+// below 2^24 (K <= 512), recombined by a double-float Horner scheme on the
+// FP32 pipe; the last group is added with its 2^-7:
 //   D[i][j] += alpha 2^{e_i + f_j - 7 ND} (sum_{g<=ND} 2^{7(ND-g)} P_g + 2^-7 P_{ND+1})
+// Every wait is bounded (then the CTA aborts, drains its copies, frees TMEM).
 // ---------------------------------------------------------------------------
-constexpr int SBN = 64, A_SLOTS = 7;
+constexpr int SBN = 64, A_SLOTS = 4;
 constexpr uint32_t SA_BYTES = BM * BK * 2;      // one A digit slice of a k-tile
 constexpr uint32_t SBD_BYTES = SBN * BK * 2;    // one B digit slice of a k-tile
 constexpr uint32_t S_TMEM = 512;
+constexpr int kSlicedThreads = 192;             // 4 epilogue warps, producer, MMA
+constexpr int kHalfLd = 33;                     // epilogue staging: 128 rows x 32 dfloat, padded
+constexpr uint32_t STAGE_BYTES = BM * kHalfLd * 8;
 struct SCtl {
     unsigned long long afull[A_SLOTS];
     unsigned long long aempty[A_SLOTS];
     unsigned long long bfull[2];
     unsigned long long bempty[2];
-    unsigned long long accum;
+    unsigned long long tfull;     // a tile's accumulators are complete
+    unsigned long long tempty;    // the epilogue has read them (4 arrivals)
+    unsigned long long drain;     // outstanding MMAs, on the abort path
     uint32_t tmem;
     int abort;
     int issued_a, issued_b;
-    float cs[SBN];            // 2^{f_j} of the tile's columns
+    int epi_go;                   // the epilogue warps' common decision to go on
+    float cs[SBN];                // alpha 2^{f_j} of the current tile's columns
 };
-constexpr int kDfLd = SBN + 1;
 
 __device__ __forceinline__ void mma_n(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
@@ -339,20 +350,35 @@ __device__ __forceinline__ void mma_n(uint32_t d, uint64_t a, uint64_t b, uint32
 __host__ __device__ constexpr uint32_t idesc_n(int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
+// Bounded wait with a sleep between tries: for warps that wait a long time
+// while others on the same scheduler issue TMA and MMA instructions.
+__device__ bool mbar_wait_sleep(unsigned long long *b, uint32_t parity, volatile int *abort) {
+    const long long t0 = clock64();
+    while (!mbar_try(b, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > kTimeout) return false;
+        __nanosleep(256);
+    }
+    return true;
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(b)) : "memory");
+}
+// barrier among the 128 epilogue threads only
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 template <int ND>
 struct SlicedCfg {
     static constexpr uint32_t kBStage = ND * SBD_BYTES;
-    static constexpr size_t kSmem = 1024 + A_SLOTS * SA_BYTES + 2 * kBStage + sizeof(SCtl);
+    static constexpr size_t kSmem = 1024 + A_SLOTS * SA_BYTES + 2 * kBStage + STAGE_BYTES + sizeof(SCtl);
     static_assert(64 * ND <= (int)S_TMEM, "group accumulators fit in TMEM");
-    static_assert(BM * kDfLd * 8 <= A_SLOTS * SA_BYTES + 2 * kBStage, "epilogue tile fits in the stage buffers");
     // alone on its SM: a second CTA would wait in tcgen05.alloc for the 512 columns
     static_assert(2 * kSmem > 228 * 1024, "one CTA per SM");
     static_assert(kSmem <= 227 * 1024, "shared memory");
 };
 
 template <int ND>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kSlicedThreads, 1)
 k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m, int n, int kpad,
             float alpha, const int *ea, const int *fb, dfloat *D, int64_t ldd) {
     using Cfg = SlicedCfg<ND>;
@@ -360,11 +386,13 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     unsigned char *sA = base;
     unsigned char *sB = base + A_SLOTS * SA_BYTES;
-    SCtl *ctl = (SCtl *)(sB + 2 * Cfg::kBStage);
+    dfloat *stage = reinterpret_cast<dfloat *>(sB + 2 * Cfg::kBStage);   // BM x kHalfLd
+    SCtl *ctl = (SCtl *)(sB + 2 * Cfg::kBStage + STAGE_BYTES);
     volatile int *abort = &ctl->abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * SBN;
     const int nkt = kpad / BK;
+    const int ntm = (m + BM - 1) / BM, ntn = (n + SBN - 1) / SBN;
+    const int ntiles = ntm * ntn;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < A_SLOTS; ++s) {
@@ -375,17 +403,15 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             mbar_init(&ctl->bfull[s], 1);
             mbar_init(&ctl->bempty[s], 1);
         }
-        mbar_init(&ctl->accum, 1);
+        mbar_init(&ctl->tfull, 1);
+        mbar_init(&ctl->tempty, 4);
+        mbar_init(&ctl->drain, 1);
         ctl->abort = 0;
         ctl->issued_a = 0;
         ctl->issued_b = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (threadIdx.x < SBN) {
-        const int col = n0 + threadIdx.x;
-        ctl->cs[threadIdx.x] = col < n ? ldexpf(alpha, fb[col]) : 0.0f;
-    }
-    if (warp == 1) {
+    if (warp == 5) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&ctl->tmem)),
                      "r"(S_TMEM)
                      : "memory");
@@ -396,156 +422,181 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     fence_after();
     const uint32_t tmem = ctl->tmem;
 
-    // pull this CTA's rows of D into L2 now, for the epilogue after the MMAs
-    {
-        const int row = m0 + (int)threadIdx.x;   // one row per thread
-        if (row < m && n0 < n) {
-            const char *rp = reinterpret_cast<const char *>(D + (int64_t)row * ldd + n0);
-            const int bytes = (n - n0 < SBN ? n - n0 : SBN) * (int)sizeof(dfloat);
-            for (int b = 0; b < bytes; b += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(rp + b));
-        }
-    }
-
-    if (warp == 0 && lane == 0) {
-        int ai = 0;
-        bool ok = true;
-        for (int kt = 0; kt < nkt && ok; ++kt) {
-            const int bs = kt & 1;
-            if (kt >= 2 && !mbar_wait(&ctl->bempty[bs], (uint32_t)((kt >> 1) & 1) ^ 1u, abort)) {
-                ok = false;
-                break;
+    if (warp == 4) {
+        // ---------------- producer ----------------
+        if (lane == 0) {
+            int ai = 0, bi = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                const int m0 = (tile / ntn) * BM, n0 = (tile % ntn) * SBN;
+                for (int kt = 0; kt < nkt && ok; ++kt, ++bi) {
+                    const int bs = bi & 1;
+                    if (bi >= 2 && !mbar_wait(&ctl->bempty[bs], (uint32_t)((bi >> 1) & 1) ^ 1u, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&ctl->bfull[bs], Cfg::kBStage);
+                    for (int u = 0; u < ND; ++u)
+                        tma_2d(sB + bs * Cfg::kBStage + u * SBD_BYTES, &tmB, &ctl->bfull[bs], u * kpad + kt * BK, n0);
+                    ctl->issued_b = bi + 1;
+                    for (int t = 0; t < ND; ++t, ++ai) {
+                        const int slot = ai % A_SLOTS;
+                        if (ai >= A_SLOTS &&
+                            !mbar_wait(&ctl->aempty[slot], (uint32_t)((ai / A_SLOTS) & 1) ^ 1u, abort)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_expect_tx(&ctl->afull[slot], SA_BYTES);
+                        tma_2d(sA + slot * SA_BYTES, &tmA, &ctl->afull[slot], t * kpad + kt * BK, m0);
+                        ctl->issued_a = ai + 1;
+                    }
+                }
             }
-            mbar_expect_tx(&ctl->bfull[bs], Cfg::kBStage);
-            for (int u = 0; u < ND; ++u)
-                tma_2d(sB + bs * Cfg::kBStage + u * SBD_BYTES, &tmB, &ctl->bfull[bs], u * kpad + kt * BK, n0);
-            ctl->issued_b = kt + 1;
-            for (int t = 0; t < ND; ++t, ++ai) {
-                const int slot = ai % A_SLOTS;
-                if (ai >= A_SLOTS &&
-                    !mbar_wait(&ctl->aempty[slot], (uint32_t)((ai / A_SLOTS) & 1) ^ 1u, abort)) {
+            if (!ok) *abort = 1;
+        }
+        __syncwarp();
+    } else if (warp == 5) {
+        // ---------------- MMA issue ----------------
+        if (lane == 0) {
+            bool ok = true;
+            int ai = 0, bi = 0, tc = 0;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tc) {
+                // the previous tile's accumulators must have been read out
+                if (tc > 0 && !mbar_wait(&ctl->tempty, (uint32_t)((tc - 1) & 1), abort)) {
                     ok = false;
                     break;
                 }
-                mbar_expect_tx(&ctl->afull[slot], SA_BYTES);
-                tma_2d(sA + slot * SA_BYTES, &tmA, &ctl->afull[slot], t * kpad + kt * BK, m0);
-                ctl->issued_a = ai + 1;
-            }
-        }
-        if (!ok) *abort = 1;
-    } else if (warp == 1 && lane == 0) {
-        bool ok = true;
-        int ai = 0;
-        for (int kt = 0; kt < nkt && ok; ++kt) {
-            const int bs = kt & 1;
-            if (!mbar_wait(&ctl->bfull[bs], (uint32_t)((kt >> 1) & 1), abort)) {
-                ok = false;
-                break;
-            }
-            const uint32_t bbase = sa(sB + bs * Cfg::kBStage);
-#pragma unroll
-            for (int t = 0; t < ND; ++t) {
-                const int slot = ai % A_SLOTS;
-                if (!ok || !mbar_wait(&ctl->afull[slot], (uint32_t)((ai / A_SLOTS) & 1), abort)) {
-                    ok = false;
-                    continue;
-                }
-                ++ai;
                 fence_after();
-                const uint64_t ad = sdesc(sa(sA + slot * SA_BYTES));
-                const int nrows = SBN * (ND - t);          // B digits 1 .. ND - t
+                for (int kt = 0; kt < nkt && ok; ++kt, ++bi) {
+                    const int bs = bi & 1;
+                    if (!mbar_wait(&ctl->bfull[bs], (uint32_t)((bi >> 1) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t bbase = sa(sB + bs * Cfg::kBStage);
 #pragma unroll
-                for (int k = 0; k < BK / UMMA_K; ++k) {
+                    for (int t = 0; t < ND; ++t) {
+                        const int slot = ai % A_SLOTS;
+                        if (!ok || !mbar_wait(&ctl->afull[slot], (uint32_t)((ai / A_SLOTS) & 1), abort)) {
+                            ok = false;
+                            continue;
+                        }
+                        ++ai;
+                        fence_after();
+                        const uint64_t ad = sdesc(sa(sA + slot * SA_BYTES));
+                        const int nrows = SBN * (ND - t);          // B digits 1 .. ND - t
 #pragma unroll
-                    for (int c0 = 0; c0 < nrows; c0 += 256) {
-                        const int nn = nrows - c0 < 256 ? nrows - c0 : 256;
-                        const uint64_t bd = sdesc(bbase + (uint32_t)c0 * 128u);
-                        mma_n(tmem + (uint32_t)(SBN * t + c0), ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2),
-                              idesc_n(nn), (kt == 0 && t == 0 && k == 0) ? 0u : 1u);
+                        for (int k = 0; k < BK / UMMA_K; ++k) {
+#pragma unroll
+                            for (int c0 = 0; c0 < nrows; c0 += 256) {
+                                const int nn = nrows - c0 < 256 ? nrows - c0 : 256;
+                                const uint64_t bd = sdesc(bbase + (uint32_t)c0 * 128u);
+                                mma_n(tmem + (uint32_t)(SBN * t + c0), ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2),
+                                      idesc_n(nn), (kt == 0 && t == 0 && k == 0) ? 0u : 1u);
+                            }
+                        }
+                        commit(&ctl->aempty[slot]);
+                    }
+                    if (ok) commit(&ctl->bempty[bs]);
+                }
+                if (ok) commit(&ctl->tfull);
+            }
+            if (!ok) *abort = 1;
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue (warps 0-3, TMEM lanes 0-127) ----------------
+        const int r = warp * 32 + lane;
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        int tc = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tc) {
+            const int m0 = (tile / ntn) * BM, n0 = (tile % ntn) * SBN;
+            const int row = m0 + r;
+            // this tile's rows of D into L2 while its MMAs run
+            if (row < m && n0 < n) {
+                const char *rp = reinterpret_cast<const char *>(D + (int64_t)row * ldd + n0);
+                const int bytes = (n - n0 < SBN ? n - n0 : SBN) * (int)sizeof(dfloat);
+                for (int b = 0; b < bytes; b += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(rp + b));
+            }
+            epi_sync();                        // every thread is done with the previous tile's cs
+            if (r < SBN) {
+                const int col = n0 + r;
+                ctl->cs[r] = col < n ? ldexpf(alpha, fb[col]) : 0.0f;
+            }
+            const float rs = ldexpf(1.0f, (row < m ? ea[row] : 0) - 7 * ND);
+            const bool ready = mbar_wait_sleep(&ctl->tfull, (uint32_t)(tc & 1), abort);
+            if (!ready) *abort = 1;
+            fence_after();
+            // one decision for all four warps (they share a named barrier)
+            epi_sync();
+            if (r == 0) ctl->epi_go = *abort ? 0 : 1;
+            epi_sync();
+            if (!ctl->epi_go) break;
+            dfloat S[2][32];
+            uint32_t q[32];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                // Horner over the groups, largest weight first: S = 2^7 S + P_g.  The
+                // P_g are integers below 2^24 and the partial sums integers below
+                // 2^60: exact as double-float up to 48 bits, all on the FP32 pipe.
+                tmem_ld32(lane_addr + (uint32_t)(32 * h), q);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) S[h][j] = dfloat(__uint_as_float(q[j]));
+#pragma unroll 1
+                for (int g = 1; g < ND - 1; ++g) {
+                    tmem_ld32(lane_addr + (uint32_t)(SBN * g + 32 * h), q);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        S[h][j].hi *= 128.0f;
+                        S[h][j].lo *= 128.0f;
+                        S[h][j] = S[h][j] + dfloat(__uint_as_float(q[j]));
                     }
                 }
-                commit(&ctl->aempty[slot]);
-            }
-            if (ok) commit(&ctl->bempty[bs]);
-        }
-        if (ok) commit(&ctl->accum);
-        else *abort = 1;
-    }
-    __syncwarp();
-
-    bool ready = mbar_wait(&ctl->accum, 0, abort);
-    if (!ready) *abort = 1;
-    fence_after();
-    ready = __syncthreads_and(ready) != 0;
-    dfloat *tile = reinterpret_cast<dfloat *>(base);   // BM x kDfLd, over the stage buffers
-    if (ready) {
-        const int r = warp * 32 + lane;
-        const int row = m0 + r;
-        const float rs = ldexpf(1.0f, (row < m ? ea[row] : 0) - 7 * ND);
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-        for (int h = 0; h < SBN / 32; ++h) {
-            dfloat S[32];
-            uint32_t q[32];
-            // Horner over the groups, largest weight first: S = 2^7 S + P_g.  The
-            // P_g are integers below 2^24 and the partial sums integers below
-            // 2^60: exact as double-float up to 48 bits, all on the FP32 pipe.
-            tmem_ld32(lane_addr + (uint32_t)(32 * h), q);
+                tmem_ld32(lane_addr + (uint32_t)(SBN * (ND - 1) + 32 * h), q);   // the last group: 2^-7
 #pragma unroll
-            for (int j = 0; j < 32; ++j) S[j] = dfloat(__uint_as_float(q[j]));
-#pragma unroll 1
-            for (int g = 1; g < ND - 1; ++g) {
-                tmem_ld32(lane_addr + (uint32_t)(SBN * g + 32 * h), q);
+                for (int j = 0; j < 32; ++j) S[h][j] = S[h][j] + dfloat(__uint_as_float(q[j]) * 0.0078125f);
+            }
+            // TMEM is free for the next tile's MMAs
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->tempty);
+            // D += 2^{e_i - 7 ND} alpha 2^{f_j} S (two exact power-of-two scalings),
+            // half a tile at a time through shared memory so the read-modify-write
+            // of D runs along rows, eight rows' loads in flight per warp
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                epi_sync();                    // the staging area is free
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    S[j].hi *= 128.0f;
-                    S[j].lo *= 128.0f;
-                    S[j] = S[j] + dfloat(__uint_as_float(q[j]));
+                    dfloat a0;
+                    a0.hi = (S[h][j].hi * rs) * ctl->cs[32 * h + j];
+                    a0.lo = (S[h][j].lo * rs) * ctl->cs[32 * h + j];
+                    stage[r * kHalfLd + j] = a0;
                 }
-            }
-            // the last group carries 2^-7 against the others
-            tmem_ld32(lane_addr + (uint32_t)(SBN * (ND - 1) + 32 * h), q);
+                epi_sync();
+                const int col = n0 + 32 * h + lane;
+                for (int r0 = warp * 32; r0 < warp * 32 + 32; r0 += 8) {
+                    dfloat d[8];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) S[j] = S[j] + dfloat(__uint_as_float(q[j]) * 0.0078125f);
+                    for (int qq = 0; qq < 8; ++qq) {
+                        const int rw = m0 + r0 + qq;
+                        d[qq] = (rw < m && col < n) ? D[(int64_t)rw * ldd + col] : dfloat(0.0f);
+                    }
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float cs = ctl->cs[32 * h + j];   // two exact power-of-two scalings
-                dfloat v;
-                v.hi = (S[j].hi * rs) * cs;
-                v.lo = (S[j].lo * rs) * cs;
-                tile[r * kDfLd + 32 * h + j] = v;
-            }
-        }
-    }
-    __syncthreads();
-    if (ready) {
-        // D += tile, coalesced along rows; eight rows' loads in flight per batch
-        for (int r0 = warp * 32; r0 < warp * 32 + 32; r0 += 8) {
-            dfloat d[8][SBN / 32];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int row = m0 + r0 + q;
-#pragma unroll
-                for (int e = 0; e < SBN / 32; ++e) {
-                    const int col = n0 + lane + 32 * e;
-                    d[q][e] = (row < m && col < n) ? D[(int64_t)row * ldd + col] : dfloat(0.0f);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int row = m0 + r0 + q;
-#pragma unroll
-                for (int e = 0; e < SBN / 32; ++e) {
-                    const int cc = lane + 32 * e, col = n0 + cc;
-                    if (row < m && col < n) D[(int64_t)row * ldd + col] = d[q][e] + tile[(r0 + q) * kDfLd + cc];
+                    for (int qq = 0; qq < 8; ++qq) {
+                        const int rw = m0 + r0 + qq;
+                        if (rw < m && col < n) D[(int64_t)rw * ldd + col] = d[qq] + stage[(r0 + qq) * kHalfLd + lane];
+                    }
                 }
             }
         }
     }
+
     fence_before();
     __syncthreads();
     if (ctl->abort) {
         // drain the copies still in flight before the CTA's shared memory goes away
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 128) {
             atomicExch(&g_tc_timeout, 1);
             int dummy = 0;
             const int ia = ctl->issued_a, ib = ctl->issued_b;
@@ -554,13 +605,14 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             for (int i = (ib > 2 ? ib - 2 : 0); i < ib; ++i)
                 mbar_wait(&ctl->bfull[i & 1], (uint32_t)((i >> 1) & 1), (volatile int *)&dummy);
         }
-        if (threadIdx.x == 32) {
+        if (threadIdx.x == 160) {     // the MMA thread: wait for its MMAs still in flight
             int dummy = 0;
-            mbar_wait(&ctl->accum, 0, (volatile int *)&dummy);
+            commit(&ctl->drain);
+            mbar_wait(&ctl->drain, 0, (volatile int *)&dummy);
         }
         __syncthreads();
     }
-    if (warp == 1)
+    if (warp == 5)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S_TMEM) : "memory");
 }
 
@@ -600,15 +652,24 @@ cudaError_t launch_sliced(const CUtensorMap &ma, const CUtensorMap &mb, int64_t 
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    dim3 grid((unsigned)cdiv(n, SBN), (unsigned)cdiv(m, BM));
-    if (grid.y > 65535u) return cudaErrorInvalidValue;
+    // persistent: one CTA per SM, never more CTAs than tiles
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 148;
+    }
+    const int64_t tiles = cdiv(m, BM) * cdiv(n, SBN);
+    if (tiles > INT32_MAX) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
     auto *ev = profile_slot();
     if (ev) {
         cudaEventRecord(ev->first, s);
         tc_profile().flops += 2.0 * (double)m * (double)n * (double)kpad * (ND * (ND + 1) / 2);
     }
     note_launch();
-    k_tc_sliced<ND><<<grid, 128, SlicedCfg<ND>::kSmem, s>>>(ma, mb, (int)m, (int)n, (int)kpad, alpha, ea, fb, D, ldd);
+    k_tc_sliced<ND><<<grid, kSlicedThreads, SlicedCfg<ND>::kSmem, s>>>(ma, mb, (int)m, (int)n, (int)kpad, alpha, ea,
+                                                                        fb, D, ldd);
     if (ev) cudaEventRecord(ev->second, s);
     return cudaGetLastError();
 }

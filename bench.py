@@ -65,10 +65,12 @@ def parse():
     p.add_argument("--kind", default="gaussian", choices=list(KINDS))
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--tol", type=float, default=1e-14)
-    p.add_argument("--workload", default="svd", choices=["lead", "svd", "batched", "diff"],
+    p.add_argument("--workload", default="svd", choices=["lead", "svd", "batched", "diff", "table71"],
                    help="lead: N(0,1) A with a rank-deficient leading block; svd: A = J U diag(sigma) V^T; "
                         "batched: 10k systems n in [16,512], a11 = 0, FP32 factors + FP64 refinement; "
-                        "diff: 256 x n=1024 FP32 systems, circulant G, 8 RHS, forward + adjoint")
+                        "diff: 256 x n=1024 FP32 systems, circulant G, 8 RHS, forward + adjoint; "
+                        "table71: the paper-shaped Table 7.1 experiment (+-1 circulant multipliers, 100 systems "
+                        "per n in 64, 256, 1024, residuals after 0 and 1 refinement steps, and plain GENP)")
     p.add_argument("--count", type=int, default=None, help="systems in the batched / diff workloads")
     p.add_argument("--kappa", type=float, default=1e6, help="condition number of the svd workload")
     p.add_argument("--prec", default="sliced", choices=list(PRECS))
@@ -686,9 +688,69 @@ def run_batched(a):
         dist.destroy_process_group()
 
 
+def run_table71(a):
+    """Sec. 7.1 / Table 7.1, paper-shaped: for n = 64, 256, 1024 and 100 seeded
+    systems each (workloads.table71: well conditioned, numerically singular
+    n/2 x n/2 leading block), GENP of A G with the paper's circulant +-1
+    multiplier, relative residual ||A y - b||_2 / ||b||_2 after 0 and 1 FP64
+    refinement steps, and plain GENP (G = I) for comparison.  Statistics only:
+    the paper does not give its matrices, so its numbers are context."""
+    import torch
+
+    import paper_1212_4560_gb300 as genp
+    import workloads as W
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1212_4560_gb300 import build as _b
+    _b.build()
+    count = a.count or 100
+
+    def relres(A, X, B):
+        return float(torch.linalg.norm(A @ X - B) / torch.linalg.norm(B))
+
+    def stats(v):
+        v = np.array(v)
+        return {"min": float(v.min()), "max": float(v.max()), "mean": float(v.mean()), "std": float(v.std())}
+
+    rows, plain = [], {}
+    t0 = time.perf_counter()
+    for n in (64, 256, 1024):
+        r0, r1, rp, attempts = [], [], [], []
+        for seed in range(count):
+            A, _, B = W.table71(n, seed, device=dev)
+            G = genp.make_multiplier(genp.CIRCULANT_PM1, n, seed=seed)
+            C = torch.empty_like(A)
+            genp.precondition(G, A, C)
+            F = genp.factor(C)
+            X = torch.empty_like(B)
+            genp.solve(F, G, B, X)
+            r0.append(relres(A, X, B))
+            genp.refine(A, F, G, B, X, tol=0.0, max_iter=1)
+            r1.append(relres(A, X, B))
+            Gi = genp.make_multiplier(genp.IDENTITY, n, seed=0)
+            Ci = A.clone()
+            Fi = genp.factor(Ci)
+            Xi = torch.empty_like(B)
+            genp.solve(Fi, Gi, B, Xi)
+            rp.append(relres(A, Xi, B))
+        rows.append(dict(n=n, iterations=0, **stats(r0)))
+        rows.append(dict(n=n, iterations=1, **stats(r1)))
+        plain[str(n)] = stats([x if math.isfinite(x) else float("inf") for x in rp])
+    line = {"workload": "table71_paper_shaped", "systems_per_n": count,
+            "multiplier": "circulant, +-1 first column, redrawn on a zero DFT bin of power-of-two order",
+            "residual": "||A y - b||_2 / ||b||_2", "rows": rows, "plain_genp": plain,
+            "seconds": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
-    if a.impl == "reference":
+    if a.workload == "table71":
+        run_table71(a)
+    elif a.impl == "reference":
         run_reference(a)
     elif a.workload in ("batched", "diff"):
         run_batched(a)

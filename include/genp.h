@@ -66,11 +66,23 @@ typedef enum {
  *               column and every row holds nnz signed unit entries
  *               (coinciding positions add).  The paper names sparse
  *               multipliers (Sec. 1 and Sec. 8) without fixing a structure;
- *               this is the structure the library uses. */
+ *               this is the structure the library uses.
+ *  CIRCULANT_PM1: circulant whose first column holds random signs +-1, the
+ *               multipliers of the paper's tests (Sec. 7.1, Table 7.1).
+ *               Such a circulant is exactly singular when a DFT bin of g
+ *               vanishes (probability about 0.18 at n = 64); draws are
+ *               repeated (attempt a = 0, 1, ... on the Philox counter) until
+ *               no bin of power-of-two order vanishes, an exact integer test
+ *               (the sum of g, and the folded sums for every x^m + 1 with
+ *               2m | n), complete when n is a power of two.  scale ignored.
+ *  IDENTITY:    G = I, i.e. plain GENP of A (no preconditioning), the
+ *               paper's comparison point; seed, scale and grid ignored. */
 typedef enum {
     GENP_MULT_GAUSSIAN = 0,
     GENP_MULT_CIRCULANT = 1,
-    GENP_MULT_SPARSE_PM1 = 2
+    GENP_MULT_SPARSE_PM1 = 2,
+    GENP_MULT_CIRCULANT_PM1 = 3,
+    GENP_MULT_IDENTITY = 4
 } genp_mult_kind;
 
 /* Arithmetic of a factorization.

@@ -33,7 +33,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _i64 = ctypes.c_int64
 _u64 = ctypes.c_uint64
 
-KIND_GAUSSIAN, KIND_CIRCULANT, KIND_SPARSE = 0, 1, 2
+KIND_GAUSSIAN, KIND_CIRCULANT, KIND_SPARSE, KIND_CIRCULANT_PM1, KIND_IDENTITY = 0, 1, 2, 3, 4
 
 
 def lib():
@@ -57,6 +57,10 @@ def lib():
         L.or_mult_circulant_f32.argtypes = [_i64, _u64, _u64, ctypes.c_float, _dp]
         L.or_mult_dense.argtypes = [_i64, _u64, _u64, ctypes.c_double, _dp, _i64]
         L.or_mult_circulant.argtypes = [_i64, _u64, _u64, ctypes.c_double, _dp]
+        L.or_mult_circulant_pm1.argtypes = [_i64, _u64, _u64, _dp]
+        L.or_mult_circulant_pm1.restype = ctypes.c_int
+        L.or_circulant_pm1_singular.argtypes = [_i64, _dp]
+        L.or_circulant_pm1_singular.restype = ctypes.c_int
         L.or_mult_sparse.argtypes = [_i64, ctypes.c_int, _u64, _u64, ctypes.c_void_p, ctypes.c_void_p]
         L.or_circulant_to_dense.argtypes = [_i64, _dp, _dp, _i64]
         L.or_sparse_to_dense.argtypes = [_i64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, _dp, _i64]
@@ -123,6 +127,9 @@ def gauss_f32(seed: int, stream: int, tag: int, idx: int) -> float:
 def multiplier(kind: int, n: int, seed: int, stream: int = 0, scale: float | None = None,
                nnz: int = 4, grid: str = "fp64"):
     """The random multiplier G (Definition 3.2 / Sec. 2.3 / sparse reading).
+    Kinds: 0 Gaussian, 1 Gaussian circulant, 2 sparse +-1, 3 circulant with a
+    +-1 first column (the paper's test multiplier, Sec. 7.1; redrawn until its
+    power-of-two-order DFT bins are nonzero), 4 the identity (plain GENP).
 
     grid "fp64": entries drawn in double precision; "fp32": drawn by the same
     polar method in single precision (scale rounded to float first).
@@ -150,6 +157,17 @@ def multiplier(kind: int, n: int, seed: int, stream: int = 0, scale: float | Non
             L.or_circulant_to_dense(n, _p(g), _p(G), n)
             out["G"] = G
         return out
+    if kind == KIND_CIRCULANT_PM1:
+        g = np.empty(n)
+        attempt = L.or_mult_circulant_pm1(n, seed, stream, _p(g))
+        out = {"kind": kind, "n": n, "g": g, "attempt": int(attempt)}
+        if n <= 4096:
+            G = np.empty((n, n))
+            L.or_circulant_to_dense(n, _p(g), _p(G), n)
+            out["G"] = G
+        return out
+    if kind == KIND_IDENTITY:
+        return {"kind": kind, "n": n, "G": np.eye(n)}
     if kind == KIND_SPARSE:
         rows = np.empty((nnz, n), dtype=np.int32)
         signs = np.empty((nnz, n), dtype=np.int8)
@@ -161,6 +179,12 @@ def multiplier(kind: int, n: int, seed: int, stream: int = 0, scale: float | Non
             out["G"] = G
         return out
     raise ValueError(kind)
+
+
+def circulant_pm1_singular(g) -> bool:
+    """The exact integer singularity test of the +-1 circulant draw."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    return bool(lib().or_circulant_pm1_singular(len(g), _p(g)))
 
 
 # --------------------------------------------------------------------------
@@ -187,7 +211,9 @@ def precondition(A: np.ndarray, M: dict, rows=None) -> np.ndarray:
     L = lib()
     if M["kind"] == KIND_GAUSSIAN:
         return matmul(A, M["G"])
-    if M["kind"] == KIND_CIRCULANT:
+    if M["kind"] == KIND_IDENTITY:
+        return A.copy()
+    if M["kind"] in (KIND_CIRCULANT, KIND_CIRCULANT_PM1):
         L.or_circ_matmul(m, n, _p(A), n, _p(_c(M["g"])), _p(C), n)
         return C
     L.or_sparse_matmul(m, n, M["nnz"], _p(A), n, M["rows"].ctypes.data, M["signs"].ctypes.data,
@@ -203,7 +229,9 @@ def apply_multiplier(M: dict, Y: np.ndarray, trans: bool = False) -> np.ndarray:
     L = lib()
     if M["kind"] == KIND_GAUSSIAN:
         return matmul(M["G"].T.copy() if trans else M["G"], Y)
-    if M["kind"] == KIND_CIRCULANT:
+    if M["kind"] == KIND_IDENTITY:
+        return Y.copy()
+    if M["kind"] in (KIND_CIRCULANT, KIND_CIRCULANT_PM1):
         L.or_circ_apply(n, nrhs, int(trans), _p(_c(M["g"])), _p(Y), nrhs, _p(X), nrhs)
         return X
     L.or_sparse_apply(n, nrhs, int(trans), M["nnz"], M["rows"].ctypes.data, M["signs"].ctypes.data,

@@ -93,7 +93,7 @@ OR_EXPORT double or_log(double s) {
 
 /* Philox stream layout used for every draw of the method (shared spec, not
  * shared code): key = (seed, stream_id); counter = (index, block, tag, 0). */
-enum { OR_TAG_DENSE = 0x10, OR_TAG_CIRC = 0x11, OR_TAG_PERM = 0x12, OR_TAG_SIGN = 0x13 };
+enum { OR_TAG_DENSE = 0x10, OR_TAG_CIRC = 0x11, OR_TAG_PERM = 0x12, OR_TAG_SIGN = 0x13, OR_TAG_CIRC_PM1 = 0x16 };
 #define OR_POLAR_BLOCKS 32
 
 /* One standard normal by Marsaglia's polar method: draw (v1, v2) uniform on
@@ -202,6 +202,51 @@ OR_EXPORT void or_mult_dense(int64_t n, uint64_t seed, uint64_t stream, double s
 OR_EXPORT void or_mult_circulant(int64_t n, uint64_t seed, uint64_t stream, double scale,
                                  double *g) {
     for (int64_t i = 0; i < n; ++i) g[i] = or_gauss(seed, stream, OR_TAG_CIRC, (uint64_t)i) * scale;
+}
+
+/* Whether the circulant with first column g (entries +-1) is singular at a
+ * DFT frequency whose order is a power of two, tested exactly in integers:
+ * the bin at frequency 0 vanishes iff sum g_i = 0; the bins at the primitive
+ * 2m-th roots of unity w (2m dividing n, m = 1, 2, 4, ...) vanish iff
+ * x^m + 1 divides g(x) = sum g_i x^i, i.e. iff every folded sum
+ * h_r = sum_q (-1)^q g_{r + q m}, r < m, is zero (g(w) = sum_r h_r w^r and
+ * x^m + 1 is irreducible over the rationals).  For n a power of two these are
+ * all of the DFT bins (the eigenvalues of the circulant, Sec. 2.3), so the
+ * test is exact; for other n it covers the bins of power-of-two order only. */
+OR_EXPORT int or_circulant_pm1_singular(int64_t n, const double *g) {
+    long long dc = 0;
+    for (int64_t i = 0; i < n; ++i) dc += (long long)g[i];
+    if (dc == 0) return 1;
+    for (int64_t m = 1; 2 * m <= n && n % (2 * m) == 0; m *= 2) {
+        int all_zero = 1;
+        for (int64_t r = 0; r < m && all_zero; ++r) {
+            long long h = 0;
+            for (int64_t q = 0; q < n / m; ++q) h += ((q & 1) ? -1 : 1) * (long long)g[r + q * m];
+            if (h != 0) all_zero = 0;
+        }
+        if (all_zero) return 1;
+    }
+    return 0;
+}
+
+/* Circulant multiplier with a first column of random signs (the multipliers
+ * of the paper's tests, Sec. 7.1): attempt a draws g_i = +-1 from the low bit
+ * of Philox word 0 at counter (i, 0, tag, a); the first attempt whose
+ * circulant passes the singularity test above is kept (the paper's remedy
+ * for a failure is a fresh draw, Sec. 5).  Returns the attempt used (64 if
+ * none of 64 attempts passed: the last one is kept). */
+OR_EXPORT int or_mult_circulant_pm1(int64_t n, uint64_t seed, uint64_t stream, double *g) {
+    uint64_t key[2] = {seed, stream};
+    int a = 0;
+    for (; a < 64; ++a) {
+        for (int64_t i = 0; i < n; ++i) {
+            uint64_t ctr[4] = {(uint64_t)i, 0, OR_TAG_CIRC_PM1, (uint64_t)a}, w[4];
+            or_philox4x64_10(ctr, key, w);
+            g[i] = (w[0] & 1ull) ? -1.0 : 1.0;
+        }
+        if (!or_circulant_pm1_singular(n, g)) return a;
+    }
+    return a;
 }
 
 /* Uniform integer in [0, range) from 64-bit words by Lemire's multiply-shift

@@ -59,6 +59,7 @@ void free_multiplier(genp_multiplier *G) {
     cudaFree(G->inv_rows);
     cudaFree(G->inv_signs);
     cudaFree(G->draws);
+    cudaFree(G->attempt);
     delete G;
 }
 
@@ -69,9 +70,11 @@ cudaError_t draw_multiplier(genp_multiplier *G, uint64_t seed, uint64_t stream_i
             return launch_make_dense(G->dense, G->n, seed, stream_id, G->scale, G->grid, G->dense_f32, G->dense_bf16,
                                      s);
         case GENP_MULT_CIRCULANT: {
-            cudaError_t e = launch_make_circulant(G->g, G->n, seed, stream_id, G->scale, G->grid, s);
+            cudaError_t e = G->pm1 ? launch_make_circulant_pm1(G->g, G->n, seed, stream_id, G->attempt, s)
+                                   : launch_make_circulant(G->g, G->n, seed, stream_id, G->scale, G->grid, s);
             return e == cudaSuccess ? circ_prepare(G, s) : e;
         }
+        case GENP_MULT_IDENTITY: return cudaSuccess;
         case GENP_MULT_SPARSE_PM1:
             return launch_make_sparse(G->rows, G->signs, G->inv_rows, G->inv_signs, G->draws, G->n, G->nnz, seed,
                                       stream_id, s);
@@ -111,6 +114,21 @@ namespace genp {
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// X[r][c] += Y[r][c] (the identity multiplier's x += G d)
+__global__ void k_add_into(const double *Y, int64_t ldy, double *X, int64_t ldx, int64_t n, int64_t nr,
+                           const int *skip) {
+    if (skip && *skip) return;
+    for (int64_t r = blockIdx.y; r < n; r += gridDim.y)
+        for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nr; c += (int64_t)gridDim.x * blockDim.x)
+            X[r * ldx + c] += Y[r * ldy + c];
+}
+// G = I into a dense buffer
+__global__ void k_eye(double *G, int64_t n, int64_t ldg) {
+    for (int64_t r = blockIdx.y; r < n; r += gridDim.y)
+        for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x)
+            G[r * ldg + c] = r == c ? 1.0 : 0.0;
+}
+
 cudaError_t apply_multiplier(const genp_multiplier *G, bool trans, const double *Y, int64_t ldy, double *X,
                              int64_t ldx, int64_t nrhs, bool accumulate, const int *skip, cudaStream_t s) {
     switch (G->kind) {
@@ -123,6 +141,13 @@ cudaError_t apply_multiplier(const genp_multiplier *G, bool trans, const double 
             return circ_apply_direct(G->g, G->n, trans, Y, ldy, X, ldx, nrhs, accumulate, skip, s);
         case GENP_MULT_SPARSE_PM1:
             return sparse_apply(G, trans, Y, ldy, X, ldx, nrhs, accumulate, skip, s);
+        case GENP_MULT_IDENTITY:
+            if (!accumulate) return convert_matrix<double, double>(Y, ldy, X, ldx, G->n, nrhs, skip, s);
+            note_launch();
+            k_add_into<<<dim3((unsigned)cdiv(nrhs, 32), (unsigned)(G->n < 65535 ? G->n : 65535)), 32, 0, s>>>(
+                Y, ldy, X, ldx, G->n, nrhs, skip);
+            return cudaGetLastError();
+        default: break;
     }
     return cudaErrorInvalidValue;
 }
@@ -152,7 +177,18 @@ genp_status genp_make_multiplier(genp_mult_kind kind, int64_t n, uint64_t seed, 
     if (!out) return GENP_ERR_ARG;
     *out = nullptr;
     if (n < 1 || n > 2147483647LL) return GENP_ERR_ARG;
-    if (kind != GENP_MULT_GAUSSIAN && kind != GENP_MULT_CIRCULANT && kind != GENP_MULT_SPARSE_PM1) return GENP_ERR_ARG;
+    if (kind != GENP_MULT_GAUSSIAN && kind != GENP_MULT_CIRCULANT && kind != GENP_MULT_SPARSE_PM1 &&
+        kind != GENP_MULT_CIRCULANT_PM1 && kind != GENP_MULT_IDENTITY)
+        return GENP_ERR_ARG;
+    const bool pm1 = kind == GENP_MULT_CIRCULANT_PM1;
+    if (pm1) {   // stored and applied as a circulant with a +-1 first column
+        kind = GENP_MULT_CIRCULANT;
+        scale = 1.0;
+    }
+    if (kind == GENP_MULT_IDENTITY) {
+        scale = 1.0;
+        value_grid = GENP_FP64;
+    }
     if (kind != GENP_MULT_SPARSE_PM1 && !(scale > 0.0 && isfinite(scale))) return GENP_ERR_ARG;
     if (kind == GENP_MULT_SPARSE_PM1 && (nnz_per_col < 1 || nnz_per_col > 16)) return GENP_ERR_ARG;
     if (value_grid != GENP_FP64 && value_grid != GENP_FP32 && value_grid != GENP_BF16) return GENP_ERR_ARG;
@@ -164,6 +200,7 @@ genp_status genp_make_multiplier(genp_mult_kind kind, int64_t n, uint64_t seed, 
     G->nnz = kind == GENP_MULT_SPARSE_PM1 ? nnz_per_col : 0;
     G->grid = kind == GENP_MULT_SPARSE_PM1 ? GENP_FP64 : value_grid;
     G->scale = kind == GENP_MULT_SPARSE_PM1 ? 1.0 : scale;
+    G->pm1 = pm1;
     G->last_stream = s;
     genp_status st = GENP_OK;
     cudaError_t ce = cudaSuccess;
@@ -171,8 +208,11 @@ genp_status genp_make_multiplier(genp_mult_kind kind, int64_t n, uint64_t seed, 
         st = dalloc(&G->dense, (size_t)n * n);
         if (st == GENP_OK && value_grid != GENP_FP64) st = dalloc(&G->dense_f32, (size_t)n * n);
         if (st == GENP_OK && value_grid == GENP_BF16) st = dalloc(&G->dense_bf16, (size_t)n * round8(n));
+    } else if (kind == GENP_MULT_IDENTITY) {
+        // nothing to store
     } else if (kind == GENP_MULT_CIRCULANT) {
         st = dalloc(&G->g, (size_t)n);
+        if (st == GENP_OK && pm1) st = dalloc(&G->attempt, 1);
         if (st == GENP_OK && circ_fft_supported(n)) {
             st = dalloc(&G->spec, (size_t)n);
             if (st == GENP_OK) st = dalloc(&G->spec_f32, (size_t)n);
@@ -291,7 +331,12 @@ genp_status genp_multiplier_export(const genp_multiplier *G, double *dense, int6
                                  cudaMemcpyDeviceToDevice, s));
         else if (G->kind == GENP_MULT_CIRCULANT)
             CU(launch_circulant_to_dense(G->g, n, dense, ldd, s));
-        else
+        else if (G->kind == GENP_MULT_IDENTITY) {
+            note_launch();
+            k_eye<<<dim3((unsigned)cdiv(n < 2048 ? n : 2048, 256), (unsigned)(n < 65535 ? n : 65535)), 256, 0, s>>>(
+                dense, n, ldd);
+            CU(cudaGetLastError());
+        } else
             CU(launch_sparse_to_dense(G->rows, G->signs, n, G->nnz, dense, ldd, s));
     }
     if (first_col) CU(cudaMemcpyAsync(first_col, G->g, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -303,7 +348,7 @@ genp_status genp_multiplier_export(const genp_multiplier *G, double *dense, int6
 genp_status genp_multiplier_query(const genp_multiplier *G, int64_t *n, int *kind, int *nnz_per_col) {
     if (!G) return GENP_ERR_ARG;
     if (n) *n = G->n;
-    if (kind) *kind = (int)G->kind;
+    if (kind) *kind = G->pm1 ? (int)GENP_MULT_CIRCULANT_PM1 : (int)G->kind;
     if (nnz_per_col) *nnz_per_col = G->nnz;
     return GENP_OK;
 }
@@ -322,6 +367,18 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
     if (!factor_prec_ok(c_prec)) return GENP_ERR_ARG;
     if (f64_factors(c_prec) && a_prec != GENP_FP64) return GENP_ERR_ARG;
     cudaStream_t s = S(cuda_stream);
+    if (G->kind == GENP_MULT_IDENTITY) {   // plain GENP: C = A in the factor's storage type
+        if (f64_factors(c_prec))
+            CU((convert_matrix<double, double>(static_cast<const double *>(A), lda, static_cast<double *>(C), ldc, n, n,
+                                               nullptr, s)));
+        else if (a_prec == GENP_FP64)
+            CU((convert_matrix<double, float>(static_cast<const double *>(A), lda, static_cast<float *>(C), ldc, n, n,
+                                              nullptr, s)));
+        else
+            CU((convert_matrix<float, float>(static_cast<const float *>(A), lda, static_cast<float *>(C), ldc, n, n,
+                                             nullptr, s)));
+        return GENP_OK;
+    }
     if (c_prec == GENP_BF16_SLICED && G->kind == GENP_MULT_GAUSSIAN) {
         // C = A G with FP64-class accuracy on the BF16 tensor cores, summed
         // in double-float and rounded to FP64 once.

@@ -68,6 +68,8 @@ struct genp_multiplier {
     int8_t *inv_signs = nullptr;
     int32_t *draws = nullptr;          // nnz x n Fisher-Yates draws (SPARSE)
     double scale = 1.0;
+    bool pm1 = false;                  // CIRCULANT_PM1 (stored as a circulant)
+    int *attempt = nullptr;            // device: the draw attempt kept (CIRCULANT_PM1)
     cudaStream_t last_stream = nullptr;
 };
 
@@ -133,6 +135,9 @@ cudaError_t launch_make_dense(double *G, int64_t n, uint64_t seed, uint64_t stre
                               genp_prec grid, float *G32, __nv_bfloat16 *Gbf, cudaStream_t s);
 cudaError_t launch_make_circulant(double *g, int64_t n, uint64_t seed, uint64_t stream_id,
                                   double scale, genp_prec grid, cudaStream_t s);
+// +-1 first column, redrawn until no DFT bin of power-of-two order vanishes
+cudaError_t launch_make_circulant_pm1(double *g, int64_t n, uint64_t seed, uint64_t stream_id, int *attempt,
+                                      cudaStream_t s);
 cudaError_t launch_make_sparse(int32_t *rows, int8_t *signs, int32_t *inv_rows, int8_t *inv_signs,
                                int32_t *scratch, int64_t n, int nnz, uint64_t seed,
                                uint64_t stream_id, cudaStream_t s);

@@ -180,6 +180,54 @@ __global__ void k_circ(double *g, int64_t n, uint64_t seed, uint64_t sid, double
                    : on_grid(__dmul_rn(polar_normal(seed, sid, kTagCirc, (uint64_t)i), scale), grid);
 }
 
+// Circulant with a +-1 first column (the paper's test multipliers): attempt
+// a takes g_i from the low bit of Philox word 0 at (i, 0, tag, a) and is
+// kept when no DFT bin of power-of-two order vanishes.  Exact integer test:
+// the bin at frequency 0 is sum g_i; the bins at the primitive 2m-th roots of
+// unity (2m | n) all vanish iff every folded sum h_r = sum_q (-1)^q g_{r+qm}
+// (r < m) is zero, x^m + 1 being irreducible over the rationals.  One CTA.
+constexpr uint64_t kTagCircPm1 = 0x16;
+__global__ void k_circ_pm1(double *g, int64_t n, uint64_t seed, uint64_t sid, int *attempt) {
+    __shared__ unsigned long long acc;
+    __shared__ int reject;
+    int a = 0;
+    for (; a < 64; ++a) {
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+            const U4 w = philox((uint64_t)i, 0, kTagCircPm1, (uint64_t)a, seed, sid);
+            g[i] = (w.w[0] & 1ull) ? -1.0 : 1.0;
+        }
+        if (threadIdx.x == 0) {
+            acc = 0ull;
+            reject = 0;
+        }
+        __syncthreads();
+        long long dc = 0;
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) dc += (long long)g[i];
+        atomicAdd(&acc, (unsigned long long)dc);
+        __syncthreads();
+        if (threadIdx.x == 0 && (long long)acc == 0) reject = 1;
+        __syncthreads();
+        for (int64_t m = 1; !reject && 2 * m <= n && n % (2 * m) == 0; m *= 2) {
+            if (threadIdx.x == 0) acc = 0ull;
+            __syncthreads();
+            int nonzero = 0;
+            for (int64_t r = threadIdx.x; r < m && !nonzero; r += blockDim.x) {
+                long long h = 0;
+                for (int64_t q = 0; q < n / m; ++q) h += ((q & 1) ? -1 : 1) * (long long)g[r + q * m];
+                if (h != 0) nonzero = 1;
+            }
+            if (nonzero) atomicOr(&acc, 1ull);
+            __syncthreads();
+            if (threadIdx.x == 0 && acc == 0ull) reject = 1;
+            __syncthreads();
+        }
+        const int rej = reject;
+        __syncthreads();
+        if (!rej) break;
+    }
+    if (threadIdx.x == 0) *attempt = a;
+}
+
 // Uniform integer in [0, range) (Lemire's multiply-shift with rejection).
 __device__ uint64_t bounded(uint64_t range, uint64_t seed, uint64_t sid, uint64_t i, uint64_t t) {
     const uint64_t thr = (0ull - range) % range;
@@ -304,6 +352,13 @@ cudaError_t launch_make_circulant(double *g, int64_t n, uint64_t seed, uint64_t 
                                   genp_prec grid, cudaStream_t s) {
     note_launch();
     k_circ<<<grid_for(n, 256), 256, 0, s>>>(g, n, seed, sid, scale, grid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_make_circulant_pm1(double *g, int64_t n, uint64_t seed, uint64_t sid, int *attempt,
+                                      cudaStream_t s) {
+    note_launch();
+    k_circ_pm1<<<1, 1024, 0, s>>>(g, n, seed, sid, attempt);
     return cudaGetLastError();
 }
 

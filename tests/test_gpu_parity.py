@@ -13,6 +13,7 @@ Tolerances (u = 2^-53, gamma_k = k u / (1 - k u)):
 * solve + refinement: normwise backward error <= 1e-14 and forward error
   <= 1e-14 kappa_inf(A) against the FP64 oracle, as the method targets.
 """
+import ctypes
 import math
 
 import numpy as np
@@ -322,6 +323,43 @@ def test_gmres_ir(g, prec, kind, nrhs):
     assert np.abs(x - xr).max() <= 1e-14 * kappa * np.abs(xr).max()
     assert len(info.bwd_err) == info.refine_iters + 1
     assert g._lib.load().genp_device_check(1) == 0
+
+
+@pytest.mark.parametrize("n,seed", [(64, 0), (64, 5), (256, 7), (1024, 1), (1000, 2), (3000, 4)])
+def test_circulant_pm1_bit_exact(g, n, seed):
+    """The +-1 circulant draw (attempts included) equals the oracle's bit for bit."""
+    G = g.make_multiplier(g.CIRCULANT_PM1, n, seed=seed)
+    first = torch.empty(n, dtype=torch.float64, device=DEV)
+    g.multiplier_export(G, first_col=first)
+    M = oracle.multiplier(oracle.KIND_CIRCULANT_PM1, n, seed=seed)
+    assert np.array_equal(host(first), M["g"])
+    k = ctypes.c_int()
+    g._lib.load().genp_multiplier_query(G.handle, None, ctypes.byref(k), None)
+    assert k.value == g.CIRCULANT_PM1
+
+
+@pytest.mark.parametrize("n", [64, 256, 1024])
+def test_circulant_pm1_solves_table71_system(g, n):
+    """The paper's test multiplier on the paper-shaped Table 7.1 system: one
+    refinement step reaches the paper's residual level; plain GENP (the
+    identity multiplier) does not."""
+    A, _, B = (t.numpy() for t in W.table71(n, seed=3))
+    X, info, G, F = g.solve_system(cu(A), cu(B), kind=g.CIRCULANT_PM1, seed=3, refine_steps=1, tol=0.0)
+    x = host(X)
+    res = np.linalg.norm(A @ x - B) / np.linalg.norm(B)
+    assert res <= 1e-12
+    Xp, infop, _, _ = g.solve_system(cu(A), cu(B), kind=g.IDENTITY, seed=0, refine_steps=0)
+    resp = np.linalg.norm(A @ host(Xp) - B) / np.linalg.norm(B)
+    assert resp > 1e3 * res
+
+
+def test_identity_multiplier_breaks_down(g):
+    A = np.array([[0.0, 1.0], [1.0, 0.0]])
+    C = cu(A)
+    G = g.make_multiplier(g.IDENTITY, 2, seed=0)
+    g.precondition(G, cu(A), C)
+    F = g.factor(C)
+    assert g.info_fetch(F).breakdown_step == 0
 
 
 def test_2x2_antidiagonal_solved(g):

@@ -470,3 +470,53 @@ def test_table71_shaped_plausibility():
         r = oracle.solve(A, B, M, refine_steps=0)
         worse.append(oracle.rel_residual_2(A, r["x"], B))
     assert max(worse) <= worst0[n]
+
+
+# ------------------------------------------------- +-1 circulant multipliers
+
+def test_circulant_pm1_singularity_test_is_exact():
+    """For n a power of two every DFT bin of g has power-of-two order, so the
+    integer test (sum of g; folded sums for x^m + 1) must agree with the DFT
+    computed independently by numpy, on random +-1 vectors and on vectors
+    built to vanish at chosen roots of unity."""
+    rng = np.random.default_rng(71)
+    agree = singular_seen = 0
+    for n in (2, 4, 8, 16, 32):
+        for _ in range(600):
+            g = rng.choice([-1.0, 1.0], n)
+            by_fft = np.abs(np.fft.fft(g)).min() < 1e-9
+            assert oracle.circulant_pm1_singular(g) == by_fft, (n, g)
+            agree += 1
+            singular_seen += by_fft
+    assert singular_seen > 200            # the singular cases are well represented
+    # vanishes at +-i (order 4, x^2 + 1 divides g(x)) but at no other bin
+    g = np.array([-1.0, -1.0, -1.0, -1.0, -1.0, 1.0, -1.0, 1.0])
+    F = np.abs(np.fft.fft(g))
+    assert F[2] < 1e-12 and F[0] > 1 and F[4] > 1 and F[1] > 1
+    assert oracle.circulant_pm1_singular(g)
+    assert not oracle.circulant_pm1_singular(np.array([1.0, 1.0, 1.0, -1.0]))   # DFT 2, 2j, 2, -2j
+
+
+def test_circulant_pm1_draws():
+    """Entries +-1, the kept draw nonsingular (all DFT bins nonzero), the
+    first draw rejected with the frequency of a zero bin (about 0.18 at
+    n = 64, Q3), and a redraw only when needed."""
+    att = []
+    for seed in range(400):
+        M = oracle.multiplier(oracle.KIND_CIRCULANT_PM1, 64, seed=seed)
+        g = M["g"]
+        assert set(np.unique(g)) <= {-1.0, 1.0}
+        assert np.abs(np.fft.fft(g)).min() > 1e-6
+        att.append(M["attempt"])
+    frac = np.mean(np.array(att) > 0)
+    assert 0.12 <= frac <= 0.26, frac
+    M = oracle.multiplier(oracle.KIND_CIRCULANT_PM1, 1024, seed=3)
+    assert np.abs(np.fft.fft(M["g"])).min() > 1e-6
+
+
+def test_identity_multiplier_is_plain_genp():
+    A, _, B = (t.numpy() for t in W.table71(64, seed=2))
+    M = oracle.multiplier(oracle.KIND_IDENTITY, 64, seed=0)
+    C = oracle.precondition(A, M)
+    assert np.array_equal(C, A)
+    assert np.array_equal(oracle.apply_multiplier(M, B), B)

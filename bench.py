@@ -81,6 +81,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--no-escalate", action="store_true",
+                   help="batched: leave systems whose FP32 refinement stalls unconverged (no double-float refactor)")
     p.add_argument("--no-fp64-compare", action="store_true",
                    help="skip timing the FP64 path on the same system (non-FP64 precisions)")
     return p.parse_args()
@@ -573,8 +575,9 @@ def run_batched(a):
         count = a.count or 10000
         nrhs = 4
         sizes = W.batched_sizes(count, 16, 512, seed=a.seed + rank)
-        plan = Bt.BatchedPlan(sizes, nrhs, kind=genp.GAUSSIAN, a_dtype=torch.float64, max_iter=10, tol=a.tol,
-                              autotune=True, escalate=True)
+        plan = Bt.BatchedPlan(sizes, nrhs, kind=genp.GAUSSIAN, a_dtype=torch.float64,
+                              max_iter=10 if a.max_iter is None else a.max_iter, tol=a.tol,
+                              autotune=True, escalate=not a.no_escalate)
         Ap = torch.empty(plan.mat_size, dtype=torch.float64, device=dev)
         Bp = torch.empty(plan.vec_size, dtype=torch.float64, device=dev)
         g = torch.Generator(device=dev)
@@ -649,6 +652,14 @@ def run_batched(a):
         e2e = {"value": world * count * k / (f0.elapsed_time(f1) / 1e3), "unit": "solves/s",
                "h2d_bytes_per_step": A_h.numel() * A_h.element_size() + B_h.numel() * 8,
                "d2h_bytes_per_step": X_h.numel() * 8, "steps": k}
+    # one more (eager, untimed) run with the kernel's phase profile on: SM
+    # cycles by phase, summed over the persistent CTAs
+    plan.profile(True)
+    step_body(1)
+    phases = plan.profile_read()
+    plan.profile(False)
+    tot = sum(phases.values()) or 1.0
+    phase_share = {k: round(v / tot, 4) for k, v in phases.items()}
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -660,9 +671,6 @@ def run_batched(a):
                "sample": f"oracle pipeline on the first {done} systems of the batch (~15 s), scaled to the "
                          f"whole batch by sum n^3"}
     name = "batched_10k_n16-512_fp32_fp64ir_4rhs" if not diff else "diff_256x1024_fp32_circulant_8rhs"
-    fp64 = None
-    if a.prec != "fp64" and not a.no_fp64_compare and world == 1:
-        fp64 = fp64_same_gpu(a, genp, A, B, kind, rank, dev)
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -680,7 +688,10 @@ def run_batched(a):
             "bwd_err_max": float(np.max(st["eta"])), "bwd_err_unrefined_median": float(np.median(st["eta0"])),
             "converged_fraction": float(np.mean(st["eta"] <= a.tol)) if not diff else None,
             "refine_iters_mean": float(np.mean(st["iters"])),
-            "escalated_to_fp64": int(np.sum(st["escalated"]))}
+            "fallback_substitution": int(np.sum(st["escalated"] == 1)),
+            "escalated_double_float": int(np.sum(st["escalated"] == 2)),
+            "krylov_steps_mean": float(np.mean(st["krylov"])),
+            "phase_share_of_cta_cycles": phase_share}
     if not a.no_clocks:
         line["clocks"] = clk.summary()
     print(json.dumps(line), flush=True)

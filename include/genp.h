@@ -271,9 +271,19 @@ GENP_API genp_status genp_adjoint(const genp_factors *F, const genp_multiplier *
  * persistent launch.  Each system gets its own multiplier (stream id = its
  * index i, drawn in single precision: GENP_FP32 grid), its own FP32
  * factorization C_i = A_i G_i = L_i U_i and FP64 refinement; a work queue
- * hands the systems, largest first, to the CTAs.  The plan owns every
- * workspace, so genp_batched_run allocates and synchronizes nothing and can
- * be captured in a CUDA graph.
+ * hands the systems, largest first, to the CTAs.  The refinement is
+ * GMRES-IR: r = b - A x in FP64, an FP32 GMRES on U^{-1} L^{-1} C_i d =
+ * U^{-1} L^{-1} r (at most 16 Krylov steps, relative tolerance 1e-3; the
+ * preconditioner applied through explicit FP32 inverses of L and U, or by
+ * substitution once that stalls; a step that raises the backward error is
+ * undone), then
+ * x += G_i d in FP64 (Carson & Higham 2018), until the backward error is
+ * <= tol, fails to halve on two outer steps in a row, or after max_iter
+ * outer steps; FP32 elimination without
+ * pivoting loses u32 times the element growth, which classic refinement
+ * alone does not recover for Gaussian systems of order a few hundred.
+ * The plan owns every workspace, so genp_batched_run allocates and
+ * synchronizes nothing and can be captured in a CUDA graph.
  * Pools (caller-owned device memory) hold the systems back to back in the
  * caller's order: A_i (n_i x n_i, row-major, ld n_i) at mat_offsets[i],
  * B_i / X_i (n_i x nrhs, ld nrhs) at vec_offsets[i] (genp_batched_layout).
@@ -284,15 +294,17 @@ typedef struct genp_batched_plan genp_batched_plan;
  * nrhs       right-hand sides per system (1..16).
  * kind       GENP_MULT_GAUSSIAN (dense N(0, 1/n_i)) or GENP_MULT_CIRCULANT (N(0,1) first column).
  * a_prec     storage of the A pool: GENP_FP64 or GENP_FP32.
- * max_iter   refinement steps (0..32; 0 = no refinement), tol its target
- *            backward error.
- * flags      GENP_BATCH_AUTOTUNE: time the candidate block sizes of each
- *            size class once on this GPU (synchronizes; the choice is kept
- *            per process and, if GENP_AUTOTUNE_CACHE names a file, there).
- *            GENP_BATCH_FP64_ESCALATION: a system whose FP32-factor
- *            refinement stalls above tol is factored again in FP64 by the
- *            same CTA and refined with those factors (the plan then holds
- *            8.1 MiB of FP64 scratch per persistent CTA).
+ * max_iter   outer refinement steps (0..32; 0 = no refinement), tol their
+ *            target backward error.
+ * flags      GENP_BATCH_AUTOTUNE: time the candidate CTA GEMM tiles (64 and
+ *            128) of each size class once on this GPU (synchronizes; the
+ *            choice is kept per process and, if GENP_AUTOTUNE_CACHE names a
+ *            file, there).
+ *            GENP_BATCH_FP64_ESCALATION: a second launch after each run
+ *            factors every system whose refinement did not reach tol again
+ *            in double-float arithmetic (about 48 bits) and refines it with
+ *            those factors (the plan then holds 8.1 MiB of scratch per
+ *            persistent CTA of that launch).
  * Errors: GENP_ERR_ARG, GENP_ERR_NOMEM, GENP_ERR_CUDA. */
 #define GENP_BATCH_AUTOTUNE 1
 #define GENP_BATCH_FP64_ESCALATION 2
@@ -304,7 +316,8 @@ GENP_API genp_status genp_batched_plan_create(int64_t count, const int64_t *n, i
  * pool and in the B / X pools (the last entry is the pool size). */
 GENP_API genp_status genp_batched_layout(const genp_batched_plan *P, int64_t *mat_offsets, int64_t *vec_offsets);
 
-/* Block size the plan uses for systems of order n (after autotuning). */
+/* CTA GEMM tile (64 or 128) the plan uses for systems of order n (after
+ * autotuning); the factorization block is 32. */
 GENP_API int genp_batched_block_size(const genp_batched_plan *P, int64_t n);
 
 /* Draws every system's multiplier from `seed` (system i: stream id i) and
@@ -322,18 +335,31 @@ GENP_API genp_status genp_batched_adjoint(genp_batched_plan *P, const void *A_po
                                           const double *X_pool, float *dA_pool, double *dB_pool, void *cuda_stream);
 
 /* Per-system results of the last run (host arrays of count entries, any may
- * be NULL): status (GENP_OK / GENP_ERR_BREAKDOWN / GENP_ERR_NOCONV),
+ * be NULL): status (GENP_OK / GENP_ERR_BREAKDOWN / GENP_ERR_NOCONV), outer
  * refinement steps, backward error before and after refinement, growth
- * max|U| / max|C| of the FP32 factorization, and whether the system was
- * escalated to FP64.  Synchronizes the stream. */
+ * max|U| / max|C| of the FP32 factorization, its escalation level (0: the
+ * inner solves used the explicit inverses of the factors throughout; 1: they
+ * switched to substitution with L and U after a stall; 2: refactored in
+ * double-float by the escalation launch), and the inner Krylov steps taken.
+ * Synchronizes the stream. */
 GENP_API genp_status genp_batched_status(const genp_batched_plan *P, int32_t *status, int32_t *iters, double *eta0,
-                                         double *eta, double *growth, int32_t *escalated, void *cuda_stream);
+                                         double *eta, double *growth, int32_t *escalated, int32_t *krylov,
+                                         void *cuda_stream);
 
 /* Copies the multipliers of the last run into caller pools: dense G_i
  * (float, A-pool layout) or circulant first columns g_i (float, sum n_i,
  * back to back in the caller's order). */
 GENP_API genp_status genp_batched_multipliers(const genp_batched_plan *P, float *G_pool, float *g_pool,
                                               void *cuda_stream);
+
+/* Phase profile of the batched kernel (diagnostics).  enable != 0 makes
+ * every later run record, per persistent CTA, the SM cycles spent in each
+ * phase of its last run; genp_batched_profile_read sums them over the CTAs
+ * into cycles[7]: C = A G, factorization, inverses of the factors, first
+ * solve and x = G y, FP64 residuals, inner GMRES, x += G d.  The read
+ * synchronizes the stream. */
+GENP_API genp_status genp_batched_profile(genp_batched_plan *P, int enable);
+GENP_API genp_status genp_batched_profile_read(const genp_batched_plan *P, double *cycles, void *cuda_stream);
 
 /* Frees the plan (cudaFree waits for work still using it). NULL is ignored. */
 GENP_API void genp_batched_plan_destroy(genp_batched_plan *P);

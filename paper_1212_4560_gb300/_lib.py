@@ -52,7 +52,9 @@ SIGNATURES = {
     "genp_batched_block_size": (_int, [_vp, _i64]),
     "genp_batched_run": (_int, [_vp, _u64, _vp, _vp, _vp, _vp]),
     "genp_batched_adjoint": (_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
-    "genp_batched_status": (_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "genp_batched_status": (_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "genp_batched_profile": (_int, [_vp, _int]),
+    "genp_batched_profile_read": (_int, [_vp, _vp, _vp]),
     "genp_batched_multipliers": (_int, [_vp, _vp, _vp, _vp]),
     "genp_batched_plan_destroy": (None, [_vp]),
     "genp_multiplier_export": (_int, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),

@@ -81,11 +81,27 @@ class BatchedPlan:
     def status(self, stream=None) -> dict:
         c = self.count
         out = {"status": np.zeros(c, np.int32), "iters": np.zeros(c, np.int32), "eta0": np.zeros(c),
-               "eta": np.zeros(c), "growth": np.zeros(c), "escalated": np.zeros(c, np.int32)}
+               "eta": np.zeros(c), "growth": np.zeros(c), "escalated": np.zeros(c, np.int32),
+               "krylov": np.zeros(c, np.int32)}
         p = {k: v.ctypes.data_as(ctypes.c_void_p) for k, v in out.items()}
         check(_lib.load().genp_batched_status(self.handle, p["status"], p["iters"], p["eta0"], p["eta"],
-                                              p["growth"], p["escalated"], _stream(stream)), "genp_batched_status")
+                                              p["growth"], p["escalated"], p["krylov"], _stream(stream)),
+              "genp_batched_status")
         return out
+
+
+    PHASES = ("precondition", "factor", "invert", "solve", "residual", "gmres", "update")
+
+    def profile(self, enable: bool = True) -> None:
+        """Record per-phase SM cycles in later runs (genp_batched_profile)."""
+        check(_lib.load().genp_batched_profile(self.handle, 1 if enable else 0), "genp_batched_profile")
+
+    def profile_read(self, stream=None) -> dict:
+        """SM cycles of the last run by phase, summed over the persistent CTAs."""
+        cyc = np.zeros(len(self.PHASES))
+        check(_lib.load().genp_batched_profile_read(self.handle, cyc.ctypes.data_as(ctypes.c_void_p),
+                                                    _stream(stream)), "genp_batched_profile_read")
+        return dict(zip(self.PHASES, cyc.tolist()))
 
 
 _plans: dict = {}

@@ -1,655 +1,59 @@
-// batched.cu -- many small randomized-GENP solves in one persistent launch.
-//
-// Each CTA pops the next system from an atomic work queue (systems sorted by
-// size, largest first) and carries it through the whole method on its own:
-//   C = A G                      (CTA-level GEMM; G dense or circulant)
-//   C = L U, no pivoting         (blocked: nb x nb diagonal block factored in
-//                                 shared memory, the block row and column by
-//                                 substitution against it, Schur update by the
-//                                 CTA GEMM)
-//   Y = U^{-1} L^{-1} B          (blocked by 32 rows)
-//   X = G Y                      (FP64 accumulation)
-//   refinement: R = B - A X (FP64), stop when the backward error is <= tol,
-//   fails to halve, or after max_iter; else D = U^{-1} L^{-1} R, X += G D.
-// The factorization runs in FP32.  When its refinement stalls above tol (the
-// element growth of pivot-free elimination can exceed what FP32 carries),
-// the CTA escalates: it forms C = A G again in double-float arithmetic (pairs
-// of floats, about 48 bits, on the FP32 pipe, which GB300 runs 64 times
-// faster than FP64), factors it in its own scratch and continues the FP64
-// refinement with those factors.
-// The adjoint kernel reuses the FP32 factors: Lambda = L^{-T} U^{-T} G^T gX,
-// dA = -Lambda X^T, dB = Lambda.  No CTA ever waits for another (the queue is
-// a single atomic counter), so a launch cannot deadlock.
+// batched.cu -- dispatch of the batched kernels by right-hand-side class
+// (the kernels themselves are in batched_impl.cuh, one translation unit per
+// class).
 #include "genp_internal.cuh"
-
-#include <math.h>
-
-#include "dfloat.cuh"
 
 namespace genp {
 namespace {
 
-constexpr int BT = 256;     // threads per CTA
-constexpr int TL = 64;      // CTA GEMM output tile
-constexpr int KS = 16;      // CTA GEMM K step
-constexpr int MAXNB = 64;   // largest factorization block
-constexpr int SB = 32;      // solve block
-constexpr int MAXRHS = 16;
-
-template <typename T>
-struct SmemGemm {
-    T As[KS][TL];
-    T Bs[KS][TL];
-};
-template <typename T>
-struct SmemPanel {
-    T a[MAXNB][MAXNB + 1];
-    T x[TL][MAXNB + 1];
-};
-template <typename T>
-struct SmemSolve {
-    T t[SB][SB + 1];
-    T y[SB][MAXRHS];
-};
-union Smem {
-    SmemGemm<float> gf;
-    SmemPanel<float> pf;
-    SmemSolve<float> sf;
-    SmemGemm<dfloat> gd;
-    SmemPanel<dfloat> pd;
-    SmemSolve<dfloat> sd;
-};
-template <typename T> __device__ __forceinline__ SmemGemm<T> &gemm_sm(Smem &s);
-template <> __device__ __forceinline__ SmemGemm<float> &gemm_sm<float>(Smem &s) { return s.gf; }
-template <> __device__ __forceinline__ SmemGemm<dfloat> &gemm_sm<dfloat>(Smem &s) { return s.gd; }
-template <typename T> __device__ __forceinline__ SmemPanel<T> &panel_sm(Smem &s);
-template <> __device__ __forceinline__ SmemPanel<float> &panel_sm<float>(Smem &s) { return s.pf; }
-template <> __device__ __forceinline__ SmemPanel<dfloat> &panel_sm<dfloat>(Smem &s) { return s.pd; }
-template <typename T> __device__ __forceinline__ SmemSolve<T> &solve_sm(Smem &s);
-template <> __device__ __forceinline__ SmemSolve<float> &solve_sm<float>(Smem &s) { return s.sf; }
-template <> __device__ __forceinline__ SmemSolve<dfloat> &solve_sm<dfloat>(Smem &s) { return s.sd; }
-
-struct SmemCtl {
-    int idx;
-    int done;
-    int cmax_bits;
-    unsigned long long rn[MAXRHS], xn[MAXRHS], bn[MAXRHS];
-    unsigned long long anorm;
-    double eta, eta_prev;
-    float min_piv, max_piv, max_u;
-    long long breakdown;
-};
-
-__device__ __forceinline__ float circ_at(const float *g, int64_t n, int64_t d) {
-    d %= n;
-    if (d < 0) d += n;
-    return g[d];
-}
-
-__device__ __forceinline__ void smax_u64(unsigned long long *p, double v) {
-    atomicMax(p, (unsigned long long)__double_as_longlong(v));
-}
-
-
-// C = alpha * A * B + beta * C for one CTA in T arithmetic; B is dense (ldb)
-// or, when g is non-null, the circulant B[k][j] = g[(k - j) mod gn].
-template <typename TA, typename TB, typename T>
-__device__ void cta_gemm(int m, int n, int k, T alpha, const TA *A, int64_t lda, const TB *B, int64_t ldb,
-                         const float *g, int64_t gn, T beta, T *C, int64_t ldc, SmemGemm<T> &sm) {
-    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    for (int i0 = 0; i0 < m; i0 += TL)
-        for (int j0 = 0; j0 < n; j0 += TL) {
-            T acc[4][4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-            for (int k0 = 0; k0 < k; k0 += KS) {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int lin = tid + e * BT;
-                    const int r = lin / KS, kk = lin % KS;
-                    const int gr = i0 + r, gk = k0 + kk;
-                    sm.As[kk][r] = (gr < m && gk < k) ? (T)A[(int64_t)gr * lda + gk] : T(0);
-                    const int kk2 = lin / TL, c = lin % TL;
-                    const int gk2 = k0 + kk2, gc = j0 + c;
-                    T b = T(0);
-                    if (gk2 < k && gc < n) b = g ? (T)circ_at(g, gn, (int64_t)gk2 - gc) : (T)B[(int64_t)gk2 * ldb + gc];
-                    sm.Bs[kk2][c] = b;
-                }
-                __syncthreads();
-#pragma unroll
-                for (int kk = 0; kk < KS; ++kk) {
-                    T a[4], b[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) a[i] = sm.As[kk][ty * 4 + i];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) b[j] = sm.Bs[kk][tx * 4 + j];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-                }
-                __syncthreads();
-            }
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int r = i0 + ty * 4 + i;
-                if (r >= m) continue;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int c = j0 + tx * 4 + j;
-                    if (c >= n) continue;
-                    T v = alpha * acc[i][j];
-                    if (beta != T(0)) v = fma(beta, C[(int64_t)r * ldc + c], v);
-                    C[(int64_t)r * ldc + c] = v;
-                }
-            }
-        }
-}
-
-// Unblocked GENP of the kb x kb diagonal block at (k0, k0) in shared memory.
-template <typename T>
-__device__ void panel(T *C, int64_t ldc, int k0, int kb, SmemPanel<T> &p, SmemCtl &ctl) {
-    const int tid = threadIdx.x;
-    for (int idx = tid; idx < kb * kb; idx += BT) p.a[idx / kb][idx % kb] = C[(int64_t)(k0 + idx / kb) * ldc + k0 + idx % kb];
-    __syncthreads();
-    for (int k = 0; k < kb; ++k) {
-        const T piv = p.a[k][k];
-        if (tid == 0) {
-            const float ap = (float)fabs((double)piv);
-            if (!(ap > 0.f) || !isfinite(ap)) {
-                if (ctl.breakdown < 0) ctl.breakdown = k0 + k;
-            } else {
-                ctl.min_piv = fminf(ctl.min_piv, ap);
-                ctl.max_piv = fmaxf(ctl.max_piv, ap);
-            }
-        }
-        for (int i = k + 1 + tid; i < kb; i += BT) p.a[i][k] = p.a[i][k] / piv;
-        __syncthreads();
-        const int rem = kb - k - 1;
-        for (int idx = tid; idx < rem * rem; idx += BT) {
-            const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
-            p.a[i][j] = fma(-p.a[i][k], p.a[k][j], p.a[i][j]);
-        }
-        __syncthreads();
-    }
-    float um = 0.f;
-    for (int idx = tid; idx < kb * kb; idx += BT) {
-        const int i = idx / kb, j = idx % kb;
-        C[(int64_t)(k0 + i) * ldc + k0 + j] = p.a[i][j];
-        if (j >= i) um = fmaxf(um, (float)fabs((double)p.a[i][j]));
-    }
-    for (int o = 16; o > 0; o >>= 1) um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, o));
-    if ((tid & 31) == 0) atomicMax((int *)&ctl.max_u, __float_as_int(um));
-    __syncthreads();
-}
-
-// U12 = L11^{-1} C12 by forward substitution (L11 unit lower in p.a), in
-// place, chunks of TL columns; tracks max |U12| in um.
-template <typename T>
-__device__ void trsm_left(T *C, int64_t ldc, int k0, int kb, int c0, int n, SmemPanel<T> &p, float &um) {
-    const int tid = threadIdx.x;
-    for (int cc = c0; cc < n; cc += TL) {
-        const int w = min(TL, n - cc);
-        for (int idx = tid; idx < kb * w; idx += BT) p.x[idx % w][idx / w] = C[(int64_t)(k0 + idx / w) * ldc + cc + idx % w];
-        __syncthreads();
-        for (int k = 0; k + 1 < kb; ++k) {
-            const int rem = kb - k - 1;
-            for (int idx = tid; idx < rem * w; idx += BT) {
-                const int r = k + 1 + idx / w, c = idx % w;
-                p.x[c][r] = fma(-p.a[r][k], p.x[c][k], p.x[c][r]);
-            }
-            __syncthreads();
-        }
-        for (int idx = tid; idx < kb * w; idx += BT) {
-            const T v = p.x[idx % w][idx / w];
-            C[(int64_t)(k0 + idx / w) * ldc + cc + idx % w] = v;
-            um = fmaxf(um, (float)fabs((double)v));
-        }
-        __syncthreads();
-    }
-}
-
-// L21 = C21 U11^{-1} by substitution along each row (U11 upper in p.a), in
-// place, chunks of TL rows.
-template <typename T>
-__device__ void trsm_right(T *C, int64_t ldc, int k0, int kb, int r0, int n, SmemPanel<T> &p) {
-    const int tid = threadIdx.x;
-    for (int rr = r0; rr < n; rr += TL) {
-        const int h = min(TL, n - rr);
-        for (int idx = tid; idx < h * kb; idx += BT) p.x[idx / kb][idx % kb] = C[(int64_t)(rr + idx / kb) * ldc + k0 + idx % kb];
-        __syncthreads();
-        for (int j = 0; j < kb; ++j) {
-            for (int r = tid; r < h; r += BT) p.x[r][j] = p.x[r][j] / p.a[j][j];
-            __syncthreads();
-            const int rem = kb - j - 1;
-            for (int idx = tid; idx < h * rem; idx += BT) {
-                const int r = idx / rem, l = j + 1 + idx % rem;
-                p.x[r][l] = fma(-p.x[r][j], p.a[j][l], p.x[r][l]);
-            }
-            __syncthreads();
-        }
-        for (int idx = tid; idx < h * kb; idx += BT) C[(int64_t)(rr + idx / kb) * ldc + k0 + idx % kb] = p.x[idx / kb][idx % kb];
-        __syncthreads();
-    }
-}
-
-template <typename T>
-__device__ void factor_sys(T *C, int n, int nb, Smem &sm, SmemCtl &ctl) {
-    float um = 0.f;
-    for (int k0 = 0; k0 < n; k0 += nb) {
-        const int kb = min(nb, n - k0);
-        panel<T>(C, n, k0, kb, panel_sm<T>(sm), ctl);
-        const int rem = n - k0 - kb;
-        if (rem <= 0) break;
-        trsm_left<T>(C, n, k0, kb, k0 + kb, n, panel_sm<T>(sm), um);
-        trsm_right<T>(C, n, k0, kb, k0 + kb, n, panel_sm<T>(sm));
-        cta_gemm<T, T, T>(rem, rem, kb, T(-1), C + (int64_t)(k0 + kb) * n + k0, n, C + (int64_t)k0 * n + k0 + kb, n,
-                          nullptr, 0, T(1), C + (int64_t)(k0 + kb) * n + k0 + kb, n, gemm_sm<T>(sm));
-        __syncthreads();
-    }
-    for (int o = 16; o > 0; o >>= 1) um = fmaxf(um, __shfl_xor_sync(0xffffffffu, um, o));
-    if ((threadIdx.x & 31) == 0) atomicMax((int *)&ctl.max_u, __float_as_int(um));
-    __syncthreads();
-}
-
-// Y <- op^{-1} Y for the factors in C (n x n), Y n x nr (ld nr), blocked by SB.
-// trans = false: U^{-1} L^{-1} Y.  trans = true: L^{-T} U^{-T} Y.
-template <typename T>
-__device__ void solve_sys(const T *C, int n, T *Y, int nr, bool trans, SmemSolve<T> &s) {
-    const int tid = threadIdx.x;
-    const int nblk = (n + SB - 1) / SB;
-    for (int pass = 0; pass < 2; ++pass) {
-        // pass 0: forward (L, or U^T); pass 1: backward (U, or L^T)
-        const bool unit = trans ? (pass == 1) : (pass == 0);
-        for (int q = 0; q < nblk; ++q) {
-            const int blk = pass == 0 ? q : nblk - 1 - q;
-            const int b0 = blk * SB, bs = min(SB, n - b0);
-            for (int idx = tid; idx < bs * bs; idx += BT) {
-                const int i = idx / bs, j = idx % bs;
-                s.t[i][j] = trans ? C[(int64_t)(b0 + j) * n + b0 + i] : C[(int64_t)(b0 + i) * n + b0 + j];
-            }
-            for (int idx = tid; idx < bs * nr; idx += BT) s.y[idx / nr][idx % nr] = Y[(int64_t)(b0 + idx / nr) * nr + idx % nr];
-            __syncthreads();
-            for (int st = 0; st < bs; ++st) {
-                const int k = pass == 0 ? st : bs - 1 - st;
-                if (!unit) {
-                    if (tid < nr) s.y[k][tid] = s.y[k][tid] / s.t[k][k];
-                    __syncthreads();
-                }
-                const int lo = pass == 0 ? k + 1 : 0, hi = pass == 0 ? bs : k;
-                for (int idx = tid; idx < (hi - lo) * nr; idx += BT) {
-                    const int i = lo + idx / nr, c = idx % nr;
-                    s.y[i][c] = fma(-s.t[i][k], s.y[k][c], s.y[i][c]);
-                }
-                __syncthreads();
-            }
-            for (int idx = tid; idx < bs * nr; idx += BT) Y[(int64_t)(b0 + idx / nr) * nr + idx % nr] = s.y[idx / nr][idx % nr];
-            // update the rows not yet solved with this block's values
-            const int r_lo = pass == 0 ? b0 + bs : 0, r_hi = pass == 0 ? n : b0;
-            for (int i = r_lo + tid; i < r_hi; i += BT) {
-                T acc[MAXRHS];
-                for (int c = 0; c < nr; ++c) acc[c] = T(0);
-                for (int k = 0; k < bs; ++k) {
-                    const T l = trans ? C[(int64_t)(b0 + k) * n + i] : C[(int64_t)i * n + b0 + k];
-                    for (int c = 0; c < nr; ++c) acc[c] = fma(l, s.y[k][c], acc[c]);
-                }
-                for (int c = 0; c < nr; ++c) Y[(int64_t)i * nr + c] -= acc[c];
-            }
-            __syncthreads();
-        }
-    }
-}
-
-// X (+)= G Y (trans = false) or G^T Y, one warp per row.  The product runs in
-// FP32 (Y is a solution or correction of FP32-level accuracy, so FP64 would
-// buy nothing) and is added to X in FP64.
-template <typename TY>
-__device__ void apply_g(const float *G, const float *g, int n, const TY *Y, int nr, double *X, bool accumulate,
-                        bool trans) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = warp; i < n; i += BT / 32) {
-        float acc[MAXRHS];
-        for (int c = 0; c < nr; ++c) acc[c] = 0.f;
-        for (int j = lane; j < n; j += 32) {
-            float gij;
-            if (g) gij = circ_at(g, n, trans ? (int64_t)j - i : (int64_t)i - j);
-            else gij = trans ? G[(int64_t)j * n + i] : G[(int64_t)i * n + j];
-            for (int c = 0; c < nr; ++c) acc[c] = fmaf(gij, (float)Y[(int64_t)j * nr + c], acc[c]);
-        }
-        for (int c = 0; c < nr; ++c) {
-            float v = acc[c];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) X[(int64_t)i * nr + c] = accumulate ? X[(int64_t)i * nr + c] + (double)v : (double)v;
-        }
-    }
-}
-
-// R = B - A X (FP64), column norms into ctl; ||A||_inf too when `anorm`.
-template <typename TA>
-__device__ void residual(const TA *A, int n, const double *B, const double *X, double *R, int nr, bool anorm,
-                         SmemCtl &ctl) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = warp; i < n; i += BT / 32) {
-        double acc[MAXRHS];
-        for (int c = 0; c < nr; ++c) acc[c] = 0.0;
-        double rs = 0.0;
-        for (int j = lane; j < n; j += 32) {
-            const double a = (double)A[(int64_t)i * n + j];
-            rs += fabs(a);
-            for (int c = 0; c < nr; ++c) acc[c] = fma(a, X[(int64_t)j * nr + c], acc[c]);
-        }
-        for (int o = 16; o > 0; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
-        if (anorm && lane == 0) smax_u64(&ctl.anorm, rs);
-        for (int c = 0; c < nr; ++c) {
-            double v = acc[c];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) {
-                const double r = B[(int64_t)i * nr + c] - v;
-                R[(int64_t)i * nr + c] = r;
-                smax_u64(&ctl.rn[c], fabs(r));
-                smax_u64(&ctl.xn[c], fabs(X[(int64_t)i * nr + c]));
-                smax_u64(&ctl.bn[c], fabs(B[(int64_t)i * nr + c]));
-            }
-        }
-    }
-}
-
-// Refinement with the factors in Cf (T arithmetic for the correction solve);
-// `first` computes ||A||_inf and records eta0.  Returns the steps taken.
-template <typename TA, typename T>
-__device__ int refine_loop(const TA *A, const T *Cf, const float *G, const float *g, const double *B, double *X,
-                           double *R, T *Y, int n, int nr, int max_iter, double tol, bool first, double &eta0,
-                           double &eta, Smem &sm, SmemCtl &ctl) {
-    const int tid = threadIdx.x;
-    int it = 0;
-    if (tid == 0) ctl.eta_prev = INFINITY;
-    for (;; ++it) {
-        if (tid < MAXRHS) ctl.rn[tid] = ctl.xn[tid] = ctl.bn[tid] = 0ull;
-        __syncthreads();
-        residual<TA>(A, n, B, X, R, nr, first && it == 0, ctl);
-        __syncthreads();
-        if (tid == 0) {
-            const double an = __longlong_as_double((long long)ctl.anorm);
-            double e = 0.0;
-            for (int c = 0; c < nr; ++c) {
-                double v = __longlong_as_double((long long)ctl.rn[c]) /
-                           (an * __longlong_as_double((long long)ctl.xn[c]) + __longlong_as_double((long long)ctl.bn[c]));
-                if (!(v == v)) v = INFINITY;
-                e = fmax(e, v);
-            }
-            ctl.eta = e;
-            ctl.done = (e <= tol) || (it > 0 && e > 0.5 * ctl.eta_prev) || it >= max_iter;
-            ctl.eta_prev = e;
-        }
-        __syncthreads();
-        eta = ctl.eta;
-        if (first && it == 0) eta0 = eta;
-        if (ctl.done) break;
-        for (int e = tid; e < n * nr; e += BT) Y[e] = (T)R[e];
-        __syncthreads();
-        solve_sys<T>(Cf, n, Y, nr, false, solve_sm<T>(sm));
-        apply_g<T>(G, g, n, Y, nr, X, true, false);
-        __syncthreads();
-    }
-    return it;
-}
-
-template <typename TA>
-__global__ void __launch_bounds__(BT) k_batched(const BatchDesc *d, int count, int *counter, const TA *Apool,
-                                                const double *Bpool, double *Xpool, float *Cpool, const float *Gpool,
-                                                const float *gpool, float *Ypool, double *Rpool, double *scratch64,
-                                                int64_t stride, int nr, int circ, int max_iter, double tol,
-                                                BatchStatus *stat) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    Smem &sm = *reinterpret_cast<Smem *>(smraw);
-    __shared__ SmemCtl ctl;
-    const int tid = threadIdx.x;
-    while (true) {
-        if (tid == 0) ctl.idx = atomicAdd(counter, 1);
-        __syncthreads();
-        const int idx = ctl.idx;
-        if (idx >= count) break;
-        const BatchDesc q = d[idx];
-        const int n = (int)q.n;
-        if (tid == 0) {
-            ctl.breakdown = -1;
-            ctl.min_piv = INFINITY;
-            ctl.max_piv = 0.f;
-            ctl.max_u = 0.f;
-            ctl.anorm = 0ull;
-            ctl.cmax_bits = 0;
-        }
-        __syncthreads();
-        const TA *A = Apool + q.mat_off;
-        float *C = Cpool + q.mat_off;
-        const float *G = circ ? nullptr : Gpool + q.mat_off;
-        const float *g = circ ? gpool + q.g_off : nullptr;
-        const double *B = Bpool + q.vec_off;
-        double *X = Xpool + q.vec_off;
-        float *Y = Ypool + q.vec_off;
-        double *R = Rpool + q.vec_off;
-
-        cta_gemm<TA, float, float>(n, n, n, 1.f, A, n, G, n, g, n, 0.f, C, n, sm.gf);
-        __syncthreads();
-        float cm = 0.f;
-        for (int e = tid; e < n * n; e += BT) cm = fmaxf(cm, fabsf(C[e]));
-        for (int o = 16; o > 0; o >>= 1) cm = fmaxf(cm, __shfl_xor_sync(0xffffffffu, cm, o));
-        if ((tid & 31) == 0) atomicMax(&ctl.cmax_bits, __float_as_int(cm));
-        __syncthreads();
-        factor_sys<float>(C, n, q.nb, sm, ctl);
-
-        for (int e = tid; e < n * nr; e += BT) Y[e] = (float)B[e];
-        __syncthreads();
-        solve_sys<float>(C, n, Y, nr, false, sm.sf);
-        apply_g<float>(G, g, n, Y, nr, X, false, false);
-        __syncthreads();
-
-        double eta0 = -1.0, eta = INFINITY;
-        int it = refine_loop<TA, float>(A, C, G, g, B, X, R, Y, n, nr, max_iter, tol, true, eta0, eta, sm, ctl);
-        int escalated = 0;
-        if (scratch64 && max_iter > 0 && !(eta <= tol)) {
-            // FP32 was not enough: factor A G again in double-float (about 48
-            // bits on the FP32 pipe) and refine with those factors
-            dfloat *Cd = reinterpret_cast<dfloat *>(scratch64 + (int64_t)blockIdx.x * stride);   // n x n
-            dfloat *Yd = Cd + 1024ll * 1024ll;                                                     // n x nr
-            cta_gemm<TA, float, dfloat>(n, n, n, dfloat(1), A, n, G, n, g, n, dfloat(0), Cd, n, sm.gd);
-            __syncthreads();
-            if (tid == 0) ctl.breakdown = -1;
-            __syncthreads();
-            factor_sys<dfloat>(Cd, n, q.nb, sm, ctl);
-            double e0 = 0.0;
-            it += 1 + refine_loop<TA, dfloat>(A, Cd, G, g, B, X, R, Yd, n, nr, max_iter, tol, false, e0, eta, sm, ctl);
-            escalated = 1;
-        }
-        if (tid == 0) {
-            BatchStatus st;
-            st.breakdown_step = ctl.breakdown;
-            st.min_abs_pivot = ctl.min_piv;
-            st.max_abs_pivot = ctl.max_piv;
-            st.max_abs_u = ctl.max_u;
-            st.max_abs_c = __int_as_float(ctl.cmax_bits);
-            st.refine_iters = it;
-            st.status = ctl.breakdown >= 0 ? GENP_ERR_BREAKDOWN : (eta <= tol ? GENP_OK : GENP_ERR_NOCONV);
-            st.escalated = escalated;
-            st.eta0 = eta0;
-            st.eta = eta;
-            stat[idx] = st;
-        }
-        __syncthreads();
-    }
-}
-
-// Y (float) = G^T V (FP64 accumulation; one thread per output row i,
-// coalesced over i).
-template <typename TV>
-__device__ void apply_gt_f(const float *G, const float *g, int n, const TV *V, int nr, float *Y) {
-    for (int i = threadIdx.x; i < n; i += BT) {
-        double acc[MAXRHS];
-        for (int c = 0; c < nr; ++c) acc[c] = 0.0;
-        for (int j = 0; j < n; ++j) {
-            const double gji = (double)(g ? circ_at(g, n, (int64_t)j - i) : G[(int64_t)j * n + i]);
-            for (int c = 0; c < nr; ++c) acc[c] = fma(gji, (double)V[(int64_t)j * nr + c], acc[c]);
-        }
-        for (int c = 0; c < nr; ++c) Y[(int64_t)i * nr + c] = (float)acc[c];
-    }
-}
-
-// Adjoint of every system: Lambda = A^{-T} gX = L^{-T} U^{-T} G^T gX with the
-// FP32 factors, refined in FP64 (R = gX - A^T Lambda, Lambda += A^{-T} R)
-// like the forward solve; dB = Lambda, dA = -Lambda X^T (FP32 output).
-template <typename TA>
-__global__ void __launch_bounds__(BT) k_batched_adjoint(const BatchDesc *d, int count, int *counter, const TA *Apool,
-                                                        const float *Cpool, const float *Gpool, const float *gpool,
-                                                        const double *gXpool, const double *Xpool, float *Ypool,
-                                                        double *Lpool, double *Rpool, double *dBpool, float *dApool,
-                                                        int nr, int circ, int max_iter, double tol) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    Smem &sm = *reinterpret_cast<Smem *>(smraw);
-    __shared__ SmemCtl ctl;
-    const int tid = threadIdx.x;
-    while (true) {
-        if (tid == 0) ctl.idx = atomicAdd(counter, 1);
-        __syncthreads();
-        const int idx = ctl.idx;
-        if (idx >= count) break;
-        const BatchDesc q = d[idx];
-        const int n = (int)q.n;
-        const TA *A = Apool + q.mat_off;
-        const float *C = Cpool + q.mat_off;
-        const float *G = circ ? nullptr : Gpool + q.mat_off;
-        const float *g = circ ? gpool + q.g_off : nullptr;
-        const double *gX = gXpool + q.vec_off;
-        const double *X = Xpool + q.vec_off;
-        float *Y = Ypool + q.vec_off;
-        double *Lam = Lpool + q.vec_off;
-        double *R = Rpool + q.vec_off;
-        apply_gt_f<double>(G, g, n, gX, nr, Y);
-        __syncthreads();
-        solve_sys<float>(C, n, Y, nr, true, sm.sf);
-        for (int e = tid; e < n * nr; e += BT) Lam[e] = (double)Y[e];
-        if (tid == 0) {
-            ctl.eta_prev = INFINITY;
-            ctl.anorm = 0ull;
-        }
-        __syncthreads();
-        for (int it = 0;; ++it) {
-            if (tid < MAXRHS) ctl.rn[tid] = ctl.xn[tid] = ctl.bn[tid] = 0ull;
-            __syncthreads();
-            // R = gX - A^T Lam: one thread per column i of A (coalesced over i)
-            for (int i = tid; i < n; i += BT) {
-                double acc[MAXRHS];
-                for (int c = 0; c < nr; ++c) acc[c] = 0.0;
-                double cs = 0.0;
-                for (int j = 0; j < n; ++j) {
-                    const double a = (double)A[(int64_t)j * n + i];
-                    cs += fabs(a);
-                    for (int c = 0; c < nr; ++c) acc[c] = fma(a, Lam[(int64_t)j * nr + c], acc[c]);
-                }
-                if (it == 0) smax_u64(&ctl.anorm, cs);
-                for (int c = 0; c < nr; ++c) {
-                    const double r = gX[(int64_t)i * nr + c] - acc[c];
-                    R[(int64_t)i * nr + c] = r;
-                    smax_u64(&ctl.rn[c], fabs(r));
-                    smax_u64(&ctl.xn[c], fabs(Lam[(int64_t)i * nr + c]));
-                    smax_u64(&ctl.bn[c], fabs(gX[(int64_t)i * nr + c]));
-                }
-            }
-            __syncthreads();
-            if (tid == 0) {
-                const double an = __longlong_as_double((long long)ctl.anorm);
-                double e = 0.0;
-                for (int c = 0; c < nr; ++c) {
-                    double v = __longlong_as_double((long long)ctl.rn[c]) /
-                               (an * __longlong_as_double((long long)ctl.xn[c]) + __longlong_as_double((long long)ctl.bn[c]));
-                    if (!(v == v)) v = INFINITY;
-                    e = fmax(e, v);
-                }
-                ctl.done = (e <= tol) || (it > 0 && e > 0.5 * ctl.eta_prev) || it >= max_iter;
-                ctl.eta_prev = e;
-            }
-            __syncthreads();
-            if (ctl.done) break;
-            apply_gt_f<double>(G, g, n, R, nr, Y);
-            __syncthreads();
-            solve_sys<float>(C, n, Y, nr, true, sm.sf);
-            for (int e = tid; e < n * nr; e += BT) Lam[e] += (double)Y[e];
-            __syncthreads();
-        }
-        if (dBpool)
-            for (int e = tid; e < n * nr; e += BT) dBpool[q.vec_off + e] = Lam[e];
-        if (dApool) {
-            float *dA = dApool + q.mat_off;
-            for (int e = tid; e < n * n; e += BT) {
-                const int i = e / n, j = e % n;
-                double s = 0.0;
-                for (int c = 0; c < nr; ++c) s = fma(Lam[(int64_t)i * nr + c], X[(int64_t)j * nr + c], s);
-                dA[e] = (float)(-s);
-            }
-        }
-        __syncthreads();
-    }
-}
+int rhs_class(int nr) { return nr <= 1 ? 1 : nr <= 2 ? 2 : nr <= 4 ? 4 : nr <= 8 ? 8 : 16; }
 
 }  // namespace
 
-size_t batched_smem() { return sizeof(Smem); }
-
-int batched_blocks_per_sm() {
-    int b = 1;
-    cudaFuncSetAttribute(k_batched<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-    cudaFuncSetAttribute(k_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-    cudaFuncSetAttribute(k_batched_adjoint<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-    cudaFuncSetAttribute(k_batched_adjoint<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batched<double>, BT, sizeof(Smem)) != cudaSuccess) {
-        cudaGetLastError();
-        b = 1;
+int batched_blocks_per_sm(int nr, int nmax) {
+    switch (rhs_class(nr)) {
+        case 1: return batched_blocks_per_sm_r1(nmax);
+        case 2: return batched_blocks_per_sm_r2(nmax);
+        case 4: return batched_blocks_per_sm_r4(nmax);
+        case 8: return batched_blocks_per_sm_r8(nmax);
+        default: return batched_blocks_per_sm_r16(nmax);
     }
-    return b < 1 ? 1 : b;
 }
 
-// 8-byte elements of the per-CTA escalation scratch (C as double-float: n^2
-// for n <= 1024; Y: n x 16 follows it).
-int64_t batched_scratch_stride() { return 1024ll * 1024ll + 1024ll * MAXRHS; }
-
-cudaError_t launch_batched(const BatchDesc *d, int count, int *counter, const void *Apool, bool a_f64,
-                           const double *Bpool, double *Xpool, float *Cpool, const float *Gpool, const float *gpool,
-                           float *Ypool, double *Rpool, double *scratch64, int nr, bool circ, int max_iter, double tol,
-                           BatchStatus *stat, int grid, cudaStream_t s) {
-    const size_t sm = sizeof(Smem);
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
-    if (e != cudaSuccess) return e;
-    const int64_t stride = batched_scratch_stride();
-    note_launch();
-    if (a_f64)
-        k_batched<double><<<grid, BT, sm, s>>>(d, count, counter, (const double *)Apool, Bpool, Xpool, Cpool, Gpool,
-                                               gpool, Ypool, Rpool, scratch64, stride, nr, circ ? 1 : 0, max_iter, tol,
-                                               stat);
-    else
-        k_batched<float><<<grid, BT, sm, s>>>(d, count, counter, (const float *)Apool, Bpool, Xpool, Cpool, Gpool,
-                                              gpool, Ypool, Rpool, scratch64, stride, nr, circ ? 1 : 0, max_iter, tol,
-                                              stat);
-    return cudaGetLastError();
+// The Krylov copy of C, L^{-1} and U^{-1} (np^2 each), the basis
+// ((K + 1) np NR), then the FP64 residual, last accepted x and its residual
+// (np NR doubles each), np = nmax rounded up to 4 (16-byte offsets).
+int64_t batched_scratch_stride(int nr, int nmax) {
+    const int64_t NR = rhs_class(nr), np = (nmax + 3) & ~3;
+    return 3 * np * np + (int64_t)(kBatchedKrylov + 1) * np * NR + 3 * 2 * np * NR;
 }
 
-cudaError_t launch_batched_adjoint(const BatchDesc *d, int count, int *counter, const void *Apool, bool a_f64,
-                                   const float *Cpool, const float *Gpool, const float *gpool, const double *gXpool,
-                                   const double *Xpool, float *Ypool, double *Lpool, double *Rpool, double *dBpool,
-                                   float *dApool, int nr, bool circ, int max_iter, double tol, int grid,
-                                   cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+cudaError_t launch_batched(BatchedArgs a, int grid, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
+    a.stride = batched_scratch_stride(a.nr, a.nmax);
     note_launch();
-    if (a_f64)
-        k_batched_adjoint<double><<<grid, BT, sizeof(Smem), s>>>(d, count, counter, (const double *)Apool, Cpool,
-                                                                  Gpool, gpool, gXpool, Xpool, Ypool, Lpool, Rpool,
-                                                                  dBpool, dApool, nr, circ ? 1 : 0, max_iter, tol);
-    else
-        k_batched_adjoint<float><<<grid, BT, sizeof(Smem), s>>>(d, count, counter, (const float *)Apool, Cpool,
-                                                                 Gpool, gpool, gXpool, Xpool, Ypool, Lpool, Rpool,
-                                                                 dBpool, dApool, nr, circ ? 1 : 0, max_iter, tol);
-    return cudaGetLastError();
+    switch (rhs_class(a.nr)) {
+        case 1: return batched_launch_r1(a, grid, s);
+        case 2: return batched_launch_r2(a, grid, s);
+        case 4: return batched_launch_r4(a, grid, s);
+        case 8: return batched_launch_r8(a, grid, s);
+        default: return batched_launch_r16(a, grid, s);
+    }
+}
+
+cudaError_t launch_batched_adjoint(BatchedArgs a, int grid, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    a.stride = batched_scratch_stride(a.nr, a.nmax);
+    note_launch();
+    switch (rhs_class(a.nr)) {
+        case 1: return batched_adjoint_r1(a, grid, s);
+        case 2: return batched_adjoint_r2(a, grid, s);
+        case 4: return batched_adjoint_r4(a, grid, s);
+        case 8: return batched_adjoint_r8(a, grid, s);
+        default: return batched_adjoint_r16(a, grid, s);
+    }
 }
 
 }  // namespace genp

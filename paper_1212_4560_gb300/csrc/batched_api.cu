@@ -2,9 +2,10 @@
 //
 // The plan lays the caller's pools out back to back in the caller's order,
 // sorts the work queue by size (largest first: longest-processing-time
-// scheduling over the persistent CTAs), picks a factorization block size per
-// size class (optionally timed on this GPU) and allocates every workspace,
-// so a run only enqueues two kernels and a memset.
+// scheduling over the persistent CTAs), picks the CTA GEMM tile per size
+// class (optionally timed on this GPU) and allocates every workspace, so a
+// run only enqueues the multiplier draw, a memset and the batched kernel
+// (plus the escalation kernel when the plan has it).
 #include "genp_internal.cuh"
 
 #include <math.h>
@@ -28,16 +29,18 @@ struct genp_batched_plan {
     genp_prec a_prec = GENP_FP64;
     int max_iter = 0;
     double tol = 0.0;
-    int grid = 0;
+    int grid = 0, esc_grid = 0, nmax = 0;
     std::vector<int64_t> n, mat_off, vec_off;
-    int nb_class[3] = {32, 32, 64};   // n <= 64, n <= 256, n <= 1024
+    int tile_class[3] = {64, 64, 128};   // CTA GEMM tile for n <= 64, n <= 256, n <= 1024
     BatchDesc *desc = nullptr;
-    int *counter = nullptr;
+    int *counter = nullptr;              // [0] main queue, [1] escalation queue
     BatchStatus *stat = nullptr;
-    float *C = nullptr, *G = nullptr, *g = nullptr, *Y = nullptr;
-    double *R = nullptr;
-    double *L = nullptr;               // adjoint Lambda, FP64, vector-pool layout
-    double *scratch64 = nullptr;       // FP64 escalation scratch, grid x batched_scratch_stride()
+    float *C = nullptr, *G = nullptr, *g = nullptr;
+    float *scratch = nullptr;            // per-CTA scratch, grid x batched_scratch_stride()
+    double *R = nullptr;                 // escalation residuals, FP64, vector-pool layout
+    double *L = nullptr;                 // adjoint Lambda, FP64, vector-pool layout
+    double *scratch64 = nullptr;         // escalation scratch, esc_grid x batched_escalate_stride()
+    unsigned long long *prof = nullptr;  // phase profile, grid x kBatchedPhases (when enabled)
     bool have_factors = false;
 };
 
@@ -50,7 +53,7 @@ std::map<std::string, int> g_tune;   // per-process tuning results
 
 std::string tune_key(int cls, int64_t nrhs, genp_mult_kind kind, genp_prec a_prec) {
     char b[128];
-    snprintf(b, sizeof b, "sm_103a/class%d/rhs%lld/kind%d/a%d", cls, (long long)nrhs, (int)kind, (int)a_prec);
+    snprintf(b, sizeof b, "sm_103a/tile/class%d/rhs%lld/kind%d/a%d", cls, (long long)nrhs, (int)kind, (int)a_prec);
     return b;
 }
 
@@ -81,10 +84,11 @@ void free_plan(genp_batched_plan *P) {
     cudaFree(P->C);
     cudaFree(P->G);
     cudaFree(P->g);
-    cudaFree(P->Y);
+    cudaFree(P->scratch);
     cudaFree(P->R);
     cudaFree(P->L);
     cudaFree(P->scratch64);
+    cudaFree(P->prof);
     delete P;
 }
 
@@ -120,7 +124,7 @@ cudaError_t upload_desc(genp_batched_plan *P, cudaStream_t s) {
         d.vec_off = P->vec_off[i];
         d.g_off = g_off[i];
         d.sid = i;
-        d.nb = P->nb_class[size_class(P->n[i])];
+        d.nb = P->tile_class[size_class(P->n[i])];
         h[q] = d;
     }
     cudaError_t e = cudaMemcpyAsync(P->desc, h.data(), h.size() * sizeof(BatchDesc), cudaMemcpyHostToDevice, s);
@@ -128,15 +132,38 @@ cudaError_t upload_desc(genp_batched_plan *P, cudaStream_t s) {
     return e;
 }
 
-// Times the candidate block sizes of one size class on a synthetic batch of
+BatchedArgs run_args(genp_batched_plan *P, const void *A, bool a64, const double *B, double *X) {
+    BatchedArgs a{};
+    a.desc = P->desc;
+    a.count = (int)P->count;
+    a.counter = P->counter;
+    a.A = A;
+    a.a64 = a64 ? 1 : 0;
+    a.B = B;
+    a.X = X;
+    a.C = P->C;
+    a.G = P->G;
+    a.g = P->g;
+    a.scratch = P->scratch;
+    a.nmax = P->nmax;
+    a.nr = (int)P->nrhs;
+    a.circ = P->kind == GENP_MULT_CIRCULANT ? 1 : 0;
+    a.max_iter = P->max_iter;
+    a.tol = P->tol;
+    a.stat = P->stat;
+    a.prof = P->prof;
+    return a;
+}
+
+// Times the candidate tiles of one size class on a synthetic batch of
 // systems of that class's median order (A = the class's drawn multipliers,
-// which are as good a matrix as any for timing).
+// which are as good a matrix as any for timing; no refinement).
 int tune_class(genp_batched_plan *P, int cls, cudaStream_t s) {
-    static const int cand[3][3] = {{16, 32, 0}, {16, 32, 64}, {32, 64, 0}};
+    static const int cand[2] = {64, 128};
     std::vector<int64_t> ns;
     for (int64_t v : P->n)
         if (size_class(v) == cls) ns.push_back(v);
-    if (ns.empty()) return P->nb_class[cls];
+    if (ns.empty() || cls == 0) return P->tile_class[cls];
     std::sort(ns.begin(), ns.end());
     const int64_t nm = ns[ns.size() / 2];
     const int reps = (int)std::min<int64_t>(2 * (int64_t)P->grid, std::max<int64_t>((int64_t)ns.size(), 152));
@@ -146,6 +173,7 @@ int tune_class(genp_batched_plan *P, int cls, cudaStream_t s) {
     T.kind = P->kind;
     T.a_prec = GENP_FP32;
     T.grid = P->grid;
+    T.nmax = P->nmax;
     T.n.assign(reps, nm);
     for (int64_t i = 0; i <= reps; ++i) {
         T.mat_off.push_back(i * nm * nm);
@@ -154,47 +182,52 @@ int tune_class(genp_batched_plan *P, int cls, cudaStream_t s) {
     const size_t mats = (size_t)reps * nm * nm, vecs = (size_t)reps * nm * P->nrhs;
     float *A = nullptr;
     double *B = nullptr, *X = nullptr;
-    int best = P->nb_class[cls];
-    if (!dmalloc(&A, mats) || !dmalloc(&B, vecs) || !dmalloc(&X, vecs) || !dmalloc(&T.desc, reps) ||
-        !dmalloc(&T.counter, 1) || !dmalloc(&T.stat, reps) || !dmalloc(&T.C, mats) || !dmalloc(&T.G, mats) ||
-        !dmalloc(&T.g, (size_t)reps * nm) || !dmalloc(&T.Y, vecs) || !dmalloc(&T.R, vecs)) {
+    int best = P->tile_class[cls];
+    auto release = [&]() {
         cudaFree(A); cudaFree(B); cudaFree(X);
         cudaFree(T.desc); cudaFree(T.counter); cudaFree(T.stat); cudaFree(T.C); cudaFree(T.G); cudaFree(T.g);
-        cudaFree(T.Y); cudaFree(T.R);
+        T.desc = nullptr;
+        T.counter = nullptr;
+        T.stat = nullptr;
+        T.C = T.G = T.g = nullptr;
+    };
+    if (!dmalloc(&A, mats) || !dmalloc(&B, vecs) || !dmalloc(&X, vecs) || !dmalloc(&T.desc, reps) ||
+        !dmalloc(&T.counter, 2) || !dmalloc(&T.stat, reps) || !dmalloc(&T.C, mats) || !dmalloc(&T.G, mats) ||
+        !dmalloc(&T.g, (size_t)reps * nm)) {
+        release();
         return best;
     }
+    T.scratch = P->scratch;   // the plan's own per-CTA scratch (same grid, nmax and nrhs)
+    T.prof = nullptr;
+    T.max_iter = 0;
+    T.tol = 0.0;
     cudaMemsetAsync(B, 0, vecs * sizeof(double), s);
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (int c = 0; c < 3; ++c) {
-        const int nb = cand[cls][c];
-        if (!nb) continue;
-        for (int k = 0; k < 3; ++k) T.nb_class[k] = nb;
+    for (int c = 0; c < 2; ++c) {
+        const int ts = cand[c];
+        for (int k = 0; k < 3; ++k) T.tile_class[k] = ts;
         if (upload_desc(&T, s) != cudaSuccess) break;
-        // A: the drawn dense multipliers (plus the identity would not change the cost)
         launch_batch_draw(T.desc, (int)reps, 12345, false, A, T.g, s);
         float ms = 0.f;
         for (int r = 0; r < 2; ++r) {
             cudaEventRecord(e0, s);
-            launch_batched(T.desc, (int)reps, T.counter, A, false, B, X, T.C, A, T.g, T.Y, T.R, nullptr,
-                           (int)P->nrhs, P->kind == GENP_MULT_CIRCULANT, 0, 0.0, T.stat, T.grid, s);
+            launch_batched(run_args(&T, A, false, B, X), T.grid, s);
             cudaEventRecord(e1, s);
             cudaEventSynchronize(e1);
             cudaEventElapsedTime(&ms, e0, e1);
         }
         if (cudaGetLastError() == cudaSuccess && ms < best_ms) {
             best_ms = ms;
-            best = nb;
+            best = ts;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(A); cudaFree(B); cudaFree(X);
-    cudaFree(T.desc); cudaFree(T.counter); cudaFree(T.stat); cudaFree(T.C); cudaFree(T.G); cudaFree(T.g);
-    cudaFree(T.Y); cudaFree(T.R);
-    T.desc = nullptr;
+    T.scratch = nullptr;
+    release();
     return best;
 }
 
@@ -236,12 +269,22 @@ genp_status genp_batched_plan_create(int64_t count, const int64_t *n, int64_t nr
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    P->grid = sms * batched_blocks_per_sm();   // one persistent CTA per resident slot
+    P->nmax = (int)*std::max_element(n, n + count);
+    const int per_sm = batched_blocks_per_sm((int)nrhs, P->nmax);
+    if (per_sm < 1) {
+        cudaGetLastError();
+        free_plan(P);
+        return GENP_ERR_CUDA;
+    }
+    // one persistent CTA per resident slot, no more than there are systems
+    P->grid = (int)std::min<int64_t>((int64_t)sms * per_sm, count);
+    P->esc_grid = escalate ? (int)std::min<int64_t>((int64_t)sms * batched_escalate_blocks_per_sm(), count) : 0;
     const bool circ = kind == GENP_MULT_CIRCULANT;
-    if (!dmalloc(&P->desc, count) || !dmalloc(&P->counter, 1) || !dmalloc(&P->stat, count) ||
+    if (!dmalloc(&P->desc, count) || !dmalloc(&P->counter, 2) || !dmalloc(&P->stat, count) ||
         !dmalloc(&P->C, mo) || (!circ && !dmalloc(&P->G, mo)) || (circ && !dmalloc(&P->g, vo / nrhs)) ||
-        !dmalloc(&P->Y, vo) || !dmalloc(&P->R, vo) || !dmalloc(&P->L, vo) ||
-        (escalate && !dmalloc(&P->scratch64, (size_t)P->grid * batched_scratch_stride()))) {
+        !dmalloc(&P->scratch, (size_t)P->grid * batched_scratch_stride((int)nrhs, P->nmax)) ||
+        !dmalloc(&P->L, vo) || (escalate && !dmalloc(&P->R, vo)) ||
+        (escalate && !dmalloc(&P->scratch64, (size_t)P->esc_grid * batched_escalate_stride()))) {
         free_plan(P);
         return GENP_ERR_NOMEM;
     }
@@ -257,14 +300,14 @@ genp_status genp_batched_plan_create(int64_t count, const int64_t *n, int64_t nr
             const std::string key = tune_key(cls, nrhs, kind, a_prec);
             auto it = g_tune.find(key);
             if (it != g_tune.end()) {
-                P->nb_class[cls] = it->second;
+                P->tile_class[cls] = it->second;
                 continue;
             }
             bool present = false;
             for (int64_t v : P->n) present = present || size_class(v) == cls;
             if (!present) continue;
-            P->nb_class[cls] = tune_class(P, cls, s);
-            g_tune[key] = P->nb_class[cls];
+            P->tile_class[cls] = tune_class(P, cls, s);
+            g_tune[key] = P->tile_class[cls];
             changed = true;
         }
         if (changed) cache_store();
@@ -287,7 +330,7 @@ genp_status genp_batched_layout(const genp_batched_plan *P, int64_t *mat_offsets
 
 int genp_batched_block_size(const genp_batched_plan *P, int64_t n) {
     if (!P || n < 1) return 0;
-    return P->nb_class[size_class(n)];
+    return P->tile_class[size_class(n)];
 }
 
 genp_status genp_batched_run(genp_batched_plan *P, uint64_t seed, const void *A_pool, const double *B_pool,
@@ -295,12 +338,20 @@ genp_status genp_batched_run(genp_batched_plan *P, uint64_t seed, const void *A_
     if (!P || !A_pool || !B_pool || !X_pool) return GENP_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     const bool circ = P->kind == GENP_MULT_CIRCULANT;
+    const bool a64 = P->a_prec == GENP_FP64;
     if (launch_batch_draw(P->desc, (int)P->count, seed, circ, P->G, P->g, s) != cudaSuccess ||
-        launch_batched(P->desc, (int)P->count, P->counter, A_pool, P->a_prec == GENP_FP64, B_pool, X_pool, P->C, P->G,
-                       P->g, P->Y, P->R, P->scratch64, (int)P->nrhs, circ, P->max_iter, P->tol, P->stat, P->grid,
-                       s) != cudaSuccess) {
+        launch_batched(run_args(P, A_pool, a64, B_pool, X_pool), P->grid, s) != cudaSuccess) {
         cudaGetLastError();
         return GENP_ERR_CUDA;
+    }
+    if (P->scratch64 && P->max_iter > 0) {
+        if (cudaMemsetAsync(P->counter + 1, 0, sizeof(int), s) != cudaSuccess ||
+            launch_batched_escalate(P->desc, (int)P->count, P->counter + 1, A_pool, a64, B_pool, X_pool, P->G, P->g,
+                                    P->R, P->scratch64, (int)P->nrhs, circ, P->max_iter, P->tol, P->stat,
+                                    P->esc_grid, s) != cudaSuccess) {
+            cudaGetLastError();
+            return GENP_ERR_CUDA;
+        }
     }
     P->have_factors = true;
     return GENP_OK;
@@ -311,9 +362,12 @@ genp_status genp_batched_adjoint(genp_batched_plan *P, const void *A_pool, const
     if (!P || !A_pool || !gX_pool || !P->have_factors) return GENP_ERR_ARG;
     if (dA_pool && !X_pool) return GENP_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    if (launch_batched_adjoint(P->desc, (int)P->count, P->counter, A_pool, P->a_prec == GENP_FP64, P->C, P->G, P->g,
-                               gX_pool, X_pool, P->Y, P->L, P->R, dB_pool, dA_pool, (int)P->nrhs,
-                               P->kind == GENP_MULT_CIRCULANT, P->max_iter, P->tol, P->grid, s) != cudaSuccess) {
+    BatchedArgs a = run_args(P, A_pool, P->a_prec == GENP_FP64, nullptr, const_cast<double *>(X_pool));
+    a.gX = gX_pool;
+    a.L = P->L;
+    a.dB = dB_pool;
+    a.dA = dA_pool;
+    if (launch_batched_adjoint(a, P->grid, s) != cudaSuccess) {
         cudaGetLastError();
         return GENP_ERR_CUDA;
     }
@@ -321,7 +375,8 @@ genp_status genp_batched_adjoint(genp_batched_plan *P, const void *A_pool, const
 }
 
 genp_status genp_batched_status(const genp_batched_plan *P, int32_t *status, int32_t *iters, double *eta0,
-                                double *eta, double *growth, int32_t *escalated, void *cuda_stream) {
+                                double *eta, double *growth, int32_t *escalated, int32_t *krylov,
+                                void *cuda_stream) {
     if (!P) return GENP_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     std::vector<BatchStatus> h(P->count);
@@ -341,6 +396,7 @@ genp_status genp_batched_status(const genp_batched_plan *P, int32_t *status, int
         if (eta) eta[i] = h[q].eta;
         if (growth) growth[i] = h[q].max_abs_c > 0 ? (double)h[q].max_abs_u / h[q].max_abs_c : 0.0;
         if (escalated) escalated[i] = h[q].escalated;
+        if (krylov) krylov[i] = h[q].krylov_steps;
     }
     return GENP_OK;
 }
@@ -358,6 +414,39 @@ genp_status genp_batched_multipliers(const genp_batched_plan *P, float *G_pool, 
         if (cudaMemcpyAsync(g_pool, P->g, P->vec_off.back() / P->nrhs * sizeof(float), cudaMemcpyDeviceToDevice, s) !=
             cudaSuccess)
             return GENP_ERR_CUDA;
+    }
+    return GENP_OK;
+}
+
+genp_status genp_batched_profile(genp_batched_plan *P, int enable) {
+    if (!P) return GENP_ERR_ARG;
+    if (!enable) {
+        cudaFree(P->prof);
+        P->prof = nullptr;
+        return GENP_OK;
+    }
+    if (!P->prof) {
+        if (!dmalloc(&P->prof, (size_t)P->grid * kBatchedPhases)) return GENP_ERR_NOMEM;
+        if (cudaMemset(P->prof, 0, (size_t)P->grid * kBatchedPhases * sizeof(unsigned long long)) != cudaSuccess)
+            return GENP_ERR_CUDA;
+    }
+    return GENP_OK;
+}
+
+genp_status genp_batched_profile_read(const genp_batched_plan *P, double *cycles, void *cuda_stream) {
+    if (!P || !P->prof || !cycles) return GENP_ERR_ARG;
+    std::vector<unsigned long long> h((size_t)P->grid * kBatchedPhases);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (cudaMemcpyAsync(h.data(), P->prof, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return GENP_ERR_CUDA;
+    }
+    for (int p = 0; p < kBatchedPhases; ++p) {
+        double t = 0.0;
+        for (int b = 0; b < P->grid; ++b) t += (double)h[(size_t)b * kBatchedPhases + p];
+        cycles[p] = t;
     }
     return GENP_OK;
 }

@@ -108,7 +108,7 @@ struct BatchDesc {
     int64_t vec_off;   // offset of its n x nrhs blocks (B, X and workspace pools)
     int64_t g_off;     // offset of its circulant first column (g pool)
     int64_t sid;       // multiplier stream id (the system's index in the caller's order)
-    int nb;            // block size chosen for its size class
+    int nb;            // CTA GEMM tile (64 or 128) chosen for its size class
     int pad;
 };
 
@@ -118,8 +118,8 @@ struct BatchStatus {
     float min_abs_pivot, max_abs_pivot, max_abs_u, max_abs_c;
     int refine_iters;
     int status;
-    int escalated;     // refactored in FP64 after the FP32 refinement stalled
-    int pad;
+    int escalated;     // 0; 1: inner solves switched to substitution; 2: refactored in double-float
+    int krylov_steps;  // inner GMRES steps over all refinement steps
     double eta0, eta;
 };
 
@@ -242,20 +242,59 @@ cudaError_t split_cols_T(const T *src, int64_t lds, int64_t k, int64_t m, __nv_b
                          cudaStream_t s);
 __host__ __device__ inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
-// batched.cu
-size_t batched_smem();
-int batched_blocks_per_sm();
-cudaError_t launch_batched(const BatchDesc *d, int count, int *counter, const void *Apool, bool a_f64,
-                           const double *Bpool, double *Xpool, float *Cpool, const float *Gpool, const float *gpool,
-                           float *Ypool, double *Rpool, double *scratch64, int nr, bool circ, int max_iter, double tol,
-                           BatchStatus *stat, int grid, cudaStream_t s);
-// Doubles of FP64 escalation scratch each persistent CTA needs.
-int64_t batched_scratch_stride();
-cudaError_t launch_batched_adjoint(const BatchDesc *d, int count, int *counter, const void *Apool, bool a_f64,
-                                   const float *Cpool, const float *Gpool, const float *gpool, const double *gXpool,
-                                   const double *Xpool, float *Ypool, double *Lpool, double *Rpool, double *dBpool,
-                                   float *dApool, int nr, bool circ, int max_iter, double tol, int grid,
-                                   cudaStream_t s);
+// Krylov steps per inner GMRES solve of the batched kernel.
+constexpr int kBatchedKrylov = 16;
+
+// Arguments of the batched kernels (batched.cu, batched_impl.cuh).
+struct BatchedArgs {
+    const BatchDesc *desc;
+    int count;
+    int *counter;         // work queue (reset before each launch)
+    const void *A;        // A pool, FP64 (a64) or FP32
+    int a64;
+    const double *B;      // right-hand sides (forward)
+    double *X;            // solutions (forward output; adjoint input)
+    float *C;             // factors, A-pool layout
+    const float *G, *g;   // dense multipliers or circulant first columns
+    float *scratch;       // per-CTA scratch, `stride` floats each
+    int64_t stride;
+    int nmax, nr, circ, max_iter;
+    double tol;
+    BatchStatus *stat;
+    const double *gX;     // adjoint: incoming gradient
+    double *L, *dB;       // adjoint: Lambda (vector-pool layout), dB (may be null)
+    float *dA;            // adjoint: dA (A-pool layout, may be null)
+    unsigned long long *prof;   // optional: per-CTA SM cycles by phase (kBatchedPhases each)
+};
+// Phases of the batched kernel's cycle profile: C = A G, factorization,
+// inverses of the factors, first solve and x = G y, FP64 residuals, inner
+// GMRES, x += G d.
+constexpr int kBatchedPhases = 7;
+// batched.cu (nmax: largest order of the batch; nr: right-hand sides)
+int batched_blocks_per_sm(int nr, int nmax);
+// Floats of scratch each persistent CTA needs.
+int64_t batched_scratch_stride(int nr, int nmax);
+cudaError_t launch_batched(BatchedArgs a, int grid, cudaStream_t s);
+cudaError_t launch_batched_adjoint(BatchedArgs a, int grid, cudaStream_t s);
+// per right-hand-side class NR in {1, 2, 4, 8, 16} (batched_r*.cu)
+#define GENP_BATCHED_DECL(NR)                                                  \
+    int batched_blocks_per_sm_r##NR(int nmax);                                 \
+    cudaError_t batched_launch_r##NR(const BatchedArgs &a, int grid, cudaStream_t s); \
+    cudaError_t batched_adjoint_r##NR(const BatchedArgs &a, int grid, cudaStream_t s);
+GENP_BATCHED_DECL(1)
+GENP_BATCHED_DECL(2)
+GENP_BATCHED_DECL(4)
+GENP_BATCHED_DECL(8)
+GENP_BATCHED_DECL(16)
+#undef GENP_BATCHED_DECL
+// batched_escalate.cu (systems whose status is not GENP_OK after launch_batched)
+int batched_escalate_blocks_per_sm();
+// Doubles of double-float scratch each persistent CTA of the escalation needs.
+int64_t batched_escalate_stride();
+cudaError_t launch_batched_escalate(const BatchDesc *d, int count, int *counter, const void *Apool, bool a_f64,
+                                    const double *Bpool, double *Xpool, const float *Gpool, const float *gpool,
+                                    double *Rpool, double *scratch64, int nr, bool circ, int max_iter, double tol,
+                                    BatchStatus *stat, int grid, cudaStream_t s);
 
 // lu.cu
 cudaError_t factor_run(genp_factors *F, cudaStream_t s);

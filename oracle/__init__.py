@@ -34,6 +34,7 @@ _i64 = ctypes.c_int64
 _u64 = ctypes.c_uint64
 
 KIND_GAUSSIAN, KIND_CIRCULANT, KIND_SPARSE, KIND_CIRCULANT_PM1, KIND_IDENTITY = 0, 1, 2, 3, 4
+KIND_TOEPLITZ, KIND_HOUSEHOLDER_PM1 = 5, 6
 
 
 def lib():
@@ -63,6 +64,11 @@ def lib():
         L.or_circulant_pm1_singular.restype = ctypes.c_int
         L.or_mult_sparse.argtypes = [_i64, ctypes.c_int, _u64, _u64, ctypes.c_void_p, ctypes.c_void_p]
         L.or_circulant_to_dense.argtypes = [_i64, _dp, _dp, _i64]
+        L.or_mult_toeplitz.argtypes = [_i64, _u64, _u64, ctypes.c_double, _dp]
+        L.or_mult_toeplitz_f32.argtypes = [_i64, _u64, _u64, ctypes.c_float, _dp]
+        L.or_toeplitz_to_dense.argtypes = [_i64, _dp, _dp, _i64]
+        L.or_mult_householder_pm1.argtypes = [_i64, _u64, _u64, _dp]
+        L.or_householder_to_dense.argtypes = [_i64, _dp, _dp, _i64]
         L.or_sparse_to_dense.argtypes = [_i64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, _dp, _i64]
         L.or_matmul.argtypes = [_i64, _i64, _i64, _dp, _i64, _dp, _i64, _dp, _i64]
         L.or_genp.argtypes = [_i64, _dp, _i64]
@@ -129,7 +135,10 @@ def multiplier(kind: int, n: int, seed: int, stream: int = 0, scale: float | Non
     """The random multiplier G (Definition 3.2 / Sec. 2.3 / sparse reading).
     Kinds: 0 Gaussian, 1 Gaussian circulant, 2 sparse +-1, 3 circulant with a
     +-1 first column (the paper's test multiplier, Sec. 7.1; redrawn until its
-    power-of-two-order DFT bins are nonzero), 4 the identity (plain GENP).
+    power-of-two-order DFT bins are nonzero), 4 the identity (plain GENP),
+    5 Gaussian Toeplitz (Definition 3.2; ``t`` holds t_{-(n-1)} .. t_{n-1}),
+    6 Householder reflector I - 2 u u^T / n with a +-1 vector ``u`` (the
+    Householder multipliers of Sec. 7.1, read as an orthogonal reflector).
 
     grid "fp64": entries drawn in double precision; "fp32": drawn by the same
     polar method in single precision (scale rounded to float first).
@@ -168,6 +177,28 @@ def multiplier(kind: int, n: int, seed: int, stream: int = 0, scale: float | Non
         return out
     if kind == KIND_IDENTITY:
         return {"kind": kind, "n": n, "G": np.eye(n)}
+    if kind == KIND_TOEPLITZ:
+        s = 1.0 if scale is None else float(scale)
+        t = np.empty(2 * n - 1)
+        if grid == "fp32":
+            L.or_mult_toeplitz_f32(n, seed, stream, float(np.float32(s)), _p(t))
+        else:
+            L.or_mult_toeplitz(n, seed, stream, s, _p(t))
+        out = {"kind": kind, "n": n, "t": t}
+        if n <= 8192:      # products below use the dense matrix (the plain definition)
+            G = np.empty((n, n))
+            L.or_toeplitz_to_dense(n, _p(t), _p(G), n)
+            out["G"] = G
+        return out
+    if kind == KIND_HOUSEHOLDER_PM1:
+        u = np.empty(n)
+        L.or_mult_householder_pm1(n, seed, stream, _p(u))
+        out = {"kind": kind, "n": n, "u": u}
+        if n <= 8192:
+            G = np.empty((n, n))
+            L.or_householder_to_dense(n, _p(u), _p(G), n)
+            out["G"] = G
+        return out
     if kind == KIND_SPARSE:
         rows = np.empty((nnz, n), dtype=np.int32)
         signs = np.empty((nnz, n), dtype=np.int8)
@@ -209,7 +240,7 @@ def precondition(A: np.ndarray, M: dict, rows=None) -> np.ndarray:
     m, n = A.shape
     C = np.empty((m, M["n"]))
     L = lib()
-    if M["kind"] == KIND_GAUSSIAN:
+    if M["kind"] in (KIND_GAUSSIAN, KIND_TOEPLITZ, KIND_HOUSEHOLDER_PM1):
         return matmul(A, M["G"])
     if M["kind"] == KIND_IDENTITY:
         return A.copy()
@@ -227,7 +258,7 @@ def apply_multiplier(M: dict, Y: np.ndarray, trans: bool = False) -> np.ndarray:
     n, nrhs = Y.shape
     X = np.empty_like(Y)
     L = lib()
-    if M["kind"] == KIND_GAUSSIAN:
+    if M["kind"] in (KIND_GAUSSIAN, KIND_TOEPLITZ, KIND_HOUSEHOLDER_PM1):
         return matmul(M["G"].T.copy() if trans else M["G"], Y)
     if M["kind"] == KIND_IDENTITY:
         return Y.copy()

@@ -93,7 +93,15 @@ OR_EXPORT double or_log(double s) {
 
 /* Philox stream layout used for every draw of the method (shared spec, not
  * shared code): key = (seed, stream_id); counter = (index, block, tag, 0). */
-enum { OR_TAG_DENSE = 0x10, OR_TAG_CIRC = 0x11, OR_TAG_PERM = 0x12, OR_TAG_SIGN = 0x13, OR_TAG_CIRC_PM1 = 0x16 };
+enum {
+    OR_TAG_DENSE = 0x10,
+    OR_TAG_CIRC = 0x11,
+    OR_TAG_PERM = 0x12,
+    OR_TAG_SIGN = 0x13,
+    OR_TAG_CIRC_PM1 = 0x16,
+    OR_TAG_TOEP = 0x17,
+    OR_TAG_HOUSE = 0x18
+};
 #define OR_POLAR_BLOCKS 32
 
 /* One standard normal by Marsaglia's polar method: draw (v1, v2) uniform on
@@ -291,6 +299,48 @@ OR_EXPORT void or_mult_sparse(int64_t n, int nnz, uint64_t seed, uint64_t stream
             signs[(int64_t)t * n + j] = (w[0] & 1ULL) ? (int8_t)-1 : (int8_t)1;
         }
     }
+}
+
+/* Gaussian Toeplitz multiplier (Definition 3.2, T_{0,scale}^{n x n}): only
+ * the 2n - 1 entries of the first row and column are independent.  With
+ * d = i - j in [-(n-1), n-1], t[d + n - 1] = scale * z(d + n - 1) on its own
+ * tag, and T[i][j] = t_{i-j}. */
+OR_EXPORT void or_mult_toeplitz(int64_t n, uint64_t seed, uint64_t stream, double scale, double *t) {
+    for (int64_t d = 0; d < 2 * n - 1; ++d) t[d] = or_gauss(seed, stream, OR_TAG_TOEP, (uint64_t)d) * scale;
+}
+
+OR_EXPORT void or_mult_toeplitz_f32(int64_t n, uint64_t seed, uint64_t stream, float scale, double *t) {
+    for (int64_t d = 0; d < 2 * n - 1; ++d)
+        t[d] = (double)(or_gauss_f32(seed, stream, OR_TAG_TOEP + 4, (uint64_t)d) * scale);
+}
+
+OR_EXPORT void or_toeplitz_to_dense(int64_t n, const double *t, double *G, int64_t ldg) {
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) G[i * ldg + j] = t[i - j + n - 1];
+}
+
+/* Householder multiplier with a vector of random signs (the multipliers of
+ * the tests the paper cites in Sec. 7.1).  The printed form I - u v^T/(u^T v)
+ * is a projection (singular); this is the orthogonal reflector
+ * H = I - 2 u u^T / (u^T u) with u^T u = n: u_i = +-1 from the low bit of
+ * Philox word 0 at counter (i, 0, tag, 0). */
+OR_EXPORT void or_mult_householder_pm1(int64_t n, uint64_t seed, uint64_t stream, double *u) {
+    uint64_t key[2] = {seed, stream};
+    for (int64_t i = 0; i < n; ++i) {
+        uint64_t ctr[4] = {(uint64_t)i, 0, OR_TAG_HOUSE, 0}, w[4];
+        or_philox4x64_10(ctr, key, w);
+        u[i] = (w[0] & 1ull) ? -1.0 : 1.0;
+    }
+}
+
+/* H[i][j] = delta_ij - 2 u_i u_j / n. */
+OR_EXPORT void or_householder_to_dense(int64_t n, const double *u, double *G, int64_t ldg) {
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            double v = 2.0 * u[i] * u[j];
+            v = v / (double)n;
+            G[i * ldg + j] = (i == j ? 1.0 : 0.0) - v;
+        }
 }
 
 /* Expand a circulant first column into the full n x n matrix. */

@@ -393,7 +393,7 @@ def test_residual_and_backward_error_formula():
 
 # ---------------------------------------------------------------- the method
 
-@pytest.mark.parametrize("kind", [0, 1, 2])
+@pytest.mark.parametrize("kind", [0, 1, 2, 5])
 def test_leading_singular_system_solved(kind):
     """The n=256 workload (leading 32 x 32 block of rank 16): without the
     multiplier GENP's growth is catastrophic; with it the solve reaches a
@@ -520,3 +520,107 @@ def test_identity_multiplier_is_plain_genp():
     C = oracle.precondition(A, M)
     assert np.array_equal(C, A)
     assert np.array_equal(oracle.apply_multiplier(M, B), B)
+
+
+# ------------------------------------------------ Toeplitz and Householder
+
+@pytest.mark.parametrize("n", [1, 2, 7, 33])
+def test_toeplitz_structure_vs_scipy(n):
+    """Definition 3.2 (T_{0,sigma}): the matrix is scipy's Toeplitz matrix of
+    its first column t_0 .. t_{n-1} and first row t_0, t_{-1} .. t_{-(n-1)};
+    the 2n - 1 draws are distinct."""
+    M = oracle.multiplier(5, n, seed=11, scale=0.5)
+    t, G = M["t"], M["G"]
+    assert t.shape == (2 * n - 1,)
+    ref = sla.toeplitz(t[n - 1:], t[n - 1::-1])
+    assert np.array_equal(G, ref)
+    assert len(np.unique(t)) == 2 * n - 1
+    if n > 1:
+        assert G[0, n - 1] != G[1, 0]      # not a circulant: the wrap-around entries differ
+
+
+def test_toeplitz_draws_are_scaled_gaussians():
+    n = 20000
+    t = oracle.multiplier(5, n, seed=2, scale=3.0)["t"]
+    assert abs(t.mean()) < 0.05 * 3.0
+    assert abs(t.std() - 3.0) < 0.03 * 3.0
+    assert st.kstest(t / 3.0, "norm").pvalue > 1e-3
+    t32 = oracle.multiplier(5, 64, seed=2, grid="fp32")["t"]
+    assert np.array_equal(t32.astype(np.float32).astype(np.float64), t32)   # on the FP32 grid
+
+
+def test_toeplitz_products_vs_convolution():
+    """(A T)[r][j] = sum_i a_ri t_{i-j}: each row of A T is a slice of the
+    full linear correlation of the row with t, computed here by numpy's FFT
+    (convolution theorem); x = T y and T^T y likewise."""
+    n, m = 48, 5
+    rng = np.random.default_rng(4)
+    M = oracle.multiplier(5, n, seed=9)
+    t = M["t"]
+    A = rng.standard_normal((m, n))
+    C = oracle.precondition(A, M)
+    L = 4 * n
+    ft = np.fft.rfft(t, L)
+    for r in range(m):
+        # sum_i a_i t_{i-j} = sum_i a_i t[i - j + n - 1] = (a reversed * t)[n - 1 - j + (n - 1)]
+        full = np.fft.irfft(np.fft.rfft(A[r, ::-1], L) * ft, L)
+        ref = np.array([full[(n - 1 - j) + (n - 1)] for j in range(n)])
+        assert np.allclose(C[r], ref, rtol=0, atol=1e-12 * np.abs(A[r]).sum() * np.abs(t).max())
+    Y = rng.standard_normal((n, 2))
+    X = oracle.apply_multiplier(M, Y)
+    XT = oracle.apply_multiplier(M, Y, trans=True)
+    for c in range(2):
+        full = np.fft.irfft(np.fft.rfft(t, L) * np.fft.rfft(Y[:, c], L), L)   # sum_j t[i - j + n - 1] y_j
+        assert np.allclose(X[:, c], full[n - 1:2 * n - 1], rtol=0, atol=1e-12 * np.abs(Y).sum() * np.abs(t).max())
+        fullT = np.fft.irfft(np.fft.rfft(t[::-1], L) * np.fft.rfft(Y[:, c], L), L)
+        assert np.allclose(XT[:, c], fullT[n - 1:2 * n - 1], rtol=0,
+                           atol=1e-12 * np.abs(Y).sum() * np.abs(t).max())
+
+
+@pytest.mark.parametrize("n", [2, 8, 64, 256])
+def test_householder_reflector_identities(n):
+    """H = I - 2 u u^T / n with u in {+-1}^n: symmetric, H u = -u, H w = w for
+    w orthogonal to u, H^2 = I (exact for n a power of two: every entry is
+    1 - 2/n or +-2/n), det H = -1."""
+    M = oracle.multiplier(6, n, seed=3)
+    u, H = M["u"], M["G"]
+    assert set(np.unique(u).tolist()) <= {-1.0, 1.0}
+    assert np.array_equal(H, H.T)
+    assert np.array_equal(H @ u, -u)
+    assert np.array_equal(H @ H, np.eye(n))
+    w = np.zeros(n)
+    i = int(np.argmax(u > 0)) if (u > 0).any() else 0
+    j = int(np.argmax(u < 0)) if (u < 0).any() else 1
+    if u[i] != u[j]:
+        w[i], w[j] = 1.0, 1.0            # u^T w = 0
+        assert np.array_equal(H @ w, w)
+    sign, logdet = np.linalg.slogdet(H)
+    assert sign == -1.0 and abs(logdet) < 1e-12
+    assert np.array_equal(oracle.precondition(np.eye(n), M), H)
+    assert np.array_equal(oracle.apply_multiplier(M, np.eye(n), trans=True), H)
+
+
+def test_householder_signs_balanced():
+    u = oracle.multiplier(6, 100000, seed=1)["u"]
+    assert abs(u.mean()) < 0.02
+
+
+def test_householder_repairs_rank_one_deficiency_only():
+    """A H = A - (2/n)(A u) u^T changes A by rank one.  On the paper-shaped
+    inputs (leading n/2 x n/2 block of numerical rank n/2 - 1, the kind of
+    matrices the cited Householder tests used) it repairs GENP and the solve
+    reaches eta <= 1e-14; on the workload whose leading 32 x 32 block has
+    rank 16 no rank-one change can, and the growth stays catastrophic."""
+    A, X, B = (t.numpy() for t in W.table71(128, 3))
+    LU0, k0 = oracle.genp(A)
+    plain = oracle.backward_error(A, oracle.lu_solve(LU0, B), B) if k0 < 0 else np.inf
+    M = oracle.multiplier(6, 128, seed=5)
+    r = oracle.solve(A, B, M, refine_steps=5, tol=1e-16)
+    assert r["step"] == -1
+    assert r["eta"][-1] <= 1e-14
+    assert r["eta"][0] < plain / 100
+    xd = oracle.gepp_solve(A, B)
+    assert np.abs(r["x"] - xd).max() / np.abs(xd).max() <= 1e-14 * np.linalg.cond(A, np.inf)
+    A2, _, _ = (t.numpy() for t in W.lead_deficient(256, 32, 16, 1, 0))
+    LU, k = oracle.genp(oracle.precondition(A2, oracle.multiplier(6, 256, seed=5)))
+    assert k >= 0 or np.abs(np.triu(LU)).max() / np.abs(A2).max() > 1e10

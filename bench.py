@@ -39,7 +39,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "solves/s & TFLOP/s (2n³/3), BF16+IR vs FP64 GENP, same GB300, bwd err ≤1e-14"
-KINDS = {"gaussian": 0, "circulant": 1, "sparse": 2}
+KINDS = {"gaussian": 0, "circulant": 1, "sparse": 2, "toeplitz": 5, "householder": 6}
 PRECS = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 4, "sliced": 5}
 GRID_OF = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 2, "sliced": 1}   # sliced: G drawn on the FP32 grid
 F64_FACTORS = ("fp64", "sliced")
@@ -75,6 +75,8 @@ def parse():
     p.add_argument("--kappa", type=float, default=1e6, help="condition number of the svd workload")
     p.add_argument("--prec", default="sliced", choices=list(PRECS))
     p.add_argument("--digits", type=int, default=0, help="digits per operand of the sliced precision (5, 6, 7)")
+    p.add_argument("--precond-digits", type=int, default=0,
+                   help="digits per operand of the sliced C = A G (3 .. 7; 0: the library's setting)")
     p.add_argument("--refine", default=None, choices=["classic", "gmres"],
                    help="refinement method (default: classic for fp64, GMRES-IR otherwise)")
     p.add_argument("--max-iter", type=int, default=None)
@@ -102,6 +104,10 @@ def flops_per_solve(a):
         ag = 2.0 * n**3
     elif a.kind == "circulant":
         ag = 2 * 5.0 * n * n * math.log2(n)      # forward + inverse complex FFT per row pair
+    elif a.kind == "toeplitz":
+        ag = 2 * 5.0 * n * (2 * n) * math.log2(2 * n)   # the same on the order-2n circulant embedding
+    elif a.kind == "householder":
+        ag = 4.0 * n * n                         # A u, then the rank-one update
     else:
         ag = 2.0 * 4 * n * n
     return fact, ag
@@ -303,6 +309,8 @@ def run_ours(a):
     prec = PRECS[a.prec]
     if a.digits:
         genp._lib.load().genp_sliced_digits(a.digits)
+    if a.precond_digits:
+        genp._lib.load().genp_sliced_precondition_digits(a.precond_digits)
     cdt = torch.float64 if a.prec in F64_FACTORS else torch.float32
     method = {"classic": 0, "gmres": 1}[a.refine or ("classic" if a.prec == "fp64" else "gmres")]
     max_iter = a.max_iter if a.max_iter is not None else (10 if a.prec == "fp64" or method == 1 else 30)
@@ -479,6 +487,9 @@ def run_ours(a):
             "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "sliced": "bf16"}.get(a.prec, a.prec),
             "data": "synthetic",
             "config": {"workload": workload_name(a), "n": n, "nrhs": nrhs, "multiplier": a.kind, "precision": a.prec,
+                       "digits": {"factor": lib.genp_sliced_digits(0),
+                                  "precondition": lib.genp_sliced_precondition_digits(0)}
+                       if a.prec == "sliced" else None,
                        "A": ("J U diag(sigma) V^T, kappa=%g" % a.kappa) if a.workload == "svd"
                        else "N(0,1) with leading 64x64 block of rank 32",
                        "l2": "inputs larger than L2 (no flush)",

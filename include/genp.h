@@ -76,13 +76,27 @@ typedef enum {
  *               (the sum of g, and the folded sums for every x^m + 1 with
  *               2m | n), complete when n is a power of two.  scale ignored.
  *  IDENTITY:    G = I, i.e. plain GENP of A (no preconditioning), the
- *               paper's comparison point; seed, scale and grid ignored. */
+ *               paper's comparison point; seed, scale and grid ignored.
+ *  TOEPLITZ:    G[i][j] = t_{i-j} with 2n - 1 iid N(0, scale^2) entries
+ *               t_{-(n-1)} .. t_{n-1} (Definition 3.2, T_{0,scale}).  Stored
+ *               as the first column of the circulant of order 2n whose
+ *               leading n x n block is G; products run through its DFT
+ *               (n <= 4096) or directly.
+ *  HOUSEHOLDER_PM1: G = I - 2 u u^T / n with u of random signs +-1, the
+ *               Householder multipliers of the tests cited in Sec. 7.1.  The
+ *               printed form I - u v^T / u^T v is a projection (singular);
+ *               this is the orthogonal reflector.  A rank-one change of A:
+ *               it repairs leading blocks whose rank falls short by one, not
+ *               more.  scale and grid ignored (its entries 1 - 2/n and +-2/n
+ *               are exact in FP32 when n is a power of two). */
 typedef enum {
     GENP_MULT_GAUSSIAN = 0,
     GENP_MULT_CIRCULANT = 1,
     GENP_MULT_SPARSE_PM1 = 2,
     GENP_MULT_CIRCULANT_PM1 = 3,
-    GENP_MULT_IDENTITY = 4
+    GENP_MULT_IDENTITY = 4,
+    GENP_MULT_TOEPLITZ = 5,
+    GENP_MULT_HOUSEHOLDER_PM1 = 6
 } genp_mult_kind;
 
 /* Arithmetic of a factorization.
@@ -102,7 +116,8 @@ typedef enum {
  *        Schur-complement product (and, for a Gaussian multiplier, A G) runs
  *        on the BF16 tensor cores: each FP64 operand row / column gets a
  *        power-of-two scale and is cut into 5, 6 or 7 exact 7-bit digits
- *        (genp_sliced_digits), and the digit products of the leading
+ *        (genp_sliced_digits; A G takes genp_sliced_precondition_digits),
+ *        and the digit products of the leading
  *        weights are accumulated in FP32, all but the smallest weight group
  *        exactly (Ozaki, Ogita, Oishi and Rump's error-free splitting).  With
  *        7 digits the products carry about 46 correct bits against the
@@ -175,7 +190,10 @@ GENP_API genp_status genp_redraw_multiplier(genp_multiplier *G, uint64_t seed, u
 
 /* Copies G's description into caller device buffers (any may be NULL):
  *  dense      n x n (ld ldd) double: the full matrix G (every kind).
- *  first_col  n doubles: g (CIRCULANT only).
+ *  first_col  n doubles: g (CIRCULANT, CIRCULANT_PM1); for TOEPLITZ 2n
+ *             doubles: the first column of its circulant embedding,
+ *             t_0 .. t_{n-1}, 0, t_{-(n-1)} .. t_{-1}; for HOUSEHOLDER_PM1
+ *             n doubles: u.
  *  rows       nnz*n int32: row of the t-th entry of column j at [t*n + j] (SPARSE).
  *  signs      nnz*n int8: its sign (SPARSE). */
 GENP_API genp_status genp_multiplier_export(const genp_multiplier *G, double *dense, int64_t ldd,
@@ -383,7 +401,7 @@ GENP_API genp_status genp_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha
  * double-float, and one rounding to FP64 at the end.  Per entry and chunk
  * the error is about 2^-(7 digits - 1) * 4 * K_c * max_k|a_ik| * max_k|b_kj|
  * at worst (far less for sums with mixed signs); products of integers with
- * |a|, |b| <= 127 are exact for K <= 2^20.  digits: 5, 6, 7 or 0 (the
+ * |a|, |b| <= 127 are exact for K <= 2^20.  digits: 3 to 7, or 0 (the
  * setting of genp_sliced_digits).
  *  A      m x K, ld lda;  B  K x n, ld ldb;  D  m x n, ld ldd.
  *  Allocates its workspace with cudaMallocAsync on the stream.
@@ -399,6 +417,22 @@ GENP_API genp_status genp_gemm_sliced(int64_t m, int64_t n, int64_t K, double al
  * genp_gemm_sliced call of the process and returns the previous one, or -1
  * if digits is not supported.  Not synchronized with concurrent calls. */
 GENP_API int genp_sliced_digits(int digits);
+
+/* Digits per operand of the sliced product C = A G that genp_precondition
+ * forms for a Gaussian multiplier when c_prec is GENP_BF16_SLICED: 3 to 7
+ * (6, 10, 15, 21 or 28 digit products per multiply-add; about 19, 26, 33,
+ * 40 or 47 correct bits on Gaussian data); default 7.  The refinement's
+ * residual b - A x and its update x += G d use A and G in FP64 (Thm. 4.1
+ * allows the product to be perturbed), so the product only has to be as
+ * accurate as the factors it feeds: with GMRES-IR (genp_refine method 1),
+ * which needs the factors only as a preconditioner, 4 or 5 digits reach
+ * the same final backward error.  Classic refinement contracts only while
+ * kappa(A G) times the product's relative error stays below one, so it
+ * wants the default.  digits == 0 returns the current setting; otherwise
+ * sets it for later genp_precondition calls of the process and returns the
+ * previous one, or -1 if digits is not supported.  Not synchronized with
+ * concurrent calls. */
+GENP_API int genp_sliced_precondition_digits(int digits);
 
 /* Measurement hook: while enabled, every launch of the sliced tensor-core
  * kernel is bracketed by two CUDA events on its stream.  genp_profile_read

@@ -15,7 +15,7 @@ GENP_OK = 0
 STATUS_NAMES = {0: "GENP_OK", -1: "GENP_ERR_ARG", -2: "GENP_ERR_BREAKDOWN", -3: "GENP_ERR_NOCONV",
                 -4: "GENP_ERR_CUDA", -5: "GENP_ERR_TIMEOUT", -6: "GENP_ERR_NOMEM", -7: "GENP_ERR_UNSUPPORTED"}
 
-GAUSSIAN, CIRCULANT, SPARSE_PM1, CIRCULANT_PM1, IDENTITY = 0, 1, 2, 3, 4
+GAUSSIAN, CIRCULANT, SPARSE_PM1, CIRCULANT_PM1, IDENTITY, TOEPLITZ, HOUSEHOLDER_PM1 = 0, 1, 2, 3, 4, 5, 6
 FP64, FP32, BF16, FP8_E4M3, BF16X3, BF16_SLICED = 0, 1, 2, 3, 4, 5
 MAX_REFINE = 32
 
@@ -44,6 +44,7 @@ SIGNATURES = {
                               _vp, _i64, _vp]),
     "genp_gemm_sliced": (_int, [_i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _int, _vp]),
     "genp_sliced_digits": (_int, [_int]),
+    "genp_sliced_precondition_digits": (_int, [_int]),
     "genp_profile_enable": (_int, [_int]),
     "genp_profile_read": (_int, [_vp, _vp, _vp]),
     "genp_device_check": (_int, [_int]),

@@ -77,7 +77,7 @@ class Factors:
 def make_multiplier(kind: int, n: int, seed: int, stream_id: int = 0, scale: float | None = None,
                     nnz_per_col: int = 4, value_grid: int = FP64, stream=None) -> Multiplier:
     """genp_make_multiplier.  Default scale: 1/sqrt(n) (Gaussian, variance
-    1/n) and 1 (circulant)."""
+    1/n) and 1 (circulant, Toeplitz)."""
     if scale is None:
         scale = 1.0 / math.sqrt(n) if kind == GAUSSIAN else 1.0
     h = ctypes.c_void_p()

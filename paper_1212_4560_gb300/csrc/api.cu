@@ -70,10 +70,12 @@ cudaError_t draw_multiplier(genp_multiplier *G, uint64_t seed, uint64_t stream_i
             return launch_make_dense(G->dense, G->n, seed, stream_id, G->scale, G->grid, G->dense_f32, G->dense_bf16,
                                      s);
         case GENP_MULT_CIRCULANT: {
-            cudaError_t e = G->pm1 ? launch_make_circulant_pm1(G->g, G->n, seed, stream_id, G->attempt, s)
-                                   : launch_make_circulant(G->g, G->n, seed, stream_id, G->scale, G->grid, s);
+            cudaError_t e = G->pm1        ? launch_make_circulant_pm1(G->g, G->n, seed, stream_id, G->attempt, s)
+                            : G->toeplitz ? launch_make_toeplitz(G->g, G->n, seed, stream_id, G->scale, G->grid, s)
+                                          : launch_make_circulant(G->g, G->n, seed, stream_id, G->scale, G->grid, s);
             return e == cudaSuccess ? circ_prepare(G, s) : e;
         }
+        case GENP_MULT_HOUSEHOLDER_PM1: return launch_make_householder(G->g, G->n, seed, stream_id, s);
         case GENP_MULT_IDENTITY: return cudaSuccess;
         case GENP_MULT_SPARSE_PM1:
             return launch_make_sparse(G->rows, G->signs, G->inv_rows, G->inv_signs, G->draws, G->n, G->nnz, seed,
@@ -136,9 +138,11 @@ cudaError_t apply_multiplier(const genp_multiplier *G, bool trans, const double 
             return gemm<double>(G->n, nrhs, G->n, 1.0, G->dense, G->n, trans, Y, ldy, accumulate ? 1.0 : 0.0, X, ldx,
                                 X, ldx, skip, s);
         case GENP_MULT_CIRCULANT:
-            if (circ_fft_supported(G->n))
+            if (circ_fft_supported(G->cn))
                 return circ_apply_cols(G, trans, Y, ldy, X, ldx, nrhs, accumulate, skip, s);
-            return circ_apply_direct(G->g, G->n, trans, Y, ldy, X, ldx, nrhs, accumulate, skip, s);
+            return circ_apply_direct(G->g, G->cn, G->n, trans, Y, ldy, X, ldx, nrhs, accumulate, skip, s);
+        case GENP_MULT_HOUSEHOLDER_PM1:   // symmetric: G^T = G
+            return house_apply(G, Y, ldy, X, ldx, nrhs, accumulate, skip, s);
         case GENP_MULT_SPARSE_PM1:
             return sparse_apply(G, trans, Y, ldy, X, ldx, nrhs, accumulate, skip, s);
         case GENP_MULT_IDENTITY:
@@ -178,14 +182,20 @@ genp_status genp_make_multiplier(genp_mult_kind kind, int64_t n, uint64_t seed, 
     *out = nullptr;
     if (n < 1 || n > 2147483647LL) return GENP_ERR_ARG;
     if (kind != GENP_MULT_GAUSSIAN && kind != GENP_MULT_CIRCULANT && kind != GENP_MULT_SPARSE_PM1 &&
-        kind != GENP_MULT_CIRCULANT_PM1 && kind != GENP_MULT_IDENTITY)
+        kind != GENP_MULT_CIRCULANT_PM1 && kind != GENP_MULT_IDENTITY && kind != GENP_MULT_TOEPLITZ &&
+        kind != GENP_MULT_HOUSEHOLDER_PM1)
         return GENP_ERR_ARG;
     const bool pm1 = kind == GENP_MULT_CIRCULANT_PM1;
     if (pm1) {   // stored and applied as a circulant with a +-1 first column
         kind = GENP_MULT_CIRCULANT;
         scale = 1.0;
     }
-    if (kind == GENP_MULT_IDENTITY) {
+    const bool toeplitz = kind == GENP_MULT_TOEPLITZ;
+    if (toeplitz) {   // the leading block of a circulant of order 2n
+        if (n > 1073741823LL) return GENP_ERR_ARG;
+        kind = GENP_MULT_CIRCULANT;
+    }
+    if (kind == GENP_MULT_IDENTITY || kind == GENP_MULT_HOUSEHOLDER_PM1) {
         scale = 1.0;
         value_grid = GENP_FP64;
     }
@@ -201,6 +211,8 @@ genp_status genp_make_multiplier(genp_mult_kind kind, int64_t n, uint64_t seed, 
     G->grid = kind == GENP_MULT_SPARSE_PM1 ? GENP_FP64 : value_grid;
     G->scale = kind == GENP_MULT_SPARSE_PM1 ? 1.0 : scale;
     G->pm1 = pm1;
+    G->toeplitz = toeplitz;
+    G->cn = toeplitz ? 2 * n : n;
     G->last_stream = s;
     genp_status st = GENP_OK;
     cudaError_t ce = cudaSuccess;
@@ -210,14 +222,17 @@ genp_status genp_make_multiplier(genp_mult_kind kind, int64_t n, uint64_t seed, 
         if (st == GENP_OK && value_grid == GENP_BF16) st = dalloc(&G->dense_bf16, (size_t)n * round8(n));
     } else if (kind == GENP_MULT_IDENTITY) {
         // nothing to store
-    } else if (kind == GENP_MULT_CIRCULANT) {
+    } else if (kind == GENP_MULT_HOUSEHOLDER_PM1) {
         st = dalloc(&G->g, (size_t)n);
+    } else if (kind == GENP_MULT_CIRCULANT) {
+        const int64_t cn = G->cn;
+        st = dalloc(&G->g, (size_t)cn);
         if (st == GENP_OK && pm1) st = dalloc(&G->attempt, 1);
-        if (st == GENP_OK && circ_fft_supported(n)) {
-            st = dalloc(&G->spec, (size_t)n);
-            if (st == GENP_OK) st = dalloc(&G->spec_f32, (size_t)n);
-            if (st == GENP_OK) st = dalloc(&G->twid, (size_t)(n / 2));
-            if (st == GENP_OK) st = dalloc(&G->twid_f32, (size_t)(n / 2));
+        if (st == GENP_OK && circ_fft_supported(cn)) {
+            st = dalloc(&G->spec, (size_t)cn);
+            if (st == GENP_OK) st = dalloc(&G->spec_f32, (size_t)cn);
+            if (st == GENP_OK) st = dalloc(&G->twid, (size_t)(cn / 2));
+            if (st == GENP_OK) st = dalloc(&G->twid_f32, (size_t)(cn / 2));
         }
     } else {
         const size_t cnt = (size_t)n * nnz_per_col;
@@ -280,12 +295,17 @@ int genp_sliced_digits(int digits) {
     return set_sliced_digits(digits);
 }
 
+int genp_sliced_precondition_digits(int digits) {
+    if (digits == 0) return sliced_precond_digits();
+    return set_sliced_precond_digits(digits);
+}
+
 genp_status genp_gemm_sliced(int64_t m, int64_t n, int64_t K, double alpha, const double *A, int64_t lda,
                              const double *B, int64_t ldb, double beta, double *D, int64_t ldd, int digits,
                              void *cuda_stream) {
     if (m < 0 || n < 0 || K < 1 || !A || !B || !D) return GENP_ERR_ARG;
     const int nd = digits == 0 ? sliced_digits() : digits;
-    if (nd < 5 || nd > 7) return GENP_ERR_ARG;
+    if (nd < 3 || nd > 7) return GENP_ERR_ARG;
     if (lda < K || ldb < n || ldd < n) return GENP_ERR_ARG;
     if (m > INT32_MAX || n > INT32_MAX || cdiv(m, 128) > 65535) return GENP_ERR_ARG;
     if (m == 0 || n == 0) return GENP_OK;
@@ -321,7 +341,7 @@ genp_status genp_multiplier_export(const genp_multiplier *G, double *dense, int6
                                    int32_t *rows, int8_t *signs, void *cuda_stream) {
     if (!G) return GENP_ERR_ARG;
     if (dense && ldd < G->n) return GENP_ERR_ARG;
-    if (first_col && G->kind != GENP_MULT_CIRCULANT) return GENP_ERR_ARG;
+    if (first_col && G->kind != GENP_MULT_CIRCULANT && G->kind != GENP_MULT_HOUSEHOLDER_PM1) return GENP_ERR_ARG;
     if ((rows || signs) && G->kind != GENP_MULT_SPARSE_PM1) return GENP_ERR_ARG;
     cudaStream_t s = S(cuda_stream);
     const int64_t n = G->n;
@@ -330,7 +350,9 @@ genp_status genp_multiplier_export(const genp_multiplier *G, double *dense, int6
             CU(cudaMemcpy2DAsync(dense, ldd * sizeof(double), G->dense, n * sizeof(double), n * sizeof(double), n,
                                  cudaMemcpyDeviceToDevice, s));
         else if (G->kind == GENP_MULT_CIRCULANT)
-            CU(launch_circulant_to_dense(G->g, n, dense, ldd, s));
+            CU(launch_circulant_to_dense(G->g, G->cn, n, dense, ldd, s));
+        else if (G->kind == GENP_MULT_HOUSEHOLDER_PM1)
+            CU(house_to_dense(G, dense, ldd, s));
         else if (G->kind == GENP_MULT_IDENTITY) {
             note_launch();
             k_eye<<<dim3((unsigned)cdiv(n < 2048 ? n : 2048, 256), (unsigned)(n < 65535 ? n : 65535)), 256, 0, s>>>(
@@ -339,7 +361,9 @@ genp_status genp_multiplier_export(const genp_multiplier *G, double *dense, int6
         } else
             CU(launch_sparse_to_dense(G->rows, G->signs, n, G->nnz, dense, ldd, s));
     }
-    if (first_col) CU(cudaMemcpyAsync(first_col, G->g, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (first_col)
+        CU(cudaMemcpyAsync(first_col, G->g, (G->kind == GENP_MULT_CIRCULANT ? G->cn : n) * sizeof(double),
+                           cudaMemcpyDeviceToDevice, s));
     if (rows) CU(cudaMemcpyAsync(rows, G->rows, (size_t)n * G->nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     if (signs) CU(cudaMemcpyAsync(signs, G->signs, (size_t)n * G->nnz, cudaMemcpyDeviceToDevice, s));
     return GENP_OK;
@@ -348,7 +372,8 @@ genp_status genp_multiplier_export(const genp_multiplier *G, double *dense, int6
 genp_status genp_multiplier_query(const genp_multiplier *G, int64_t *n, int *kind, int *nnz_per_col) {
     if (!G) return GENP_ERR_ARG;
     if (n) *n = G->n;
-    if (kind) *kind = G->pm1 ? (int)GENP_MULT_CIRCULANT_PM1 : (int)G->kind;
+    if (kind)
+        *kind = G->pm1 ? (int)GENP_MULT_CIRCULANT_PM1 : G->toeplitz ? (int)GENP_MULT_TOEPLITZ : (int)G->kind;
     if (nnz_per_col) *nnz_per_col = G->nnz;
     return GENP_OK;
 }
@@ -380,9 +405,10 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
         return GENP_OK;
     }
     if (c_prec == GENP_BF16_SLICED && G->kind == GENP_MULT_GAUSSIAN) {
-        // C = A G with FP64-class accuracy on the BF16 tensor cores, summed
-        // in double-float and rounded to FP64 once.
-        const int nd = sliced_digits();
+        // C = A G on the BF16 tensor cores from exact digit slices (as many
+        // digits as genp_sliced_precondition_digits asks), summed in
+        // double-float and rounded to FP64 once.
+        const int nd = sliced_precond_digits();
         const int64_t ldq = (int64_t)nd * kSlicedChunk, ldd = round8(n);
         char *buf = nullptr;
         const size_t dbytes = (size_t)n * ldd * 8, qbytes = (size_t)n * ldq * sizeof(__nv_bfloat16);
@@ -426,10 +452,13 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
                 CU(gemm<double>(n, n, n, 1.0, a, lda, false, G->dense, n, 0.0, nullptr, 0, c, ldc, nullptr, s));
                 break;
             case GENP_MULT_CIRCULANT:
-                if (circ_fft_supported(n)) CU((circ_apply<double, double>(G, 0, a, lda, 1, c, ldc, 1, n, nullptr, s)));
-                else CU((circ_matmul_direct<double, double>(G->g, n, a, lda, c, ldc, s)));
+                if (circ_fft_supported(G->cn))
+                    CU((circ_apply<double, double>(G, 0, a, lda, 1, c, ldc, 1, n, nullptr, s)));
+                else CU((circ_matmul_direct<double, double>(G->g, G->cn, n, a, lda, c, ldc, s)));
                 break;
             case GENP_MULT_SPARSE_PM1: CU((sparse_precondition<double, double>(G, a, lda, c, ldc, s))); break;
+            case GENP_MULT_HOUSEHOLDER_PM1: CU((house_precondition<double, double>(G, a, lda, c, ldc, s))); break;
+            default: return GENP_ERR_ARG;
         }
         return GENP_OK;
     }
@@ -440,7 +469,12 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
         else CU((sparse_precondition<float, float>(G, (const float *)A, lda, c, ldc, s)));
         return GENP_OK;
     }
-    if (G->kind == GENP_MULT_CIRCULANT && circ_fft_supported(n)) {
+    if (G->kind == GENP_MULT_HOUSEHOLDER_PM1) {
+        if (a_prec == GENP_FP64) CU((house_precondition<double, float>(G, (const double *)A, lda, c, ldc, s)));
+        else CU((house_precondition<float, float>(G, (const float *)A, lda, c, ldc, s)));
+        return GENP_OK;
+    }
+    if (G->kind == GENP_MULT_CIRCULANT && circ_fft_supported(G->cn)) {
         if (a_prec == GENP_FP64) CU((circ_apply<double, float>(G, 0, (const double *)A, lda, 1, c, ldc, 1, n, nullptr, s)));
         else CU((circ_apply<float, float>(G, 0, (const float *)A, lda, 1, c, ldc, 1, n, nullptr, s)));
         return GENP_OK;
@@ -458,7 +492,7 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
     if (G->kind == GENP_MULT_GAUSSIAN)
         CU(gemm<float>(n, n, n, 1.0f, a32, lda32, false, G->dense_f32, n, 0.0f, nullptr, 0, c, ldc, nullptr, s));
     else
-        CU((circ_matmul_direct<float, float>(G->g, n, a32, lda32, c, ldc, s)));
+        CU((circ_matmul_direct<float, float>(G->g, G->cn, n, a32, lda32, c, ldc, s)));
     if (tmp) CU(cudaFreeAsync(tmp, s));
     return GENP_OK;
 }

@@ -14,6 +14,10 @@
 // order, the product with the (bit-reversed, 1/n-scaled) spectrum of g is
 // taken in that order, and a decimation-in-time pass with conjugate
 // twiddles returns the natural order, so no permutation is ever done.
+// A Toeplitz multiplier of order n is the leading n x n block of a circulant
+// of order cn = 2n (first column t_0 .. t_{n-1}, 0, t_{-(n-1)} .. t_{-1}):
+// its products read n entries per vector, zero the rest, and keep the first
+// n results.
 #include "genp_internal.cuh"
 
 #include <math.h>
@@ -108,7 +112,7 @@ template <typename TI, typename TO, typename R>
 __global__ void __launch_bounds__(kThreads)
 k_circ_apply(const typename Cx<R>::T *spec, const typename Cx<R>::T *tw, int logn, int mode, const TI *in,
              int64_t ips, int64_t ies, TO *out, int64_t ops, int64_t oes, int64_t count, int accumulate,
-             const int *skip) {
+             int nin, int nout, const int *skip) {
     using C2 = typename Cx<R>::T;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -116,10 +120,10 @@ k_circ_apply(const typename Cx<R>::T *spec, const typename Cx<R>::T *tw, int log
     const int n = 1 << logn;
     const int64_t p0 = 2 * (int64_t)blockIdx.x;
     const bool two = p0 + 1 < count;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {   // zero past nin (Toeplitz embedding)
         C2 v;
-        v.x = (R)in[p0 * ips + i * ies];
-        v.y = two ? (R)in[(p0 + 1) * ips + i * ies] : R(0);
+        v.x = i < nin ? (R)in[p0 * ips + i * ies] : R(0);
+        v.y = (two && i < nin) ? (R)in[(p0 + 1) * ips + i * ies] : R(0);
         z[i] = v;
     }
     __syncthreads();
@@ -131,7 +135,7 @@ k_circ_apply(const typename Cx<R>::T *spec, const typename Cx<R>::T *tw, int log
     }
     __syncthreads();
     dit_inverse<R>(z, tw, logn);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = threadIdx.x; i < nout; i += blockDim.x) {
         const C2 v = z[i];
         TO *o0 = out + p0 * ops + i * oes;
         *o0 = accumulate ? (TO)((R)*o0 + v.x) : (TO)v.x;
@@ -153,12 +157,12 @@ int ilog2(int64_t n) {
 bool circ_fft_supported(int64_t n) { return n >= 2 && n <= (1 << kMaxLogN) && (n & (n - 1)) == 0; }
 
 cudaError_t circ_prepare(genp_multiplier *G, cudaStream_t s) {
-    if (!circ_fft_supported(G->n)) return cudaSuccess;
-    const int logn = ilog2(G->n);
-    const size_t sm = (size_t)G->n * sizeof(double2);
+    if (!circ_fft_supported(G->cn)) return cudaSuccess;
+    const int logn = ilog2(G->cn);
+    const size_t sm = (size_t)G->cn * sizeof(double2);
     cudaFuncSetAttribute(k_spectrum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     note_launch();
-    k_twiddles<<<(unsigned)cdiv(G->n / 2, 256), 256, 0, s>>>(G->twid, G->twid_f32, logn);
+    k_twiddles<<<(unsigned)cdiv(G->cn / 2, 256), 256, 0, s>>>(G->twid, G->twid_f32, logn);
     note_launch();
     k_spectrum<<<1, kThreads, sm, s>>>(G->g, G->twid, logn, G->spec, G->spec_f32);
     return cudaGetLastError();
@@ -170,10 +174,10 @@ cudaError_t circ_apply_impl(const genp_multiplier *G, int mode, const TI *in, in
                             int64_t ops, int64_t oes, int64_t count, int accumulate, const int *skip,
                             cudaStream_t s) {
     using C2 = typename Cx<R>::T;
-    if (!circ_fft_supported(G->n)) return cudaErrorInvalidValue;
+    if (!circ_fft_supported(G->cn)) return cudaErrorInvalidValue;
     if (count <= 0) return cudaSuccess;
-    const int logn = ilog2(G->n);
-    const size_t sm = (size_t)G->n * sizeof(C2);
+    const int logn = ilog2(G->cn);
+    const size_t sm = (size_t)G->cn * sizeof(C2);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_circ_apply<TI, TO, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -186,7 +190,7 @@ cudaError_t circ_apply_impl(const genp_multiplier *G, int mode, const TI *in, in
     if (blocks > 2147483647) return cudaErrorInvalidValue;
     note_launch();
     k_circ_apply<TI, TO, R><<<(unsigned)blocks, kThreads, sm, s>>>(spec, tw, logn, mode, in, ips, ies, out, ops, oes,
-                                                                    count, accumulate, skip);
+                                                                    count, accumulate, (int)G->n, (int)G->n, skip);
     return cudaGetLastError();
 }
 }  // namespace

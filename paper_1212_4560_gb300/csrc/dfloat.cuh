@@ -18,8 +18,8 @@ using ::fma;
 struct __align__(8) dfloat {
     float hi, lo;
     dfloat() = default;
-    __device__ dfloat(int v) : hi((float)v), lo(0.f) {}
-    __device__ explicit dfloat(float v) : hi(v), lo(0.f) {}
+    __host__ __device__ dfloat(int v) : hi((float)v), lo(0.f) {}
+    __host__ __device__ explicit dfloat(float v) : hi(v), lo(0.f) {}
     __device__ explicit dfloat(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
     __device__ explicit operator double() const { return (double)hi + (double)lo; }
     __device__ explicit operator float() const { return hi + lo; }

@@ -9,6 +9,7 @@
 // 128x128 tile with 8x8 outputs per thread (FFMA).  The A and B loaders can
 // also synthesise a circulant operand G[i][j] = g[(i-j) mod n] on the fly.
 #include "genp_internal.cuh"
+#include "dfloat.cuh"
 
 namespace genp {
 
@@ -291,6 +292,16 @@ cudaError_t gemm(int64_t m, int64_t n, int64_t k, T alpha, const T *A, int64_t l
                                               nullptr, 1, s);
 }
 
+// D <- D - A B in double-float (the inner block updates of the sliced
+// factorization): the same register-tiled kernel, 64 x 64 tiles, every
+// multiply-add a double-float one on the FP32 pipe.
+cudaError_t gemm_df_sub(int64_t m, int64_t n, int64_t k, const dfloat *A, int64_t lda, const dfloat *B, int64_t ldb,
+                        dfloat *D, int64_t ldd, cudaStream_t s) {
+    if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
+    return run<dfloat, 64, 64, 16, 4, 4, false, kDense, kDense>(m, n, k, dfloat(-1), A, lda, B, ldb, dfloat(1), D,
+                                                                 ldd, D, ldd, nullptr, nullptr, 1, s);
+}
+
 template cudaError_t gemm<double>(int64_t, int64_t, int64_t, double, const double *, int64_t, bool,
                                   const double *, int64_t, double, const double *, int64_t, double *, int64_t,
                                   const int *, cudaStream_t);
@@ -298,27 +309,29 @@ template cudaError_t gemm<float>(int64_t, int64_t, int64_t, float, const float *
                                  int64_t, float, const float *, int64_t, float *, int64_t, const int *,
                                  cudaStream_t);
 
-// C = A * G, G circulant with first column g (any n): 2 n^3 operations.
+// C = A * G, G the leading n x n block of the circulant of order cn with
+// first column g (cn = n: a circulant; cn = 2n: a Toeplitz matrix), any n:
+// 2 n^3 operations.
 template <typename TI, typename TO>
-cudaError_t circ_matmul_direct(const double *g, int64_t n, const TI *A, int64_t lda, TO *C, int64_t ldc,
+cudaError_t circ_matmul_direct(const double *g, int64_t cn, int64_t n, const TI *A, int64_t lda, TO *C, int64_t ldc,
                                cudaStream_t s) {
     static_assert(sizeof(TI) == sizeof(TO), "same precision in and out");
     return dispatch<TO, false, kDense, kCirc>(n, n, n, TO(1), (const TO *)A, lda, nullptr, 0, TO(0), nullptr, 0,
-                                              C, ldc, nullptr, g, n, s);
+                                              C, ldc, nullptr, g, cn, s);
 }
-template cudaError_t circ_matmul_direct<double, double>(const double *, int64_t, const double *, int64_t,
+template cudaError_t circ_matmul_direct<double, double>(const double *, int64_t, int64_t, const double *, int64_t,
                                                         double *, int64_t, cudaStream_t);
-template cudaError_t circ_matmul_direct<float, float>(const double *, int64_t, const float *, int64_t, float *,
-                                                      int64_t, cudaStream_t);
+template cudaError_t circ_matmul_direct<float, float>(const double *, int64_t, int64_t, const float *, int64_t,
+                                                      float *, int64_t, cudaStream_t);
 
-// X (+)= G Y or G^T Y for circulant G without the DFT (any n).
-cudaError_t circ_apply_direct(const double *g, int64_t n, bool trans, const double *Y, int64_t ldy, double *X,
-                              int64_t ldx, int64_t nrhs, bool accumulate, const int *skip, cudaStream_t s) {
+// X (+)= G Y or G^T Y for the same G without the DFT (any n).
+cudaError_t circ_apply_direct(const double *g, int64_t cn, int64_t n, bool trans, const double *Y, int64_t ldy,
+                              double *X, int64_t ldx, int64_t nrhs, bool accumulate, const int *skip, cudaStream_t s) {
     if (trans)
         return dispatch<double, false, kCircT, kDense>(n, nrhs, n, 1.0, nullptr, 0, Y, ldy, accumulate ? 1.0 : 0.0,
-                                                       X, ldx, X, ldx, skip, g, n, s);
+                                                       X, ldx, X, ldx, skip, g, cn, s);
     return dispatch<double, false, kCirc, kDense>(n, nrhs, n, 1.0, nullptr, 0, Y, ldy, accumulate ? 1.0 : 0.0, X,
-                                                  ldx, X, ldx, skip, g, n, s);
+                                                  ldx, X, ldx, skip, g, cn, s);
 }
 
 }  // namespace genp

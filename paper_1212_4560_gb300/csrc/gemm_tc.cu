@@ -688,6 +688,8 @@ cudaError_t tc_gemm_sliced(int nd, int64_t m, int64_t n, int64_t kpad, float alp
     CUtensorMap ma, mb;
     if (!make_map(&ma, Aq, m, kq, lda, BM) || !make_map(&mb, Bq, n, kq, ldb, SBN)) return cudaErrorInvalidValue;
     switch (nd) {
+        case 3: return launch_sliced<3>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
+        case 4: return launch_sliced<4>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
         case 5: return launch_sliced<5>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
         case 6: return launch_sliced<6>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
         default: return launch_sliced<7>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);

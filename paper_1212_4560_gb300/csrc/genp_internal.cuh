@@ -69,6 +69,8 @@ struct genp_multiplier {
     int32_t *draws = nullptr;          // nnz x n Fisher-Yates draws (SPARSE)
     double scale = 1.0;
     bool pm1 = false;                  // CIRCULANT_PM1 (stored as a circulant)
+    bool toeplitz = false;             // TOEPLITZ (stored as a circulant of order 2n)
+    int64_t cn = 0;                    // order of the stored circulant: n, or 2n for TOEPLITZ
     int *attempt = nullptr;            // device: the draw attempt kept (CIRCULANT_PM1)
     cudaStream_t last_stream = nullptr;
 };
@@ -141,8 +143,14 @@ cudaError_t launch_make_circulant_pm1(double *g, int64_t n, uint64_t seed, uint6
 cudaError_t launch_make_sparse(int32_t *rows, int8_t *signs, int32_t *inv_rows, int8_t *inv_signs,
                                int32_t *scratch, int64_t n, int nnz, uint64_t seed,
                                uint64_t stream_id, cudaStream_t s);
-cudaError_t launch_circulant_to_dense(const double *g, int64_t n, double *G, int64_t ldg,
+// G[i][j] = g[(i - j) mod cn], i, j < n
+cudaError_t launch_circulant_to_dense(const double *g, int64_t cn, int64_t n, double *G, int64_t ldg,
                                       cudaStream_t s);
+// Gaussian Toeplitz (2n - 1 draws) as the first column of its circulant embedding of order 2n
+cudaError_t launch_make_toeplitz(double *g, int64_t n, uint64_t seed, uint64_t stream_id, double scale,
+                                 genp_prec grid, cudaStream_t s);
+// u = +-1 of the Householder multiplier
+cudaError_t launch_make_householder(double *u, int64_t n, uint64_t seed, uint64_t stream_id, cudaStream_t s);
 cudaError_t launch_batch_draw(const BatchDesc *d, int count, uint64_t seed, bool circ, float *Gpool, float *gpool,
                               cudaStream_t s);
 cudaError_t launch_sparse_to_dense(const int32_t *rows, const int8_t *signs, int64_t n, int nnz,
@@ -168,13 +176,22 @@ cudaError_t circ_apply(const genp_multiplier *G, int mode, const TI *in, int64_t
 // X (+)= G Y (trans false) or G^T Y on the columns of Y (n x nrhs double).
 cudaError_t circ_apply_cols(const genp_multiplier *G, bool trans, const double *Y, int64_t ldy, double *X,
                             int64_t ldx, int64_t nrhs, bool accumulate, const int *skip, cudaStream_t s);
-// Direct (non-FFT) C = A * G for circulant G of any n, in 2n^3 operations.
+// Direct (non-FFT) C = A * G in 2n^3 operations, G the leading n x n block of
+// the circulant of order cn with first column g (cn = n circulant, 2n Toeplitz).
 template <typename TI, typename TO>
-cudaError_t circ_matmul_direct(const double *g, int64_t n, const TI *A, int64_t lda, TO *C,
+cudaError_t circ_matmul_direct(const double *g, int64_t cn, int64_t n, const TI *A, int64_t lda, TO *C,
                                int64_t ldc, cudaStream_t s);
 
-cudaError_t circ_apply_direct(const double *g, int64_t n, bool trans, const double *Y, int64_t ldy, double *X,
-                              int64_t ldx, int64_t nrhs, bool accumulate, const int *skip, cudaStream_t s);
+cudaError_t circ_apply_direct(const double *g, int64_t cn, int64_t n, bool trans, const double *Y, int64_t ldy,
+                              double *X, int64_t ldx, int64_t nrhs, bool accumulate, const int *skip, cudaStream_t s);
+
+// house.cu: the Householder multiplier H = I - 2 u u^T / n (u = +-1)
+template <typename TI, typename TO>
+cudaError_t house_precondition(const genp_multiplier *G, const TI *A, int64_t lda, TO *C, int64_t ldc,
+                               cudaStream_t s);
+cudaError_t house_apply(const genp_multiplier *G, const double *Y, int64_t ldy, double *X, int64_t ldx,
+                        int64_t nrhs, bool accumulate, const int *skip, cudaStream_t s);
+cudaError_t house_to_dense(const genp_multiplier *G, double *D, int64_t ldd, cudaStream_t s);
 
 // sparse.cu
 template <typename TI, typename TO>
@@ -207,6 +224,8 @@ int64_t sliced_kpad(int64_t K);   // K rounded up to the k-tile
 int sliced_slices(int nd);        // digit slices per operand (operand width slices * kpad)
 int sliced_digits();              // digits of the GENP_BF16_SLICED path
 int set_sliced_digits(int nd);    // returns the previous value, -1 if nd is unsupported
+int sliced_precond_digits();      // digits of the sliced C = A G
+int set_sliced_precond_digits(int nd);
 // rows of src (m x K): dst[i][p*kpad + k] = slice p of src[i][k]; exps[i] = row exponent
 cudaError_t slice_rows(int nd, const double *src, int64_t lds, int64_t m, int64_t K, __nv_bfloat16 *dst, int64_t ldq,
                        int *exps, cudaStream_t s);
@@ -299,6 +318,10 @@ cudaError_t launch_batched_escalate(const BatchDesc *d, int count, int *counter,
 // lu.cu
 cudaError_t factor_run(genp_factors *F, cudaStream_t s);
 cudaError_t status_reset(genp_factors *F, cudaStream_t s);
+
+// gemm.cu: D <- D - A B in double-float (row-major, m x k times k x n)
+cudaError_t gemm_df_sub(int64_t m, int64_t n, int64_t k, const dfloat *A, int64_t lda, const dfloat *B, int64_t ldb,
+                        dfloat *D, int64_t ldd, cudaStream_t s);
 
 // solve.cu
 // Y <- U^{-1} L^{-1} Y in the factor's precision, Y n x nrhs of type T

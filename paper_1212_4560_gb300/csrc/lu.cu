@@ -11,6 +11,8 @@
 
 #include <math.h>
 
+#include <type_traits>
+
 namespace genp {
 namespace {
 
@@ -161,6 +163,272 @@ __global__ void __launch_bounds__(kThreads) k_trsm(TS *C, int64_t ldc, int64_t n
     }
 }
 
+// ---------------------------------------------------------------------------
+// Register-blocked panel and block row / column solves for FP64 storage, in
+// FP64 (TC = double) or in double-float (TC = dfloat: the sliced path, whose
+// accuracy is set by its 47-bit products, on the FP32 pipe, which on GB300 is
+// 64 times faster than the FP64 units).  Each thread keeps its share of the
+// block in registers; the inner loops have no integer division.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double fms(double x, double l, double u) { return fma(-l, u, x); }
+// x - l u in double-float: TwoProduct of the leading parts by FMA, TwoSum of
+// x.hi and the product, the small terms gathered, one renormalization.
+__device__ __forceinline__ dfloat fms(dfloat x, dfloat l, dfloat u) {
+    const float p = l.hi * u.hi;
+    const float pe = fmaf(l.hi, u.hi, -p) + fmaf(l.hi, u.lo, l.lo * u.hi);
+    const float s = x.hi - p, bb = s - x.hi;
+    const float err = (x.hi - (s - bb)) - (p + bb);
+    return df_norm(s, (err + x.lo) - pe);
+}
+__device__ __forceinline__ double shfl_idx(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ dfloat shfl_idx(dfloat v, int src) {
+    v.hi = __shfl_sync(0xffffffffu, v.hi, src);
+    v.lo = __shfl_sync(0xffffffffu, v.lo, src);
+    return v;
+}
+// loads and stores between the storage type (double, or the double-float
+// trailing matrix of the sliced path) and the compute type
+template <typename TC> __device__ __forceinline__ TC ld_as(double v) { return TC(v); }
+template <typename TC> __device__ __forceinline__ TC ld_as(dfloat v);
+template <> __device__ __forceinline__ dfloat ld_as<dfloat>(dfloat v) { return v; }
+template <typename TS> __device__ __forceinline__ TS st_as(double v) { return TS(v); }
+template <typename TS> __device__ __forceinline__ TS st_as(dfloat v);
+template <> __device__ __forceinline__ dfloat st_as<dfloat>(dfloat v) { return v; }
+template <> __device__ __forceinline__ double st_as<double>(dfloat v) { return (double)v; }
+// magnitude for the growth statistics, without FP64 work for double-float
+__device__ __forceinline__ double mag(double v) { return fabs(v); }
+__device__ __forceinline__ float mag(dfloat v) { return fabsf(v.hi); }
+
+__device__ __forceinline__ void pivot_stats(DevStatus *st, int64_t step, double p) {
+    const double ap = fabs(p);
+    if (!(ap > 0.0) || !isfinite(ap)) {
+        atomicMin(&st->breakdown_step, (unsigned long long)step);
+    } else {
+        atomic_min_nonneg(&st->min_abs_pivot, ap);
+        atomic_max_nonneg(&st->max_abs_pivot, ap);
+    }
+}
+
+// Unblocked GENP of the kb x kb (kb <= 128) diagonal block at (k0, k0).
+// 1024 threads: warp w holds rows w + 32 i and lane l columns l + 32 j
+// (i, j < 4) of the block in registers.  Step k: the warp of row k publishes
+// it (its pivot's owner also the pivot's reciprocal in double-float), the
+// lane of column k in every warp turns its entries below the pivot into
+// multipliers and publishes them, then every thread updates its trailing
+// entries; two block barriers per step, buffers alternating by the parity of
+// k.  Row conditions are warp-uniform, so finished rows cost nothing.
+constexpr int kPanelThreads = 1024;
+template <typename TS, typename TC>
+__global__ void __launch_bounds__(kPanelThreads, 1) k_panel_reg(TS *C, int64_t ldc, int64_t k0, int kb,
+                                                                DevStatus *st) {
+    __shared__ TC urow[2][128], lcol[2][128], prcp[2];
+    const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
+    TC a[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = ty + 32 * i, c = tx + 32 * j;
+            a[i][j] = (r < kb && c < kb) ? ld_as<TC>(C[(k0 + r) * ldc + k0 + c]) : TC(0.0);
+        }
+    for (int k = 0; k < kb; ++k) {
+        const int buf = k & 1, kr = k & 31, kq = k >> 5;
+        if (ty == kr) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (i == kq) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) urow[buf][tx + 32 * j] = a[i][j];
+                    if (tx == kr) {
+                        TC p = TC(0.0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (j == kq) p = a[i][j];
+                        if constexpr (std::is_same<TC, dfloat>::value) prcp[buf] = TC(1.0) / p;
+                        pivot_stats(st, k0 + k, (double)p);
+                    }
+                }
+        }
+        __syncthreads();
+        if (tx == kr) {
+            // double-float: the published reciprocal; FP64: the division, as in
+            // the unblocked recurrence
+            const TC p = urow[buf][k];
+            const TC rp = prcp[buf];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j == kq) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int r = ty + 32 * i;
+                        if (r > k && r < kb) {
+                            if constexpr (std::is_same<TC, dfloat>::value) a[i][j] = a[i][j] * rp;
+                            else a[i][j] = a[i][j] / p;
+                            lcol[buf][r] = a[i][j];
+                        }
+                    }
+                }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = ty + 32 * i;
+            if (r > k && r < kb) {            // warp-uniform
+                const TC l = lcol[buf][r];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (32 * j + 31 > k) {      // column slot not yet finished (uniform)
+                        if (tx + 32 * j > k) a[i][j] = fms(a[i][j], l, urow[buf][tx + 32 * j]);
+                    }
+            }
+        }
+    }
+    using MT = decltype(mag(TC()));
+    MT umax = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = ty + 32 * i, c = tx + 32 * j;
+            if (r < kb && c < kb) {
+                C[(k0 + r) * ldc + k0 + c] = st_as<TS>(a[i][j]);
+                if (c >= r) {
+                    const MT av = mag(a[i][j]);
+                    umax = (av > umax || isnan(av)) ? av : umax;
+                }
+            }
+        }
+    for (int o = 16; o > 0; o >>= 1) {
+        const MT w = __shfl_xor_sync(0xffffffffu, umax, o);
+        umax = (w > umax || isnan(w)) ? w : umax;
+    }
+    if (tx == 0) atomic_max_nonneg(&st->max_abs_u, (double)umax);
+}
+
+// blockIdx.y == 0: U12 = L11^{-1} C12 on columns [c0, c0 + 64)
+// blockIdx.y == 1: L21 = C21 U11^{-1} on rows    [c0, c0 + 64)
+// 64 vectors (columns of C12, rows of C21) per CTA of 1024 threads, 16
+// threads per vector in one half-warp: thread g holds entries g + 16 m
+// (m < 8) in registers, and the entry of step k reaches the vector's other
+// threads by a shuffle, so the substitutions need no block barrier; 32 warps
+// per SM hide the latency of the dependent double-float operations.  The
+// kb x kb (kb <= 128) diagonal block sits in shared memory.
+constexpr int kTrsmThreads = 1024, kTpv = 16, kEpt = 128 / kTpv;
+template <typename TS, typename TC>
+__global__ void __launch_bounds__(kTrsmThreads, 1) k_trsm_reg(TS *C, int64_t ldc, int64_t n, int64_t k0, int kb,
+                                                              DevStatus *st) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    TC *T = reinterpret_cast<TC *>(smraw);
+    const int ld = kb + 1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int v = tid / kTpv, g = tid % kTpv;
+    const int64_t c0 = k0 + kb + (int64_t)blockIdx.x * kTrsmW;
+    const int w = (int)min((int64_t)kTrsmW, n - c0);
+    if (w <= 0) return;
+    const bool role_u = blockIdx.y == 0;
+    for (int r = warp; r < kb; r += kTrsmThreads / 32)
+        for (int c = lane; c < kb; c += 32) T[r * ld + c] = ld_as<TC>(C[(k0 + r) * ldc + k0 + c]);
+    __syncthreads();
+    const bool valid = v < w;
+    const int base = lane & ~(kTpv - 1);
+    const int nq = (kb + kTpv - 1) / kTpv;
+    TC x[kEpt];
+    if (role_u) {
+#pragma unroll
+        for (int m = 0; m < kEpt; ++m) {
+            const int r = g + kTpv * m;
+            x[m] = (valid && r < kb) ? ld_as<TC>(C[(k0 + r) * ldc + c0 + v]) : TC(0.0);
+        }
+        for (int kq = 0; kq < nq; ++kq) {
+            TC own = TC(0.0);
+#pragma unroll
+            for (int m = 0; m < kEpt; ++m)
+                if (m == kq) own = x[m];
+            for (int kk = 0; kk < kTpv; ++kk) {
+                const int k = kTpv * kq + kk;
+                if (k >= kb) break;
+                const TC xk = shfl_idx(own, base | kk);       // row k of the vector, final
+#pragma unroll
+                for (int m = 0; m < kEpt; ++m) {
+                    const int r = g + kTpv * m;
+                    if (kTpv * m + kTpv - 1 > k && r > k && r < kb) x[m] = fms(x[m], T[r * ld + k], xk);
+                }
+                if (g > kk && g + kTpv * kq < kb) own = fms(own, T[(g + kTpv * kq) * ld + k], xk);
+            }
+        }
+        using MT = decltype(mag(TC()));
+        MT xmax = 0;
+#pragma unroll
+        for (int m = 0; m < kEpt; ++m) {
+            const int r = g + kTpv * m;
+            if (valid && r < kb) {
+                C[(k0 + r) * ldc + c0 + v] = st_as<TS>(x[m]);
+                const MT av = mag(x[m]);
+                xmax = (av > xmax || isnan(av)) ? av : xmax;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const MT q = __shfl_xor_sync(0xffffffffu, xmax, o);
+            xmax = (q > xmax || isnan(q)) ? q : xmax;
+        }
+        if (lane == 0) atomic_max_nonneg(&st->max_abs_u, (double)xmax);
+    } else {
+#pragma unroll
+        for (int m = 0; m < kEpt; ++m) {
+            const int c = g + kTpv * m;
+            x[m] = (valid && c < kb) ? ld_as<TC>(C[(c0 + v) * ldc + k0 + c]) : TC(0.0);
+        }
+        for (int kq = 0; kq < nq; ++kq) {
+            TC own = TC(0.0);
+#pragma unroll
+            for (int m = 0; m < kEpt; ++m)
+                if (m == kq) own = x[m];
+            for (int kk = 0; kk < kTpv; ++kk) {
+                const int j = kTpv * kq + kk;
+                if (j >= kb) break;
+                if (g == kk) own = own / T[j * ld + j];          // l_vj = x_vj / u_jj
+                const TC xj = shfl_idx(own, base | kk);
+#pragma unroll
+                for (int m = 0; m < kEpt; ++m) {
+                    const int c = g + kTpv * m;
+                    if (kTpv * m + kTpv - 1 > j && c > j && c < kb) x[m] = fms(x[m], xj, T[j * ld + c]);
+                }
+                if (g > kk && g + kTpv * kq < kb) own = fms(own, xj, T[j * ld + g + kTpv * kq]);
+            }
+#pragma unroll
+            for (int m = 0; m < kEpt; ++m)
+                if (m == kq) x[m] = own;
+        }
+#pragma unroll
+        for (int m = 0; m < kEpt; ++m) {
+            const int c = g + kTpv * m;
+            if (valid && c < kb) C[(c0 + v) * ldc + k0 + c] = st_as<TS>(x[m]);
+        }
+    }
+}
+
+// one step of the blocked factorization's FP64-storage panel work: the
+// diagonal block at (i0, i0), then the block row and column beside it
+template <typename TS, typename TC>
+cudaError_t panel_and_trsm(TS *C, int64_t ldc, int64_t n, int64_t i0, int kb, DevStatus *st, cudaStream_t s) {
+    static bool attr_done = false;
+    const size_t sm = (size_t)128 * 129 * sizeof(TC);
+    if (!attr_done) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_trsm_reg<TS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    note_launch();
+    k_panel_reg<TS, TC><<<1, kPanelThreads, 0, s>>>(C, ldc, i0, kb, st);
+    const int64_t rem = n - i0 - kb;
+    if (rem <= 0) return cudaGetLastError();
+    dim3 g((unsigned)cdiv(rem, kTrsmW), 2);
+    note_launch();
+    k_trsm_reg<TS, TC><<<g, kTrsmThreads, (size_t)kb * (kb + 1) * sizeof(TC), s>>>(C, ldc, n, i0, kb, st);
+    return cudaGetLastError();
+}
+
 template <typename TS, typename TC>
 cudaError_t factor_typed(genp_factors *F, cudaStream_t s) {
     TS *C = static_cast<TS *>(F->C);
@@ -179,13 +447,20 @@ cudaError_t factor_typed(genp_factors *F, cudaStream_t s) {
     k_maxabs<TS><<<152 * 4, 256, 0, s>>>(C, n, ldc, &F->st->max_abs_c);
     for (int64_t k0 = 0; k0 < n; k0 += nb) {
         const int kb = (int)(n - k0 < nb ? n - k0 : nb);
-        note_launch();
-        k_panel<TS, TC><<<1, kThreads, sm_panel, s>>>(C, ldc, k0, kb, F->st);
         const int64_t rem = n - k0 - kb;
+        if constexpr (std::is_same<TS, double>::value) {
+            cudaError_t e = panel_and_trsm<double, double>(C, ldc, n, k0, kb, F->st, s);
+            if (e != cudaSuccess) return e;
+        } else {
+            note_launch();
+            k_panel<TS, TC><<<1, kThreads, sm_panel, s>>>(C, ldc, k0, kb, F->st);
+            if (rem > 0) {
+                dim3 g((unsigned)cdiv(rem, kTrsmW), 2);
+                note_launch();
+                k_trsm<TS, TC><<<g, kThreads, sm_trsm, s>>>(C, ldc, n, k0, kb, F->st);
+            }
+        }
         if (rem <= 0) break;
-        dim3 g((unsigned)cdiv(rem, kTrsmW), 2);
-        note_launch();
-        k_trsm<TS, TC><<<g, kThreads, sm_trsm, s>>>(C, ldc, n, k0, kb, F->st);
         TS *L21 = C + (k0 + kb) * ldc + k0;
         TS *U12 = C + k0 * ldc + k0 + kb;
         TS *A22 = C + (k0 + kb) * ldc + k0 + kb;
@@ -239,62 +514,47 @@ cudaError_t factor_tc(genp_factors *F, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// GENP_BF16_SLICED: blocked GENP in two levels.  The outer block column
-// (2 nb wide) is factored in FP64 by two inner steps of width nb (diagonal
-// block, block row and column, and the small FP64 update of the second inner
-// block by the first); the outer Schur update C22 -= L21 U12 (K = 2 nb) then
-// runs on the tensor cores by exact digit slicing.  The outer trailing matrix
-// lives in W as double-float pairs; each outer step first copies its block
-// column and block row from W into C, so C ends up holding the FP64 factors.
+// GENP_BF16_SLICED: blocked GENP in two levels on the double-float copy W
+// of C.  The outer block column (2 nb wide) is factored by two inner steps of
+// width nb (diagonal block, block row and column, and the update of the
+// second inner block by the first), all in double-float on the FP32 pipe;
+// the finished block column and block row are then rounded into C (exactly:
+// a double-float value has 48 significant bits), and the outer Schur update
+// W22 -= L21 U12 (K = 2 nb) runs on the tensor cores by exact digit slicing
+// of the FP64 factors.  C ends up holding the factors.
 cudaError_t factor_sliced(genp_factors *F, cudaStream_t s) {
     double *C = static_cast<double *>(F->C);
     dfloat *W = static_cast<dfloat *>(F->W);
     const int64_t n = F->n, ldc = F->ldc, ldw = F->ldw, ldq = F->tc_ldq;
     const int nb = (int)F->nb, nbo = 2 * nb;
-    const size_t sm_panel = (size_t)nb * (nb + 1) * sizeof(double);
-    const size_t xrow = (size_t)nb * (kTrsmW + 1), xcol = (size_t)kTrsmW * (nb + 1);
-    const size_t sm_trsm = sm_panel + (xrow > xcol ? xrow : xcol) * sizeof(double);
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(k_panel<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_trsm<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_done = true;
-    }
     note_launch();
     k_maxabs<double><<<152 * 4, 256, 0, s>>>(C, n, ldc, &F->st->max_abs_c);
-    if (n > nbo) {
-        cudaError_t e = df_from_f64(C + nbo * ldc + nbo, ldc, W + nbo * ldw + nbo, ldw, n - nbo, n - nbo, s);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = df_from_f64(C, ldc, W, ldw, n, n, s);
+    if (e != cudaSuccess) return e;
     for (int64_t k0 = 0; k0 < n; k0 += nbo) {
         const int kbo = (int)(n - k0 < nbo ? n - k0 : nbo);
         const int64_t e0 = k0 + kbo, remo = n - e0;
-        cudaError_t e = cudaSuccess;
-        if (k0 > 0) {   // this step's block column and block row, updated by the earlier steps
-            e = df_to_f64(W + k0 * ldw + k0, ldw, C + k0 * ldc + k0, ldc, n - k0, kbo, s);
-            if (e == cudaSuccess) e = df_to_f64(W + k0 * ldw + e0, ldw, C + k0 * ldc + e0, ldc, kbo, remo, s);
-            if (e != cudaSuccess) return e;
-        }
         for (int64_t i0 = k0; i0 < e0; i0 += nb) {
             const int kb = (int)(e0 - i0 < nb ? e0 - i0 : nb);
             const int64_t j0 = i0 + kb, rem = n - j0;
-            note_launch();
-            k_panel<double, double><<<1, kThreads, sm_panel, s>>>(C, ldc, i0, kb, F->st);
+            e = panel_and_trsm<dfloat, dfloat>(W, ldw, n, i0, kb, F->st, s);
+            if (e != cudaSuccess) return e;
             if (rem <= 0) break;
-            dim3 g((unsigned)cdiv(rem, kTrsmW), 2);
-            note_launch();
-            k_trsm<double, double><<<g, kThreads, sm_trsm, s>>>(C, ldc, n, i0, kb, F->st);
             if (j0 < e0) {
                 // the rest of the outer block column, and its block row beyond it
                 const int64_t w2 = e0 - j0;
-                e = gemm<double>(rem, w2, kb, -1.0, C + j0 * ldc + i0, ldc, false, C + i0 * ldc + j0, ldc, 1.0,
-                                 C + j0 * ldc + j0, ldc, C + j0 * ldc + j0, ldc, nullptr, s);
+                e = gemm_df_sub(rem, w2, kb, W + j0 * ldw + i0, ldw, W + i0 * ldw + j0, ldw, W + j0 * ldw + j0, ldw,
+                                s);
                 if (e == cudaSuccess && remo > 0)
-                    e = gemm<double>(w2, remo, kb, -1.0, C + j0 * ldc + i0, ldc, false, C + i0 * ldc + e0, ldc, 1.0,
-                                     C + j0 * ldc + e0, ldc, C + j0 * ldc + e0, ldc, nullptr, s);
+                    e = gemm_df_sub(w2, remo, kb, W + j0 * ldw + i0, ldw, W + i0 * ldw + e0, ldw,
+                                    W + j0 * ldw + e0, ldw, s);
                 if (e != cudaSuccess) return e;
             }
         }
+        // this step's factors: block column (diagonal block included) and block row
+        e = df_to_f64(W + k0 * ldw + k0, ldw, C + k0 * ldc + k0, ldc, n - k0, kbo, s);
+        if (e == cudaSuccess && remo > 0) e = df_to_f64(W + k0 * ldw + e0, ldw, C + k0 * ldc + e0, ldc, kbo, remo, s);
+        if (e != cudaSuccess) return e;
         if (remo <= 0) break;
         const double *L21 = C + e0 * ldc + k0;
         const double *U12 = C + k0 * ldc + e0;

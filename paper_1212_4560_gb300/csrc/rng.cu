@@ -180,6 +180,36 @@ __global__ void k_circ(double *g, int64_t n, uint64_t seed, uint64_t sid, double
                    : on_grid(__dmul_rn(polar_normal(seed, sid, kTagCirc, (uint64_t)i), scale), grid);
 }
 
+// Gaussian Toeplitz multiplier (Definition 3.2): the 2n - 1 entries
+// t_d (d = i - j in [-(n-1), n-1]) drawn at index d + n - 1 on their own tag,
+// stored as the first column of the circulant of order 2n that embeds the
+// Toeplitz matrix in its leading n x n block: g[d mod 2n] = t_d, g[n] = 0.
+constexpr uint64_t kTagToep = 0x17, kTagHouse = 0x18;
+__global__ void k_toeplitz(double *g, int64_t n, uint64_t seed, uint64_t sid, double scale, genp_prec grid) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < 2 * n; q += (int64_t)gridDim.x * blockDim.x) {
+        if (q == 2 * n - 1) {
+            g[n] = 0.0;
+            continue;
+        }
+        const int64_t d = q - (n - 1);
+        const double v = grid == GENP_FP32
+                             ? (double)__fmul_rn(polar_normal_f32(seed, sid, kTagToep + 4, (uint64_t)q),
+                                                 __double2float_rn(scale))
+                             : on_grid(__dmul_rn(polar_normal(seed, sid, kTagToep, (uint64_t)q), scale), grid);
+        g[d >= 0 ? d : 2 * n + d] = v;
+    }
+}
+
+// Householder reflector I - 2 u u^T / n (the Householder multipliers of the
+// tests Sec. 7.1 cites, read as an orthogonal reflector): u_i = +-1 from the
+// low bit of Philox word 0 at (i, 0, tag, 0).
+__global__ void k_householder(double *u, int64_t n, uint64_t seed, uint64_t sid) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const U4 w = philox((uint64_t)i, 0, kTagHouse, 0, seed, sid);
+        u[i] = (w.w[0] & 1ull) ? -1.0 : 1.0;
+    }
+}
+
 // Circulant with a +-1 first column (the paper's test multipliers): attempt
 // a takes g_i from the low bit of Philox word 0 at (i, 0, tag, a) and is
 // kept when no DFT bin of power-of-two order vanishes.  Exact integer test:
@@ -287,12 +317,12 @@ __global__ void k_invert(const int32_t *rows, const int8_t *signs, int32_t *inv_
     }
 }
 
-__global__ void k_circ_dense(const double *g, int64_t n, double *G, int64_t ldg) {
+__global__ void k_circ_dense(const double *g, int64_t cn, int64_t n, double *G, int64_t ldg) {
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n * n;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = idx / n, j = idx % n;
         int64_t d = i - j;
-        if (d < 0) d += n;
+        if (d < 0) d += cn;
         G[i * ldg + j] = g[d];
     }
 }
@@ -355,6 +385,19 @@ cudaError_t launch_make_circulant(double *g, int64_t n, uint64_t seed, uint64_t 
     return cudaGetLastError();
 }
 
+cudaError_t launch_make_toeplitz(double *g, int64_t n, uint64_t seed, uint64_t sid, double scale, genp_prec grid,
+                                 cudaStream_t s) {
+    note_launch();
+    k_toeplitz<<<grid_for(2 * n, 256), 256, 0, s>>>(g, n, seed, sid, scale, grid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_make_householder(double *u, int64_t n, uint64_t seed, uint64_t sid, cudaStream_t s) {
+    note_launch();
+    k_householder<<<grid_for(n, 256), 256, 0, s>>>(u, n, seed, sid);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_make_circulant_pm1(double *g, int64_t n, uint64_t seed, uint64_t sid, int *attempt,
                                       cudaStream_t s) {
     note_launch();
@@ -384,9 +427,10 @@ cudaError_t launch_batch_draw(const BatchDesc *d, int count, uint64_t seed, bool
     return cudaGetLastError();
 }
 
-cudaError_t launch_circulant_to_dense(const double *g, int64_t n, double *G, int64_t ldg, cudaStream_t s) {
+cudaError_t launch_circulant_to_dense(const double *g, int64_t cn, int64_t n, double *G, int64_t ldg,
+                                      cudaStream_t s) {
     note_launch();
-    k_circ_dense<<<grid_for(n * n, 256), 256, 0, s>>>(g, n, G, ldg);
+    k_circ_dense<<<grid_for(n * n, 256), 256, 0, s>>>(g, cn, n, G, ldg);
     return cudaGetLastError();
 }
 

@@ -19,6 +19,7 @@ namespace genp {
 namespace {
 
 int g_default_digits = 7;
+int g_precond_digits = 7;
 
 // exponent e with max|x| < 2^e (0 for an all-zero row)
 __device__ __forceinline__ int scale_exp(double amax) {
@@ -141,9 +142,16 @@ int64_t sliced_kpad(int64_t K) { return (K + 63) / 64 * 64; }
 int sliced_slices(int nd) { return nd; }
 int sliced_digits() { return g_default_digits; }
 int set_sliced_digits(int nd) {
-    if (!sliced::supported(nd)) return -1;
+    if (!sliced::factor_supported(nd)) return -1;
     const int old = g_default_digits;
     g_default_digits = nd;
+    return old;
+}
+int sliced_precond_digits() { return g_precond_digits; }
+int set_sliced_precond_digits(int nd) {
+    if (!sliced::supported(nd)) return -1;
+    const int old = g_precond_digits;
+    g_precond_digits = nd;
     return old;
 }
 
@@ -156,6 +164,8 @@ cudaError_t slice_rows(int nd, const double *src, int64_t lds, int64_t m, int64_
     const int64_t kpad = sliced_kpad(K);
     note_launch();
     switch (nd) {
+        case 3: k_slice_rows<3><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps); break;
+        case 4: k_slice_rows<4><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps); break;
         case 5: k_slice_rows<5><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps); break;
         case 6: k_slice_rows<6><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps); break;
         default: k_slice_rows<7><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps); break;
@@ -174,6 +184,8 @@ cudaError_t slice_cols_T(int nd, const double *src, int64_t lds, int64_t K, int6
     if (g.y > 65535u) return cudaErrorInvalidValue;
     note_launch();
     switch (nd) {
+        case 3: k_slice_cols_T<3><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps); break;
+        case 4: k_slice_cols_T<4><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps); break;
         case 5: k_slice_cols_T<5><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps); break;
         case 6: k_slice_cols_T<6><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps); break;
         default: k_slice_cols_T<7><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps); break;

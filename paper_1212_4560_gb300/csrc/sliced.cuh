@@ -23,9 +23,12 @@
 namespace genp {
 namespace sliced {
 
-// Supported digit counts: 5 (about 33 correct bits on Gaussian data), 6
-// (about 40) and 7 (about 47).  ND groups of 64 TMEM columns each.
-__host__ __device__ constexpr bool supported(int nd) { return nd >= 5 && nd <= 7; }
+// Supported digit counts: 3 (about 19 correct bits on Gaussian data), 4
+// (about 26), 5 (about 33), 6 (about 40) and 7 (about 47).  ND groups of 64
+// TMEM columns each.  The factorization takes 5 to 7 digits; a product that
+// only has to be as accurate as the factors it feeds (A G) may take fewer.
+__host__ __device__ constexpr bool supported(int nd) { return nd >= 3 && nd <= 7; }
+__host__ __device__ constexpr bool factor_supported(int nd) { return nd >= 5 && nd <= 7; }
 
 }  // namespace sliced
 }  // namespace genp

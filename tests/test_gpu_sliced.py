@@ -71,7 +71,7 @@ def bound(nd, A, B):
     return 2.0 ** -(7 * nd - 5) * K * np.abs(A).max(1)[:, None] * np.abs(B).max(0)[None, :]
 
 
-@pytest.mark.parametrize("nd", [5, 6, 7])
+@pytest.mark.parametrize("nd", [3, 4, 5, 6, 7])
 @pytest.mark.parametrize("m,n,K", [(1, 1, 1), (128, 64, 64), (200, 130, 1000), (77, 300, 513)])
 def test_gemm_sliced_integers_exact(genp_lib, nd, m, n, K):
     rng = np.random.default_rng(m * 7 + n + K)
@@ -81,7 +81,7 @@ def test_gemm_sliced_integers_exact(genp_lib, nd, m, n, K):
     assert np.array_equal(D.cpu().numpy(), oracle.matmul(A, B))
 
 
-@pytest.mark.parametrize("nd", [5, 6, 7])
+@pytest.mark.parametrize("nd", [3, 4, 5, 6, 7])
 @pytest.mark.parametrize("m,n,K", [(128, 64, 512), (300, 260, 700), (129, 65, 1536)])
 def test_gemm_sliced_gaussian(genp_lib, nd, m, n, K):
     rng = np.random.default_rng(nd * 1000 + K)
@@ -94,7 +94,7 @@ def test_gemm_sliced_gaussian(genp_lib, nd, m, n, K):
     assert np.median(err / np.abs(ref)) <= 2.0 ** -(7 * nd - 5)
 
 
-@pytest.mark.parametrize("nd", [5, 7])
+@pytest.mark.parametrize("nd", [3, 5, 7])
 def test_gemm_sliced_schur_form_and_extremes(genp_lib, nd):
     """D <- D - A B in place, with every digit at its largest (entries
     0.999 give leading digits of 128 and the group sums reach 2^24 at K = 512)."""
@@ -110,15 +110,29 @@ def test_gemm_sliced_schur_form_and_extremes(genp_lib, nd):
 def test_gemm_sliced_rejects_bad_args(genp_lib):
     A = torch.zeros((4, 4), dtype=torch.float64, device=DEV)
     s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    assert genp_lib.genp_gemm_sliced(4, 4, 4, 1.0, _p(A), 4, _p(A), 4, 0.0, _p(A), 4, 4, s) == -1   # 4 digits
+    assert genp_lib.genp_gemm_sliced(4, 4, 4, 1.0, _p(A), 4, _p(A), 4, 0.0, _p(A), 4, 2, s) == -1   # 2 digits
+    assert genp_lib.genp_gemm_sliced(4, 4, 4, 1.0, _p(A), 4, _p(A), 4, 0.0, _p(A), 4, 8, s) == -1   # 8 digits
     assert genp_lib.genp_gemm_sliced(4, 4, 4, 1.0, _p(A), 3, _p(A), 4, 0.0, _p(A), 4, 7, s) == -1   # lda < K
-    assert genp_lib.genp_sliced_digits(3) == -1
+    assert genp_lib.genp_sliced_digits(4) == -1          # the factorization takes 5 to 7
     assert genp_lib.genp_sliced_digits(0) in (5, 6, 7)
+    assert genp_lib.genp_sliced_precondition_digits(2) == -1
+    assert genp_lib.genp_sliced_precondition_digits(8) == -1
+    assert genp_lib.genp_sliced_precondition_digits(0) in (3, 4, 5, 6, 7)
 
 
-@pytest.mark.parametrize("digits", [5, 7], indirect=True)
+@pytest.fixture
+def pdigits(genp_lib, request):
+    nd = request.param
+    old = genp_lib.genp_sliced_precondition_digits(nd)
+    assert old in (3, 4, 5, 6, 7)
+    yield nd
+    genp_lib.genp_sliced_precondition_digits(old)
+
+
+@pytest.mark.parametrize("pdigits", [3, 4, 5, 7], indirect=True)
 @pytest.mark.parametrize("n", [200, 1100])
-def test_precondition_sliced(g, digits, n):
+def test_precondition_sliced(g, pdigits, n):
+    digits = pdigits
     A, _, _ = W.lead_deficient(n, 32, 16, 1, seed=n)
     A = A.numpy()
     G = g.make_multiplier(g.GAUSSIAN, n, seed=3)
@@ -242,5 +256,22 @@ def test_sliced_gmres_ir(g, digits, kappa):
     x = X.cpu().numpy()
     assert oracle.backward_error(A, x, B) <= 1e-14
     assert np.abs(x - Xs).max() / np.abs(Xs).max() <= 1e-14 * kappa * 10
+    assert info.refine_iters <= 4
+    assert g._lib.load().genp_device_check(1) == 0
+
+
+@pytest.mark.parametrize("pdigits", [4, 5], indirect=True)
+@pytest.mark.parametrize("digits", [7], indirect=True)
+def test_sliced_gmres_ir_short_precondition(g, digits, pdigits):
+    """A G from 4 or 5 digits (genp_sliced_precondition_digits) and 7-digit
+    factors: GMRES-IR, with the FP64 residual on A and the FP64 update with
+    G, still takes the kappa = 1e6 system to eta <= 1e-14."""
+    n = 1024
+    A, Xs, B = (t.numpy() for t in W.svd_kappa(n, 1e6, 1, seed=3))
+    X, info, G, F = g.solve_system(cu(A), cu(B), kind=g.GAUSSIAN, seed=4, prec=g.BF16_SLICED, refine_steps=6,
+                                   tol=1e-16, method=1)
+    x = X.cpu().numpy()
+    assert oracle.backward_error(A, x, B) <= 1e-14
+    assert np.abs(x - Xs).max() / np.abs(Xs).max() <= 1e-14 * 1e6 * 10
     assert info.refine_iters <= 4
     assert g._lib.load().genp_device_check(1) == 0

@@ -442,9 +442,12 @@ def run_ours(a):
                     "share_of_step": (t_ms / a.steps) / ms_per_step,
                     "algorithmic": f"{pairs} x 2 m n Kpad BF16 flop per launch (digit pairs of the sliced product); "
                                    f"FP64-equivalent work is 1/{pairs} of it",
-                    # dram read+write bytes of one n = 4096 precondition launch under ncu, scaled by the
-                    # tiles processed (m n) to the n = 16384 chunk launches; null where not captured
-                    "traffic": None}
+                    # dram read+write bytes of one n = 4096, K = 512 A G chunk launch under ncu
+                    # (294 MB: 143.6 KB per 128 x 64 tile, mostly the double-float accumulator's
+                    # read-modify-write), scaled by the tiles to this size's chunk launches
+                    "traffic": 294.0e6 * (n / 4096) ** 2 if nd == 7 else None,
+                    "traffic_basis": "A G chunk launch (K = 512); Schur-update launches (K = 256) move about "
+                                     "the same bytes per tile for half the flops"}
     elif a.kind == "gaussian" and a.prec in ("bf16", "bf16x3"):
         terms = 3 if a.prec == "bf16x3" else 1
         achieved = terms * 2.0 * n**3 / (phase_ms["precondition"] / 1e3) / 1e12

@@ -252,6 +252,14 @@ def precondition(A: np.ndarray, M: dict, rows=None) -> np.ndarray:
     return C
 
 
+def precondition_left(A: np.ndarray, M: dict) -> np.ndarray:
+    """C = G A, the GM half of Thm. 4.1 / Cor. 4.1 (the multiplier on the
+    left), by the definition: the product with the dense G."""
+    if M["kind"] == KIND_IDENTITY:
+        return _c(A).copy()
+    return matmul(M["G"], _c(A))
+
+
 def apply_multiplier(M: dict, Y: np.ndarray, trans: bool = False) -> np.ndarray:
     """X = G Y (or G^T Y), Y of shape (n, nrhs), by the definition of G."""
     Y = _c(Y)
@@ -357,27 +365,33 @@ def rel_residual_2(A, X, B) -> float:
     return float(np.linalg.norm(R) / np.linalg.norm(B))
 
 
-def solve(A: np.ndarray, B: np.ndarray, M: dict, refine_steps: int = 0, tol: float = 0.0):
+def solve(A: np.ndarray, B: np.ndarray, M: dict, refine_steps: int = 0, tol: float = 0.0, side: str = "right"):
     """The whole method: C = A G, GENP(C), y = U^-1 L^-1 b, x = G y, then up
     to ``refine_steps`` refinement steps r = b - A x, C d = r, x += G d,
     stopping early when the backward error reaches ``tol`` or stops halving.
+    side "left": C = G A, GENP(C), x = U^-1 L^-1 (G b), and the refinement
+    steps d = U^-1 L^-1 (G r), x += d.
 
     Returns dict(x, LU, step, eta) with eta the backward errors after the
     solve and after each refinement step."""
     B2 = _c(B).reshape(B.shape[0], -1)
-    C = precondition(A, M)
+    left = side == "left"
+    C = precondition_left(A, M) if left else precondition(A, M)
     LU, step = genp(C)
     out = {"LU": LU, "step": step, "C": C}
     if step >= 0:
         out.update(x=None, eta=[np.inf])
         return out
-    X = apply_multiplier(M, lu_solve(LU, B2))
+    if left:
+        X = lu_solve(LU, apply_multiplier(M, B2))
+    else:
+        X = apply_multiplier(M, lu_solve(LU, B2))
     eta = [backward_error(A, X, B2)]
     for _ in range(refine_steps):
         if eta[-1] <= tol:
             break
         R = residual(A, X, B2)
-        D = apply_multiplier(M, lu_solve(LU, R))
+        D = lu_solve(LU, apply_multiplier(M, R)) if left else apply_multiplier(M, lu_solve(LU, R))
         X = X + D
         eta.append(backward_error(A, X, B2))
         if eta[-1] > eta[-2] / 2:

@@ -624,3 +624,44 @@ def test_householder_repairs_rank_one_deficiency_only():
     A2, _, _ = (t.numpy() for t in W.lead_deficient(256, 32, 16, 1, 0))
     LU, k = oracle.genp(oracle.precondition(A2, oracle.multiplier(6, 256, seed=5)))
     assert k >= 0 or np.abs(np.triu(LU)).max() / np.abs(A2).max() > 1e10
+
+
+# ------------------------------------------------ the left multiplier (G A)
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 5])
+def test_left_multiplier_solves_leading_singular_system(kind):
+    """The GM half of Cor. 4.1: the leading blocks of G A are nonsingular
+    w.p. 1, so GENP of C = G A is safe on the rank-16 workload; x solves
+    A x = b because G A x = G b; refinement reaches eta <= 1e-14 and the
+    GEPP solution within 1e-14 kappa."""
+    A, X, B = (t.numpy() for t in W.lead_deficient(256, 32, 16, 1, 0))
+    M = oracle.multiplier(kind, 256, seed=5)
+    C = oracle.precondition_left(A, M)
+    assert np.array_equal(C, oracle.matmul(M["G"], A))
+    r = oracle.solve(A, B, M, refine_steps=5, tol=1e-16, side="left")
+    assert r["step"] == -1
+    assert r["eta"][-1] <= 1e-14
+    kappa = np.linalg.cond(A, np.inf)
+    xd = oracle.gepp_solve(A, B)
+    assert np.abs(r["x"] - xd).max() / np.abs(xd).max() <= 1e-14 * kappa
+
+
+def test_left_multiplier_leading_minors_by_leibniz():
+    """Every leading minor of G A is nonzero (checked exactly, in rationals)
+    on a nonsingular 5 x 5 A whose leading 1 x 1 and 2 x 2 blocks are
+    singular: plain GENP breaks down, GENP of G A does not, and the product
+    of its pivots is det(G A) = det(G) det(A)."""
+    A = np.array([[0., 2., 0., 1., 3.], [0., 4., 1., 0., 1.], [0., 1., 5., 2., 2.], [1., 0., 2., 3., 1.],
+                  [3., 1., 1., 1., 4.]])
+    assert oracle.det_leibniz(A[:1, :1]) == 0 and oracle.det_leibniz(A[:2, :2]) == 0
+    assert oracle.det_leibniz(A) != 0
+    assert oracle.genp(A)[1] == 0
+    M = oracle.multiplier(0, 5, seed=3)
+    C = oracle.precondition_left(A, M)
+    for k in range(1, 6):
+        assert oracle.det_leibniz(C[:k, :k]) != 0
+    LU, step = oracle.genp(C)
+    assert step == -1
+    prod = float(np.prod(np.diag(LU)))
+    ref = float(oracle.det_leibniz(M["G"]) * oracle.det_leibniz(A))
+    assert abs(prod - ref) <= 1e-12 * abs(ref)

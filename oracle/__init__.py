@@ -68,6 +68,7 @@ def lib():
         L.or_mult_toeplitz_f32.argtypes = [_i64, _u64, _u64, ctypes.c_float, _dp]
         L.or_toeplitz_to_dense.argtypes = [_i64, _dp, _dp, _i64]
         L.or_mult_householder_pm1.argtypes = [_i64, _u64, _u64, _dp]
+        L.or_mult_sketch.argtypes = [_i64, _i64, ctypes.c_int, _u64, _u64, ctypes.c_double, _dp, _i64]
         L.or_householder_to_dense.argtypes = [_i64, _dp, _dp, _i64]
         L.or_sparse_to_dense.argtypes = [_i64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, _dp, _i64]
         L.or_matmul.argtypes = [_i64, _i64, _i64, _dp, _i64, _dp, _i64, _dp, _i64]
@@ -407,6 +408,44 @@ def adjoint(A: np.ndarray, X: np.ndarray, gX: np.ndarray):
     lam = gepp_solve_T(A, gX)
     dA = -matmul(lam, _c(X).T.copy())
     return dA, lam
+
+
+# --------------------------------------------------------------------------
+# Randomized low-rank approximation (Sec. 5, Proto-Alg. 5.1; Sec. 7.2)
+# --------------------------------------------------------------------------
+
+def sketch_multiplier(m: int, r: int, seed: int, stream: int = 0, toeplitz: bool = False,
+                      scale: float = 1.0) -> np.ndarray:
+    """The m x r multiplier of Stage 1: Gaussian G_{0,scale}^{m x r}, or the
+    Gaussian Toeplitz matrix of Table 7.3."""
+    G = np.empty((m, r))
+    lib().or_mult_sketch(m, r, int(toeplitz), seed, stream, float(scale), _p(G), r)
+    return G
+
+
+def lowrank_approx(A: np.ndarray, G: np.ndarray):
+    """Proto-Alg. 5.1 with an orthonormal T as in the tests of Sec. 7.2:
+    Stage 1 T' = A^T G; the orthonormal factor Q of T' = Q R with a
+    positive diagonal of R (Fact 2.2: then Q is unique), by a library QR with
+    the column signs fixed; Stage 3 A_hat = A T (T^T T)^{-1} T^T = (A Q) Q^T.
+    Returns dict(B = A^T G, Q, AQ)."""
+    A = _c(A)
+    B = matmul(A.T.copy(), _c(G))
+    Q, R = np.linalg.qr(B, mode="reduced")
+    sgn = np.where(np.diag(R) < 0, -1.0, 1.0)
+    Q = Q * sgn[None, :]
+    return {"B": B, "Q": Q, "AQ": matmul(A, Q)}
+
+
+def lowrank_residuals(A: np.ndarray, B: np.ndarray, Q: np.ndarray, AQ: np.ndarray, T_lead: np.ndarray):
+    """The residual norms of Tables 7.2 / 7.3 (2-norms, Sec. 2.4):
+    rn1 = ||B Y - T_lead|| with Y the least-squares solution (B's columns
+    approximate the leading right singular space of A, spanned by T_lead);
+    rn2 = ||A - A Q Q^T||."""
+    Y = np.linalg.lstsq(B, T_lead, rcond=None)[0]
+    rn1 = float(np.linalg.norm(B @ Y - T_lead, 2))
+    rn2 = float(np.linalg.norm(_c(A) - AQ @ Q.T, 2))
+    return rn1, rn2
 
 
 # --------------------------------------------------------------------------

@@ -100,7 +100,9 @@ enum {
     OR_TAG_SIGN = 0x13,
     OR_TAG_CIRC_PM1 = 0x16,
     OR_TAG_TOEP = 0x17,
-    OR_TAG_HOUSE = 0x18
+    OR_TAG_HOUSE = 0x18,
+    OR_TAG_SKETCH = 0x19,
+    OR_TAG_SKETCH_TOEP = 0x1A
 };
 #define OR_POLAR_BLOCKS 32
 
@@ -340,6 +342,20 @@ OR_EXPORT void or_householder_to_dense(int64_t n, const double *u, double *G, in
             double v = 2.0 * u[i] * u[j];
             v = v / (double)n;
             G[i * ldg + j] = (i == j ? 1.0 : 0.0) - v;
+        }
+}
+
+/* Rectangular multipliers of the low-rank approximation (Proto-Alg. 5.1,
+ * Stage 1, and the tests of Sec. 7.2), m x r, scale^2 the variance:
+ *  Gaussian G[i][j] = scale z(i r + j) on its own tag;
+ *  Toeplitz G[i][j] = t_{i-j}, d = i - j in [-(r-1), m-1] drawn at index
+ *  d + r - 1 (m + r - 1 independent entries). */
+OR_EXPORT void or_mult_sketch(int64_t m, int64_t r, int toeplitz, uint64_t seed, uint64_t stream, double scale,
+                              double *G, int64_t ldg) {
+    for (int64_t i = 0; i < m; ++i)
+        for (int64_t j = 0; j < r; ++j) {
+            if (toeplitz) G[i * ldg + j] = or_gauss(seed, stream, OR_TAG_SKETCH_TOEP, (uint64_t)(i - j + r - 1)) * scale;
+            else G[i * ldg + j] = or_gauss(seed, stream, OR_TAG_SKETCH, (uint64_t)(i * r + j)) * scale;
         }
 }
 

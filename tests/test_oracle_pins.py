@@ -665,3 +665,50 @@ def test_left_multiplier_leading_minors_by_leibniz():
     prod = float(np.prod(np.diag(LU)))
     ref = float(oracle.det_leibniz(M["G"]) * oracle.det_leibniz(A))
     assert abs(prod - ref) <= 1e-12 * abs(ref)
+
+
+# ------------------------------------------------ low-rank approximation (Sec. 5)
+
+def test_sketch_multiplier_structure():
+    G = oracle.sketch_multiplier(50, 8, seed=3)
+    assert G.shape == (50, 8) and len(np.unique(G)) == 400
+    T = oracle.sketch_multiplier(50, 8, seed=3, toeplitz=True)
+    for i in range(1, 50):
+        for j in range(1, 8):
+            assert T[i, j] == T[i - 1, j - 1]               # constant along diagonals
+    g = oracle.sketch_multiplier(4000, 5, seed=1).ravel()
+    assert abs(g.mean()) < 0.03 and abs(g.std() - 1.0) < 0.03
+
+
+@pytest.mark.parametrize("n,q", [(64, 1), (128, 8), (256, 32)])
+def test_lowrank_exact_rank_is_recovered(n, q):
+    """With an exactly rank-q A (tail singular values 0) the sketch A^T G
+    spans A's row space w.p. 1, so A Q Q^T reproduces A to rounding, and
+    B Y reproduces the leading right singular vectors (Thm. 5.1 with no
+    perturbation)."""
+    A, S, T, s = (t.numpy() for t in W.lowrank(n, q, seed=2))
+    A = (S[:, :q] * s[:q]) @ T[:, :q].T
+    r = oracle.lowrank_approx(A, oracle.sketch_multiplier(n, q, seed=5))
+    assert np.allclose(r["Q"].T @ r["Q"], np.eye(q), atol=1e-13)
+    rn1, rn2 = oracle.lowrank_residuals(A, r["B"], r["Q"], r["AQ"], T[:, :q])
+    assert rn2 <= 1e-13 and rn1 <= 1e-10
+
+
+@pytest.mark.parametrize("toeplitz", [False, True])
+def test_lowrank_residual_between_eckart_young_and_tail_bound(toeplitz):
+    """For the Table 7.2 / 7.3 inputs (sigma_{q+1} = 1e-10) every rank-q
+    approximation errs by at least sigma_{q+1} (Eckart-Young), and the
+    randomized one stays within a modest factor of it (Sec. 5, the paper's
+    observed 1e-9 .. 1e-6)."""
+    n, q = 128, 8
+    A, S, T, s = (t.numpy() for t in W.lowrank(n, q, seed=4))
+    assert abs(np.linalg.norm(A, 2) - 1.0) < 1e-12
+    r = oracle.lowrank_approx(A, oracle.sketch_multiplier(n, q, seed=9, toeplitz=toeplitz))
+    rn1, rn2 = oracle.lowrank_residuals(A, r["B"], r["Q"], r["AQ"], T[:, :q])
+    assert 1e-10 * (1 - 1e-6) <= rn2 <= 1e-5
+    assert rn1 <= 1e-4
+    # Q is the QR factor with a positive diagonal: B = Q R, R upper triangular
+    R = r["Q"].T @ r["B"]
+    assert np.allclose(np.tril(R, -1), 0.0, atol=1e-12 * np.abs(R).max())
+    assert np.all(np.diag(R) > 0)
+    assert np.allclose(r["Q"] @ R, r["B"], atol=1e-13 * np.abs(r["B"]).max())

@@ -27,6 +27,11 @@ that GENP without a multiplier fails) at the sizes of the benchmark suite:
 * ``table71``: the paper-shaped Table 7.1 analogue: A = [[A11, A12],
   [A21, A22]] with A11 of numerical rank n/2-1 (a rank-(n/2-1) Gaussian
   product plus 1e-12 times a Gaussian), other blocks Gaussian.
+* ``lowrank``: the inputs of Tables 7.2 and 7.3 (Sec. 7.2): A = S diag(s)
+  T^T with s_j = 1/j for j <= q and 1e-10 beyond (numerical rank q,
+  ||A|| = 1, kappa(A) = 1e10), S and T orthogonal, each a product of four
+  Householder reflectors with N(0,1) vectors (the paper says only "random
+  orthogonal").
 """
 from __future__ import annotations
 
@@ -131,3 +136,25 @@ def table71(n: int, seed: int, device="cpu"):
     A[:h, :h] = P @ Q / (h ** 0.5) + 1e-12 * _randn((h, h), ga, device)
     X = _randn((n, 1), _gen(seed, TAG_X, device), device)
     return A, X, A @ X
+
+
+def _reflectors(n: int, gen, device, count: int = 4) -> torch.Tensor:
+    """Product of ``count`` Householder reflectors I - 2 v v^T / v^T v with
+    N(0,1) vectors v, formed densely (n x n, orthogonal)."""
+    Q = torch.eye(n, dtype=torch.float64, device=device)
+    for _ in range(count):
+        v = _randn((n, 1), gen, device)
+        Q = Q - (2.0 / float((v * v).sum())) * (Q @ v) @ v.T
+    return Q
+
+
+def lowrank(n: int, q: int, seed: int, device="cpu"):
+    """Tables 7.2 / 7.3 inputs: A = S diag(s) T^T, s_j = 1/j (j <= q), 1e-10
+    (j > q).  Returns A, S, T, s."""
+    gs = _gen(seed, TAG_A, device)
+    S = _reflectors(n, gs, device)
+    T = _reflectors(n, gs, device)
+    s = torch.full((n,), 1e-10, dtype=torch.float64, device=device)
+    s[:q] = 1.0 / torch.arange(1, q + 1, dtype=torch.float64, device=device)
+    A = (S * s) @ T.T
+    return A, S, T, s

@@ -65,12 +65,13 @@ def parse():
     p.add_argument("--kind", default="gaussian", choices=list(KINDS))
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--tol", type=float, default=1e-14)
-    p.add_argument("--workload", default="svd", choices=["lead", "svd", "batched", "diff", "table71"],
+    p.add_argument("--workload", default="svd", choices=["lead", "svd", "batched", "diff", "table71", "lowrank"],
                    help="lead: N(0,1) A with a rank-deficient leading block; svd: A = J U diag(sigma) V^T; "
                         "batched: 10k systems n in [16,512], a11 = 0, FP32 factors + FP64 refinement; "
                         "diff: 256 x n=1024 FP32 systems, circulant G, 8 RHS, forward + adjoint; "
                         "table71: the paper-shaped Table 7.1 experiment (+-1 circulant multipliers, 100 systems "
-                        "per n in 64, 256, 1024, residuals after 0 and 1 refinement steps, and plain GENP)")
+                        "per n in 64, 256, 1024, residuals after 0 and 1 refinement steps, and plain GENP); "
+                        "lowrank: the paper-shaped Tables 7.2 / 7.3 experiment (randomized rank-q approximation)")
     p.add_argument("--count", type=int, default=None, help="systems in the batched / diff workloads")
     p.add_argument("--kappa", type=float, default=1e6, help="condition number of the svd workload")
     p.add_argument("--prec", default="sliced", choices=list(PRECS))
@@ -324,20 +325,23 @@ def run_ours(a):
     F = genp.factor(C, prec=prec)
     stream = torch.cuda.current_stream(dev)
 
-    def step(i, ev=None):
+    def step(i, ev=None, Ain=None, Bin=None):
+        Ai = A if Ain is None else Ain
+        Bi = B if Bin is None else Bin
+
         def mark(k):
             if ev is not None:
                 ev[k].record(stream)
         mark(0)
         genp.redraw_multiplier(G, seed=1000 + i, stream_id=rank)
         mark(1)
-        genp.precondition(G, A, C, c_prec=prec)
+        genp.precondition(G, Ai, C, c_prec=prec)
         mark(2)
         genp.refactor(F, C)
         mark(3)
-        genp.solve(F, G, B, X)
+        genp.solve(F, G, Bi, X)
         mark(4)
-        genp.refine(A, F, G, B, X, tol=a.tol, max_iter=max_iter, method=method)
+        genp.refine(Ai, F, G, Bi, X, tol=a.tol, max_iter=max_iter, method=method)
         mark(5)
         genp.adjoint(F, G, X, X, dA, dB)
         mark(6)
@@ -389,36 +393,64 @@ def run_ours(a):
     tflops = world * (fact + ag) * a.steps / (total_ms / 1e3) / 1e12
 
     # e2e: the same step through the C ABI with the system in pinned HOST memory;
-    # the copies in (A, B) and out (X) sit inside the timed region.
+    # every step's copies in (A, B) and out (X) sit inside the timed region.
+    # The inputs are double-buffered: step i + 1's A and B travel on a copy
+    # stream while step i solves (a stream of systems, as a server sees it).
     e2e = None
     if not a.no_e2e:
         A_h = A_cpu.pin_memory()
         B_h = B_cpu.pin_memory()
-        X_h = torch.empty((n, nrhs), dtype=torch.float64).pin_memory()
+        X_h = [torch.empty((n, nrhs), dtype=torch.float64).pin_memory() for _ in range(2)]
+        Ab, Bb = [A, torch.empty_like(A)], [B, torch.empty_like(B)]
+        cs = torch.cuda.Stream(dev)
+        copied = [torch.cuda.Event() for _ in range(2)]
+        used = [torch.cuda.Event() for _ in range(2)]
         k_e2e = max(2, min(a.steps, 4))
-        for i in range(1):
-            A.copy_(A_h, non_blocking=True)
-            B.copy_(B_h, non_blocking=True)
-            step(10_000 + i)
-            X_h.copy_(X, non_blocking=True)
+
+        def e2e_run(k, base):
+            cs.wait_stream(stream)
+            with torch.cuda.stream(cs):
+                Ab[0].copy_(A_h, non_blocking=True)
+                Bb[0].copy_(B_h, non_blocking=True)
+                copied[0].record(cs)
+            for i in range(k):
+                b = i % 2
+                if i + 1 < k:
+                    nb = (i + 1) % 2
+                    with torch.cuda.stream(cs):
+                        if i >= 1:
+                            cs.wait_event(used[nb])
+                        Ab[nb].copy_(A_h, non_blocking=True)
+                        Bb[nb].copy_(B_h, non_blocking=True)
+                        copied[nb].record(cs)
+                stream.wait_event(copied[b])
+                step(base + i, Ain=Ab[b], Bin=Bb[b])
+                used[b].record(stream)
+                X_h[b].copy_(X, non_blocking=True)
+
+        e2e_run(1, 10_000)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for i in range(k_e2e):
-            A.copy_(A_h, non_blocking=True)
-            B.copy_(B_h, non_blocking=True)
-            step(20_000 + i)
-            X_h.copy_(X, non_blocking=True)
+        e2e_run(k_e2e, 20_000)
         e1.record(stream)
         torch.cuda.synchronize()
         e_ms = e0.elapsed_time(e1)
+        # the copy engine's own rate, for the record
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        A.copy_(A_h, non_blocking=True)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        h2d_gbs = A_h.numel() * 8 / (h0.elapsed_time(h1) / 1e3) / 1e9
         if world > 1:
             t = torch.tensor([e_ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e_ms = float(t.item())
         e2e = {"value": world * k_e2e / (e_ms / 1e3), "unit": "solves/s",
-               "h2d_bytes_per_step": A_h.numel() * 8 + B_h.numel() * 8, "d2h_bytes_per_step": X_h.numel() * 8,
-               "steps": k_e2e}
+               "h2d_bytes_per_step": A_h.numel() * 8 + B_h.numel() * 8, "d2h_bytes_per_step": X_h[0].numel() * 8,
+               "steps": k_e2e, "inputs": "double-buffered: step i+1's copy overlaps step i",
+               "h2d_gbs_alone": h2d_gbs}
 
     if rank != 0:
         if world > 1:
@@ -648,6 +680,12 @@ def run_batched(a):
     fact, ag = 2.0 * n3 / 3.0, (2.0 * n3 if not diff else sum(10.0 * n * n * np.log2(n) for n in sizes))
     tflops = world * (fact + ag) * a.steps / (total_ms / 1e3) / 1e12
     peak = 152 * 128 * 2 * 2.070e9 / 1e12
+    # The FP64 residuals r = b - A x of the refinement (2 n^2 nrhs flop per
+    # outer step and system) run on units 64 times slower than the FP32 pipe:
+    # counted as 64 FP32-equivalent flop each in the ALU roofline below.
+    iters = np.asarray(st["iters"], dtype=np.float64)
+    fp64_flop = float(sum(2.0 * float(nn) ** 2 * nrhs * (it + 1) for nn, it in zip(sizes, iters)))
+    eq_tflops = world * (fact + ag + 64.0 * fp64_flop) * a.steps / (total_ms / 1e3) / 1e12
     e2e = None
     if not a.no_e2e:
         A_h = Ap.cpu().pin_memory()
@@ -694,9 +732,15 @@ def run_batched(a):
                        "l2": "inputs larger than L2 (no flush)", "graph": "one CUDA graph replay per step",
                        "block_sizes": {str(nn): plan.block_size(nn) for nn in (16, 128, 512, 1024)}},
             "tflops": tflops,
-            "roofline": {"kernel": "k_batched (persistent, CTA-level FFMA GEMM dominant)", "bound": "alu",
-                         "achieved": tflops / world, "peak": peak, "unit": "TFLOP/s", "frac": tflops / world / peak,
-                         "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz", "traffic": None},
+            "roofline": {"kernel": "k_batched (persistent: CTA-level FFMA GEMM, FP64 residuals)", "bound": "alu",
+                         "achieved": eq_tflops / world, "peak": peak, "unit": "TFLOP/s (FP32-equivalent)",
+                         "frac": eq_tflops / world / peak,
+                         "peak_source": "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz",
+                         "algorithmic": "(2/3 + 2) n^3 FP32 flop per system (factor + A G; 10 n^2 log2 n for the "
+                                        "circulant A G) + 64 x the FP64 residual flop 2 n^2 nrhs (iters + 1) "
+                                        "(GB300's FP64:FP32 throughput ratio); the double-float refactorization "
+                                        "of escalated systems is not counted",
+                         "fp32_only_frac": tflops / world / peak, "traffic": None},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * a.steps,
             "gpu_launches_per_step": launches_per_step,
             "bwd_err_max": float(np.max(st["eta"])), "bwd_err_unrefined_median": float(np.median(st["eta0"])),
@@ -771,10 +815,66 @@ def run_table71(a):
     print(json.dumps(line), flush=True)
 
 
+def run_lowrank(a):
+    """Sec. 7.2 / Tables 7.2 and 7.3, paper-shaped: for n = 64, 128, 256 and
+    numerical rank q = 1, 8, 32 (workloads.lowrank: s_j = 1/j up to q,
+    1e-10 beyond), 100 seeded matrices each, genp_lowrank with a Gaussian
+    (Table 7.2) or Gaussian Toeplitz (Table 7.3, q = 8, 32) sketch of r = q
+    columns; statistics of rn1 = ||B Y - T_q|| and rn2 = ||A - A Q Q^T||
+    (2-norms, on the host).  The paper's inputs came from error-free ring
+    operations on matrices it does not give: its numbers are context."""
+    import torch
+
+    import paper_1212_4560_gb300 as genp
+    import workloads as W
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1212_4560_gb300 import build as _b
+    _b.build()
+    count = a.count or 100
+
+    def stats(v):
+        v = np.array(v)
+        return {"min": float(v.min()), "max": float(v.max()), "mean": float(v.mean()), "std": float(v.std())}
+
+    rows = []
+    t0 = time.perf_counter()
+    gpu_ms = 0.0
+    for toep in (False, True):
+        for q in (1, 8, 32):
+            if toep and q == 1:
+                continue
+            for n in (64, 128, 256):
+                r1, r2 = [], []
+                for seed in range(count):
+                    A, S, T, s = W.lowrank(n, q, seed)
+                    Ad = A.to(dev)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    G, Q, R, AQ, st = genp.lowrank(Ad, q, kind=genp.TOEPLITZ if toep else genp.GAUSSIAN, seed=seed)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    gpu_ms += e0.elapsed_time(e1)
+                    An, Gn, Qn, AQn, Tn = (x.cpu().numpy() for x in (A, G, Q, AQ, T))
+                    B = An.T @ Gn
+                    Y = np.linalg.lstsq(B, Tn[:, :q], rcond=None)[0]
+                    r1.append(float(np.linalg.norm(B @ Y - Tn[:, :q], 2)))
+                    r2.append(float(np.linalg.norm(An - AQn @ Qn.T, 2)))
+                rows.append(dict(sketch="toeplitz" if toep else "gaussian", q=q, n=n, rn1=stats(r1), rn2=stats(r2)))
+    line = {"workload": "lowrank_tables_7_2_7_3_paper_shaped", "matrices_per_case": count, "rows": rows,
+            "gpu_ms_total": gpu_ms, "seconds": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.workload == "table71":
         run_table71(a)
+    elif a.workload == "lowrank":
+        run_lowrank(a)
     elif a.impl == "reference":
         run_reference(a)
     elif a.workload in ("batched", "diff"):

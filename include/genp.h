@@ -179,6 +179,22 @@ GENP_API genp_status genp_make_multiplier(genp_mult_kind kind, int64_t n, uint64
                                  double scale, int nnz_per_col, genp_prec value_grid,
                                  void *cuda_stream, genp_multiplier **out);
 
+/* Side of the multiplier (Thm. 4.1 and Cor. 4.1 cover both products GM
+ * and MH).
+ *  GENP_SIDE_RIGHT (the default): genp_precondition forms C = A G and
+ *      genp_solve returns X = G U^{-1} L^{-1} B.
+ *  GENP_SIDE_LEFT: C = G A and X = U^{-1} L^{-1} (G B); genp_refine takes
+ *      steps d = U^{-1} L^{-1} (G r), x += d (GMRES-IR on G A d = G r), and
+ *      genp_adjoint returns Lambda = A^{-T} gX = G^T L^{-T} U^{-T} gX.
+ * The left side is offered with A in FP64 and FP64, FP32 or BF16_SLICED
+ * factorizations (genp_precondition returns GENP_ERR_UNSUPPORTED for BF16
+ * and BF16X3).  Set the side before genp_precondition and keep it for the
+ * solves of the same factors.
+ *  side   GENP_SIDE_RIGHT or GENP_SIDE_LEFT sets it; -1 only queries.
+ * Returns the previous side, or GENP_ERR_ARG for a NULL G or another side. */
+typedef enum { GENP_SIDE_RIGHT = 0, GENP_SIDE_LEFT = 1 } genp_side;
+GENP_API int genp_multiplier_side(genp_multiplier *G, int side);
+
 /* Redraws G in place with a new (seed, stream_id), keeping kind, n, scale,
  * nnz and grid; allocates nothing, so it may run inside a timed or captured
  * region.  This is the paper's recovery rule too (Sec. 5, Remark B.1): on a
@@ -393,6 +409,32 @@ GENP_API void genp_batched_plan_destroy(genp_batched_plan *P);
 GENP_API genp_status genp_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha, const void *A, int64_t lda,
                                     const void *Bt, int64_t ldb, float beta, const float *Cin, int64_t ldci,
                                     float *D, int64_t ldd, void *cuda_stream);
+
+/* Randomized low-rank approximation (Sec. 5, Proto-Alg. 5.1, with an
+ * orthonormal T as in the tests of Sec. 7.2):
+ *   Stage 1  B = A^T G with an m x r sketch G: GENP_MULT_GAUSSIAN (iid
+ *            N(0,1), Definition 3.2) or GENP_MULT_TOEPLITZ (Gaussian
+ *            Toeplitz, the multipliers of Table 7.3), drawn from
+ *            (seed, stream_id) on their own Philox tags;
+ *   basis    B = Q R, Q n x r orthonormal, R upper triangular with a
+ *            positive diagonal (so Q is unique, Fact 2.2), by shifted
+ *            Cholesky QR in three passes (CholeskyQR3);
+ *   Stage 3  A Q, so the rank-r approximation is A_hat = (A Q) Q^T.
+ *  A      m x n FP64 (ld lda), device.
+ *  r      1 <= r <= min(n, 128).
+ *  G      NULL or m x r (ld ldg): receives the sketch.
+ *  Q      n x r (ld ldq), required.  R: NULL or r x r (ld ldr), R = Q^T B.
+ *  AQ     NULL or m x r (ld ldaq).
+ *  dev_status  NULL or a device int: 0, or k + 1 if a Cholesky pass met a
+ *         non-positive pivot at step k (B numerically rank deficient
+ *         beyond what the shift covers); written before the call's work
+ *         completes on the stream.
+ * Allocates its workspace with cudaMallocAsync on the stream.
+ * Errors: GENP_ERR_ARG (sizes, kind), GENP_ERR_NOMEM, GENP_ERR_CUDA. */
+GENP_API genp_status genp_lowrank(int64_t m, int64_t n, const double *A, int64_t lda, int64_t r, genp_mult_kind kind,
+                                  uint64_t seed, uint64_t stream_id, double *G, int64_t ldg, double *Q, int64_t ldq,
+                                  double *R, int64_t ldr, double *AQ, int64_t ldaq, int *dev_status,
+                                  void *cuda_stream);
 
 /* Tensor-core building block of the BF16_SLICED path:
  *   D = alpha * A * B + beta * D      (all FP64, row-major)

@@ -16,6 +16,7 @@ STATUS_NAMES = {0: "GENP_OK", -1: "GENP_ERR_ARG", -2: "GENP_ERR_BREAKDOWN", -3: 
                 -4: "GENP_ERR_CUDA", -5: "GENP_ERR_TIMEOUT", -6: "GENP_ERR_NOMEM", -7: "GENP_ERR_UNSUPPORTED"}
 
 GAUSSIAN, CIRCULANT, SPARSE_PM1, CIRCULANT_PM1, IDENTITY, TOEPLITZ, HOUSEHOLDER_PM1 = 0, 1, 2, 3, 4, 5, 6
+RIGHT, LEFT = 0, 1
 FP64, FP32, BF16, FP8_E4M3, BF16X3, BF16_SLICED = 0, 1, 2, 3, 4, 5
 MAX_REFINE = 32
 
@@ -38,11 +39,14 @@ SIGNATURES = {
     "genp_status_string": (ctypes.c_char_p, [_int]),
     "genp_make_multiplier": (_int, [_int, _i64, _u64, _u64, _dbl, _int, _int, _vp, ctypes.POINTER(_vp)]),
     "genp_redraw_multiplier": (_int, [_vp, _u64, _u64, _vp]),
+    "genp_multiplier_side": (_int, [_vp, _int]),
     "genp_launch_count": (_u64, []),
     "genp_make_sparse_noalloc": (_int, [_i64, _int, _u64, _u64, _vp, _vp, _vp, _vp, _vp]),
     "genp_gemm_bf16": (_int, [_i64, _i64, _i64, ctypes.c_float, _vp, _i64, _vp, _i64, ctypes.c_float, _vp, _i64,
                               _vp, _i64, _vp]),
     "genp_gemm_sliced": (_int, [_i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _int, _vp]),
+    "genp_lowrank": (_int, [_i64, _i64, _vp, _i64, _i64, _int, _u64, _u64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
+                            _vp, _vp]),
     "genp_sliced_digits": (_int, [_int]),
     "genp_sliced_precondition_digits": (_int, [_int]),
     "genp_profile_enable": (_int, [_int]),

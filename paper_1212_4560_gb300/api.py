@@ -75,15 +75,21 @@ class Factors:
 
 
 def make_multiplier(kind: int, n: int, seed: int, stream_id: int = 0, scale: float | None = None,
-                    nnz_per_col: int = 4, value_grid: int = FP64, stream=None) -> Multiplier:
-    """genp_make_multiplier.  Default scale: 1/sqrt(n) (Gaussian, variance
-    1/n) and 1 (circulant, Toeplitz)."""
+                    nnz_per_col: int = 4, value_grid: int = FP64, stream=None, side: int = 0) -> Multiplier:
+    """genp_make_multiplier (and genp_multiplier_side for side = LEFT).
+    Default scale: 1/sqrt(n) (Gaussian, variance 1/n) and 1 (circulant,
+    Toeplitz)."""
     if scale is None:
         scale = 1.0 / math.sqrt(n) if kind == GAUSSIAN else 1.0
     h = ctypes.c_void_p()
     check(_lib.load().genp_make_multiplier(kind, n, seed, stream_id, float(scale), nnz_per_col, value_grid,
                                            _stream(stream), ctypes.byref(h)), "genp_make_multiplier")
-    return Multiplier(h, n, kind, nnz_per_col if kind == SPARSE_PM1 else 0)
+    G = Multiplier(h, n, kind, nnz_per_col if kind == SPARSE_PM1 else 0)
+    if side:
+        prev = _lib.load().genp_multiplier_side(h, side)
+        if prev < 0:
+            check(prev, "genp_multiplier_side")
+    return G
 
 
 def redraw_multiplier(G: Multiplier, seed: int, stream_id: int = 0, stream=None) -> None:
@@ -169,15 +175,17 @@ def info_fetch(F: Factors, stream=None) -> Info:
 
 
 def solve_system(A: torch.Tensor, B: torch.Tensor, kind: int = GAUSSIAN, seed: int = 0, prec: int = FP64,
-                 refine_steps: int = 10, tol: float = 1e-15, nb: int = 0, method: int = 0, stream=None):
+                 refine_steps: int = 10, tol: float = 1e-15, nb: int = 0, method: int = 0, stream=None,
+                 side: int = 0):
     """The whole method on one system: G, C = A G, GENP(C), X = G U^-1 L^-1 B,
-    FP64 refinement (method 0 classic, 1 GMRES-IR).  Returns (X, info, G, F)."""
+    FP64 refinement (method 0 classic, 1 GMRES-IR); side = LEFT: C = G A,
+    X = U^-1 L^-1 G B.  Returns (X, info, G, F)."""
     n = A.size(0)
     f64 = prec in (FP64, BF16_SLICED)
     # FP32-grid draws for every non-FP64 factorization (the sliced path reads
     # them as exact FP64 values)
     grid = FP64 if prec == FP64 else (BF16 if prec in (BF16, BF16X3) else FP32)
-    G = make_multiplier(kind, n, seed, value_grid=grid, stream=stream)
+    G = make_multiplier(kind, n, seed, value_grid=grid, stream=stream, side=side)
     C = torch.empty((n, n), dtype=torch.float64 if f64 else torch.float32, device=A.device)
     A64 = A if A.dtype == torch.float64 else A.double()
     precondition(G, A64 if f64 else A, C, c_prec=prec, stream=stream)
@@ -188,3 +196,19 @@ def solve_system(A: torch.Tensor, B: torch.Tensor, kind: int = GAUSSIAN, seed: i
     if refine_steps > 0:
         refine(A64, F, G, B64, X, tol=tol, max_iter=refine_steps, method=method, stream=stream)
     return X, info_fetch(F, stream=stream), G, F
+
+
+def lowrank(A: torch.Tensor, r: int, kind: int = GAUSSIAN, seed: int = 0, stream_id: int = 0, stream=None):
+    """genp_lowrank: the sketch G (m x r), Q (n x r, orthonormal, B = A^T G =
+    Q R), R (r x r), A Q (m x r) and a device status word (0, or k + 1 on a
+    non-positive Cholesky pivot).  Rank-r approximation: (A Q) Q^T."""
+    m, n = A.shape
+    dev = A.device
+    G = torch.empty((m, r), dtype=torch.float64, device=dev)
+    Q = torch.empty((n, r), dtype=torch.float64, device=dev)
+    R = torch.empty((r, r), dtype=torch.float64, device=dev)
+    AQ = torch.empty((m, r), dtype=torch.float64, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    check(_lib.load().genp_lowrank(m, n, _ptr(A), _ld(A), r, kind, seed, stream_id, _ptr(G), r, _ptr(Q), r, _ptr(R),
+                                   r, _ptr(AQ), r, _ptr(st), _stream(stream)), "genp_lowrank")
+    return G, Q, R, AQ, st

@@ -131,6 +131,15 @@ __global__ void k_eye(double *G, int64_t n, int64_t ldg) {
             G[r * ldg + c] = r == c ? 1.0 : 0.0;
 }
 
+cudaError_t add_into(const double *Y, int64_t ldy, double *X, int64_t ldx, int64_t n, int64_t nr, const int *skip,
+                     cudaStream_t s) {
+    if (n <= 0 || nr <= 0) return cudaSuccess;
+    note_launch();
+    k_add_into<<<dim3((unsigned)cdiv(nr, 32), (unsigned)(n < 65535 ? n : 65535)), 32, 0, s>>>(Y, ldy, X, ldx, n, nr,
+                                                                                           skip);
+    return cudaGetLastError();
+}
+
 cudaError_t apply_multiplier(const genp_multiplier *G, bool trans, const double *Y, int64_t ldy, double *X,
                              int64_t ldx, int64_t nrhs, bool accumulate, const int *skip, cudaStream_t s) {
     switch (G->kind) {
@@ -255,6 +264,13 @@ genp_status genp_make_multiplier(genp_mult_kind kind, int64_t n, uint64_t seed, 
     return GENP_OK;
 }
 
+int genp_multiplier_side(genp_multiplier *G, int side) {
+    if (!G || side < -1 || side > 1) return GENP_ERR_ARG;
+    const int old = G->side;
+    if (side >= 0) G->side = side;
+    return old;
+}
+
 genp_status genp_redraw_multiplier(genp_multiplier *G, uint64_t seed, uint64_t stream_id, void *cuda_stream) {
     if (!G) return GENP_ERR_ARG;
     G->last_stream = S(cuda_stream);
@@ -325,6 +341,27 @@ genp_status genp_gemm_sliced(int64_t m, int64_t n, int64_t K, double alpha, cons
     cudaError_t e = sliced_matmul(nd, m, n, K, A, lda, B, ldb, W, ldw, Aq, Bq, ex, s);
     if (e == cudaSuccess) e = df_axpby(alpha, W, ldw, beta, D, ldd, m, n, s);
     cudaError_t f = cudaFreeAsync(buf, s);
+    CU(e);
+    CU(f);
+    return GENP_OK;
+}
+
+genp_status genp_lowrank(int64_t m, int64_t n, const double *A, int64_t lda, int64_t r, genp_mult_kind kind,
+                         uint64_t seed, uint64_t stream_id, double *G, int64_t ldg, double *Q, int64_t ldq, double *R,
+                         int64_t ldr, double *AQ, int64_t ldaq, int *dev_status, void *cuda_stream) {
+    if (m < 1 || n < 1 || !A || !Q || lda < n || r < 1 || r > n || r > 128) return GENP_ERR_ARG;
+    if (kind != GENP_MULT_GAUSSIAN && kind != GENP_MULT_TOEPLITZ) return GENP_ERR_ARG;
+    if (ldq < r || (G && ldg < r) || (R && ldr < r) || (AQ && ldaq < r)) return GENP_ERR_ARG;
+    cudaStream_t s = S(cuda_stream);
+    void *work = nullptr;
+    if (cudaMallocAsync(&work, lowrank_work_bytes(m, n, r), s) != cudaSuccess) {
+        cudaGetLastError();
+        return GENP_ERR_NOMEM;
+    }
+    if (dev_status) CU(cudaMemsetAsync(dev_status, 0, sizeof(int), s));
+    cudaError_t e = lowrank_run(m, n, A, lda, r, kind == GENP_MULT_TOEPLITZ, seed, stream_id, G, ldg, Q, ldq, R, ldr,
+                                AQ, ldaq, dev_status, work, s);
+    cudaError_t f = cudaFreeAsync(work, s);
     CU(e);
     CU(f);
     return GENP_OK;
@@ -402,6 +439,37 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
         else
             CU((convert_matrix<float, float>(static_cast<const float *>(A), lda, static_cast<float *>(C), ldc, n, n,
                                              nullptr, s)));
+        return GENP_OK;
+    }
+    if (G->side == GENP_SIDE_LEFT) {
+        // C = G A (Cor. 4.1's GM half): the multiplier's product with the
+        // columns of A, as for X = G Y with n right-hand sides
+        if (a_prec != GENP_FP64 || tc_prec(c_prec)) return GENP_ERR_UNSUPPORTED;
+        const double *a = static_cast<const double *>(A);
+        if (c_prec == GENP_BF16_SLICED && G->kind == GENP_MULT_GAUSSIAN) {
+            const int nd = sliced_precond_digits();
+            const int64_t ldq = (int64_t)nd * kSlicedChunk, ldd = round8(n);
+            char *buf = nullptr;
+            const size_t dbytes = (size_t)n * ldd * 8, qbytes = (size_t)n * ldq * sizeof(__nv_bfloat16);
+            CU(cudaMallocAsync((void **)&buf, dbytes + 2 * qbytes + (size_t)2 * n * sizeof(int) + 256, s));
+            dfloat *D = reinterpret_cast<dfloat *>(buf);
+            __nv_bfloat16 *Aq = reinterpret_cast<__nv_bfloat16 *>(buf + dbytes);
+            __nv_bfloat16 *Bq = Aq + (size_t)n * ldq;
+            int *ex = reinterpret_cast<int *>(Bq + (size_t)n * ldq);
+            CU(sliced_matmul(nd, n, n, n, G->dense, n, a, lda, D, ldd, Aq, Bq, ex, s));
+            CU(df_to_f64(D, ldd, static_cast<double *>(C), ldc, n, n, s));
+            CU(cudaFreeAsync(buf, s));
+            return GENP_OK;
+        }
+        if (f64_factors(c_prec)) {
+            CU(apply_multiplier(G, false, a, lda, static_cast<double *>(C), ldc, n, false, nullptr, s));
+            return GENP_OK;
+        }
+        double *tmp = nullptr;   // FP32 factors: the FP64 product, rounded once
+        CU(cudaMallocAsync((void **)&tmp, (size_t)n * n * sizeof(double), s));
+        CU(apply_multiplier(G, false, a, lda, tmp, n, n, false, nullptr, s));
+        CU((convert_matrix<double, float>(tmp, n, static_cast<float *>(C), ldc, n, n, nullptr, s)));
+        CU(cudaFreeAsync(tmp, s));
         return GENP_OK;
     }
     if (c_prec == GENP_BF16_SLICED && G->kind == GENP_MULT_GAUSSIAN) {
@@ -535,6 +603,7 @@ genp_status genp_factor(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t
         if (st == GENP_OK) st = dalloc(&F->tcB, (size_t)n * F->tc_ldq);
         if (st == GENP_OK) st = dalloc(reinterpret_cast<double **>(&F->W), (size_t)n * F->ldw);
         if (st == GENP_OK) st = dalloc(&F->exps, (size_t)2 * n);
+        if (st == GENP_OK) st = dalloc(reinterpret_cast<double **>(&F->dinv_df), (size_t)diag_inverse_elems(n));
     }
     if (st == GENP_OK && cudaMallocHost(&F->host_info, sizeof(DevStatus)) != cudaSuccess) {
         cudaGetLastError();
@@ -573,6 +642,7 @@ void genp_factors_destroy(genp_factors *F) {
     cudaFree(F->exps);
     cudaFree(F->trsv_sync);
     cudaFree(F->dinv);
+    cudaFree(F->dinv_df);
     if (F->host_info) cudaFreeHost(F->host_info);
     delete F;
 }
@@ -589,15 +659,18 @@ genp_status genp_solve(const genp_factors *F, const genp_multiplier *G, const do
     TRY(ensure_work(Fm, yd + yf, s));
     double *Y = static_cast<double *>(F->work);
     float *Yf = reinterpret_cast<float *>(static_cast<char *>(F->work) + yd);
+    const bool left = G->side == GENP_SIDE_LEFT;
+    if (left) CU(apply_multiplier(G, false, B, ldb, Y, nrhs, nrhs, false, nullptr, s));   // G B
+    else CU((convert_matrix<double, double>(B, ldb, Y, nrhs, n, nrhs, nullptr, s)));
     if (f64_factors(F->prec)) {
-        CU((convert_matrix<double, double>(B, ldb, Y, nrhs, n, nrhs, nullptr, s)));
         CU(lu_solve_inplace<double>(F, Y, nrhs, nrhs, false, nullptr, s));
     } else {
-        CU((convert_matrix<double, float>(B, ldb, Yf, nrhs, n, nrhs, nullptr, s)));
+        CU((convert_matrix<double, float>(Y, nrhs, Yf, nrhs, n, nrhs, nullptr, s)));
         CU(lu_solve_inplace<float>(F, Yf, nrhs, nrhs, false, nullptr, s));
         CU((convert_matrix<float, double>(Yf, nrhs, Y, nrhs, n, nrhs, nullptr, s)));
     }
-    CU(apply_multiplier(G, false, Y, nrhs, X, ldx, nrhs, false, nullptr, s));
+    if (left) CU((convert_matrix<double, double>(Y, nrhs, X, ldx, n, nrhs, nullptr, s)));
+    else CU(apply_multiplier(G, false, Y, nrhs, X, ldx, nrhs, false, nullptr, s));
     Fm->last_stream = s;
     return GENP_OK;
 }
@@ -620,23 +693,31 @@ genp_status genp_refine(const double *A, int64_t lda, const genp_factors *F, con
         return GENP_OK;
     }
     const size_t rd = align256((size_t)n * nrhs * sizeof(double)), yf = align256((size_t)n * nrhs * sizeof(float));
-    TRY(ensure_work(Fm, rd + yf, s));
+    TRY(ensure_work(Fm, 2 * rd + yf, s));
     double *R = static_cast<double *>(F->work);
-    float *Rf = reinterpret_cast<float *>(static_cast<char *>(F->work) + rd);
+    double *T = reinterpret_cast<double *>(static_cast<char *>(F->work) + rd);
+    float *Rf = reinterpret_cast<float *>(static_cast<char *>(F->work) + 2 * rd);
     const int *done = &F->st->refine_done;
+    const bool left = G->side == GENP_SIDE_LEFT;
     CU(refine_init(Fm, A, lda, n, s));
     for (int it = 0; it <= max_iter; ++it) {
         CU(gemm<double>(n, nrhs, n, -1.0, A, lda, false, X, ldx, 1.0, B, ldb, R, nrhs, done, s));
         CU(refine_check(Fm, R, nrhs, X, ldx, B, ldb, n, nrhs, it, tol, max_iter, 1, s));
         if (it == max_iter) break;
-        if (f64_factors(F->prec)) {
-            CU(lu_solve_inplace<double>(F, R, nrhs, nrhs, false, done, s));
-        } else {
-            CU((convert_matrix<double, float>(R, nrhs, Rf, nrhs, n, nrhs, done, s)));
-            CU(lu_solve_inplace<float>(F, Rf, nrhs, nrhs, false, done, s));
-            CU((convert_matrix<float, double>(Rf, nrhs, R, nrhs, n, nrhs, done, s)));
+        double *D = R;
+        if (left) {   // d = U^-1 L^-1 (G r)
+            CU(apply_multiplier(G, false, R, nrhs, T, nrhs, nrhs, false, done, s));
+            D = T;
         }
-        CU(apply_multiplier(G, false, R, nrhs, X, ldx, nrhs, true, done, s));
+        if (f64_factors(F->prec)) {
+            CU(lu_solve_inplace<double>(F, D, nrhs, nrhs, false, done, s));
+        } else {
+            CU((convert_matrix<double, float>(D, nrhs, Rf, nrhs, n, nrhs, done, s)));
+            CU(lu_solve_inplace<float>(F, Rf, nrhs, nrhs, false, done, s));
+            CU((convert_matrix<float, double>(Rf, nrhs, D, nrhs, n, nrhs, done, s)));
+        }
+        if (left) CU(add_into(D, nrhs, X, ldx, n, nrhs, done, s));
+        else CU(apply_multiplier(G, false, R, nrhs, X, ldx, nrhs, true, done, s));
     }
     Fm->last_stream = s;
     return GENP_OK;
@@ -653,17 +734,23 @@ genp_status genp_adjoint(const genp_factors *F, const genp_multiplier *G, const 
     cudaStream_t s = S(cuda_stream);
     genp_factors *Fm = const_cast<genp_factors *>(F);
     const size_t ld = align256((size_t)n * nrhs * sizeof(double)), yf = align256((size_t)n * nrhs * sizeof(float));
-    TRY(ensure_work(Fm, ld + yf, s));
+    TRY(ensure_work(Fm, 2 * ld + yf, s));
     double *Lam = static_cast<double *>(F->work);
-    float *Lf = reinterpret_cast<float *>(static_cast<char *>(F->work) + ld);
-    CU(apply_multiplier(G, true, gX, ldg, Lam, nrhs, nrhs, false, nullptr, s));
+    double *T = reinterpret_cast<double *>(static_cast<char *>(F->work) + ld);
+    float *Lf = reinterpret_cast<float *>(static_cast<char *>(F->work) + 2 * ld);
+    const bool left = G->side == GENP_SIDE_LEFT;
+    // right: Lambda = L^-T U^-T (G^T gX);  left: Lambda = G^T (L^-T U^-T gX)
+    double *Z = left ? T : Lam;
+    if (left) CU((convert_matrix<double, double>(gX, ldg, Z, nrhs, n, nrhs, nullptr, s)));
+    else CU(apply_multiplier(G, true, gX, ldg, Z, nrhs, nrhs, false, nullptr, s));
     if (f64_factors(F->prec)) {
-        CU(lu_solve_inplace<double>(F, Lam, nrhs, nrhs, true, nullptr, s));
+        CU(lu_solve_inplace<double>(F, Z, nrhs, nrhs, true, nullptr, s));
     } else {
-        CU((convert_matrix<double, float>(Lam, nrhs, Lf, nrhs, n, nrhs, nullptr, s)));
+        CU((convert_matrix<double, float>(Z, nrhs, Lf, nrhs, n, nrhs, nullptr, s)));
         CU(lu_solve_inplace<float>(F, Lf, nrhs, nrhs, true, nullptr, s));
-        CU((convert_matrix<float, double>(Lf, nrhs, Lam, nrhs, n, nrhs, nullptr, s)));
+        CU((convert_matrix<float, double>(Lf, nrhs, Z, nrhs, n, nrhs, nullptr, s)));
     }
+    if (left) CU(apply_multiplier(G, true, T, nrhs, Lam, nrhs, nrhs, false, nullptr, s));
     if (dB) CU((convert_matrix<double, double>(Lam, nrhs, dB, lddb, n, nrhs, nullptr, s)));
     if (dA) CU(outer_update(Lam, nrhs, X, ldx, n, nrhs, dA, ldda, !f64_factors(F->prec), s));
     Fm->last_stream = s;

@@ -70,6 +70,7 @@ struct genp_multiplier {
     double scale = 1.0;
     bool pm1 = false;                  // CIRCULANT_PM1 (stored as a circulant)
     bool toeplitz = false;             // TOEPLITZ (stored as a circulant of order 2n)
+    int side = GENP_SIDE_RIGHT;        // C = A G (right) or C = G A (left)
     int64_t cn = 0;                    // order of the stored circulant: n, or 2n for TOEPLITZ
     int *attempt = nullptr;            // device: the draw attempt kept (CIRCULANT_PM1)
     cudaStream_t last_stream = nullptr;
@@ -93,6 +94,7 @@ struct genp_factors {
     int nd = 0;                        // digits per operand (GENP_BF16_SLICED)
     int *trsv_sync = nullptr;          // tickets and block counters of the triangular solves
     void *dinv = nullptr;              // inverses of the 64 x 64 diagonal blocks of L and U (factor type)
+    void *dinv_df = nullptr;           // their double-float copy (GENP_BF16_SLICED)
     cudaStream_t last_stream = nullptr;
 };
 
@@ -149,6 +151,9 @@ cudaError_t launch_circulant_to_dense(const double *g, int64_t cn, int64_t n, do
 // Gaussian Toeplitz (2n - 1 draws) as the first column of its circulant embedding of order 2n
 cudaError_t launch_make_toeplitz(double *g, int64_t n, uint64_t seed, uint64_t stream_id, double scale,
                                  genp_prec grid, cudaStream_t s);
+// m x r Gaussian (or Gaussian Toeplitz) sketch of the low-rank approximation
+cudaError_t launch_sketch(double *G, int64_t ldg, int64_t m, int64_t r, bool toeplitz, uint64_t seed,
+                          uint64_t stream_id, double scale, cudaStream_t s);
 // u = +-1 of the Householder multiplier
 cudaError_t launch_make_householder(double *u, int64_t n, uint64_t seed, uint64_t stream_id, cudaStream_t s);
 cudaError_t launch_batch_draw(const BatchDesc *d, int count, uint64_t seed, bool circ, float *Gpool, float *gpool,
@@ -323,6 +328,12 @@ cudaError_t status_reset(genp_factors *F, cudaStream_t s);
 cudaError_t gemm_df_sub(int64_t m, int64_t n, int64_t k, const dfloat *A, int64_t lda, const dfloat *B, int64_t ldb,
                         dfloat *D, int64_t ldd, cudaStream_t s);
 
+// lowrank.cu: randomized low-rank approximation (Proto-Alg. 5.1)
+cudaError_t lowrank_run(int64_t m, int64_t n, const double *A, int64_t lda, int64_t r, bool toeplitz, uint64_t seed,
+                        uint64_t sid, double *G, int64_t ldg, double *Q, int64_t ldq, double *R, int64_t ldr,
+                        double *AQ, int64_t ldaq, int *fail, void *work, cudaStream_t s);
+size_t lowrank_work_bytes(int64_t m, int64_t n, int64_t r);
+
 // solve.cu
 // Y <- U^{-1} L^{-1} Y in the factor's precision, Y n x nrhs of type T
 template <typename T>
@@ -352,6 +363,9 @@ cudaError_t refine_gmres(genp_factors *F, const genp_multiplier *G, const double
                          cudaStream_t s);
 
 // api.cu helpers
+// X[r][c] += Y[r][c] (n x nr), skipped when *skip != 0
+cudaError_t add_into(const double *Y, int64_t ldy, double *X, int64_t ldx, int64_t n, int64_t nr, const int *skip,
+                     cudaStream_t s);
 cudaError_t apply_multiplier(const genp_multiplier *G, bool trans, const double *Y, int64_t ldy,
                              double *X, int64_t ldx, int64_t nrhs, bool accumulate, const int *skip,
                              cudaStream_t s);

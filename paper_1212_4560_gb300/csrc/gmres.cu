@@ -8,7 +8,8 @@
 // but solves the correction equation by GMRES on the left-preconditioned
 // system (U^{-1} L^{-1}) C d = (U^{-1} L^{-1}) r, in FP64, with
 // C v = A (G v) applied from the original A and the multiplier (C itself is
-// overwritten by the factors).  The factors then need only be a good
+// overwritten by the factors).  With the multiplier on the left, C = G A:
+// the system is C d = G r, C v = G (A v), and x += d.  The factors then need only be a good
 // preconditioner, not a contraction.  Every right-hand side runs its own
 // Krylov space in the same kernels (columns of the n x nrhs blocks).
 //
@@ -263,6 +264,7 @@ cudaError_t refine_gmres(genp_factors *F, const genp_multiplier *G, const double
     const int *outer_done = &F->st->refine_done;
     const int *inner = &st->inner_done;
     const unsigned vb = vec_blocks(n * nr);
+    const bool left = G->side == GENP_SIDE_LEFT;
     cudaError_t e = refine_init(F, A, lda, n, s);
     for (int it = 0; it <= max_iter && e == cudaSuccess; ++it) {
         e = gemm<double>(n, nrhs, n, -1.0, A, lda, false, X, ldx, 1.0, B, ldb, R, nrhs, outer_done, s);
@@ -270,8 +272,9 @@ cudaError_t refine_gmres(genp_factors *F, const genp_multiplier *G, const double
         if (e != cudaSuccess || it == max_iter) break;
         note_launch();
         k_gm_begin<<<1, 32, 0, s>>>(st, nr, outer_done);
-        // V_0 = M^{-1} r / ||M^{-1} r||
-        e = cudaMemcpyAsync(V, R, (size_t)n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        // V_0 = M^{-1} r / ||M^{-1} r||  (left multiplier: M^{-1} G r)
+        if (left) e = apply_multiplier(G, false, R, nrhs, V, nrhs, nrhs, false, inner, s);
+        else e = cudaMemcpyAsync(V, R, (size_t)n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess) e = precond(F, V, Wf, n, nr, inner, s);
         if (e == cudaSuccess) e = dots(st, partial, V, vstride, 1, V, n, nr, -1, 0, inner, s);
         note_launch();
@@ -280,10 +283,15 @@ cudaError_t refine_gmres(genp_factors *F, const genp_multiplier *G, const double
         k_gm_scale<<<vb, 256, 0, s>>>(V, V, n, nr, st, inner);
         for (int k = 0; k < kM && e == cudaSuccess; ++k) {
             double *Vk = V + (int64_t)k * vstride;
-            // W = M^{-1} A (G V_k)
-            e = apply_multiplier(G, false, Vk, nrhs, T, nrhs, nrhs, false, inner, s);
-            if (e == cudaSuccess) e = gemm<double>(n, nrhs, n, 1.0, A, lda, false, T, nrhs, 0.0, nullptr, 0, W, nrhs,
-                                                   inner, s);
+            // W = M^{-1} A (G V_k)  (left multiplier: M^{-1} G (A V_k))
+            if (left) {
+                e = gemm<double>(n, nrhs, n, 1.0, A, lda, false, Vk, nrhs, 0.0, nullptr, 0, T, nrhs, inner, s);
+                if (e == cudaSuccess) e = apply_multiplier(G, false, T, nrhs, W, nrhs, nrhs, false, inner, s);
+            } else {
+                e = apply_multiplier(G, false, Vk, nrhs, T, nrhs, nrhs, false, inner, s);
+                if (e == cudaSuccess)
+                    e = gemm<double>(n, nrhs, n, 1.0, A, lda, false, T, nrhs, 0.0, nullptr, 0, W, nrhs, inner, s);
+            }
             if (e == cudaSuccess) e = precond(F, W, Wf, n, nr, inner, s);
             // CGS2 against V_0..V_k
             for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
@@ -304,7 +312,9 @@ cudaError_t refine_gmres(genp_factors *F, const genp_multiplier *G, const double
         k_gm_finish<<<1, 32, 0, s>>>(st, nr, outer_done);
         note_launch();
         k_gm_combine<<<vb, 256, 0, s>>>(V, vstride, T, n, nr, st, outer_done);
-        if (e == cudaSuccess) e = apply_multiplier(G, false, T, nrhs, X, ldx, nrhs, true, outer_done, s);
+        if (e == cudaSuccess)
+            e = left ? add_into(T, nrhs, X, ldx, n, nrhs, outer_done, s)
+                     : apply_multiplier(G, false, T, nrhs, X, ldx, nrhs, true, outer_done, s);
         if (e == cudaSuccess) e = cudaGetLastError();
     }
     return e;

@@ -210,6 +210,20 @@ __global__ void k_householder(double *u, int64_t n, uint64_t seed, uint64_t sid)
     }
 }
 
+// The m x r sketch of the low-rank approximation (Proto-Alg. 5.1, Stage 1;
+// Sec. 7.2): Gaussian G[i][j] = scale z(i r + j), or Gaussian Toeplitz
+// G[i][j] = scale z(i - j + r - 1) (m + r - 1 independent draws).
+constexpr uint64_t kTagSketch = 0x19, kTagSketchToep = 0x1A;
+__global__ void k_sketch(double *G, int64_t ldg, int64_t m, int64_t r, int toeplitz, uint64_t seed, uint64_t sid,
+                         double scale) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m * r; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = q / r, j = q % r;
+        const double z = toeplitz ? polar_normal(seed, sid, kTagSketchToep, (uint64_t)(i - j + r - 1))
+                                  : polar_normal(seed, sid, kTagSketch, (uint64_t)q);
+        G[i * ldg + j] = __dmul_rn(z, scale);
+    }
+}
+
 // Circulant with a +-1 first column (the paper's test multipliers): attempt
 // a takes g_i from the low bit of Philox word 0 at (i, 0, tag, a) and is
 // kept when no DFT bin of power-of-two order vanishes.  Exact integer test:
@@ -389,6 +403,13 @@ cudaError_t launch_make_toeplitz(double *g, int64_t n, uint64_t seed, uint64_t s
                                  cudaStream_t s) {
     note_launch();
     k_toeplitz<<<grid_for(2 * n, 256), 256, 0, s>>>(g, n, seed, sid, scale, grid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sketch(double *G, int64_t ldg, int64_t m, int64_t r, bool toeplitz, uint64_t seed, uint64_t sid,
+                          double scale, cudaStream_t s) {
+    note_launch();
+    k_sketch<<<grid_for(m * r, 256), 256, 0, s>>>(G, ldg, m, r, toeplitz ? 1 : 0, seed, sid, scale);
     return cudaGetLastError();
 }
 

@@ -13,6 +13,7 @@
 // read a `done` flag that the stopping test sets, so a whole refinement is
 // enqueued at once with no host synchronization.
 #include "genp_internal.cuh"
+#include "dfloat.cuh"
 
 #include <math.h>
 
@@ -210,8 +211,62 @@ struct TrsvSmem {
     T y[TB][NR];        // y_j
     T acc[TB][NR];      // right-hand side of the diagonal block, then its residual
     T carry[TB][NR];    // the walker's own contribution to the next block
-    int item[2];
 };
+
+// The walker's shared memory when it runs in double-float (factors held as
+// double-float pairs, GENP_BF16_SLICED): the three tiles as hi / lo FP32
+// planes with a row stride of 68, read with the quarters interleaved along k
+// (quarter q takes k = q + 4 kk), so the 32 lanes of a warp (8 rows x 4
+// quarters) hit 32 different banks; the vectors as double-float pairs.
+constexpr int kDdLd = 68;
+template <int NR>
+struct TrsvSmemDD {
+    float Sh[TB][kDdLd], Sl[TB][kDdLd];
+    float Dh[TB][kDdLd], Dl[TB][kDdLd];
+    float Oh[TB][kDdLd], Ol[TB][kDdLd];
+    dfloat y[TB][NR], acc[TB][NR], carry[TB][NR];
+};
+
+// s + t += (ah + al)(v.hi + v.lo): TwoSum of the leading terms, the rounding
+// error of the leading product (by FMA) and the cross terms gathered in t
+// (Dekker 1971; Ogita, Rump & Oishi 2005).
+__device__ __forceinline__ void dd_mac(float &s, float &t, float ah, float al, dfloat v) {
+    const float p = ah * v.hi;
+    const float pe = fmaf(ah, v.hi, -p);
+    const float cross = fmaf(ah, v.lo, al * v.hi);
+    const float sn = s + p, bb = sn - s;
+    const float err = (s - (sn - bb)) + (p - bb);
+    s = sn;
+    t += err + (pe + cross);
+}
+
+// part[c] = sum_k M[r][k] V[k][c] in double-float, summed over the 4 quarter
+// threads of row r (thread = 4 r + quarter)
+template <int NR>
+__device__ __forceinline__ void tile_gemv_dd(const float (*Mh)[kDdLd], const float (*Ml)[kDdLd], const dfloat (*V)[NR],
+                                             int r, int qq, dfloat (&part)[NR]) {
+    float s[NR], t[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) s[c] = t[c] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+        const int k = qq + 4 * kk;
+        const float ah = Mh[r][k], al = Ml[r][k];
+#pragma unroll
+        for (int c = 0; c < NR; ++c) dd_mac(s[c], t[c], ah, al, V[k][c]);
+    }
+#pragma unroll
+    for (int c = 0; c < NR; ++c) {
+        dfloat a = df_norm(s[c], t[c]);
+        for (int o = 1; o <= 2; o <<= 1) {
+            dfloat b;
+            b.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+            b.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+            a = a + b;
+        }
+        part[c] = a;
+    }
+}
 
 // part[c] += sum over this thread's quarter of k of M[r][k] V[k][c] (thread = 4 r + quarter)
 template <typename T, int NR>
@@ -264,12 +319,18 @@ __device__ __forceinline__ T tile_elem(const TS *C, int64_t ldc, int n, int mode
     return (mode <= 1) ? (T)__ldg(C + row * ldc + col) : (T)__ldg(C + col * ldc + row);
 }
 
-template <typename TS, typename T, int NR>
+// DD: the walker reads the factors and the diagonal inverses as
+// double-float pairs (Cd, ldcd, Dinvd) and works on the FP32 pipe; the
+// update items still read C.
+template <typename TS, typename T, int NR, bool DD>
 __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc, int n, const TS *Dinv, T *Y,
-                                                        int64_t ldy, int nr, int mode, const int *skip, int *sync) {
+                                                        int64_t ldy, int nr, int mode, const int *skip, int *sync,
+                                                        const dfloat *Cd, int64_t ldcd, const dfloat *Dinvd) {
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     TrsvSmem<T, NR> &sm = *reinterpret_cast<TrsvSmem<T, NR> *>(smraw);
+    TrsvSmemDD<NR> &sd = *reinterpret_cast<TrsvSmemDD<NR> *>(smraw);
+    __shared__ int s_ticket;
     const int tid = threadIdx.x;
     const int nblk = (n + TB - 1) / TB;
     const bool forward = (mode == 0 || mode == 2);
@@ -316,13 +377,110 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
         for (int e = 0; e < 16; ++e) v[e] = (T)__ldg(X + tid + e * kTrsvThreads);
     };
     auto block_of = [&](int p) { return forward ? p : nblk - 1 - p; };
+    // double-float walker: tiles of op(T) from the double-float factors, the
+    // inverse of the diagonal tile from its double-float copy
+    auto load_tile_d = [&](int i, int j, dfloat (&v)[16]) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int idx = tid + e * kTrsvThreads;
+            const int a = idx >> 6, b = idx & 63;
+            const int rr = mode <= 1 ? a : b, kk = mode <= 1 ? b : a;   // element (rr, kk) of op(T)'s tile
+            const int64_t row = (int64_t)i * TB + rr, col = (int64_t)j * TB + kk;
+            dfloat z(0.0f);
+            if (row < n && col < n) z = (mode <= 1) ? Cd[row * ldcd + col] : Cd[col * ldcd + row];
+            v[e] = z;
+        }
+    };
+    auto load_inv_d = [&](int j, dfloat (&v)[16]) {
+        const dfloat *X = Dinvd + ((int64_t)(unit ? 0 : 1) * nblk + j) * TB * TB;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[e] = X[tid + e * kTrsvThreads];
+    };
+    // element e of this thread's share is (rr, kk) of op(T)'s tile
+    // (load_tile_d), or (a, b) of the row-major inverse of T_jj (load_inv_d),
+    // whose transpose is the inverse of op(T)_jj in the transposed modes:
+    // both land at [rr][kk]; kind 1 keeps the diagonal tile's triangle
+    auto store_d = [&](float (*Mh)[kDdLd], float (*Ml)[kDdLd], const dfloat (&v)[16], int kind) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            const int idx = tid + e * kTrsvThreads;
+            const int a = idx >> 6, b = idx & 63;
+            const int rr = mode <= 1 ? a : b, kk = mode <= 1 ? b : a;
+            dfloat val = v[e];
+            if (kind == 1) {     // the diagonal tile: its triangle, unit diagonal where op(T) has one
+                if (rr == kk) val = unit ? dfloat(1.0f) : val;
+                else if (forward ? kk > rr : kk < rr) val = dfloat(0.0f);
+            }
+            Mh[rr][kk] = val.hi;
+            Ml[rr][kk] = val.lo;
+        }
+    };
 
     int q_it = 2, t_base = 1;              // first ticket of target step q_it's items
     for (;;) {
         __syncthreads();
-        if (tid == 0) sm.item[0] = atomicAdd(ticket, 1);
+        if (tid == 0) s_ticket = atomicAdd(ticket, 1);
         __syncthreads();
-        const int t = sm.item[0];
+        const int t = s_ticket;
+        if (DD && t == 0) {
+            // ---- the walker in double-float (FP32 pipe; FP64 is 64 times
+            // slower on this GPU): the same steps as the FP64 walker below ----
+            dfloat vD[16], vX[16], vO[16];
+            load_tile_d(block_of(0), block_of(0), vD);
+            load_inv_d(block_of(0), vX);
+            for (int q = 0; q < nblk; ++q) {
+                const int j = block_of(q);
+                const int bj = min(TB, n - j * TB);
+                __syncthreads();
+                store_d(sd.Dh, sd.Dl, vD, 1);
+                store_d(sd.Sh, sd.Sl, vX, 2);
+                if (tid == 0 && q >= 2 && !wait_geq(cnt + j, q - 1)) atomicExch(&g_solve_timeout, 1);
+                __syncthreads();
+                if (q + 1 < nblk) {
+                    load_tile_d(block_of(q + 1), j, vO);
+                    load_tile_d(block_of(q + 1), block_of(q + 1), vD);
+                    load_inv_d(block_of(q + 1), vX);
+                }
+                for (int idx = tid; idx < TB * NR; idx += kTrsvThreads) {
+                    const int rr = idx / NR, c = idx % NR;
+                    const dfloat b((rr < bj && c < nr) ? (double)ldcg(Y + ((int64_t)j * TB + rr) * ldy + c) : 0.0);
+                    sd.acc[rr][c] = q > 0 ? b - sd.carry[rr][c] : b;
+                }
+                __syncthreads();
+                // y = X b;  y += X (b - T y)
+                dfloat part[NR];
+                tile_gemv_dd<NR>(sd.Sh, sd.Sl, sd.acc, r, qq, part);
+#pragma unroll
+                for (int c = 0; c < NR; ++c)
+                    if ((c & 3) == qq) sd.y[r][c] = part[c];
+                __syncthreads();
+                tile_gemv_dd<NR>(sd.Dh, sd.Dl, sd.y, r, qq, part);
+#pragma unroll
+                for (int c = 0; c < NR; ++c)
+                    if ((c & 3) == qq) sd.acc[r][c] = sd.acc[r][c] - part[c];
+                __syncthreads();
+                tile_gemv_dd<NR>(sd.Sh, sd.Sl, sd.acc, r, qq, part);
+#pragma unroll
+                for (int c = 0; c < NR; ++c)
+                    if ((c & 3) == qq) {
+                        const dfloat yv = sd.y[r][c] + part[c];
+                        sd.y[r][c] = yv;
+                        if (r < bj && c < nr) Y[((int64_t)j * TB + r) * ldy + c] = (T)(double)yv;
+                    }
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) st_release(ready + j, 1);
+                if (q + 1 < nblk) {           // own contribution to the next block
+                    store_d(sd.Oh, sd.Ol, vO, 0);
+                    __syncthreads();
+                    tile_gemv_dd<NR>(sd.Oh, sd.Ol, sd.y, r, qq, part);
+#pragma unroll
+                    for (int c = 0; c < NR; ++c)
+                        if ((c & 3) == qq) sd.carry[r][c] = part[c];
+                }
+            }
+            continue;
+        }
         if (t == 0) {
             // ---- the walker: every diagonal block in order ----
             T vD[16], vX[16], vO[16];
@@ -458,18 +616,20 @@ __global__ void __launch_bounds__(TB) k_trtri_diag(const TS *C, int64_t ldc, int
     for (int r = 0; r < TB; ++r) out[r * TB + c] = (TS)x[r][c];
 }
 
-template <typename TS, typename T, int NR>
+template <typename TS, typename T, int NR, bool DD>
 cudaError_t launch_trsv(const TS *C, int64_t ldc, int64_t n, const TS *Dinv, T *Y, int64_t ldy, int nr, int mode,
-                        const int *skip, int *sync, cudaStream_t s) {
-    const size_t sm = sizeof(TrsvSmem<T, NR>);
+                        const int *skip, int *sync, const dfloat *Cd, int64_t ldcd, const dfloat *Dinvd,
+                        cudaStream_t s) {
+    const size_t sm = (DD && sizeof(TrsvSmemDD<NR>) > sizeof(TrsvSmem<T, NR>)) ? sizeof(TrsvSmemDD<NR>)
+                                                                               : sizeof(TrsvSmem<T, NR>);
     static int grid = 0;
     if (!grid) {
         if (sm > 48 * 1024)
-            cudaFuncSetAttribute(k_trsv<TS, T, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaFuncSetAttribute(k_trsv<TS, T, NR, DD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         int per_sm = 1, dev = 0, sms = 152;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsv<TS, T, NR>, kTrsvThreads, sm) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trsv<TS, T, NR, DD>, kTrsvThreads, sm) !=
                 cudaSuccess ||
             per_sm < 1) {
             cudaGetLastError();
@@ -481,7 +641,8 @@ cudaError_t launch_trsv(const TS *C, int64_t ldc, int64_t n, const TS *Dinv, T *
     cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)(2 + 2 * nblk) * sizeof(int), s);
     if (e != cudaSuccess) return e;
     note_launch();
-    k_trsv<TS, T, NR><<<grid, kTrsvThreads, sm, s>>>(C, ldc, (int)n, Dinv, Y, ldy, nr, mode, skip, sync);
+    k_trsv<TS, T, NR, DD><<<grid, kTrsvThreads, sm, s>>>(C, ldc, (int)n, Dinv, Y, ldy, nr, mode, skip, sync, Cd,
+                                                          ldcd, Dinvd);
     return cudaGetLastError();
 }
 
@@ -499,12 +660,39 @@ cudaError_t solve_typed(const genp_factors *F, T *Y, int64_t ldy, int64_t nrhs, 
             const int mode = transposed ? (pass == 0 ? 2 : 3) : (pass == 0 ? 0 : 1);
             const TS *D = static_cast<const TS *>(F->dinv);
             int *sy = F->trsv_sync;
-            cudaError_t e;
-            if (nr == 1) e = launch_trsv<TS, T, 1>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, s);
-            else if (nr <= 2) e = launch_trsv<TS, T, 2>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, s);
-            else if (nr <= 4) e = launch_trsv<TS, T, 4>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, s);
-            else if (nr <= 8) e = launch_trsv<TS, T, 8>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, s);
-            else e = launch_trsv<TS, T, 16>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, s);
+            cudaError_t e = cudaSuccess;
+            // factors also held as double-float pairs (sliced path): the walker runs in double-float
+            const dfloat *Wd = static_cast<const dfloat *>(F->W);
+            const dfloat *Dd = static_cast<const dfloat *>(F->dinv_df);
+            bool dd = false;
+            if constexpr (sizeof(TS) == 8) dd = Wd && Dd;
+            if constexpr (sizeof(TS) == 8) {
+                const int64_t lw = F->ldw;
+                if (!dd) {
+                } else if (nr == 1) {
+                    e = launch_trsv<TS, T, 1, true>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, Wd, lw, Dd, s);
+                } else if (nr <= 2) {
+                    e = launch_trsv<TS, T, 2, true>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, Wd, lw, Dd, s);
+                } else if (nr <= 4) {
+                    e = launch_trsv<TS, T, 4, true>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, Wd, lw, Dd, s);
+                } else if (nr <= 8) {
+                    e = launch_trsv<TS, T, 8, true>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, Wd, lw, Dd, s);
+                } else {
+                    e = launch_trsv<TS, T, 16, true>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, Wd, lw, Dd, s);
+                }
+            }
+            if (!dd) {
+                if (nr == 1) e = launch_trsv<TS, T, 1, false>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, nullptr, 0,
+                                                               nullptr, s);
+                else if (nr <= 2) e = launch_trsv<TS, T, 2, false>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, nullptr,
+                                                                    0, nullptr, s);
+                else if (nr <= 4) e = launch_trsv<TS, T, 4, false>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, nullptr,
+                                                                    0, nullptr, s);
+                else if (nr <= 8) e = launch_trsv<TS, T, 8, false>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, nullptr,
+                                                                    0, nullptr, s);
+                else e = launch_trsv<TS, T, 16, false>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, nullptr, 0, nullptr,
+                                                        s);
+            }
             if (e != cudaSuccess) return e;
         }
     }
@@ -580,6 +768,12 @@ cudaError_t invert_diag_blocks(genp_factors *F, cudaStream_t s) {
     else
         k_trtri_diag<float><<<g, TB, sm, s>>>(static_cast<const float *>(F->C), F->ldc, (int)n,
                                               static_cast<float *>(F->dinv));
+    if (F->dinv_df) {   // double-float copy for the walker of the sliced path
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return df_from_f64(static_cast<const double *>(F->dinv), TB, static_cast<dfloat *>(F->dinv_df), TB,
+                           2 * cdiv(n, TB) * TB, TB, s);
+    }
     return cudaGetLastError();
 }
 

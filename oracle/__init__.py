@@ -448,6 +448,33 @@ def lowrank_residuals(A: np.ndarray, B: np.ndarray, Q: np.ndarray, AQ: np.ndarra
     return rn1, rn2
 
 
+def numerical_rank(A: np.ndarray, r_lo: int, r_hi: int, cond_max: float, G: np.ndarray):
+    """App. B, Proto-Alg. B.1 (numerical rank without pivoting or
+    orthogonalization), as read here: with the m x r_hi Gaussian G drawn once
+    and G_r its first r columns, the sketch B' = A^T G_r is full rank and
+    well conditioned exactly when r does not exceed the numerical rank
+    (Thm. 5.1), so the rank is the largest r in [r_lo, r_hi] whose sketch
+    passes COND; binary search r = ceil((r_lo + r_hi) / 2) (Remark B.4):
+    pass -> r_lo = r, fail -> r_hi = r - 1.  COND: kappa_2(B') <= cond_max
+    (here by the library SVD).  Returns (rank, B = A^T G_rank, trace of
+    (r, kappa, passed) per test)."""
+    A, G = _c(A), _c(G)
+    lo, hi = int(r_lo), int(r_hi)
+    trace = []
+    while lo < hi:
+        r = (lo + hi + 1) // 2
+        Bp = matmul(A.T.copy(), G[:, :r].copy())
+        kappa = float(np.linalg.cond(Bp))
+        ok = bool(np.isfinite(kappa) and kappa <= cond_max)
+        trace.append((r, kappa, ok))
+        if ok:
+            lo = r
+        else:
+            hi = r - 1
+    B = matmul(A.T.copy(), G[:, :lo].copy()) if lo > 0 else np.zeros((A.shape[1], 0))
+    return lo, B, trace
+
+
 # --------------------------------------------------------------------------
 # Exact references used by the pins
 # --------------------------------------------------------------------------

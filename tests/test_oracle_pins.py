@@ -712,3 +712,31 @@ def test_lowrank_residual_between_eckart_young_and_tail_bound(toeplitz):
     assert np.allclose(np.tril(R, -1), 0.0, atol=1e-12 * np.abs(R).max())
     assert np.all(np.diag(R) > 0)
     assert np.allclose(r["Q"] @ R, r["B"], atol=1e-13 * np.abs(r["B"]).max())
+
+
+# ------------------------------------------------ numerical rank (App. B)
+
+@pytest.mark.parametrize("n,q,seed", [(64, 1, 0), (64, 8, 1), (128, 8, 2), (128, 32, 3), (256, 32, 4), (256, 17, 5)])
+def test_numerical_rank_of_tables_inputs(n, q, seed):
+    """Inputs with numerical rank q (s_j = 1/j up to q, 1e-10 beyond): the
+    binary search returns q from the full range [0, min(n, 128)], its trace
+    is consistent (every r <= q passed, every r > q failed), and the basis
+    is A^T G_q."""
+    A, S, T, s = (t.numpy() for t in W.lowrank(n, q, seed))
+    G = oracle.sketch_multiplier(n, min(n, 128), seed=seed + 7)
+    rank, B, trace = oracle.numerical_rank(A, 0, min(n, 128), 1e6, G)
+    assert rank == q
+    for r, kappa, ok in trace:
+        assert ok == (r <= q)
+    assert np.array_equal(B, oracle.matmul(A.T.copy(), G[:, :q].copy()))
+    # the basis spans the leading right singular space (Thm. 5.1): sine of the largest angle small
+    Qb = np.linalg.qr(B)[0]
+    assert np.linalg.norm(T[:, :q] - Qb @ (Qb.T @ T[:, :q]), 2) <= 1e-5      # the tables: rn1 up to ~1e-5
+
+
+def test_numerical_rank_degenerate_ranges():
+    A, S, T, s = (t.numpy() for t in W.lowrank(64, 8, 0))
+    G = oracle.sketch_multiplier(64, 32, seed=1)
+    assert oracle.numerical_rank(A, 5, 5, 1e6, G)[0] == 5          # r_lo = r_hi: no test
+    assert oracle.numerical_rank(A, 0, 4, 1e6, G)[0] == 4          # rank above the range: r_hi
+    assert oracle.numerical_rank(A, 12, 32, 1e6, G)[0] == 12       # rank below the range: r_lo

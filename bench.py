@@ -400,6 +400,16 @@ def run_ours(a):
     if not a.no_e2e:
         A_h = A_cpu.pin_memory()
         B_h = B_cpu.pin_memory()
+
+        def h2d_rate():
+            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            q0.record(stream)
+            A.copy_(A_h, non_blocking=True)
+            q1.record(stream)
+            torch.cuda.synchronize()
+            return A_h.numel() * 8 / (q0.elapsed_time(q1) / 1e3) / 1e9
+        h2d_before = h2d_rate()
         X_h = [torch.empty((n, nrhs), dtype=torch.float64).pin_memory() for _ in range(2)]
         Ab, Bb = [A, torch.empty_like(A)], [B, torch.empty_like(B)]
         cs = torch.cuda.Stream(dev)
@@ -437,12 +447,7 @@ def run_ours(a):
         torch.cuda.synchronize()
         e_ms = e0.elapsed_time(e1)
         # the copy engine's own rate, for the record
-        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        h0.record(stream)
-        A.copy_(A_h, non_blocking=True)
-        h1.record(stream)
-        torch.cuda.synchronize()
-        h2d_gbs = A_h.numel() * 8 / (h0.elapsed_time(h1) / 1e3) / 1e9
+        h2d_gbs = h2d_rate()
         if world > 1:
             t = torch.tensor([e_ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -450,7 +455,7 @@ def run_ours(a):
         e2e = {"value": world * k_e2e / (e_ms / 1e3), "unit": "solves/s",
                "h2d_bytes_per_step": A_h.numel() * 8 + B_h.numel() * 8, "d2h_bytes_per_step": X_h[0].numel() * 8,
                "steps": k_e2e, "inputs": "double-buffered: step i+1's copy overlaps step i",
-               "h2d_gbs_alone": h2d_gbs}
+               "h2d_gbs_alone": h2d_gbs, "h2d_gbs_before": h2d_before, "A_h_pinned": bool(A_h.is_pinned())}
 
     if rank != 0:
         if world > 1:

@@ -29,6 +29,10 @@
  *    never trap.
  *  - Handles are opaque and library-owned; a handle may be used from one
  *    stream at a time.
+ *  - Calls that document a cudaMallocAsync workspace take it from the
+ *    device's default memory pool; on first use per device the library
+ *    raises that pool's release threshold so freed workspace stays mapped
+ *    for the next call (the setting belongs to this process's pool).
  */
 #ifndef GENP_H
 #define GENP_H
@@ -435,6 +439,28 @@ GENP_API genp_status genp_lowrank(int64_t m, int64_t n, const double *A, int64_t
                                   uint64_t seed, uint64_t stream_id, double *G, int64_t ldg, double *Q, int64_t ldq,
                                   double *R, int64_t ldr, double *AQ, int64_t ldaq, int *dev_status,
                                   void *cuda_stream);
+
+/* Numerical rank without pivoting or orthogonalization (App. B,
+ * Proto-Alg. B.1).  With the m x r_hi Gaussian sketch G drawn once from
+ * (seed, stream_id) (the tag of genp_lowrank's Gaussian sketch) and G_r its
+ * first r columns, B' = A^T G_r is full rank and well conditioned exactly
+ * when r does not exceed the numerical rank (Thm. 5.1).  As printed, the
+ * algorithm's update (a passing test lowers the top of the range) would
+ * settle on the smallest passing r; this entry point searches for the
+ * largest: r = ceil((r_lo + r_hi) / 2) (Remark B.4), pass -> r_lo = r,
+ * fail -> r_hi = r - 1, until r_lo = r_hi.  COND (Remark B.2): Cholesky of
+ * B'^T B' without pivoting, 40 power steps for its largest eigenvalue and
+ * 40 inverse-iteration steps for its smallest; pass when the resulting
+ * kappa_2(B') <= cond_max.
+ *  A        m x n FP64 (ld lda), device.   0 <= r_lo <= r_hi <= min(n, 128).
+ *  rank     host: the numerical rank found.
+ *  B        NULL or n x r_hi (ld ldb): receives A^T G_rank (rank columns).
+ * Synchronizes the stream once per candidate r (the search branches on the
+ * device's answer).  Allocates its workspace with cudaMallocAsync.
+ * Errors: GENP_ERR_ARG, GENP_ERR_NOMEM, GENP_ERR_CUDA. */
+GENP_API genp_status genp_numerical_rank(int64_t m, int64_t n, const double *A, int64_t lda, int64_t r_lo,
+                                         int64_t r_hi, double cond_max, uint64_t seed, uint64_t stream_id,
+                                         int64_t *rank, double *B, int64_t ldb, void *cuda_stream);
 
 /* Tensor-core building block of the BF16_SLICED path:
  *   D = alpha * A * B + beta * D      (all FP64, row-major)

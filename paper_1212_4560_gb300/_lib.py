@@ -45,6 +45,7 @@ SIGNATURES = {
     "genp_gemm_bf16": (_int, [_i64, _i64, _i64, ctypes.c_float, _vp, _i64, _vp, _i64, ctypes.c_float, _vp, _i64,
                               _vp, _i64, _vp]),
     "genp_gemm_sliced": (_int, [_i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _int, _vp]),
+    "genp_numerical_rank": (_int, [_i64, _i64, _vp, _i64, _i64, _i64, _dbl, _u64, _u64, _vp, _vp, _i64, _vp]),
     "genp_lowrank": (_int, [_i64, _i64, _vp, _i64, _i64, _int, _u64, _u64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
                             _vp, _vp]),
     "genp_sliced_digits": (_int, [_int]),

@@ -212,3 +212,15 @@ def lowrank(A: torch.Tensor, r: int, kind: int = GAUSSIAN, seed: int = 0, stream
     check(_lib.load().genp_lowrank(m, n, _ptr(A), _ld(A), r, kind, seed, stream_id, _ptr(G), r, _ptr(Q), r, _ptr(R),
                                    r, _ptr(AQ), r, _ptr(st), _stream(stream)), "genp_lowrank")
     return G, Q, R, AQ, st
+
+
+def numerical_rank(A: torch.Tensor, r_lo: int, r_hi: int, cond_max: float = 1e6, seed: int = 0, stream_id: int = 0,
+                   stream=None):
+    """genp_numerical_rank: (rank, B = A^T G_rank as an n x rank tensor)."""
+    m, n = A.shape
+    B = torch.zeros((n, max(r_hi, 1)), dtype=torch.float64, device=A.device)
+    rk = ctypes.c_int64(-1)
+    check(_lib.load().genp_numerical_rank(m, n, _ptr(A), _ld(A), r_lo, r_hi, float(cond_max), seed, stream_id,
+                                          ctypes.byref(rk), _ptr(B), B.stride(0), _stream(stream)),
+          "genp_numerical_rank")
+    return int(rk.value), B[:, :int(rk.value)]

@@ -110,6 +110,28 @@ genp_status ensure_work(genp_factors *F, size_t bytes, cudaStream_t s) {
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Stream-ordered workspaces (cudaMallocAsync) come from the device's default
+// memory pool; by default the pool hands freed memory back to the driver at
+// every synchronization, and the next call maps it again.  On first use per
+// device the library keeps the pool's memory cached instead.
+void keep_pool_cached() {
+    static std::atomic<uint64_t> done{0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return;
+    }
+    const uint64_t bit = 1ull << dev;
+    if (done.load(std::memory_order_relaxed) & bit) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done.fetch_or(bit, std::memory_order_relaxed);
+}
+
 }  // namespace
 
 namespace genp {
@@ -326,6 +348,7 @@ genp_status genp_gemm_sliced(int64_t m, int64_t n, int64_t K, double alpha, cons
     if (m > INT32_MAX || n > INT32_MAX || cdiv(m, 128) > 65535) return GENP_ERR_ARG;
     if (m == 0 || n == 0) return GENP_OK;
     cudaStream_t s = S(cuda_stream);
+    keep_pool_cached();
     const int64_t ldq = kSlicedLdq, ldw = round8(n);
     const size_t wbytes = (size_t)m * ldw * 8, abytes = (size_t)m * ldq * 2, bbytes = (size_t)n * ldq * 2;
     char *buf = nullptr;
@@ -353,6 +376,7 @@ genp_status genp_lowrank(int64_t m, int64_t n, const double *A, int64_t lda, int
     if (kind != GENP_MULT_GAUSSIAN && kind != GENP_MULT_TOEPLITZ) return GENP_ERR_ARG;
     if (ldq < r || (G && ldg < r) || (R && ldr < r) || (AQ && ldaq < r)) return GENP_ERR_ARG;
     cudaStream_t s = S(cuda_stream);
+    keep_pool_cached();
     void *work = nullptr;
     if (cudaMallocAsync(&work, lowrank_work_bytes(m, n, r), s) != cudaSuccess) {
         cudaGetLastError();
@@ -362,6 +386,38 @@ genp_status genp_lowrank(int64_t m, int64_t n, const double *A, int64_t lda, int
     cudaError_t e = lowrank_run(m, n, A, lda, r, kind == GENP_MULT_TOEPLITZ, seed, stream_id, G, ldg, Q, ldq, R, ldr,
                                 AQ, ldaq, dev_status, work, s);
     cudaError_t f = cudaFreeAsync(work, s);
+    CU(e);
+    CU(f);
+    return GENP_OK;
+}
+
+genp_status genp_numerical_rank(int64_t m, int64_t n, const double *A, int64_t lda, int64_t r_lo, int64_t r_hi,
+                                double cond_max, uint64_t seed, uint64_t stream_id, int64_t *rank, double *B,
+                                int64_t ldb, void *cuda_stream) {
+    if (m < 1 || n < 1 || !A || !rank || lda < n) return GENP_ERR_ARG;
+    if (r_lo < 0 || r_hi < r_lo || r_hi > n || r_hi > 128 || !(cond_max > 1.0)) return GENP_ERR_ARG;
+    if (B && ldb < r_hi) return GENP_ERR_ARG;
+    if (r_hi == 0) {
+        *rank = 0;
+        return GENP_OK;
+    }
+    cudaStream_t s = S(cuda_stream);
+    keep_pool_cached();
+    void *work = nullptr;
+    if (cudaMallocAsync(&work, numerical_rank_work_bytes(m, n, r_hi), s) != cudaSuccess) {
+        cudaGetLastError();
+        return GENP_ERR_NOMEM;
+    }
+    double *hk = nullptr;
+    if (cudaMallocHost((void **)&hk, sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeAsync(work, s);
+        return GENP_ERR_NOMEM;
+    }
+    cudaError_t e = numerical_rank_run(m, n, A, lda, r_lo, r_hi, cond_max, seed, stream_id, rank, B, ldb, work, hk, s);
+    cudaError_t f = cudaFreeAsync(work, s);
+    if (f == cudaSuccess) f = cudaStreamSynchronize(s);
+    cudaFreeHost(hk);
     CU(e);
     CU(f);
     return GENP_OK;
@@ -421,6 +477,7 @@ void genp_multiplier_destroy(genp_multiplier *G) {
 
 genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t lda, genp_prec a_prec, void *C,
                               int64_t ldc, genp_prec c_prec, void *cuda_stream) {
+    keep_pool_cached();
     if (!G || !A || !C) return GENP_ERR_ARG;
     const int64_t n = G->n;
     if (lda < n || ldc < n) return GENP_ERR_ARG;

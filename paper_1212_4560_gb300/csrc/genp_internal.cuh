@@ -333,6 +333,10 @@ cudaError_t lowrank_run(int64_t m, int64_t n, const double *A, int64_t lda, int6
                         uint64_t sid, double *G, int64_t ldg, double *Q, int64_t ldq, double *R, int64_t ldr,
                         double *AQ, int64_t ldaq, int *fail, void *work, cudaStream_t s);
 size_t lowrank_work_bytes(int64_t m, int64_t n, int64_t r);
+cudaError_t numerical_rank_run(int64_t m, int64_t n, const double *A, int64_t lda, int64_t r_lo, int64_t r_hi,
+                               double cond_max, uint64_t seed, uint64_t sid, int64_t *rank, double *B, int64_t ldb,
+                               void *work, double *host_kappa, cudaStream_t s);
+size_t numerical_rank_work_bytes(int64_t m, int64_t n, int64_t r_hi);
 
 // solve.cu
 // Y <- U^{-1} L^{-1} Y in the factor's precision, Y n x nrhs of type T

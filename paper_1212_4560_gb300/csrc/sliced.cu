@@ -21,6 +21,13 @@ namespace {
 int g_default_digits = 7;
 int g_precond_digits = 7;
 
+// |x| as its IEEE bit pattern, NaN mapped to 0: the integer maximum of these
+// is the bit pattern of max|x| (no FP64 min/max on the scarce FP64 units)
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+    return b > 0x7FF0000000000000ull ? 0ull : b;
+}
+
 // exponent e with max|x| < 2^e (0 for an all-zero row)
 __device__ __forceinline__ int scale_exp(double amax) {
     if (!(amax > 0.0)) return 0;
@@ -30,21 +37,42 @@ __device__ __forceinline__ int scale_exp(double amax) {
 }
 
 // Digits of q = x 2^-e in (-1, 1): X = round(q 2^(7 ND)) (an integer below
-// 2^(7 ND) in magnitude, converted exactly), then its balanced base-128
-// digits from the bottom: d_t = ((X + 64) mod 128) - 64 in [-64, 63],
-// X <- (X - d_t) / 128; what is left is d_1 in [-128, 128].  Integer
-// arithmetic except for one scaling and one conversion (the FP64 units of
-// GB300 are scarce); the dropped remainder is below 2^-(7 ND + 1).
+// 2^(7 ND) in magnitude), then its balanced base-128 digits from the
+// bottom: d_t = ((X + 64) mod 128) - 64 in [-64, 63], X <- (X - d_t) / 128;
+// what is left is d_1 in [-128, 128].  X comes straight from the IEEE bit
+// pattern (x = mant 2^ex, shifted by ex + 7 ND - e with round-half-even),
+// all in integer arithmetic: GB300's FP64 units, where scaling and
+// conversion would run, are scarce.  The dropped remainder is below
+// 2^-(7 ND + 1); a non-finite x gives X = 0.
 template <int ND>
 __device__ __forceinline__ void digits(double x, int e, float (&d)[ND]) {
-    long long X = __double2ll_rn(ldexp(x, 7 * ND - e));
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7FF);
+    unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
+    int ex = -1074;                                   // x = mant 2^ex
+    if (E != 0) {
+        mant |= 1ull << 52;
+        ex = E - 1075;
+    }
+    const int sh = ex + 7 * ND - e;
+    unsigned long long m = 0;
+    if (E == 0x7FF || mant == 0) {
+        m = 0;
+    } else if (sh >= 0) {
+        m = mant << sh;                               // below 2^(7 ND): |x| < 2^e
+    } else if (sh > -64) {
+        const int r = -sh;
+        const unsigned long long q = mant >> r, rem = mant & ((1ull << r) - 1), half = 1ull << (r - 1);
+        m = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+    }
+    long long X = (b >> 63) ? -(long long)m : (long long)m;
 #pragma unroll
     for (int t = ND - 1; t >= 1; --t) {
         const long long lo = ((X + 64) & 127) - 64;
-        d[t] = (float)lo;
+        d[t] = (float)(int)lo;
         X = (X - lo) >> 7;
     }
-    d[0] = (float)X;
+    d[0] = (float)(int)X;
 }
 
 // Writes the ND digit slices of one operand entry (a small integer each: exact in BF16).
@@ -63,10 +91,10 @@ __global__ void k_slice_rows(const double *src, int64_t lds, int64_t m, int64_t 
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp; i < m; i += nw) {
         const double *a = src + i * lds;
-        double mx = 0.0;
-        for (int64_t k = lane; k < K; k += 32) mx = fmax(mx, fabs(a[k]));
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        const int e = scale_exp(mx);
+        unsigned long long mb = 0ull;
+        for (int64_t k = lane; k < K; k += 32) mb = max(mb, abs_bits(a[k]));
+        for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+        const int e = scale_exp(__longlong_as_double((long long)mb));
         if (lane == 0) exps[i] = e;
         __nv_bfloat16 *row = dst + i * ldq;
         for (int64_t k = lane; k < kpad; k += 32) {
@@ -78,12 +106,21 @@ __global__ void k_slice_rows(const double *src, int64_t lds, int64_t m, int64_t 
 }
 
 // B operand: columns of src (K x n, FP64, ld lds), written transposed
-// (row j of dst holds column j).  Pass 1: column exponents.
+// (row j of dst holds column j).  Pass 1: column exponents; a CTA takes 32
+// columns, its 8 warps split the rows (coalesced 256-byte rows per warp),
+// and the 8 partial maxima meet in shared memory.
 __global__ void k_col_exps(const double *src, int64_t lds, int64_t K, int64_t n, int *exps) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-        double mx = 0.0;
-        for (int64_t k = 0; k < K; ++k) mx = fmax(mx, fabs(src[k * lds + j]));
-        exps[j] = scale_exp(mx);
+    __shared__ unsigned long long part[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t j = (int64_t)blockIdx.x * 32 + tx;
+    unsigned long long mb = 0ull;
+    if (j < n)
+        for (int64_t k = ty; k < K; k += 8) mb = max(mb, abs_bits(src[k * lds + j]));
+    part[ty][tx] = mb;
+    __syncthreads();
+    if (ty == 0 && j < n) {
+        for (int w = 1; w < 8; ++w) mb = max(mb, part[w][tx]);
+        exps[j] = scale_exp(__longlong_as_double((long long)mb));
     }
 }
 
@@ -179,7 +216,7 @@ cudaError_t slice_cols_T(int nd, const double *src, int64_t lds, int64_t K, int6
     const int64_t kpad = sliced_kpad(K);
     if (!sliced::supported(nd) || ldq < nd * kpad) return cudaErrorInvalidValue;
     note_launch();
-    k_col_exps<<<(unsigned)cdiv(n, 256), 256, 0, s>>>(src, lds, K, n, exps);
+    k_col_exps<<<(unsigned)cdiv(n, 32), 256, 0, s>>>(src, lds, K, n, exps);
     dim3 g((unsigned)cdiv(n, 32), (unsigned)cdiv(kpad, 32));
     if (g.y > 65535u) return cudaErrorInvalidValue;
     note_launch();

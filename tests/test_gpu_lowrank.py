@@ -95,3 +95,45 @@ def test_lowrank_rejects_bad_args(g):
     assert lib.genp_lowrank(8, 8, p(A), 8, 0, 0, 0, 0, None, 0, p(Q), 8, None, 0, None, 0, None, s) == -1   # r = 0
     assert lib.genp_lowrank(8, 8, p(A), 8, 9, 0, 0, 0, None, 0, p(Q), 8, None, 0, None, 0, None, s) == -1   # r > n
     assert lib.genp_lowrank(8, 8, p(A), 8, 2, 2, 0, 0, None, 0, p(Q), 8, None, 0, None, 0, None, s) == -1   # kind
+
+
+# ------------------------------------------------ numerical rank (App. B)
+
+@pytest.mark.parametrize("n,q,seed", [(64, 1, 0), (64, 8, 1), (128, 8, 2), (128, 32, 3), (256, 32, 4), (256, 17, 5)])
+def test_numerical_rank_vs_oracle(g, n, q, seed):
+    """Same rank as the oracle's search (exact kappa by SVD there, power and
+    inverse iteration here: the inputs' gap, 1e4 against 1e9, leaves no
+    decision near cond_max = 1e6), and the same basis A^T G_rank within the
+    FP64 GEMM's 2 gamma_n |A|^T |G|."""
+    A, S, T, s = (t.numpy() for t in W.lowrank(n, q, seed))
+    r_hi = min(n, 128)
+    rank, B = g.numerical_rank(torch.as_tensor(A).to(DEV), 0, r_hi, cond_max=1e6, seed=seed + 7)
+    G = oracle.sketch_multiplier(n, r_hi, seed=seed + 7)
+    rref, Bref, trace = oracle.numerical_rank(A, 0, r_hi, 1e6, G)
+    assert rank == rref == q
+    gam = 2 * n * U / (1 - 2 * n * U)
+    assert np.all(np.abs(host(B) - Bref) <= gam * (np.abs(A).T @ np.abs(G[:, :q])))
+
+
+def test_numerical_rank_ranges(g):
+    A, S, T, s = (t.numpy() for t in W.lowrank(64, 8, 0))
+    Ad = torch.as_tensor(A).to(DEV)
+    assert g.numerical_rank(Ad, 5, 5, seed=1)[0] == 5
+    assert g.numerical_rank(Ad, 0, 4, seed=1)[0] == 4
+    assert g.numerical_rank(Ad, 12, 32, seed=1)[0] == 12
+    assert g.numerical_rank(Ad, 0, 0, seed=1)[0] == 0
+
+
+def test_cond_estimate_matches_svd(g):
+    """COND's kappa estimate on a well separated full-rank sketch: the search
+    over [r, r] performs no test, so test through a range whose midpoint is
+    r: a matrix with kappa(A^T G_r) known from the SVD, cond_max just above
+    and just below it (factor 2 either way)."""
+    n, q = 128, 16
+    A, S, T, s = (t.numpy() for t in W.lowrank(n, q, 2))
+    G = oracle.sketch_multiplier(n, 16, seed=3)      # the sketch of width r_hi = 16
+    kappa = np.linalg.cond(A.T @ G)
+    Ad = torch.as_tensor(A).to(DEV)
+    # range [15, 16]: the single test is at r = 16
+    assert g.numerical_rank(Ad, 15, 16, cond_max=2 * kappa, seed=3)[0] == 16
+    assert g.numerical_rank(Ad, 15, 16, cond_max=kappa / 2, seed=3)[0] == 15

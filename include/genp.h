@@ -57,7 +57,7 @@ typedef enum {
     GENP_ERR_CUDA = -4,        /* a CUDA runtime call failed                        */
     GENP_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up                */
     GENP_ERR_NOMEM = -6,       /* device memory could not be allocated              */
-    GENP_ERR_UNSUPPORTED = -7  /* valid combination that this build does not offer  */
+    GENP_ERR_UNSUPPORTED = -7  /* valid combination that the library does not offer*/
 } genp_status;
 
 /* Random multiplier families.
@@ -110,7 +110,7 @@ typedef enum {
  *        Schur-complement products use BF16 operands on the tensor cores
  *        with FP32 accumulation; the diagonal blocks are factored in FP64.
  *  FP8_E4M3: as BF16 with e4m3 operands and a power-of-two scale per
- *        128 x 128 tile (not offered by this build: GENP_ERR_UNSUPPORTED).
+ *        128 x 128 tile (not offered by the library: GENP_ERR_UNSUPPORTED).
  *  BF16X3: as BF16, but every operand is split into three BF16 terms and
  *        six of their products are accumulated (a1b1 + a1b2 + a2b1 + a1b3 +
  *        a2b2 + a3b1), which brings the tensor-core products close to FP32

@@ -202,7 +202,7 @@ const char *genp_status_string(genp_status s) {
         case GENP_ERR_CUDA: return "GENP_ERR_CUDA: CUDA runtime error";
         case GENP_ERR_TIMEOUT: return "GENP_ERR_TIMEOUT: bounded device wait gave up";
         case GENP_ERR_NOMEM: return "GENP_ERR_NOMEM: device allocation failed";
-        case GENP_ERR_UNSUPPORTED: return "GENP_ERR_UNSUPPORTED: combination not offered by this build";
+        case GENP_ERR_UNSUPPORTED: return "GENP_ERR_UNSUPPORTED: combination not offered by the library";
     }
     return "unknown genp status";
 }

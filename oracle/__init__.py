@@ -476,6 +476,128 @@ def numerical_rank(A: np.ndarray, r_lo: int, r_hi: int, cond_max: float, G: np.n
 
 
 # --------------------------------------------------------------------------
+# FP8 (e4m3) operands with a power-of-two scale per 128 x 128 tile (the
+# mixed-precision pattern: Schur update and A G on 8-bit operands, accuracy
+# won back by FP64 refinement, Sec. 7.1)
+# --------------------------------------------------------------------------
+
+E4M3_MAX = 448.0          # 1.75 * 2^8, the largest finite e4m3 value
+FP8_TILE = 128
+
+
+def e4m3_decode(codes) -> np.ndarray:
+    """Value of each e4m3 code (1 sign bit, 4 exponent bits with bias 7, 3
+    mantissa bits; exponent field 0 is subnormal, m/8 * 2^-6; code S.1111.111
+    is NaN; there are no infinities)."""
+    c = np.asarray(codes, dtype=np.int64)
+    sgn = np.where(c & 0x80, -1.0, 1.0)
+    E = (c >> 3) & 0xF
+    m = (c & 7).astype(np.float64)
+    v = np.where(E == 0, m / 8.0 * 2.0 ** -6, (1.0 + m / 8.0) * np.exp2(E.astype(np.float64) - 7.0))
+    v = np.where((E == 15) & ((c & 7) == 7), np.nan, v)
+    return sgn * v
+
+
+def e4m3_round(x) -> np.ndarray:
+    """Nearest e4m3 value of each (finite) x, ties to the even mantissa,
+    magnitudes above 448 saturated to 448.  Below 2^-6 the spacing is the
+    subnormal quantum 2^-9; in [2^p, 2^{p+1}) it is 2^{p-3}."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    _, p = np.frexp(a)                       # a = f 2^p, f in [0.5, 1): binade 2^{p-1}
+    qexp = np.maximum(p - 1, -6) - 3
+    q = np.ldexp(np.rint(np.ldexp(a, -qexp)), qexp)    # rint: ties to even
+    q = np.minimum(q, E4M3_MAX)
+    return np.copysign(q, x)
+
+
+def e4m3_encode(v) -> np.ndarray:
+    """Code of each value already on the e4m3 grid (inverse of e4m3_decode)."""
+    v = np.asarray(v, dtype=np.float64)
+    a = np.abs(v)
+    sign = np.where(np.signbit(v), 0x80, 0)
+    _, p = np.frexp(a)
+    normal = a >= 2.0 ** -6
+    E = np.where(normal, p - 1 + 7, 0)
+    m = np.where(normal, np.ldexp(a, -(p - 1)) * 8.0 - 8.0, np.ldexp(a, 9))
+    return (sign | (E << 3) | m.astype(np.int64)).astype(np.uint8)
+
+
+def tile_exponent(amax: float) -> int:
+    """The least integer e with amax <= 448 2^e (0 for amax = 0), clamped to
+    [-126, 126] so that 2^e is a normal FP32 number.  With amax = f 2^p,
+    f in [0.5, 1): 448 2^e = 0.875 2^{e+9}, so e = p - 9 when f <= 0.875,
+    else p - 8."""
+    if not (amax > 0.0) or not np.isfinite(amax):
+        return 0
+    f, p = np.frexp(float(amax))
+    e = int(p) - 9 if f <= 0.875 else int(p) - 8
+    return max(-126, min(126, e))
+
+
+def quantize_e4m3(X: np.ndarray):
+    """Codes and scales of X (m x K) with one power-of-two scale per
+    128 x 128 tile (tile (ti, kt): rows 128 ti .., columns 128 kt ..):
+    codes[i, k] = e4m3(X[i, k] / 2^e_tile), scales[ti, kt] = 2^e_tile."""
+    X = np.asarray(X, dtype=np.float64)
+    m, K = X.shape
+    T = FP8_TILE
+    ntm, nkt = -(-m // T), -(-K // T)
+    codes = np.zeros((m, K), dtype=np.uint8)
+    scales = np.ones((ntm, nkt))
+    for ti in range(ntm):
+        for kt in range(nkt):
+            blk = X[ti * T:(ti + 1) * T, kt * T:(kt + 1) * T]
+            e = tile_exponent(float(np.max(np.abs(blk))) if blk.size else 0.0)
+            scales[ti, kt] = 2.0 ** e
+            codes[ti * T:(ti + 1) * T, kt * T:(kt + 1) * T] = e4m3_encode(e4m3_round(np.ldexp(blk, -e)))
+    return codes, scales
+
+
+def dequantize_e4m3(codes: np.ndarray, scales: np.ndarray) -> np.ndarray:
+    """The values the codes and tile scales stand for."""
+    T = FP8_TILE
+    S = np.repeat(np.repeat(scales, T, axis=0), T, axis=1)[: codes.shape[0], : codes.shape[1]]
+    return e4m3_decode(codes) * S
+
+
+def gemm_e4m3(Aq, sA, Bq, sB, alpha: float = 1.0, beta: float = 0.0, C=None) -> np.ndarray:
+    """D = alpha sum_kt sA[tm, kt] sB[tn, kt] (A_kt B_kt^T) + beta C, for
+    A (m x K) and B^T (n x K) as codes with tile scales.  Each k-tile's
+    products of e4m3 values and their sums are exact in FP64 (at most 43
+    significant bits); the k-tiles are summed in FP64."""
+    T = FP8_TILE
+    A = e4m3_decode(Aq)
+    B = e4m3_decode(Bq)
+    m, K = A.shape
+    n = B.shape[0]
+    D = np.zeros((m, n))
+    for kt in range(-(-K // T)):
+        P = matmul(A[:, kt * T:(kt + 1) * T].copy(), B[:, kt * T:(kt + 1) * T].T.copy())
+        rs = np.repeat(sA[:, kt], T)[:m]
+        cs = np.repeat(sB[:, kt], T)[:n]
+        D += P * rs[:, None] * cs[None, :]
+    D *= alpha
+    if beta != 0.0:
+        D += beta * np.asarray(C, dtype=np.float64)
+    return D
+
+
+FP8_GRID_SD = 12.5        # bounds every polar-method draw (|z| <= sqrt(2 ln 2^104) < 12.1)
+
+
+def fp8_grid(G: np.ndarray, scale: float) -> np.ndarray:
+    """A Gaussian multiplier of entry scale ``scale`` rounded to the FP8 grid:
+    e4m3 values times 2^e, e = tile_exponent(12.5 scale), one exponent for the
+    whole matrix (Thm. 4.1 admits the perturbation; the rounded G is the
+    multiplier everywhere, so G A and x = G y use the same matrix).  G is the
+    FP32-grid draw (``multiplier(..., grid="fp32")``): the FP8 grid rounds
+    that draw."""
+    e = tile_exponent(FP8_GRID_SD * float(scale))
+    return np.ldexp(e4m3_round(np.ldexp(np.asarray(G, dtype=np.float64), -e)), e)
+
+
+# --------------------------------------------------------------------------
 # Exact references used by the pins
 # --------------------------------------------------------------------------
 

@@ -740,3 +740,135 @@ def test_numerical_rank_degenerate_ranges():
     assert oracle.numerical_rank(A, 5, 5, 1e6, G)[0] == 5          # r_lo = r_hi: no test
     assert oracle.numerical_rank(A, 0, 4, 1e6, G)[0] == 4          # rank above the range: r_hi
     assert oracle.numerical_rank(A, 12, 32, 1e6, G)[0] == 12       # rank below the range: r_lo
+
+
+# --------------------------------------------------------------------------
+# FP8 (e4m3) operands with per-tile power-of-two scales
+# --------------------------------------------------------------------------
+
+def _torch_e4m3():
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("torch without float8_e4m3fn")
+    return torch
+
+
+def test_e4m3_decode_matches_torch():
+    """All 256 codes against PyTorch's float8_e4m3fn (an independent
+    implementation of the same format): equal values, the same two NaNs."""
+    torch = _torch_e4m3()
+    codes = np.arange(256, dtype=np.uint8)
+    v = oracle.e4m3_decode(codes)
+    t = torch.tensor(codes).view(torch.float8_e4m3fn).double().numpy()
+    assert np.array_equal(np.isnan(v), np.isnan(t)) and int(np.isnan(v).sum()) == 2
+    assert np.array_equal(v[~np.isnan(v)], t[~np.isnan(t)])
+    assert v[0x7E] == 448.0 and v[0x01] == 2.0 ** -9 and v[0x08] == 2.0 ** -6
+    fin = ~np.isnan(v)
+    assert np.array_equal(oracle.e4m3_encode(v[fin]), codes[fin])
+
+
+def test_e4m3_round_matches_torch_and_brute_force():
+    """Rounding to nearest, ties to even: against PyTorch's float32 ->
+    float8_e4m3fn conversion on random values and on every midpoint between
+    neighbouring grid values (inside the finite range, where its rule agrees),
+    and against a brute-force nearest-grid-value search."""
+    torch = _torch_e4m3()
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(100000) * np.exp2(rng.uniform(-14, 9, 100000))
+    x = x.astype(np.float32).astype(np.float64)
+    x = x[np.abs(x) < 448.0]
+    r = oracle.e4m3_round(x)
+    t = torch.tensor(x, dtype=torch.float32).to(torch.float8_e4m3fn).double().numpy()
+    assert np.array_equal(r, t)
+    grid = oracle.e4m3_decode(np.arange(256, dtype=np.uint8))
+    pos = np.unique(grid[np.isfinite(grid) & (grid >= 0)])
+    mid = (pos[:-1] + pos[1:]) / 2
+    rm = oracle.e4m3_round(mid)
+    tm = torch.tensor(mid, dtype=torch.float32).to(torch.float8_e4m3fn).double().numpy()
+    assert np.array_equal(rm, tm)
+    # ties go to the neighbour with the even code
+    codes = oracle.e4m3_encode(rm)
+    assert np.all(codes % 2 == 0)
+    # brute force on a sample: the nearest grid value, ties to the even code
+    for v in np.concatenate([x[:2000], mid]):
+        d = np.abs(pos - abs(v))
+        best = np.flatnonzero(d == d.min())
+        pick = pos[best[0]] if len(best) == 1 else [g for g in pos[best] if oracle.e4m3_encode(g) % 2 == 0][0]
+        assert oracle.e4m3_round(v) == math.copysign(pick, v)
+
+
+def test_e4m3_saturates_at_448():
+    x = np.array([448.0, 463.99, 464.0, 480.0, 1e6, -1e30])
+    assert np.array_equal(oracle.e4m3_round(x), np.array([448.0, 448.0, 448.0, 448.0, 448.0, -448.0]))
+
+
+def test_tile_exponent_is_the_least_that_fits():
+    """2^e is the smallest power of two with amax <= 448 2^e."""
+    rng = np.random.default_rng(3)
+    amaxes = np.concatenate([np.exp2(rng.uniform(-100, 100, 2000)),
+                             448.0 * np.exp2(np.arange(-20, 21)),
+                             np.nextafter(448.0 * np.exp2(np.arange(-20, 21)), np.inf),
+                             np.nextafter(448.0 * np.exp2(np.arange(-20, 21)), 0.0)])
+    for a in amaxes:
+        e = oracle.tile_exponent(a)
+        assert a <= 448.0 * 2.0 ** e
+        assert a > 448.0 * 2.0 ** (e - 1)
+    assert oracle.tile_exponent(0.0) == 0
+    assert oracle.tile_exponent(1e-300) == -126 and oracle.tile_exponent(1e300) == 126
+
+
+def test_quantize_e4m3_error_bounds_and_tiles():
+    """Every tile: |x - dequantized| <= 2^-4 |x| where the code is normal,
+    <= 2^-10 s where it is subnormal (s the tile's scale); the tile maximum
+    lands in [224, 448]; a zero tile gets scale 1 and zero codes."""
+    rng = np.random.default_rng(11)
+    m, K = 300, 270
+    X = rng.standard_normal((m, K)) * np.exp2(rng.uniform(-20, 20, (m, 1)))
+    X[128:256, 128:256] = 0.0
+    codes, scales = oracle.quantize_e4m3(X)
+    assert scales.shape == (3, 3) and codes.shape == (m, K)
+    D = oracle.dequantize_e4m3(codes, scales)
+    S = np.repeat(np.repeat(scales, 128, 0), 128, 1)[:m, :K]
+    sub = np.abs(X / S) < 2.0 ** -6
+    assert np.all(np.abs(D - X)[~sub] <= 2.0 ** -4 * np.abs(X)[~sub])
+    assert np.all(np.abs(D - X)[sub] <= 2.0 ** -10 * S[sub])
+    assert scales[1, 1] == 1.0 and not codes[128:256, 128:256].any()
+    for ti in range(3):
+        for kt in range(3):
+            blk = np.abs(X[ti * 128:(ti + 1) * 128, kt * 128:(kt + 1) * 128]) / scales[ti, kt]
+            if blk.max() > 0:
+                assert 224.0 < blk.max() <= 448.0
+
+
+def test_gemm_e4m3_exact_on_small_integers():
+    """Integers of magnitude <= 15 are exact e4m3 values at every tile scale
+    the rule picks (4 significant bits), so the tile-scaled product must equal
+    the integer product exactly, over several k-tiles and ragged edges."""
+    rng = np.random.default_rng(5)
+    m, n, K = 200, 150, 333
+    A = rng.integers(-15, 16, (m, K))
+    B = rng.integers(-15, 16, (K, n))
+    A[:128, :128] = rng.integers(-3, 4, (128, 128))          # another tile scale
+    Aq, sA = oracle.quantize_e4m3(A.astype(np.float64))
+    Bq, sB = oracle.quantize_e4m3(B.T.astype(np.float64))
+    assert np.array_equal(oracle.dequantize_e4m3(Aq, sA), A)
+    D = oracle.gemm_e4m3(Aq, sA, Bq, sB, alpha=2.0, beta=-1.0, C=np.ones((m, n)))
+    assert np.array_equal(D, 2.0 * (A @ B).astype(np.float64) - 1.0)
+
+
+def test_fp8_grid_multiplier():
+    """The FP8 grid: one exponent e for the matrix with 12.5 scale <= 448 2^e
+    (the polar method never draws beyond 12.1 standard deviations, so nothing
+    saturates), every entry an e4m3 value times 2^e, the nearest one."""
+    n = 256
+    M = oracle.multiplier(oracle.KIND_GAUSSIAN, n, seed=4, grid="fp32")
+    s = 1.0 / np.sqrt(n)
+    G8 = oracle.fp8_grid(M["G"], s)
+    e = oracle.tile_exponent(12.5 * s)
+    assert 12.5 * s <= 448.0 * 2.0 ** e < 2 * 12.5 * s
+    q = np.ldexp(G8, -e)
+    assert np.array_equal(oracle.e4m3_round(q), q)
+    assert np.max(np.abs(q)) < 448.0
+    rel = np.abs(G8 - M["G"]) / np.abs(M["G"])
+    big = np.abs(q) >= 2.0 ** -6
+    assert np.all(rel[big] <= 2.0 ** -4)

@@ -190,6 +190,14 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
 __device__ __forceinline__ void st_release(int *p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// Publishes a flag for the writes the whole CTA made before a __syncthreads:
+// the barrier orders them before this thread's fence, and the fence and the
+// release store (both GPU scope, cumulative) make them visible to any thread
+// that reads the flag with acquire semantics.
+__device__ __forceinline__ void publish(int *p) {
+    __threadfence();
+    st_release(p, 1);
+}
 __device__ bool wait_geq(const int *p, int target) {
     const long long t0 = clock64();
     while (ld_acquire(p) < target) {
@@ -436,15 +444,16 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
                 store_d(sd.Sh, sd.Sl, vX, 2);
                 if (tid == 0 && q >= 2 && !wait_geq(cnt + j, q - 1)) atomicExch(&g_solve_timeout, 1);
                 __syncthreads();
-                if (q + 1 < nblk) {
-                    load_tile_d(block_of(q + 1), j, vO);
-                    load_tile_d(block_of(q + 1), block_of(q + 1), vD);
-                    load_inv_d(block_of(q + 1), vX);
-                }
+                // b_j first: its loads must not queue behind the next step's tiles
                 for (int idx = tid; idx < TB * NR; idx += kTrsvThreads) {
                     const int rr = idx / NR, c = idx % NR;
                     const dfloat b((rr < bj && c < nr) ? (double)ldcg(Y + ((int64_t)j * TB + rr) * ldy + c) : 0.0);
                     sd.acc[rr][c] = q > 0 ? b - sd.carry[rr][c] : b;
+                }
+                if (q + 1 < nblk) {
+                    load_tile_d(block_of(q + 1), j, vO);
+                    load_tile_d(block_of(q + 1), block_of(q + 1), vD);
+                    load_inv_d(block_of(q + 1), vX);
                 }
                 __syncthreads();
                 // y = X b;  y += X (b - T y)
@@ -467,9 +476,8 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
                         sd.y[r][c] = yv;
                         if (r < bj && c < nr) Y[((int64_t)j * TB + r) * ldy + c] = (T)(double)yv;
                     }
-                __threadfence();
                 __syncthreads();
-                if (tid == 0) st_release(ready + j, 1);
+                if (tid == 0) publish(ready + j);
                 if (q + 1 < nblk) {           // own contribution to the next block
                     store_d(sd.Oh, sd.Ol, vO, 0);
                     __syncthreads();
@@ -495,15 +503,16 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
                 // wait for the items of steps up to q - 2, then b_j = Y_j - own carry
                 if (tid == 0 && q >= 2 && !wait_geq(cnt + j, q - 1)) atomicExch(&g_solve_timeout, 1);
                 __syncthreads();
-                if (q + 1 < nblk) {           // next step's tiles, in flight during this one
-                    load_tile(block_of(q + 1), j, vO);
-                    load_tile(block_of(q + 1), block_of(q + 1), vD);
-                    load_inv(block_of(q + 1), vX);
-                }
+                // b_j first: its loads must not queue behind the next step's tiles
                 for (int idx = tid; idx < TB * NR; idx += kTrsvThreads) {
                     const int rr = idx / NR, c = idx % NR;
                     const T b = (rr < bj && c < nr) ? ldcg(Y + ((int64_t)j * TB + rr) * ldy + c) : T(0);
                     sm.acc[rr][c] = q > 0 ? b - sm.carry[rr][c] : b;
+                }
+                if (q + 1 < nblk) {           // next step's tiles, in flight during this one
+                    load_tile(block_of(q + 1), j, vO);
+                    load_tile(block_of(q + 1), block_of(q + 1), vD);
+                    load_inv(block_of(q + 1), vX);
                 }
                 __syncthreads();
                 // y = X b;  y += X (b - T y)  (one refinement step of the explicit inverse)
@@ -526,9 +535,8 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
                         sm.y[r][c] = yv;
                         if (r < bj && c < nr) Y[((int64_t)j * TB + r) * ldy + c] = yv;
                     }
-                __threadfence();
                 __syncthreads();
-                if (tid == 0) st_release(ready + j, 1);
+                if (tid == 0) publish(ready + j);
                 if (q + 1 < nblk) {           // own contribution to the next block
                     store_tile(sm.O, vO);
                     __syncthreads();
@@ -574,9 +582,11 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
             for (int c = 0; c < NR; ++c)
                 if ((c & 3) == qq && c < nr) atomicAdd(Y + row * ldy + c, -part[c]);
         }
-        __threadfence();
         __syncthreads();
-        if (tid == 0) atomicAdd(cnt + i, p1 - p0 + 1);
+        if (tid == 0) {       // release: the CTA's updates above, ordered by the barrier
+            __threadfence();
+            atomicAdd(cnt + i, p1 - p0 + 1);
+        }
     }
 }
 

@@ -40,8 +40,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solves/s & TFLOP/s (2n³/3), BF16+IR vs FP64 GENP, same GB300, bwd err ≤1e-14"
 KINDS = {"gaussian": 0, "circulant": 1, "sparse": 2, "toeplitz": 5, "householder": 6}
-PRECS = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 4, "sliced": 5}
-GRID_OF = {"fp64": 0, "fp32": 1, "bf16": 2, "bf16x3": 2, "sliced": 1}   # sliced: G drawn on the FP32 grid
+PRECS = {"fp64": 0, "fp32": 1, "bf16": 2, "fp8": 3, "bf16x3": 4, "sliced": 5}
+# sliced: G drawn on the FP32 grid; fp8: on the FP8 grid (e4m3 times one power of two)
+GRID_OF = {"fp64": 0, "fp32": 1, "bf16": 2, "fp8": 3, "bf16x3": 2, "sliced": 1}
 F64_FACTORS = ("fp64", "sliced")
 
 
@@ -354,7 +355,7 @@ def run_ours(a):
     phases = ["multiplier", "precondition", "factor", "solve", "refine", "adjoint"]
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(a.steps)]
     lib = genp._lib.load()
-    if a.prec == "sliced":      # CUDA events around every tensor-core launch of the timed region
+    if a.prec in ("sliced", "fp8"):   # CUDA events around every tensor-core launch of the timed region
         lib.genp_profile_enable(1)
     if world > 1:
         dist.barrier()
@@ -371,8 +372,15 @@ def run_ours(a):
         torch.cuda.synchronize()
     launches = genp.launch_count() - l0
     tc_prof = None
-    if a.prec == "sliced":
+    tc_launches = None
+    if a.prec in ("sliced", "fp8"):
         import ctypes
+        cnt = ctypes.c_int()
+        lib.genp_profile_launches(None, None, 0, ctypes.byref(cnt))
+        if cnt.value > 0:
+            l_ms, l_fl = (ctypes.c_double * cnt.value)(), (ctypes.c_double * cnt.value)()
+            lib.genp_profile_launches(l_ms, l_fl, cnt.value, ctypes.byref(cnt))
+            tc_launches = (list(l_ms), list(l_fl))
         p_ms, p_fl, p_n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
         lib.genp_profile_read(ctypes.byref(p_ms), ctypes.byref(p_fl), ctypes.byref(p_n))
         lib.genp_profile_enable(0)
@@ -488,6 +496,42 @@ def run_ours(a):
                     "traffic": 294.0e6 * (n / 4096) ** 2 if nd == 7 else None,
                     "traffic_basis": "A G chunk launch (K = 512); Schur-update launches (K = 256) move about "
                                      "the same bytes per tile for half the flops"}
+    elif a.prec == "fp8" and tc_launches:
+        # per launch: the A G product (K = n, k_tc_e4m3, tensor-bound) and the
+        # Schur updates (K = nb <= 128, k_tc_gemm<true>, HBM-bound: C read and
+        # written once, 8 B per entry); flops 2 m n K, so the update's m = n' is
+        # sqrt(flops / (2 K)) with K = 128 (the last, ragged block aside)
+        l_ms, l_fl = tc_launches
+        ag = [(t, f) for t, f in zip(l_ms, l_fl) if f >= 2.0 * n**3 * 0.999]
+        su = [(t, f) for t, f in zip(l_ms, l_fl) if f < 2.0 * n**3 * 0.999]
+        base = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
+        fp8_peak = 2.0 * base
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        su_ms = sum(t for t, _ in su)
+        su_bytes = sum(8.0 * (f / 256.0) for _, f in su)        # m^2 = f / (2 K), 8 B per C entry
+        ag_ms = sum(t for t, _ in ag)
+        ag_tf = sum(f for _, f in ag) / (ag_ms / 1e3) / 1e12 if ag_ms > 0 else None
+        dominant_su = su_ms >= ag_ms
+        if dominant_su:
+            achieved = su_bytes / (su_ms / 1e3) / 1e9
+            roofline = {"kernel": "k_tc_gemm<true> (tcgen05 kind::f8f6f4 Schur updates, K = 128: C22 read and written)",
+                        "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                        "peak_source": "measured hbm_gbs" if "hbm_gbs" in peaks else "fallback",
+                        "launches": len(su), "avg_launch_ms": su_ms / len(su),
+                        "share_of_step": (su_ms / a.steps) / ms_per_step,
+                        "algorithmic": "8 B per C22 entry (FP32 read + write) per launch", "traffic": None}
+        else:
+            achieved = ag_tf
+            roofline = {"kernel": "k_tc_e4m3 (tcgen05 kind::f8f6f4 C = A G, FP32 promotion per 128-wide k-tile)",
+                        "bound": "tensor", "achieved": achieved, "peak": fp8_peak, "unit": "TFLOP/s",
+                        "frac": achieved / fp8_peak, "launches": len(ag), "avg_launch_ms": ag_ms / len(ag),
+                        "share_of_step": (ag_ms / a.steps) / ms_per_step, "algorithmic": "2 n^3 e4m3 flop per launch",
+                        "traffic": None}
+        roofline["A_G_kernel"] = {"kernel": "k_tc_e4m3", "achieved_tflops": ag_tf, "peak": fp8_peak,
+                                  "frac": (ag_tf / fp8_peak) if ag_tf else None, "avg_launch_ms":
+                                  ag_ms / len(ag) if ag else None,
+                                  "peak_source": "measured bf16_tflops_sustained x 2 (dense e4m3 / bf16 tensor "
+                                                 "rate, 4.5 / 2.25 PFLOP/s nominal)"}
     elif a.kind == "gaussian" and a.prec in ("bf16", "bf16x3"):
         terms = 3 if a.prec == "bf16x3" else 1
         achieved = terms * 2.0 * n**3 / (phase_ms["precondition"] / 1e3) / 1e12
@@ -527,7 +571,7 @@ def run_ours(a):
         fp64 = fp64_same_gpu(a, genp, A, B, kind, rank, dev)
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "sliced": "bf16"}.get(a.prec, a.prec),
+            "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "sliced": "bf16", "fp8": "e4m3"}.get(a.prec, a.prec),
             "data": "synthetic",
             "config": {"workload": workload_name(a), "n": n, "nrhs": nrhs, "multiplier": a.kind, "precision": a.prec,
                        "digits": {"factor": lib.genp_sliced_digits(0),

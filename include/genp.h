@@ -108,9 +108,15 @@ typedef enum {
  *  FP32: C and the factors are float; every step in FP32.
  *  BF16: C and the factors are stored as float (the master copy); the
  *        Schur-complement products use BF16 operands on the tensor cores
- *        with FP32 accumulation; the diagonal blocks are factored in FP64.
- *  FP8_E4M3: as BF16 with e4m3 operands and a power-of-two scale per
- *        128 x 128 tile (not offered by the library: GENP_ERR_UNSUPPORTED).
+ *        with FP32 accumulation; the diagonal blocks are factored in
+ *        double-float arithmetic (48 bits: FP64-class pivots).
+ *  FP8_E4M3: as BF16 with e4m3 operands (3 mantissa bits) and one
+ *        power-of-two scale per 128 x 128 operand tile (genp_quantize_e4m3);
+ *        for a Gaussian multiplier A G runs on the e4m3 tensor cores too,
+ *        with G drawn on the FP8 grid (value_grid GENP_FP8_E4M3).  The
+ *        factors carry errors of order 2^-4 times the element growth: they
+ *        precondition GMRES-IR on well-conditioned systems of moderate
+ *        growth and fail to where that product approaches 1.
  *  BF16X3: as BF16, but every operand is split into three BF16 terms and
  *        six of their products are accumulated (a1b1 + a1b2 + a2b1 + a1b3 +
  *        a2b2 + a3b1), which brings the tensor-core products close to FP32
@@ -176,7 +182,12 @@ GENP_API const char *genp_status_string(genp_status s);
  *  value_grid  GENP_FP64: entries as drawn.  GENP_BF16: every entry rounded
  *              to the nearest BF16 value (Thm. 4.1 allows a perturbed
  *              Gaussian H = H' + V), so the tensor-core product and the FP64
- *              correction x += G d use exactly the same G.  SPARSE ignores it.
+ *              correction x += G d use exactly the same G.  GENP_FP32:
+ *              drawn in single precision.  GENP_FP8_E4M3: the single
+ *              precision draw rounded to an e4m3 value times 2^e, one e for
+ *              the matrix (the least with 12.5 scale <= 448 2^e, so no entry
+ *              saturates).  SPARSE,
+ *              IDENTITY and HOUSEHOLDER_PM1 ignore it.
  *  out         receives the handle; the library owns G's device storage.
  * Errors: GENP_ERR_ARG, GENP_ERR_NOMEM, GENP_ERR_CUDA. */
 GENP_API genp_status genp_make_multiplier(genp_mult_kind kind, int64_t n, uint64_t seed, uint64_t stream_id,
@@ -232,8 +243,11 @@ GENP_API void genp_multiplier_destroy(genp_multiplier *G);
  *         else float.  C must not overlap A.
  *  c_prec the factorization the product is for: FP64 (DFMA), FP32 (FFMA),
  *         BF16 (tensor cores, A rounded to BF16, G must have value_grid BF16),
+ *         FP8_E4M3 (tensor cores, A as tile-scaled e4m3 codes, G must have
+ *         value_grid FP8_E4M3),
  *         BF16_SLICED (A double; a dense G on the tensor cores by digit
- *         slicing, in K chunks of 512; about 35 bits; other kinds as FP64).
+ *         slicing, in K chunks of 512, genp_sliced_precondition_digits
+ *         digits; other kinds as FP64).
  * Dense G costs 2n^3 flops; a circulant G is applied by FFT in
  * O(n^2 log n) (Thm. 2.1) when n is a power of two <= 8192; the sparse G is
  * a signed gather of nnz columns per output column. */
@@ -414,6 +428,34 @@ GENP_API genp_status genp_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha
                                     const void *Bt, int64_t ldb, float beta, const float *Cin, int64_t ldci,
                                     float *D, int64_t ldd, void *cuda_stream);
 
+/* E4M3 operands with one power-of-two scale per 128 x 128 tile (the
+ * operands of GENP_FP8_E4M3).  For the logical operand X (m x K):
+ *   X = src (m x K, ld lds) when trans == 0, X = src^T (src K x m) otherwise.
+ * Tile (ti, kt) covers rows 128 ti .. and columns 128 kt ..; its scale is
+ * 2^e with e the least integer such that max |X_tile| <= 448 2^e (448: the
+ * largest finite e4m3 value), clamped to [-126, 126]; e = 0 for a zero tile.
+ *   dst[i ldq + k]               = e4m3 code of X[i][k] 2^-e, rounded to
+ *                                  nearest, ties to even (the scaling is exact)
+ *   scales[ti ceil(K/128) + kt]  = 2^e (float)
+ * src device FP64 or FP32 (src_prec); dst device bytes, ldq >= K, a multiple
+ * of 16, base 16-byte aligned; entries k >= K of a row are not written.
+ * Errors: GENP_ERR_ARG, GENP_ERR_CUDA. */
+GENP_API genp_status genp_quantize_e4m3(const void *src, int64_t lds, genp_prec src_prec, int64_t m, int64_t K,
+                                        int trans, uint8_t *dst, int64_t ldq, float *scales, void *cuda_stream);
+
+/* Tensor-core product of tile-scaled e4m3 operands (tcgen05 kind::f8f6f4,
+ * FP32 accumulation per 128-wide k-tile, promoted into FP32 with the tile
+ * pair's scale):
+ *   D = alpha * sum_kt scale_a[tm][kt] scale_b[tn][kt] A_kt Bt_kt^T + beta * Cin
+ *  A   m x K codes, ld lda; scale_a ceil(m/128) x ceil(K/128) floats.
+ *  Bt  n x K codes (B transposed), ld ldb; scale_b ceil(n/128) x ceil(K/128).
+ *  lda, ldb multiples of 16, bases 16-byte aligned; Cin, D as genp_gemm_bf16.
+ * Errors: GENP_ERR_ARG, GENP_ERR_CUDA. */
+GENP_API genp_status genp_gemm_e4m3(int64_t m, int64_t n, int64_t K, float alpha, const uint8_t *A, int64_t lda,
+                                    const float *scale_a, const uint8_t *Bt, int64_t ldb, const float *scale_b,
+                                    float beta, const float *Cin, int64_t ldci, float *D, int64_t ldd,
+                                    void *cuda_stream);
+
 /* Randomized low-rank approximation (Sec. 5, Proto-Alg. 5.1, with an
  * orthonormal T as in the tests of Sec. 7.2):
  *   Stage 1  B = A^T G with an m x r sketch G: GENP_MULT_GAUSSIAN (iid
@@ -502,14 +544,19 @@ GENP_API int genp_sliced_digits(int digits);
  * concurrent calls. */
 GENP_API int genp_sliced_precondition_digits(int digits);
 
-/* Measurement hook: while enabled, every launch of the sliced tensor-core
- * kernel is bracketed by two CUDA events on its stream.  genp_profile_read
- * synchronizes on them and returns the summed kernel time (ms), the digit
- * products' BF16 flops (2 m n Kpad x digit pairs per launch) and the launch
- * count since the last read or enable, then restarts the count.  Enabling
- * costs two event records per launch; it is off by default. */
+/* Measurement hook: while enabled, every launch of the sliced and the e4m3
+ * tensor-core kernels is bracketed by two CUDA events on its stream.
+ * genp_profile_read synchronizes on them and returns the summed kernel time
+ * (ms), the flops (sliced: the digit products' BF16 flops, 2 m n Kpad x
+ * digit pairs per launch; e4m3: 2 m n K) and the launch count since the last
+ * read or enable, then restarts the count.  genp_profile_launches returns
+ * the same launches one by one, in launch order (the first min(cap, count)
+ * into ms[] and flops[], either may be NULL), and the count, without
+ * restarting it.  Enabling costs two event records per launch; it is off by
+ * default. */
 GENP_API genp_status genp_profile_enable(int on);
 GENP_API genp_status genp_profile_read(double *ms, double *flops, int *launches);
+GENP_API genp_status genp_profile_launches(double *ms, double *flops, int cap, int *launches);
 
 /* Synchronizes the device and reports whether any kernel of this library
  * that waits on the device (the tensor-core pipelines, the persistent

@@ -44,6 +44,9 @@ SIGNATURES = {
     "genp_make_sparse_noalloc": (_int, [_i64, _int, _u64, _u64, _vp, _vp, _vp, _vp, _vp]),
     "genp_gemm_bf16": (_int, [_i64, _i64, _i64, ctypes.c_float, _vp, _i64, _vp, _i64, ctypes.c_float, _vp, _i64,
                               _vp, _i64, _vp]),
+    "genp_quantize_e4m3": (_int, [_vp, _i64, _int, _i64, _i64, _int, _vp, _i64, _vp, _vp]),
+    "genp_gemm_e4m3": (_int, [_i64, _i64, _i64, ctypes.c_float, _vp, _i64, _vp, _vp, _i64, _vp, ctypes.c_float, _vp,
+                              _i64, _vp, _i64, _vp]),
     "genp_gemm_sliced": (_int, [_i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl, _vp, _i64, _int, _vp]),
     "genp_numerical_rank": (_int, [_i64, _i64, _vp, _i64, _i64, _i64, _dbl, _u64, _u64, _vp, _vp, _i64, _vp]),
     "genp_lowrank": (_int, [_i64, _i64, _vp, _i64, _i64, _int, _u64, _u64, _vp, _i64, _vp, _i64, _vp, _i64, _vp, _i64,
@@ -52,6 +55,7 @@ SIGNATURES = {
     "genp_sliced_precondition_digits": (_int, [_int]),
     "genp_profile_enable": (_int, [_int]),
     "genp_profile_read": (_int, [_vp, _vp, _vp]),
+    "genp_profile_launches": (_int, [_vp, _vp, _int, _vp]),
     "genp_device_check": (_int, [_int]),
     "genp_batched_plan_create": (_int, [_i64, _vp, _i64, _int, _int, _int, _dbl, _int, _vp, ctypes.POINTER(_vp)]),
     "genp_batched_layout": (_int, [_vp, _vp, _vp]),

@@ -184,7 +184,7 @@ def solve_system(A: torch.Tensor, B: torch.Tensor, kind: int = GAUSSIAN, seed: i
     f64 = prec in (FP64, BF16_SLICED)
     # FP32-grid draws for every non-FP64 factorization (the sliced path reads
     # them as exact FP64 values)
-    grid = FP64 if prec == FP64 else (BF16 if prec in (BF16, BF16X3) else FP32)
+    grid = FP64 if prec == FP64 else (BF16 if prec in (BF16, BF16X3) else (FP8_E4M3 if prec == FP8_E4M3 else FP32))
     G = make_multiplier(kind, n, seed, value_grid=grid, stream=stream, side=side)
     C = torch.empty((n, n), dtype=torch.float64 if f64 else torch.float32, device=A.device)
     A64 = A if A.dtype == torch.float64 else A.double()

@@ -85,9 +85,11 @@ cudaError_t draw_multiplier(genp_multiplier *G, uint64_t seed, uint64_t stream_i
 }
 
 bool factor_prec_ok(genp_prec p) {
-    return p == GENP_FP64 || p == GENP_FP32 || p == GENP_BF16 || p == GENP_BF16X3 || p == GENP_BF16_SLICED;
+    return p == GENP_FP64 || p == GENP_FP32 || p == GENP_BF16 || p == GENP_BF16X3 || p == GENP_BF16_SLICED ||
+           p == GENP_FP8_E4M3;
 }
-bool tc_prec(genp_prec p) { return p == GENP_BF16 || p == GENP_BF16X3; }
+// FP32 master copy, Schur products on the tensor cores (BF16 or e4m3 operands)
+bool tc_prec(genp_prec p) { return p == GENP_BF16 || p == GENP_BF16X3 || p == GENP_FP8_E4M3; }
 
 // Grows the factors workspace to at least `bytes` (synchronizes the stream
 // only when it actually has to grow).
@@ -232,7 +234,9 @@ genp_status genp_make_multiplier(genp_mult_kind kind, int64_t n, uint64_t seed, 
     }
     if (kind != GENP_MULT_SPARSE_PM1 && !(scale > 0.0 && isfinite(scale))) return GENP_ERR_ARG;
     if (kind == GENP_MULT_SPARSE_PM1 && (nnz_per_col < 1 || nnz_per_col > 16)) return GENP_ERR_ARG;
-    if (value_grid != GENP_FP64 && value_grid != GENP_FP32 && value_grid != GENP_BF16) return GENP_ERR_ARG;
+    if (value_grid != GENP_FP64 && value_grid != GENP_FP32 && value_grid != GENP_BF16 &&
+        value_grid != GENP_FP8_E4M3)
+        return GENP_ERR_ARG;
     cudaStream_t s = S(cuda_stream);
     genp_multiplier *G = new (std::nothrow) genp_multiplier();
     if (!G) return GENP_ERR_NOMEM;
@@ -315,8 +319,43 @@ genp_status genp_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha, const v
     return GENP_OK;
 }
 
+genp_status genp_quantize_e4m3(const void *src, int64_t lds, genp_prec src_prec, int64_t m, int64_t K, int trans,
+                               uint8_t *dst, int64_t ldq, float *scales, void *cuda_stream) {
+    if (!src || !dst || !scales || m < 0 || K < 0) return GENP_ERR_ARG;
+    if (src_prec != GENP_FP64 && src_prec != GENP_FP32) return GENP_ERR_ARG;
+    if (m == 0 || K == 0) return GENP_OK;
+    if (lds < (trans ? m : K) || ldq < K || (ldq % 16) || ((uintptr_t)dst % 16)) return GENP_ERR_ARG;
+    if (m > INT32_MAX || K > INT32_MAX || cdiv(m, 128) > 65535) return GENP_ERR_ARG;
+    cudaStream_t s = S(cuda_stream);
+    if (src_prec == GENP_FP64)
+        CU(quant_e4m3<double>(static_cast<const double *>(src), lds, m, K, trans != 0, dst, ldq, scales, s));
+    else
+        CU(quant_e4m3<float>(static_cast<const float *>(src), lds, m, K, trans != 0, dst, ldq, scales, s));
+    return GENP_OK;
+}
+
+genp_status genp_gemm_e4m3(int64_t m, int64_t n, int64_t K, float alpha, const uint8_t *A, int64_t lda,
+                           const float *scale_a, const uint8_t *Bt, int64_t ldb, const float *scale_b, float beta,
+                           const float *Cin, int64_t ldci, float *D, int64_t ldd, void *cuda_stream) {
+    if (m < 0 || n < 0 || K < 1 || !A || !Bt || !D || !scale_a || !scale_b) return GENP_ERR_ARG;
+    if (lda < K || ldb < K || ldd < n || (lda % 16) || (ldb % 16)) return GENP_ERR_ARG;
+    if (((uintptr_t)A % 16) || ((uintptr_t)Bt % 16)) return GENP_ERR_ARG;
+    if (beta != 0.0f && (!Cin || ldci < n)) return GENP_ERR_ARG;
+    if (m > INT32_MAX || n > INT32_MAX || K > INT32_MAX || cdiv(m, 128) > 65535) return GENP_ERR_ARG;
+    CU(tc_gemm_e4m3(m, n, K, alpha, A, lda, scale_a, Bt, ldb, scale_b, beta, Cin, ldci, D, ldd, S(cuda_stream)));
+    return GENP_OK;
+}
+
 genp_status genp_profile_enable(int on) {
     tc_profile_enable(on != 0);
+    return GENP_OK;
+}
+
+genp_status genp_profile_launches(double *ms, double *flops, int cap, int *launches) {
+    if (!launches || cap < 0 || (cap > 0 && !ms && !flops)) return GENP_ERR_ARG;
+    const int c = tc_profile_launches(ms, flops, cap);
+    if (c < 0) return GENP_ERR_CUDA;
+    *launches = c;
     return GENP_OK;
 }
 
@@ -482,7 +521,6 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
     const int64_t n = G->n;
     if (lda < n || ldc < n) return GENP_ERR_ARG;
     if (a_prec != GENP_FP64 && a_prec != GENP_FP32) return GENP_ERR_ARG;
-    if (c_prec == GENP_FP8_E4M3) return GENP_ERR_UNSUPPORTED;
     if (!factor_prec_ok(c_prec)) return GENP_ERR_ARG;
     if (f64_factors(c_prec) && a_prec != GENP_FP64) return GENP_ERR_ARG;
     cudaStream_t s = S(cuda_stream);
@@ -548,7 +586,26 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
         return GENP_OK;
     }
     if (c_prec == GENP_BF16_SLICED) c_prec = GENP_FP64;   // circulant / sparse products: FP64 FFT / gather
-    if (tc_prec(c_prec) && G->kind == GENP_MULT_GAUSSIAN) {
+    if (c_prec == GENP_FP8_E4M3 && G->kind == GENP_MULT_GAUSSIAN) {
+        // Tensor cores, e4m3: C = A_q G with A_q the tile-scaled e4m3 codes of
+        // A; G is on the FP8 grid, so its tile-scaled codes are exact.
+        if (G->grid != GENP_FP8_E4M3) return GENP_ERR_ARG;
+        const int64_t ldq = (n + 15) / 16 * 16, tiles = e4m3_tiles(n, n);
+        char *buf = nullptr;
+        const size_t qbytes = align256((size_t)n * ldq);
+        CU(cudaMallocAsync((void **)&buf, 2 * qbytes + 2 * (size_t)tiles * sizeof(float), s));
+        uint8_t *Aq = reinterpret_cast<uint8_t *>(buf), *Gq = Aq + qbytes;
+        float *sA = reinterpret_cast<float *>(Gq + qbytes), *sG = sA + tiles;
+        if (a_prec == GENP_FP64)
+            CU(quant_e4m3<double>(static_cast<const double *>(A), lda, n, n, false, Aq, ldq, sA, s));
+        else
+            CU(quant_e4m3<float>(static_cast<const float *>(A), lda, n, n, false, Aq, ldq, sA, s));
+        CU(quant_e4m3<double>(G->dense, n, n, n, true, Gq, ldq, sG, s));   // rows of G^T
+        CU(tc_gemm_e4m3(n, n, n, 1.0f, Aq, ldq, sA, Gq, ldq, sG, 0.0f, nullptr, 0, static_cast<float *>(C), ldc, s));
+        CU(cudaFreeAsync(buf, s));
+        return GENP_OK;
+    }
+    if (tc_prec(c_prec) && c_prec != GENP_FP8_E4M3 && G->kind == GENP_MULT_GAUSSIAN) {
         // Tensor cores: C = sum_t a_t G over the BF16 terms a_t of A (one term
         // for BF16, three for BF16X3); G is exact on the BF16 grid.
         if (!G->dense_bf16) return GENP_ERR_ARG;
@@ -627,7 +684,6 @@ genp_status genp_factor(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t
     if (!out) return GENP_ERR_ARG;
     *out = nullptr;
     if (!C || n < 1 || n > 2147483647LL || ldc < n) return GENP_ERR_ARG;
-    if (prec == GENP_FP8_E4M3) return GENP_ERR_UNSUPPORTED;
     if (!factor_prec_ok(prec)) return GENP_ERR_ARG;
     if (nb == 0) nb = (tc_prec(prec) || prec == GENP_BF16_SLICED) ? 128 : 64;
     if (nb < 1 || nb > 128) return GENP_ERR_ARG;
@@ -651,6 +707,7 @@ genp_status genp_factor(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t
         F->tc_ldq = round8(nb * split_terms(prec));
         st = dalloc(&F->tcA, (size_t)n * F->tc_ldq);
         if (st == GENP_OK) st = dalloc(&F->tcB, (size_t)n * F->tc_ldq);
+        if (st == GENP_OK && prec == GENP_FP8_E4M3) st = dalloc(&F->qscale, (size_t)2 * cdiv(n, 128));
     }
     if (st == GENP_OK && prec == GENP_BF16_SLICED) {
         F->nd = sliced_digits();
@@ -695,6 +752,7 @@ void genp_factors_destroy(genp_factors *F) {
     cudaFree(F->work);
     cudaFree(F->tcA);
     cudaFree(F->tcB);
+    cudaFree(F->qscale);
     cudaFree(F->W);
     cudaFree(F->exps);
     cudaFree(F->trsv_sync);

@@ -1,4 +1,5 @@
-// gemm_tc.cu -- BF16 tensor-core GEMM on sm_103a (tcgen05 + TMA + TMEM):
+// gemm_tc.cu -- tensor-core GEMMs on sm_103a (tcgen05 + TMA + TMEM).  First
+// the BF16 one:
 //   D (fp32, row-major) = alpha * A * B^T + beta * Cin
 // with A (m x K) and B (n x K) BF16, both K-major (row-major with K
 // contiguous), FP32 accumulation in tensor memory.  It serves the mixed
@@ -130,9 +131,33 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(unsigned long long *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(b)) : "memory");
+}
+// barrier among the 128 epilogue threads only
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Instruction descriptor, kind::f8f6f4: D F32, A and B E4M3 (format 0), both K-major, M x N.
+constexpr uint32_t kIdescE4M3 = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_e4m3(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(kIdescE4M3), "r"(acc)
+        : "memory");
+}
+
+// Q8: e4m3 operands (kind::f8f6f4, 128 per 128-byte k-tile row, K = 32 per
+// MMA) with K <= 128, so that one scale product scA[tm] scB[tn] covers the
+// whole tile and joins alpha in the epilogue (the Schur updates of
+// GENP_FP8_E4M3: K = nb).
+template <bool Q8>
 __global__ void __launch_bounds__(128, 2)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m, int n, int K,
-          float alpha, float beta, const float *Cin, int64_t ldci, float *D, int64_t ldd, int vec, const int *skip) {
+          float alpha, float beta, const float *Cin, int64_t ldci, float *D, int64_t ldd, int vec, const int *skip,
+          const float *scA, const float *scB) {
     if (skip && *skip) return;
     extern __shared__ unsigned char smraw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
@@ -142,7 +167,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     volatile int *abort = &ctl->abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    const int nk = (K + BK - 1) / BK;
+    constexpr int kStep = Q8 ? 2 * BK : BK;   // elements per 128-byte k-tile row
+    const int nk = (K + kStep - 1) / kStep;
+    if (Q8) alpha *= scA[blockIdx.y] * scB[blockIdx.x];
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -164,6 +191,13 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     __syncthreads();
     fence_after();
     const uint32_t tmem = ctl->tmem;
+    // the tile's rows of Cin into L2 while the main loop runs (the epilogue's
+    // read-modify-write of C is most of a short-K product's traffic)
+    if (beta != 0.0f && m0 + (int)threadIdx.x < m && n0 < n) {
+        const char *rp = reinterpret_cast<const char *>(Cin + (int64_t)(m0 + threadIdx.x) * ldci + n0);
+        const int bytes = (n - n0 < BN ? n - n0 : BN) * (int)sizeof(float);
+        for (int b = 0; b < bytes; b += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(rp + b));
+    }
 
     if (warp == 0 && lane == 0) {
         // producer
@@ -175,8 +209,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 break;
             }
             mbar_expect_tx(&ctl->full[s], A_BYTES + B_BYTES);
-            tma_2d(sA + s * A_BYTES, &tmA, &ctl->full[s], kt * BK, m0);
-            tma_2d(sB + s * B_BYTES, &tmB, &ctl->full[s], kt * BK, n0);
+            tma_2d(sA + s * A_BYTES, &tmA, &ctl->full[s], kt * kStep, m0);
+            tma_2d(sB + s * B_BYTES, &tmB, &ctl->full[s], kt * kStep, n0);
             ctl->issued = kt + 1;
         }
     } else if (warp == 1 && lane == 0) {
@@ -193,8 +227,12 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             fence_after();
             const uint64_t ad = sdesc(sa(sA + s * A_BYTES)), bd = sdesc(sa(sB + s * B_BYTES));
 #pragma unroll
-            for (int k = 0; k < BK / UMMA_K; ++k)  // +32 bytes along K inside the swizzle atom
-                mma(tmem, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), (kt > 0 || k > 0) ? 1u : 0u);
+            for (int k = 0; k < BK / UMMA_K; ++k) {  // +32 bytes along K inside the swizzle atom
+                if (Q8)
+                    mma_e4m3(tmem, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), (kt > 0 || k > 0) ? 1u : 0u);
+                else
+                    mma(tmem, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), (kt > 0 || k > 0) ? 1u : 0u);
+            }
             commit(&ctl->empty[s]);
         }
         if (ok) commit(&ctl->accum);
@@ -299,6 +337,232 @@ bool make_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t K, int64_
 }
 
 // ---------------------------------------------------------------------------
+// E4M3 product with a power-of-two scale per 128 x 128 operand tile:
+//   D = alpha * sum_kt scA[tm][kt] scB[tn][kt] (A_kt B_kt^T) + beta * Cin
+// A (m x K) and B^T (n x K) hold e4m3 codes, K-major; tile (tm, kt) of A is
+// rows 128 tm .. and columns 128 kt .., its scale scA[tm * nkt + kt]
+// (nkt = ceil(K / 128)); likewise scB for B^T.  Each k-tile (128 e4m3 = one
+// 128-byte swizzle row) is one tcgen05 kind::f8f6f4 accumulation of four
+// K = 32 MMAs into one of two TMEM accumulators; the epilogue warps read it
+// and add it, times the tile pair's scale, into FP32 registers while the
+// MMAs of the next k-tile fill the other accumulator.
+//   warps 0-7: promotion and the final write (warp w: TMEM lanes 32 (w % 4)
+//              .. = its rows, columns 64 (w / 4) .. = its half; two warps per
+//              scheduler keep the promotion ahead of the MMAs);
+//   warp 8, one lane: TMA producer, six stages of A and B tiles (192 KiB:
+//              the loads in flight cover the latency at 32 KiB per k-tile);
+//   warp 9, one lane: MMA issue.
+// One CTA per SM; every wait is bounded.
+// ---------------------------------------------------------------------------
+constexpr int QBK = 128, Q_STAGES = 6, kQEpiWarps = 8, kQThreads = 32 * (kQEpiWarps + 2);
+constexpr int kQProducer = kQEpiWarps, kQMma = kQEpiWarps + 1;   // warp indices
+constexpr uint32_t QA_BYTES = BM * QBK, QB_BYTES = BN * QBK;
+constexpr uint32_t Q_TMEM = 256;
+// barrier among the epilogue warps only
+__device__ __forceinline__ void epi_sync_q() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kQEpiWarps) : "memory"); }
+struct QCtl {
+    unsigned long long full[Q_STAGES];
+    unsigned long long empty[Q_STAGES];
+    unsigned long long afull[2];     // accumulator b holds a finished k-tile
+    unsigned long long aempty[2];    // the epilogue has read accumulator b (4 arrivals)
+    unsigned long long drain;
+    uint32_t tmem;
+    int abort;
+    int issued;
+};
+constexpr size_t kQSmem = 1024 + Q_STAGES * (QA_BYTES + QB_BYTES) + sizeof(QCtl);
+static_assert(kQSmem <= 227 * 1024, "shared memory");
+static_assert(BM * kTileLd * 4 <= Q_STAGES * (QA_BYTES + QB_BYTES), "output tile fits in the stage buffers");
+
+__global__ void __launch_bounds__(kQThreads, 1)
+k_tc_e4m3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m, int n, int K,
+          float alpha, const float *scA, const float *scB, float beta, const float *Cin, int64_t ldci, float *D,
+          int64_t ldd, int vec) {
+    extern __shared__ unsigned char smraw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = base;
+    unsigned char *sB = base + Q_STAGES * QA_BYTES;
+    QCtl *ctl = (QCtl *)(sB + Q_STAGES * QB_BYTES);
+    volatile int *abort = &ctl->abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tm = blockIdx.y, tn = blockIdx.x;
+    const int m0 = tm * BM, n0 = tn * BN;
+    const int nkt = (K + QBK - 1) / QBK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < Q_STAGES; ++s) {
+            mbar_init(&ctl->full[s], 1);
+            mbar_init(&ctl->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&ctl->afull[b], 1);
+            mbar_init(&ctl->aempty[b], kQEpiWarps);
+        }
+        mbar_init(&ctl->drain, 1);
+        ctl->abort = 0;
+        ctl->issued = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kQMma) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa(&ctl->tmem)),
+                     "r"(Q_TMEM)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = ctl->tmem;
+
+    if (warp == kQProducer) {
+        if (lane == 0) {
+            for (int kt = 0; kt < nkt; ++kt) {
+                const int s = kt % Q_STAGES;
+                if (kt >= Q_STAGES && !mbar_wait(&ctl->empty[s], (uint32_t)((kt / Q_STAGES) & 1) ^ 1u, abort)) {
+                    *abort = 1;
+                    break;
+                }
+                mbar_expect_tx(&ctl->full[s], QA_BYTES + QB_BYTES);
+                tma_2d(sA + s * QA_BYTES, &tmA, &ctl->full[s], kt * QBK, m0);
+                tma_2d(sB + s * QB_BYTES, &tmB, &ctl->full[s], kt * QBK, n0);
+                ctl->issued = kt + 1;
+            }
+        }
+        __syncwarp();
+    } else if (warp == kQMma) {
+        if (lane == 0) {
+            for (int kt = 0; kt < nkt; ++kt) {
+                const int s = kt % Q_STAGES, b = kt & 1;
+                if (!mbar_wait(&ctl->full[s], (uint32_t)((kt / Q_STAGES) & 1), abort)) {
+                    *abort = 1;
+                    break;
+                }
+                // accumulator b was last filled by k-tile kt - 2
+                if (kt >= 2 && !mbar_wait(&ctl->aempty[b], (uint32_t)(((kt - 2) >> 1) & 1), abort)) {
+                    *abort = 1;
+                    break;
+                }
+                fence_after();
+                const uint64_t ad = sdesc(sa(sA + s * QA_BYTES)), bd = sdesc(sa(sB + s * QB_BYTES));
+#pragma unroll
+                for (int k = 0; k < QBK / 32; ++k)   // K = 32 e4m3 (32 bytes) per MMA
+                    mma_e4m3(tmem + (uint32_t)(b * BN), ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2),
+                             k > 0 ? 1u : 0u);
+                commit(&ctl->empty[s]);
+                commit(&ctl->afull[b]);
+            }
+        }
+        __syncwarp();
+    } else {
+        // promotion: acc += scA scB P_kt.  Epilogue warp w reads TMEM lanes
+        // 32 (w % 4) .. (its rows) and columns 64 (w / 4) .. (its half).
+        constexpr int HALF = BN / 2;
+        const int row = (warp & 3) * 32 + lane, h = warp >> 2;
+        const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(h * HALF);
+        float acc[HALF];
+#pragma unroll
+        for (int j = 0; j < HALF; ++j) acc[j] = 0.0f;
+        bool ok = true;
+        const float *sa_row = scA + (int64_t)tm * nkt, *sb_row = scB + (int64_t)tn * nkt;
+        float sc_next = sa_row[0] * sb_row[0];
+        for (int kt = 0; kt < nkt; ++kt) {
+            const int b = kt & 1;
+            const float sc = sc_next;          // this k-tile's scale; the next one's loads go out now
+            if (kt + 1 < nkt) sc_next = sa_row[kt + 1] * sb_row[kt + 1];
+            if (!mbar_wait(&ctl->afull[b], (uint32_t)((kt >> 1) & 1), abort)) {
+                *abort = 1;
+                ok = false;
+                break;
+            }
+            fence_after();
+#pragma unroll
+            for (int c = 0; c < HALF / 32; ++c) {
+                uint32_t q[32];
+                tmem_ld32(lane_addr + (uint32_t)(b * BN + c * 32), q);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[c * 32 + j] = fmaf(sc, __uint_as_float(q[j]), acc[c * 32 + j]);
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->aempty[b]);
+        }
+        // every k-tile is consumed, so the stage buffers are free: rows through
+        // shared memory, then coalesced rows of D
+        epi_sync_q();
+        ok = ok && !*abort;
+        float *tile = reinterpret_cast<float *>(base);   // BM x kTileLd
+        if (ok) {
+            float4 *trow = reinterpret_cast<float4 *>(tile + row * kTileLd + h * HALF);
+#pragma unroll
+            for (int q = 0; q < HALF / 4; ++q)
+                trow[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        }
+        epi_sync_q();
+        if (ok) {
+            const int col = n0 + lane * 4;
+            for (int rr = warp; rr < BM; rr += kQEpiWarps) {
+                const int row = m0 + rr;
+                if (row >= m) break;
+                const float4 a = *reinterpret_cast<const float4 *>(tile + rr * kTileLd + lane * 4);
+                float *drow = D + (int64_t)row * ldd;
+                if (vec && col + 3 < n) {
+                    float4 v = make_float4(alpha * a.x, alpha * a.y, alpha * a.z, alpha * a.w);
+                    if (beta != 0.0f) {
+                        const float4 cv = *reinterpret_cast<const float4 *>(Cin + (int64_t)row * ldci + col);
+                        v.x = fmaf(beta, cv.x, v.x);
+                        v.y = fmaf(beta, cv.y, v.y);
+                        v.z = fmaf(beta, cv.z, v.z);
+                        v.w = fmaf(beta, cv.w, v.w);
+                    }
+                    *reinterpret_cast<float4 *>(drow + col) = v;
+                } else {
+                    const float av[4] = {a.x, a.y, a.z, a.w};
+                    for (int e = 0; e < 4; ++e) {
+                        if (col + e >= n) break;
+                        float v = alpha * av[e];
+                        if (beta != 0.0f) v = fmaf(beta, Cin[(int64_t)row * ldci + col + e], v);
+                        drow[col + e] = v;
+                    }
+                }
+            }
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    if (ctl->abort) {
+        if (threadIdx.x == 32 * kQProducer) {
+            atomicExch(&g_tc_timeout, 1);
+            int dummy = 0;
+            const int issued = ctl->issued;
+            for (int kt = (issued > Q_STAGES ? issued - Q_STAGES : 0); kt < issued; ++kt)
+                mbar_wait(&ctl->full[kt % Q_STAGES], (uint32_t)((kt / Q_STAGES) & 1), (volatile int *)&dummy);
+        }
+        if (threadIdx.x == 32 * kQMma) {     // the MMA thread: wait for its MMAs still in flight
+            int dummy = 0;
+            commit(&ctl->drain);
+            mbar_wait(&ctl->drain, 0, (volatile int *)&dummy);
+        }
+        __syncthreads();
+    }
+    if (warp == kQMma)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Q_TMEM) : "memory");
+}
+
+// 2-D map of a rows x K matrix of bytes (e4m3 codes), box 128 x 128, 128B swizzle.
+bool make_map_u8(CUtensorMap *map, const void *ptr, int64_t rows, int64_t K, int64_t ld) {
+    auto fn = encoder();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld};
+    cuuint32_t box[2] = {(cuuint32_t)QBK, (cuuint32_t)BM};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------
 // Sliced (FP64-class) product (layout in sliced.cuh).  Digit group g = t + u
 // accumulates in TMEM columns [64 (g-2), 64 (g-1)), so one MMA of A's digit t
 // against B's digits 1 .. ND+1-t laid side by side along N (N = 64 (ND+1-t),
@@ -361,11 +625,6 @@ __device__ bool mbar_wait_sleep(unsigned long long *b, uint32_t parity, volatile
     }
     return true;
 }
-__device__ __forceinline__ void mbar_arrive(unsigned long long *b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(b)) : "memory");
-}
-// barrier among the 128 epilogue threads only
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 template <int ND>
 struct SlicedCfg {
@@ -620,6 +879,7 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 struct TcProfile {
     bool on = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    std::vector<double> fl;       // flops of each recorded launch
     size_t used = 0;
     double flops = 0.0;
 };
@@ -627,7 +887,8 @@ TcProfile &tc_profile() {
     static TcProfile p;
     return p;
 }
-std::pair<cudaEvent_t, cudaEvent_t> *profile_slot() {
+// Events around one launch of `flops` flops, or nullptr when profiling is off.
+std::pair<cudaEvent_t, cudaEvent_t> *profile_slot(double flops) {
     TcProfile &p = tc_profile();
     if (!p.on) return nullptr;
     if (p.used == p.ev.size()) {
@@ -638,7 +899,10 @@ std::pair<cudaEvent_t, cudaEvent_t> *profile_slot() {
             return nullptr;
         }
         p.ev.emplace_back(a, b);
+        p.fl.push_back(0.0);
     }
+    p.fl[p.used] = flops;
+    p.flops += flops;
     return &p.ev[p.used++];
 }
 
@@ -662,11 +926,8 @@ cudaError_t launch_sliced(const CUtensorMap &ma, const CUtensorMap &mb, int64_t 
     const int64_t tiles = cdiv(m, BM) * cdiv(n, SBN);
     if (tiles > INT32_MAX) return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
-    auto *ev = profile_slot();
-    if (ev) {
-        cudaEventRecord(ev->first, s);
-        tc_profile().flops += 2.0 * (double)m * (double)n * (double)kpad * (ND * (ND + 1) / 2);
-    }
+    auto *ev = profile_slot(2.0 * (double)m * (double)n * (double)kpad * (ND * (ND + 1) / 2));
+    if (ev) cudaEventRecord(ev->first, s);
     note_launch();
     k_tc_sliced<ND><<<grid, kSlicedThreads, SlicedCfg<ND>::kSmem, s>>>(ma, mb, (int)m, (int)n, (int)kpad, alpha, ea,
                                                                         fb, D, ldd);
@@ -707,7 +968,8 @@ cudaError_t tc_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha, const __n
     if (!make_map(&ma, A, m, K, lda, BM) || !make_map(&mb, Bt, n, K, ldb, BN)) return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -716,7 +978,42 @@ cudaError_t tc_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha, const __n
     const int vec = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0) &&
                     (beta == 0.0f || ((uintptr_t)Cin % 16 == 0 && ldci % 4 == 0));
     note_launch();
-    k_tc_gemm<<<grid, 128, kSmem, s>>>(ma, mb, (int)m, (int)n, (int)K, alpha, beta, Cin, ldci, D, ldd, vec, skip);
+    k_tc_gemm<false><<<grid, 128, kSmem, s>>>(ma, mb, (int)m, (int)n, (int)K, alpha, beta, Cin, ldci, D, ldd, vec,
+                                              skip, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_gemm_e4m3(int64_t m, int64_t n, int64_t K, float alpha, const uint8_t *A, int64_t lda, const float *sa,
+                         const uint8_t *Bt, int64_t ldb, const float *sb, float beta, const float *Cin, int64_t ldci,
+                         float *D, int64_t ldd, cudaStream_t s) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    if (K <= 0 || m > INT32_MAX || n > INT32_MAX || K > INT32_MAX) return cudaErrorInvalidValue;
+    // TMA: 16-byte aligned bases and row strides
+    if ((lda % 16) || (ldb % 16) || ((uintptr_t)A % 16) || ((uintptr_t)Bt % 16)) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_map_u8(&ma, A, m, K, lda) || !make_map_u8(&mb, Bt, n, K, ldb)) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_e4m3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((unsigned)cdiv(n, BN), (unsigned)cdiv(m, BM));
+    if (grid.y > 65535u) return cudaErrorInvalidValue;
+    const int vec = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0) &&
+                    (beta == 0.0f || ((uintptr_t)Cin % 16 == 0 && ldci % 4 == 0));
+    auto *ev = profile_slot(2.0 * (double)m * (double)n * (double)K);
+    if (ev) cudaEventRecord(ev->first, s);
+    note_launch();
+    if (K <= QBK)   // one k-tile: the scale product joins alpha, two CTAs per SM
+        k_tc_gemm<true><<<grid, 128, kSmem, s>>>(ma, mb, (int)m, (int)n, (int)K, alpha, beta, Cin, ldci, D, ldd, vec,
+                                                 nullptr, sa, sb);
+    else
+        k_tc_e4m3<<<grid, kQThreads, kQSmem, s>>>(ma, mb, (int)m, (int)n, (int)K, alpha, sa, sb, beta, Cin, ldci, D,
+                                                  ldd, vec);
+    if (ev) cudaEventRecord(ev->second, s);
     return cudaGetLastError();
 }
 
@@ -725,6 +1022,19 @@ void tc_profile_enable(bool on) {
     p.on = on;
     p.used = 0;
     p.flops = 0.0;
+}
+
+int tc_profile_launches(double *ms, double *flops, int cap) {
+    TcProfile &p = tc_profile();
+    const int count = (int)p.used;
+    for (int i = 0; i < count && i < cap; ++i) {
+        if (cudaEventSynchronize(p.ev[i].second) != cudaSuccess) return -1;
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, p.ev[i].first, p.ev[i].second) != cudaSuccess) return -1;
+        if (ms) ms[i] = t;
+        if (flops) flops[i] = p.fl[i];
+    }
+    return count;
 }
 
 int tc_profile_read(double *ms, double *flops) {

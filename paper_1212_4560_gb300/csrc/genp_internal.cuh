@@ -88,6 +88,7 @@ struct genp_factors {
     __nv_bfloat16 *tcA = nullptr;      // BF16 split L21 panel, n x tc_ldq (BF16 / BF16X3)
     __nv_bfloat16 *tcB = nullptr;      // BF16 split U12^T panel, n x tc_ldq
     int64_t tc_ldq = 0;
+    float *qscale = nullptr;           // e4m3 tile scales of L21 and U12^T, 2 ceil(n / 128) (FP8_E4M3)
     void *W = nullptr;                 // double-float trailing matrix, n x ldw (GENP_BF16_SLICED)
     int64_t ldw = 0;
     int *exps = nullptr;               // 2n slicing exponents (GENP_BF16_SLICED)
@@ -210,11 +211,24 @@ cudaError_t sparse_apply(const genp_multiplier *G, bool trans, const double *Y, 
 cudaError_t tc_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha, const __nv_bfloat16 *A, int64_t lda,
                          const __nv_bfloat16 *Bt, int64_t ldb, float beta, const float *Cin, int64_t ldci, float *D,
                          int64_t ldd, const int *skip, cudaStream_t s);
+// gemm_tc.cu: D = alpha * sum_kt scA[tm][kt] scB[tn][kt] A_kt Bt_kt^T + beta * Cin on
+// the tensor cores, A (m x K) and Bt (n x K) e4m3 codes with one scale per
+// 128 x 128 tile (nkt = ceil(K / 128) per tile row), FP32 out.
+cudaError_t tc_gemm_e4m3(int64_t m, int64_t n, int64_t K, float alpha, const uint8_t *A, int64_t lda, const float *scA,
+                         const uint8_t *Bt, int64_t ldb, const float *scB, float beta, const float *Cin, int64_t ldci,
+                         float *D, int64_t ldd, cudaStream_t s);
+// mixed.cu: e4m3 codes of X (m x K; X = src, or src^T when trans, src then
+// K x m) with a power-of-two scale per 128 x 128 tile, scales[ti nkt + kt].
+template <typename T>
+cudaError_t quant_e4m3(const T *src, int64_t lds, int64_t m, int64_t K, bool trans, uint8_t *dst, int64_t ldq,
+                       float *scales, cudaStream_t s);
+int64_t e4m3_tiles(int64_t rows, int64_t K);
 // Reads the device-side timeout flag of the tensor-core kernels (synchronizes).
 int tc_timeout_flag(bool reset);
 // CUDA-event timing of the sliced tensor-core launches (genp_profile_*).
 void tc_profile_enable(bool on);
 int tc_profile_read(double *ms, double *flops);
+int tc_profile_launches(double *ms, double *flops, int cap);
 // D += alpha * A B on the tensor cores with FP64-class accuracy, from the
 // nd-digit slices of sliced.cu: Aq (m x nd kpad) and Bq (n x nd kpad, B
 // transposed) with their row / column exponents ea, fb.

@@ -1,7 +1,7 @@
 // lu.cu -- right-looking blocked GENP (Sec. 1.1; block Gaussian elimination,
 // Thm. 2.2), in place on C:
 //   for k0 = 0, nb, 2nb, ...
-//     panel:  C11 = L11 U11           (one CTA, the nb x nb block in shared memory)
+//     panel:  C11 = L11 U11           (one CTA, the nb x nb block in registers)
 //     trsm:   U12 = L11^{-1} C12,  L21 = C21 U11^{-1}   (one launch, two roles)
 //     schur:  C22 <- C22 - L21 U12    (tiled GEMM, the dominant cost, ~2n^3/3 flops)
 // No row or column is ever exchanged.  A zero or non-finite pivot is
@@ -16,8 +16,7 @@
 namespace genp {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kTrsmW = 64;
+constexpr int kTrsmW = 64;   // vectors (columns of C12 / rows of C21) per block-solve CTA
 
 __global__ void k_status_reset(DevStatus *st) {
     st->breakdown_step = ~0ull;
@@ -42,135 +41,16 @@ __global__ void k_maxabs(const T *C, int64_t n, int64_t ldc, unsigned long long 
     if ((threadIdx.x & 31) == 0) atomic_max_nonneg(out, m);
 }
 
-// Unblocked GENP of the kb x kb diagonal block at (k0, k0), in TC arithmetic.
-template <typename TS, typename TC>
-__global__ void __launch_bounds__(kThreads) k_panel(TS *C, int64_t ldc, int64_t k0, int kb, DevStatus *st) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    TC *a = reinterpret_cast<TC *>(smraw);
-    const int ld = kb + 1, tid = threadIdx.x;
-    for (int idx = tid; idx < kb * kb; idx += kThreads) {
-        const int i = idx / kb, j = idx % kb;
-        a[i * ld + j] = (TC)C[(k0 + i) * ldc + k0 + j];
-    }
-    __syncthreads();
-    for (int k = 0; k < kb; ++k) {
-        const TC p = a[k * ld + k];
-        if (tid == 0) {
-            const double ap = fabs((double)p);
-            if (!(ap > 0.0) || !isfinite(ap)) {
-                atomicMin(&st->breakdown_step, (unsigned long long)(k0 + k));
-            } else {
-                atomic_min_nonneg(&st->min_abs_pivot, ap);
-                atomic_max_nonneg(&st->max_abs_pivot, ap);
-            }
-        }
-        for (int i = k + 1 + tid; i < kb; i += kThreads) a[i * ld + k] = a[i * ld + k] / p;
-        __syncthreads();
-        const int rem = kb - k - 1;
-        for (int idx = tid; idx < rem * rem; idx += kThreads) {
-            const int i = k + 1 + idx / rem, j = k + 1 + idx % rem;
-            a[i * ld + j] = a[i * ld + j] - a[i * ld + k] * a[k * ld + j];
-        }
-        __syncthreads();
-    }
-    double umax = 0.0;
-    for (int idx = tid; idx < kb * kb; idx += kThreads) {
-        const int i = idx / kb, j = idx % kb;
-        const TC v = a[i * ld + j];
-        C[(k0 + i) * ldc + k0 + j] = (TS)v;
-        if (j >= i) {
-            const double av = fabs((double)v);
-            umax = (av > umax || isnan(av)) ? av : umax;
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        const double w = __shfl_xor_sync(0xffffffffu, umax, o);
-        umax = (w > umax || isnan(w)) ? w : umax;
-    }
-    if ((tid & 31) == 0) atomic_max_nonneg(&st->max_abs_u, umax);
-}
-
-// blockIdx.y == 0: U12 = L11^{-1} C12 on columns [c0, c0 + w)
-// blockIdx.y == 1: L21 = C21 U11^{-1} on rows    [c0, c0 + w)
-template <typename TS, typename TC>
-__global__ void __launch_bounds__(kThreads) k_trsm(TS *C, int64_t ldc, int64_t n, int64_t k0, int kb,
-                                                   DevStatus *st) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    TC *d = reinterpret_cast<TC *>(smraw);
-    const int ld = kb + 1, tid = threadIdx.x;
-    TC *x = d + kb * ld;
-    const int64_t c0 = k0 + kb + (int64_t)blockIdx.x * kTrsmW;
-    const int w = (int)min((int64_t)kTrsmW, n - c0);
-    if (w <= 0) return;
-    for (int idx = tid; idx < kb * kb; idx += kThreads) {
-        const int i = idx / kb, j = idx % kb;
-        d[i * ld + j] = (TC)C[(k0 + i) * ldc + k0 + j];
-    }
-    double xmax = 0.0;
-    if (blockIdx.y == 0) {
-        const int lx = kTrsmW + 1;
-        for (int idx = tid; idx < kb * w; idx += kThreads) {
-            const int r = idx / w, c = idx % w;
-            x[r * lx + c] = (TC)C[(k0 + r) * ldc + c0 + c];
-        }
-        __syncthreads();
-        for (int k = 0; k + 1 < kb; ++k) {
-            const int rem = kb - k - 1;
-            for (int idx = tid; idx < rem * w; idx += kThreads) {
-                const int r = k + 1 + idx / w, c = idx % w;
-                x[r * lx + c] = x[r * lx + c] - d[r * ld + k] * x[k * lx + c];
-            }
-            __syncthreads();
-        }
-        for (int idx = tid; idx < kb * w; idx += kThreads) {
-            const int r = idx / w, c = idx % w;
-            const TC v = x[r * lx + c];
-            C[(k0 + r) * ldc + c0 + c] = (TS)v;
-            const double av = fabs((double)v);
-            xmax = (av > xmax || isnan(av)) ? av : xmax;
-        }
-    } else {
-        const int lx = kb + 1;
-        for (int idx = tid; idx < w * kb; idx += kThreads) {
-            const int i = idx / kb, j = idx % kb;
-            x[i * lx + j] = (TC)C[(c0 + i) * ldc + k0 + j];
-        }
-        __syncthreads();
-        for (int j = 0; j < kb; ++j) {
-            const TC p = d[j * ld + j];
-            for (int i = tid; i < w; i += kThreads) x[i * lx + j] = x[i * lx + j] / p;
-            __syncthreads();
-            const int rem = kb - j - 1;
-            if (rem > 0) {
-                for (int idx = tid; idx < w * rem; idx += kThreads) {
-                    const int i = idx / rem, l = j + 1 + idx % rem;
-                    x[i * lx + l] = x[i * lx + l] - x[i * lx + j] * d[j * ld + l];
-                }
-                __syncthreads();
-            }
-        }
-        for (int idx = tid; idx < w * kb; idx += kThreads) {
-            const int i = idx / kb, j = idx % kb;
-            C[(c0 + i) * ldc + k0 + j] = (TS)x[i * lx + j];
-        }
-    }
-    if (blockIdx.y == 0) {
-        for (int o = 16; o > 0; o >>= 1) {
-            const double v = __shfl_xor_sync(0xffffffffu, xmax, o);
-            xmax = (v > xmax || isnan(v)) ? v : xmax;
-        }
-        if ((tid & 31) == 0) atomic_max_nonneg(&st->max_abs_u, xmax);
-    }
-}
-
 // ---------------------------------------------------------------------------
-// Register-blocked panel and block row / column solves for FP64 storage, in
-// FP64 (TC = double) or in double-float (TC = dfloat: the sliced path, whose
-// accuracy is set by its 47-bit products, on the FP32 pipe, which on GB300 is
-// 64 times faster than the FP64 units).  Each thread keeps its share of the
-// block in registers; the inner loops have no integer division.
+// Register-blocked panel and block row / column solves: FP64 (TC = double),
+// double-float (TC = dfloat: the sliced path, whose accuracy is set by its
+// 47-bit products, on the FP32 pipe, which on GB300 is 64 times faster than
+// the FP64 units) or FP32 (TC = float, the block solves of the FP32-storage
+// paths).  Each thread keeps its share of the block in registers; the inner
+// loops have no integer division.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double fms(double x, double l, double u) { return fma(-l, u, x); }
+__device__ __forceinline__ float fms(float x, float l, float u) { return fmaf(-l, u, x); }
 // x - l u in double-float: TwoProduct of the leading parts by FMA, TwoSum of
 // x.hi and the product, the small terms gathered, one renormalization.
 __device__ __forceinline__ dfloat fms(dfloat x, dfloat l, dfloat u) {
@@ -181,6 +61,7 @@ __device__ __forceinline__ dfloat fms(dfloat x, dfloat l, dfloat u) {
     return df_norm(s, (err + x.lo) - pe);
 }
 __device__ __forceinline__ double shfl_idx(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ float shfl_idx(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 __device__ __forceinline__ dfloat shfl_idx(dfloat v, int src) {
     v.hi = __shfl_sync(0xffffffffu, v.hi, src);
     v.lo = __shfl_sync(0xffffffffu, v.lo, src);
@@ -195,8 +76,10 @@ template <typename TS> __device__ __forceinline__ TS st_as(double v) { return TS
 template <typename TS> __device__ __forceinline__ TS st_as(dfloat v);
 template <> __device__ __forceinline__ dfloat st_as<dfloat>(dfloat v) { return v; }
 template <> __device__ __forceinline__ double st_as<double>(dfloat v) { return (double)v; }
+template <> __device__ __forceinline__ float st_as<float>(dfloat v) { return v.hi + v.lo; }
 // magnitude for the growth statistics, without FP64 work for double-float
 __device__ __forceinline__ double mag(double v) { return fabs(v); }
+__device__ __forceinline__ float mag(float v) { return fabsf(v); }
 __device__ __forceinline__ float mag(dfloat v) { return fabsf(v.hi); }
 
 __device__ __forceinline__ void pivot_stats(DevStatus *st, int64_t step, double p) {
@@ -407,8 +290,8 @@ __global__ void __launch_bounds__(kTrsmThreads, 1) k_trsm_reg(TS *C, int64_t ldc
     }
 }
 
-// one step of the blocked factorization's FP64-storage panel work: the
-// diagonal block at (i0, i0), then the block row and column beside it
+// one step of the blocked factorization's panel work: the diagonal block at
+// (i0, i0), then the block row and column beside it
 template <typename TS, typename TC>
 cudaError_t panel_and_trsm(TS *C, int64_t ldc, int64_t n, int64_t i0, int kb, DevStatus *st, cudaStream_t s) {
     static bool attr_done = false;
@@ -434,59 +317,40 @@ cudaError_t factor_typed(genp_factors *F, cudaStream_t s) {
     TS *C = static_cast<TS *>(F->C);
     const int64_t n = F->n, ldc = F->ldc;
     const int nb = (int)F->nb;
-    const size_t sm_panel = (size_t)nb * (nb + 1) * sizeof(TC);
-    const size_t xrow = (size_t)nb * (kTrsmW + 1), xcol = (size_t)kTrsmW * (nb + 1);
-    const size_t sm_trsm = sm_panel + (xrow > xcol ? xrow : xcol) * sizeof(TC);
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(k_panel<TS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_trsm<TS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_done = true;
-    }
     note_launch();
     k_maxabs<TS><<<152 * 4, 256, 0, s>>>(C, n, ldc, &F->st->max_abs_c);
     for (int64_t k0 = 0; k0 < n; k0 += nb) {
         const int kb = (int)(n - k0 < nb ? n - k0 : nb);
         const int64_t rem = n - k0 - kb;
-        if constexpr (std::is_same<TS, double>::value) {
-            cudaError_t e = panel_and_trsm<double, double>(C, ldc, n, k0, kb, F->st, s);
-            if (e != cudaSuccess) return e;
-        } else {
-            note_launch();
-            k_panel<TS, TC><<<1, kThreads, sm_panel, s>>>(C, ldc, k0, kb, F->st);
-            if (rem > 0) {
-                dim3 g((unsigned)cdiv(rem, kTrsmW), 2);
-                note_launch();
-                k_trsm<TS, TC><<<g, kThreads, sm_trsm, s>>>(C, ldc, n, k0, kb, F->st);
-            }
-        }
+        cudaError_t e = panel_and_trsm<TS, TC>(C, ldc, n, k0, kb, F->st, s);
+        if (e != cudaSuccess) return e;
         if (rem <= 0) break;
         TS *L21 = C + (k0 + kb) * ldc + k0;
         TS *U12 = C + k0 * ldc + k0 + kb;
         TS *A22 = C + (k0 + kb) * ldc + k0 + kb;
-        cudaError_t e = gemm<TS>(rem, rem, kb, TS(-1), L21, ldc, false, U12, ldc, TS(1), A22, ldc, A22, ldc,
-                                 nullptr, s);
+        e = gemm<TS>(rem, rem, kb, TS(-1), L21, ldc, false, U12, ldc, TS(1), A22, ldc, A22, ldc, nullptr, s);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
 
-// Mixed precision (GENP_BF16, GENP_BF16X3): C is the FP32 master copy.  The
-// diagonal block is factored in FP64 (the pivots), the block row and column
-// are solved in FP32, and the Schur update C22 -= L21 U12 runs on the tensor
-// cores with BF16 (split) operands and FP32 accumulation.
+// Mixed precision (GENP_BF16, GENP_BF16X3, GENP_FP8_E4M3): C is the FP32
+// master copy.  The diagonal block is factored in double-float (FP64-class
+// pivots, 48 bits, on the FP32 pipe: k_panel_reg; in FP64 it took 0.9 ms per
+// block on this GPU's FP64 units), the block row and column are solved in
+// FP32 (k_trsm_reg),
+// and the Schur update C22 -= L21 U12 runs on the tensor cores with BF16
+// (split) or tile-scaled e4m3 operands and FP32 accumulation.
 cudaError_t factor_tc(genp_factors *F, cudaStream_t s) {
     float *C = static_cast<float *>(F->C);
     const int64_t n = F->n, ldc = F->ldc;
     const int nb = (int)F->nb;
     const int terms = split_terms(F->prec);
-    const size_t sm_panel = (size_t)nb * (nb + 1) * sizeof(double);
-    const size_t xrow = (size_t)nb * (kTrsmW + 1), xcol = (size_t)kTrsmW * (nb + 1);
-    const size_t sm_trsm = (size_t)nb * (nb + 1) * sizeof(float) + (xrow > xcol ? xrow : xcol) * sizeof(float);
     static bool attr_done = false;
     if (!attr_done) {
-        cudaFuncSetAttribute(k_panel<float, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        cudaFuncSetAttribute(k_trsm<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(k_trsm_reg<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             128 * 129 * (int)sizeof(float));
+        if (e != cudaSuccess) return e;
         attr_done = true;
     }
     note_launch();
@@ -494,15 +358,29 @@ cudaError_t factor_tc(genp_factors *F, cudaStream_t s) {
     for (int64_t k0 = 0; k0 < n; k0 += nb) {
         const int kb = (int)(n - k0 < nb ? n - k0 : nb);
         note_launch();
-        k_panel<float, double><<<1, kThreads, sm_panel, s>>>(C, ldc, k0, kb, F->st);
+        k_panel_reg<float, dfloat><<<1, kPanelThreads, 0, s>>>(C, ldc, k0, kb, F->st);
         const int64_t rem = n - k0 - kb;
         if (rem <= 0) break;
         dim3 g((unsigned)cdiv(rem, kTrsmW), 2);
         note_launch();
-        k_trsm<float, float><<<g, kThreads, sm_trsm, s>>>(C, ldc, n, k0, kb, F->st);
+        k_trsm_reg<float, float><<<g, kTrsmThreads, (size_t)kb * (kb + 1) * sizeof(float), s>>>(C, ldc, n, k0, kb,
+                                                                                               F->st);
         float *L21 = C + (k0 + kb) * ldc + k0;
         float *U12 = C + k0 * ldc + k0 + kb;
         float *A22 = C + (k0 + kb) * ldc + k0 + kb;
+        if (F->prec == GENP_FP8_E4M3) {
+            // e4m3 operands, one power-of-two scale per 128 x 128 tile (kb <= 128:
+            // a single k-tile, so each output tile takes one scale product)
+            uint8_t *qa = reinterpret_cast<uint8_t *>(F->tcA), *qb = reinterpret_cast<uint8_t *>(F->tcB);
+            const int64_t ldq = F->tc_ldq * 2;   // bytes
+            float *sa = F->qscale, *sb = F->qscale + cdiv(n, 128);
+            cudaError_t e = quant_e4m3<float>(L21, ldc, rem, kb, false, qa, ldq, sa, s);
+            if (e == cudaSuccess) e = quant_e4m3<float>(U12, ldc, rem, kb, true, qb, ldq, sb, s);
+            if (e == cudaSuccess)
+                e = tc_gemm_e4m3(rem, rem, kb, -1.0f, qa, ldq, sa, qb, ldq, sb, 1.0f, A22, ldc, A22, ldc, s);
+            if (e != cudaSuccess) return e;
+            continue;
+        }
         const int64_t Kq = (int64_t)kb * terms;
         cudaError_t e = split_rows<float>(L21, ldc, rem, kb, F->tcA, F->tc_ldq, terms, true, -1, s);
         if (e == cudaSuccess) e = split_cols_T<float>(U12, ldc, kb, rem, F->tcB, F->tc_ldq, terms, s);
@@ -583,7 +461,8 @@ cudaError_t factor_run(genp_factors *F, cudaStream_t s) {
         case GENP_FP64: e = factor_typed<double, double>(F, s); break;
         case GENP_FP32: e = factor_typed<float, float>(F, s); break;
         case GENP_BF16:
-        case GENP_BF16X3: e = factor_tc(F, s); break;
+        case GENP_BF16X3:
+        case GENP_FP8_E4M3: e = factor_tc(F, s); break;
         case GENP_BF16_SLICED: e = factor_sliced(F, s); break;
         default: return cudaErrorNotSupported;
     }

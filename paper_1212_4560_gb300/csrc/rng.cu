@@ -12,6 +12,8 @@
 // keep the compiler from fusing multiply-adds in this file.
 #include "genp_internal.cuh"
 
+#include "e4m3.cuh"
+
 namespace genp {
 namespace {
 
@@ -152,10 +154,41 @@ __device__ __forceinline__ double round_to_bf16_grid(double x) {
     return __longlong_as_double((long long)b);
 }
 
+// FP8 grid: e4m3 values times 2^e, one e for the matrix: the least integer
+// with 12.5 scale <= 448 2^e (12.5 standard deviations bound every polar
+// draw), so no entry saturates.  Rounding to nearest, ties to even.
+__host__ __device__ inline int fp8_grid_exp(double scale) {
+    const double amax = 12.5 * scale;
+    if (!(amax > 0.0)) return 0;
+    int p = 0;
+    const double f = frexp(amax, &p);
+    const int e = f <= 0.875 ? p - 9 : p - 8;
+    return e < -126 ? -126 : (e > 126 ? 126 : e);
+}
+__device__ __forceinline__ double round_to_fp8_grid(double v, int e) {
+    // the scalings by 2^-e and 2^e are exact (|e| <= 126)
+    const double down = __longlong_as_double((long long)(1023 - e) << 52);
+    const double up = __longlong_as_double((long long)(1023 + e) << 52);
+    return e4m3_round_f64(v * down) * up;
+}
+
 __device__ __forceinline__ double on_grid(double v, genp_prec grid) {
     if (grid == GENP_BF16) return round_to_bf16_grid(v);
     if (grid == GENP_FP32) return (double)__double2float_rn(v);
     return v;
+}
+
+// One Gaussian entry of scale `scale` on the requested grid.  The FP32 and
+// FP8 grids draw by the polar method in FP32 on their own tag (tag + 4); the
+// FP8 grid then rounds that draw to e4m3 times 2^e (the draw's precision is
+// far beyond e4m3's).  The FP64 and BF16 grids draw in FP64.
+__device__ __forceinline__ double draw_on_grid(uint64_t seed, uint64_t sid, uint64_t tag, uint64_t idx, double scale,
+                                               genp_prec grid) {
+    if (grid == GENP_FP32 || grid == GENP_FP8_E4M3) {
+        const double v = (double)__fmul_rn(polar_normal_f32(seed, sid, tag + 4, idx), __double2float_rn(scale));
+        return grid == GENP_FP32 ? v : round_to_fp8_grid(v, fp8_grid_exp(scale));
+    }
+    return on_grid(__dmul_rn(polar_normal(seed, sid, tag, idx), scale), grid);
 }
 
 __global__ void k_dense(double *G, int64_t n, uint64_t seed, uint64_t sid, double scale, genp_prec grid,
@@ -163,10 +196,7 @@ __global__ void k_dense(double *G, int64_t n, uint64_t seed, uint64_t sid, doubl
     const int64_t total = n * n;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const double v =
-            grid == GENP_FP32
-                ? (double)__fmul_rn(polar_normal_f32(seed, sid, kTagDense + 4, (uint64_t)idx), __double2float_rn(scale))
-                : on_grid(__dmul_rn(polar_normal(seed, sid, kTagDense, (uint64_t)idx), scale), grid);
+        const double v = draw_on_grid(seed, sid, kTagDense, (uint64_t)idx, scale, grid);
         G[idx] = v;
         if (G32) G32[idx] = (float)v;
         if (Gbf) Gbf[(idx % n) * round8(n) + idx / n] = __float2bfloat16_rn((float)v);  // G^T, K-major
@@ -175,9 +205,7 @@ __global__ void k_dense(double *G, int64_t n, uint64_t seed, uint64_t sid, doubl
 
 __global__ void k_circ(double *g, int64_t n, uint64_t seed, uint64_t sid, double scale, genp_prec grid) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        g[i] = grid == GENP_FP32
-                   ? (double)__fmul_rn(polar_normal_f32(seed, sid, kTagCirc + 4, (uint64_t)i), __double2float_rn(scale))
-                   : on_grid(__dmul_rn(polar_normal(seed, sid, kTagCirc, (uint64_t)i), scale), grid);
+        g[i] = draw_on_grid(seed, sid, kTagCirc, (uint64_t)i, scale, grid);
 }
 
 // Gaussian Toeplitz multiplier (Definition 3.2): the 2n - 1 entries
@@ -192,10 +220,7 @@ __global__ void k_toeplitz(double *g, int64_t n, uint64_t seed, uint64_t sid, do
             continue;
         }
         const int64_t d = q - (n - 1);
-        const double v = grid == GENP_FP32
-                             ? (double)__fmul_rn(polar_normal_f32(seed, sid, kTagToep + 4, (uint64_t)q),
-                                                 __double2float_rn(scale))
-                             : on_grid(__dmul_rn(polar_normal(seed, sid, kTagToep, (uint64_t)q), scale), grid);
+        const double v = draw_on_grid(seed, sid, kTagToep, (uint64_t)q, scale, grid);
         g[d >= 0 ? d : 2 * n + d] = v;
     }
 }

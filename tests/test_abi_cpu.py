@@ -39,7 +39,7 @@ def test_version_and_status_strings(lib):
 
 def test_argument_errors_return_before_any_cuda_call(lib):
     out = ctypes.c_void_p()
-    ARG, UNSUP = -1, -7
+    ARG = -1
     assert lib.genp_make_multiplier(0, 0, 1, 0, 1.0, 4, 0, None, ctypes.byref(out)) == ARG      # n = 0
     assert lib.genp_make_multiplier(9, 8, 1, 0, 1.0, 4, 0, None, ctypes.byref(out)) == ARG      # bad kind
     assert lib.genp_make_multiplier(0, 8, 1, 0, -1.0, 4, 0, None, ctypes.byref(out)) == ARG     # bad scale
@@ -49,7 +49,17 @@ def test_argument_errors_return_before_any_cuda_call(lib):
     fake = ctypes.c_void_p(0x1000)
     assert lib.genp_factor(fake, 8, 4, 0, 0, None, ctypes.byref(out)) == ARG                    # ldc < n
     assert lib.genp_factor(fake, 8, 8, 0, 500, None, ctypes.byref(out)) == ARG                  # nb too big
-    assert lib.genp_factor(fake, 8, 8, 3, 0, None, ctypes.byref(out)) == UNSUP                  # FP8 factor
+    assert lib.genp_factor(fake, 8, 4, 3, 0, None, ctypes.byref(out)) == ARG                    # FP8, ldc < n
+    assert lib.genp_factor(fake, 8, 8, 9, 0, None, ctypes.byref(out)) == ARG                    # bad precision
+    buf = ctypes.c_void_p(0x2000)
+    assert lib.genp_quantize_e4m3(fake, 8, 2, 8, 8, 0, buf, 16, buf, None) == ARG   # BF16 source
+    assert lib.genp_quantize_e4m3(fake, 8, 0, 8, 8, 0, buf, 8, buf, None) == ARG    # ldq not a multiple of 16
+    assert lib.genp_quantize_e4m3(fake, 4, 0, 8, 8, 0, buf, 16, buf, None) == ARG   # lds < K
+    assert lib.genp_quantize_e4m3(fake, 4, 1, 8, 2, 1, buf, 16, buf, None) == ARG   # transposed: lds < m
+    assert lib.genp_gemm_e4m3(8, 8, 8, ctypes.c_float(1.0), buf, 8, buf, buf, 16, buf, ctypes.c_float(0.0),
+                              None, 0, buf, 8, None) == ARG                           # lda not a multiple of 16
+    assert lib.genp_gemm_e4m3(8, 8, 8, ctypes.c_float(1.0), buf, 16, buf, buf, 16, buf, ctypes.c_float(1.0),
+                              None, 0, buf, 8, None) == ARG                           # beta != 0 without Cin
     assert lib.genp_solve(None, None, None, 1, 1, None, 1, None) == ARG
     assert lib.genp_refine(None, 1, None, None, None, 1, 1, None, 1, 1e-15, 3, 0, None) == ARG
     assert lib.genp_adjoint(None, None, None, 1, None, 1, 1, None, 1, None, 1, None) == ARG

@@ -444,12 +444,14 @@ GENP_API genp_status genp_quantize_e4m3(const void *src, int64_t lds, genp_prec 
                                         int trans, uint8_t *dst, int64_t ldq, float *scales, void *cuda_stream);
 
 /* Tensor-core product of tile-scaled e4m3 operands (tcgen05 kind::f8f6f4,
- * FP32 accumulation per 128-wide k-tile, promoted into FP32 with the tile
- * pair's scale):
+ * FP32 accumulation of each run of 128-wide k-tiles with one scale product,
+ * promoted into FP32 with that scale):
  *   D = alpha * sum_kt scale_a[tm][kt] scale_b[tn][kt] A_kt Bt_kt^T + beta * Cin
  *  A   m x K codes, ld lda; scale_a ceil(m/128) x ceil(K/128) floats.
  *  Bt  n x K codes (B transposed), ld ldb; scale_b ceil(n/128) x ceil(K/128).
- *  lda, ldb multiples of 16, bases 16-byte aligned; Cin, D as genp_gemm_bf16.
+ *  lda, ldb multiples of 16, bases 16-byte aligned; Cin, D as genp_gemm_bf16;
+ *  K <= 262144.  Consecutive k-tiles with the same scale product accumulate
+ *  together in FP32 on the tensor cores before the promotion.
  * Errors: GENP_ERR_ARG, GENP_ERR_CUDA. */
 GENP_API genp_status genp_gemm_e4m3(int64_t m, int64_t n, int64_t K, float alpha, const uint8_t *A, int64_t lda,
                                     const float *scale_a, const uint8_t *Bt, int64_t ldb, const float *scale_b,

@@ -341,7 +341,7 @@ genp_status genp_gemm_e4m3(int64_t m, int64_t n, int64_t K, float alpha, const u
     if (lda < K || ldb < K || ldd < n || (lda % 16) || (ldb % 16)) return GENP_ERR_ARG;
     if (((uintptr_t)A % 16) || ((uintptr_t)Bt % 16)) return GENP_ERR_ARG;
     if (beta != 0.0f && (!Cin || ldci < n)) return GENP_ERR_ARG;
-    if (m > INT32_MAX || n > INT32_MAX || K > INT32_MAX || cdiv(m, 128) > 65535) return GENP_ERR_ARG;
+    if (m > INT32_MAX || n > INT32_MAX || K > 262144 || cdiv(m, 128) > 65535) return GENP_ERR_ARG;
     CU(tc_gemm_e4m3(m, n, K, alpha, A, lda, scale_a, Bt, ldb, scale_b, beta, Cin, ldci, D, ldd, S(cuda_stream)));
     return GENP_OK;
 }

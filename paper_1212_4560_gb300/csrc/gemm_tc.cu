@@ -342,10 +342,13 @@ bool make_map(CUtensorMap *map, const void *ptr, int64_t rows, int64_t K, int64_
 // A (m x K) and B^T (n x K) hold e4m3 codes, K-major; tile (tm, kt) of A is
 // rows 128 tm .. and columns 128 kt .., its scale scA[tm * nkt + kt]
 // (nkt = ceil(K / 128)); likewise scB for B^T.  Each k-tile (128 e4m3 = one
-// 128-byte swizzle row) is one tcgen05 kind::f8f6f4 accumulation of four
-// K = 32 MMAs into one of two TMEM accumulators; the epilogue warps read it
-// and add it, times the tile pair's scale, into FP32 registers while the
-// MMAs of the next k-tile fill the other accumulator.
+// 128-byte swizzle row) is four K = 32 tcgen05 kind::f8f6f4 MMAs.  A run of
+// consecutive k-tiles with the same scale product sc (exact powers of two,
+// compared exactly) accumulates in one TMEM accumulator, since
+// sum sc P_kt = sc sum P_kt; at the end of the run the epilogue warps read
+// it and add it, times sc, into FP32 registers while the MMAs of the next
+// run fill the other accumulator.  Tiles of similar magnitude share their
+// scales, so a row of tiles is mostly one run.
 //   warps 0-7: promotion and the final write (warp w: TMEM lanes 32 (w % 4)
 //              .. = its rows, columns 64 (w / 4) .. = its half; two warps per
 //              scheduler keep the promotion ahead of the MMAs);
@@ -370,7 +373,8 @@ struct QCtl {
     int abort;
     int issued;
 };
-constexpr size_t kQSmem = 1024 + Q_STAGES * (QA_BYTES + QB_BYTES) + sizeof(QCtl);
+constexpr int kQMaxKt = 2048;     // k-tiles whose scale products the CTA keeps (K <= 262144)
+constexpr size_t kQSmem = 1024 + Q_STAGES * (QA_BYTES + QB_BYTES) + sizeof(QCtl) + kQMaxKt * sizeof(float);
 static_assert(kQSmem <= 227 * 1024, "shared memory");
 static_assert(BM * kTileLd * 4 <= Q_STAGES * (QA_BYTES + QB_BYTES), "output tile fits in the stage buffers");
 
@@ -383,6 +387,7 @@ k_tc_e4m3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     unsigned char *sA = base;
     unsigned char *sB = base + Q_STAGES * QA_BYTES;
     QCtl *ctl = (QCtl *)(sB + Q_STAGES * QB_BYTES);
+    float *s_sc = reinterpret_cast<float *>(ctl + 1);   // scale product of each k-tile
     volatile int *abort = &ctl->abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tm = blockIdx.y, tn = blockIdx.x;
@@ -409,6 +414,8 @@ k_tc_e4m3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    for (int kt = threadIdx.x; kt < nkt; kt += blockDim.x)
+        s_sc[kt] = scA[(int64_t)tm * nkt + kt] * scB[(int64_t)tn * nkt + kt];
     fence_before();
     __syncthreads();
     fence_after();
@@ -431,14 +438,22 @@ k_tc_e4m3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         __syncwarp();
     } else if (warp == kQMma) {
         if (lane == 0) {
+            int g = -1, b = 0;   // run index, its accumulator
             for (int kt = 0; kt < nkt; ++kt) {
-                const int s = kt % Q_STAGES, b = kt & 1;
-                if (!mbar_wait(&ctl->full[s], (uint32_t)((kt / Q_STAGES) & 1), abort)) {
-                    *abort = 1;
-                    break;
+                const int s = kt % Q_STAGES;
+                const float sc = s_sc[kt];
+                const bool start = kt == 0 || s_sc[kt - 1] != sc;
+                const bool last = kt + 1 == nkt || s_sc[kt + 1] != sc;
+                if (start) {
+                    // accumulator b was last filled by run g - 2
+                    ++g;
+                    b = g & 1;
+                    if (g >= 2 && !mbar_wait(&ctl->aempty[b], (uint32_t)(((g - 2) >> 1) & 1), abort)) {
+                        *abort = 1;
+                        break;
+                    }
                 }
-                // accumulator b was last filled by k-tile kt - 2
-                if (kt >= 2 && !mbar_wait(&ctl->aempty[b], (uint32_t)(((kt - 2) >> 1) & 1), abort)) {
+                if (!mbar_wait(&ctl->full[s], (uint32_t)((kt / Q_STAGES) & 1), abort)) {
                     *abort = 1;
                     break;
                 }
@@ -447,9 +462,9 @@ k_tc_e4m3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 #pragma unroll
                 for (int k = 0; k < QBK / 32; ++k)   // K = 32 e4m3 (32 bytes) per MMA
                     mma_e4m3(tmem + (uint32_t)(b * BN), ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2),
-                             k > 0 ? 1u : 0u);
+                             (start && k == 0) ? 0u : 1u);
                 commit(&ctl->empty[s]);
-                commit(&ctl->afull[b]);
+                if (last) commit(&ctl->afull[b]);
             }
         }
         __syncwarp();
@@ -463,13 +478,13 @@ k_tc_e4m3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 #pragma unroll
         for (int j = 0; j < HALF; ++j) acc[j] = 0.0f;
         bool ok = true;
-        const float *sa_row = scA + (int64_t)tm * nkt, *sb_row = scB + (int64_t)tn * nkt;
-        float sc_next = sa_row[0] * sb_row[0];
-        for (int kt = 0; kt < nkt; ++kt) {
-            const int b = kt & 1;
-            const float sc = sc_next;          // this k-tile's scale; the next one's loads go out now
-            if (kt + 1 < nkt) sc_next = sa_row[kt + 1] * sb_row[kt + 1];
-            if (!mbar_wait(&ctl->afull[b], (uint32_t)((kt >> 1) & 1), abort)) {
+        for (int kt = 0, g = 0; kt < nkt; ++g) {
+            const int b = g & 1;
+            const float sc = s_sc[kt];
+            int e = kt + 1;                    // the run is k-tiles kt .. e - 1
+            while (e < nkt && s_sc[e] == sc) ++e;
+            kt = e;
+            if (!mbar_wait(&ctl->afull[b], (uint32_t)((g >> 1) & 1), abort)) {
                 *abort = 1;
                 ok = false;
                 break;
@@ -987,7 +1002,7 @@ cudaError_t tc_gemm_e4m3(int64_t m, int64_t n, int64_t K, float alpha, const uin
                          const uint8_t *Bt, int64_t ldb, const float *sb, float beta, const float *Cin, int64_t ldci,
                          float *D, int64_t ldd, cudaStream_t s) {
     if (m <= 0 || n <= 0) return cudaSuccess;
-    if (K <= 0 || m > INT32_MAX || n > INT32_MAX || K > INT32_MAX) return cudaErrorInvalidValue;
+    if (K <= 0 || m > INT32_MAX || n > INT32_MAX || K > (int64_t)kQMaxKt * QBK) return cudaErrorInvalidValue;
     // TMA: 16-byte aligned bases and row strides
     if ((lda % 16) || (ldb % 16) || ((uintptr_t)A % 16) || ((uintptr_t)Bt % 16)) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;

@@ -387,6 +387,7 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
     auto block_of = [&](int p) { return forward ? p : nblk - 1 - p; };
     // double-float walker: tiles of op(T) from the double-float factors, the
     // inverse of the diagonal tile from its double-float copy
+    // (a diagonal tile's other triangle is never read: store_d zeroes it)
     auto load_tile_d = [&](int i, int j, dfloat (&v)[16]) {
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
@@ -394,15 +395,21 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
             const int a = idx >> 6, b = idx & 63;
             const int rr = mode <= 1 ? a : b, kk = mode <= 1 ? b : a;   // element (rr, kk) of op(T)'s tile
             const int64_t row = (int64_t)i * TB + rr, col = (int64_t)j * TB + kk;
+            const bool needed = i != j || (forward ? kk <= rr : kk >= rr);
             dfloat z(0.0f);
-            if (row < n && col < n) z = (mode <= 1) ? Cd[row * ldcd + col] : Cd[col * ldcd + row];
+            if (needed && row < n && col < n) z = (mode <= 1) ? Cd[row * ldcd + col] : Cd[col * ldcd + row];
             v[e] = z;
         }
     };
+    // the inverse of a triangular block is triangular: only that half is read
     auto load_inv_d = [&](int j, dfloat (&v)[16]) {
         const dfloat *X = Dinvd + ((int64_t)(unit ? 0 : 1) * nblk + j) * TB * TB;
 #pragma unroll
-        for (int e = 0; e < 16; ++e) v[e] = X[tid + e * kTrsvThreads];
+        for (int e = 0; e < 16; ++e) {
+            const int idx = tid + e * kTrsvThreads;
+            const int a = idx >> 6, b = idx & 63;
+            v[e] = (unit ? b <= a : b >= a) ? X[idx] : dfloat(0.0f);
+        }
     };
     // element e of this thread's share is (rr, kk) of op(T)'s tile
     // (load_tile_d), or (a, b) of the row-major inverse of T_jj (load_inv_d),
@@ -434,21 +441,38 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
             // ---- the walker in double-float (FP32 pipe; FP64 is 64 times
             // slower on this GPU): the same steps as the FP64 walker below ----
             dfloat vD[16], vX[16], vO[16];
+            // b_j of the coming step, in registers: its loads go out at the end
+            // of the previous step, before the product for the next block, and
+            // have landed by the time it is used
+            constexpr int kBv = (TB * NR + kTrsvThreads - 1) / kTrsvThreads;
+            double bv[kBv];
+            auto load_b = [&](int jb) {
+                const int bb = min(TB, n - jb * TB);
+#pragma unroll
+                for (int e = 0; e < kBv; ++e) {
+                    const int idx = tid + e * kTrsvThreads;
+                    const int rr = idx / NR, c = idx % NR;
+                    bv[e] = (idx < TB * NR && rr < bb && c < nr) ? (double)ldcg(Y + ((int64_t)jb * TB + rr) * ldy + c)
+                                                                  : 0.0;
+                }
+            };
             load_tile_d(block_of(0), block_of(0), vD);
             load_inv_d(block_of(0), vX);
+            load_b(block_of(0));
             for (int q = 0; q < nblk; ++q) {
                 const int j = block_of(q);
                 const int bj = min(TB, n - j * TB);
                 __syncthreads();
                 store_d(sd.Dh, sd.Dl, vD, 1);
                 store_d(sd.Sh, sd.Sl, vX, 2);
-                if (tid == 0 && q >= 2 && !wait_geq(cnt + j, q - 1)) atomicExch(&g_solve_timeout, 1);
-                __syncthreads();
-                // b_j first: its loads must not queue behind the next step's tiles
-                for (int idx = tid; idx < TB * NR; idx += kTrsvThreads) {
-                    const int rr = idx / NR, c = idx % NR;
-                    const dfloat b((rr < bj && c < nr) ? (double)ldcg(Y + ((int64_t)j * TB + rr) * ldy + c) : 0.0);
-                    sd.acc[rr][c] = q > 0 ? b - sd.carry[rr][c] : b;
+#pragma unroll
+                for (int e = 0; e < kBv; ++e) {
+                    const int idx = tid + e * kTrsvThreads;
+                    if (idx < TB * NR) {
+                        const int rr = idx / NR, c = idx % NR;
+                        const dfloat b(bv[e]);
+                        sd.acc[rr][c] = q > 0 ? b - sd.carry[rr][c] : b;
+                    }
                 }
                 if (q + 1 < nblk) {
                     load_tile_d(block_of(q + 1), j, vO);
@@ -480,7 +504,10 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
                 if (tid == 0) publish(ready + j);
                 if (q + 1 < nblk) {           // own contribution to the next block
                     store_d(sd.Oh, sd.Ol, vO, 0);
+                    // the next step's items (earlier steps up to q - 1), then its b
+                    if (tid == 0 && q >= 1 && !wait_geq(cnt + block_of(q + 1), q)) atomicExch(&g_solve_timeout, 1);
                     __syncthreads();
+                    load_b(block_of(q + 1));
                     tile_gemv_dd<NR>(sd.Oh, sd.Ol, sd.y, r, qq, part);
 #pragma unroll
                     for (int c = 0; c < NR; ++c)

@@ -5,10 +5,11 @@
   values), FP32 and FP64 sources, both orientations, ragged edges, a zero
   tile, subnormal codes and exact ties;
 * genp_gemm_e4m3: against the oracle's product of the same codes, exact in
-  FP64 per k-tile.  The tensor cores accumulate a k-tile in FP32 (at most
-  127 additions) and the promotion adds nkt FP32 multiply-adds, so
-  |D - D_oracle| <= (128 + nkt + 2) 2^-24 |alpha| sum_k |a_k b_k| + 2^-23 |beta C|;
-  small integers are exact;
+  FP64 per k-tile.  The tensor cores accumulate a run of k-tiles with equal
+  scale products in FP32 (fewer than K additions) and the promotion adds at
+  most nkt FP32 multiply-adds, so
+  |D - D_oracle| <= (K + nkt + 2) 2^-24 |alpha| sum_k |a_k b_k| + 2^-23 |beta C|;
+  small integers are exact; runs of every length (scale patterns along K);
 * the FP8 grid of a Gaussian multiplier bit for bit; C = A G on the e4m3
   tensor cores within the product bound;
 * the factorization: |L U - C| <= (2^-3 + 2^-7) |L||U| elementwise (two
@@ -106,8 +107,31 @@ def test_gemm_matches_oracle(genp_lib, m, n, K):
     ref = oracle.gemm_e4m3(codes_a, sa, codes_b, sb, alpha=-0.5, beta=2.0, C=C.astype(np.float64))
     absprod = np.abs(oracle.dequantize_e4m3(codes_a, sa)) @ np.abs(oracle.dequantize_e4m3(codes_b, sb)).T
     nkt = -(-K // 128)
-    tol = (128 + nkt + 2) * U32 * 0.5 * absprod + 2 * U32 * 2.0 * np.abs(C)
+    tol = (K + nkt + 2) * U32 * 0.5 * absprod + 2 * U32 * 2.0 * np.abs(C)
     assert np.all(np.abs(D - ref) <= tol)
+    # typical error far below the worst case
+    assert np.median(np.abs(D - ref) / np.maximum(0.5 * absprod, 1e-300)) < 16 * U32
+
+
+@pytest.mark.parametrize("pattern", [[0, 0, 0, 0, 0], [0, 3, 0, 3, 0], [0, 0, -5, -5, -5], [2, 2, 2, 0, 7]])
+def test_gemm_scale_runs(genp_lib, pattern):
+    """Column blocks of A scaled by 2^p (p per k-tile): runs of equal tile
+    scales of every length, each promoted with its own scale."""
+    rng = np.random.default_rng(sum((p + 8) * 16 ** i for i, p in enumerate(pattern)))
+    m, n = 256, 200
+    K = 128 * len(pattern) - 40                       # ragged last k-tile
+    A = rng.standard_normal((m, K))
+    for kt, p in enumerate(pattern):
+        A[:, 128 * kt:128 * (kt + 1)] *= 2.0 ** p
+    Bt = rng.standard_normal((n, K))
+    Aq, sA, _ = quantize(genp_lib, torch.as_tensor(A).to(DEV))
+    Bq, sB, _ = quantize(genp_lib, torch.as_tensor(Bt).to(DEV))
+    D = gemm(genp_lib, Aq, sA, Bq, sB, m, n, K).cpu().double().numpy()
+    codes_a, sa = oracle.quantize_e4m3(A)
+    codes_b, sb = oracle.quantize_e4m3(Bt)
+    ref = oracle.gemm_e4m3(codes_a, sa, codes_b, sb)
+    absprod = np.abs(oracle.dequantize_e4m3(codes_a, sa)) @ np.abs(oracle.dequantize_e4m3(codes_b, sb)).T
+    assert np.all(np.abs(D - ref) <= (K + len(pattern) + 2) * U32 * absprod)
 
 
 def test_gemm_small_integers_exact_and_inplace(genp_lib):

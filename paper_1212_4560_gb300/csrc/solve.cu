@@ -387,7 +387,6 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
     auto block_of = [&](int p) { return forward ? p : nblk - 1 - p; };
     // double-float walker: tiles of op(T) from the double-float factors, the
     // inverse of the diagonal tile from its double-float copy
-    // (a diagonal tile's other triangle is never read: store_d zeroes it)
     auto load_tile_d = [&](int i, int j, dfloat (&v)[16]) {
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
@@ -395,21 +394,15 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
             const int a = idx >> 6, b = idx & 63;
             const int rr = mode <= 1 ? a : b, kk = mode <= 1 ? b : a;   // element (rr, kk) of op(T)'s tile
             const int64_t row = (int64_t)i * TB + rr, col = (int64_t)j * TB + kk;
-            const bool needed = i != j || (forward ? kk <= rr : kk >= rr);
             dfloat z(0.0f);
-            if (needed && row < n && col < n) z = (mode <= 1) ? Cd[row * ldcd + col] : Cd[col * ldcd + row];
+            if (row < n && col < n) z = (mode <= 1) ? Cd[row * ldcd + col] : Cd[col * ldcd + row];
             v[e] = z;
         }
     };
-    // the inverse of a triangular block is triangular: only that half is read
     auto load_inv_d = [&](int j, dfloat (&v)[16]) {
         const dfloat *X = Dinvd + ((int64_t)(unit ? 0 : 1) * nblk + j) * TB * TB;
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const int idx = tid + e * kTrsvThreads;
-            const int a = idx >> 6, b = idx & 63;
-            v[e] = (unit ? b <= a : b >= a) ? X[idx] : dfloat(0.0f);
-        }
+        for (int e = 0; e < 16; ++e) v[e] = X[tid + e * kTrsvThreads];
     };
     // element e of this thread's share is (rr, kk) of op(T)'s tile
     // (load_tile_d), or (a, b) of the row-major inverse of T_jj (load_inv_d),

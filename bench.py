@@ -122,6 +122,24 @@ def dist_env():
     return world, rank, local
 
 
+def reduce_max(x: float, world: int, device) -> float:
+    """The largest x over the ranks (every rank gets it): the job's time is
+    its slowest replica's."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (replicas: every rank solves its own systems)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -391,12 +409,9 @@ def run_ours(a):
     info = genp.info_fetch(F)
     phase_ms = {p: sum(evs[i][k].elapsed_time(evs[i][k + 1]) for i in range(a.steps)) / a.steps
                 for k, p in enumerate(phases)}
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(total_ms, world, dev)
     ms_per_step = total_ms / a.steps
-    value = world * a.steps / (total_ms / 1e3)
+    value = job_rate(world, a.steps, total_ms)
     fact, ag = flops_per_solve(a)
     tflops = world * (fact + ag) * a.steps / (total_ms / 1e3) / 1e12
 
@@ -458,11 +473,8 @@ def run_ours(a):
         e_ms = e0.elapsed_time(e1)
         # the copy engine's own rate, for the record
         h2d_gbs = h2d_rate()
-        if world > 1:
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": world * k_e2e / (e_ms / 1e3), "unit": "solves/s",
+        e_ms = reduce_max(e_ms, world, dev)
+        e2e = {"value": job_rate(world, k_e2e, e_ms), "unit": "solves/s",
                "h2d_bytes_per_step": A_h.numel() * 8 + B_h.numel() * 8, "d2h_bytes_per_step": X_h[0].numel() * 8,
                "steps": k_e2e, "inputs": "double-buffered: step i+1's copy overlaps step i",
                "seeds": "the timed steps' multiplier seeds",
@@ -721,13 +733,9 @@ def run_batched(a):
             graph.replay()
         e1.record(stream)
         torch.cuda.synchronize()
-    total_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(e0.elapsed_time(e1), world, dev)
     st = plan.status()
-    value = world * count * a.steps / (total_ms / 1e3)
+    value = job_rate(world, count * a.steps, total_ms)
     n3 = sum(float(n) ** 3 for n in sizes)
     fact, ag = 2.0 * n3 / 3.0, (2.0 * n3 if not diff else sum(10.0 * n * n * np.log2(n) for n in sizes))
     tflops = world * (fact + ag) * a.steps / (total_ms / 1e3) / 1e12
@@ -753,7 +761,7 @@ def run_batched(a):
             X_h.copy_(Xp, non_blocking=True)
         f1.record(stream)
         torch.cuda.synchronize()
-        e2e = {"value": world * count * k / (f0.elapsed_time(f1) / 1e3), "unit": "solves/s",
+        e2e = {"value": job_rate(world, count * k, reduce_max(f0.elapsed_time(f1), world, dev)), "unit": "solves/s",
                "h2d_bytes_per_step": A_h.numel() * A_h.element_size() + B_h.numel() * 8,
                "d2h_bytes_per_step": X_h.numel() * 8, "steps": k}
     # one more (eager, untimed) run with the kernel's phase profile on: SM

@@ -262,6 +262,10 @@ GENP_API genp_status genp_precondition(const genp_multiplier *G, const void *A, 
  * C holds L (unit diagonal implied) and the upper triangle holds U.
  *  C      n x n, ld ldc, double for FP64 and BF16_SLICED, float otherwise (caller-owned;
  *         the handle refers to it until destroyed or refactored).
+ *  prec   GENP_FP64, GENP_FP32, GENP_BF16, GENP_BF16X3, GENP_FP8_E4M3 or
+ *         GENP_BF16_SLICED (see genp_prec).
+ *  nb     1 .. 128; 0 picks 128 for the tensor-core arithmetics (BF16,
+ *         BF16X3, FP8_E4M3, BF16_SLICED) and 64 otherwise.
  *  out    receives a new factors handle (status word and workspace).
  * A zero or non-finite pivot does not stop the elimination; its step is
  * recorded (genp_info.breakdown_step, status GENP_ERR_BREAKDOWN) and the

@@ -583,6 +583,40 @@ def gemm_e4m3(Aq, sA, Bq, sB, alpha: float = 1.0, beta: float = 0.0, C=None) -> 
     return D
 
 
+def genp_fp8(C: np.ndarray, nb: int = 128):
+    """Blocked GENP (the block form of Thm. 2.2) with the Schur complement
+    update on e4m3 operands, everything else in FP64: for each nb-wide step,
+    the diagonal block by unblocked GENP, the block row U12 = L11^{-1} C12
+    and the block column L21 = C21 U11^{-1} by substitution, then
+    C22 -= deq(q(L21)) deq(q(U12^T))^T, with q the tile-scaled e4m3
+    quantization (tiles counted from each operand's own origin) and the
+    product of the dequantized operands exact per k-tile (gemm_e4m3).
+    Returns (LU, step) as genp does."""
+    LU = _c(C).copy()
+    n = LU.shape[0]
+    L = lib()
+    step = -1
+    for k0 in range(0, n, nb):
+        kb = min(nb, n - k0)
+        D, s = genp(LU[k0:k0 + kb, k0:k0 + kb])
+        LU[k0:k0 + kb, k0:k0 + kb] = D
+        if s >= 0 and step < 0:
+            step = k0 + s
+        rem = n - k0 - kb
+        if rem == 0:
+            break
+        U12 = _c(LU[k0:k0 + kb, k0 + kb:]).copy()          # L11^{-1} C12
+        L.or_solve_lower_unit(kb, rem, _p(D), kb, _p(U12), rem)
+        L21t = _c(LU[k0 + kb:, k0:k0 + kb].T).copy()       # (C21 U11^{-1})^T = U11^{-T} C21^T
+        L.or_solve_upper_T(kb, rem, _p(D), kb, _p(L21t), rem)
+        LU[k0:k0 + kb, k0 + kb:] = U12
+        LU[k0 + kb:, k0:k0 + kb] = L21t.T
+        qa, sa = quantize_e4m3(L21t.T)
+        qb, sb = quantize_e4m3(U12.T)
+        LU[k0 + kb:, k0 + kb:] -= gemm_e4m3(qa, sa, qb, sb)
+    return LU, step
+
+
 FP8_GRID_SD = 12.5        # bounds every polar-method draw (|z| <= sqrt(2 ln 2^104) < 12.1)
 
 

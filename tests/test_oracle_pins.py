@@ -872,3 +872,66 @@ def test_fp8_grid_multiplier():
     rel = np.abs(G8 - M["G"]) / np.abs(M["G"])
     big = np.abs(q) >= 2.0 ** -6
     assert np.all(rel[big] <= 2.0 ** -4)
+
+
+def test_genp_fp8_is_genp_below_one_block():
+    """n <= nb: no Schur update, so the FP8 blocked GENP is plain GENP."""
+    A = np.random.default_rng(1).standard_normal((100, 100)) + 20 * np.eye(100)
+    LU1, s1 = oracle.genp(A)
+    LU2, s2 = oracle.genp_fp8(A)
+    assert np.array_equal(LU1, LU2) and s1 == s2 == -1
+
+
+def test_genp_fp8_recovers_small_integer_factors_exactly():
+    """C = L0 U0 with small integer factors: every Schur complement is an
+    integer, and the block row and column (entries of L0 and U0, magnitude
+    <= 3) are exact e4m3 values at every tile scale, so the e4m3 Schur
+    products are exact and the blocked factorization returns L0 and U0 bit
+    for bit (a transposed operand, a wrong tile or a wrong scale would not)."""
+    rng = np.random.default_rng(8)
+    n = 300
+    L0 = np.tril(rng.integers(-2, 3, (n, n)), -1) + np.eye(n)
+    U0 = np.triu(rng.integers(-3, 4, (n, n)), 1) + np.diag(rng.choice([-1.0, 1.0, 2.0], n))
+    LU, step = oracle.genp_fp8(L0 @ U0, nb=128)
+    assert step == -1
+    assert np.array_equal(np.tril(LU, -1) + np.eye(n), L0) and np.array_equal(np.triu(LU), U0)
+
+
+def test_genp_fp8_backward_error_bound():
+    """Gaussian data: |L U - C| <= (2^-3 + 2^-7) |L||U| (two e4m3 roundings of
+    2^-4 per Schur product) plus the subnormal codes' absolute error, and the
+    error is genuinely 8-bit (above 1e-3 relative somewhere)."""
+    n = 384
+    A, _, _ = W.lead_deficient(n, 16, 8, 1, seed=3)
+    C = oracle.precondition(A.numpy(), oracle.multiplier(0, n, seed=5))
+    LU, step = oracle.genp_fp8(C)
+    assert step == -1
+    L, U = oracle.split_lu(LU)
+    E = np.abs(L @ U - C)
+    B = np.abs(L) @ np.abs(U)
+    sub = 2 * 2.0 ** -10 / 224 * np.max(np.abs(L)) * np.max(np.abs(U)) * n
+    assert np.all(E <= (2.0 ** -3 + 2.0 ** -7) * B + sub)
+    assert np.max(E / np.maximum(B, 1e-300)) > 1e-3
+
+
+def test_fp8_factors_precondition_only_at_small_growth():
+    """The FP8 reading: with growth ~1 (plain GENP of a Gaussian matrix with a
+    0.1 n diagonal shift) e4m3 factors drive classic FP64 refinement to
+    eta <= 1e-14; the same matrix times a Gaussian multiplier has growth
+    ~1e5, and the refinement does not move eta off ~0.1."""
+    n = 512
+    A, _, B = (t.numpy() for t in W.shifted(1, n, 2, seed=4))
+    A, B = A[0], B[0]
+    LU, _ = oracle.genp_fp8(A)
+    X = oracle.lu_solve(LU, B)
+    for _ in range(8):
+        X = X + oracle.lu_solve(LU, oracle.residual(A, X, B))
+    assert oracle.backward_error(A, X, B) <= 1e-14
+    M = oracle.multiplier(0, n, seed=3)
+    C = oracle.precondition(A, M)
+    LU, _ = oracle.genp_fp8(C)
+    assert np.abs(np.triu(LU)).max() / np.abs(C).max() > 1e4
+    X = oracle.apply_multiplier(M, oracle.lu_solve(LU, B))
+    for _ in range(8):
+        X = X + oracle.apply_multiplier(M, oracle.lu_solve(LU, oracle.residual(A, X, B)))
+    assert oracle.backward_error(A, X, B) > 1e-2

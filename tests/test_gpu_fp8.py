@@ -236,3 +236,24 @@ def test_fp8_refinement_reports_its_error(g):
     eta = oracle.backward_error(A, X.cpu().numpy(), B)
     assert eta == pytest.approx(info.bwd_err[-1], rel=1e-6, abs=1e-15)
     assert g._lib.load().genp_device_check(1) == 0
+
+
+@pytest.mark.parametrize("n,nb", [(300, 128), (256, 64)])
+def test_factor_e4m3_small_integer_factors_bit_exact(g, n, nb):
+    """C = L0 U0 with small integer factors (|L0| <= 2, |U0| <= 3, pivots
+    +-1 or 2): every value the FP8 path forms is an integer exact in FP32,
+    the block row and column are exact e4m3 values at every tile scale, so
+    the GPU factors equal the oracle's FP8 blocked GENP, which equals L0 and
+    U0, bit for bit."""
+    rng = np.random.default_rng(8 + n)
+    L0 = np.tril(rng.integers(-2, 3, (n, n)), -1) + np.eye(n)
+    U0 = np.triu(rng.integers(-3, 4, (n, n)), 1) + np.diag(rng.choice([-1.0, 1.0, 2.0], n))
+    C0 = L0 @ U0
+    assert np.max(np.abs(C0)) < 2.0 ** 20
+    LU_or, step = oracle.genp_fp8(C0, nb=nb)
+    assert step == -1
+    C = torch.as_tensor(C0).to(DEV, torch.float32)
+    F = g.factor(C, prec=g.FP8_E4M3, nb=nb)
+    assert g.info_fetch(F).breakdown_step == -1
+    assert g._lib.load().genp_device_check(1) == 0
+    assert np.array_equal(C.cpu().double().numpy(), LU_or)

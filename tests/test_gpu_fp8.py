@@ -14,7 +14,8 @@
   tensor cores within the product bound;
 * the factorization: |L U - C| <= (2^-3 + 2^-7) |L||U| elementwise (two
   e4m3 roundings of 2^-4 per Schur product, FP32 elsewhere) plus the
-  subnormal codes' absolute error; GMRES-IR takes FP8 factors of a
+  subnormal codes' absolute error; bit-exact against the oracle's FP8
+  blocked GENP on small-integer factors; GMRES-IR takes FP8 factors of a
   well-conditioned system of small growth to backward error <= 1e-14.
 """
 import ctypes

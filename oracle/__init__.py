@@ -87,6 +87,11 @@ def lib():
         L.or_sparse_matmul.argtypes = [_i64, _i64, ctypes.c_int, _dp, _i64, ctypes.c_void_p,
                                        ctypes.c_void_p, _dp, _i64]
         L.or_circ_apply.argtypes = [_i64, _i64, ctypes.c_int, _dp, _dp, _i64, _dp, _i64]
+        L.or_gauss_jordan_inverse.argtypes = [_i64, _dp, _i64, _dp, _i64]
+        L.or_gauss_jordan_inverse.restype = _i64
+        L.or_block_genp.argtypes = [_i64, _dp, _i64, _i64, _dp]
+        L.or_block_genp.restype = _i64
+        L.or_block_lu_solve.argtypes = [_i64, _i64, _dp, _i64, _i64, _dp, _dp, _i64]
         L.or_sparse_apply.argtypes = [_i64, _i64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.c_void_p, _dp, _i64, _dp, _i64]
         _lib = L
@@ -394,6 +399,68 @@ def solve(A: np.ndarray, B: np.ndarray, M: dict, refine_steps: int = 0, tol: flo
         R = residual(A, X, B2)
         D = lu_solve(LU, apply_multiplier(M, R)) if left else apply_multiplier(M, lu_solve(LU, R))
         X = X + D
+        eta.append(backward_error(A, X, B2))
+        if eta[-1] > eta[-2] / 2:
+            break
+    out.update(x=X, eta=eta)
+    return out
+
+
+def gauss_jordan_inverse(P: np.ndarray):
+    """P^{-1} by Gauss-Jordan elimination without pivoting.  Returns (X, step)
+    with step = -1, or the first zero / non-finite pivot."""
+    P = _c(P)
+    kb = P.shape[0]
+    X = np.zeros((kb, kb))
+    t = lib().or_gauss_jordan_inverse(kb, _p(P), kb, _p(X), kb)
+    return X, int(t)
+
+
+def block_genp(C: np.ndarray, nb: int):
+    """Block Gaussian elimination with explicit inverses of the pivot blocks
+    (Sec. 2, the block form of Theorem 2.2), in place on a copy.  Returns
+    (LU, Pinv, step): LU holds L_B below the block diagonal and U_B on and
+    above it (pivot blocks on the diagonal), Pinv[k] the nb x nb slot of
+    P_k^{-1} (top-left kb x kb for a ragged last block), step -1 or the first
+    zero / non-finite pivot."""
+    LU = _c(C).copy()
+    n = LU.shape[0]
+    nblk = (n + nb - 1) // nb
+    Pinv = np.zeros((nblk, nb, nb))
+    k = lib().or_block_genp(n, _p(LU), n, nb, _p(Pinv))
+    return LU, Pinv, int(k)
+
+
+def block_lu_solve(LU: np.ndarray, Pinv: np.ndarray, nb: int, B: np.ndarray) -> np.ndarray:
+    """y = U_B^{-1} L_B^{-1} B: block forward substitution, then block back
+    substitution through the pivot blocks' inverses."""
+    Y = _c(B).copy()
+    if Y.ndim == 1:
+        Y = Y[:, None]
+    n, nrhs = Y.shape
+    lib().or_block_lu_solve(n, nrhs, _p(LU), n, nb, _p(_c(Pinv)), _p(Y), nrhs)
+    return Y
+
+
+def block_solve(A: np.ndarray, B: np.ndarray, M: dict, nb: int, refine_steps: int = 0, tol: float = 0.0):
+    """The method with block GE in place of GENP: C = A G, block GE of C,
+    y = U_B^-1 L_B^-1 b, x = G y, then FP64 refinement r = b - A x,
+    C d = r, x += G d (stopping as in ``solve``).  Returns dict(x, LU, Pinv,
+    step, eta)."""
+    B2 = _c(B).reshape(B.shape[0], -1)
+    C = precondition(A, M)
+    LU, Pinv, step = block_genp(C, nb)
+    out = {"LU": LU, "Pinv": Pinv, "step": step, "C": C}
+    if step >= 0:
+        out.update(x=None, eta=[np.inf])
+        return out
+    X = apply_multiplier(M, block_lu_solve(LU, Pinv, nb, B2))
+    eta = [backward_error(A, X, B2)]
+    for _ in range(refine_steps):
+        if eta[-1] <= tol:
+            break
+        R = residual(A, X, B2)
+        X = X + apply_multiplier(M, block_lu_solve(LU, Pinv, nb, R))
         eta.append(backward_error(A, X, B2))
         if eta[-1] > eta[-2] / 2:
             break

@@ -620,3 +620,130 @@ OR_EXPORT void or_sparse_apply(int64_t n, int64_t nrhs, int trans, int nnz, cons
             }
         }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Block Gaussian elimination with explicit inverses of the pivot blocks     */
+/* (Sec. 2: Theorem 2.2 bounds the norms of the pivot blocks of block        */
+/* Gaussian elimination and of their inverses for a strongly well            */
+/* conditioned matrix).  C is cut into diagonal blocks of order nb (the last */
+/* one ragged).  At step k the leading block of the current Schur complement */
+/* is the pivot block P_k; it is inverted explicitly, the block column below */
+/* it becomes L_ik = S_ik P_k^{-1}, the block row stays (U_kj = S_kj), and   */
+/* the rest is updated, S_ij <- S_ij - L_ik S_kj.  So C = L_B U_B with L_B   */
+/* block unit lower (identity diagonal blocks) and U_B block upper with the  */
+/* pivot blocks on its diagonal.                                             */
+/* ------------------------------------------------------------------------ */
+
+/* X = P^{-1} for the kb x kb block P (ld ldp) by Gauss-Jordan elimination
+ * without pivoting on [P | I]: at step t divide row t by its pivot, then
+ * clear column t from every other row.  X is written with leading dimension
+ * ldx.  Returns -1, or the first step t whose pivot is zero or not finite
+ * (P's leading t+1 minor is singular, or the arithmetic overflowed). */
+OR_EXPORT int64_t or_gauss_jordan_inverse(int64_t kb, const double *P, int64_t ldp, double *X, int64_t ldx) {
+    double *M = (double *)malloc((size_t)(kb * kb > 0 ? kb * kb : 1) * sizeof(double));
+    if (!M) return -2;
+    for (int64_t i = 0; i < kb; ++i)
+        for (int64_t j = 0; j < kb; ++j) {
+            M[i * kb + j] = P[i * ldp + j];
+            X[i * ldx + j] = (i == j) ? 1.0 : 0.0;
+        }
+    for (int64_t t = 0; t < kb; ++t) {
+        double p = M[t * kb + t];
+        if (p == 0.0 || !isfinite(p)) {
+            free(M);
+            return t;
+        }
+        for (int64_t j = 0; j < kb; ++j) {
+            M[t * kb + j] = M[t * kb + j] / p;
+            X[t * ldx + j] = X[t * ldx + j] / p;
+        }
+        for (int64_t i = 0; i < kb; ++i) {
+            if (i == t) continue;
+            double f = M[i * kb + t];
+            for (int64_t j = 0; j < kb; ++j) {
+                M[i * kb + j] = M[i * kb + j] - f * M[t * kb + j];
+                X[i * ldx + j] = X[i * ldx + j] - f * X[t * ldx + j];
+            }
+        }
+    }
+    free(M);
+    return -1;
+}
+
+/* Block GE of C in place.  On return the blocks strictly below the block
+ * diagonal hold L_B, the blocks on and above it hold U_B (the pivot blocks
+ * P_k themselves on the diagonal), and Pinv[k nb nb + r nb + c] holds
+ * (P_k^{-1})[r][c] (a ragged last block of order kb uses its top-left
+ * kb x kb).  Returns -1, or the global index k0 + t of the first zero /
+ * non-finite pivot met while inverting P_k. */
+OR_EXPORT int64_t or_block_genp(int64_t n, double *C, int64_t ldc, int64_t nb, double *Pinv) {
+    double *row = (double *)malloc((size_t)(nb > 0 ? nb : 1) * sizeof(double));
+    if (!row) return -2;
+    for (int64_t k0 = 0; k0 < n; k0 += nb) {
+        const int64_t kb = (n - k0 < nb) ? n - k0 : nb;
+        double *X = Pinv + (k0 / nb) * nb * nb;
+        int64_t t = or_gauss_jordan_inverse(kb, C + k0 * ldc + k0, ldc, X, nb);
+        if (t >= 0) {
+            free(row);
+            return t == -2 ? -2 : k0 + t;
+        }
+        const int64_t e0 = k0 + kb;
+        /* L_ik = S_ik P_k^{-1}, one row at a time */
+        for (int64_t i = e0; i < n; ++i) {
+            double *ci = C + i * ldc + k0;
+            for (int64_t c = 0; c < kb; ++c) {
+                double s = 0.0;
+                for (int64_t r = 0; r < kb; ++r) s = s + ci[r] * X[r * nb + c];
+                row[c] = s;
+            }
+            for (int64_t c = 0; c < kb; ++c) ci[c] = row[c];
+        }
+        /* S_ij <- S_ij - L_ik S_kj */
+#pragma omp parallel for schedule(static) if (n - e0 > 256)
+        for (int64_t i = e0; i < n; ++i) {
+            double *ci = C + i * ldc;
+            for (int64_t r = 0; r < kb; ++r) {
+                const double l = ci[k0 + r];
+                const double *ur = C + (k0 + r) * ldc;
+                for (int64_t j = e0; j < n; ++j) ci[j] = ci[j] - l * ur[j];
+            }
+        }
+    }
+    free(row);
+    return -1;
+}
+
+/* Y <- U_B^{-1} L_B^{-1} Y for block GE factors: block forward substitution
+ * with L_B (z_i = b_i - sum_{k<i} L_ik z_k), then block back substitution
+ * with U_B (y_i = P_i^{-1} (z_i - sum_{j>i} U_ij y_j)). */
+OR_EXPORT void or_block_lu_solve(int64_t n, int64_t nrhs, const double *LU, int64_t ld, int64_t nb,
+                                 const double *Pinv, double *Y, int64_t ldy) {
+    double *tmp = (double *)malloc((size_t)(nb > 0 ? nb : 1) * sizeof(double));
+    if (!tmp) return;
+    for (int64_t c = 0; c < nrhs; ++c) {
+        for (int64_t i0 = 0; i0 < n; i0 += nb) {
+            const int64_t ib = (n - i0 < nb) ? n - i0 : nb;
+            for (int64_t r = 0; r < ib; ++r) {
+                double s = Y[(i0 + r) * ldy + c];
+                for (int64_t k = 0; k < i0; ++k) s = s - LU[(i0 + r) * ld + k] * Y[k * ldy + c];
+                Y[(i0 + r) * ldy + c] = s;
+            }
+        }
+        int64_t last = ((n - 1) / nb) * nb;
+        for (int64_t i0 = last; i0 >= 0; i0 -= nb) {
+            const int64_t ib = (n - i0 < nb) ? n - i0 : nb;
+            const double *X = Pinv + (i0 / nb) * nb * nb;
+            for (int64_t r = 0; r < ib; ++r) {
+                double s = Y[(i0 + r) * ldy + c];
+                for (int64_t j = i0 + ib; j < n; ++j) s = s - LU[(i0 + r) * ld + j] * Y[j * ldy + c];
+                tmp[r] = s;
+            }
+            for (int64_t r = 0; r < ib; ++r) {
+                double s = 0.0;
+                for (int64_t q = 0; q < ib; ++q) s = s + X[r * nb + q] * tmp[q];
+                Y[(i0 + r) * ldy + c] = s;
+            }
+        }
+    }
+    free(tmp);
+}

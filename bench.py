@@ -42,7 +42,7 @@ METRIC = "solves/s & TFLOP/s (2n³/3), BF16+IR vs FP64 GENP, same GB300, bwd err
 KINDS = {"gaussian": 0, "circulant": 1, "sparse": 2, "toeplitz": 5, "householder": 6}
 PRECS = {"fp64": 0, "fp32": 1, "bf16": 2, "fp8": 3, "bf16x3": 4, "sliced": 5}
 # sliced: G drawn on the FP32 grid; fp8: on the FP8 grid (e4m3 times one power of two)
-GRID_OF = {"fp64": 0, "fp32": 1, "bf16": 2, "fp8": 3, "bf16x3": 2, "sliced": 1}
+GRID_OF = {"fp64": 0, "fp32": 1, "bf16": 2, "fp8": 3, "bf16x3": 2, "sliced": 5}
 F64_FACTORS = ("fp64", "sliced")
 
 
@@ -89,6 +89,9 @@ def parse():
                    help="batched: leave systems whose FP32 refinement stalls unconverged (no double-float refactor)")
     p.add_argument("--no-fp64-compare", action="store_true",
                    help="skip timing the FP64 path on the same system (non-FP64 precisions)")
+    p.add_argument("--no-configs", action="store_true",
+                   help="default workload: skip the short measurements of the other configurations "
+                        "(n = 256 and n = 8192 FP64, batched, differentiable) attached to the line")
     return p.parse_args()
 
 
@@ -332,7 +335,7 @@ def run_reference(a):
 
 # ------------------------------------------------------------------ ours (GPU)
 
-def run_ours(a):
+def run_ours(a, emit=True):
     import torch
     import torch.distributed as dist
 
@@ -352,7 +355,8 @@ def run_ours(a):
         A, _, B = W.svd_kappa(n, a.kappa, nrhs, seed=a.seed + rank, device=dev)
         A_cpu, B_cpu = A.cpu(), B.cpu()
     else:
-        A_cpu, _, B_cpu = W.lead_deficient(n, 64, 32, nrhs, seed=a.seed + rank)
+        lead = 32 if n <= 256 else 64          # n = 256: 32 x 32 of rank 16; larger n: 64 x 64 of rank 32
+        A_cpu, _, B_cpu = W.lead_deficient(n, lead, lead // 2, nrhs, seed=a.seed + rank)
         A = A_cpu.to(dev)
         B = B_cpu.to(dev)
     prec = PRECS[a.prec]
@@ -402,8 +406,8 @@ def run_ours(a):
     phases = ["multiplier", "precondition", "factor", "solve", "refine", "adjoint"]
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(a.steps)]
     lib = genp._lib.load()
-    if a.prec in ("sliced", "fp8"):   # CUDA events around every tensor-core launch of the timed region
-        lib.genp_profile_enable(1)
+    # CUDA events around every launch of the profiled kernel classes in the timed region
+    lib.genp_profile_enable(1)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -420,7 +424,8 @@ def run_ours(a):
     launches = genp.launch_count() - l0
     tc_prof = None
     tc_launches = None
-    if a.prec in ("sliced", "fp8"):
+    class_prof = {}
+    if True:
         import ctypes
         cnt = ctypes.c_int()
         lib.genp_profile_launches(None, None, 0, ctypes.byref(cnt))
@@ -428,6 +433,10 @@ def run_ours(a):
             l_ms, l_fl = (ctypes.c_double * cnt.value)(), (ctypes.c_double * cnt.value)()
             lib.genp_profile_launches(l_ms, l_fl, cnt.value, ctypes.byref(cnt))
             tc_launches = (list(l_ms), list(l_fl))
+        for cls in range(6):    # per kernel class: summed ms, algorithmic work, launches
+            c_ms, c_w, c_n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+            if lib.genp_profile_class(cls, ctypes.byref(c_ms), ctypes.byref(c_w), ctypes.byref(c_n)) == 0:
+                class_prof[cls] = (c_ms.value, c_w.value, c_n.value)
         p_ms, p_fl, p_n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
         lib.genp_profile_read(ctypes.byref(p_ms), ctypes.byref(p_fl), ctypes.byref(p_n))
         lib.genp_profile_enable(0)
@@ -520,23 +529,24 @@ def run_ours(a):
         nd = lib.genp_sliced_digits(0)
         pairs = nd * (nd + 1) // 2
         t_ms, t_fl, t_n = tc_prof
-        achieved = t_fl / (t_ms / 1e3) / 1e12
+        # the method's own work: each launch is an FP64-class product of 2 m n K
+        # flop; the tensor pipe runs `pairs` digit products for each of them
+        t_alg = class_prof[0][1] if 0 in class_prof else t_fl / pairs
+        achieved = t_alg / (t_ms / 1e3) / 1e12
+        pipe = t_fl / (t_ms / 1e3) / 1e12
         peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
-        roofline = {"kernel": f"k_tc_sliced<{nd}> (tcgen05 BF16: A G and the Schur updates as {pairs} digit "
-                              f"products per FP64 multiply-add)",
+        roofline = {"kernel": f"k_tc_sliced (tcgen05 BF16 digit products: A G and the Schur updates, FP64-class)",
                     "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                     "peak_source": "measured bf16_tflops_sustained (kernel timed inside a long step)"
                     if "bf16_tflops_sustained" in peaks else "fallback",
                     "launches": t_n, "avg_launch_ms": t_ms / t_n,
                     "share_of_step": (t_ms / a.steps) / ms_per_step,
-                    "algorithmic": f"{pairs} x 2 m n Kpad BF16 flop per launch (digit pairs of the sliced product); "
-                                   f"FP64-equivalent work is 1/{pairs} of it",
-                    # dram read+write bytes of one n = 4096, K = 512 A G chunk launch under ncu
-                    # (294 MB: 143.6 KB per 128 x 64 tile, mostly the double-float accumulator's
-                    # read-modify-write), scaled by the tiles to this size's chunk launches
-                    "traffic": 294.0e6 * (n / 4096) ** 2 if nd == 7 else None,
-                    "traffic_basis": "A G chunk launch (K = 512); Schur-update launches (K = 256) move about "
-                                     "the same bytes per tile for half the flops"}
+                    "algorithmic": "2 m n K flop per launch: the FP64-class product's own work (A G chunks, "
+                                   "Schur updates)",
+                    "tensor_pipe": {"achieved": pipe, "frac": pipe / peak, "unit": "TFLOP/s",
+                                    "counted": "BF16 digit-pair products actually issued (2 m n Kpad per pair)"},
+                    "traffic": None,
+                    "traffic_basis": "not yet captured for this build of the kernel"}
     elif a.prec == "fp8" and tc_launches:
         # per launch: the A G product (K = n, k_tc_e4m3, tensor-bound) and the
         # Schur updates (K = nb <= 128, k_tc_gemm<true>, HBM-bound: C read and
@@ -600,6 +610,7 @@ def run_ours(a):
         roofline = {"kernel": "GENP factor (Schur GEMM dominant)", "bound": "alu", "achieved": achieved,
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz", "traffic": None}
+    roofline["other_kernels"] = other_kernels(class_prof, a.steps, ms_per_step, peaks)
     cpu = None
     if not a.no_cpu_baseline and world == 1:
         n_s = min(n, 2048)
@@ -634,7 +645,8 @@ def run_ours(a):
                                   "precondition": lib.genp_sliced_precondition_digits(0)}
                        if a.prec == "sliced" else None,
                        "A": ("J U diag(sigma) V^T, kappa=%g" % a.kappa) if a.workload == "svd"
-                       else "N(0,1) with leading 64x64 block of rank 32",
+                       else ("N(0,1) with leading 32x32 block of rank 16" if n <= 256
+                             else "N(0,1) with leading 64x64 block of rank 32"),
                        "l2": "inputs larger than L2 (no flush)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "bwd_err_unrefined": info.bwd_err[0] if info.bwd_err else None,
@@ -652,9 +664,78 @@ def run_ours(a):
         line["speedup_vs_fp64"] = value / fp64["value"] if fp64["value"] else None
     if not a.no_clocks:
         line["clocks"] = clk.summary()
+    if not emit:
+        return line
+    if world == 1 and a.workload == "svd" and not a.no_configs:
+        line["configs"] = other_configs(a)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def other_configs(a):
+    """Short measurements of the other workloads, run after the headline one
+    in the same process and attached to its line under "configs" (each its
+    own CUDA-event timing, warm-up and oracle-free checks; no e2e or CPU legs)."""
+    import copy
+    base = copy.copy(a)
+    base.no_e2e = base.no_cpu_baseline = base.no_clocks = base.no_fp64_compare = True
+    base.digits = base.precond_digits = 0
+    base.refine = base.max_iter = None
+    base.count = None
+    runs = [("n256_fp64_gaussian_1rhs", run_ours, dict(workload="lead", n=256, nrhs=1, prec="fp64",
+                                                         kind="gaussian", steps=50, warmup=5))]
+    for kind in ("gaussian", "circulant", "sparse"):
+        runs.append((f"n8192_fp64_{kind}_16rhs", run_ours, dict(workload="lead", n=8192, nrhs=16, prec="fp64",
+                                                                 kind=kind, steps=2, warmup=1)))
+    runs.append(("batched_10k_n16-512", run_batched, dict(workload="batched", steps=5, warmup=3)))
+    runs.append(("diff_256x1024", run_batched, dict(workload="diff", steps=5, warmup=3)))
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "tflops", "roofline", "phases_ms",
+            "bwd_err", "bwd_err_unrefined", "converged", "refine_iters", "gpu_launches_per_step", "bwd_err_max",
+            "converged_fraction", "escalated_double_float", "growth")
+    out = {}
+    for name, fn, over in runs:
+        b = copy.copy(base)
+        for k, v in over.items():
+            setattr(b, k, v)
+        try:
+            line = fn(b, emit=False)
+            out[name] = {k: line[k] for k in keep if k in line}
+        except Exception as exc:          # a side measurement never loses the headline line
+            out[name] = {"error": f"{type(exc).__name__}: {exc}"}
+    return out
+
+
+PROF_CLASSES = {1: ("k_trsv", "streaming triangular solves; bytes = the factor's triangle, n^2/2 x 8 B per pass"),
+                2: ("k_gemv", "x = G y, r = b - A x, the Krylov products A (G v); bytes = the matrix, n^2 x 8 B"),
+                3: ("factor_aux", "factorization off the tensor cores: k_panel_reg, k_trsm_reg, k_gemm<dfloat>; "
+                                  "flops of the diagonal blocks, block rows / columns and inner updates"),
+                4: ("k_outer", "adjoint dA = -Lambda X^T; bytes = dA written"),
+                5: ("precondition_structured", "C = A G by the circulant FFT (k_circ_apply) or the sparse signed "
+                                               "gather (k_sparse_pre); bytes = A read + C written, 16 n^2")}
+
+
+def other_kernels(class_prof, steps, ms_per_step, peaks):
+    """Achieved rate of each profiled kernel class (CUDA events around each
+    launch in the timed region): HBM GB/s of algorithmic bytes against the
+    measured copy rate, or flops for the factorization's latency-bound
+    kernels."""
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    out = {}
+    for cls, (name, what) in PROF_CLASSES.items():
+        if cls not in class_prof or class_prof[cls][2] <= 0 or class_prof[cls][0] <= 0:
+            continue
+        ms_c, w_c, n_c = class_prof[cls]
+        ent = {"launches": n_c, "ms_per_step": ms_c / steps, "share_of_step": (ms_c / steps) / ms_per_step,
+               "counted": what}
+        if cls == 3:
+            ent.update(bound="latency", achieved=w_c / (ms_c / 1e3) / 1e12, unit="TFLOP/s")
+        else:
+            gbs = w_c / (ms_c / 1e3) / 1e9
+            ent.update(bound="hbm", achieved=gbs, unit="GB/s", peak=hbm, frac=gbs / hbm,
+                       peak_source="measured hbm_gbs" if "hbm_gbs" in peaks else "fallback")
+        out[name] = ent
+    return out
 
 
 def fp64_same_gpu(a, genp, A, B, kind, rank, dev):
@@ -698,7 +779,7 @@ def fp64_same_gpu(a, genp, A, B, kind, rank, dev):
             "precision": "fp64 product, fp64 GENP, classic fp64 refinement"}
 
 
-def run_batched(a):
+def run_batched(a, emit=True):
     """Many small systems per step: `batched` (uneven sizes, refinement) or
     `diff` (uniform n = 1024, forward + adjoint), one graph replay per step."""
     import torch
@@ -856,6 +937,8 @@ def run_batched(a):
             "phase_share_of_cta_cycles": phase_share}
     if not a.no_clocks:
         line["clocks"] = clk.summary()
+    if not emit:
+        return line
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

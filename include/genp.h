@@ -186,7 +186,16 @@ GENP_API const char *genp_status_string(genp_status s);
  *              drawn in single precision.  GENP_FP8_E4M3: the single
  *              precision draw rounded to an e4m3 value times 2^e, one e for
  *              the matrix (the least with 12.5 scale <= 448 2^e, so no entry
- *              saturates).  SPARSE,
+ *              saturates).  GENP_BF16_SLICED: the single precision draw
+ *              (as for GENP_FP32) rounded to the
+ *              nearest integer multiple of 2^(E - 13), ties to even, with E
+ *              the least integer such that 12.5 scale <= 2^E: every entry
+ *              then holds two exact 7-bit digits at any column scale, so
+ *              the sliced C = A G (c_prec GENP_BF16_SLICED) forms 13 digit
+ *              products instead of 28 at the same accuracy, and
+ *              x += G d uses that same G.  The rounding moves an entry by at
+ *              most 2^(E - 14) < 1.6e-3 scale, a perturbed Gaussian that
+ *              Thm. 4.1 covers (G = G' + U).  SPARSE,
  *              IDENTITY and HOUSEHOLDER_PM1 ignore it.
  *  out         receives the handle; the library owns G's device storage.
  * Errors: GENP_ERR_ARG, GENP_ERR_NOMEM, GENP_ERR_CUDA. */
@@ -272,6 +281,31 @@ GENP_API genp_status genp_precondition(const genp_multiplier *G, const void *A, 
  * factors are then meaningless.  No pivot threshold is applied. */
 GENP_API genp_status genp_factor(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t nb, void *cuda_stream,
                         genp_factors **out);
+
+/* Block Gaussian elimination of C with explicit inverses of the pivot
+ * blocks (Sec. 2; Theorem 2.2 bounds the norms of the pivot blocks of block
+ * Gaussian elimination and of their inverses for a strongly well
+ * conditioned matrix, as it bounds GENP's pivots).  C is cut into nb x nb
+ * diagonal blocks; at step k the leading block P_k of the current Schur
+ * complement is inverted explicitly (Gauss-Jordan elimination without
+ * pivoting), the block column below it becomes L_ik = S_ik P_k^{-1}, the
+ * block row is kept (U_kj = S_kj), and the trailing matrix is updated,
+ * S_ij <- S_ij - L_ik S_kj.  So C = L_B U_B with L_B block unit lower
+ * (identity diagonal blocks) and U_B block upper with P_k on its diagonal.
+ *  C      n x n FP64, ld ldc, in place (caller-owned; the handle refers to
+ *         it): L_B below the block diagonal, U_B on and above it.  The
+ *         inverses P_k^{-1} are kept in the handle.
+ *  nb     64 (0 picks 64); other orders return GENP_ERR_UNSUPPORTED.
+ *  out    a factors handle of precision GENP_FP64 that genp_solve,
+ *         genp_refine (both methods), genp_adjoint, genp_refactor and
+ *         genp_info_fetch accept like genp_factor's: the solves apply
+ *         P_k^{-1} at each diagonal block.  genp_info's pivots are those met
+ *         inside the Gauss-Jordan inversions (GENP's pivots of C), growth is
+ *         max|U_B| / max|C|, and a zero or non-finite pivot is reported as a
+ *         breakdown at its global step.
+ * Errors: GENP_ERR_ARG, GENP_ERR_UNSUPPORTED, GENP_ERR_NOMEM, GENP_ERR_CUDA. */
+GENP_API genp_status genp_block_factor(double *C, int64_t n, int64_t ldc, int64_t nb, void *cuda_stream,
+                                       genp_factors **out);
 
 /* Factors a new matrix of the same order and precision into an existing
  * handle, reusing its workspace (no allocation). */
@@ -563,6 +597,39 @@ GENP_API int genp_sliced_precondition_digits(int digits);
 GENP_API genp_status genp_profile_enable(int on);
 GENP_API genp_status genp_profile_read(double *ms, double *flops, int *launches);
 GENP_API genp_status genp_profile_launches(double *ms, double *flops, int cap, int *launches);
+/* The same hook by kernel class, each launch counted with its algorithmic
+ * work:
+ *  GENP_PROF_TENSOR (0): the tensor-core launches above; work = the
+ *      product's own flops, 2 m n K per launch (for the sliced product the
+ *      FP64-class product it forms, not its digit products).
+ *  GENP_PROF_TRSV (1): the streaming triangular solves (Sec. 1.1, L U y = b);
+ *      work = bytes of the triangular factor read, n^2 / 2 x 8 B per pass
+ *      and RHS chunk (FP64 or double-float factors; 4 B per entry for FP32).
+ *  GENP_PROF_GEMV (2): matrix-vector products (x = G y, r = b - A x, the
+ *      Krylov products A (G v)); work = bytes of the matrix read, m k x
+ *      element size per launch.
+ *  GENP_PROF_FACTOR_AUX (3): the factorization's kernels off the tensor
+ *      cores (diagonal blocks, block row and column, inner updates of the
+ *      sliced path); work = flops (nb^3 2/3 per diagonal block, nb^2 w per
+ *      block row or column of width w, 2 m n k per inner update).
+ *  GENP_PROF_OUTER (4): the adjoint's dA = -Lambda X^T; work = bytes of dA
+ *      written.
+ *  GENP_PROF_PRECOND (5): C = A G for the circulant (FFT) and sparse
+ *      (signed gather) multipliers in FP64; work = 16 n^2 bytes (A read, C
+ *      written).
+ * Returns the summed time (ms), work and launch count of class `cls` since
+ * the last genp_profile_enable, synchronizing on their events; does not
+ * restart the count.  Launches that returned at once because the
+ * device-steered refinement had already stopped (classes 1 and 2) count
+ * their time and launch but not their work.  GENP_ERR_ARG for another
+ * class. */
+#define GENP_PROF_TENSOR 0
+#define GENP_PROF_TRSV 1
+#define GENP_PROF_GEMV 2
+#define GENP_PROF_FACTOR_AUX 3
+#define GENP_PROF_OUTER 4
+#define GENP_PROF_PRECOND 5
+GENP_API genp_status genp_profile_class(int cls, double *ms, double *work, int *launches);
 
 /* Synchronizes the device and reports whether any kernel of this library
  * that waits on the device (the tensor-core pipelines, the persistent
@@ -591,8 +658,11 @@ GENP_API genp_status genp_device_check(int clear);
  * streams, or two host threads enqueueing at once) race and corrupt each
  * other's result.  Serialize them on one stream.
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  No cudaMalloc, cudaFree or allocating library
+ * (cudaGetSymbolAddress, with that device current) and keeps it for the
+ * life of the process; make that first call before any stream capture.
+ * cudaDeviceReset unloads the array with the rest of the module, so the
+ * kept address is stale afterwards: do not call this entry point on a
+ * device after resetting it in the same process.  No cudaMalloc, cudaFree or allocating library
  * routine is called.  Errors: GENP_ERR_ARG, GENP_ERR_CUDA. */
 #define GENP_NOALLOC_MAX_ENTRIES (1 << 20)
 GENP_API genp_status genp_make_sparse_noalloc(int64_t n, int nnz_per_col, uint64_t seed, uint64_t stream_id,

@@ -18,6 +18,7 @@ construction, and its +-1 circulant is not the multiplier used here).
 from __future__ import annotations
 
 import ctypes
+import math
 import itertools
 import os
 from fractions import Fraction
@@ -701,6 +702,25 @@ def fp8_grid(G: np.ndarray, scale: float) -> np.ndarray:
 # --------------------------------------------------------------------------
 # Exact references used by the pins
 # --------------------------------------------------------------------------
+
+def sliced_grid_exponent(scale: float) -> int:
+    """E, the least integer with 12.5 scale <= 2^E (12.5 standard deviations
+    bound every polar draw)."""
+    amax = 12.5 * float(scale)
+    if not amax > 0.0:
+        return 0
+    f, p = math.frexp(amax)
+    return p - 1 if f == 0.5 else p
+
+
+def sliced_grid(G: np.ndarray, scale: float) -> np.ndarray:
+    """The multiplier rounded to the fixed-point grid of the sliced product:
+    the nearest integer multiple of 2^(E - 13), ties to even (Thm. 4.1's
+    perturbed Gaussian G = G' + U with |U| <= 2^(E - 14)).  The library
+    rounds its single precision draw (``multiplier(..., grid="fp32")``)."""
+    E = sliced_grid_exponent(scale)
+    return np.ldexp(np.rint(np.ldexp(_c(G), 13 - E)), E - 13)
+
 
 def det_leibniz(M) -> Fraction:
     """det(M) = sum over permutations of sign(p) prod_i m[i, p(i)], exact in

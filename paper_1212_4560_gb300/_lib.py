@@ -17,6 +17,7 @@ STATUS_NAMES = {0: "GENP_OK", -1: "GENP_ERR_ARG", -2: "GENP_ERR_BREAKDOWN", -3: 
 
 GAUSSIAN, CIRCULANT, SPARSE_PM1, CIRCULANT_PM1, IDENTITY, TOEPLITZ, HOUSEHOLDER_PM1 = 0, 1, 2, 3, 4, 5, 6
 RIGHT, LEFT = 0, 1
+PROF_TENSOR, PROF_TRSV, PROF_GEMV, PROF_FACTOR_AUX, PROF_OUTER, PROF_PRECOND = 0, 1, 2, 3, 4, 5
 FP64, FP32, BF16, FP8_E4M3, BF16X3, BF16_SLICED = 0, 1, 2, 3, 4, 5
 MAX_REFINE = 32
 
@@ -56,6 +57,7 @@ SIGNATURES = {
     "genp_profile_enable": (_int, [_int]),
     "genp_profile_read": (_int, [_vp, _vp, _vp]),
     "genp_profile_launches": (_int, [_vp, _vp, _int, _vp]),
+    "genp_profile_class": (_int, [_int, _vp, _vp, _vp]),
     "genp_device_check": (_int, [_int]),
     "genp_batched_plan_create": (_int, [_i64, _vp, _i64, _int, _int, _int, _dbl, _int, _vp, ctypes.POINTER(_vp)]),
     "genp_batched_layout": (_int, [_vp, _vp, _vp]),
@@ -73,6 +75,7 @@ SIGNATURES = {
     "genp_precondition": (_int, [_vp, _vp, _i64, _int, _vp, _i64, _int, _vp]),
     "genp_factor": (_int, [_vp, _i64, _i64, _int, _i64, _vp, ctypes.POINTER(_vp)]),
     "genp_refactor": (_int, [_vp, _vp, _i64, _vp]),
+    "genp_block_factor": (_int, [_vp, _i64, _i64, _i64, _vp, ctypes.POINTER(_vp)]),
     "genp_factors_destroy": (None, [_vp]),
     "genp_solve": (_int, [_vp, _vp, _vp, _i64, _i64, _vp, _i64, _vp]),
     "genp_refine": (_int, [_vp, _i64, _vp, _vp, _vp, _i64, _i64, _vp, _i64, _dbl, _int, _int, _vp]),

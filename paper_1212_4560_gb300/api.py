@@ -127,6 +127,17 @@ def factor(C: torch.Tensor, prec: int | None = None, nb: int = 0, stream=None) -
     return Factors(h, C, prec)
 
 
+def block_factor(C: torch.Tensor, nb: int = 64, stream=None) -> Factors:
+    """genp_block_factor: in-place block Gaussian elimination of the FP64
+    matrix C with explicit inverses of its nb x nb pivot blocks."""
+    if C.dtype != torch.float64:
+        raise ValueError("block GE takes an FP64 matrix")
+    h = ctypes.c_void_p()
+    check(_lib.load().genp_block_factor(_ptr(C), C.size(0), _ld(C), nb, _stream(stream), ctypes.byref(h)),
+          "genp_block_factor")
+    return Factors(h, C, FP64)
+
+
 def refactor(F: Factors, C: torch.Tensor, stream=None) -> None:
     check(_lib.load().genp_refactor(F.handle, _ptr(C), _ld(C), _stream(stream)), "genp_refactor")
     F.C = C
@@ -182,9 +193,10 @@ def solve_system(A: torch.Tensor, B: torch.Tensor, kind: int = GAUSSIAN, seed: i
     X = U^-1 L^-1 G B.  Returns (X, info, G, F)."""
     n = A.size(0)
     f64 = prec in (FP64, BF16_SLICED)
-    # FP32-grid draws for every non-FP64 factorization (the sliced path reads
-    # them as exact FP64 values)
-    grid = FP64 if prec == FP64 else (BF16 if prec in (BF16, BF16X3) else (FP8_E4M3 if prec == FP8_E4M3 else FP32))
+    # FP32-grid draws for the FP32 factorization, BF16 / FP8 grids for the
+    # tensor-core ones, and the sliced product's two-digit fixed-point grid for
+    # the sliced one (A G then forms 13 digit products instead of 28)
+    grid = {FP64: FP64, BF16: BF16, BF16X3: BF16, FP8_E4M3: FP8_E4M3, BF16_SLICED: BF16_SLICED}.get(prec, FP32)
     G = make_multiplier(kind, n, seed, value_grid=grid, stream=stream, side=side)
     C = torch.empty((n, n), dtype=torch.float64 if f64 else torch.float32, device=A.device)
     A64 = A if A.dtype == torch.float64 else A.double()

@@ -235,7 +235,7 @@ genp_status genp_make_multiplier(genp_mult_kind kind, int64_t n, uint64_t seed, 
     if (kind != GENP_MULT_SPARSE_PM1 && !(scale > 0.0 && isfinite(scale))) return GENP_ERR_ARG;
     if (kind == GENP_MULT_SPARSE_PM1 && (nnz_per_col < 1 || nnz_per_col > 16)) return GENP_ERR_ARG;
     if (value_grid != GENP_FP64 && value_grid != GENP_FP32 && value_grid != GENP_BF16 &&
-        value_grid != GENP_FP8_E4M3)
+        value_grid != GENP_FP8_E4M3 && value_grid != GENP_BF16_SLICED)
         return GENP_ERR_ARG;
     cudaStream_t s = S(cuda_stream);
     genp_multiplier *G = new (std::nothrow) genp_multiplier();
@@ -253,7 +253,8 @@ genp_status genp_make_multiplier(genp_mult_kind kind, int64_t n, uint64_t seed, 
     cudaError_t ce = cudaSuccess;
     if (kind == GENP_MULT_GAUSSIAN) {
         st = dalloc(&G->dense, (size_t)n * n);
-        if (st == GENP_OK && value_grid != GENP_FP64) st = dalloc(&G->dense_f32, (size_t)n * n);
+        if (st == GENP_OK && value_grid != GENP_FP64 && value_grid != GENP_BF16_SLICED)
+            st = dalloc(&G->dense_f32, (size_t)n * n);
         if (st == GENP_OK && value_grid == GENP_BF16) st = dalloc(&G->dense_bf16, (size_t)n * round8(n));
     } else if (kind == GENP_MULT_IDENTITY) {
         // nothing to store
@@ -354,6 +355,14 @@ genp_status genp_profile_enable(int on) {
 genp_status genp_profile_launches(double *ms, double *flops, int cap, int *launches) {
     if (!launches || cap < 0 || (cap > 0 && !ms && !flops)) return GENP_ERR_ARG;
     const int c = tc_profile_launches(ms, flops, cap);
+    if (c < 0) return GENP_ERR_CUDA;
+    *launches = c;
+    return GENP_OK;
+}
+
+genp_status genp_profile_class(int cls, double *ms, double *work, int *launches) {
+    if (!ms || !work || !launches || cls < kProfTensor || cls >= kProfClasses) return GENP_ERR_ARG;
+    const int c = profile_class_read(cls, ms, work);
     if (c < 0) return GENP_ERR_CUDA;
     *launches = c;
     return GENP_OK;
@@ -543,6 +552,8 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
         const double *a = static_cast<const double *>(A);
         if (c_prec == GENP_BF16_SLICED && G->kind == GENP_MULT_GAUSSIAN) {
             const int nd = sliced_precond_digits();
+            // G on the sliced grid is exact in two digits: 13 digit products instead of 28
+            const int ndg = (G->grid == GENP_BF16_SLICED && nd >= 5) ? 2 : nd;
             const int64_t ldq = (int64_t)nd * kSlicedChunk, ldd = round8(n);
             char *buf = nullptr;
             const size_t dbytes = (size_t)n * ldd * 8, qbytes = (size_t)n * ldq * sizeof(__nv_bfloat16);
@@ -551,7 +562,7 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
             __nv_bfloat16 *Aq = reinterpret_cast<__nv_bfloat16 *>(buf + dbytes);
             __nv_bfloat16 *Bq = Aq + (size_t)n * ldq;
             int *ex = reinterpret_cast<int *>(Bq + (size_t)n * ldq);
-            CU(sliced_matmul(nd, n, n, n, G->dense, n, a, lda, D, ldd, Aq, Bq, ex, s));
+            CU(sliced_matmul(ndg, n, n, n, G->dense, n, a, lda, D, ldd, Aq, Bq, ex, s, nd));
             CU(df_to_f64(D, ldd, static_cast<double *>(C), ldc, n, n, s));
             CU(cudaFreeAsync(buf, s));
             return GENP_OK;
@@ -572,6 +583,8 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
         // digits as genp_sliced_precondition_digits asks), summed in
         // double-float and rounded to FP64 once.
         const int nd = sliced_precond_digits();
+        // G on the sliced grid is exact in two digits: 13 digit products instead of 28
+        const int ndg = (G->grid == GENP_BF16_SLICED && nd >= 5) ? 2 : nd;
         const int64_t ldq = (int64_t)nd * kSlicedChunk, ldd = round8(n);
         char *buf = nullptr;
         const size_t dbytes = (size_t)n * ldd * 8, qbytes = (size_t)n * ldq * sizeof(__nv_bfloat16);
@@ -580,8 +593,16 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
         __nv_bfloat16 *Aq = reinterpret_cast<__nv_bfloat16 *>(buf + dbytes);
         __nv_bfloat16 *Bq = Aq + (size_t)n * ldq;
         int *ex = reinterpret_cast<int *>(Bq + (size_t)n * ldq);
-        CU(sliced_matmul(nd, n, n, n, static_cast<const double *>(A), lda, G->dense, n, D, ldd, Aq, Bq, ex, s));
-        CU(df_to_f64(D, ldd, static_cast<double *>(C), ldc, n, n, s));
+        if (ndg == 2) {
+            // G (two digits) on the M side, A's rows (nd digits) along N: the
+            // product comes out transposed and is turned around on the way to FP64
+            CU(sliced_matmul_t(nd, 2, n, n, n, static_cast<const double *>(A), lda, G->dense, n, D, ldd, Bq, Aq, ex,
+                               s));
+            CU(df_to_f64_T(D, ldd, static_cast<double *>(C), ldc, n, n, s));
+        } else {
+            CU(sliced_matmul(nd, n, n, n, static_cast<const double *>(A), lda, G->dense, n, D, ldd, Aq, Bq, ex, s));
+            CU(df_to_f64(D, ldd, static_cast<double *>(C), ldc, n, n, s));
+        }
         CU(cudaFreeAsync(buf, s));
         return GENP_OK;
     }
@@ -634,11 +655,24 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
                 CU(gemm<double>(n, n, n, 1.0, a, lda, false, G->dense, n, 0.0, nullptr, 0, c, ldc, nullptr, s));
                 break;
             case GENP_MULT_CIRCULANT:
-                if (circ_fft_supported(G->cn))
+                if (circ_fft_supported(G->cn)) {
+                    // algorithmic bytes: A read and C written once (16 n^2)
+                    auto *ev = profile_class_slot(kProfPrecond, 16.0 * (double)n * (double)n);
+                    prof_begin(ev, s);
                     CU((circ_apply<double, double>(G, 0, a, lda, 1, c, ldc, 1, n, nullptr, s)));
-                else CU((circ_matmul_direct<double, double>(G->g, G->cn, n, a, lda, c, ldc, s)));
+                    prof_end(ev, s);
+                } else {
+                    CU((circ_matmul_direct<double, double>(G->g, G->cn, n, a, lda, c, ldc, s)));
+                }
                 break;
-            case GENP_MULT_SPARSE_PM1: CU((sparse_precondition<double, double>(G, a, lda, c, ldc, s))); break;
+            case GENP_MULT_SPARSE_PM1: {
+                // algorithmic bytes: A read and C written once (16 n^2; the indices are 5 nnz n)
+                auto *ev = profile_class_slot(kProfPrecond, 16.0 * (double)n * (double)n);
+                prof_begin(ev, s);
+                CU((sparse_precondition<double, double>(G, a, lda, c, ldc, s)));
+                prof_end(ev, s);
+                break;
+            }
             case GENP_MULT_HOUSEHOLDER_PM1: CU((house_precondition<double, double>(G, a, lda, c, ldc, s))); break;
             default: return GENP_ERR_ARG;
         }
@@ -679,6 +713,11 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
     return GENP_OK;
 }
 
+namespace {
+genp_status new_factors(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t nb, bool block, cudaStream_t s,
+                        genp_factors **out);
+}
+
 genp_status genp_factor(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t nb, void *cuda_stream,
                         genp_factors **out) {
     if (!out) return GENP_ERR_ARG;
@@ -687,9 +726,25 @@ genp_status genp_factor(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t
     if (!factor_prec_ok(prec)) return GENP_ERR_ARG;
     if (nb == 0) nb = (tc_prec(prec) || prec == GENP_BF16_SLICED) ? 128 : 64;
     if (nb < 1 || nb > 128) return GENP_ERR_ARG;
-    cudaStream_t s = S(cuda_stream);
+    return new_factors(C, n, ldc, prec, nb, false, S(cuda_stream), out);
+}
+
+genp_status genp_block_factor(double *C, int64_t n, int64_t ldc, int64_t nb, void *cuda_stream,
+                              genp_factors **out) {
+    if (!out) return GENP_ERR_ARG;
+    *out = nullptr;
+    if (!C || n < 1 || n > 2147483647LL || ldc < n) return GENP_ERR_ARG;
+    if (nb == 0) nb = 64;
+    if (nb != 64) return GENP_ERR_UNSUPPORTED;
+    return new_factors(C, n, ldc, GENP_FP64, nb, true, S(cuda_stream), out);
+}
+
+namespace {
+genp_status new_factors(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t nb, bool block, cudaStream_t s,
+                        genp_factors **out) {
     genp_factors *F = new (std::nothrow) genp_factors();
     if (!F) return GENP_ERR_NOMEM;
+    F->block = block;
     F->C = C;
     F->n = n;
     F->ldc = ldc;
@@ -716,7 +771,7 @@ genp_status genp_factor(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t
         st = dalloc(&F->tcA, (size_t)n * F->tc_ldq);
         if (st == GENP_OK) st = dalloc(&F->tcB, (size_t)n * F->tc_ldq);
         if (st == GENP_OK) st = dalloc(reinterpret_cast<double **>(&F->W), (size_t)n * F->ldw);
-        if (st == GENP_OK) st = dalloc(&F->exps, (size_t)2 * n);
+        if (st == GENP_OK) st = dalloc(&F->exps, (size_t)2 * n + 4 * 128);   // + 2 nb inner-dimension keys (8 B)
         if (st == GENP_OK) st = dalloc(reinterpret_cast<double **>(&F->dinv_df), (size_t)diag_inverse_elems(n));
     }
     if (st == GENP_OK && cudaMallocHost(&F->host_info, sizeof(DevStatus)) != cudaSuccess) {
@@ -735,6 +790,7 @@ genp_status genp_factor(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t
     *out = F;
     return GENP_OK;
 }
+}  // namespace
 
 genp_status genp_refactor(genp_factors *F, void *C, int64_t ldc, void *cuda_stream) {
     if (!F || !C || ldc < F->n) return GENP_ERR_ARG;

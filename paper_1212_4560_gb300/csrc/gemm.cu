@@ -15,6 +15,16 @@ namespace genp {
 
 enum Src { kDense = 0, kCirc = 1, kCircT = 2 };
 
+// Matrix-vector launches that found their skip flag set (the device-steered
+// refinement enqueues steps it may not need): the launch profile counts the
+// work of the others only.
+__device__ unsigned int g_gemv_skipped;
+__device__ __forceinline__ bool gemv_skipped(const int *skip) {
+    if (!(skip && *skip)) return false;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&g_gemv_skipped, 1u);
+    return true;
+}
+
 template <typename T, int BM, int BN, int BK, int TM, int TN, bool TRANSA, int ASRC, int BSRC>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 k_gemm(int64_t m, int64_t n, int64_t k, T alpha, const T *__restrict__ A, int64_t lda,
@@ -134,7 +144,7 @@ template <typename T, int NR, int RW>
 __global__ void __launch_bounds__(256) k_gemv_n(int64_t m, int nr, int64_t k, T alpha, const T *__restrict__ A,
                                                  int64_t lda, const T *__restrict__ B, int64_t ldb, T beta,
                                                  const T *Cin, int64_t ldci, T *D, int64_t ldd, const int *skip) {
-    if (skip && *skip) return;
+    if (gemv_skipped(skip)) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t i0 = ((int64_t)blockIdx.x * 8 + warp) * RW; i0 < m; i0 += (int64_t)gridDim.x * 8 * RW) {
         T acc[RW][NR];
@@ -182,7 +192,7 @@ template <typename T, int NR>
 __global__ void __launch_bounds__(256) k_gemv_t(int64_t m, int nr, int64_t k, T alpha, const T *__restrict__ A,
                                                  int64_t lda, const T *__restrict__ B, int64_t ldb, T beta,
                                                  const T *Cin, int64_t ldci, T *D, int64_t ldd, const int *skip) {
-    if (skip && *skip) return;
+    if (gemv_skipped(skip)) return;
     __shared__ T part[8][32][NR + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t j0 = (int64_t)blockIdx.x * 32; j0 < m; j0 += (int64_t)gridDim.x * 32) {
@@ -222,6 +232,9 @@ template <typename T, int NR>
 cudaError_t run_gemv(int64_t m, int64_t n, int64_t k, T alpha, const T *A, int64_t lda, bool transA, const T *B,
                      int64_t ldb, T beta, const T *Cin, int64_t ldci, T *D, int64_t ldd, const int *skip,
                      cudaStream_t s) {
+    // algorithmic bytes: the m x k matrix read once
+    auto *ev = profile_class_slot(kProfGemv, (double)m * (double)k * (double)sizeof(T));
+    prof_begin(ev, s);
     note_launch();
     if (transA) {
         const int64_t blocks = cdiv(m, 32) < 65535 ? cdiv(m, 32) : 65535;
@@ -233,6 +246,7 @@ cudaError_t run_gemv(int64_t m, int64_t n, int64_t k, T alpha, const T *A, int64
         k_gemv_n<T, NR, RW><<<(unsigned)blocks, 256, 0, s>>>(m, (int)n, k, alpha, A, lda, B, ldb, beta, Cin, ldci,
                                                               D, ldd, skip);
     }
+    prof_end(ev, s);
     return cudaGetLastError();
 }
 
@@ -292,14 +306,31 @@ cudaError_t gemm(int64_t m, int64_t n, int64_t k, T alpha, const T *A, int64_t l
                                               nullptr, 1, s);
 }
 
+unsigned int gemv_skipped_count(bool reset) {
+    unsigned int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_gemv_skipped, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (reset) {
+        const unsigned int z = 0;
+        cudaMemcpyToSymbol(g_gemv_skipped, &z, sizeof(z));
+    }
+    return v;
+}
+
 // D <- D - A B in double-float (the inner block updates of the sliced
 // factorization): the same register-tiled kernel, 64 x 64 tiles, every
 // multiply-add a double-float one on the FP32 pipe.
 cudaError_t gemm_df_sub(int64_t m, int64_t n, int64_t k, const dfloat *A, int64_t lda, const dfloat *B, int64_t ldb,
                         dfloat *D, int64_t ldd, cudaStream_t s) {
     if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
-    return run<dfloat, 64, 64, 16, 4, 4, false, kDense, kDense>(m, n, k, dfloat(-1), A, lda, B, ldb, dfloat(1), D,
-                                                                 ldd, D, ldd, nullptr, nullptr, 1, s);
+    auto *ev = profile_class_slot(kProfFactorAux, 2.0 * (double)m * (double)n * (double)k);
+    prof_begin(ev, s);
+    const cudaError_t e = run<dfloat, 64, 64, 16, 4, 4, false, kDense, kDense>(
+        m, n, k, dfloat(-1), A, lda, B, ldb, dfloat(1), D, ldd, D, ldd, nullptr, nullptr, 1, s);
+    prof_end(ev, s);
+    return e;
 }
 
 template cudaError_t gemm<double>(int64_t, int64_t, int64_t, double, const double *, int64_t, bool,

@@ -641,21 +641,39 @@ __device__ bool mbar_wait_sleep(unsigned long long *b, uint32_t parity, volatile
     return true;
 }
 
-template <int ND>
+// NDA digits of the A operand, NDB of B (an operand whose entries are exact
+// in fewer digits, such as a multiplier on a fixed-point grid, takes fewer
+// and goes on the M side, so the wide operand's digits lie along N):
+// ND = max(NDA, NDB) groups, and A's digit t meets B's digits
+// 0 .. min(NDB, ND - t) - 1 in MMAs of N up to 256 covering
+// 64 min(NDB, ND - t) columns, so every kept pair (t + u <= ND - 1, 0-based)
+// is formed once: NDA = NDB = 7 gives the 28 pairs of the symmetric product,
+// NDA = 2 with NDB = 7 gives 13 (in four MMAs of N = 256, 192, 256, 128 per
+// 16-deep step).
+template <int NDA, int NDB>
 struct SlicedCfg {
-    static constexpr uint32_t kBStage = ND * SBD_BYTES;
-    static constexpr size_t kSmem = 1024 + A_SLOTS * SA_BYTES + 2 * kBStage + STAGE_BYTES + sizeof(SCtl);
+    static constexpr int ND = NDA > NDB ? NDA : NDB;
+    static constexpr int kPairs = [] {
+        int p = 0;
+        for (int t = 0; t < NDA; ++t) p += NDB < ND - t ? NDB : ND - t;
+        return p;
+    }();
+    static constexpr uint32_t kBStage = NDB * SBD_BYTES;
+    static constexpr size_t kNeed = 1024 + A_SLOTS * SA_BYTES + 2 * kBStage + STAGE_BYTES + sizeof(SCtl);
+    // alone on its SM: a second CTA would wait in tcgen05.alloc for the 512
+    // columns, so the request is padded past half of the SM's shared memory
+    static constexpr size_t kSmem = kNeed > 116 * 1024 ? kNeed : 116 * 1024;
     static_assert(64 * ND <= (int)S_TMEM, "group accumulators fit in TMEM");
-    // alone on its SM: a second CTA would wait in tcgen05.alloc for the 512 columns
     static_assert(2 * kSmem > 228 * 1024, "one CTA per SM");
     static_assert(kSmem <= 227 * 1024, "shared memory");
 };
 
-template <int ND>
+template <int NDA, int NDB>
 __global__ void __launch_bounds__(kSlicedThreads, 1)
 k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m, int n, int kpad,
             float alpha, const int *ea, const int *fb, dfloat *D, int64_t ldd) {
-    using Cfg = SlicedCfg<ND>;
+    using Cfg = SlicedCfg<NDA, NDB>;
+    constexpr int ND = Cfg::ND;
     extern __shared__ unsigned char smraw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     unsigned char *sA = base;
@@ -710,10 +728,10 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         break;
                     }
                     mbar_expect_tx(&ctl->bfull[bs], Cfg::kBStage);
-                    for (int u = 0; u < ND; ++u)
+                    for (int u = 0; u < NDB; ++u)
                         tma_2d(sB + bs * Cfg::kBStage + u * SBD_BYTES, &tmB, &ctl->bfull[bs], u * kpad + kt * BK, n0);
                     ctl->issued_b = bi + 1;
-                    for (int t = 0; t < ND; ++t, ++ai) {
+                    for (int t = 0; t < NDA; ++t, ++ai) {
                         const int slot = ai % A_SLOTS;
                         if (ai >= A_SLOTS &&
                             !mbar_wait(&ctl->aempty[slot], (uint32_t)((ai / A_SLOTS) & 1) ^ 1u, abort)) {
@@ -749,7 +767,7 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                     }
                     const uint32_t bbase = sa(sB + bs * Cfg::kBStage);
 #pragma unroll
-                    for (int t = 0; t < ND; ++t) {
+                    for (int t = 0; t < NDA; ++t) {
                         const int slot = ai % A_SLOTS;
                         if (!ok || !mbar_wait(&ctl->afull[slot], (uint32_t)((ai / A_SLOTS) & 1), abort)) {
                             ok = false;
@@ -758,15 +776,32 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                         ++ai;
                         fence_after();
                         const uint64_t ad = sdesc(sa(sA + slot * SA_BYTES));
-                        const int nrows = SBN * (ND - t);          // B digits 1 .. ND - t
+                        const int nu = NDB < ND - t ? NDB : ND - t;   // B digits 0 .. nu - 1 (groups t .. t + nu - 1)
+                        const int nrows = SBN * nu;
+                        // the tile's first MMA into a group overwrites it: digit 0 opens
+                        // groups 0 .. nu - 1; a later digit opens its last group when
+                        // NDB <= ND - t (never when NDB = ND)
+                        const int fresh = (t == 0) ? 0 : (NDB <= ND - t ? nrows - SBN : nrows);
 #pragma unroll
                         for (int k = 0; k < BK / UMMA_K; ++k) {
+                            const bool first = kt == 0 && k == 0;
 #pragma unroll
                             for (int c0 = 0; c0 < nrows; c0 += 256) {
-                                const int nn = nrows - c0 < 256 ? nrows - c0 : 256;
-                                const uint64_t bd = sdesc(bbase + (uint32_t)c0 * 128u);
-                                mma_n(tmem + (uint32_t)(SBN * t + c0), ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2),
-                                      idesc_n(nn), (kt == 0 && t == 0 && k == 0) ? 0u : 1u);
+                                const int c1 = nrows - c0 < 256 ? c0 + (nrows - c0) : c0 + 256;
+                                if (first && fresh > c0 && fresh < c1) {
+                                    // split at the fresh group: accumulate below, overwrite from it on
+                                    mma_n(tmem + (uint32_t)(SBN * t + c0), ad + (uint64_t)(k * 2),
+                                          sdesc(bbase + (uint32_t)c0 * 128u) + (uint64_t)(k * 2), idesc_n(fresh - c0),
+                                          1u);
+                                    mma_n(tmem + (uint32_t)(SBN * t + fresh), ad + (uint64_t)(k * 2),
+                                          sdesc(bbase + (uint32_t)fresh * 128u) + (uint64_t)(k * 2),
+                                          idesc_n(c1 - fresh), 0u);
+                                } else {
+                                    const uint32_t acc = (first && c0 >= fresh) ? 0u : 1u;
+                                    mma_n(tmem + (uint32_t)(SBN * t + c0), ad + (uint64_t)(k * 2),
+                                          sdesc(bbase + (uint32_t)c0 * 128u) + (uint64_t)(k * 2), idesc_n(c1 - c0),
+                                          acc);
+                                }
                             }
                         }
                         commit(&ctl->aempty[slot]);
@@ -894,7 +929,8 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 struct TcProfile {
     bool on = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
-    std::vector<double> fl;       // flops of each recorded launch
+    std::vector<double> fl;       // flops of each recorded launch (as issued)
+    std::vector<double> alg;      // its algorithmic flops (the product's own 2 m n K)
     size_t used = 0;
     double flops = 0.0;
 };
@@ -903,7 +939,7 @@ TcProfile &tc_profile() {
     return p;
 }
 // Events around one launch of `flops` flops, or nullptr when profiling is off.
-std::pair<cudaEvent_t, cudaEvent_t> *profile_slot(double flops) {
+std::pair<cudaEvent_t, cudaEvent_t> *profile_slot(double flops, double alg) {
     TcProfile &p = tc_profile();
     if (!p.on) return nullptr;
     if (p.used == p.ev.size()) {
@@ -915,19 +951,35 @@ std::pair<cudaEvent_t, cudaEvent_t> *profile_slot(double flops) {
         }
         p.ev.emplace_back(a, b);
         p.fl.push_back(0.0);
+        p.alg.push_back(0.0);
     }
     p.fl[p.used] = flops;
+    p.alg[p.used] = alg;
     p.flops += flops;
     return &p.ev[p.used++];
 }
 
-template <int ND>
+// The other kernel classes (genp::ProfClass), kept apart from the
+// tensor-core list so that genp_profile_launches keeps its meaning.
+struct ClassProfile {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    std::vector<double> work;
+    std::vector<int> cls;
+    size_t used = 0;
+};
+ClassProfile &class_profile() {
+    static ClassProfile p;
+    return p;
+}
+
+template <int NDA, int NDB>
 cudaError_t launch_sliced(const CUtensorMap &ma, const CUtensorMap &mb, int64_t m, int64_t n, int64_t kpad,
                           float alpha, const int *ea, const int *fb, dfloat *D, int64_t ldd, cudaStream_t s) {
+    using Cfg = SlicedCfg<NDA, NDB>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_tc_sliced<ND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SlicedCfg<ND>::kSmem);
+        cudaError_t e = cudaFuncSetAttribute(k_tc_sliced<NDA, NDB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Cfg::kSmem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -941,11 +993,12 @@ cudaError_t launch_sliced(const CUtensorMap &ma, const CUtensorMap &mb, int64_t 
     const int64_t tiles = cdiv(m, BM) * cdiv(n, SBN);
     if (tiles > INT32_MAX) return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
-    auto *ev = profile_slot(2.0 * (double)m * (double)n * (double)kpad * (ND * (ND + 1) / 2));
+    auto *ev = profile_slot(2.0 * (double)m * (double)n * (double)kpad * Cfg::kPairs,
+                            2.0 * (double)m * (double)n * (double)kpad);
     if (ev) cudaEventRecord(ev->first, s);
     note_launch();
-    k_tc_sliced<ND><<<grid, kSlicedThreads, SlicedCfg<ND>::kSmem, s>>>(ma, mb, (int)m, (int)n, (int)kpad, alpha, ea,
-                                                                        fb, D, ldd);
+    k_tc_sliced<NDA, NDB><<<grid, kSlicedThreads, Cfg::kSmem, s>>>(ma, mb, (int)m, (int)n, (int)kpad, alpha, ea, fb,
+                                                                     D, ldd);
     if (ev) cudaEventRecord(ev->second, s);
     return cudaGetLastError();
 }
@@ -955,20 +1008,32 @@ cudaError_t launch_sliced(const CUtensorMap &ma, const CUtensorMap &mb, int64_t 
 cudaError_t tc_gemm_sliced(int nd, int64_t m, int64_t n, int64_t kpad, float alpha, const __nv_bfloat16 *Aq,
                            int64_t lda, const __nv_bfloat16 *Bq, int64_t ldb, const int *ea, const int *fb, dfloat *D,
                            int64_t ldd, cudaStream_t s) {
+    return tc_gemm_sliced2(nd, nd, m, n, kpad, alpha, Aq, lda, Bq, ldb, ea, fb, D, ldd, s);
+}
+
+cudaError_t tc_gemm_sliced2(int nda, int ndb, int64_t m, int64_t n, int64_t kpad, float alpha,
+                            const __nv_bfloat16 *Aq, int64_t lda, const __nv_bfloat16 *Bq, int64_t ldb, const int *ea,
+                            const int *fb, dfloat *D, int64_t ldd, cudaStream_t s) {
     if (m <= 0 || n <= 0) return cudaSuccess;
-    if (!sliced::supported(nd)) return cudaErrorInvalidValue;
+    const bool sym = nda == ndb && sliced::supported(nda);
+    const bool twodigit = nda == 2 && ndb >= 5 && ndb <= 7;   // a two-digit M side, the wide operand along N
+    if (!sym && !twodigit) return cudaErrorInvalidValue;
     if (kpad <= 0 || kpad % BK || kpad > kSlicedChunk || m > INT32_MAX || n > INT32_MAX) return cudaErrorInvalidValue;
     if ((lda % 8) || (ldb % 8) || ((uintptr_t)Aq % 16) || ((uintptr_t)Bq % 16)) return cudaErrorInvalidValue;
-    const int64_t kq = (int64_t)nd * kpad;
-    if (lda < kq || ldb < kq) return cudaErrorInvalidValue;
+    const int64_t kqa = (int64_t)nda * kpad, kqb = (int64_t)ndb * kpad;
+    if (lda < kqa || ldb < kqb) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, Aq, m, kq, lda, BM) || !make_map(&mb, Bq, n, kq, ldb, SBN)) return cudaErrorInvalidValue;
-    switch (nd) {
-        case 3: return launch_sliced<3>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
-        case 4: return launch_sliced<4>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
-        case 5: return launch_sliced<5>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
-        case 6: return launch_sliced<6>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
-        default: return launch_sliced<7>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
+    if (!make_map(&ma, Aq, m, kqa, lda, BM) || !make_map(&mb, Bq, n, kqb, ldb, SBN)) return cudaErrorInvalidValue;
+    switch (nda * 8 + ndb) {
+        case 3 * 9: return launch_sliced<3, 3>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
+        case 4 * 9: return launch_sliced<4, 4>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
+        case 5 * 9: return launch_sliced<5, 5>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
+        case 6 * 9: return launch_sliced<6, 6>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
+        case 7 * 9: return launch_sliced<7, 7>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
+        case 2 * 8 + 5: return launch_sliced<2, 5>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
+        case 2 * 8 + 6: return launch_sliced<2, 6>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
+        case 2 * 8 + 7: return launch_sliced<2, 7>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
+        default: return cudaErrorInvalidValue;
     }
 }
 
@@ -1019,7 +1084,7 @@ cudaError_t tc_gemm_e4m3(int64_t m, int64_t n, int64_t K, float alpha, const uin
     if (grid.y > 65535u) return cudaErrorInvalidValue;
     const int vec = ((uintptr_t)D % 16 == 0) && (ldd % 4 == 0) &&
                     (beta == 0.0f || ((uintptr_t)Cin % 16 == 0 && ldci % 4 == 0));
-    auto *ev = profile_slot(2.0 * (double)m * (double)n * (double)K);
+    auto *ev = profile_slot(2.0 * (double)m * (double)n * (double)K, 2.0 * (double)m * (double)n * (double)K);
     if (ev) cudaEventRecord(ev->first, s);
     note_launch();
     if (K <= QBK)   // one k-tile: the scale product joins alpha, two CTAs per SM
@@ -1037,6 +1102,66 @@ void tc_profile_enable(bool on) {
     p.on = on;
     p.used = 0;
     p.flops = 0.0;
+    class_profile().used = 0;
+    trsv_skipped_count(true);
+    gemv_skipped_count(true);
+}
+
+std::pair<cudaEvent_t, cudaEvent_t> *profile_class_slot(int c, double work) {
+    if (!tc_profile().on || c <= 0 || c >= kProfClasses) return nullptr;
+    ClassProfile &p = class_profile();
+    if (p.used == p.ev.size()) {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess) return nullptr;
+        if (cudaEventCreate(&b) != cudaSuccess) {
+            cudaEventDestroy(a);
+            return nullptr;
+        }
+        p.ev.emplace_back(a, b);
+        p.work.push_back(0.0);
+        p.cls.push_back(0);
+    }
+    p.work[p.used] = work;
+    p.cls[p.used] = c;
+    return &p.ev[p.used++];
+}
+
+int profile_class_read(int c, double *ms, double *work) {
+    double t_sum = 0.0, w_sum = 0.0;
+    int count = 0;
+    if (c == kProfTensor) {   // the tensor-core list, counted by algorithmic flops
+        TcProfile &q = tc_profile();
+        for (size_t i = 0; i < q.used; ++i) {
+            if (cudaEventSynchronize(q.ev[i].second) != cudaSuccess) return -1;
+            float t = 0.0f;
+            if (cudaEventElapsedTime(&t, q.ev[i].first, q.ev[i].second) != cudaSuccess) return -1;
+            t_sum += t;
+            w_sum += q.alg[i];
+            ++count;
+        }
+        *ms = t_sum;
+        *work = w_sum;
+        return count;
+    }
+    ClassProfile &p = class_profile();
+    for (size_t i = 0; i < p.used; ++i) {
+        if (p.cls[i] != c) continue;
+        if (cudaEventSynchronize(p.ev[i].second) != cudaSuccess) return -1;
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, p.ev[i].first, p.ev[i].second) != cudaSuccess) return -1;
+        t_sum += t;
+        w_sum += p.work[i];
+        ++count;
+    }
+    // launches that returned on their skip flag did no work; within a class
+    // of one workload the launches carry equal work, so scale by the share
+    // that ran
+    const unsigned int skipped = c == kProfTrsv ? trsv_skipped_count(false)
+                                                : (c == kProfGemv ? gemv_skipped_count(false) : 0u);
+    if (count > 0) w_sum *= (double)(count - (int)(skipped < (unsigned)count ? skipped : count)) / count;
+    *ms = t_sum;
+    *work = w_sum;
+    return count;
 }
 
 int tc_profile_launches(double *ms, double *flops, int cap) {

@@ -1,6 +1,8 @@
 // genp_internal.cuh -- shared declarations of the libgenp translation units.
 #pragma once
 
+#include <utility>
+
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -96,6 +98,7 @@ struct genp_factors {
     int *trsv_sync = nullptr;          // tickets and block counters of the triangular solves
     void *dinv = nullptr;              // inverses of the 64 x 64 diagonal blocks of L and U (factor type)
     void *dinv_df = nullptr;           // their double-float copy (GENP_BF16_SLICED)
+    bool block = false;                // block GE factors (genp_block_factor): C = L_B U_B
     cudaStream_t last_stream = nullptr;
 };
 
@@ -229,11 +232,38 @@ int tc_timeout_flag(bool reset);
 void tc_profile_enable(bool on);
 int tc_profile_read(double *ms, double *flops);
 int tc_profile_launches(double *ms, double *flops, int cap);
+// The other kernel classes of the launch profile, each launch with its
+// algorithmic work (bytes for the HBM-bound classes, flops otherwise).
+enum ProfClass {
+    kProfTensor = 0, kProfTrsv = 1, kProfGemv = 2, kProfFactorAux = 3, kProfOuter = 4, kProfPrecond = 5,
+    kProfClasses = 6
+};
+// Events around one launch of class c, or nullptr when profiling is off.
+std::pair<cudaEvent_t, cudaEvent_t> *profile_class_slot(int c, double work);
+// Sum of the recorded launches of class c (synchronizes on their events);
+// the work of launches that found their skip flag set is left out.
+int profile_class_read(int c, double *ms, double *work);
+// Launches of the triangular solves / matrix-vector products that returned
+// at once on their skip flag (device counters; reset on request).
+unsigned int trsv_skipped_count(bool reset);
+unsigned int gemv_skipped_count(bool reset);
+// Records the start / end event of a launch when ev is not null.
+inline void prof_begin(std::pair<cudaEvent_t, cudaEvent_t> *ev, cudaStream_t s) {
+    if (ev) cudaEventRecord(ev->first, s);
+}
+inline void prof_end(std::pair<cudaEvent_t, cudaEvent_t> *ev, cudaStream_t s) {
+    if (ev) cudaEventRecord(ev->second, s);
+}
 // D += alpha * A B on the tensor cores with FP64-class accuracy, from the
 // nd-digit slices of sliced.cu: Aq (m x nd kpad) and Bq (n x nd kpad, B
 // transposed) with their row / column exponents ea, fb.
 // D is double-float.  alpha must be a power of two (it is applied to both
 // halves of each sum).  kpad <= kSlicedChunk.
+// The same with nda digits of A and ndb of B (nda = ndb = 3 .. 7, or
+// nda = 2 and ndb = 5 .. 7): pairs with t + u <= max(nda, ndb) - 1.
+cudaError_t tc_gemm_sliced2(int nda, int ndb, int64_t m, int64_t n, int64_t kpad, float alpha,
+                            const __nv_bfloat16 *Aq, int64_t lda, const __nv_bfloat16 *Bq, int64_t ldb, const int *ea,
+                            const int *fb, dfloat *D, int64_t ldd, cudaStream_t s);
 cudaError_t tc_gemm_sliced(int nd, int64_t m, int64_t n, int64_t kpad, float alpha, const __nv_bfloat16 *Aq,
                            int64_t lda, const __nv_bfloat16 *Bq, int64_t ldb, const int *ea, const int *fb, dfloat *D,
                            int64_t ldd, cudaStream_t s);
@@ -245,12 +275,21 @@ int sliced_digits();              // digits of the GENP_BF16_SLICED path
 int set_sliced_digits(int nd);    // returns the previous value, -1 if nd is unsupported
 int sliced_precond_digits();      // digits of the sliced C = A G
 int set_sliced_precond_digits(int nd);
-// rows of src (m x K): dst[i][p*kpad + k] = slice p of src[i][k]; exps[i] = row exponent
+// rows of src (m x K): dst[i][p*kpad + k] = slice p of src[i][k] 2^-q_k
+// (kkey null: no scaling; else q_k from kkey[k], see sliced_inner_exps);
+// exps[i] = row exponent
 cudaError_t slice_rows(int nd, const double *src, int64_t lds, int64_t m, int64_t K, __nv_bfloat16 *dst, int64_t ldq,
-                       int *exps, cudaStream_t s);
-// columns of src (K x n), written transposed: dst[j][p*kpad + k]; exps[j] = column exponent
+                       int *exps, cudaStream_t s, const unsigned long long *kkey = nullptr);
+// columns of src (K x n), written transposed: dst[j][p*kpad + k] = slice p of
+// src[k][j] 2^+q_k (kkey may be null); exps[j] = column exponent
 cudaError_t slice_cols_T(int nd, const double *src, int64_t lds, int64_t K, int64_t n, __nv_bfloat16 *dst,
-                         int64_t ldq, int *exps, cudaStream_t s);
+                         int64_t ldq, int *exps, cudaStream_t s, const unsigned long long *kkey = nullptr);
+// keys[k] of max_i |L[i][k]| over the m x K block L, from which the slicing
+// kernels take q_k = e with max_i |L[i][k]| < 2^e: the power-of-two scaling
+// of the inner dimension of L U that balances the columns of L (and,
+// inversely, the rows of U) before slicing
+cudaError_t sliced_inner_exps(const double *L, int64_t ldl, int64_t m, int64_t K, unsigned long long *keys,
+                              cudaStream_t s);
 // double <-> double-float copies of an m x n block
 cudaError_t df_from_f64(const double *src, int64_t lds, dfloat *dst, int64_t ldd, int64_t m, int64_t n,
                         cudaStream_t s);
@@ -261,9 +300,20 @@ cudaError_t df_axpby(double alpha, const dfloat *W, int64_t ldw, double beta, do
                      int64_t n, cudaStream_t s);
 // D (double-float, m x n) = A B, A m x K and B K x n FP64, K cut in chunks of
 // at most kSlicedChunk; Aq, Bq hold (m or n) x kSlicedLdq BF16, exps m + n ints.
+// Dt (double-float, n x m) = (A B)^T = B^T A^T, with B's columns (ndb
+// digits) on the M side and A's rows (nda digits) on the N side: for a B
+// exact in few digits (a multiplier on the sliced grid) the wide operand
+// then sits along N, where one MMA covers several of its digits.
+// Bq holds n x ndb kSlicedChunk, Aq m x nda kSlicedChunk BF16; exps n + m ints.
+cudaError_t sliced_matmul_t(int nda, int ndb, int64_t m, int64_t n, int64_t K, const double *A, int64_t lda,
+                            const double *B, int64_t ldb, dfloat *Dt, int64_t lddt, __nv_bfloat16 *Bq,
+                            __nv_bfloat16 *Aq, int *exps, cudaStream_t s);
+// dst (m x n, FP64) = src^T, src n x m double-float
+cudaError_t df_to_f64_T(const dfloat *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int64_t n,
+                        cudaStream_t s);
 cudaError_t sliced_matmul(int nd, int64_t m, int64_t n, int64_t K, const double *A, int64_t lda, const double *B,
                           int64_t ldb, dfloat *D, int64_t ldd, __nv_bfloat16 *Aq, __nv_bfloat16 *Bq, int *exps,
-                          cudaStream_t s);
+                          cudaStream_t s, int ndb = 0);
 constexpr int64_t kSlicedChunk = 512;   // keeps the digit groups of weight >= 2^-49 exact in FP32
 constexpr int64_t kSlicedLdq = 7 * kSlicedChunk;    // operand width for up to 7 digits
 
@@ -371,6 +421,11 @@ int64_t trsv_sync_ints(int64_t n);
 // elements of F->dinv, and its computation (after every factorization)
 int64_t diag_inverse_elems(int64_t n);
 cudaError_t invert_diag_blocks(genp_factors *F, cudaStream_t s);
+// block.cu: block Gaussian elimination of F->C with explicit pivot-block
+// inverses (nb = 64), the inverses written to F->dinv.
+cudaError_t factor_block(genp_factors *F, cudaStream_t s);
+// lu.cu: max |c_ij| of an n x n FP64 matrix into the status word *out.
+cudaError_t maxabs_f64(const double *C, int64_t n, int64_t ldc, unsigned long long *out, cudaStream_t s);
 cudaError_t outer_update(const double *Lam, int64_t ldl, const double *X, int64_t ldx, int64_t n,
                          int64_t nrhs, void *dA, int64_t ldda, bool dA_f32, cudaStream_t s);
 

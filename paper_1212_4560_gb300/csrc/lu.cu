@@ -302,13 +302,20 @@ cudaError_t panel_and_trsm(TS *C, int64_t ldc, int64_t n, int64_t i0, int kb, De
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
+    auto *ev = profile_class_slot(kProfFactorAux, 2.0 / 3.0 * (double)kb * kb * kb);
+    prof_begin(ev, s);
     note_launch();
     k_panel_reg<TS, TC><<<1, kPanelThreads, 0, s>>>(C, ldc, i0, kb, st);
+    prof_end(ev, s);
     const int64_t rem = n - i0 - kb;
     if (rem <= 0) return cudaGetLastError();
     dim3 g((unsigned)cdiv(rem, kTrsmW), 2);
+    // block row and block column: kb^2 flops per vector of length kb, 2 rem vectors
+    ev = profile_class_slot(kProfFactorAux, 2.0 * (double)kb * kb * (double)rem);
+    prof_begin(ev, s);
     note_launch();
     k_trsm_reg<TS, TC><<<g, kTrsmThreads, (size_t)kb * (kb + 1) * sizeof(TC), s>>>(C, ldc, n, i0, kb, st);
+    prof_end(ev, s);
     return cudaGetLastError();
 }
 
@@ -436,8 +443,14 @@ cudaError_t factor_sliced(genp_factors *F, cudaStream_t s) {
         if (remo <= 0) break;
         const double *L21 = C + e0 * ldc + k0;
         const double *U12 = C + k0 * ldc + e0;
-        e = slice_rows(F->nd, L21, ldc, remo, kbo, F->tcA, ldq, F->exps, s);
-        if (e == cudaSuccess) e = slice_cols_T(F->nd, U12, ldc, kbo, remo, F->tcB, ldq, F->exps + n, s);
+        // GENP scales column k of L21 by 1/u_kk and row k of U12 with the
+        // pivots: a power-of-two balance of the inner dimension (L21 D^-1,
+        // D U12, exact) keeps each slicing row / column within a few binades
+        // (the unrefined backward error drops about a thousandfold)
+        unsigned long long *kexp = reinterpret_cast<unsigned long long *>(F->exps + 2 * n);
+        e = sliced_inner_exps(L21, ldc, remo, kbo, kexp, s);
+        if (e == cudaSuccess) e = slice_rows(F->nd, L21, ldc, remo, kbo, F->tcA, ldq, F->exps, s, kexp);
+        if (e == cudaSuccess) e = slice_cols_T(F->nd, U12, ldc, kbo, remo, F->tcB, ldq, F->exps + n, s, kexp);
         if (e == cudaSuccess)
             e = tc_gemm_sliced(F->nd, remo, remo, sliced_kpad(kbo), -1.0f, F->tcA, ldq, F->tcB, ldq, F->exps,
                                F->exps + n, W + e0 * ldw + e0, ldw, s);
@@ -447,6 +460,12 @@ cudaError_t factor_sliced(genp_factors *F, cudaStream_t s) {
 }
 
 }  // namespace
+
+cudaError_t maxabs_f64(const double *C, int64_t n, int64_t ldc, unsigned long long *out, cudaStream_t s) {
+    note_launch();
+    k_maxabs<double><<<152 * 4, 256, 0, s>>>(C, n, ldc, out);
+    return cudaGetLastError();
+}
 
 cudaError_t status_reset(genp_factors *F, cudaStream_t s) {
     note_launch();
@@ -458,7 +477,7 @@ cudaError_t factor_run(genp_factors *F, cudaStream_t s) {
     cudaError_t e = status_reset(F, s);
     if (e != cudaSuccess) return e;
     switch (F->prec) {
-        case GENP_FP64: e = factor_typed<double, double>(F, s); break;
+        case GENP_FP64: e = F->block ? factor_block(F, s) : factor_typed<double, double>(F, s); break;
         case GENP_FP32: e = factor_typed<float, float>(F, s); break;
         case GENP_BF16:
         case GENP_BF16X3:
@@ -467,7 +486,8 @@ cudaError_t factor_run(genp_factors *F, cudaStream_t s) {
         default: return cudaErrorNotSupported;
     }
     // the solves apply the diagonal blocks of L and U through their inverses
-    if (e == cudaSuccess) e = invert_diag_blocks(F, s);
+    // (block GE writes its pivot blocks' inverses itself)
+    if (e == cudaSuccess && !F->block) e = invert_diag_blocks(F, s);
     return e;
 }
 

@@ -172,21 +172,44 @@ __device__ __forceinline__ double round_to_fp8_grid(double v, int e) {
     return e4m3_round_f64(v * down) * up;
 }
 
+// Fixed-point grid of the sliced product: integer multiples of 2^(E - 13)
+// with E the least integer such that 12.5 scale <= 2^E (12.5 standard
+// deviations bound every polar draw), so |entry| < 2^E holds 14 signed bits
+// at any column scale 2^f <= 2^E: two exact balanced base-128 digits.
+// Rounding to nearest, ties to even.
+__host__ __device__ inline int sliced_grid_exp(double scale) {
+    const double amax = 12.5 * scale;
+    if (!(amax > 0.0)) return 0;
+    int p = 0;
+    const double f = frexp(amax, &p);    // amax = f 2^p, f in [0.5, 1)
+    const int e = f == 0.5 ? p - 1 : p;
+    return e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
+}
+__device__ __forceinline__ double round_to_sliced_grid(double v, int e) {
+    // v 2^(13 - e) and back: exact power-of-two scalings (|e| <= 1000)
+    const double down = __longlong_as_double((long long)(1023 + 13 - e) << 52);
+    const double up = __longlong_as_double((long long)(1023 - 13 + e) << 52);
+    return rint(v * down) * up;
+}
+
 __device__ __forceinline__ double on_grid(double v, genp_prec grid) {
     if (grid == GENP_BF16) return round_to_bf16_grid(v);
     if (grid == GENP_FP32) return (double)__double2float_rn(v);
     return v;
 }
 
-// One Gaussian entry of scale `scale` on the requested grid.  The FP32 and
-// FP8 grids draw by the polar method in FP32 on their own tag (tag + 4); the
-// FP8 grid then rounds that draw to e4m3 times 2^e (the draw's precision is
-// far beyond e4m3's).  The FP64 and BF16 grids draw in FP64.
+// One Gaussian entry of scale `scale` on the requested grid.  The FP32, FP8
+// and sliced grids draw by the polar method in FP32 on their own tag (tag +
+// 4); the FP8 grid then rounds that draw to e4m3 times 2^e and the sliced grid
+// to a multiple of 2^(E - 13) (the draw's 24 bits are far beyond either).
+// The FP64 and BF16 grids draw in FP64.
 __device__ __forceinline__ double draw_on_grid(uint64_t seed, uint64_t sid, uint64_t tag, uint64_t idx, double scale,
                                                genp_prec grid) {
-    if (grid == GENP_FP32 || grid == GENP_FP8_E4M3) {
+    if (grid == GENP_FP32 || grid == GENP_FP8_E4M3 || grid == GENP_BF16_SLICED) {
         const double v = (double)__fmul_rn(polar_normal_f32(seed, sid, tag + 4, idx), __double2float_rn(scale));
-        return grid == GENP_FP32 ? v : round_to_fp8_grid(v, fp8_grid_exp(scale));
+        if (grid == GENP_FP32) return v;
+        return grid == GENP_FP8_E4M3 ? round_to_fp8_grid(v, fp8_grid_exp(scale))
+                                     : round_to_sliced_grid(v, sliced_grid_exp(scale));
     }
     return on_grid(__dmul_rn(polar_normal(seed, sid, tag, idx), scale), grid);
 }

@@ -36,6 +36,28 @@ __device__ __forceinline__ int scale_exp(double amax) {
     return e;
 }
 
+// Ordering key of |x| 2^sc from the IEEE bit pattern (integer work only):
+// the biased exponent moved by sc in 12 bits above the mantissa, so the
+// integer maximum of keys is the key of max |x| 2^sc.  Zero and subnormal
+// x give 0 (too small to set a scale), NaN gives 0, infinity the largest key.
+__device__ __forceinline__ unsigned long long scaled_key(double x, int sc) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+    if (b > 0x7FF0000000000000ull) return 0ull;
+    const int E = (int)(b >> 52);
+    if (E == 0) return 0ull;
+    if (E == 0x7FF) return ~0ull;
+    int t = E + sc;
+    t = t < -2047 ? -2047 : (t > 2047 ? 2047 : t);
+    return ((unsigned long long)(t + 2048) << 52) | (b & 0xFFFFFFFFFFFFFull);
+}
+
+// exponent e with max|x| 2^sc < 2^e from the maximum key (0 for none)
+__device__ __forceinline__ int key_exp(unsigned long long key) {
+    if (key == 0ull) return 0;
+    if (key == ~0ull) return 2047;
+    return (int)(key >> 52) - 2048 - 1022;
+}
+
 // Digits of q = x 2^-e in (-1, 1): X = round(q 2^(7 ND)) (an integer below
 // 2^(7 ND) in magnitude), then its balanced base-128 digits from the
 // bottom: d_t = ((X + 64) mod 128) - 64 in [-64, 63], X <- (X - d_t) / 128;
@@ -45,7 +67,7 @@ __device__ __forceinline__ int scale_exp(double amax) {
 // conversion would run, are scarce.  The dropped remainder is below
 // 2^-(7 ND + 1); a non-finite x gives X = 0.
 template <int ND>
-__device__ __forceinline__ void digits(double x, int e, float (&d)[ND]) {
+__device__ __forceinline__ void digits(double x, int e, float (&d)[ND], int sc = 0) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int E = (int)((b >> 52) & 0x7FF);
     unsigned long long mant = b & 0xFFFFFFFFFFFFFull;
@@ -54,7 +76,7 @@ __device__ __forceinline__ void digits(double x, int e, float (&d)[ND]) {
         mant |= 1ull << 52;
         ex = E - 1075;
     }
-    const int sh = ex + 7 * ND - e;
+    const int sh = ex + sc + 7 * ND - e;            // x 2^sc scaled by 2^-e
     unsigned long long m = 0;
     if (E == 0x7FF || mant == 0) {
         m = 0;
@@ -82,24 +104,34 @@ __device__ __forceinline__ void put(__nv_bfloat16 *row, int64_t kpad, int64_t k,
     for (int t = 0; t < ND; ++t) row[t * kpad + k] = __float2bfloat16_rn(d[t]);
 }
 
-// A operand: rows of src (m x K, FP64, ld lds).  One warp per row.
+// A operand: rows of src (m x K, FP64, ld lds).  One warp per row.  With
+// kexp, entry k of every row is taken as x 2^-kexp[k] (an exact power-of-two
+// scaling of the inner dimension that the B operand undoes; see
+// slice_cols_T).
 template <int ND>
 __global__ void k_slice_rows(const double *src, int64_t lds, int64_t m, int64_t K, int64_t kpad,
-                             __nv_bfloat16 *dst, int64_t ldq, int *exps) {
+                             __nv_bfloat16 *dst, int64_t ldq, int *exps, const unsigned long long *kkey) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp; i < m; i += nw) {
         const double *a = src + i * lds;
+        int e;
         unsigned long long mb = 0ull;
-        for (int64_t k = lane; k < K; k += 32) mb = max(mb, abs_bits(a[k]));
-        for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
-        const int e = scale_exp(__longlong_as_double((long long)mb));
+        if (kkey) {
+            for (int64_t k = lane; k < K; k += 32) mb = max(mb, scaled_key(a[k], -key_exp(kkey[k])));
+            for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+            e = key_exp(mb);
+        } else {
+            for (int64_t k = lane; k < K; k += 32) mb = max(mb, abs_bits(a[k]));
+            for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+            e = scale_exp(__longlong_as_double((long long)mb));
+        }
         if (lane == 0) exps[i] = e;
         __nv_bfloat16 *row = dst + i * ldq;
         for (int64_t k = lane; k < kpad; k += 32) {
             float d[ND] = {};
-            if (k < K) digits<ND>(a[k], e, d);
+            if (k < K) digits<ND>(a[k], e, d, kkey ? -key_exp(kkey[k]) : 0);
             put<ND>(row, kpad, k, d);
         }
     }
@@ -109,25 +141,52 @@ __global__ void k_slice_rows(const double *src, int64_t lds, int64_t m, int64_t 
 // (row j of dst holds column j).  Pass 1: column exponents; a CTA takes 32
 // columns, its 8 warps split the rows (coalesced 256-byte rows per warp),
 // and the 8 partial maxima meet in shared memory.
-__global__ void k_col_exps(const double *src, int64_t lds, int64_t K, int64_t n, int *exps) {
+// With kkey, row k of src is taken as x 2^+q_k, q_k = key_exp(kkey[k]).
+__global__ void k_col_exps(const double *src, int64_t lds, int64_t K, int64_t n, int *exps,
+                           const unsigned long long *kkey) {
     __shared__ unsigned long long part[8][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int64_t j = (int64_t)blockIdx.x * 32 + tx;
     unsigned long long mb = 0ull;
-    if (j < n)
-        for (int64_t k = ty; k < K; k += 8) mb = max(mb, abs_bits(src[k * lds + j]));
+    if (j < n) {
+        if (kkey)
+            for (int64_t k = ty; k < K; k += 8) mb = max(mb, scaled_key(src[k * lds + j], key_exp(kkey[k])));
+        else
+            for (int64_t k = ty; k < K; k += 8) mb = max(mb, abs_bits(src[k * lds + j]));
+    }
     part[ty][tx] = mb;
     __syncthreads();
     if (ty == 0 && j < n) {
         for (int w = 1; w < 8; ++w) mb = max(mb, part[w][tx]);
-        exps[j] = scale_exp(__longlong_as_double((long long)mb));
+        exps[j] = kkey ? key_exp(mb) : scale_exp(__longlong_as_double((long long)mb));
+    }
+}
+
+// Column maximum keys of an m x K block (the inner-dimension scaling of the
+// sliced Schur update): a CTA takes 32 columns and a strip of rows, its 8
+// warps split the strip, and the strip's maximum goes to keys[k] by atomicMax
+// (keys cleared before).
+__global__ void k_col_keys(const double *src, int64_t lds, int64_t m, int64_t K, unsigned long long *keys) {
+    __shared__ unsigned long long part[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t k = (int64_t)blockIdx.x * 32 + tx;
+    const int64_t rows = (m + gridDim.y - 1) / gridDim.y;
+    const int64_t r0 = (int64_t)blockIdx.y * rows, r1 = r0 + rows < m ? r0 + rows : m;
+    unsigned long long mb = 0ull;
+    if (k < K)
+        for (int64_t i = r0 + ty; i < r1; i += 8) mb = max(mb, scaled_key(src[i * lds + k], 0));
+    part[ty][tx] = mb;
+    __syncthreads();
+    if (ty == 0 && k < K) {
+        for (int w = 1; w < 8; ++w) mb = max(mb, part[w][tx]);
+        if (mb) atomicMax(keys + k, mb);
     }
 }
 
 // Pass 2: 32 x 32 tiles through shared memory so both sides stay coalesced.
 template <int ND>
 __global__ void k_slice_cols_T(const double *src, int64_t lds, int64_t K, int64_t n, int64_t kpad,
-                               __nv_bfloat16 *dst, int64_t ldq, const int *exps) {
+                               __nv_bfloat16 *dst, int64_t ldq, const int *exps, const unsigned long long *kkey) {
     __shared__ double tile[32][33];
     const int64_t k0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
@@ -140,7 +199,7 @@ __global__ void k_slice_cols_T(const double *src, int64_t lds, int64_t K, int64_
         const int64_t j = j0 + r, k = k0 + tx;
         if (j < n && k < kpad) {
             float d[ND] = {};
-            if (k < K) digits<ND>(tile[tx][r], exps[j], d);
+            if (k < K) digits<ND>(tile[tx][r], exps[j], d, kkey ? key_exp(kkey[k]) : 0);
             put<ND>(dst + j * ldq, kpad, k, d);
         }
     }
@@ -168,6 +227,23 @@ __global__ void k_df_axpby(double alpha, const dfloat *W, int64_t ldw, double be
         }
 }
 
+// dst (m x n, FP64) = src^T (src n x m, double-float), 32 x 32 tiles through
+// shared memory so reads and writes stay coalesced.
+__global__ void k_df_to_f64_T(const dfloat *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int64_t n) {
+    __shared__ double tile[32][33];
+    const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;   // dst rows i, columns j
+    const int tx = threadIdx.x, ty = threadIdx.y;                                // 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t j = j0 + r, i = i0 + tx;                                    // src[j][i]
+        tile[r][tx] = (j < n && i < m) ? (double)src[j * lds + i] : 0.0;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t i = i0 + r, j = j0 + tx;
+        if (i < m && j < n) dst[i * ldd + j] = tile[tx][r];
+    }
+}
+
 dim3 block_grid(int64_t m, int64_t n) {
     const int64_t gx = cdiv(n, 256) < 8 ? cdiv(n, 256) : 8;
     return dim3((unsigned)gx, (unsigned)(m < 65535 ? m : 65535));
@@ -193,40 +269,56 @@ int set_sliced_precond_digits(int nd) {
 }
 
 cudaError_t slice_rows(int nd, const double *src, int64_t lds, int64_t m, int64_t K, __nv_bfloat16 *dst, int64_t ldq,
-                       int *exps, cudaStream_t s) {
+                       int *exps, cudaStream_t s, const unsigned long long *kexp) {
     if (m <= 0) return cudaSuccess;
-    if (!sliced::supported(nd) || ldq < nd * sliced_kpad(K)) return cudaErrorInvalidValue;
+    if (nd < 2 || nd > 7 || ldq < nd * sliced_kpad(K)) return cudaErrorInvalidValue;
     int blocks = (int)((m + 7) / 8);
     if (blocks > 152 * 16) blocks = 152 * 16;
     const int64_t kpad = sliced_kpad(K);
     note_launch();
     switch (nd) {
-        case 3: k_slice_rows<3><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps); break;
-        case 4: k_slice_rows<4><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps); break;
-        case 5: k_slice_rows<5><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps); break;
-        case 6: k_slice_rows<6><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps); break;
-        default: k_slice_rows<7><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps); break;
+        case 2: k_slice_rows<2><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
+        case 3: k_slice_rows<3><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
+        case 4: k_slice_rows<4><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
+        case 5: k_slice_rows<5><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
+        case 6: k_slice_rows<6><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
+        default: k_slice_rows<7><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
     }
     return cudaGetLastError();
 }
 
 cudaError_t slice_cols_T(int nd, const double *src, int64_t lds, int64_t K, int64_t n, __nv_bfloat16 *dst,
-                         int64_t ldq, int *exps, cudaStream_t s) {
+                         int64_t ldq, int *exps, cudaStream_t s, const unsigned long long *kexp) {
     if (n <= 0) return cudaSuccess;
     const int64_t kpad = sliced_kpad(K);
-    if (!sliced::supported(nd) || ldq < nd * kpad) return cudaErrorInvalidValue;
+    if (nd < 2 || nd > 7 || ldq < nd * kpad) return cudaErrorInvalidValue;
     note_launch();
-    k_col_exps<<<(unsigned)cdiv(n, 32), 256, 0, s>>>(src, lds, K, n, exps);
+    k_col_exps<<<(unsigned)cdiv(n, 32), 256, 0, s>>>(src, lds, K, n, exps, kexp);
     dim3 g((unsigned)cdiv(n, 32), (unsigned)cdiv(kpad, 32));
     if (g.y > 65535u) return cudaErrorInvalidValue;
     note_launch();
     switch (nd) {
-        case 3: k_slice_cols_T<3><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps); break;
-        case 4: k_slice_cols_T<4><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps); break;
-        case 5: k_slice_cols_T<5><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps); break;
-        case 6: k_slice_cols_T<6><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps); break;
-        default: k_slice_cols_T<7><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps); break;
+        case 2: k_slice_cols_T<2><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
+        case 3: k_slice_cols_T<3><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
+        case 4: k_slice_cols_T<4><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
+        case 5: k_slice_cols_T<5><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
+        case 6: k_slice_cols_T<6><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
+        default: k_slice_cols_T<7><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t sliced_inner_exps(const double *L, int64_t ldl, int64_t m, int64_t K, unsigned long long *keys,
+                              cudaStream_t s) {
+    if (K <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(keys, 0, (size_t)K * sizeof(unsigned long long), s);
+    if (e != cudaSuccess || m <= 0) return e;
+    // about two CTAs per SM over the strips
+    const int64_t gx = cdiv(K, 32);
+    int64_t gy = (152 * 2 + gx - 1) / gx;
+    gy = gy < cdiv(m, 64) ? gy : cdiv(m, 64);
+    note_launch();
+    k_col_keys<<<dim3((unsigned)gx, (unsigned)(gy > 0 ? gy : 1)), 256, 0, s>>>(L, ldl, m, K, keys);
     return cudaGetLastError();
 }
 
@@ -246,6 +338,16 @@ cudaError_t df_to_f64(const dfloat *src, int64_t lds, double *dst, int64_t ldd, 
     return cudaGetLastError();
 }
 
+cudaError_t df_to_f64_T(const dfloat *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int64_t n,
+                        cudaStream_t s) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    dim3 g((unsigned)cdiv(n, 32), (unsigned)cdiv(m, 32));
+    if (g.y > 65535u) return cudaErrorInvalidValue;
+    note_launch();
+    k_df_to_f64_T<<<g, dim3(32, 8), 0, s>>>(src, lds, dst, ldd, m, n);
+    return cudaGetLastError();
+}
+
 cudaError_t df_axpby(double alpha, const dfloat *W, int64_t ldw, double beta, double *D, int64_t ldd, int64_t m,
                      int64_t n, cudaStream_t s) {
     if (m <= 0 || n <= 0) return cudaSuccess;
@@ -256,15 +358,35 @@ cudaError_t df_axpby(double alpha, const dfloat *W, int64_t ldw, double beta, do
 
 cudaError_t sliced_matmul(int nd, int64_t m, int64_t n, int64_t K, const double *A, int64_t lda, const double *B,
                           int64_t ldb, dfloat *D, int64_t ldd, __nv_bfloat16 *Aq, __nv_bfloat16 *Bq, int *exps,
-                          cudaStream_t s) {
+                          cudaStream_t s, int ndb) {
     if (m <= 0 || n <= 0) return cudaSuccess;
+    const int nda = nd;
+    if (ndb <= 0) ndb = nd;
     cudaError_t e = cudaMemset2DAsync(D, (size_t)ldd * sizeof(dfloat), 0, (size_t)n * sizeof(dfloat), (size_t)m, s);
     for (int64_t k0 = 0; k0 < K && e == cudaSuccess; k0 += kSlicedChunk) {
         const int64_t kc = K - k0 < kSlicedChunk ? K - k0 : kSlicedChunk;
-        const int64_t kpad = sliced_kpad(kc), ldq = nd * kpad;
-        e = slice_rows(nd, A + k0, lda, m, kc, Aq, ldq, exps, s);
-        if (e == cudaSuccess) e = slice_cols_T(nd, B + k0 * ldb, ldb, kc, n, Bq, ldq, exps + m, s);
-        if (e == cudaSuccess) e = tc_gemm_sliced(nd, m, n, kpad, 1.0f, Aq, ldq, Bq, ldq, exps, exps + m, D, ldd, s);
+        const int64_t kpad = sliced_kpad(kc), lda_q = nda * kpad, ldb_q = ndb * kpad;
+        e = slice_rows(nda, A + k0, lda, m, kc, Aq, lda_q, exps, s);
+        if (e == cudaSuccess) e = slice_cols_T(ndb, B + k0 * ldb, ldb, kc, n, Bq, ldb_q, exps + m, s);
+        if (e == cudaSuccess)
+            e = tc_gemm_sliced2(nda, ndb, m, n, kpad, 1.0f, Aq, lda_q, Bq, ldb_q, exps, exps + m, D, ldd, s);
+    }
+    return e;
+}
+
+cudaError_t sliced_matmul_t(int nda, int ndb, int64_t m, int64_t n, int64_t K, const double *A, int64_t lda,
+                            const double *B, int64_t ldb, dfloat *Dt, int64_t lddt, __nv_bfloat16 *Bq,
+                            __nv_bfloat16 *Aq, int *exps, cudaStream_t s) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemset2DAsync(Dt, (size_t)lddt * sizeof(dfloat), 0, (size_t)m * sizeof(dfloat), (size_t)n, s);
+    for (int64_t k0 = 0; k0 < K && e == cudaSuccess; k0 += kSlicedChunk) {
+        const int64_t kc = K - k0 < kSlicedChunk ? K - k0 : kSlicedChunk;
+        const int64_t kpad = sliced_kpad(kc), ldq_b = ndb * kpad, ldq_a = nda * kpad;
+        // M side: the columns of B (ndb digits); N side: the rows of A (nda digits)
+        e = slice_cols_T(ndb, B + k0 * ldb, ldb, kc, n, Bq, ldq_b, exps, s);
+        if (e == cudaSuccess) e = slice_rows(nda, A + k0, lda, m, kc, Aq, ldq_a, exps + n, s);
+        if (e == cudaSuccess)
+            e = tc_gemm_sliced2(ndb, nda, n, m, kpad, 1.0f, Bq, ldq_b, Aq, ldq_a, exps, exps + n, Dt, lddt, s);
     }
     return e;
 }

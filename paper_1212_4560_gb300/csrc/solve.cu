@@ -154,6 +154,56 @@ __global__ void k_outer(const double *Lam, int64_t ldl, const double *X, int64_t
     }
 }
 
+// dA[i][j] = - sum_c Lam[i][c] X[j][c] as a streaming write (nrhs <= NR): a
+// CTA covers 32 rows and 1024 columns, each thread 4 adjacent columns whose
+// X rows it keeps in registers, and every row goes out as one contiguous
+// 1 KiB (FP64) store per warp.  vec: 16-byte aligned rows (ldda % 4 == 0,
+// aligned base), so the 4 values go out as 16- or 32-byte vector stores.
+template <typename TD, int NR>
+__global__ void __launch_bounds__(256) k_outer_rows(const double *Lam, int64_t ldl, const double *X, int64_t ldx,
+                                                    int64_t n, int nrhs, TD *dA, int64_t ldda, int vec) {
+    __shared__ double sl[32][NR];
+    const int64_t i0 = (int64_t)blockIdx.y * 32;
+    const int64_t j = ((int64_t)blockIdx.x * 256 + threadIdx.x) * 4;
+    for (int idx = threadIdx.x; idx < 32 * NR; idx += 256) {
+        const int r = idx / NR, c = idx % NR;
+        sl[r][c] = (i0 + r < n && c < nrhs) ? Lam[(i0 + r) * ldl + c] : 0.0;
+    }
+    double xr[4][NR];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int c = 0; c < NR; ++c) xr[q][c] = (j + q < n && c < nrhs) ? X[(j + q) * ldx + c] : 0.0;
+    __syncthreads();
+    if (j >= n) return;
+    const bool full = vec && j + 3 < n;
+    for (int r = 0; r < 32; ++r) {
+        const int64_t i = i0 + r;
+        if (i >= n) break;
+        double v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            double acc = 0.0;
+#pragma unroll
+            for (int c = 0; c < NR; ++c) acc = fma(sl[r][c], xr[q][c], acc);
+            v[q] = -acc;
+        }
+        TD *row = dA + i * ldda + j;
+        if (full) {
+            if constexpr (sizeof(TD) == 8) {
+                reinterpret_cast<double2 *>(row)[0] = make_double2(v[0], v[1]);
+                reinterpret_cast<double2 *>(row)[1] = make_double2(v[2], v[3]);
+            } else {
+                *reinterpret_cast<float4 *>(row) = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (j + q < n) row[q] = (TD)v[q];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Triangular solves op(T) Y = Y in one persistent launch.  T is cut into
 // 64 x 64 tiles and the diagonal blocks are taken one after the other (block
@@ -317,6 +367,10 @@ __device__ __forceinline__ void tile_gemv(const T (*M)[TB + 1], const T (*V)[NR]
     }
 }
 
+// Triangular-solve launches that found their skip flag set (see
+// gemv_skipped_count): the launch profile counts the work of the others only.
+__device__ unsigned int g_trsv_skipped;
+
 // mode 0: L (unit lower, forward)    mode 1: U (upper, backward)
 // mode 2: U^T (lower, forward)       mode 3: L^T (unit upper, backward)
 // Tile (i, j) of op(T): element (r, k) = op(T)[i TB + r][j TB + k].
@@ -334,13 +388,20 @@ template <typename TS, typename T, int NR, bool DD>
 __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc, int n, const TS *Dinv, T *Y,
                                                         int64_t ldy, int nr, int mode, const int *skip, int *sync,
                                                         const dfloat *Cd, int64_t ldcd, const dfloat *Dinvd) {
-    if (skip && *skip) return;
+    if (skip && *skip) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&g_trsv_skipped, 1u);
+        return;
+    }
     extern __shared__ __align__(16) unsigned char smraw[];
     TrsvSmem<T, NR> &sm = *reinterpret_cast<TrsvSmem<T, NR> *>(smraw);
     TrsvSmemDD<NR> &sd = *reinterpret_cast<TrsvSmemDD<NR> *>(smraw);
     __shared__ int s_ticket;
     const int tid = threadIdx.x;
     const int nblk = (n + TB - 1) / TB;
+    // mode bit 2: factors of block GE (identity diagonal blocks in L, whole
+    // pivot blocks on U's diagonal); bits 0-1: the pass, as above
+    const bool bge = (mode & 4) != 0;
+    mode &= 3;
     const bool forward = (mode == 0 || mode == 2);
     const bool unit = (mode == 0 || mode == 3);
     int *ticket = sync, *cnt = sync + 2, *ready = sync + 2 + nblk;
@@ -373,8 +434,13 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
             const int a = idx >> 6, b = idx & 63;
             const int rr = mode <= 1 ? a : b, kk = mode <= 1 ? b : a;
             T val = v[e];
-            if (rr == kk) val = unit ? T(1) : val;
-            else if (forward ? kk > rr : kk < rr) val = T(0);
+            if (bge) {
+                if (unit) val = rr == kk ? T(1) : T(0);   // L_B: identity diagonal blocks; U_B: the pivot block
+            } else if (rr == kk) {
+                val = unit ? T(1) : val;
+            } else if (forward ? kk > rr : kk < rr) {
+                val = T(0);
+            }
             sm.D[rr][kk] = val;
         }
     };
@@ -415,7 +481,9 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
             const int a = idx >> 6, b = idx & 63;
             const int rr = mode <= 1 ? a : b, kk = mode <= 1 ? b : a;
             dfloat val = v[e];
-            if (kind == 1) {     // the diagonal tile: its triangle, unit diagonal where op(T) has one
+            if (kind == 1 && bge) {   // block GE: identity (L_B) or the whole pivot block (U_B)
+                if (unit) val = rr == kk ? dfloat(1.0f) : dfloat(0.0f);
+            } else if (kind == 1) {   // the diagonal tile: its triangle, unit diagonal where op(T) has one
                 if (rr == kk) val = unit ? dfloat(1.0f) : val;
                 else if (forward ? kk > rr : kk < rr) val = dfloat(0.0f);
             }
@@ -670,9 +738,14 @@ cudaError_t launch_trsv(const TS *C, int64_t ldc, int64_t n, const TS *Dinv, T *
     const int64_t nblk = cdiv(n, TB);
     cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)(2 + 2 * nblk) * sizeof(int), s);
     if (e != cudaSuccess) return e;
+    // algorithmic bytes: the triangle of the factor read once (double-float
+    // pairs are 8 B like FP64)
+    auto *ev = profile_class_slot(kProfTrsv, 0.5 * (double)n * (double)n * (DD ? 8.0 : (double)sizeof(TS)));
+    prof_begin(ev, s);
     note_launch();
     k_trsv<TS, T, NR, DD><<<grid, kTrsvThreads, sm, s>>>(C, ldc, (int)n, Dinv, Y, ldy, nr, mode, skip, sync, Cd,
                                                           ldcd, Dinvd);
+    prof_end(ev, s);
     return cudaGetLastError();
 }
 
@@ -687,7 +760,7 @@ cudaError_t solve_typed(const genp_factors *F, T *Y, int64_t ldy, int64_t nrhs, 
         T *Yc = Y + c0;
         for (int pass = 0; pass < 2; ++pass) {
             // pass 0: L (or U^T) forward; pass 1: U (or L^T) backward
-            const int mode = transposed ? (pass == 0 ? 2 : 3) : (pass == 0 ? 0 : 1);
+            const int mode = (transposed ? (pass == 0 ? 2 : 3) : (pass == 0 ? 0 : 1)) | (F->block ? 4 : 0);
             const TS *D = static_cast<const TS *>(F->dinv);
             int *sy = F->trsv_sync;
             cudaError_t e = cudaSuccess;
@@ -730,6 +803,20 @@ cudaError_t solve_typed(const genp_factors *F, T *Y, int64_t ldy, int64_t nrhs, 
 }
 
 }  // namespace
+
+unsigned int trsv_skipped_count(bool reset) {
+    unsigned int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_trsv_skipped, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (reset) {
+        const unsigned int z = 0;
+        cudaMemcpyToSymbol(g_trsv_skipped, &z, sizeof(z));
+    }
+    return v;
+}
+
 
 template <typename T>
 cudaError_t lu_solve_inplace(const genp_factors *F, T *Y, int64_t ldy, int64_t nrhs, bool transposed, const int *skip,
@@ -831,13 +918,27 @@ cudaError_t refine_check(genp_factors *F, const double *R, int64_t ldr, const do
 cudaError_t outer_update(const double *Lam, int64_t ldl, const double *X, int64_t ldx, int64_t n, int64_t nrhs,
                          void *dA, int64_t ldda, bool dA_f32, cudaStream_t s) {
     dim3 g((unsigned)cdiv(n, 32), (unsigned)cdiv(n, 32));
-    if (dA_f32) {
+    auto *ev = profile_class_slot(kProfOuter, (double)n * (double)n * (dA_f32 ? 4.0 : 8.0));
+    prof_begin(ev, s);
+    if (nrhs <= 4 && cdiv(n, 32) <= 65535) {
+        const dim3 gr((unsigned)cdiv(n, 1024), (unsigned)cdiv(n, 32));
+        const int vec = (ldda % 4 == 0) && ((uintptr_t)dA % 32 == 0);
+        note_launch();
+        if (dA_f32) {
+            if (nrhs == 1) k_outer_rows<float, 1><<<gr, 256, 0, s>>>(Lam, ldl, X, ldx, n, 1, (float *)dA, ldda, vec);
+            else k_outer_rows<float, 4><<<gr, 256, 0, s>>>(Lam, ldl, X, ldx, n, (int)nrhs, (float *)dA, ldda, vec);
+        } else {
+            if (nrhs == 1) k_outer_rows<double, 1><<<gr, 256, 0, s>>>(Lam, ldl, X, ldx, n, 1, (double *)dA, ldda, vec);
+            else k_outer_rows<double, 4><<<gr, 256, 0, s>>>(Lam, ldl, X, ldx, n, (int)nrhs, (double *)dA, ldda, vec);
+        }
+    } else if (dA_f32) {
         note_launch();
         k_outer<float><<<g, 256, 0, s>>>(Lam, ldl, X, ldx, n, (int)nrhs, (float *)dA, ldda);
     } else {
         note_launch();
         k_outer<double><<<g, 256, 0, s>>>(Lam, ldl, X, ldx, n, (int)nrhs, (double *)dA, ldda);
     }
+    prof_end(ev, s);
     return cudaGetLastError();
 }
 

@@ -382,19 +382,21 @@ def test_refinement_reports_history(g):
 
 # ---------------------------------------------------------------- FP32 path
 
-@pytest.mark.parametrize("kind", [0, 1, 2])
-def test_fp32_factor_with_fp64_refinement(g, kind):
+@pytest.mark.parametrize("kind,method", [(0, 1), (1, 0), (2, 0), (1, 1), (2, 1)])
+def test_fp32_factor_with_fp64_refinement(g, kind, method):
+    """FP32 factors, FP64 refinement, eta <= 1e-14 for every multiplier.
+    Classic refinement (method 0) contracts by u32 kappa(C) growth per step;
+    with the dense Gaussian multiplier (kappa(G) ~ 3n) that ratio nears 1/2
+    and the stop rule (eta must halve) can end it just above 1e-14, so the
+    dense case takes GMRES-IR (method 1), which needs the factors only as a
+    preconditioner; the structured multipliers are checked with both."""
     n, nrhs = 256, 4
     A, _, B = (t.numpy() for t in W.shifted(1, n, nrhs, seed=4))
     A, B = A[0], B[0]
     X, info, G, F = g.solve_system(cu(A, torch.float32), cu(B), kind=kind, seed=2, prec=g.FP32, refine_steps=12,
-                                   tol=1e-16)
+                                   tol=1e-16, method=method)
     A32 = A.astype(np.float32).astype(np.float64)       # the matrix actually solved
-    # The dense Gaussian multiplier (kappa(G) ~ 3n) leaves FP32 factors whose
-    # refinement contracts by about 1/2 per step near the end, so the
-    # halving rule stops it a little above 1e-14; the structured multipliers
-    # reach the target.
-    assert oracle.backward_error(A32, host(X), B) <= (1e-13 if kind == 0 else 1e-14)
+    assert oracle.backward_error(A32, host(X), B) <= 1e-14
     assert info.bwd_err[0] > 1e-10                      # FP32 factors before refinement
 
 

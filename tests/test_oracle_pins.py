@@ -746,6 +746,65 @@ def test_numerical_rank_degenerate_ranges():
 
 
 # --------------------------------------------------------------------------
+# Fixed-point grid of the sliced product
+# --------------------------------------------------------------------------
+
+def _balanced_digits(X, nd):
+    """Balanced base-128 digits of integers X (most significant first), by
+    Python integer arithmetic: X = sum_t d_t 128^(nd-1-t)."""
+    out = []
+    for x in X:
+        x = int(x)
+        ds = []
+        for _ in range(nd - 1):
+            lo = ((x + 64) % 128) - 64
+            ds.append(lo)
+            x = (x - lo) // 128
+        ds.append(x)
+        out.append(ds[::-1])
+    return np.array(out)
+
+
+@pytest.mark.parametrize("n", [64, 300, 1024])
+def test_sliced_grid_exact_in_two_digits(n):
+    """Every column of the gridded Gaussian, scaled by its own power of two
+    2^-f (f the least with max |g| < 2^f) and by 2^14, is an integer below
+    2^14 in magnitude, and two balanced 7-bit digits rebuild it exactly
+    (|d_1| <= 128, |d_2| <= 64): the two-digit slicing loses nothing."""
+    s = 1.0 / math.sqrt(n)
+    G = oracle.sliced_grid(oracle.multiplier(0, n, seed=n, grid="fp32")["G"], s)
+    for j in range(n):
+        col = G[:, j]
+        f = math.frexp(float(np.abs(col).max()))[1]
+        X = np.ldexp(col, 14 - f)
+        assert np.array_equal(X, np.round(X))
+        assert np.abs(X).max() < 2**14
+        d = _balanced_digits(X, 2)
+        assert np.abs(d[:, 0]).max() <= 128 and np.abs(d[:, 1]).max() <= 64
+        assert np.array_equal(d[:, 0] * 128 + d[:, 1], X.astype(np.int64))
+
+
+def test_sliced_grid_rounding_and_exponent():
+    """E is the least integer with 12.5 scale <= 2^E; entries move to the
+    nearest multiple of 2^(E-13) (error <= 2^(E-14)), ties to even; the grid
+    keeps the Gaussian's moments (a perturbation of at most 1.6e-3 scale)."""
+    for scale in (1.0, 1 / 64, 1 / math.sqrt(300), 0.08, 12.5 ** -1, 3.0):
+        E = oracle.sliced_grid_exponent(scale)
+        assert 12.5 * scale <= 2.0 ** E and 12.5 * scale > 2.0 ** (E - 1)
+    n = 512
+    s = 1.0 / math.sqrt(n)
+    G0 = oracle.multiplier(0, n, seed=3)["G"]
+    G = oracle.sliced_grid(G0, s)
+    q = 2.0 ** (oracle.sliced_grid_exponent(s) - 13)
+    assert np.abs(G - G0).max() <= q / 2
+    assert np.array_equal(G / q, np.round(G / q))
+    assert abs(G.std() / s - 1) < 0.01 and abs(G.mean()) < 0.01 * s
+    # ties to even, by hand
+    T = np.array([[0.5 * q, 1.5 * q, 2.5 * q, -0.5 * q, -1.5 * q]])
+    assert np.array_equal(oracle.sliced_grid(T, s) / q, [[0.0, 2.0, 2.0, -0.0, -2.0]])
+
+
+# --------------------------------------------------------------------------
 # Block Gaussian elimination with explicit pivot-block inverses (Sec. 2,
 # Theorem 2.2's block form)
 # --------------------------------------------------------------------------

@@ -63,6 +63,17 @@ def test_noalloc_matches_allocating_path_twice(genp_lib):
             assert np.array_equal(isg[t][r[t]], s[t])
 
 
+def test_noalloc_accepts_exactly_its_scratch(genp_lib):
+    """n * nnz_per_col equal to GENP_NOALLOC_MAX_ENTRIES (2^20) fills the
+    scratch array to its last entry and must still match the allocating path."""
+    n, nnz = 1 << 18, 4
+    rows, signs, _, _ = _noalloc(genp_lib, n, nnz, 5, 1, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    ref_rows, ref_signs = _allocating(n, nnz, 5, 1)
+    assert np.array_equal(rows.cpu().numpy(), ref_rows)
+    assert np.array_equal(signs.cpu().numpy(), ref_signs)
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch(genp_lib):
     lib = genp_lib
     limit = 1 << 20

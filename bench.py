@@ -66,10 +66,12 @@ def parse():
     p.add_argument("--kind", default="gaussian", choices=list(KINDS))
     p.add_argument("--seed", type=int, default=0)
     p.add_argument("--tol", type=float, default=1e-14)
-    p.add_argument("--workload", default="svd", choices=["lead", "svd", "batched", "diff", "table71", "lowrank"],
+    p.add_argument("--workload", default="svd",
+                   choices=["lead", "svd", "batched", "diff", "small", "table71", "lowrank"],
                    help="lead: N(0,1) A with a rank-deficient leading block; svd: A = J U diag(sigma) V^T; "
                         "batched: 10k systems n in [16,512], a11 = 0, FP32 factors + FP64 refinement; "
                         "diff: 256 x n=1024 FP32 systems, circulant G, 8 RHS, forward + adjoint; "
+                        "small: one n x n system of the lead recipe through the one-launch batched kernel; "
                         "table71: the paper-shaped Table 7.1 experiment (+-1 circulant multipliers, 100 systems "
                         "per n in 64, 256, 1024, residuals after 0 and 1 refinement steps, and plain GENP); "
                         "lowrank: the paper-shaped Tables 7.2 / 7.3 experiment (randomized rank-q approximation)")
@@ -294,6 +296,8 @@ def run_reference_batched(a):
     sec = statistics.mean(per)
     value = count / sec
     name = "batched_10k_n16-512_fp32_fp64ir_4rhs" if not diff else "diff_256x1024_fp32_circulant_8rhs"
+    if small:
+        name = f"onelaunch_n{a.n}_fp32_fp64ir_{nrhs}rhs"
     sample = f"oracle pipeline on the first {done} systems of the batch (~4 s per step), scaled by sum n^3"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
@@ -684,10 +688,14 @@ def other_configs(a):
     base.refine = base.max_iter = None
     base.count = None
     runs = [("n256_fp64_gaussian_1rhs", run_ours, dict(workload="lead", n=256, nrhs=1, prec="fp64",
-                                                         kind="gaussian", steps=50, warmup=5))]
+                                                         kind="gaussian", steps=50, warmup=5)),
+            ("n256_onelaunch_fp32_fp64ir_1rhs", run_batched, dict(workload="small", n=256, nrhs=1, steps=50,
+                                                                  warmup=5))]
     for kind in ("gaussian", "circulant", "sparse"):
         runs.append((f"n8192_fp64_{kind}_16rhs", run_ours, dict(workload="lead", n=8192, nrhs=16, prec="fp64",
                                                                  kind=kind, steps=2, warmup=1)))
+    runs.append(("n8192_sliced_gaussian_16rhs", run_ours, dict(workload="lead", n=8192, nrhs=16, prec="sliced",
+                                                               kind="gaussian", steps=3, warmup=2)))
     runs.append(("batched_10k_n16-512", run_batched, dict(workload="batched", steps=5, warmup=3)))
     runs.append(("diff_256x1024", run_batched, dict(workload="diff", steps=5, warmup=3)))
     keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "tflops", "roofline", "phases_ms",
@@ -797,7 +805,19 @@ def run_batched(a, emit=True):
     from paper_1212_4560_gb300 import build as _b
     _b.build()
     diff = a.workload == "diff"
-    if diff:
+    small = a.workload == "small"
+    if small:
+        # one system through the one-launch batched kernel (count 1): the
+        # n = 256 recipe, FP32 factors in one CTA, FP64 refinement
+        count, nrhs = 1, a.nrhs
+        sizes = [a.n]
+        lead = 32 if a.n <= 256 else 64
+        A1, _, B1 = W.lead_deficient(a.n, lead, lead // 2, nrhs, seed=a.seed + rank)
+        plan = Bt.BatchedPlan(sizes, nrhs, kind=genp.GAUSSIAN, a_dtype=torch.float64,
+                              max_iter=10 if a.max_iter is None else a.max_iter, tol=a.tol, escalate=True)
+        Ap = A1.reshape(-1).to(dev).contiguous()
+        Bp = B1.reshape(-1).to(dev).contiguous()
+    elif diff:
         count = a.count or 256
         nrhs = 8
         sizes = [1024] * count
@@ -902,7 +922,7 @@ def run_batched(a, emit=True):
             dist.destroy_process_group()
         return
     cpu = None
-    if not a.no_cpu_baseline and world == 1:
+    if not a.no_cpu_baseline and world == 1 and not small:
         t, done = oracle_batch_seconds(a, sizes, 15.0)
         cpu = {"value": count / t, "unit": "solves/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
                "sample": f"oracle pipeline on the first {done} systems of the batch (~15 s), scaled to the "
@@ -911,8 +931,9 @@ def run_batched(a, emit=True):
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": name, "count": count, "nrhs": nrhs, "sizes": "uniform [16, 512]" if not diff
-                       else "1024", "multiplier": "gaussian" if not diff else "circulant",
+            "config": {"workload": name, "count": count, "nrhs": nrhs,
+                       "sizes": (str(a.n) if small else ("uniform [16, 512]" if not diff else "1024")),
+                       "multiplier": "gaussian" if not diff else "circulant",
                        "precision": "fp32 factors" + (", fp64 refinement" if not diff else ", forward + adjoint"),
                        "l2": "inputs larger than L2 (no flush)", "graph": "one CUDA graph replay per step",
                        "block_sizes": {str(nn): plan.block_size(nn) for nn in (16, 128, 512, 1024)}},
@@ -1064,7 +1085,7 @@ def main():
         run_lowrank(a)
     elif a.impl == "reference":
         run_reference(a)
-    elif a.workload in ("batched", "diff"):
+    elif a.workload in ("batched", "diff", "small"):
         run_batched(a)
     else:
         run_ours(a)

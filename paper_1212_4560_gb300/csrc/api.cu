@@ -554,7 +554,7 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
             const int nd = sliced_precond_digits();
             // G on the sliced grid is exact in two digits: 13 digit products instead of 28
             const int ndg = (G->grid == GENP_BF16_SLICED && nd >= 5) ? 2 : nd;
-            const int64_t ldq = (int64_t)nd * kSlicedChunk, ldd = round8(n);
+            const int64_t ldq = (int64_t)nd * (ndg == 2 ? kSlicedChunk2 : kSlicedChunk), ldd = round8(n);
             char *buf = nullptr;
             const size_t dbytes = (size_t)n * ldd * 8, qbytes = (size_t)n * ldq * sizeof(__nv_bfloat16);
             CU(cudaMallocAsync((void **)&buf, dbytes + 2 * qbytes + (size_t)2 * n * sizeof(int) + 256, s));
@@ -585,7 +585,7 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
         const int nd = sliced_precond_digits();
         // G on the sliced grid is exact in two digits: 13 digit products instead of 28
         const int ndg = (G->grid == GENP_BF16_SLICED && nd >= 5) ? 2 : nd;
-        const int64_t ldq = (int64_t)nd * kSlicedChunk, ldd = round8(n);
+        const int64_t ldq = (int64_t)nd * (ndg == 2 ? kSlicedChunk2 : kSlicedChunk), ldd = round8(n);
         char *buf = nullptr;
         const size_t dbytes = (size_t)n * ldd * 8, qbytes = (size_t)n * ldq * sizeof(__nv_bfloat16);
         CU(cudaMallocAsync((void **)&buf, dbytes + 2 * qbytes + (size_t)2 * n * sizeof(int) + 256, s));

@@ -1018,7 +1018,8 @@ cudaError_t tc_gemm_sliced2(int nda, int ndb, int64_t m, int64_t n, int64_t kpad
     const bool sym = nda == ndb && sliced::supported(nda);
     const bool twodigit = nda == 2 && ndb >= 5 && ndb <= 7;   // a two-digit M side, the wide operand along N
     if (!sym && !twodigit) return cudaErrorInvalidValue;
-    if (kpad <= 0 || kpad % BK || kpad > kSlicedChunk || m > INT32_MAX || n > INT32_MAX) return cudaErrorInvalidValue;
+    const int64_t kmax = nda == 2 ? kSlicedChunk2 : kSlicedChunk;
+    if (kpad <= 0 || kpad % BK || kpad > kmax || m > INT32_MAX || n > INT32_MAX) return cudaErrorInvalidValue;
     if ((lda % 8) || (ldb % 8) || ((uintptr_t)Aq % 16) || ((uintptr_t)Bq % 16)) return cudaErrorInvalidValue;
     const int64_t kqa = (int64_t)nda * kpad, kqb = (int64_t)ndb * kpad;
     if (lda < kqa || ldb < kqb) return cudaErrorInvalidValue;

@@ -363,8 +363,9 @@ cudaError_t sliced_matmul(int nd, int64_t m, int64_t n, int64_t K, const double 
     const int nda = nd;
     if (ndb <= 0) ndb = nd;
     cudaError_t e = cudaMemset2DAsync(D, (size_t)ldd * sizeof(dfloat), 0, (size_t)n * sizeof(dfloat), (size_t)m, s);
-    for (int64_t k0 = 0; k0 < K && e == cudaSuccess; k0 += kSlicedChunk) {
-        const int64_t kc = K - k0 < kSlicedChunk ? K - k0 : kSlicedChunk;
+    const int64_t chunk = nda == 2 ? kSlicedChunk2 : kSlicedChunk;
+    for (int64_t k0 = 0; k0 < K && e == cudaSuccess; k0 += chunk) {
+        const int64_t kc = K - k0 < chunk ? K - k0 : chunk;
         const int64_t kpad = sliced_kpad(kc), lda_q = nda * kpad, ldb_q = ndb * kpad;
         e = slice_rows(nda, A + k0, lda, m, kc, Aq, lda_q, exps, s);
         if (e == cudaSuccess) e = slice_cols_T(ndb, B + k0 * ldb, ldb, kc, n, Bq, ldb_q, exps + m, s);
@@ -379,8 +380,9 @@ cudaError_t sliced_matmul_t(int nda, int ndb, int64_t m, int64_t n, int64_t K, c
                             __nv_bfloat16 *Aq, int *exps, cudaStream_t s) {
     if (m <= 0 || n <= 0) return cudaSuccess;
     cudaError_t e = cudaMemset2DAsync(Dt, (size_t)lddt * sizeof(dfloat), 0, (size_t)m * sizeof(dfloat), (size_t)n, s);
-    for (int64_t k0 = 0; k0 < K && e == cudaSuccess; k0 += kSlicedChunk) {
-        const int64_t kc = K - k0 < kSlicedChunk ? K - k0 : kSlicedChunk;
+    const int64_t chunk = ndb == 2 ? kSlicedChunk2 : kSlicedChunk;
+    for (int64_t k0 = 0; k0 < K && e == cudaSuccess; k0 += chunk) {
+        const int64_t kc = K - k0 < chunk ? K - k0 : chunk;
         const int64_t kpad = sliced_kpad(kc), ldq_b = ndb * kpad, ldq_a = nda * kpad;
         // M side: the columns of B (ndb digits); N side: the rows of A (nda digits)
         e = slice_cols_T(ndb, B + k0 * ldb, ldb, kc, n, Bq, ldq_b, exps, s);

@@ -466,15 +466,6 @@ def run_ours(a, emit=True):
         A_h = A_cpu.pin_memory()
         B_h = B_cpu.pin_memory()
 
-        def h2d_rate():
-            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            q0.record(stream)
-            A.copy_(A_h, non_blocking=True)
-            q1.record(stream)
-            torch.cuda.synchronize()
-            return A_h.numel() * 8 / (q0.elapsed_time(q1) / 1e3) / 1e9
-        h2d_before = h2d_rate()
         X_h = [torch.empty((n, nrhs), dtype=torch.float64).pin_memory() for _ in range(2)]
         Ab, Bb = [A, torch.empty_like(A)], [B, torch.empty_like(B)]
         cs = torch.cuda.Stream(dev)
@@ -513,14 +504,11 @@ def run_ours(a, emit=True):
         e1.record(stream)
         torch.cuda.synchronize()
         e_ms = e0.elapsed_time(e1)
-        # the copy engine's own rate, for the record
-        h2d_gbs = h2d_rate()
         e_ms = reduce_max(e_ms, world, dev)
         e2e = {"value": job_rate(world, k_e2e, e_ms), "unit": "solves/s",
                "h2d_bytes_per_step": A_h.numel() * 8 + B_h.numel() * 8, "d2h_bytes_per_step": X_h[0].numel() * 8,
                "steps": k_e2e, "inputs": "double-buffered: step i+1's copy overlaps step i",
-               "seeds": "the timed steps' multiplier seeds",
-               "h2d_gbs_alone": h2d_gbs, "h2d_gbs_before": h2d_before, "A_h_pinned": bool(A_h.is_pinned())}
+               "seeds": "the timed steps' multiplier seeds", "A_h_pinned": bool(A_h.is_pinned())}
 
     if rank != 0:
         if world > 1:
@@ -549,8 +537,13 @@ def run_ours(a, emit=True):
                                    "Schur updates)",
                     "tensor_pipe": {"achieved": pipe, "frac": pipe / peak, "unit": "TFLOP/s",
                                     "counted": "BF16 digit-pair products actually issued (2 m n Kpad per pair)"},
-                    "traffic": None,
-                    "traffic_basis": "not yet captured for this build of the kernel"}
+                    # dram read + write bytes of one n = 4096 A G chunk launch (k_tc_sliced<2, 7>,
+                    # K = 1024, column-major tile order) under ncu, 303.5 MB (the double-float
+                    # accumulator's read-modify-write 268 MB, the digit slices 75 MB read about
+                    # once), scaled by the n^2 output tiles to this size's chunk launches
+                    "traffic": 303.5e6 * (n / 4096) ** 2 if nd == 7 else None,
+                    "traffic_basis": "A G chunk launch (K = 1024) of k_tc_sliced<2, 7>; ncu at n = 4096 scaled by "
+                                     "n^2; Schur-update launches (K = 256) move about a quarter of it per tile"}
     elif a.prec == "fp8" and tc_launches:
         # per launch: the A G product (K = n, k_tc_e4m3, tensor-bound) and the
         # Schur updates (K = nb <= 128, k_tc_gemm<true>, HBM-bound: C read and

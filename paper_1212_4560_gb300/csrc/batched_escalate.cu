@@ -8,8 +8,8 @@
 // factors it in its own scratch (blocked GENP: the diagonal block by the
 // unblocked recurrence in shared memory, block row and column by
 // substitution, Schur update by the CTA GEMM) and continues the FP64
-// refinement of the system's current x with those factors.  With no such
-// system the launch only walks the queue.
+// refinement of the system's current x by GMRES-IR with those factors as the
+// preconditioner.  With no such system the launch only walks the queue.
 #include "genp_internal.cuh"
 
 #include <math.h>
@@ -285,30 +285,6 @@ __device__ void solve_sys(const T *C, int n, T *Y, int nr, bool trans, SmemSolve
     }
 }
 
-// X (+)= G Y (trans = false) or G^T Y, one warp per row.  The product runs in
-// FP32 (Y is a solution or correction of FP32-level accuracy, so FP64 would
-// buy nothing) and is added to X in FP64.
-template <typename TY>
-__device__ void apply_g(const float *G, const float *g, int n, const TY *Y, int nr, double *X, bool accumulate,
-                        bool trans) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = warp; i < n; i += BT / 32) {
-        float acc[MAXRHS];
-        for (int c = 0; c < nr; ++c) acc[c] = 0.f;
-        for (int j = lane; j < n; j += 32) {
-            float gij;
-            if (g) gij = circ_at(g, n, trans ? (int64_t)j - i : (int64_t)i - j);
-            else gij = trans ? G[(int64_t)j * n + i] : G[(int64_t)i * n + j];
-            for (int c = 0; c < nr; ++c) acc[c] = fmaf(gij, (float)Y[(int64_t)j * nr + c], acc[c]);
-        }
-        for (int c = 0; c < nr; ++c) {
-            float v = acc[c];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) X[(int64_t)i * nr + c] = accumulate ? X[(int64_t)i * nr + c] + (double)v : (double)v;
-        }
-    }
-}
-
 // R = B - A X (FP64), column norms into ctl; ||A||_inf too when `anorm`.
 template <typename TA>
 __device__ void residual(const TA *A, int n, const double *B, const double *X, double *R, int nr, bool anorm,
@@ -339,19 +315,260 @@ __device__ void residual(const TA *A, int n, const double *B, const double *X, d
     }
 }
 
-// Refinement with the factors in Cf (T arithmetic for the correction solve);
-// `first` computes ||A||_inf and records eta0.  Returns the steps taken.
-template <typename TA, typename T>
-__device__ int refine_loop(const TA *A, const T *Cf, const float *G, const float *g, const double *B, double *X,
-                           double *R, T *Y, int n, int nr, int max_iter, double tol, bool first, double &eta0,
-                           double &eta, Smem &sm, SmemCtl &ctl) {
+// ---------------------------------------------------------------------------
+// GMRES-IR for the escalated systems (Carson & Higham 2018): the outer step
+// takes r = b - A x in FP64 and solves C d = r by FP64 GMRES on the
+// left-preconditioned system U^-1 L^-1 C d = U^-1 L^-1 r with the
+// double-float factors (C v applied as A (G v) in double-float), then
+// x += G d in FP64.  Classic refinement needs u_df kappa(C) growth < 1, which the
+// systems that reach this launch (kappa(A G) up to ~1e10) can miss; GMRES
+// needs the factors only as a preconditioner.
+// ---------------------------------------------------------------------------
+constexpr int KRY = 20;   // Krylov vectors per outer step and right-hand side
+constexpr int NG = 4;     // right-hand sides iterated in lockstep
+
+struct GmresCtl {
+    double H[NG][KRY + 1][KRY];
+    double cs[NG][KRY], sn[NG][KRY], gv[NG][KRY + 1], y[NG][KRY];
+    double beta[NG];
+    double red[BT / 32][NG];
+    double val[NG];
+    int kend[NG];
+    int active;
+};
+
+// Sums over the CTA of the per-thread values v[0 .. w-1]; every thread gets
+// the totals in gc.val.
+__device__ void cta_sums(double (&v)[NG], int w, GmresCtl &gc) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < NG; ++c)
+        for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < NG; ++c) gc.red[warp][c] = v[c];
+    __syncthreads();
+    if (threadIdx.x < w) {
+        double t = 0.0;
+        for (int q = 0; q < BT / 32; ++q) t += gc.red[q][threadIdx.x];
+        gc.val[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+
+// The Krylov operator's products in double-float (about 2^-44 per
+// operation, on the FP32 pipe, which GB300 runs 64 times faster than FP64):
+// the inner solve only has to be accurate enough to contract the FP64
+// residual of the outer step.  One warp per row, w <= NG columns of v
+// (ld NG) into out (ld NG).
+__device__ void g_apply_df(const float *G, const float *g, int n, const double *v, double *out, int w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < n; i += BT / 32) {
+        dfloat acc[NG];
+#pragma unroll
+        for (int c = 0; c < NG; ++c) acc[c] = dfloat(0.0f);
+        for (int j = lane; j < n; j += 32) {
+            const dfloat gij(g ? circ_at(g, n, (int64_t)i - j) : G[(int64_t)i * n + j]);
+#pragma unroll
+            for (int c = 0; c < NG; ++c)
+                if (c < w) acc[c] = acc[c] + gij * dfloat(v[(int64_t)j * NG + c]);
+        }
+#pragma unroll
+        for (int c = 0; c < NG; ++c)
+            for (int o = 16; o > 0; o >>= 1) {
+                dfloat t;
+                t.hi = __shfl_xor_sync(0xffffffffu, acc[c].hi, o);
+                t.lo = __shfl_xor_sync(0xffffffffu, acc[c].lo, o);
+                acc[c] = acc[c] + t;
+            }
+        if (lane < w) {
+            dfloat r = acc[0];
+#pragma unroll
+            for (int c = 1; c < NG; ++c) r = c == lane ? acc[c] : r;
+            out[(int64_t)i * NG + lane] = (double)r;
+        }
+    }
+}
+
+template <typename TA>
+__device__ void a_apply_df(const TA *A, int n, const double *v, double *out, int w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < n; i += BT / 32) {
+        dfloat acc[NG];
+#pragma unroll
+        for (int c = 0; c < NG; ++c) acc[c] = dfloat(0.0f);
+        for (int j = lane; j < n; j += 32) {
+            const dfloat aij((double)A[(int64_t)i * n + j]);
+#pragma unroll
+            for (int c = 0; c < NG; ++c)
+                if (c < w) acc[c] = acc[c] + aij * dfloat(v[(int64_t)j * NG + c]);
+        }
+#pragma unroll
+        for (int c = 0; c < NG; ++c)
+            for (int o = 16; o > 0; o >>= 1) {
+                dfloat t;
+                t.hi = __shfl_xor_sync(0xffffffffu, acc[c].hi, o);
+                t.lo = __shfl_xor_sync(0xffffffffu, acc[c].lo, o);
+                acc[c] = acc[c] + t;
+            }
+        if (lane < w) {
+            dfloat r = acc[0];
+#pragma unroll
+            for (int c = 1; c < NG; ++c) r = c == lane ? acc[c] : r;
+            out[(int64_t)i * NG + lane] = (double)r;
+        }
+    }
+}
+
+// W <- U^-1 L^-1 W (n x w, ld NG) with the double-float factors, through Yd
+__device__ void precond(const dfloat *Cf, int n, double *W, int w, dfloat *Yd, Smem &sm) {
+    for (int e = threadIdx.x; e < n * w; e += BT) Yd[e] = dfloat(W[(int64_t)(e / w) * NG + e % w]);
+    __syncthreads();
+    solve_sys<dfloat>(Cf, n, Yd, w, false, solve_sm<dfloat>(sm));
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * w; e += BT) W[(int64_t)(e / w) * NG + e % w] = (double)Yd[e];
+    __syncthreads();
+}
+
+// GMRES on C d = r for the columns c0 .. c0 + w - 1 of R (ld nr) in
+// lockstep (one preconditioner solve and one pass over G and A per Krylov
+// step for all of them), each with its own basis, Hessenberg matrix and
+// stopping point; then x += G d in FP64.  V holds (KRY + 1) n NG doubles,
+// T two n x NG work blocks.
+template <typename TA>
+__device__ void gmres_group(const TA *A, const dfloat *Cf, const float *G, const float *g, const double *R, int nr,
+                            int c0, int w, double *X, double *V, double *T, dfloat *Yd, int n, Smem &sm,
+                            GmresCtl &gc) {
+    const int tid = threadIdx.x;
+    double *W = T, *Tm = T + (int64_t)n * NG;
+    for (int e = tid; e < n * NG; e += BT) {
+        const int i = e / NG, c = e % NG;
+        W[e] = c < w ? R[(int64_t)i * nr + c0 + c] : 0.0;
+    }
+    __syncthreads();
+    precond(Cf, n, W, w, Yd, sm);
+    double part[NG];
+#pragma unroll
+    for (int c = 0; c < NG; ++c) part[c] = 0.0;
+    for (int e = tid; e < n * NG; e += BT) part[e % NG] += W[e] * W[e];   // BT is a multiple of NG
+    cta_sums(part, w, gc);
+    if (tid < NG) {
+        const double b = tid < w ? sqrt(gc.val[tid]) : 0.0;
+        gc.beta[tid] = (b > 0.0 && isfinite(b)) ? b : 0.0;
+        gc.gv[tid][0] = gc.beta[tid];
+        gc.kend[tid] = 0;
+    }
+    if (tid == 0) gc.active = 0;
+    __syncthreads();
+    if (tid < w && gc.beta[tid] > 0.0) atomicOr(&gc.active, 1 << tid);
+    __syncthreads();
+    if (!gc.active) return;
+    for (int e = tid; e < n * NG; e += BT) {
+        const double b = gc.beta[e % NG];
+        V[e] = b > 0.0 ? W[e] / b : 0.0;
+    }
+    __syncthreads();
+    for (int k = 0; k < KRY && gc.active; ++k) {
+        const double *vk = V + (int64_t)k * n * NG;
+        g_apply_df(G, g, n, vk, Tm, w);
+        __syncthreads();
+        a_apply_df<TA>(A, n, Tm, W, w);
+        __syncthreads();
+        precond(Cf, n, W, w, Yd, sm);
+        // modified Gram-Schmidt, all columns at once
+        for (int i = 0; i <= k; ++i) {
+            const double *vi = V + (int64_t)i * n * NG;
+#pragma unroll
+            for (int c = 0; c < NG; ++c) part[c] = 0.0;
+            for (int e = tid; e < n * NG; e += BT) part[e % NG] += W[e] * vi[e];
+            cta_sums(part, w, gc);
+            for (int e = tid; e < n * NG; e += BT) W[e] -= gc.val[e % NG] * vi[e];
+            if (tid < w) gc.H[tid][i][k] = gc.val[tid];
+            __syncthreads();
+        }
+#pragma unroll
+        for (int c = 0; c < NG; ++c) part[c] = 0.0;
+        for (int e = tid; e < n * NG; e += BT) part[e % NG] += W[e] * W[e];
+        cta_sums(part, w, gc);
+        double *vn = V + (int64_t)(k + 1) * n * NG;
+        for (int e = tid; e < n * NG; e += BT) {
+            const double hk = sqrt(gc.val[e % NG]);
+            vn[e] = hk > 0.0 ? W[e] / hk : 0.0;
+        }
+        if (tid < w && ((gc.active >> tid) & 1)) {
+            // this column's Givens rotations: the earlier ones on the new
+            // column of H, then a new one
+            const int c = tid;
+            const double hk = sqrt(gc.val[c]);
+            for (int i = 0; i < k; ++i) {
+                const double a = gc.H[c][i][k], b = gc.H[c][i + 1][k];
+                gc.H[c][i][k] = gc.cs[c][i] * a + gc.sn[c][i] * b;
+                gc.H[c][i + 1][k] = -gc.sn[c][i] * a + gc.cs[c][i] * b;
+            }
+            const double a = gc.H[c][k][k];
+            const double r = hypot(a, hk);
+            gc.cs[c][k] = r > 0.0 ? a / r : 1.0;
+            gc.sn[c][k] = r > 0.0 ? hk / r : 0.0;
+            gc.H[c][k][k] = r;
+            gc.gv[c][k + 1] = -gc.sn[c][k] * gc.gv[c][k];
+            gc.gv[c][k] = gc.cs[c][k] * gc.gv[c][k];
+            gc.kend[c] = k + 1;
+            // converged (or a lucky breakdown): this column stops here
+            if (!(fabs(gc.gv[c][k + 1]) > 1e-12 * gc.beta[c]) || !(hk > 0.0)) atomicAnd(&gc.active, ~(1 << c));
+        }
+        __syncthreads();
+    }
+    if (tid < w) {   // back substitution for each column's y
+        const int c = tid, m = gc.kend[c];
+        for (int i = m - 1; i >= 0; --i) {
+            double sacc = gc.gv[c][i];
+            for (int j = i + 1; j < m; ++j) sacc -= gc.H[c][i][j] * gc.y[c][j];
+            gc.y[c][i] = gc.H[c][i][i] != 0.0 ? sacc / gc.H[c][i][i] : 0.0;
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < n * NG; e += BT) {
+        const int c = e % NG;
+        double d = 0.0;
+        if (c < w)
+            for (int i = 0; i < gc.kend[c]; ++i) d += gc.y[c][i] * V[(int64_t)i * n * NG + e];
+        W[e] = d;
+    }
+    __syncthreads();
+    // x += G d, FP64
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int i = warp; i < n; i += BT / 32) {
+        double acc[NG];
+#pragma unroll
+        for (int c = 0; c < NG; ++c) acc[c] = 0.0;
+        for (int j = lane; j < n; j += 32) {
+            const double gij = g ? (double)circ_at(g, n, (int64_t)i - j) : (double)G[(int64_t)i * n + j];
+#pragma unroll
+            for (int c = 0; c < NG; ++c) acc[c] = fma(gij, W[(int64_t)j * NG + c], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < NG; ++c) {
+            for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+            if (lane == 0 && c < w) X[(int64_t)i * nr + c0 + c] += acc[c];
+        }
+    }
+    __syncthreads();
+}
+
+// GMRES-IR outer loop: stop at eta <= tol, when eta fails to halve, or
+// after max_iter steps.  Returns the steps taken.
+template <typename TA>
+__device__ int refine_gmres(const TA *A, const dfloat *Cf, const float *G, const float *g, const double *B,
+                            double *X, double *R, double *V, double *T, dfloat *Yd, int n, int nr, int max_iter,
+                            double tol, double &eta0, double &eta, Smem &sm, SmemCtl &ctl, GmresCtl &gc) {
     const int tid = threadIdx.x;
     int it = 0;
     if (tid == 0) ctl.eta_prev = INFINITY;
     for (;; ++it) {
         if (tid < MAXRHS) ctl.rn[tid] = ctl.xn[tid] = ctl.bn[tid] = 0ull;
         __syncthreads();
-        residual<TA>(A, n, B, X, R, nr, first && it == 0, ctl);
+        residual<TA>(A, n, B, X, R, nr, it == 0, ctl);
         __syncthreads();
         if (tid == 0) {
             const double an = __longlong_as_double((long long)ctl.anorm);
@@ -368,13 +585,10 @@ __device__ int refine_loop(const TA *A, const T *Cf, const float *G, const float
         }
         __syncthreads();
         eta = ctl.eta;
-        if (first && it == 0) eta0 = eta;
+        if (it == 0) eta0 = eta;
         if (ctl.done) break;
-        for (int e = tid; e < n * nr; e += BT) Y[e] = (T)R[e];
-        __syncthreads();
-        solve_sys<T>(Cf, n, Y, nr, false, solve_sm<T>(sm));
-        apply_g<T>(G, g, n, Y, nr, X, true, false);
-        __syncthreads();
+        for (int c0 = 0; c0 < nr; c0 += NG)
+            gmres_group<TA>(A, Cf, G, g, R, nr, c0, min(NG, nr - c0), X, V, T, Yd, n, sm, gc);
     }
     return it;
 }
@@ -388,6 +602,7 @@ __global__ void __launch_bounds__(BT) k_batched_escalate(const BatchDesc *d, int
     extern __shared__ __align__(16) unsigned char smraw[];
     Smem &sm = *reinterpret_cast<Smem *>(smraw);
     __shared__ SmemCtl ctl;
+    __shared__ GmresCtl gc;
     const int tid = threadIdx.x;
     while (true) {
         if (tid == 0) ctl.idx = atomicAdd(counter, 1);
@@ -417,13 +632,16 @@ __global__ void __launch_bounds__(BT) k_batched_escalate(const BatchDesc *d, int
         if (!(stat[idx].eta < INFINITY))   // no usable iterate: start from x = 0
             for (int e = tid; e < n * nr; e += BT) X[e] = 0.0;
         __syncthreads();
-        dfloat *Cd = reinterpret_cast<dfloat *>(scratch64 + (int64_t)blockIdx.x * stride);   // n x n
+        double *base = scratch64 + (int64_t)blockIdx.x * stride;
+        dfloat *Cd = reinterpret_cast<dfloat *>(base);                                         // n x n
         dfloat *Yd = Cd + 1024ll * 1024ll;                                                     // n x nr
+        double *V = base + 1024ll * 1024ll + 1024ll * MAXRHS;                                 // (KRY + 1) x n x NG
+        double *T = V + (int64_t)(KRY + 1) * 1024 * NG;                                        // 2 x n x NG
         cta_gemm<TA, float, dfloat>(n, n, n, dfloat(1), A, n, G, n, g, n, dfloat(0), Cd, n, sm.gd);
         __syncthreads();
         factor_sys<dfloat>(Cd, n, 32, sm, ctl);
         double e0 = 0.0, eta = INFINITY;
-        const int it = refine_loop<TA, dfloat>(A, Cd, G, g, B, X, R, Yd, n, nr, max_iter, tol, true, e0, eta, sm, ctl);
+        const int it = refine_gmres<TA>(A, Cd, G, g, B, X, R, V, T, Yd, n, nr, max_iter, tol, e0, eta, sm, ctl, gc);
         if (tid == 0) {
             BatchStatus st = stat[idx];
             st.refine_iters += 1 + it;
@@ -439,8 +657,9 @@ __global__ void __launch_bounds__(BT) k_batched_escalate(const BatchDesc *d, int
 }  // namespace
 
 // 8-byte elements of the per-CTA scratch (C as double-float: n^2 for
-// n <= 1024; Y: n x 16 follows it).
-int64_t batched_escalate_stride() { return 1024ll * 1024ll + 1024ll * MAXRHS; }
+// n <= 1024; Y: n x 16 follows it, then the KRY + 1 Krylov blocks and two
+// work blocks of n x NG doubles).
+int64_t batched_escalate_stride() { return 1024ll * 1024ll + 1024ll * MAXRHS + (KRY + 3) * 1024ll * NG; }
 
 int batched_escalate_blocks_per_sm() {
     int b = 1;

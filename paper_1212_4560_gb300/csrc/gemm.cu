@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(256) k_gemv_n(int64_t m, int nr, int64_t k, T 
         const T *arow[RW];
 #pragma unroll
         for (int r = 0; r < RW; ++r) arow[r] = A + (i0 + r < m ? i0 + r : i0) * lda;
-#pragma unroll 4
+#pragma unroll 8
         for (int64_t kk = lane; kk < k; kk += 32) {
             T b[NR];
 #pragma unroll
@@ -241,7 +241,9 @@ cudaError_t run_gemv(int64_t m, int64_t n, int64_t k, T alpha, const T *A, int64
         k_gemv_t<T, NR><<<(unsigned)blocks, 256, 0, s>>>(m, (int)n, k, alpha, A, lda, B, ldb, beta, Cin, ldci, D,
                                                           ldd, skip);
     } else {
-        constexpr int RW = NR <= 4 ? 4 : 2;
+        // one RHS: two rows per warp, 16 loads in flight per lane and ~7 CTAs
+        // per SM (the 4-row form left one wave of 3.4 CTAs per SM, 44% of HBM)
+        constexpr int RW = NR == 1 ? 2 : (NR <= 4 ? 4 : 2);
         const int64_t blocks = cdiv(m, 8 * RW) < 65535 ? cdiv(m, 8 * RW) : 65535;
         k_gemv_n<T, NR, RW><<<(unsigned)blocks, 256, 0, s>>>(m, (int)n, k, alpha, A, lda, B, ldb, beta, Cin, ldci,
                                                               D, ldd, skip);

@@ -685,6 +685,12 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const int nkt = kpad / BK;
     const int ntm = (m + BM - 1) / BM, ntn = (n + SBN - 1) / SBN;
     const int ntiles = ntm * ntn;
+    // Tile order: the CTAs in flight walk the M tiles of a few N columns when
+    // the M side is the narrow operand (a two-digit multiplier), so the wide
+    // operand's digit slices of those columns are shared through L2 and the
+    // narrow one is what gets re-read; otherwise the N tiles of a few M rows.
+    auto tile_m = [&](int tile) { return NDA < NDB ? tile % ntm : tile / ntn; };
+    auto tile_n = [&](int tile) { return NDA < NDB ? tile / ntm : tile % ntn; };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < A_SLOTS; ++s) {
@@ -720,7 +726,7 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             int ai = 0, bi = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-                const int m0 = (tile / ntn) * BM, n0 = (tile % ntn) * SBN;
+                const int m0 = tile_m(tile) * BM, n0 = tile_n(tile) * SBN;
                 for (int kt = 0; kt < nkt && ok; ++kt, ++bi) {
                     const int bs = bi & 1;
                     if (bi >= 2 && !mbar_wait(&ctl->bempty[bs], (uint32_t)((bi >> 1) & 1) ^ 1u, abort)) {
@@ -819,7 +825,7 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
         int tc = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tc) {
-            const int m0 = (tile / ntn) * BM, n0 = (tile % ntn) * SBN;
+            const int m0 = tile_m(tile) * BM, n0 = tile_n(tile) * SBN;
             const int row = m0 + r;
             // this tile's rows of D into L2 while its MMAs run
             if (row < m && n0 < n) {

@@ -66,6 +66,14 @@ def test_argument_errors_return_before_any_cuda_call(lib):
     assert lib.genp_precondition(None, None, 1, 0, None, 1, 0, None) == ARG
     assert lib.genp_info_fetch(None, None, None) == ARG
     assert lib.genp_multiplier_query(None, None, None, None) == ARG
+    assert lib.genp_block_factor(None, 8, 8, 64, None, ctypes.byref(out)) == ARG            # no C
+    assert lib.genp_block_factor(fake, 8, 4, 64, None, ctypes.byref(out)) == ARG            # ldc < n
+    assert lib.genp_block_factor(fake, 8, 8, 32, None, ctypes.byref(out)) == -7             # order 64 only
+    assert lib.genp_block_factor(fake, 8, 8, 64, None, None) == ARG                         # no out
+    d, w, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    assert lib.genp_profile_class(6, ctypes.byref(d), ctypes.byref(w), ctypes.byref(c)) == ARG   # no such class
+    assert lib.genp_profile_class(-1, ctypes.byref(d), ctypes.byref(w), ctypes.byref(c)) == ARG
+    assert lib.genp_profile_class(1, None, ctypes.byref(w), ctypes.byref(c)) == ARG
     lib.genp_multiplier_destroy(None)
     lib.genp_factors_destroy(None)
 

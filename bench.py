@@ -445,10 +445,26 @@ def run_ours(a, emit=True):
         lib.genp_profile_read(ctypes.byref(p_ms), ctypes.byref(p_fl), ctypes.byref(p_n))
         lib.genp_profile_enable(0)
         tc_prof = (p_ms.value, p_fl.value, p_n.value)
+    # the refinement runs as a cached CUDA graph in the timed steps, and the
+    # launch profile skips what a graph holds: one more (untimed) step with
+    # the refinement enqueued launch by launch gives the per-class rates
+    info = genp.info_fetch(F)             # the last timed step's report
+    eager_prof = {}
+    if a.prec != "fp8":
+        prev_graphs = lib.genp_refine_graphs(0)
+        lib.genp_profile_enable(1)
+        step(a.warmup + a.steps)
+        torch.cuda.synchronize()
+        import ctypes
+        for cls in range(1, 6):
+            c_ms, c_w, c_n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+            if lib.genp_profile_class(cls, ctypes.byref(c_ms), ctypes.byref(c_w), ctypes.byref(c_n)) == 0:
+                eager_prof[cls] = (c_ms.value, c_w.value, c_n.value)
+        lib.genp_profile_enable(0)
+        lib.genp_refine_graphs(prev_graphs)
     if world > 1:
         dist.barrier()
     total_ms = t_start.elapsed_time(t_end)
-    info = genp.info_fetch(F)
     phase_ms = {p: sum(evs[i][k].elapsed_time(evs[i][k + 1]) for i in range(a.steps)) / a.steps
                 for k, p in enumerate(phases)}
     total_ms = reduce_max(total_ms, world, dev)
@@ -496,7 +512,7 @@ def run_ours(a, emit=True):
                 used[b].record(stream)
                 X_h[b].copy_(X, non_blocking=True)
 
-        e2e_run(1, 10_000)
+        e2e_run(2, 10_000)          # both input buffers once (their refinement graphs are recorded here)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -607,7 +623,11 @@ def run_ours(a, emit=True):
         roofline = {"kernel": "GENP factor (Schur GEMM dominant)", "bound": "alu", "achieved": achieved,
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz", "traffic": None}
-    roofline["other_kernels"] = other_kernels(class_prof, a.steps, ms_per_step, peaks)
+    roofline["other_kernels"] = other_kernels(eager_prof or class_prof, 1 if eager_prof else a.steps, ms_per_step,
+                                              peaks)
+    if eager_prof:
+        roofline["other_kernels_basis"] = ("one extra step after the timed ones with the refinement enqueued launch by "
+                                           "launch (in the timed steps it runs as one cached CUDA graph)")
     cpu = None
     if not a.no_cpu_baseline and world == 1:
         n_s = min(n, 2048)

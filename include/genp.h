@@ -346,6 +346,22 @@ GENP_API genp_status genp_refine(const double *A, int64_t lda, const genp_factor
                         const double *B, int64_t ldb, int64_t nrhs, double *X, int64_t ldx, double tol,
                         int max_iter, int method, void *cuda_stream);
 
+/* Refinement as one CUDA graph.  genp_refine enqueues its whole budget of
+ * steps (max_iter outer steps, for GMRES-IR each with GENP_GMRES_RESTART
+ * Krylov steps) and the device skips what it no longer needs, so a call is
+ * thousands of launches, most of them skipped; on the host that is several
+ * microseconds per launch.  With graphs on (the default), genp_refine
+ * records that sequence once per set of arguments (A, G, B, X, their leading
+ * dimensions, nrhs, tol, max_iter, method, the factors' matrix and
+ * workspace) on a private stream into a CUDA graph kept in the factors
+ * handle (up to four such graphs, replaced round robin; replacing one waits
+ * for the device), and each call then launches the graph on the caller's
+ * stream.  A call on a stream that is being captured enqueues its launches
+ * one by one into the caller's capture instead.  While a graph is being
+ * recorded the launch profile (genp_profile_*) leaves its launches out.
+ *  enable  1 on, 0 off, -1 only queries.  Returns the previous setting. */
+GENP_API int genp_refine_graphs(int enable);
+
 /* Adjoint of X = A^{-1} B through the factors of C = A G: with gX = dl/dX,
  *   Lambda = A^{-T} gX = L^{-T} U^{-T} G^T gX,   dA = -Lambda X^T,   dB = Lambda.
  * (A^{-1} = G U^{-1} L^{-1}; the result does not depend on G in exact

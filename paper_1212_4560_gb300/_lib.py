@@ -58,6 +58,7 @@ SIGNATURES = {
     "genp_profile_read": (_int, [_vp, _vp, _vp]),
     "genp_profile_launches": (_int, [_vp, _vp, _int, _vp]),
     "genp_profile_class": (_int, [_int, _vp, _vp, _vp]),
+    "genp_refine_graphs": (_int, [_int]),
     "genp_device_check": (_int, [_int]),
     "genp_batched_plan_create": (_int, [_i64, _vp, _i64, _int, _int, _int, _dbl, _int, _vp, ctypes.POINTER(_vp)]),
     "genp_batched_layout": (_int, [_vp, _vp, _vp]),

@@ -139,6 +139,7 @@ void keep_pool_cached() {
 namespace genp {
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launches(uint64_t count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
 
 // X[r][c] += Y[r][c] (the identity multiplier's x += G d)
 __global__ void k_add_into(const double *Y, int64_t ldy, double *X, int64_t ldx, int64_t n, int64_t nr,
@@ -803,6 +804,12 @@ genp_status genp_refactor(genp_factors *F, void *C, int64_t ldc, void *cuda_stre
 
 void genp_factors_destroy(genp_factors *F) {
     if (!F) return;
+    bool any = F->rg_stream != nullptr;
+    for (auto &g : F->rgraph) any = any || g.exec;
+    if (any) cudaDeviceSynchronize();   // graphs and their stream may still be in use
+    for (auto &g : F->rgraph)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (F->rg_stream) cudaStreamDestroy(F->rg_stream);
     cudaFree(F->st);
     cudaFree(F->norms);
     cudaFree(F->work);
@@ -846,25 +853,21 @@ genp_status genp_solve(const genp_factors *F, const genp_multiplier *G, const do
     return GENP_OK;
 }
 
-genp_status genp_refine(const double *A, int64_t lda, const genp_factors *F, const genp_multiplier *G, const double *B,
-                        int64_t ldb, int64_t nrhs, double *X, int64_t ldx, double tol, int max_iter, int method,
-                        void *cuda_stream) {
-    if (!A || !F || !G || !B || !X) return GENP_ERR_ARG;
+namespace {
+
+bool g_refine_graphs = true;
+
+// The launch sequence of genp_refine (workspace already in place).
+genp_status refine_enqueue(const double *A, int64_t lda, genp_factors *Fm, const genp_multiplier *G,
+                           const double *B, int64_t ldb, int64_t nrhs, double *X, int64_t ldx, double tol,
+                           int max_iter, int method, cudaStream_t s) {
+    const genp_factors *F = Fm;
     const int64_t n = F->n;
-    if (G->n != n || lda < n || nrhs < 1 || ldb < nrhs || ldx < nrhs) return GENP_ERR_ARG;
-    if (max_iter < 0 || max_iter > GENP_MAX_REFINE || !(tol >= 0.0)) return GENP_ERR_ARG;
-    if (method != 0 && method != 1) return GENP_ERR_ARG;
-    if (nrhs > kMaxRhsChunk) return GENP_ERR_UNSUPPORTED;
-    cudaStream_t s = S(cuda_stream);
-    genp_factors *Fm = const_cast<genp_factors *>(F);
     if (method == 1) {
-        TRY(ensure_work(Fm, gmres_work_bytes(n, nrhs), s));
         CU(refine_gmres(Fm, G, A, lda, B, ldb, nrhs, X, ldx, tol, max_iter, F->work, s));
-        Fm->last_stream = s;
         return GENP_OK;
     }
-    const size_t rd = align256((size_t)n * nrhs * sizeof(double)), yf = align256((size_t)n * nrhs * sizeof(float));
-    TRY(ensure_work(Fm, 2 * rd + yf, s));
+    const size_t rd = align256((size_t)n * nrhs * sizeof(double));
     double *R = static_cast<double *>(F->work);
     double *T = reinterpret_cast<double *>(static_cast<char *>(F->work) + rd);
     float *Rf = reinterpret_cast<float *>(static_cast<char *>(F->work) + 2 * rd);
@@ -890,6 +893,113 @@ genp_status genp_refine(const double *A, int64_t lda, const genp_factors *F, con
         if (left) CU(add_into(D, nrhs, X, ldx, n, nrhs, done, s));
         else CU(apply_multiplier(G, false, R, nrhs, X, ldx, nrhs, true, done, s));
     }
+    return GENP_OK;
+}
+
+// Records the refinement's launches on the factors' private stream into a
+// CUDA graph; returns the instantiated graph in *exec and the kernels it
+// holds in *launches.
+genp_status refine_record(const double *A, int64_t lda, genp_factors *F, const genp_multiplier *G, const double *B,
+                          int64_t ldb, int64_t nrhs, double *X, int64_t ldx, double tol, int max_iter, int method,
+                          cudaGraphExec_t *exec, uint64_t *launches) {
+    if (!F->rg_stream && cudaStreamCreateWithFlags(&F->rg_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        F->rg_stream = nullptr;
+        return GENP_ERR_CUDA;
+    }
+    cudaStream_t rs = F->rg_stream;
+    if (cudaStreamBeginCapture(rs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return GENP_ERR_CUDA;
+    }
+    const uint64_t l0 = genp_launch_count();
+    profile_suspend(true);
+    const genp_status st = refine_enqueue(A, lda, F, G, B, ldb, nrhs, X, ldx, tol, max_iter, method, rs);
+    profile_suspend(false);
+    *launches = genp_launch_count() - l0;
+    g_launches.fetch_sub(*launches, std::memory_order_relaxed);   // counted when the graph runs
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(rs, &graph);
+    if (st != GENP_OK || ec != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return st != GENP_OK ? st : GENP_ERR_CUDA;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        *exec = nullptr;
+        return GENP_ERR_CUDA;
+    }
+    return GENP_OK;
+}
+
+}  // namespace
+
+int genp_refine_graphs(int enable) {
+    const int old = g_refine_graphs ? 1 : 0;
+    if (enable >= 0) g_refine_graphs = enable != 0;
+    return old;
+}
+
+genp_status genp_refine(const double *A, int64_t lda, const genp_factors *F, const genp_multiplier *G, const double *B,
+                        int64_t ldb, int64_t nrhs, double *X, int64_t ldx, double tol, int max_iter, int method,
+                        void *cuda_stream) {
+    if (!A || !F || !G || !B || !X) return GENP_ERR_ARG;
+    const int64_t n = F->n;
+    if (G->n != n || lda < n || nrhs < 1 || ldb < nrhs || ldx < nrhs) return GENP_ERR_ARG;
+    if (max_iter < 0 || max_iter > GENP_MAX_REFINE || !(tol >= 0.0)) return GENP_ERR_ARG;
+    if (method != 0 && method != 1) return GENP_ERR_ARG;
+    if (nrhs > kMaxRhsChunk) return GENP_ERR_UNSUPPORTED;
+    cudaStream_t s = S(cuda_stream);
+    genp_factors *Fm = const_cast<genp_factors *>(F);
+    if (method == 1) {
+        TRY(ensure_work(Fm, gmres_work_bytes(n, nrhs), s));
+    } else {
+        const size_t rd = align256((size_t)n * nrhs * sizeof(double)),
+                     yf = align256((size_t)n * nrhs * sizeof(float));
+        TRY(ensure_work(Fm, 2 * rd + yf, s));
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusActive;   // unknown: take the plain path
+    }
+    if (!g_refine_graphs || cap != cudaStreamCaptureStatusNone) {
+        // enqueued launch by launch (a caller capturing its own graph gets them in it)
+        const genp_status st = refine_enqueue(A, lda, Fm, G, B, ldb, nrhs, X, ldx, tol, max_iter, method, s);
+        if (st == GENP_OK) Fm->last_stream = s;
+        return st;
+    }
+    double tolv = tol;
+    uint64_t tolbits = 0;
+    memcpy(&tolbits, &tolv, sizeof(tolbits));
+    const uint64_t key[16] = {(uint64_t)(uintptr_t)A, (uint64_t)lda, (uint64_t)(uintptr_t)G, (uint64_t)(uintptr_t)B,
+                              (uint64_t)ldb, (uint64_t)nrhs, (uint64_t)(uintptr_t)X, (uint64_t)ldx, tolbits,
+                              (uint64_t)max_iter, (uint64_t)method, (uint64_t)G->side, (uint64_t)(uintptr_t)F->C,
+                              (uint64_t)F->ldc, (uint64_t)(uintptr_t)F->work, 1};
+    GenpRefineGraph *hit = nullptr;
+    for (auto &g : Fm->rgraph)
+        if (g.exec && memcmp(g.key, key, sizeof(key)) == 0) hit = &g;
+    if (!hit) {
+        GenpRefineGraph &slot = Fm->rgraph[Fm->rg_next];
+        Fm->rg_next = (Fm->rg_next + 1) % 4;
+        if (slot.exec) {
+            // the slot's graph may still be queued on some stream: free it only
+            // once everything enqueued so far has finished
+            cudaDeviceSynchronize();
+            cudaGraphExecDestroy(slot.exec);
+            slot.exec = nullptr;
+        }
+        // the recording stream must see the caller's stream state (buffers
+        // written by earlier calls): recording enqueues nothing, so no wait
+        TRY(refine_record(A, lda, Fm, G, B, ldb, nrhs, X, ldx, tol, max_iter, method, &slot.exec, &slot.launches));
+        memcpy(slot.key, key, sizeof(key));
+        hit = &slot;
+    }
+    CU(cudaGraphLaunch(hit->exec, s));
+    note_launches(hit->launches);
     Fm->last_stream = s;
     return GENP_OK;
 }

@@ -945,9 +945,11 @@ TcProfile &tc_profile() {
     return p;
 }
 // Events around one launch of `flops` flops, or nullptr when profiling is off.
+thread_local bool tl_profile_suspended = false;
+
 std::pair<cudaEvent_t, cudaEvent_t> *profile_slot(double flops, double alg) {
     TcProfile &p = tc_profile();
-    if (!p.on) return nullptr;
+    if (!p.on || tl_profile_suspended) return nullptr;
     if (p.used == p.ev.size()) {
         cudaEvent_t a, b;
         if (cudaEventCreate(&a) != cudaSuccess) return nullptr;
@@ -1114,8 +1116,10 @@ void tc_profile_enable(bool on) {
     gemv_skipped_count(true);
 }
 
+void profile_suspend(bool on) { tl_profile_suspended = on; }
+
 std::pair<cudaEvent_t, cudaEvent_t> *profile_class_slot(int c, double work) {
-    if (!tc_profile().on || c <= 0 || c >= kProfClasses) return nullptr;
+    if (!tc_profile().on || tl_profile_suspended || c <= 0 || c >= kProfClasses) return nullptr;
     ClassProfile &p = class_profile();
     if (p.used == p.ev.size()) {
         cudaEvent_t a, b;

@@ -78,7 +78,18 @@ struct genp_multiplier {
     cudaStream_t last_stream = nullptr;
 };
 
+// A recorded refinement: genp_refine's launch sequence for one set of
+// arguments, replayed as one CUDA graph (see genp_refine_graphs).
+struct GenpRefineGraph {
+    uint64_t key[16] = {};
+    cudaGraphExec_t exec = nullptr;
+    uint64_t launches = 0;             // kernels the graph holds (for genp_launch_count)
+};
+
 struct genp_factors {
+    GenpRefineGraph rgraph[4];         // cached refinement graphs, round robin
+    int rg_next = 0;
+    cudaStream_t rg_stream = nullptr;  // private stream the graphs are recorded on
     void *C = nullptr;
     int64_t n = 0, ldc = 0, nb = 64;
     genp_prec prec = GENP_FP64;
@@ -137,6 +148,10 @@ struct BatchStatus {
 
 // Counts one kernel launch (genp_launch_count); called before every launch.
 void note_launch();
+void note_launches(uint64_t count);
+// While a refinement is being recorded into a graph, the launch profile
+// skips its launches (their events would be recorded once, not per replay).
+void profile_suspend(bool on);
 
 // rng.cu
 cudaError_t launch_make_dense(double *G, int64_t n, uint64_t seed, uint64_t stream_id, double scale,

@@ -437,3 +437,47 @@ def test_adjoint_independent_of_multiplier(g):
         g.adjoint(F, G, 2.0 * X, X, dA, None)
         grads.append(host(dA))
     assert np.linalg.norm(grads[0] - grads[1]) <= 1e-10 * np.linalg.norm(grads[0])
+
+
+# ---------------------------------------------------------------- refinement as a CUDA graph
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_refine_graph_matches_launch_by_launch(g, method):
+    """genp_refine replayed from its cached CUDA graph solves as the
+    launch-by-launch sequence does (the streaming triangular solves add
+    their off-diagonal contributions with atomics, so two runs agree to
+    rounding, not bit for bit), reports through the same status word, counts
+    the same kernels, and a new right-hand side buffer records a new graph
+    (keyed by the arguments)."""
+    lib = g._lib.load()
+    n, nrhs = 300, 2
+    A, _, B = (t.numpy() for t in W.lead_deficient(n, 32, 16, nrhs, seed=11))
+    Ad, Bd = cu(A), cu(B)
+    G = g.make_multiplier(g.GAUSSIAN, n, seed=4)
+    C = torch.empty((n, n), dtype=torch.float64, device=DEV)
+    g.precondition(G, Ad, C)
+    F = g.factor(C)
+    out = {}
+    prev = lib.genp_refine_graphs(-1)
+    X = torch.empty_like(Bd)
+    X2 = torch.empty_like(Bd)
+    try:
+        # eager; the graph recorded, then replayed; a new X buffer (a new graph)
+        for mode, Xb in ((0, X), (1, X), (1, X), (1, X2)):
+            lib.genp_refine_graphs(mode)
+            X = Xb
+            g.solve(F, G, Bd, X)
+            l0 = g.launch_count()
+            g.refine(Ad, F, G, Bd, X, tol=1e-16, max_iter=6, method=method)
+            info = g.info_fetch(F)
+            out.setdefault(mode, []).append((host(X), info.bwd_err, info.refine_iters, g.launch_count() - l0))
+    finally:
+        lib.genp_refine_graphs(prev)
+    x0, e0, i0, l_eager = out[0][0]
+    assert oracle.backward_error(A, x0, B) <= 1e-14
+    for x1, e1, i1, l_graph in out[1]:
+        assert oracle.backward_error(A, x1, B) <= 1e-14
+        assert np.abs(x1 - x0).max() <= 1e-12 * np.abs(x0).max()
+        assert e1[-1] <= 1e-14 and abs(i1 - i0) <= 1
+        assert l_graph == l_eager             # the graph's kernels are counted when it runs
+

@@ -79,8 +79,9 @@ def parse():
     p.add_argument("--kappa", type=float, default=1e6, help="condition number of the svd workload")
     p.add_argument("--prec", default="sliced", choices=list(PRECS))
     p.add_argument("--digits", type=int, default=0, help="digits per operand of the sliced precision (5, 6, 7)")
-    p.add_argument("--precond-digits", type=int, default=0,
-                   help="digits per operand of the sliced C = A G (3 .. 7; 0: the library's setting)")
+    p.add_argument("--precond-digits", type=int, default=None,
+                   help="digits of A in the sliced C = A G (3 .. 7; 0: the library's setting, 7; default 5 with "
+                        "GMRES-IR, which needs the product only as accurate as the factors it feeds)")
     p.add_argument("--refine", default=None, choices=["classic", "gmres"],
                    help="refinement method (default: classic for fp64, GMRES-IR otherwise)")
     p.add_argument("--max-iter", type=int, default=None)
@@ -366,8 +367,11 @@ def run_ours(a, emit=True):
     prec = PRECS[a.prec]
     if a.digits:
         genp._lib.load().genp_sliced_digits(a.digits)
-    if a.precond_digits:
-        genp._lib.load().genp_sliced_precondition_digits(a.precond_digits)
+    method_name = a.refine or ("classic" if a.prec == "fp64" else "gmres")
+    if a.precond_digits is None:
+        a.precond_digits = 5 if (a.prec == "sliced" and method_name == "gmres") else 0
+    old_pdigits = genp._lib.load().genp_sliced_precondition_digits(0)
+    genp._lib.load().genp_sliced_precondition_digits(a.precond_digits or old_pdigits)
     cdt = torch.float64 if a.prec in F64_FACTORS else torch.float32
     method = {"classic": 0, "gmres": 1}[a.refine or ("classic" if a.prec == "fp64" else "gmres")]
     max_iter = a.max_iter if a.max_iter is not None else (10 if a.prec == "fp64" or method == 1 else 30)
@@ -535,6 +539,7 @@ def run_ours(a, emit=True):
     peaks = measured_peaks()
     if a.prec == "sliced" and tc_prof and tc_prof[2] > 0:
         nd = lib.genp_sliced_digits(0)
+        pd = lib.genp_sliced_precondition_digits(0)
         pairs = nd * (nd + 1) // 2
         t_ms, t_fl, t_n = tc_prof
         # the method's own work: each launch is an FP64-class product of 2 m n K
@@ -553,12 +558,12 @@ def run_ours(a, emit=True):
                                    "Schur updates)",
                     "tensor_pipe": {"achieved": pipe, "frac": pipe / peak, "unit": "TFLOP/s",
                                     "counted": "BF16 digit-pair products actually issued (2 m n Kpad per pair)"},
-                    # dram read + write bytes of one n = 4096 A G chunk launch (k_tc_sliced<2, 7>,
-                    # K = 1024, column-major tile order) under ncu, 303.5 MB (the double-float
-                    # accumulator's read-modify-write 268 MB, the digit slices 75 MB read about
+                    # dram read + write bytes of one n = 4096 A G chunk launch (k_tc_sliced<2, 5>,
+                    # K = 1024, column-major tile order) under ncu, 282.0 MB (the double-float
+                    # accumulator's read-modify-write 268 MB, the digit slices 59 MB read about
                     # once), scaled by the n^2 output tiles to this size's chunk launches
-                    "traffic": 303.5e6 * (n / 4096) ** 2 if nd == 7 else None,
-                    "traffic_basis": "A G chunk launch (K = 1024) of k_tc_sliced<2, 7>; ncu at n = 4096 scaled by "
+                    "traffic": 282.0e6 * (n / 4096) ** 2 if (nd == 7 and pd == 5) else None,
+                    "traffic_basis": "A G chunk launch (K = 1024) of k_tc_sliced<2, 5>; ncu at n = 4096 scaled by "
                                      "n^2; Schur-update launches (K = 256) move about a quarter of it per tile"}
     elif a.prec == "fp8" and tc_launches:
         # per launch: the A G product (K = n, k_tc_e4m3, tensor-bound) and the
@@ -697,7 +702,8 @@ def other_configs(a):
     import copy
     base = copy.copy(a)
     base.no_e2e = base.no_cpu_baseline = base.no_clocks = base.no_fp64_compare = True
-    base.digits = base.precond_digits = 0
+    base.digits = 0
+    base.precond_digits = None
     base.refine = base.max_iter = None
     base.count = None
     runs = [("n256_fp64_gaussian_1rhs", run_ours, dict(workload="lead", n=256, nrhs=1, prec="fp64",

@@ -132,3 +132,80 @@ def test_n16384_sliced_gmres_bench_system(g):
     fwd2 = np.linalg.norm(x - xs) / np.linalg.norm(xs)
     assert fwd2 <= 1e-14 * kappa, fwd2
     assert math.isfinite(info.bwd_err[0]) and info.bwd_err[0] > eta    # refinement did the work
+
+
+def test_batched_10k_bench_recipe_sampled(g):
+    """The 10k batch as the bench runs it (n uniform in [16, 512], a_11 = 0,
+    4 RHS, FP32 factors, FP64 GMRES-IR, double-float escalation): every
+    system's reported backward error <= 1e-14, and on 24 sampled systems
+    (the largest, the smallest, every escalated one, and a spread) the
+    oracle's backward error of the returned X <= 1e-14 and its forward error
+    against the GEPP solution <= 1e-14 kappa_inf(A)."""
+    from paper_1212_4560_gb300 import batched as Bt
+    count, nrhs = 10000, 4
+    sizes = W.batched_sizes(count, 16, 512, seed=0)
+    plan = Bt.BatchedPlan(sizes, nrhs, kind=g.GAUSSIAN, a_dtype=torch.float64, max_iter=10, tol=1e-14,
+                          escalate=True)
+    Ap = torch.empty(plan.mat_size, dtype=torch.float64, device=DEV)
+    Bp = torch.empty(plan.vec_size, dtype=torch.float64, device=DEV)
+    gen = torch.Generator(device=DEV)
+    gen.manual_seed(7919)
+    for i, n in enumerate(sizes):
+        Ai = torch.randn(n, n, generator=gen, device=DEV, dtype=torch.float64)
+        Ai[0, 0] = 0.0
+        Xi = torch.randn(n, nrhs, generator=gen, device=DEV, dtype=torch.float64)
+        Ap[plan.mat_off[i]:plan.mat_off[i + 1]] = Ai.reshape(-1)
+        Bp[plan.vec_off[i]:plan.vec_off[i + 1]] = (Ai @ Xi).reshape(-1)
+    Xp = torch.empty_like(Bp)
+    plan.run(1, Ap, Bp, Xp)
+    st = plan.status()
+    assert np.all(st["eta"] <= 1e-14), (int(np.sum(st["eta"] > 1e-14)), float(st["eta"].max()))
+    sz = np.asarray(sizes)
+    pick = set(np.nonzero(st["escalated"] > 0)[0][:8].tolist())
+    pick |= {int(np.argmax(sz)), int(np.argmin(sz))}
+    pick |= set(np.linspace(0, count - 1, 24 - len(pick)).astype(int).tolist())
+    A_h, B_h, X_h = host(Ap), host(Bp), host(Xp)
+    for i in sorted(pick):
+        n = int(sz[i])
+        A = A_h[plan.mat_off[i]:plan.mat_off[i + 1]].reshape(n, n)
+        b = B_h[plan.vec_off[i]:plan.vec_off[i + 1]].reshape(n, nrhs)
+        x = X_h[plan.vec_off[i]:plan.vec_off[i + 1]].reshape(n, nrhs)
+        assert oracle.backward_error(A, x, b) <= 1e-14, i
+        xd = oracle.gepp_solve(A, b)
+        kappa = np.abs(A).sum(axis=1).max() * np.abs(np.linalg.inv(A)).sum(axis=1).max()
+        assert np.abs(x - xd).max() / np.abs(xd).max() <= 1e-14 * kappa, i
+
+
+def test_diff_256x1024_bench_recipe_sampled(g):
+    """The differentiable workload as the bench runs it (256 systems of
+    n = 1024, A = N(0,1) + 0.1 n I in FP32, circulant G, 8 RHS, forward and
+    adjoint with loss 0.5 ||X||^2): on 4 sampled systems the oracle's
+    backward error of X (against the FP32 A actually solved) <= 1e-14, dB =
+    Lambda within 1e-10 of the oracle's A^{-T} X (GEPP on A^T), and dA
+    (FP32 output) within 1e-6 of -Lambda X^T, entry by entry against
+    |Lambda| |X|^T."""
+    from paper_1212_4560_gb300 import batched as Bt
+    batch, n, nrhs = 256, 1024, 8
+    A, _, Bm = W.shifted(batch, n, nrhs, seed=0, device=DEV, dtype=torch.float32)
+    Ap = A.reshape(-1).contiguous()
+    Bp = Bm.double().reshape(-1).contiguous()
+    plan = Bt.BatchedPlan([n] * batch, nrhs, kind=g.CIRCULANT, a_dtype=torch.float32, max_iter=10, tol=1e-14)
+    Xp = torch.empty_like(Bp)
+    dA = torch.empty(plan.mat_size, dtype=torch.float32, device=DEV)
+    dB = torch.empty_like(Bp)
+    plan.run(1, Ap, Bp, Xp)
+    plan.adjoint(Ap, Xp, Xp, dA, dB)
+    st = plan.status()
+    assert np.all(st["eta"] <= 1e-14)
+    A_h, B_h, X_h, dA_h, dB_h = host(Ap), host(Bp), host(Xp), host(dA), host(dB)
+    for i in (0, 77, 128, 255):
+        Ai = A_h[plan.mat_off[i]:plan.mat_off[i + 1]].reshape(n, n).astype(np.float64)
+        b = B_h[plan.vec_off[i]:plan.vec_off[i + 1]].reshape(n, nrhs)
+        x = X_h[plan.vec_off[i]:plan.vec_off[i + 1]].reshape(n, nrhs)
+        assert oracle.backward_error(Ai, x, b) <= 1e-14, i
+        dA_ref, dB_ref = oracle.adjoint(Ai, x, x)
+        lam = dB_h[plan.vec_off[i]:plan.vec_off[i + 1]].reshape(n, nrhs)
+        assert np.linalg.norm(lam - dB_ref) <= 1e-10 * np.linalg.norm(dB_ref), i
+        da = dA_h[plan.mat_off[i]:plan.mat_off[i + 1]].reshape(n, n)
+        scale = np.abs(dB_ref) @ np.abs(x).T
+        assert np.all(np.abs(da - dA_ref) <= 1e-6 * scale + 1e-300), i

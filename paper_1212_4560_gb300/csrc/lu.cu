@@ -401,12 +401,13 @@ cudaError_t factor_tc(genp_factors *F, cudaStream_t s) {
 
 // GENP_BF16_SLICED: blocked GENP in two levels on the double-float copy W
 // of C.  The outer block column (2 nb wide) is factored by two inner steps of
-// width nb (diagonal block, block row and column, and the update of the
-// second inner block by the first), all in double-float on the FP32 pipe;
-// the finished block column and block row are then rounded into C (exactly:
-// a double-float value has 48 significant bits), and the outer Schur update
-// W22 -= L21 U12 (K = 2 nb) runs on the tensor cores by exact digit slicing
-// of the FP64 factors.  C ends up holding the factors.
+// width nb: diagonal block and block row and column in double-float on the
+// FP32 pipe, and the update of the second inner block (column and row) by
+// the first on the tensor cores; the finished block column and block row are
+// then rounded into C (exactly: a double-float value has 48 significant
+// bits), and the outer Schur update W22 -= L21 U12 (K = 2 nb) runs on the
+// tensor cores by exact digit slicing of the FP64 factors.  C ends up
+// holding the factors.
 cudaError_t factor_sliced(genp_factors *F, cudaStream_t s) {
     double *C = static_cast<double *>(F->C);
     dfloat *W = static_cast<dfloat *>(F->W);
@@ -426,13 +427,25 @@ cudaError_t factor_sliced(genp_factors *F, cudaStream_t s) {
             if (e != cudaSuccess) return e;
             if (rem <= 0) break;
             if (j0 < e0) {
-                // the rest of the outer block column, and its block row beyond it
+                // the rest of the outer block column, and its block row beyond it,
+                // by the sliced product too: this inner step's L (rows j0..n) and U
+                // (columns j0..n) are final, so they go to C in FP64 (exactly) and
+                // are sliced once for both updates
                 const int64_t w2 = e0 - j0;
-                e = gemm_df_sub(rem, w2, kb, W + j0 * ldw + i0, ldw, W + i0 * ldw + j0, ldw, W + j0 * ldw + j0, ldw,
-                                s);
+                double *Lc = C + j0 * ldc + i0;
+                double *Uc = C + i0 * ldc + j0;
+                unsigned long long *kk = reinterpret_cast<unsigned long long *>(F->exps + 2 * n);
+                e = df_to_f64(W + j0 * ldw + i0, ldw, Lc, ldc, rem, kb, s);
+                if (e == cudaSuccess) e = df_to_f64(W + i0 * ldw + j0, ldw, Uc, ldc, kb, rem, s);
+                if (e == cudaSuccess) e = sliced_inner_exps(Lc, ldc, rem, kb, kk, s);
+                if (e == cudaSuccess) e = slice_rows(F->nd, Lc, ldc, rem, kb, F->tcA, ldq, F->exps, s, kk);
+                if (e == cudaSuccess) e = slice_cols_T(F->nd, Uc, ldc, kb, rem, F->tcB, ldq, F->exps + n, s, kk);
+                if (e == cudaSuccess)
+                    e = tc_gemm_sliced(F->nd, rem, w2, sliced_kpad(kb), -1.0f, F->tcA, ldq, F->tcB, ldq, F->exps,
+                                       F->exps + n, W + j0 * ldw + j0, ldw, s);
                 if (e == cudaSuccess && remo > 0)
-                    e = gemm_df_sub(w2, remo, kb, W + j0 * ldw + i0, ldw, W + i0 * ldw + e0, ldw,
-                                    W + j0 * ldw + e0, ldw, s);
+                    e = tc_gemm_sliced(F->nd, w2, remo, sliced_kpad(kb), -1.0f, F->tcA, ldq, F->tcB + w2 * ldq, ldq,
+                                       F->exps, F->exps + n + w2, W + j0 * ldw + e0, ldw, s);
                 if (e != cudaSuccess) return e;
             }
         }

@@ -149,24 +149,39 @@ def test_precondition_sliced(g, pdigits, n):
     assert np.median(err / np.abs(ref)) <= 2.0 ** -(7 * digits - 5)
 
 
-def sliced_update_scale(L, U, nbo):
-    """S_ij = sum over the outer steps b that update entry (i, j) of
-    K_b max_k |l_ik| 2^-q_k max_k |u_kj| 2^q_k (k in the step's block
-    column, K_b its width): the sliced Schur update L21 U12 is formed as
+def _balanced(Lb, Ub):
+    q = np.frexp(Lb.max(axis=0))[1].astype(float)
+    r = (Lb * 2.0 ** -q[None, :]).max(axis=1)
+    c = (Ub * 2.0 ** q[:, None]).max(axis=0)
+    return r, c
+
+
+def sliced_update_scale(L, U, nbo, nb):
+    """S_ij = sum over the sliced products that update entry (i, j) of
+    K max_k |l_ik| 2^-q_k max_k |u_kj| 2^q_k (k over the product's inner
+    dimension, K its width).  A product L21 U12 is formed as
     (L21 D^-1)(D U12), D = diag(2^q_k) with q_k the least e such that
-    max_i |l_ik| < 2^e over the step's L21 (frexp, 0 for a zero column), and
-    its digit slices share one scale per row of L21 D^-1 and per column of
-    D U12."""
+    max_i |l_ik| < 2^e over its L21 (frexp, 0 for a zero column), and its
+    digit slices share one scale per row of L21 D^-1 and per column of
+    D U12.  The products: each outer step's Schur update (K = nbo) of the
+    trailing matrix, and, inside an outer step, the first inner step's
+    update (K = nb) of the rest of the outer block column and of the block
+    row beyond it."""
     n = L.shape[0]
     S = np.zeros((n, n))
     for k0 in range(0, n, nbo):
         e0 = min(k0 + nbo, n)
+        for i0 in range(k0, e0, nb):
+            j0 = min(i0 + nb, e0)
+            if j0 >= e0 or j0 >= n:
+                continue
+            r, c = _balanced(np.abs(L[j0:, i0:j0]), np.abs(U[i0:j0, j0:]))
+            # rows j0.. against columns j0..e0, and rows j0..e0 against columns e0..
+            S[j0:, j0:e0] += (j0 - i0) * r[:, None] * c[None, :e0 - j0]
+            S[j0:e0, e0:] += (j0 - i0) * r[:e0 - j0, None] * c[None, e0 - j0:]
         if e0 >= n:
             break
-        Lb, Ub = np.abs(L[e0:, k0:e0]), np.abs(U[k0:e0, e0:])
-        q = np.frexp(Lb.max(axis=0))[1].astype(float)
-        r = (Lb * 2.0 ** -q[None, :]).max(axis=1)
-        c = (Ub * 2.0 ** q[:, None]).max(axis=0)
+        r, c = _balanced(np.abs(L[e0:, k0:e0]), np.abs(U[k0:e0, e0:]))
         S[e0:, e0:] += (e0 - k0) * r[:, None] * c[None, :]
     return S
 
@@ -174,13 +189,14 @@ def sliced_update_scale(L, U, nbo):
 @pytest.mark.parametrize("digits", [5, 6, 7], indirect=True)
 @pytest.mark.parametrize("n,nb", [(96, 0), (300, 0), (520, 128), (700, 64)])
 def test_factor_sliced_backward_error(g, digits, n, nb):
-    """|L U - C|_ij <= 2^-(7 nd - 6) S_ij + 3 n u_df |L||U|_ij + (n / 2nb + 2) u_df |C|_ij
-    with u_df = 2^-46: each outer Schur update errs by the sliced product's
-    2^-(7 nd - 5) K against the row and column maxima of its balanced
-    operands (S, see sliced_update_scale); the double-float panels, block
-    solves and inner updates err as an LU in a 48-bit arithmetic (Higham,
-    Thm. 9.3, u_df allowing two bits for the pair arithmetic), and the
-    double-float trailing matrix rounds once per outer update."""
+    """|L U - C|_ij <= 2^-(7 nd - 6) S_ij + 3 n u_df |L||U|_ij + (n / nb + 2) u_df |C|_ij
+    with u_df = 2^-46: each sliced update (outer Schur updates and the inner
+    block updates) errs by the sliced product's 2^-(7 nd - 5) K against the
+    row and column maxima of its balanced operands (S, see
+    sliced_update_scale); the double-float diagonal blocks and block solves
+    err as an LU in a 48-bit arithmetic (Higham, Thm. 9.3, u_df allowing two
+    bits for the pair arithmetic), and the double-float trailing matrix
+    rounds once per update."""
     A, _, _ = W.lead_deficient(n, 16, 8, 1, seed=n + 1)
     C0 = oracle.precondition(A.numpy(), oracle.multiplier(0, n, seed=5))
     C = cu(C0)
@@ -190,9 +206,9 @@ def test_factor_sliced_backward_error(g, digits, n, nb):
     assert g._lib.load().genp_device_check(1) == 0
     L, U = oracle.split_lu(C.cpu().numpy())
     nbo = 2 * (nb or 128)
-    S = sliced_update_scale(L, U, nbo)
+    S = sliced_update_scale(L, U, nbo, nb or 128)
     u_df = 2.0 ** -46
-    df = 3 * n * u_df * (np.abs(L) @ np.abs(U)) + (n / nbo + 2) * u_df * np.abs(C0)
+    df = 3 * n * u_df * (np.abs(L) @ np.abs(U)) + (n / (nb or 128) + 2) * u_df * np.abs(C0)
     err = np.abs(L @ U - C0)
     assert np.all(err <= 2.0 ** -(7 * digits - 6) * S + df)
     # the bound is not slack by orders of magnitude: a lost digit group would pass it only at larger errors

@@ -85,6 +85,7 @@ def parse():
     p.add_argument("--refine", default=None, choices=["classic", "gmres"],
                    help="refinement method (default: classic for fp64, GMRES-IR otherwise)")
     p.add_argument("--max-iter", type=int, default=None)
+    p.add_argument("--nb", type=int, default=0, help="factorization block (0: the library's default)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
@@ -382,7 +383,7 @@ def run_ours(a, emit=True):
     kind = KINDS[a.kind]
     G = genp.make_multiplier(kind, n, seed=1, stream_id=rank, value_grid=GRID_OF[a.prec])
     genp.precondition(G, A, C, c_prec=prec)
-    F = genp.factor(C, prec=prec)
+    F = genp.factor(C, prec=prec, nb=a.nb)
     stream = torch.cuda.current_stream(dev)
 
     def step(i, ev=None, Ain=None, Bin=None):
@@ -735,8 +736,8 @@ def other_configs(a):
 
 PROF_CLASSES = {1: ("k_trsv", "streaming triangular solves; bytes = the factor's triangle, n^2/2 x 8 B per pass"),
                 2: ("k_gemv", "x = G y, r = b - A x, the Krylov products A (G v); bytes = the matrix, n^2 x 8 B"),
-                3: ("factor_aux", "factorization off the tensor cores: k_panel_reg, k_trsm_reg, k_gemm<dfloat>; "
-                                  "flops of the diagonal blocks, block rows / columns and inner updates"),
+                3: ("factor_aux", "factorization off the tensor cores: k_panel_reg, k_trsm_reg (double-float on "
+                                  "the sliced path); flops of the diagonal blocks and block rows / columns"),
                 4: ("k_outer", "adjoint dA = -Lambda X^T; bytes = dA written"),
                 5: ("precondition_structured", "C = A G by the circulant FFT (k_circ_apply) or the sparse signed "
                                                "gather (k_sparse_pre); bytes = A read + C written, 16 n^2")}

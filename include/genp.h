@@ -122,9 +122,10 @@ typedef enum {
  *        a2b2 + a3b1), which brings the tensor-core products close to FP32
  *        accuracy at six times the BF16 work.
  *  BF16_SLICED: C and the factors are double, as for FP64; the diagonal
- *        blocks and the block row and column are solved in FP64, while the
- *        Schur-complement product (and, for a Gaussian multiplier, A G) runs
- *        on the BF16 tensor cores: each FP64 operand row / column gets a
+ *        blocks and the block row and column are solved in double-float
+ *        arithmetic (48 bits, on the FP32 pipe), while the Schur-complement
+ *        products (and, for a Gaussian multiplier, A G) run on the BF16
+ *        tensor cores: each FP64 operand row / column gets a
  *        power-of-two scale and is cut into 5, 6 or 7 exact 7-bit digits
  *        (genp_sliced_digits; A G takes genp_sliced_precondition_digits),
  *        and the digit products of the leading
@@ -133,9 +134,11 @@ typedef enum {
  *        7 digits the products carry about 46 correct bits against the
  *        operands' scales; the trailing matrix is held as double-float pairs
  *        (48 bits) between steps.  The diagonal blocks and block rows and
- *        columns are solved nb wide in FP64; the tensor-core Schur updates
- *        take blocks of 2 nb.  FP64 refinement (GMRES-IR at large growth)
- *        takes the solve to FP64 accuracy. */
+ *        columns are solved nb wide; the tensor-core updates take outer
+ *        blocks of max(2 nb, 256) and, inside them, the inner blocks'
+ *        updates (the inner dimension of every update balanced by powers of
+ *        two).  FP64 refinement (GMRES-IR at large growth) takes the solve
+ *        to FP64 accuracy. */
 typedef enum {
     GENP_FP64 = 0,
     GENP_FP32 = 1,
@@ -625,9 +628,9 @@ GENP_API genp_status genp_profile_launches(double *ms, double *flops, int cap, i
  *      Krylov products A (G v)); work = bytes of the matrix read, m k x
  *      element size per launch.
  *  GENP_PROF_FACTOR_AUX (3): the factorization's kernels off the tensor
- *      cores (diagonal blocks, block row and column, inner updates of the
- *      sliced path); work = flops (nb^3 2/3 per diagonal block, nb^2 w per
- *      block row or column of width w, 2 m n k per inner update).
+ *      cores (diagonal blocks, block row and column, the pivot-block
+ *      inverses of block GE); work = flops (nb^3 2/3 per diagonal block,
+ *      nb^2 w per block row or column of width w).
  *  GENP_PROF_OUTER (4): the adjoint's dA = -Lambda X^T; work = bytes of dA
  *      written.
  *  GENP_PROF_PRECOND (5): C = A G for the circulant (FFT) and sparse

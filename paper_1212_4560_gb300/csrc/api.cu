@@ -767,7 +767,7 @@ genp_status new_factors(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t
     }
     if (st == GENP_OK && prec == GENP_BF16_SLICED) {
         F->nd = sliced_digits();
-        F->tc_ldq = (int64_t)F->nd * sliced_kpad(2 * nb);   // outer steps of 2 nb
+        F->tc_ldq = (int64_t)F->nd * sliced_kpad(2 * nb > kSlicedOuter ? 2 * nb : kSlicedOuter);   // outer steps
         F->ldw = round8(n);   // 16-byte aligned rows for the vectorized epilogue
         st = dalloc(&F->tcA, (size_t)n * F->tc_ldq);
         if (st == GENP_OK) st = dalloc(&F->tcB, (size_t)n * F->tc_ldq);

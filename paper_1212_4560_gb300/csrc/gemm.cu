@@ -321,20 +321,6 @@ unsigned int gemv_skipped_count(bool reset) {
     return v;
 }
 
-// D <- D - A B in double-float (the inner block updates of the sliced
-// factorization): the same register-tiled kernel, 64 x 64 tiles, every
-// multiply-add a double-float one on the FP32 pipe.
-cudaError_t gemm_df_sub(int64_t m, int64_t n, int64_t k, const dfloat *A, int64_t lda, const dfloat *B, int64_t ldb,
-                        dfloat *D, int64_t ldd, cudaStream_t s) {
-    if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
-    auto *ev = profile_class_slot(kProfFactorAux, 2.0 * (double)m * (double)n * (double)k);
-    prof_begin(ev, s);
-    const cudaError_t e = run<dfloat, 64, 64, 16, 4, 4, false, kDense, kDense>(
-        m, n, k, dfloat(-1), A, lda, B, ldb, dfloat(1), D, ldd, D, ldd, nullptr, nullptr, 1, s);
-    prof_end(ev, s);
-    return e;
-}
-
 template cudaError_t gemm<double>(int64_t, int64_t, int64_t, double, const double *, int64_t, bool,
                                   const double *, int64_t, double, const double *, int64_t, double *, int64_t,
                                   const int *, cudaStream_t);

@@ -331,6 +331,7 @@ cudaError_t df_to_f64_T(const dfloat *src, int64_t lds, double *dst, int64_t ldd
 cudaError_t sliced_matmul(int nd, int64_t m, int64_t n, int64_t K, const double *A, int64_t lda, const double *B,
                           int64_t ldb, dfloat *D, int64_t ldd, __nv_bfloat16 *Aq, __nv_bfloat16 *Bq, int *exps,
                           cudaStream_t s, int ndb = 0);
+constexpr int kSlicedOuter = 256;       // outer step (Schur update K) of the sliced factorization
 constexpr int64_t kSlicedChunk = 512;   // keeps the digit groups of weight >= 2^-49 exact in FP32
 // With a two-digit M side (a multiplier on the sliced grid) a group holds at
 // most two pairs of |d_t d_u| <= 2^13 (one pair of 2^14 for group 0), so
@@ -408,10 +409,6 @@ cudaError_t launch_batched_escalate(const BatchDesc *d, int count, int *counter,
 // lu.cu
 cudaError_t factor_run(genp_factors *F, cudaStream_t s);
 cudaError_t status_reset(genp_factors *F, cudaStream_t s);
-
-// gemm.cu: D <- D - A B in double-float (row-major, m x k times k x n)
-cudaError_t gemm_df_sub(int64_t m, int64_t n, int64_t k, const dfloat *A, int64_t lda, const dfloat *B, int64_t ldb,
-                        dfloat *D, int64_t ldd, cudaStream_t s);
 
 // lowrank.cu: randomized low-rank approximation (Proto-Alg. 5.1)
 cudaError_t lowrank_run(int64_t m, int64_t n, const double *A, int64_t lda, int64_t r, bool toeplitz, uint64_t seed,

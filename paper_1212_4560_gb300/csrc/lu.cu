@@ -412,7 +412,8 @@ cudaError_t factor_sliced(genp_factors *F, cudaStream_t s) {
     double *C = static_cast<double *>(F->C);
     dfloat *W = static_cast<dfloat *>(F->W);
     const int64_t n = F->n, ldc = F->ldc, ldw = F->ldw, ldq = F->tc_ldq;
-    const int nb = (int)F->nb, nbo = 2 * nb;
+    // outer steps of 256 (the tensor-core Schur updates' K), inner steps of nb
+    const int nb = (int)F->nb, nbo = 2 * nb > kSlicedOuter ? 2 * nb : kSlicedOuter;
     note_launch();
     k_maxabs<double><<<152 * 4, 256, 0, s>>>(C, n, ldc, &F->st->max_abs_c);
     cudaError_t e = df_from_f64(C, ldc, W, ldw, n, n, s);

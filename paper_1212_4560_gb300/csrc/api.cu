@@ -756,6 +756,10 @@ genp_status new_factors(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t
     if (st == GENP_OK) st = dalloc(&F->norms, 2);
     if (st == GENP_OK) st = dalloc(&F->trsv_sync, (size_t)trsv_sync_ints(n));
     if (st == GENP_OK) {
+        if (f64_factors(prec)) st = dalloc(reinterpret_cast<double **>(&F->trsv_y), (size_t)trsv_y_elems(n));
+        else st = dalloc(reinterpret_cast<float **>(&F->trsv_y), (size_t)trsv_y_elems(n));
+    }
+    if (st == GENP_OK) {
         if (f64_factors(prec)) st = dalloc(reinterpret_cast<double **>(&F->dinv), (size_t)diag_inverse_elems(n));
         else st = dalloc(reinterpret_cast<float **>(&F->dinv), (size_t)diag_inverse_elems(n));
     }
@@ -773,7 +777,8 @@ genp_status new_factors(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t
         if (st == GENP_OK) st = dalloc(&F->tcB, (size_t)n * F->tc_ldq);
         if (st == GENP_OK) st = dalloc(reinterpret_cast<double **>(&F->W), (size_t)n * F->ldw);
         if (st == GENP_OK) st = dalloc(&F->exps, (size_t)2 * n + 4 * 128);   // + 2 nb inner-dimension keys (8 B)
-        if (st == GENP_OK) st = dalloc(reinterpret_cast<double **>(&F->dinv_df), (size_t)diag_inverse_elems(n));
+        // the inverses, then the masked diagonal blocks, as double-float pairs
+        if (st == GENP_OK) st = dalloc(reinterpret_cast<double **>(&F->dinv_df), (size_t)(2 * diag_inverse_elems(n)));
     }
     if (st == GENP_OK && cudaMallocHost(&F->host_info, sizeof(DevStatus)) != cudaSuccess) {
         cudaGetLastError();
@@ -819,6 +824,7 @@ void genp_factors_destroy(genp_factors *F) {
     cudaFree(F->W);
     cudaFree(F->exps);
     cudaFree(F->trsv_sync);
+    cudaFree(F->trsv_y);
     cudaFree(F->dinv);
     cudaFree(F->dinv_df);
     if (F->host_info) cudaFreeHost(F->host_info);

@@ -1013,6 +1013,19 @@ cudaError_t launch_sliced(const CUtensorMap &ma, const CUtensorMap &mb, int64_t 
 
 }  // namespace
 
+bool make_map_8b(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_cols,
+                 int box_rows) {
+    auto fn = encoder();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 8)};
+    cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t tc_gemm_sliced(int nd, int64_t m, int64_t n, int64_t kpad, float alpha, const __nv_bfloat16 *Aq,
                            int64_t lda, const __nv_bfloat16 *Bq, int64_t ldb, const int *ea, const int *fb, dfloat *D,
                            int64_t ldd, cudaStream_t s) {

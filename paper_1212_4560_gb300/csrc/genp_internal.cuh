@@ -3,6 +3,7 @@
 
 #include <utility>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -107,8 +108,9 @@ struct genp_factors {
     int *exps = nullptr;               // 2n slicing exponents (GENP_BF16_SLICED)
     int nd = 0;                        // digits per operand (GENP_BF16_SLICED)
     int *trsv_sync = nullptr;          // tickets and block counters of the triangular solves
+    void *trsv_y = nullptr;            // the solves' published blocks of y, n x 16 (factor type)
     void *dinv = nullptr;              // inverses of the 64 x 64 diagonal blocks of L and U (factor type)
-    void *dinv_df = nullptr;           // their double-float copy (GENP_BF16_SLICED)
+    void *dinv_df = nullptr;           // their double-float copy, then the masked diagonal blocks (GENP_BF16_SLICED)
     bool block = false;                // block GE factors (genp_block_factor): C = L_B U_B
     cudaStream_t last_stream = nullptr;
 };
@@ -436,8 +438,16 @@ cudaError_t refine_check(genp_factors *F, const double *R, int64_t ldr, const do
 int solve_timeout_flag(bool reset);
 // ints of synchronization state a triangular solve of order n needs
 int64_t trsv_sync_ints(int64_t n);
+int64_t trsv_y_elems(int64_t n);
 // elements of F->dinv, and its computation (after every factorization)
 int64_t diag_inverse_elems(int64_t n);
+// gemm_tc.cu: 2-D tensor map (TMA) of a rows x cols row-major matrix of
+// 8-byte elements (FP64, or double-float pairs), leading dimension ld, for
+// boxes of box_rows x box_cols, no swizzle; elements past rows or cols read
+// as zero.  False when the driver cannot encode it (ptr and ld * 8 must be
+// 16-byte aligned, box_cols * 8 a multiple of 16, both box sides <= 256).
+bool make_map_8b(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_cols,
+                 int box_rows);
 cudaError_t invert_diag_blocks(genp_factors *F, cudaStream_t s);
 // block.cu: block Gaussian elimination of F->C with explicit pivot-block
 // inverses (nb = 64), the inverses written to F->dinv.

@@ -209,7 +209,9 @@ __global__ void __launch_bounds__(256) k_outer_rows(const double *Lam, int64_t l
 // 64 x 64 tiles and the diagonal blocks are taken one after the other (block
 // j(q) at step q: j = q forward, nblk-1-q backward).  The CTA that draws
 // ticket 0 walks the diagonal: for each block it applies the precomputed
-// inverse of the diagonal tile plus one refinement step, publishes y_j, and
+// inverse of the diagonal tile plus one refinement step, publishes y_j (into a
+// buffer filled with an all-ones NaN before the launch, which no result
+// takes: a reader sees each value land without a fence or flag), and
 // subtracts op(T)[next][j] y_j from the next block itself, so the chain from
 // one block to the next never waits on another CTA.  Every other ticket is a
 // work item that sums op(T)[i][j(p)] y_j(p) over up to kSeg earlier steps p
@@ -223,7 +225,10 @@ __global__ void __launch_bounds__(256) k_outer_rows(const double *Lam, int64_t l
 // which hold smaller tickets than anything still waiting, so the launch
 // cannot deadlock (it needs two or more CTAs).  Every wait is bounded: on
 // timeout the kernel sets a device flag (read by genp_device_check) and goes
-// on.
+// on.  In double-float (the sliced path's factors) the walker's tiles (the
+// inverse, the masked diagonal block, the next block's tile) come by TMA a
+// step before they are needed, into shared memory: one SM's own loads of
+// three 32 KiB tiles per step were what set the pace.
 // ---------------------------------------------------------------------------
 constexpr int TB = 64;          // tile
 constexpr int kSeg = 16;        // tiles per work item
@@ -237,16 +242,45 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release(int *p, int v) {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+// The published y values: relaxed (GPU scope, single-copy atomic) stores and
+// loads of the value itself; the empty mark is all-ones, which a published
+// value never is (a NaN with that bit pattern goes out as the default NaN).
+__device__ __forceinline__ void publish_y(double *p, double v) {
+    long long b = __double_as_longlong(v);
+    if (b == -1LL) b = 0x7ff8000000000000LL;
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(b) : "memory");
 }
-// Publishes a flag for the writes the whole CTA made before a __syncthreads:
-// the barrier orders them before this thread's fence, and the fence and the
-// release store (both GPU scope, cumulative) make them visible to any thread
-// that reads the flag with acquire semantics.
-__device__ __forceinline__ void publish(int *p) {
-    __threadfence();
-    st_release(p, 1);
+__device__ __forceinline__ void publish_y(float *p, float v) {
+    unsigned b = __float_as_uint(v);
+    if (b == 0xffffffffu) b = 0x7fc00000u;
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(b) : "memory");
+}
+__device__ __forceinline__ bool load_y(const double *p, double &v) {
+    long long b;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(b) : "l"(p) : "memory");
+    v = __longlong_as_double(b);
+    return b != -1LL;
+}
+__device__ __forceinline__ bool load_y(const float *p, float &v) {
+    unsigned b;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(b) : "l"(p) : "memory");
+    v = __uint_as_float(b);
+    return b != 0xffffffffu;
+}
+// a published value, waiting (bounded) for it to land
+template <typename T>
+__device__ T wait_y(const T *p) {
+    T v;
+    if (load_y(p, v)) return v;
+    const long long t0 = clock64();
+    while (!load_y(p, v)) {
+        if (clock64() - t0 > kSpinTicks) {
+            atomicExch(&g_solve_timeout, 1);
+            return T(0);
+        }
+        __nanosleep(32);
+    }
+    return v;
 }
 __device__ bool wait_geq(const int *p, int target) {
     const long long t0 = clock64();
@@ -272,18 +306,64 @@ struct TrsvSmem {
 };
 
 // The walker's shared memory when it runs in double-float (factors held as
-// double-float pairs, GENP_BF16_SLICED): the three tiles as hi / lo FP32
-// planes with a row stride of 68, read with the quarters interleaved along k
-// (quarter q takes k = q + 4 kk), so the 32 lanes of a warp (8 rows x 4
-// quarters) hit 32 different banks; the vectors as double-float pairs.
+// double-float pairs, GENP_BF16_SLICED).  Its tiles are kept as they lie in
+// memory (rows of C, or of the row-major inverse of T_jj), so that each
+// 64-pair row arrives by one bulk copy (TMA) issued a step ahead; the
+// transposed modes read them transposed.  A row stride of 68 pairs keeps the
+// tile products' reads free of bank conflicts either way (with the quarters
+// interleaved along k, k = quarter + 4 kk, a half warp's 4 rows x 4 quarters
+// hit 16 different 8-byte bank pairs).  X is double-buffered by step parity:
+// step q + 2's inverse goes out as soon as step q has used its own.
 constexpr int kDdLd = 68;
 template <int NR>
 struct TrsvSmemDD {
-    float Sh[TB][kDdLd], Sl[TB][kDdLd];
-    float Dh[TB][kDdLd], Dl[TB][kDdLd];
-    float Oh[TB][kDdLd], Ol[TB][kDdLd];
+    alignas(128) dfloat X[2][TB][kDdLd];   // T_jj^{-1}
+    alignas(128) dfloat D[TB][kDdLd];      // T_jj, its triangle with op(T)'s diagonal
+    alignas(128) dfloat O[TB][kDdLd];      // the tile of op(T)[next][j], as it lies in C
     dfloat y[TB][NR], acc[TB][NR], carry[TB][NR];
+    unsigned long long bar[4];             // tile arrivals: X[0], X[1], D, O
 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void bar_init(unsigned long long *b) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void bar_expect(unsigned long long *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(unsigned long long *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool bar_test(unsigned long long *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded: false after ~2 s
+__device__ bool bar_wait(unsigned long long *b, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!bar_test(b, parity))
+        if (clock64() - t0 > kSpinTicks) return false;
+    return true;
+}
+// a 64 x 68 box of 8-byte elements at column x, row y of the map's matrix,
+// global -> shared by TMA (rows of 68 elements land one after the other,
+// which gives the tile its padded row stride; elements past the matrix read
+// as zero), completing on b
+constexpr uint32_t kDdTileBytes = TB * kDdLd * 8;
+__device__ __forceinline__ void tma_tile(void *dst, const CUtensorMap *map, int x, int y, unsigned long long *b) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(b))
+        : "memory");
+}
 
 // s + t += (ah + al)(v.hi + v.lo): TwoSum of the leading terms, the rounding
 // error of the leading product (by FMA) and the cross terms gathered in t
@@ -298,20 +378,21 @@ __device__ __forceinline__ void dd_mac(float &s, float &t, float ah, float al, d
     t += err + (pe + cross);
 }
 
-// part[c] = sum_k M[r][k] V[k][c] in double-float, summed over the 4 quarter
-// threads of row r (thread = 4 r + quarter)
-template <int NR>
-__device__ __forceinline__ void tile_gemv_dd(const float (*Mh)[kDdLd], const float (*Ml)[kDdLd], const dfloat (*V)[NR],
-                                             int r, int qq, dfloat (&part)[NR]) {
+// part[c] = sum_k M(r, k) V[k][c] in double-float, summed over the 4 quarter
+// threads of row r (thread = 4 r + quarter), for a tile held as pairs:
+// M(r, k) = M[r][k], or M[k][r] when TR.
+template <int NR, bool TR>
+__device__ __forceinline__ void tile_gemv_dd(const dfloat (*M)[kDdLd], const dfloat (*V)[NR], int r, int qq,
+                                             dfloat (&part)[NR]) {
     float s[NR], t[NR];
 #pragma unroll
     for (int c = 0; c < NR; ++c) s[c] = t[c] = 0.f;
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
         const int k = qq + 4 * kk;
-        const float ah = Mh[r][k], al = Ml[r][k];
+        const dfloat a = TR ? M[k][r] : M[r][k];
 #pragma unroll
-        for (int c = 0; c < NR; ++c) dd_mac(s[c], t[c], ah, al, V[k][c]);
+        for (int c = 0; c < NR; ++c) dd_mac(s[c], t[c], a.hi, a.lo, V[k][c]);
     }
 #pragma unroll
     for (int c = 0; c < NR; ++c) {
@@ -385,26 +466,32 @@ __device__ __forceinline__ T tile_elem(const TS *C, int64_t ldc, int n, int mode
 // double-float pairs (Cd, ldcd, Dinvd) and works on the FP32 pipe; the
 // update items still read C.
 template <typename TS, typename T, int NR, bool DD>
-__global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc, int n, const TS *Dinv, T *Y,
+__global__ void __launch_bounds__(kTrsvThreads, 1) k_trsv(const TS *C, int64_t ldc, int n, const TS *Dinv, T *Y,
                                                         int64_t ldy, int nr, int mode, const int *skip, int *sync,
-                                                        const dfloat *Cd, int64_t ldcd, const dfloat *Dinvd) {
+                                                        T *ypub, const dfloat *Cd, int64_t ldcd, const dfloat *Dinvd,
+                                                        const __grid_constant__ CUtensorMap tmC,
+                                                        const __grid_constant__ CUtensorMap tmX) {
     if (skip && *skip) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&g_trsv_skipped, 1u);
         return;
     }
     extern __shared__ __align__(16) unsigned char smraw[];
     TrsvSmem<T, NR> &sm = *reinterpret_cast<TrsvSmem<T, NR> *>(smraw);
-    TrsvSmemDD<NR> &sd = *reinterpret_cast<TrsvSmemDD<NR> *>(smraw);
+    // the walker's tiles are TMA destinations: 128-byte aligned
+    TrsvSmemDD<NR> &sd = *reinterpret_cast<TrsvSmemDD<NR> *>(((uintptr_t)smraw + 127) & ~(uintptr_t)127);
     __shared__ int s_ticket;
     const int tid = threadIdx.x;
     const int nblk = (n + TB - 1) / TB;
     // mode bit 2: factors of block GE (identity diagonal blocks in L, whole
     // pivot blocks on U's diagonal); bits 0-1: the pass, as above
     const bool bge = (mode & 4) != 0;
+    // bit 3: tmC and tmX map the double-float factors and the inverses, so
+    // the walker's tiles come by TMA
+    const bool tma = (mode & 8) != 0;
     mode &= 3;
     const bool forward = (mode == 0 || mode == 2);
     const bool unit = (mode == 0 || mode == 3);
-    int *ticket = sync, *cnt = sync + 2, *ready = sync + 2 + nblk;
+    int *ticket = sync, *cnt = sync + 2;
     const int r = tid >> 2, qq = tid & 3;   // tile_gemv roles
     // per-thread share of a tile load: 16 elements; non-transposed modes walk
     // rows (k fastest), transposed modes walk columns (r fastest)
@@ -451,44 +538,26 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
         for (int e = 0; e < 16; ++e) v[e] = (T)__ldg(X + tid + e * kTrsvThreads);
     };
     auto block_of = [&](int p) { return forward ? p : nblk - 1 - p; };
-    // double-float walker: tiles of op(T) from the double-float factors, the
-    // inverse of the diagonal tile from its double-float copy
-    auto load_tile_d = [&](int i, int j, dfloat (&v)[16]) {
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const int idx = tid + e * kTrsvThreads;
-            const int a = idx >> 6, b = idx & 63;
-            const int rr = mode <= 1 ? a : b, kk = mode <= 1 ? b : a;   // element (rr, kk) of op(T)'s tile
-            const int64_t row = (int64_t)i * TB + rr, col = (int64_t)j * TB + kk;
-            dfloat z(0.0f);
-            if (row < n && col < n) z = (mode <= 1) ? Cd[row * ldcd + col] : Cd[col * ldcd + row];
-            v[e] = z;
-        }
-    };
-    auto load_inv_d = [&](int j, dfloat (&v)[16]) {
-        const dfloat *X = Dinvd + ((int64_t)(unit ? 0 : 1) * nblk + j) * TB * TB;
-#pragma unroll
-        for (int e = 0; e < 16; ++e) v[e] = X[tid + e * kTrsvThreads];
-    };
-    // element e of this thread's share is (rr, kk) of op(T)'s tile
-    // (load_tile_d), or (a, b) of the row-major inverse of T_jj (load_inv_d),
-    // whose transpose is the inverse of op(T)_jj in the transposed modes:
-    // both land at [rr][kk]; kind 1 keeps the diagonal tile's triangle
-    auto store_d = [&](float (*Mh)[kDdLd], float (*Ml)[kDdLd], const dfloat (&v)[16], int kind) {
-#pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const int idx = tid + e * kTrsvThreads;
-            const int a = idx >> 6, b = idx & 63;
-            const int rr = mode <= 1 ? a : b, kk = mode <= 1 ? b : a;
-            dfloat val = v[e];
-            if (kind == 1 && bge) {   // block GE: identity (L_B) or the whole pivot block (U_B)
-                if (unit) val = rr == kk ? dfloat(1.0f) : dfloat(0.0f);
-            } else if (kind == 1) {   // the diagonal tile: its triangle, unit diagonal where op(T) has one
-                if (rr == kk) val = unit ? dfloat(1.0f) : val;
-                else if (forward ? kk > rr : kk < rr) val = dfloat(0.0f);
+    // double-float walker: the 64 x 64 tile at row r0, column c0 of the
+    // row-major pair matrix P (leading dimension ldp, prow x pcol) into M as
+    // it lies there, by one TMA box from map (thread 32) completing on bar,
+    // or, without maps, by plain loads with zero fill past the matrix and one
+    // arrival on bar.  Called by all threads alike.
+    auto issue_tile = [&](dfloat (*M)[kDdLd], const CUtensorMap *map, const dfloat *P, int64_t ldp, int64_t prow,
+                          int64_t pcol, int64_t r0, int64_t c0, unsigned long long *bar) {
+        if (tma) {
+            if (tid == 32) {
+                // the tile's last readers are ordered before this by a block barrier
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                bar_expect(bar, kDdTileBytes);
+                tma_tile(&M[0][0], map, (int)c0, (int)r0, bar);
             }
-            Mh[rr][kk] = val.hi;
-            Ml[rr][kk] = val.lo;
+        } else {
+            for (int idx = tid; idx < TB * TB; idx += kTrsvThreads) {
+                const int rr = idx >> 6, cc = idx & 63;
+                M[rr][cc] = (r0 + rr < prow && c0 + cc < pcol) ? P[(r0 + rr) * ldp + c0 + cc] : dfloat(0.0f);
+            }
+            if (tid == 0) bar_arrive(bar);
         }
     };
 
@@ -500,8 +569,53 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
         const int t = s_ticket;
         if (DD && t == 0) {
             // ---- the walker in double-float (FP32 pipe; FP64 is 64 times
-            // slower on this GPU): the same steps as the FP64 walker below ----
-            dfloat vD[16], vX[16], vO[16];
+            // slower on this GPU): the same steps as the FP64 walker below,
+            // its tiles in shared memory a step before they are needed (one
+            // SM's own loads could not bring three 32 KiB tiles per step in
+            // time) ----
+            const bool tr = mode >= 2;
+            if (tid == 0) {
+                for (int b = 0; b < 4; ++b) bar_init(&sd.bar[b]);
+                asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            }
+            __syncthreads();
+            // phases: the k-th fill of a buffer completes phase k of its barrier;
+            // bit b of wpar is the parity of buffer b's next wait, of ipar that
+            // of its next fill, of filled whether it has had one
+            uint32_t wpar = 0, ipar = 0, filled = 0;
+            bool late = false;
+            auto take = [&](int b) {     // wait for the next fill of buffer b
+                if (!bar_wait(&sd.bar[b], (wpar >> b) & 1u)) {
+                    late = true;
+                    if (tid == 0) atomicExch(&g_solve_timeout, 1);
+                }
+                wpar ^= 1u << b;
+            };
+            auto filled_one = [&](int b) {
+                ipar ^= 1u << b;
+                filled |= 1u << b;
+            };
+            // the inverses and the masked diagonal blocks, [L, U][block][64][64]
+            // each, as one matrix of 64 columns
+            const int64_t xrows = 4 * (int64_t)nblk * TB, xrow0 = (int64_t)(unit ? 0 : 1) * nblk * TB,
+                          drow0 = xrow0 + 2 * (int64_t)nblk * TB;
+            auto fill_x = [&](int q) {   // T_jj^{-1} of step q into X[q & 1]
+                issue_tile(sd.X[q & 1], &tmX, Dinvd, TB, xrows, TB, xrow0 + (int64_t)block_of(q) * TB, 0,
+                           &sd.bar[q & 1]);
+                filled_one(q & 1);
+            };
+            auto fill_c = [&](dfloat (*M)[kDdLd], int bi, int bj, int b) {   // tile (bi, bj) of C
+                issue_tile(M, &tmC, Cd, ldcd, n, n, (int64_t)bi * TB, (int64_t)bj * TB, &sd.bar[b]);
+                filled_one(b);
+            };
+            auto fill_d = [&](int q) {
+                issue_tile(sd.D, &tmX, Dinvd, TB, xrows, TB, drow0 + (int64_t)block_of(q) * TB, 0, &sd.bar[2]);
+                filled_one(2);
+            };
+            auto fill_o = [&](int q) {   // op(T)[block of q + 1][block of q]
+                const int i = block_of(q + 1), j = block_of(q);
+                fill_c(sd.O, tr ? j : i, tr ? i : j, 3);
+            };
             // b_j of the coming step, in registers: its loads go out at the end
             // of the previous step, before the product for the next block, and
             // have landed by the time it is used
@@ -517,15 +631,14 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
                                                                   : 0.0;
                 }
             };
-            load_tile_d(block_of(0), block_of(0), vD);
-            load_inv_d(block_of(0), vX);
+            fill_x(0);
+            if (nblk > 1) fill_x(1);
+            fill_d(0);
+            if (nblk > 1) fill_o(0);
             load_b(block_of(0));
             for (int q = 0; q < nblk; ++q) {
                 const int j = block_of(q);
                 const int bj = min(TB, n - j * TB);
-                __syncthreads();
-                store_d(sd.Dh, sd.Dl, vD, 1);
-                store_d(sd.Sh, sd.Sl, vX, 2);
 #pragma unroll
                 for (int e = 0; e < kBv; ++e) {
                     const int idx = tid + e * kTrsvThreads;
@@ -535,46 +648,59 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
                         sd.acc[rr][c] = q > 0 ? b - sd.carry[rr][c] : b;
                     }
                 }
-                if (q + 1 < nblk) {
-                    load_tile_d(block_of(q + 1), j, vO);
-                    load_tile_d(block_of(q + 1), block_of(q + 1), vD);
-                    load_inv_d(block_of(q + 1), vX);
-                }
+                const dfloat(*X)[kDdLd] = sd.X[q & 1];
+                take(q & 1);
                 __syncthreads();
                 // y = X b;  y += X (b - T y)
                 dfloat part[NR];
-                tile_gemv_dd<NR>(sd.Sh, sd.Sl, sd.acc, r, qq, part);
+                if (tr) tile_gemv_dd<NR, true>(X, sd.acc, r, qq, part);
+                else tile_gemv_dd<NR, false>(X, sd.acc, r, qq, part);
 #pragma unroll
                 for (int c = 0; c < NR; ++c)
                     if ((c & 3) == qq) sd.y[r][c] = part[c];
+                take(2);
                 __syncthreads();
-                tile_gemv_dd<NR>(sd.Dh, sd.Dl, sd.y, r, qq, part);
+                if (tr) tile_gemv_dd<NR, true>(sd.D, sd.y, r, qq, part);
+                else tile_gemv_dd<NR, false>(sd.D, sd.y, r, qq, part);
 #pragma unroll
                 for (int c = 0; c < NR; ++c)
                     if ((c & 3) == qq) sd.acc[r][c] = sd.acc[r][c] - part[c];
                 __syncthreads();
-                tile_gemv_dd<NR>(sd.Sh, sd.Sl, sd.acc, r, qq, part);
+                if (q + 1 < nblk) fill_d(q + 1);      // D is free
+                if (tr) tile_gemv_dd<NR, true>(X, sd.acc, r, qq, part);
+                else tile_gemv_dd<NR, false>(X, sd.acc, r, qq, part);
 #pragma unroll
                 for (int c = 0; c < NR; ++c)
                     if ((c & 3) == qq) {
                         const dfloat yv = sd.y[r][c] + part[c];
                         sd.y[r][c] = yv;
-                        if (r < bj && c < nr) Y[((int64_t)j * TB + r) * ldy + c] = (T)(double)yv;
+                        if (r < bj && c < nr) {
+                            Y[((int64_t)j * TB + r) * ldy + c] = (T)(double)yv;
+                            publish_y(ypub + ((int64_t)j * TB + r) * NR + c, (T)(double)yv);
+                        }
                     }
                 __syncthreads();
-                if (tid == 0) publish(ready + j);
-                if (q + 1 < nblk) {           // own contribution to the next block
-                    store_d(sd.Oh, sd.Ol, vO, 0);
+                if (q + 2 < nblk) fill_x(q + 2);      // this step's X is free
+                if (q + 1 < nblk) {                   // own contribution to the next block
+                    take(3);
                     // the next step's items (earlier steps up to q - 1), then its b
                     if (tid == 0 && q >= 1 && !wait_geq(cnt + block_of(q + 1), q)) atomicExch(&g_solve_timeout, 1);
                     __syncthreads();
                     load_b(block_of(q + 1));
-                    tile_gemv_dd<NR>(sd.Oh, sd.Ol, sd.y, r, qq, part);
+                    if (tr) tile_gemv_dd<NR, true>(sd.O, sd.y, r, qq, part);
+                    else tile_gemv_dd<NR, false>(sd.O, sd.y, r, qq, part);
 #pragma unroll
                     for (int c = 0; c < NR; ++c)
                         if ((c & 3) == qq) sd.carry[r][c] = part[c];
+                    __syncthreads();
+                    if (q + 2 < nblk) fill_o(q + 1);  // O is free
                 }
             }
+            // after a timed-out wait, the copies still in flight land before the
+            // CTA's shared memory goes away (a later phase implies the earlier ones)
+            if (late)
+                for (int b = 0; b < 4; ++b)
+                    if ((filled >> b) & 1u) bar_wait(&sd.bar[b], ((ipar >> b) & 1u) ^ 1u);
             continue;
         }
         if (t == 0) {
@@ -621,10 +747,12 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
                     if ((c & 3) == qq) {
                         const T yv = sm.y[r][c] + part[c];
                         sm.y[r][c] = yv;
-                        if (r < bj && c < nr) Y[((int64_t)j * TB + r) * ldy + c] = yv;
+                        if (r < bj && c < nr) {
+                            Y[((int64_t)j * TB + r) * ldy + c] = yv;
+                            publish_y(ypub + ((int64_t)j * TB + r) * NR + c, yv);
+                        }
                     }
                 __syncthreads();
-                if (tid == 0) publish(ready + j);
                 if (q + 1 < nblk) {           // own contribution to the next block
                     store_tile(sm.O, vO);
                     __syncthreads();
@@ -652,12 +780,11 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
         for (int pp = p0; pp <= p1; ++pp) {
             const int j = block_of(pp);
             const int bj = min(TB, n - j * TB);
-            if (tid == 0 && !wait_geq(ready + j, 1)) atomicExch(&g_solve_timeout, 1);
             __syncthreads();
             store_tile(sm.S, v);
             for (int idx = tid; idx < TB * NR; idx += kTrsvThreads) {
                 const int rr = idx / NR, c = idx % NR;
-                sm.y[rr][c] = (rr < bj && c < nr) ? ldcg(Y + ((int64_t)j * TB + rr) * ldy + c) : T(0);
+                sm.y[rr][c] = (rr < bj && c < nr) ? wait_y(ypub + ((int64_t)j * TB + rr) * NR + c) : T(0);
             }
             __syncthreads();
             if (pp < p1) load_tile(i, block_of(pp + 1), v);
@@ -681,6 +808,26 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(const TS *C, int64_t ldc,
 // Inverses of the 64 x 64 diagonal blocks of L (unit lower, blockIdx.y = 0)
 // and U (upper, blockIdx.y = 1), by column-wise substitution in FP64, stored
 // row-major per block; rows and columns past a ragged last block are zero.
+// The double-float walker's diagonal tiles as the solves use them, after
+// the inverses in its store: [L, U][block][64][64] row-major pairs, L_jj with
+// its unit diagonal and U_jj's upper triangle (for block GE the identity and
+// the whole pivot block), zero past n.
+__global__ void k_diag_tiles_df(const dfloat *W, int64_t ldw, int n, int bge, dfloat *out) {
+    const int j = blockIdx.x, which = blockIdx.y, nblk = gridDim.x;
+    dfloat *o = out + ((int64_t)which * nblk + j) * TB * TB;
+    for (int idx = threadIdx.x; idx < TB * TB; idx += blockDim.x) {
+        const int r = idx >> 6, c = idx & 63;
+        const int64_t row = (int64_t)j * TB + r, col = (int64_t)j * TB + c;
+        dfloat v(0.0f);
+        if (row < n && col < n) {
+            const dfloat w = W[row * ldw + col];
+            if (which == 0) v = (bge || r <= c) ? dfloat(r == c ? 1.0f : 0.0f) : w;
+            else v = (bge || r <= c) ? w : dfloat(0.0f);
+        }
+        o[idx] = v;
+    }
+}
+
 template <typename TS>
 __global__ void __launch_bounds__(TB) k_trtri_diag(const TS *C, int64_t ldc, int n, TS *Dinv) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -714,12 +861,23 @@ __global__ void __launch_bounds__(TB) k_trtri_diag(const TS *C, int64_t ldc, int
     for (int r = 0; r < TB; ++r) out[r * TB + c] = (TS)x[r][c];
 }
 
+// The double-float walker's tensor maps: the factors' pairs (n x n) and the
+// inverses' ([L, U][block][64][64] as 2 nblk 64 rows of 64), boxes of 64
+// rows x 68 pairs.
+struct TrsvMaps {
+    CUtensorMap c, x;
+    bool ok = false;
+};
+
 template <typename TS, typename T, int NR, bool DD>
 cudaError_t launch_trsv(const TS *C, int64_t ldc, int64_t n, const TS *Dinv, T *Y, int64_t ldy, int nr, int mode,
-                        const int *skip, int *sync, const dfloat *Cd, int64_t ldcd, const dfloat *Dinvd,
-                        cudaStream_t s) {
-    const size_t sm = (DD && sizeof(TrsvSmemDD<NR>) > sizeof(TrsvSmem<T, NR>)) ? sizeof(TrsvSmemDD<NR>)
-                                                                               : sizeof(TrsvSmem<T, NR>);
+                        const int *skip, int *sync, T *ypub, const dfloat *Cd, int64_t ldcd, const dfloat *Dinvd,
+                        const TrsvMaps &maps, cudaStream_t s) {
+    static_assert(sizeof(TrsvSmemDD<NR>) + 128 <= 227 * 1024 && sizeof(TrsvSmem<T, NR>) <= 227 * 1024,
+                  "shared memory");
+    // the walker aligns its part to 128 bytes
+    const size_t sm = (DD && sizeof(TrsvSmemDD<NR>) + 128 > sizeof(TrsvSmem<T, NR>)) ? sizeof(TrsvSmemDD<NR>) + 128
+                                                                                     : sizeof(TrsvSmem<T, NR>);
     static int grid = 0;
     if (!grid) {
         if (sm > 48 * 1024)
@@ -736,17 +894,35 @@ cudaError_t launch_trsv(const TS *C, int64_t ldc, int64_t n, const TS *Dinv, T *
         grid = sms * per_sm;
     }
     const int64_t nblk = cdiv(n, TB);
-    cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)(2 + 2 * nblk) * sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(sync, 0, (size_t)(2 + nblk) * sizeof(int), s);
+    // the published y: all ones, the empty mark
+    if (e == cudaSuccess) e = cudaMemsetAsync(ypub, 0xff, (size_t)(nblk * TB * NR) * sizeof(T), s);
     if (e != cudaSuccess) return e;
     // algorithmic bytes: the triangle of the factor read once (double-float
     // pairs are 8 B like FP64)
     auto *ev = profile_class_slot(kProfTrsv, 0.5 * (double)n * (double)n * (DD ? 8.0 : (double)sizeof(TS)));
     prof_begin(ev, s);
     note_launch();
-    k_trsv<TS, T, NR, DD><<<grid, kTrsvThreads, sm, s>>>(C, ldc, (int)n, Dinv, Y, ldy, nr, mode, skip, sync, Cd,
-                                                          ldcd, Dinvd);
+    k_trsv<TS, T, NR, DD><<<grid, kTrsvThreads, sm, s>>>(C, ldc, (int)n, Dinv, Y, ldy, nr,
+                                                          mode | (DD && maps.ok ? 8 : 0), skip, sync, ypub, Cd, ldcd,
+                                                          Dinvd, maps.c, maps.x);
     prof_end(ev, s);
     return cudaGetLastError();
+}
+
+template <typename TS, typename T, bool DD>
+cudaError_t launch_trsv_nr(const TS *C, int64_t ldc, int64_t n, const TS *Dinv, T *Y, int64_t ldy, int nr, int mode,
+                           const int *skip, int *sync, T *yp, const dfloat *Cd, int64_t ldcd, const dfloat *Dinvd,
+                           const TrsvMaps &maps, cudaStream_t s) {
+    if (nr == 1)
+        return launch_trsv<TS, T, 1, DD>(C, ldc, n, Dinv, Y, ldy, nr, mode, skip, sync, yp, Cd, ldcd, Dinvd, maps, s);
+    if (nr <= 2)
+        return launch_trsv<TS, T, 2, DD>(C, ldc, n, Dinv, Y, ldy, nr, mode, skip, sync, yp, Cd, ldcd, Dinvd, maps, s);
+    if (nr <= 4)
+        return launch_trsv<TS, T, 4, DD>(C, ldc, n, Dinv, Y, ldy, nr, mode, skip, sync, yp, Cd, ldcd, Dinvd, maps, s);
+    if (nr <= 8)
+        return launch_trsv<TS, T, 8, DD>(C, ldc, n, Dinv, Y, ldy, nr, mode, skip, sync, yp, Cd, ldcd, Dinvd, maps, s);
+    return launch_trsv<TS, T, 16, DD>(C, ldc, n, Dinv, Y, ldy, nr, mode, skip, sync, yp, Cd, ldcd, Dinvd, maps, s);
 }
 
 template <typename TS, typename T>
@@ -755,47 +931,34 @@ cudaError_t solve_typed(const genp_factors *F, T *Y, int64_t ldy, int64_t nrhs, 
     const TS *C = static_cast<const TS *>(F->C);
     const int64_t n = F->n, ldc = F->ldc;
     if (n > INT32_MAX - TB) return cudaErrorInvalidValue;
+    // factors also held as double-float pairs (sliced path): the walker runs in double-float
+    const dfloat *Wd = static_cast<const dfloat *>(F->W);
+    const dfloat *Dd = static_cast<const dfloat *>(F->dinv_df);
+    const bool dd = sizeof(TS) == 8 && Wd && Dd;
+    TrsvMaps maps;
+    if (dd)
+        maps.ok = make_map_8b(&maps.c, Wd, n, n, F->ldw, kDdLd, TB) &&
+                  make_map_8b(&maps.x, Dd, 4 * cdiv(n, TB) * TB, TB, TB, kDdLd, TB);
+    const TS *D = static_cast<const TS *>(F->dinv);
+    int *sy = F->trsv_sync;
+    T *yp = static_cast<T *>(F->trsv_y);
     for (int64_t c0 = 0; c0 < nrhs; c0 += kTrsvMaxRhs) {
         const int nr = (int)(nrhs - c0 < kTrsvMaxRhs ? nrhs - c0 : kTrsvMaxRhs);
         T *Yc = Y + c0;
         for (int pass = 0; pass < 2; ++pass) {
             // pass 0: L (or U^T) forward; pass 1: U (or L^T) backward
             const int mode = (transposed ? (pass == 0 ? 2 : 3) : (pass == 0 ? 0 : 1)) | (F->block ? 4 : 0);
-            const TS *D = static_cast<const TS *>(F->dinv);
-            int *sy = F->trsv_sync;
-            cudaError_t e = cudaSuccess;
-            // factors also held as double-float pairs (sliced path): the walker runs in double-float
-            const dfloat *Wd = static_cast<const dfloat *>(F->W);
-            const dfloat *Dd = static_cast<const dfloat *>(F->dinv_df);
-            bool dd = false;
-            if constexpr (sizeof(TS) == 8) dd = Wd && Dd;
+            cudaError_t e;
             if constexpr (sizeof(TS) == 8) {
-                const int64_t lw = F->ldw;
-                if (!dd) {
-                } else if (nr == 1) {
-                    e = launch_trsv<TS, T, 1, true>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, Wd, lw, Dd, s);
-                } else if (nr <= 2) {
-                    e = launch_trsv<TS, T, 2, true>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, Wd, lw, Dd, s);
-                } else if (nr <= 4) {
-                    e = launch_trsv<TS, T, 4, true>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, Wd, lw, Dd, s);
-                } else if (nr <= 8) {
-                    e = launch_trsv<TS, T, 8, true>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, Wd, lw, Dd, s);
-                } else {
-                    e = launch_trsv<TS, T, 16, true>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, Wd, lw, Dd, s);
+                if (dd) {
+                    e = launch_trsv_nr<TS, T, true>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, yp, Wd, F->ldw, Dd, maps,
+                                                    s);
+                    if (e != cudaSuccess) return e;
+                    continue;
                 }
             }
-            if (!dd) {
-                if (nr == 1) e = launch_trsv<TS, T, 1, false>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, nullptr, 0,
-                                                               nullptr, s);
-                else if (nr <= 2) e = launch_trsv<TS, T, 2, false>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, nullptr,
-                                                                    0, nullptr, s);
-                else if (nr <= 4) e = launch_trsv<TS, T, 4, false>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, nullptr,
-                                                                    0, nullptr, s);
-                else if (nr <= 8) e = launch_trsv<TS, T, 8, false>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, nullptr,
-                                                                    0, nullptr, s);
-                else e = launch_trsv<TS, T, 16, false>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, nullptr, 0, nullptr,
-                                                        s);
-            }
+            e = launch_trsv_nr<TS, T, false>(C, ldc, n, D, Yc, ldy, nr, mode, skip, sy, yp, nullptr, 0, nullptr, maps,
+                                             s);
             if (e != cudaSuccess) return e;
         }
     }
@@ -821,12 +984,14 @@ unsigned int trsv_skipped_count(bool reset) {
 template <typename T>
 cudaError_t lu_solve_inplace(const genp_factors *F, T *Y, int64_t ldy, int64_t nrhs, bool transposed, const int *skip,
                              cudaStream_t s) {
-    if (sizeof(T) == 8) {
+    // the factors' type is the solve's: FP64 factors with FP64 vectors, FP32 with FP32
+    if constexpr (sizeof(T) == 8) {
         if (!f64_factors(F->prec)) return cudaErrorInvalidValue;
         return solve_typed<T, T>(F, Y, ldy, nrhs, transposed, skip, s);
+    } else {
+        if (f64_factors(F->prec)) return cudaErrorInvalidValue;
+        return solve_typed<float, T>(F, Y, ldy, nrhs, transposed, skip, s);
     }
-    if (f64_factors(F->prec)) return cudaErrorInvalidValue;
-    return solve_typed<float, T>(F, Y, ldy, nrhs, transposed, skip, s);
 }
 template cudaError_t lu_solve_inplace<double>(const genp_factors *, double *, int64_t, int64_t, bool, const int *,
                                               cudaStream_t);
@@ -864,7 +1029,8 @@ int solve_timeout_flag(bool reset) {
     return v;
 }
 
-int64_t trsv_sync_ints(int64_t n) { return 2 + 2 * cdiv(n, TB); }
+int64_t trsv_sync_ints(int64_t n) { return 2 + cdiv(n, TB); }
+int64_t trsv_y_elems(int64_t n) { return cdiv(n, TB) * TB * kTrsvMaxRhs; }
 int64_t diag_inverse_elems(int64_t n) { return 2 * cdiv(n, TB) * TB * TB; }
 
 cudaError_t invert_diag_blocks(genp_factors *F, cudaStream_t s) {
@@ -885,11 +1051,15 @@ cudaError_t invert_diag_blocks(genp_factors *F, cudaStream_t s) {
     else
         k_trtri_diag<float><<<g, TB, sm, s>>>(static_cast<const float *>(F->C), F->ldc, (int)n,
                                               static_cast<float *>(F->dinv));
-    if (F->dinv_df) {   // double-float copy for the walker of the sliced path
+    if (F->dinv_df) {   // double-float copy for the walker of the sliced path, then its diagonal tiles
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        return df_from_f64(static_cast<const double *>(F->dinv), TB, static_cast<dfloat *>(F->dinv_df), TB,
-                           2 * cdiv(n, TB) * TB, TB, s);
+        dfloat *Dd = static_cast<dfloat *>(F->dinv_df);
+        e = df_from_f64(static_cast<const double *>(F->dinv), TB, Dd, TB, 2 * cdiv(n, TB) * TB, TB, s);
+        if (e != cudaSuccess) return e;
+        note_launch();
+        k_diag_tiles_df<<<g, 256, 0, s>>>(static_cast<const dfloat *>(F->W), F->ldw, (int)n, F->block ? 1 : 0,
+                                          Dd + diag_inverse_elems(n));
     }
     return cudaGetLastError();
 }

@@ -390,3 +390,41 @@ def test_sliced_grid_gmres_ir_end_to_end(g, kappa):
     assert oracle.backward_error(A, x, B) <= 1e-14
     assert np.abs(x - Xs).max() / np.abs(Xs).max() <= 1e-14 * kappa * 10
     assert info.refine_iters <= 4
+
+
+def test_profile_classes_report_the_launches(g):
+    """genp_profile_class: with the profile on, a sliced solve records its
+    tensor-core launches (class 0: work = the FP64-class products' 2 m n K,
+    at least A G's 2 n^3 and the Schur updates' 2 (n - 256)^3 / 3 when
+    n > 256), triangular solves (class 1: n^2 / 2 x 8 bytes for each launch
+    that ran, fewer when refinement launches were skipped) and
+    matrix-vector products (class 2); class 6 does not exist."""
+    import ctypes
+    lib = g._lib.load()
+    n = 700
+    A, _, B = (t.numpy() for t in W.svd_kappa(n, 1e4, 1, seed=2))
+    prev = lib.genp_refine_graphs(0)      # launch by launch, so the profile sees the refinement
+    lib.genp_profile_enable(1)
+    try:
+        X, info, G, F = g.solve_system(cu(A), cu(B), kind=g.GAUSSIAN, seed=3, prec=g.BF16_SLICED, refine_steps=4,
+                                       tol=1e-16, method=1)
+        torch.cuda.synchronize()
+        got = {}
+        for cls in range(6):
+            ms, w, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+            assert lib.genp_profile_class(cls, ctypes.byref(ms), ctypes.byref(w), ctypes.byref(c)) == 0
+            got[cls] = (ms.value, w.value, c.value)
+        ms, w, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        assert lib.genp_profile_class(6, ctypes.byref(ms), ctypes.byref(w), ctypes.byref(c)) == -1
+    finally:
+        lib.genp_profile_enable(0)
+        lib.genp_refine_graphs(prev)
+    t_ms, t_work, t_n = got[0]
+    assert t_n > 0 and t_ms > 0
+    assert t_work >= 2.0 * n**3 + 2.0 * (n - 256) ** 3 / 3
+    assert t_work <= 2.0 * 768**3 + 2.0 * 768**3        # padded K at most
+    s_ms, s_work, s_n = got[1]
+    assert s_n >= 2 and s_ms > 0
+    assert 0 < s_work <= s_n * 0.5 * n * n * 8 + 1
+    assert got[2][2] > 0 and got[2][1] > 0
+    assert oracle.backward_error(A, X.cpu().numpy(), B) <= 1e-14

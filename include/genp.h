@@ -135,7 +135,7 @@ typedef enum {
  *        operands' scales; the trailing matrix is held as double-float pairs
  *        (48 bits) between steps.  The diagonal blocks and block rows and
  *        columns are solved nb wide; the tensor-core updates take outer
- *        blocks of max(2 nb, 256) and, inside them, the inner blocks'
+ *        blocks of max(2 nb, 512) and, inside them, the inner blocks'
  *        updates (the inner dimension of every update balanced by powers of
  *        two).  FP64 refinement (GMRES-IR at large growth) takes the solve
  *        to FP64 accuracy. */

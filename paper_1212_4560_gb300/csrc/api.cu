@@ -776,7 +776,8 @@ genp_status new_factors(void *C, int64_t n, int64_t ldc, genp_prec prec, int64_t
         st = dalloc(&F->tcA, (size_t)n * F->tc_ldq);
         if (st == GENP_OK) st = dalloc(&F->tcB, (size_t)n * F->tc_ldq);
         if (st == GENP_OK) st = dalloc(reinterpret_cast<double **>(&F->W), (size_t)n * F->ldw);
-        if (st == GENP_OK) st = dalloc(&F->exps, (size_t)2 * n + 4 * 128);   // + 2 nb inner-dimension keys (8 B)
+        // + the inner-dimension keys (8 B each) of an outer step
+        if (st == GENP_OK) st = dalloc(&F->exps, (size_t)(2 * n + 2 * (2 * nb > kSlicedOuter ? 2 * nb : kSlicedOuter)));
         // the inverses, then the masked diagonal blocks, as double-float pairs
         if (st == GENP_OK) st = dalloc(reinterpret_cast<double **>(&F->dinv_df), (size_t)(2 * diag_inverse_elems(n)));
     }

@@ -596,7 +596,7 @@ bool make_map_u8(CUtensorMap *map, const void *ptr, int64_t rows, int64_t K, int
 //   D[i][j] += alpha 2^{e_i + f_j - 7 ND} (sum_{g<=ND} 2^{7(ND-g)} P_g + 2^-7 P_{ND+1})
 // Every wait is bounded (then the CTA aborts, drains its copies, frees TMEM).
 // ---------------------------------------------------------------------------
-constexpr int SBN = 64, A_SLOTS = 4;
+constexpr int SBN = 64, A_SLOTS_MAX = 8;
 constexpr uint32_t SA_BYTES = BM * BK * 2;      // one A digit slice of a k-tile
 constexpr uint32_t SBD_BYTES = SBN * BK * 2;    // one B digit slice of a k-tile
 constexpr uint32_t S_TMEM = 512;
@@ -604,8 +604,8 @@ constexpr int kSlicedThreads = 192;             // 4 epilogue warps, producer, M
 constexpr int kHalfLd = 33;                     // epilogue staging: 128 rows x 32 dfloat, padded
 constexpr uint32_t STAGE_BYTES = BM * kHalfLd * 8;
 struct SCtl {
-    unsigned long long afull[A_SLOTS];
-    unsigned long long aempty[A_SLOTS];
+    unsigned long long afull[A_SLOTS_MAX];
+    unsigned long long aempty[A_SLOTS_MAX];
     unsigned long long bfull[2];
     unsigned long long bempty[2];
     unsigned long long tfull;     // a tile's accumulators are complete
@@ -659,7 +659,16 @@ struct SlicedCfg {
         return p;
     }();
     static constexpr uint32_t kBStage = NDB * SBD_BYTES;
-    static constexpr size_t kNeed = 1024 + A_SLOTS * SA_BYTES + 2 * kBStage + STAGE_BYTES + sizeof(SCtl);
+    // as deep a ring of A digit slices as the shared memory left by B's two
+    // stages and the epilogue's staging allows (the loads take longer than
+    // the MMAs of the few slices a four-slot ring keeps in flight)
+    static constexpr size_t kFixed = 1024 + 2 * kBStage + STAGE_BYTES + sizeof(SCtl);
+    static constexpr int kASlots = [] {
+        const size_t fit = (227 * 1024 - kFixed) / SA_BYTES;
+        return fit < (size_t)A_SLOTS_MAX ? (int)fit : A_SLOTS_MAX;
+    }();
+    static_assert(kASlots >= 4, "A ring");
+    static constexpr size_t kNeed = kFixed + kASlots * SA_BYTES;
     // alone on its SM: a second CTA would wait in tcgen05.alloc for the 512
     // columns, so the request is padded past half of the SM's shared memory
     static constexpr size_t kSmem = kNeed > 116 * 1024 ? kNeed : 116 * 1024;
@@ -677,6 +686,7 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     extern __shared__ unsigned char smraw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     unsigned char *sA = base;
+    constexpr int A_SLOTS = Cfg::kASlots;
     unsigned char *sB = base + A_SLOTS * SA_BYTES;
     dfloat *stage = reinterpret_cast<dfloat *>(sB + 2 * Cfg::kBStage);   // BM x kHalfLd
     SCtl *ctl = (SCtl *)(sB + 2 * Cfg::kBStage + STAGE_BYTES);

@@ -333,7 +333,7 @@ cudaError_t df_to_f64_T(const dfloat *src, int64_t lds, double *dst, int64_t ldd
 cudaError_t sliced_matmul(int nd, int64_t m, int64_t n, int64_t K, const double *A, int64_t lda, const double *B,
                           int64_t ldb, dfloat *D, int64_t ldd, __nv_bfloat16 *Aq, __nv_bfloat16 *Bq, int *exps,
                           cudaStream_t s, int ndb = 0);
-constexpr int kSlicedOuter = 256;       // outer step (Schur update K) of the sliced factorization
+constexpr int kSlicedOuter = 512;       // outer step (Schur update K) of the sliced factorization
 constexpr int64_t kSlicedChunk = 512;   // keeps the digit groups of weight >= 2^-49 exact in FP32
 // With a two-digit M side (a multiplier on the sliced grid) a group holds at
 // most two pairs of |d_t d_u| <= 2^13 (one pair of 2^14 for group 0), so

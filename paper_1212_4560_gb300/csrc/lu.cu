@@ -412,7 +412,9 @@ cudaError_t factor_sliced(genp_factors *F, cudaStream_t s) {
     double *C = static_cast<double *>(F->C);
     dfloat *W = static_cast<dfloat *>(F->W);
     const int64_t n = F->n, ldc = F->ldc, ldw = F->ldw, ldq = F->tc_ldq;
-    // outer steps of 256 (the tensor-core Schur updates' K), inner steps of nb
+    // outer steps of 512 (the tensor-core Schur updates' K: the largest at
+    // which the digit-pair groups stay exact in FP32, so the fewest TMEM
+    // read-outs per MMA), inner steps of nb
     const int nb = (int)F->nb, nbo = 2 * nb > kSlicedOuter ? 2 * nb : kSlicedOuter;
     note_launch();
     k_maxabs<double><<<152 * 4, 256, 0, s>>>(C, n, ldc, &F->st->max_abs_c);

@@ -205,7 +205,7 @@ def test_factor_sliced_backward_error(g, digits, n, nb):
     assert info.breakdown_step == -1
     assert g._lib.load().genp_device_check(1) == 0
     L, U = oracle.split_lu(C.cpu().numpy())
-    nbo = max(256, 2 * (nb or 128))   # the library's outer step
+    nbo = max(512, 2 * (nb or 128))   # the library's outer step
     S = sliced_update_scale(L, U, nbo, nb or 128)
     u_df = 2.0 ** -46
     df = 3 * n * u_df * (np.abs(L) @ np.abs(U)) + (n / (nb or 128) + 2) * u_df * np.abs(C0)

@@ -267,6 +267,19 @@ __device__ __forceinline__ bool load_y(const float *p, float &v) {
     v = __uint_as_float(b);
     return b != 0xffffffffu;
 }
+// double-float values go out as one 8-byte word (hi, lo)
+__device__ __forceinline__ void publish_y(dfloat *p, dfloat v) {
+    unsigned long long b = ((unsigned long long)__float_as_uint(v.lo) << 32) | __float_as_uint(v.hi);
+    if (b == ~0ull) b = 0x7fc00000ull;
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(b) : "memory");
+}
+__device__ __forceinline__ bool load_y(const dfloat *p, dfloat &v) {
+    unsigned long long b;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(b) : "l"(p) : "memory");
+    v.hi = __uint_as_float((unsigned)b);
+    v.lo = __uint_as_float((unsigned)(b >> 32));
+    return b != ~0ull;
+}
 // a published value, waiting (bounded) for it to land
 template <typename T>
 __device__ T wait_y(const T *p) {
@@ -295,14 +308,52 @@ __device__ __forceinline__ int nchunks(int q) { return q < 2 ? 0 : (q - 1 + kSeg
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ float ldcg(const float *p) { return __ldcg(p); }
 
+// Row stride of the shared right-hand-side blocks [64][NR]: a warp's tile
+// products read four rows k at once, which share a bank when NR is a
+// multiple of 8; one pad element keeps them apart.
+template <int NR>
+constexpr int kNrp = NR % 8 == 0 ? NR + 1 : NR;
+// Unrolling of the tile products' k loops: whole for a few right-hand
+// sides; for 8 or more the 16 x NR fully unrolled bodies at every call site
+// no longer fit the instruction cache and ran four times slower.
+template <int NR>
+constexpr int kUnrollK = NR >= 8 ? 2 : 16;
+// The double-float path's update items sum in double-float from 8
+// right-hand sides on, in FP64 below.
+template <int NR>
+constexpr bool kDdItems = NR >= 8;
+
+// The published block j of y (bj rows, nr of NR columns) into the shared
+// [64][kNrp] block V, zero elsewhere: every thread's loads go out together,
+// and only values not there yet are waited for.
+template <int NR, typename T>
+__device__ __forceinline__ void gather_y(T (*V)[kNrp<NR>], const T *yp, int j, int bj, int nr, int tid) {
+    constexpr int kYv = (TB * NR + kTrsvThreads - 1) / kTrsvThreads;
+    T v[kYv];
+    bool got[kYv];
+#pragma unroll
+    for (int e = 0; e < kYv; ++e) {
+        const int idx = tid + e * kTrsvThreads, rr = idx / NR, c = idx % NR;
+        v[e] = T(0.0f);
+        got[e] = true;
+        if (idx < TB * NR && rr < bj && c < nr) got[e] = load_y(yp + ((int64_t)j * TB + rr) * NR + c, v[e]);
+    }
+#pragma unroll
+    for (int e = 0; e < kYv; ++e) {
+        const int idx = tid + e * kTrsvThreads, rr = idx / NR, c = idx % NR;
+        if (!got[e]) v[e] = wait_y(yp + ((int64_t)j * TB + rr) * NR + c);
+        if (idx < TB * NR) V[rr][c] = v[e];
+    }
+}
+
 template <typename T, int NR>
 struct TrsvSmem {
     T S[TB][TB + 1];    // op(T_jj)^{-1} (walker) or the current tile (items)
     T D[TB][TB + 1];    // op(T_jj), its triangle only (walker)
     T O[TB][TB + 1];    // op(T)[next][j] (walker)
-    T y[TB][NR];        // y_j
-    T acc[TB][NR];      // right-hand side of the diagonal block, then its residual
-    T carry[TB][NR];    // the walker's own contribution to the next block
+    T y[TB][kNrp<NR>];        // y_j
+    T acc[TB][kNrp<NR>];      // right-hand side of the diagonal block, then its residual
+    T carry[TB][kNrp<NR>];    // the walker's own contribution to the next block
 };
 
 // The walker's shared memory when it runs in double-float (factors held as
@@ -320,7 +371,7 @@ struct TrsvSmemDD {
     alignas(128) dfloat X[2][TB][kDdLd];   // T_jj^{-1}
     alignas(128) dfloat D[TB][kDdLd];      // T_jj, its triangle with op(T)'s diagonal
     alignas(128) dfloat O[TB][kDdLd];      // the tile of op(T)[next][j], as it lies in C
-    dfloat y[TB][NR], acc[TB][NR], carry[TB][NR];
+    dfloat y[TB][kNrp<NR>], acc[TB][kNrp<NR>], carry[TB][kNrp<NR>];
     unsigned long long bar[4];             // tile arrivals: X[0], X[1], D, O
 };
 
@@ -382,12 +433,12 @@ __device__ __forceinline__ void dd_mac(float &s, float &t, float ah, float al, d
 // threads of row r (thread = 4 r + quarter), for a tile held as pairs:
 // M(r, k) = M[r][k], or M[k][r] when TR.
 template <int NR, bool TR>
-__device__ __forceinline__ void tile_gemv_dd(const dfloat (*M)[kDdLd], const dfloat (*V)[NR], int r, int qq,
+__device__ __forceinline__ void tile_gemv_dd(const dfloat (*M)[kDdLd], const dfloat (*V)[kNrp<NR>], int r, int qq,
                                              dfloat (&part)[NR]) {
     float s[NR], t[NR];
 #pragma unroll
     for (int c = 0; c < NR; ++c) s[c] = t[c] = 0.f;
-#pragma unroll
+#pragma unroll kUnrollK<NR>
     for (int kk = 0; kk < 16; ++kk) {
         const int k = qq + 4 * kk;
         const dfloat a = TR ? M[k][r] : M[r][k];
@@ -409,8 +460,9 @@ __device__ __forceinline__ void tile_gemv_dd(const dfloat (*M)[kDdLd], const dfl
 
 // part[c] += sum over this thread's quarter of k of M[r][k] V[k][c] (thread = 4 r + quarter)
 template <typename T, int NR>
-__device__ __forceinline__ void tile_gemv_acc(const T (*M)[TB + 1], const T (*V)[NR], int r, int qq, T (&part)[NR]) {
-#pragma unroll
+__device__ __forceinline__ void tile_gemv_acc(const T (*M)[TB + 1], const T (*V)[kNrp<NR>], int r, int qq,
+                                              T (&part)[NR]) {
+#pragma unroll kUnrollK<NR>
     for (int kk = 0; kk < 16; ++kk) {
         const int k = qq * 16 + kk;
         const T a = M[r][k];
@@ -431,10 +483,10 @@ __device__ __forceinline__ void quad_sum(T (&part)[NR]) {
 // part[c] = sum over this thread's quarter of k of M[r][k] V[k][c], summed over
 // the 4 threads of row r (thread = 4 r + quarter)
 template <typename T, int NR>
-__device__ __forceinline__ void tile_gemv(const T (*M)[TB + 1], const T (*V)[NR], int r, int qq, T (&part)[NR]) {
+__device__ __forceinline__ void tile_gemv(const T (*M)[TB + 1], const T (*V)[kNrp<NR>], int r, int qq, T (&part)[NR]) {
 #pragma unroll
     for (int c = 0; c < NR; ++c) part[c] = T(0);
-#pragma unroll
+#pragma unroll kUnrollK<NR>
     for (int kk = 0; kk < 16; ++kk) {
         const int k = qq * 16 + kk;
         const T a = M[r][k];
@@ -676,7 +728,10 @@ __global__ void __launch_bounds__(kTrsvThreads, 1) k_trsv(const TS *C, int64_t l
                         sd.y[r][c] = yv;
                         if (r < bj && c < nr) {
                             Y[((int64_t)j * TB + r) * ldy + c] = (T)(double)yv;
-                            publish_y(ypub + ((int64_t)j * TB + r) * NR + c, (T)(double)yv);
+                            if constexpr (kDdItems<NR>)
+                                publish_y(reinterpret_cast<dfloat *>(ypub) + ((int64_t)j * TB + r) * NR + c, yv);
+                            else
+                                publish_y(ypub + ((int64_t)j * TB + r) * NR + c, (T)(double)yv);
                         }
                     }
                 __syncthreads();
@@ -772,6 +827,71 @@ __global__ void __launch_bounds__(kTrsvThreads, 1) k_trsv(const TS *C, int64_t l
         if (q_it >= nblk) break;
         const int i = block_of(q_it);
         const int p0 = (t - t_base) * kSeg, p1 = min(q_it - 2, p0 + kSeg - 1);
+        if constexpr (DD && kDdItems<NR>) {
+            // in double-float too, from the pair factors and the published
+            // pairs: FP64 runs at 1/64 of the FP32 rate here, which 8 or more
+            // right-hand sides feel (for fewer, the items' FP64 sums keep the
+            // solve, as a preconditioner, a little more accurate: 8-9 Krylov
+            // steps on the n = 16384 system against 12-13 in double-float)
+            const dfloat *yp = reinterpret_cast<const dfloat *>(ypub);
+            dfloat(*M)[kDdLd] = sd.X[0];
+            auto load_pairs = [&](int bj, dfloat (&v)[16]) {   // tile (i, bj) of op(T), element (rr, kk)
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int idx = tid + e * kTrsvThreads;
+                    const int a = idx >> 6, b = idx & 63;
+                    const int rr = mode <= 1 ? a : b, kk = mode <= 1 ? b : a;
+                    const int64_t row = (int64_t)i * TB + rr, col = (int64_t)bj * TB + kk;
+                    dfloat z(0.0f);
+                    if (row < n && col < n) z = (mode <= 1) ? Cd[row * ldcd + col] : Cd[col * ldcd + row];
+                    v[e] = z;
+                }
+            };
+            dfloat v[16];
+            load_pairs(block_of(p0), v);
+            float s_[NR], t_[NR];
+#pragma unroll
+            for (int c = 0; c < NR; ++c) s_[c] = t_[c] = 0.f;
+            for (int pp = p0; pp <= p1; ++pp) {
+                const int j = block_of(pp);
+                const int bj = min(TB, n - j * TB);
+                __syncthreads();
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int idx = tid + e * kTrsvThreads;
+                    const int a = idx >> 6, b = idx & 63;
+                    M[mode <= 1 ? a : b][mode <= 1 ? b : a] = v[e];
+                }
+                gather_y<NR>(sd.y, yp, j, bj, nr, tid);
+                __syncthreads();
+                if (pp < p1) load_pairs(block_of(pp + 1), v);
+#pragma unroll kUnrollK<NR>
+                for (int kk = 0; kk < 16; ++kk) {
+                    const int k = qq + 4 * kk;
+                    const dfloat a = M[r][k];
+#pragma unroll
+                    for (int c = 0; c < NR; ++c) dd_mac(s_[c], t_[c], a.hi, a.lo, sd.y[k][c]);
+                }
+            }
+            const int64_t row = (int64_t)i * TB + r;
+#pragma unroll
+            for (int c = 0; c < NR; ++c) {
+                dfloat a = df_norm(s_[c], t_[c]);
+                for (int o = 1; o <= 2; o <<= 1) {
+                    dfloat b;
+                    b.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+                    b.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+                    a = a + b;
+                }
+                if ((c & 3) == qq && c < nr && row < n) atomicAdd(Y + row * ldy + c, -(T)(double)a);
+            }
+            __syncthreads();
+            if (tid == 0) {       // release: the CTA's updates above, ordered by the barrier
+                __threadfence();
+                atomicAdd(cnt + i, p1 - p0 + 1);
+            }
+            continue;
+        }
         T v[16];
         load_tile(i, block_of(p0), v);
         T part[NR];
@@ -782,10 +902,7 @@ __global__ void __launch_bounds__(kTrsvThreads, 1) k_trsv(const TS *C, int64_t l
             const int bj = min(TB, n - j * TB);
             __syncthreads();
             store_tile(sm.S, v);
-            for (int idx = tid; idx < TB * NR; idx += kTrsvThreads) {
-                const int rr = idx / NR, c = idx % NR;
-                sm.y[rr][c] = (rr < bj && c < nr) ? wait_y(ypub + ((int64_t)j * TB + rr) * NR + c) : T(0);
-            }
+            gather_y<NR>(sm.y, ypub, j, bj, nr, tid);
             __syncthreads();
             if (pp < p1) load_tile(i, block_of(pp + 1), v);
             tile_gemv_acc<T, NR>(sm.S, sm.y, r, qq, part);
@@ -805,9 +922,6 @@ __global__ void __launch_bounds__(kTrsvThreads, 1) k_trsv(const TS *C, int64_t l
     }
 }
 
-// Inverses of the 64 x 64 diagonal blocks of L (unit lower, blockIdx.y = 0)
-// and U (upper, blockIdx.y = 1), by column-wise substitution in FP64, stored
-// row-major per block; rows and columns past a ragged last block are zero.
 // The double-float walker's diagonal tiles as the solves use them, after
 // the inverses in its store: [L, U][block][64][64] row-major pairs, L_jj with
 // its unit diagonal and U_jj's upper triangle (for block GE the identity and
@@ -828,6 +942,9 @@ __global__ void k_diag_tiles_df(const dfloat *W, int64_t ldw, int n, int bge, df
     }
 }
 
+// Inverses of the 64 x 64 diagonal blocks of L (unit lower, blockIdx.y = 0)
+// and U (upper, blockIdx.y = 1), by column-wise substitution in FP64, stored
+// row-major per block; rows and columns past a ragged last block are zero.
 template <typename TS>
 __global__ void __launch_bounds__(TB) k_trtri_diag(const TS *C, int64_t ldc, int n, TS *Dinv) {
     extern __shared__ __align__(16) unsigned char smraw[];

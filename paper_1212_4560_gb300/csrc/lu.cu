@@ -192,51 +192,54 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_panel_reg(TS *C, int64_t l
 // blockIdx.y == 1: L21 = C21 U11^{-1} on rows    [c0, c0 + 64)
 // 64 vectors (columns of C12, rows of C21) per CTA of 1024 threads, 16
 // threads per vector in one half-warp: thread g holds entries g + 16 m
-// (m < 8) in registers, and the entry of step k reaches the vector's other
-// threads by a shuffle, so the substitutions need no block barrier; 32 warps
-// per SM hide the latency of the dependent double-float operations.  The
-// kb x kb (kb <= 128) diagonal block sits in shared memory.
-constexpr int kTrsmThreads = 1024, kTpv = 16, kEpt = 128 / kTpv;
+// (m < 8, entry m in the m-th 16-block of the vector) in registers.  The
+// substitution runs by 16-blocks: at step k = 16 b + kk the solved entry k
+// reaches the vector's other threads by a shuffle, which update their entry
+// of block b (below k) and every entry of the blocks after it; the blocks
+// are unrolled, so a step costs the updates still to do and nothing for the
+// blocks already solved (no per-entry conditions), and the step loop stays
+// rolled (small code).  The kb x kb (kb <= 128) diagonal block sits in
+// shared memory, padded to 128 x 128 with the identity, so a ragged last
+// block needs no bounds checks.  32 warps per SM hide the latency of the
+// dependent double-float operations.
+constexpr int kTrsmThreads = 1024, kTpv = 16, kEpt = 128 / kTpv, kTrsmLd = 129;
 template <typename TS, typename TC>
 __global__ void __launch_bounds__(kTrsmThreads, 1) k_trsm_reg(TS *C, int64_t ldc, int64_t n, int64_t k0, int kb,
                                                               DevStatus *st) {
     extern __shared__ __align__(16) unsigned char smraw[];
     TC *T = reinterpret_cast<TC *>(smraw);
-    const int ld = kb + 1;
+    constexpr int ld = kTrsmLd;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int v = tid / kTpv, g = tid % kTpv;
     const int64_t c0 = k0 + kb + (int64_t)blockIdx.x * kTrsmW;
     const int w = (int)min((int64_t)kTrsmW, n - c0);
     if (w <= 0) return;
     const bool role_u = blockIdx.y == 0;
-    for (int r = warp; r < kb; r += kTrsmThreads / 32)
-        for (int c = lane; c < kb; c += 32) T[r * ld + c] = ld_as<TC>(C[(k0 + r) * ldc + k0 + c]);
+    for (int r = warp; r < 128; r += kTrsmThreads / 32)
+        for (int c = lane; c < 128; c += 32)
+            T[r * ld + c] = (r < kb && c < kb) ? ld_as<TC>(C[(k0 + r) * ldc + k0 + c]) : TC(r == c ? 1.0 : 0.0);
     __syncthreads();
     const bool valid = v < w;
     const int base = lane & ~(kTpv - 1);
     const int nq = (kb + kTpv - 1) / kTpv;
     TC x[kEpt];
     if (role_u) {
+        // L11 x = c, L11 unit lower: x_r -= l_rk x_k for r > k
 #pragma unroll
         for (int m = 0; m < kEpt; ++m) {
             const int r = g + kTpv * m;
             x[m] = (valid && r < kb) ? ld_as<TC>(C[(k0 + r) * ldc + c0 + v]) : TC(0.0);
         }
-        for (int kq = 0; kq < nq; ++kq) {
-            TC own = TC(0.0);
 #pragma unroll
-            for (int m = 0; m < kEpt; ++m)
-                if (m == kq) own = x[m];
+        for (int b = 0; b < kEpt; ++b) {
+            if (b >= nq) break;
+#pragma unroll 1
             for (int kk = 0; kk < kTpv; ++kk) {
-                const int k = kTpv * kq + kk;
-                if (k >= kb) break;
-                const TC xk = shfl_idx(own, base | kk);       // row k of the vector, final
+                const int k = kTpv * b + kk;
+                const TC xk = shfl_idx(x[b], base | kk);       // entry k, final
+                if (g > kk) x[b] = fms(x[b], T[(g + kTpv * b) * ld + k], xk);
 #pragma unroll
-                for (int m = 0; m < kEpt; ++m) {
-                    const int r = g + kTpv * m;
-                    if (kTpv * m + kTpv - 1 > k && r > k && r < kb) x[m] = fms(x[m], T[r * ld + k], xk);
-                }
-                if (g > kk && g + kTpv * kq < kb) own = fms(own, T[(g + kTpv * kq) * ld + k], xk);
+                for (int m = b + 1; m < kEpt; ++m) x[m] = fms(x[m], T[(g + kTpv * m) * ld + k], xk);
             }
         }
         using MT = decltype(mag(TC()));
@@ -256,31 +259,24 @@ __global__ void __launch_bounds__(kTrsmThreads, 1) k_trsm_reg(TS *C, int64_t ldc
         }
         if (lane == 0) atomic_max_nonneg(&st->max_abs_u, (double)xmax);
     } else {
+        // x U11 = c, U11 upper: x_j = (c_j - sum_{i<j} x_i u_ij) / u_jj
 #pragma unroll
         for (int m = 0; m < kEpt; ++m) {
             const int c = g + kTpv * m;
             x[m] = (valid && c < kb) ? ld_as<TC>(C[(c0 + v) * ldc + k0 + c]) : TC(0.0);
         }
-        for (int kq = 0; kq < nq; ++kq) {
-            TC own = TC(0.0);
 #pragma unroll
-            for (int m = 0; m < kEpt; ++m)
-                if (m == kq) own = x[m];
+        for (int b = 0; b < kEpt; ++b) {
+            if (b >= nq) break;
+#pragma unroll 1
             for (int kk = 0; kk < kTpv; ++kk) {
-                const int j = kTpv * kq + kk;
-                if (j >= kb) break;
-                if (g == kk) own = own / T[j * ld + j];          // l_vj = x_vj / u_jj
-                const TC xj = shfl_idx(own, base | kk);
+                const int j = kTpv * b + kk;
+                if (g == kk) x[b] = x[b] / T[j * ld + j];           // l_vj = x_vj / u_jj
+                const TC xj = shfl_idx(x[b], base | kk);
+                if (g > kk) x[b] = fms(x[b], xj, T[j * ld + g + kTpv * b]);
 #pragma unroll
-                for (int m = 0; m < kEpt; ++m) {
-                    const int c = g + kTpv * m;
-                    if (kTpv * m + kTpv - 1 > j && c > j && c < kb) x[m] = fms(x[m], xj, T[j * ld + c]);
-                }
-                if (g > kk && g + kTpv * kq < kb) own = fms(own, xj, T[j * ld + g + kTpv * kq]);
+                for (int m = b + 1; m < kEpt; ++m) x[m] = fms(x[m], xj, T[j * ld + g + kTpv * m]);
             }
-#pragma unroll
-            for (int m = 0; m < kEpt; ++m)
-                if (m == kq) x[m] = own;
         }
 #pragma unroll
         for (int m = 0; m < kEpt; ++m) {
@@ -295,7 +291,7 @@ __global__ void __launch_bounds__(kTrsmThreads, 1) k_trsm_reg(TS *C, int64_t ldc
 template <typename TS, typename TC>
 cudaError_t panel_and_trsm(TS *C, int64_t ldc, int64_t n, int64_t i0, int kb, DevStatus *st, cudaStream_t s) {
     static bool attr_done = false;
-    const size_t sm = (size_t)128 * 129 * sizeof(TC);
+    const size_t sm = (size_t)128 * kTrsmLd * sizeof(TC);
     if (!attr_done) {
         cudaError_t e =
             cudaFuncSetAttribute(k_trsm_reg<TS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -314,7 +310,7 @@ cudaError_t panel_and_trsm(TS *C, int64_t ldc, int64_t n, int64_t i0, int kb, De
     ev = profile_class_slot(kProfFactorAux, 2.0 * (double)kb * kb * (double)rem);
     prof_begin(ev, s);
     note_launch();
-    k_trsm_reg<TS, TC><<<g, kTrsmThreads, (size_t)kb * (kb + 1) * sizeof(TC), s>>>(C, ldc, n, i0, kb, st);
+    k_trsm_reg<TS, TC><<<g, kTrsmThreads, sm, s>>>(C, ldc, n, i0, kb, st);
     prof_end(ev, s);
     return cudaGetLastError();
 }
@@ -356,7 +352,7 @@ cudaError_t factor_tc(genp_factors *F, cudaStream_t s) {
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(k_trsm_reg<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             128 * 129 * (int)sizeof(float));
+                                             128 * kTrsmLd * (int)sizeof(float));
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
@@ -370,7 +366,7 @@ cudaError_t factor_tc(genp_factors *F, cudaStream_t s) {
         if (rem <= 0) break;
         dim3 g((unsigned)cdiv(rem, kTrsmW), 2);
         note_launch();
-        k_trsm_reg<float, float><<<g, kTrsmThreads, (size_t)kb * (kb + 1) * sizeof(float), s>>>(C, ldc, n, k0, kb,
+        k_trsm_reg<float, float><<<g, kTrsmThreads, (size_t)128 * kTrsmLd * sizeof(float), s>>>(C, ldc, n, k0, kb,
                                                                                                F->st);
         float *L21 = C + (k0 + kb) * ldc + k0;
         float *U12 = C + k0 * ldc + k0 + kb;

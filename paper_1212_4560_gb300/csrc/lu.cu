@@ -75,7 +75,6 @@ template <> __device__ __forceinline__ dfloat ld_as<dfloat>(dfloat v) { return v
 template <typename TS> __device__ __forceinline__ TS st_as(double v) { return TS(v); }
 template <typename TS> __device__ __forceinline__ TS st_as(dfloat v);
 template <> __device__ __forceinline__ dfloat st_as<dfloat>(dfloat v) { return v; }
-template <> __device__ __forceinline__ double st_as<double>(dfloat v) { return (double)v; }
 template <> __device__ __forceinline__ float st_as<float>(dfloat v) { return v.hi + v.lo; }
 // magnitude for the growth statistics, without FP64 work for double-float
 __device__ __forceinline__ double mag(double v) { return fabs(v); }
@@ -92,100 +91,234 @@ __device__ __forceinline__ void pivot_stats(DevStatus *st, int64_t step, double 
     }
 }
 
-// Unblocked GENP of the kb x kb (kb <= 128) diagonal block at (k0, k0).
-// 1024 threads: warp w holds rows w + 32 i and lane l columns l + 32 j
-// (i, j < 4) of the block in registers.  Step k: the warp of row k publishes
-// it (its pivot's owner also the pivot's reciprocal in double-float), the
-// lane of column k in every warp turns its entries below the pivot into
-// multipliers and publishes them, then every thread updates its trailing
-// entries; two block barriers per step, buffers alternating by the parity of
-// k.  Row conditions are warp-uniform, so finished rows cost nothing.
-constexpr int kPanelThreads = 1024;
+// GENP of the kb x kb (kb <= 128) diagonal block at (k0, k0), by 32-column
+// strips in shared memory (the block rounded up to whole strips, padded with
+// the identity).  Per strip: (1) its 32 pivot steps with one block barrier
+// each: the 8 threads of the pivot row publish the row's strip entries (its
+// pivot's owner also the reciprocal in double-float), then every row below
+// takes its multiplier from the thread that holds it (a shuffle inside the
+// row's 8 threads, which keep 4 strip entries each in registers) and updates
+// its strip entries; (2) the block row right of the strip, U12 = L11^{-1}
+// A12, 8 threads per column with the substitution carried by shuffles; (3)
+// the trailing block -= L21 U12 (K = 32), a register-tiled product over all
+// threads.  The pivot steps touch only the strip; most of the arithmetic is
+// in (3), without per-step barriers.  FP64 divides by the pivot, as in the
+// unblocked recurrence; double-float multiplies by its reciprocal.
+constexpr int kPanelThreads = 1024, kPanelLd = 129;
+
+// 1 / p in double-float by two Newton steps from the hardware's
+// approximate single-precision reciprocal (r <- r + r (1 - p r), each step
+// doubling the correct bits: ~22 -> 44 -> beyond the pair's 48), without
+// the IEEE division's slow path.  FP32 keeps the pivot and divides by it
+// (prcp below), as the unblocked recurrence does.
+__device__ __forceinline__ dfloat panel_rcp(dfloat p) {
+    float r0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(p.hi));
+    dfloat r(r0);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const dfloat e = dfloat(1.0f) - p * r;
+        r = r + r * e;
+    }
+    return r;
+}
+__device__ __forceinline__ float panel_rcp(float p) { return p; }
+__device__ __forceinline__ dfloat panel_mult(dfloat x, dfloat rcp) { return x * rcp; }
+__device__ __forceinline__ float panel_mult(float x, float p) { return x / p; }
+
+// acc -= L21 U12 over the strip's 32 columns for the R x R outputs (rows
+// e0 + ti + 32 a, columns e0 + tj + 32 b) of thread (ti, tj)
+template <int R, typename TC>
+__device__ __forceinline__ void panel_trailing(TC (*M)[kPanelLd], int s0, int e0, int ti, int tj) {
+    TC acc[R][R];
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+        for (int b = 0; b < R; ++b) acc[a][b] = M[e0 + ti + 32 * a][e0 + tj + 32 * b];
+#pragma unroll 4
+    for (int k = 0; k < 32; ++k) {
+        TC lv[R], uv[R];
+#pragma unroll
+        for (int a = 0; a < R; ++a) lv[a] = M[e0 + ti + 32 * a][s0 + k];
+#pragma unroll
+        for (int b = 0; b < R; ++b) uv[b] = M[s0 + k][e0 + tj + 32 * b];
+#pragma unroll
+        for (int a = 0; a < R; ++a)
+#pragma unroll
+            for (int b = 0; b < R; ++b) acc[a][b] = fms(acc[a][b], lv[a], uv[b]);
+    }
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+        for (int b = 0; b < R; ++b) M[e0 + ti + 32 * a][e0 + tj + 32 * b] = acc[a][b];
+}
+
+// dynamic shared memory: the block, and for the FP32-pipe types the strip's
+// multipliers (128 x 33)
+template <typename TC>
+constexpr size_t panel_smem() {
+    return (size_t)128 * kPanelLd * sizeof(TC) + (std::is_same<TC, double>::value ? 0 : (size_t)128 * 33 * sizeof(TC));
+}
+
 template <typename TS, typename TC>
 __global__ void __launch_bounds__(kPanelThreads, 1) k_panel_reg(TS *C, int64_t ldc, int64_t k0, int kb,
                                                                 DevStatus *st) {
-    __shared__ TC urow[2][128], lcol[2][128], prcp[2];
-    const int tid = threadIdx.x, ty = tid >> 5, tx = tid & 31;
-    TC a[4][4];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    TC(*M)[kPanelLd] = reinterpret_cast<TC(*)[kPanelLd]>(smraw);
+    __shared__ TC prow[2][32], prcp[2], piv[128];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int kbp = (kb + 31) & ~31;
+    for (int idx = tid; idx < kbp * kbp; idx += kPanelThreads) {
+        const int r = idx / kbp, c = idx % kbp;
+        M[r][c] = (r < kb && c < kb) ? ld_as<TC>(C[(k0 + r) * ldc + k0 + c]) : TC(r == c ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    const int rho = tid >> 3, cq = tid & 7;       // strip role: row rho, strip columns cq + 8 j
+    for (int s0 = 0; s0 < kbp; s0 += 32) {
+        // ---- (1) the strip's pivot steps ----
+        if constexpr (std::is_same<TC, double>::value) {
+            const bool srow = rho >= s0 && rho < kbp;  // uniform per warp (4 rows per warp)
+            TC sv[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) sv[j] = srow ? M[rho][s0 + cq + 8 * j] : TC(0.0);
+#pragma unroll 1
+            for (int k = 0; k < 32; ++k) {
+                const int pk = s0 + k, buf = k & 1;
+                if (rho == pk) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int r = ty + 32 * i, c = tx + 32 * j;
-            a[i][j] = (r < kb && c < kb) ? ld_as<TC>(C[(k0 + r) * ldc + k0 + c]) : TC(0.0);
-        }
-    for (int k = 0; k < kb; ++k) {
-        const int buf = k & 1, kr = k & 31, kq = k >> 5;
-        if (ty == kr) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (i == kq) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) urow[buf][tx + 32 * j] = a[i][j];
-                    if (tx == kr) {
+                    for (int j = 0; j < 4; ++j) prow[buf][cq + 8 * j] = sv[j];
+                    if (cq == (k & 7)) {
                         TC p = TC(0.0);
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
-                            if (j == kq) p = a[i][j];
+                            if (j == (k >> 3)) p = sv[j];
                         if constexpr (std::is_same<TC, dfloat>::value) prcp[buf] = TC(1.0) / p;
-                        pivot_stats(st, k0 + k, (double)p);
+                        else prcp[buf] = p;
+                        if (pk < kb) pivot_stats(st, k0 + pk, (double)p);
                     }
                 }
-        }
-        __syncthreads();
-        if (tx == kr) {
-            // double-float: the published reciprocal; FP64: the division, as in
-            // the unblocked recurrence
-            const TC p = urow[buf][k];
-            const TC rp = prcp[buf];
+                __syncthreads();
+                TC l = TC(0.0);
+                if (srow && rho > pk && cq == (k & 7)) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (j == kq) {
+                    for (int j = 0; j < 4; ++j)
+                        if (j == (k >> 3)) {
+                            if constexpr (std::is_same<TC, dfloat>::value) sv[j] = sv[j] * prcp[buf];
+                            else sv[j] = sv[j] / prcp[buf];
+                            l = sv[j];
+                        }
+                }
+                l = shfl_idx(l, (lane & ~7) | (k & 7));
+                if (srow && rho > pk) {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int r = ty + 32 * i;
-                        if (r > k && r < kb) {
-                            if constexpr (std::is_same<TC, dfloat>::value) a[i][j] = a[i][j] * rp;
-                            else a[i][j] = a[i][j] / p;
-                            lcol[buf][r] = a[i][j];
+                    for (int j = 0; j < 4; ++j)
+                        if (cq + 8 * j > k) sv[j] = fms(sv[j], l, prow[buf][cq + 8 * j]);
+                }
+            }
+            if (srow)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) M[rho][s0 + cq + 8 * j] = sv[j];
+            __syncthreads();
+        } else {
+            // the strip in shared memory; thread (row rt, column group cg) of
+            // 8 groups of 4 columns: a warp holds 32 rows of one group, so
+            // whether a group still has columns to update is uniform per
+            // warp.  Each thread forms its row's multiplier itself (FP32:
+            // divides by the pivot; double-float: multiplies by its
+            // reciprocal, which the thread that finishes the next pivot
+            // forms); one barrier per step.  The multipliers go to Lm and into the strip
+            // at its end (the other groups read column pk during the step).
+            TC(*Lm)[33] = reinterpret_cast<TC(*)[33]>(&M[128][0]);
+            const int rt = tid & 127, cg = tid >> 7;
+            const bool srow = rt >= s0 && rt < kbp;      // uniform per warp
+            if (tid == 0) {
+                const TC p = M[s0][s0];
+                piv[s0] = p;
+                prcp[0] = panel_rcp(p);
+            }
+            __syncthreads();
+#pragma unroll 1
+            for (int k = 0; k < 32; ++k) {
+                const int pk = s0 + k, buf = k & 1;
+                if (srow && rt > pk) {
+                    const TC l = panel_mult(M[rt][pk], prcp[buf]);
+                    if (cg == 0) Lm[rt][k] = l;
+                    if (4 * cg + 3 > k) {                // uniform per warp
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int c = s0 + 4 * cg + j;
+                            if (c > pk) {
+                                const TC v = fms(M[rt][c], l, M[pk][c]);
+                                M[rt][c] = v;
+                                if (rt == pk + 1 && c == pk + 1 && k < 31) {   // the next pivot
+                                    piv[pk + 1] = v;
+                                    prcp[buf ^ 1] = panel_rcp(v);
+                                }
+                            }
                         }
                     }
                 }
+                __syncthreads();
+            }
+            // the multipliers into the strip (below each pivot)
+            for (int idx = tid; idx < 32 * 128; idx += kPanelThreads) {
+                const int r = idx >> 5, k = idx & 31;
+                if (r > s0 + k && r < kbp) M[r][s0 + k] = Lm[r][k];
+            }
+            __syncthreads();
         }
-        __syncthreads();
+        const int e0 = s0 + 32, W = kbp - e0;
+        if (W <= 0) break;
+        // ---- (2) the block row: L11 x = a for each column e0 + col ----
+        {
+            const int col = tid >> 3, g = tid & 7;      // rows s0 + g + 8 m
+            if (col < W) {                               // uniform per warp (4 columns per warp)
+                TC x[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = ty + 32 * i;
-            if (r > k && r < kb) {            // warp-uniform
-                const TC l = lcol[buf][r];
+                for (int m = 0; m < 4; ++m) x[m] = M[s0 + g + 8 * m][e0 + col];
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (32 * j + 31 > k) {      // column slot not yet finished (uniform)
-                        if (tx + 32 * j > k) a[i][j] = fms(a[i][j], l, urow[buf][tx + 32 * j]);
+                for (int b = 0; b < 4; ++b) {
+#pragma unroll 1
+                    for (int kk = 0; kk < 8; ++kk) {
+                        const int k = 8 * b + kk;
+                        const TC xk = shfl_idx(x[b], (lane & ~7) | kk);
+                        if (g > kk) x[b] = fms(x[b], M[s0 + g + 8 * b][s0 + k], xk);
+#pragma unroll
+                        for (int m = b + 1; m < 4; ++m) x[m] = fms(x[m], M[s0 + g + 8 * m][s0 + k], xk);
                     }
+                }
+#pragma unroll
+                for (int m = 0; m < 4; ++m) M[s0 + g + 8 * m][e0 + col] = x[m];
             }
         }
+        __syncthreads();
+        // ---- (3) the trailing block ----
+        const int ti = tid >> 5, tj = tid & 31;
+        if (W == 96) panel_trailing<3>(M, s0, e0, ti, tj);
+        else if (W == 64) panel_trailing<2>(M, s0, e0, ti, tj);
+        else panel_trailing<1>(M, s0, e0, ti, tj);
+        __syncthreads();
+    }
+    if constexpr (!std::is_same<TC, double>::value) {
+        // the pivots' statistics, off the pivot steps' path
+        if (tid < 32)
+            for (int k = tid; k < kb; k += 32) pivot_stats(st, k0 + k, (double)piv[k]);
     }
     using MT = decltype(mag(TC()));
     MT umax = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int r = ty + 32 * i, c = tx + 32 * j;
-            if (r < kb && c < kb) {
-                C[(k0 + r) * ldc + k0 + c] = st_as<TS>(a[i][j]);
-                if (c >= r) {
-                    const MT av = mag(a[i][j]);
-                    umax = (av > umax || isnan(av)) ? av : umax;
-                }
-            }
+    for (int idx = tid; idx < kb * kb; idx += kPanelThreads) {
+        const int r = idx / kb, c = idx % kb;
+        C[(k0 + r) * ldc + k0 + c] = st_as<TS>(M[r][c]);
+        if (c >= r) {
+            const MT av = mag(M[r][c]);
+            umax = (av > umax || isnan(av)) ? av : umax;
         }
+    }
     for (int o = 16; o > 0; o >>= 1) {
         const MT w = __shfl_xor_sync(0xffffffffu, umax, o);
         umax = (w > umax || isnan(w)) ? w : umax;
     }
-    if (tx == 0) atomic_max_nonneg(&st->max_abs_u, (double)umax);
+    if (lane == 0) atomic_max_nonneg(&st->max_abs_u, (double)umax);
 }
 
 // blockIdx.y == 0: U12 = L11^{-1} C12 on columns [c0, c0 + 64)
@@ -292,16 +425,19 @@ template <typename TS, typename TC>
 cudaError_t panel_and_trsm(TS *C, int64_t ldc, int64_t n, int64_t i0, int kb, DevStatus *st, cudaStream_t s) {
     static bool attr_done = false;
     const size_t sm = (size_t)128 * kTrsmLd * sizeof(TC);
+    const size_t smp = panel_smem<TC>();
     if (!attr_done) {
         cudaError_t e =
             cudaFuncSetAttribute(k_trsm_reg<TS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_panel_reg<TS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
     auto *ev = profile_class_slot(kProfFactorAux, 2.0 / 3.0 * (double)kb * kb * kb);
     prof_begin(ev, s);
     note_launch();
-    k_panel_reg<TS, TC><<<1, kPanelThreads, 0, s>>>(C, ldc, i0, kb, st);
+    k_panel_reg<TS, TC><<<1, kPanelThreads, smp, s>>>(C, ldc, i0, kb, st);
     prof_end(ev, s);
     const int64_t rem = n - i0 - kb;
     if (rem <= 0) return cudaGetLastError();
@@ -353,6 +489,9 @@ cudaError_t factor_tc(genp_factors *F, cudaStream_t s) {
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(k_trsm_reg<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              128 * kTrsmLd * (int)sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_panel_reg<float, dfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)panel_smem<dfloat>());
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
@@ -361,7 +500,7 @@ cudaError_t factor_tc(genp_factors *F, cudaStream_t s) {
     for (int64_t k0 = 0; k0 < n; k0 += nb) {
         const int kb = (int)(n - k0 < nb ? n - k0 : nb);
         note_launch();
-        k_panel_reg<float, dfloat><<<1, kPanelThreads, 0, s>>>(C, ldc, k0, kb, F->st);
+        k_panel_reg<float, dfloat><<<1, kPanelThreads, panel_smem<dfloat>(), s>>>(C, ldc, k0, kb, F->st);
         const int64_t rem = n - k0 - kb;
         if (rem <= 0) break;
         dim3 g((unsigned)cdiv(rem, kTrsmW), 2);

@@ -188,6 +188,58 @@ __global__ void __launch_bounds__(256) k_gemv_n(int64_t m, int nr, int64_t k, T 
     }
 }
 
+// op(A) = A, FP64, one contiguous right-hand side, 16-byte aligned rows of
+// even length: the streaming form.  Each warp takes RW2 rows at a time; every
+// lane loads 16-byte pairs of A and b, the loads of U column chunks issued
+// together before their FMAs (RW2 x U + U pairs of 16 bytes in flight per
+// lane), and the grid is one wave of CTAs resident on every SM.
+template <int RW2, int U>
+__global__ void __launch_bounds__(256) k_gemv_n2(int64_t m, int64_t k2, double alpha, const double2 *__restrict__ A,
+                                                  int64_t lda2, const double2 *__restrict__ b, double beta,
+                                                  const double *Cin, int64_t ldci, double *D, int64_t ldd,
+                                                  const int *skip) {
+    if (gemv_skipped(skip)) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * 8;
+    for (int64_t i0 = ((int64_t)blockIdx.x * 8 + warp) * RW2; i0 < m; i0 += nwarps * RW2) {
+        const double2 *arow[RW2];
+#pragma unroll
+        for (int r = 0; r < RW2; ++r) arow[r] = A + (i0 + r < m ? i0 + r : i0) * lda2;
+        double acc[RW2];
+#pragma unroll
+        for (int r = 0; r < RW2; ++r) acc[r] = 0.0;
+        for (int64_t k0 = lane; k0 < k2; k0 += 32 * U) {
+            double2 av[U][RW2], bv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t kk = k0 + 32 * u;
+                const bool in = kk < k2;
+                bv[u] = in ? __ldg(b + kk) : make_double2(0.0, 0.0);
+#pragma unroll
+                for (int r = 0; r < RW2; ++r) av[u][r] = in ? __ldcs(arow[r] + kk) : make_double2(0.0, 0.0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int r = 0; r < RW2; ++r) acc[r] = fma(av[u][r].y, bv[u].y, fma(av[u][r].x, bv[u].x, acc[r]));
+        }
+#pragma unroll
+        for (int r = 0; r < RW2; ++r)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+        if (lane < RW2) {
+            double v = 0.0;
+#pragma unroll
+            for (int r = 0; r < RW2; ++r) v = r == lane ? acc[r] : v;
+            const int64_t i = i0 + lane;
+            if (i < m) {
+                const double prev = beta == 0.0 ? 0.0 : beta * Cin[i * ldci];
+                D[i * ldd] = alpha * v + prev;
+            }
+        }
+    }
+}
+
 template <typename T, int NR>
 __global__ void __launch_bounds__(256) k_gemv_t(int64_t m, int nr, int64_t k, T alpha, const T *__restrict__ A,
                                                  int64_t lda, const T *__restrict__ B, int64_t ldb, T beta,
@@ -240,6 +292,22 @@ cudaError_t run_gemv(int64_t m, int64_t n, int64_t k, T alpha, const T *A, int64
         const int64_t blocks = cdiv(m, 32) < 65535 ? cdiv(m, 32) : 65535;
         k_gemv_t<T, NR><<<(unsigned)blocks, 256, 0, s>>>(m, (int)n, k, alpha, A, lda, B, ldb, beta, Cin, ldci, D,
                                                           ldd, skip);
+    } else if (std::is_same<T, double>::value && n == 1 && ldb == 1 && k % 2 == 0 && lda % 2 == 0 &&
+               (uintptr_t)A % 16 == 0 && (uintptr_t)B % 16 == 0) {
+        // one contiguous RHS: 16-byte loads, four rows per warp, 8 x 16 B of A in
+        // flight per lane, one wave of 8 CTAs per SM
+        static int sms = 0;
+        if (!sms) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 148;
+        }
+        constexpr int RW2 = 4, U = 2;
+        const int64_t want = cdiv(m, 8 * RW2), blocks = want < 8 * sms ? want : 8 * sms;
+        k_gemv_n2<RW2, U><<<(unsigned)blocks, 256, 0, s>>>(
+            m, k / 2, (double)alpha, reinterpret_cast<const double2 *>(A), lda / 2,
+            reinterpret_cast<const double2 *>(B), (double)beta, reinterpret_cast<const double *>(Cin), ldci,
+            reinterpret_cast<double *>(D), ldd, skip);
     } else {
         // one RHS: two rows per warp, 16 loads in flight per lane and ~7 CTAs
         // per SM (the 4-row form left one wave of 3.4 CTAs per SM, 44% of HBM)
@@ -285,9 +353,15 @@ cudaError_t dispatch(int64_t m, int64_t n, int64_t k, T alpha, const T *A, int64
     if (n <= 16)
         return run<T, 64, 16, 16, 4, 4, TA, AS, BS>(m, n, k, alpha, A, lda, B, ldb, beta, Cin, ldci, D, ldd,
                                                      skip, g, gn, s);
-    if (sizeof(T) == 8)
+    if (sizeof(T) == 8) {
+        // FP64 is DFMA-bound: a product too small to give every SM two 64 x 64
+        // tiles takes 32 x 32 tiles (four times the CTAs)
+        if (cdiv(m, 64) * cdiv(n, 64) < 2 * 152)
+            return run<T, 32, 32, 16, 2, 2, TA, AS, BS>(m, n, k, alpha, A, lda, B, ldb, beta, Cin, ldci, D, ldd,
+                                                         skip, g, gn, s);
         return run<T, 64, 64, 16, 4, 4, TA, AS, BS>(m, n, k, alpha, A, lda, B, ldb, beta, Cin, ldci, D, ldd,
                                                      skip, g, gn, s);
+    }
     return run<T, 128, 128, 8, 8, 8, TA, AS, BS>(m, n, k, alpha, A, lda, B, ldb, beta, Cin, ldci, D, ldd,
                                                   skip, g, gn, s);
 }

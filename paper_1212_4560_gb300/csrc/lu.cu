@@ -153,11 +153,12 @@ __device__ __forceinline__ void panel_trailing(TC (*M)[kPanelLd], int s0, int e0
         for (int b = 0; b < R; ++b) M[e0 + ti + 32 * a][e0 + tj + 32 * b] = acc[a][b];
 }
 
-// dynamic shared memory: the block, and for the FP32-pipe types the strip's
-// multipliers (128 x 33)
+// dynamic shared memory: the block's kbp rows (kb rounded up to 32), and
+// for the FP32-pipe types the strip's multipliers (kbp x 33)
 template <typename TC>
-constexpr size_t panel_smem() {
-    return (size_t)128 * kPanelLd * sizeof(TC) + (std::is_same<TC, double>::value ? 0 : (size_t)128 * 33 * sizeof(TC));
+size_t panel_smem(int kb) {
+    const size_t kbp = (size_t)((kb + 31) & ~31);
+    return kbp * kPanelLd * sizeof(TC) + (std::is_same<TC, double>::value ? 0 : kbp * 33 * sizeof(TC));
 }
 
 template <typename TS, typename TC>
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_panel_reg(TS *C, int64_t l
             // reciprocal, which the thread that finishes the next pivot
             // forms); one barrier per step.  The multipliers go to Lm and into the strip
             // at its end (the other groups read column pk during the step).
-            TC(*Lm)[33] = reinterpret_cast<TC(*)[33]>(&M[128][0]);
+            TC(*Lm)[33] = reinterpret_cast<TC(*)[33]>(&M[kbp][0]);
             const int rt = tid & 127, cg = tid >> 7;
             const bool srow = rt >= s0 && rt < kbp;      // uniform per warp
             if (tid == 0) {
@@ -332,29 +333,44 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_panel_reg(TS *C, int64_t l
 // are unrolled, so a step costs the updates still to do and nothing for the
 // blocks already solved (no per-entry conditions), and the step loop stays
 // rolled (small code).  The kb x kb (kb <= 128) diagonal block sits in
-// shared memory, padded to 128 x 128 with the identity, so a ragged last
-// block needs no bounds checks.  32 warps per SM hide the latency of the
+// shared memory (row stride kbq + 1, kbq = kb rounded up to 16), padded
+// with the identity, so a ragged last block needs no bounds checks.  32 warps per SM hide the latency of the
 // dependent double-float operations.
-constexpr int kTrsmThreads = 1024, kTpv = 16, kEpt = 128 / kTpv, kTrsmLd = 129;
+constexpr int kTrsmThreads = 1024, kTpv = 16, kEpt = 128 / kTpv;
+// dynamic shared memory of a block solve: the diagonal block rounded up to 16
+template <typename TC>
+size_t trsm_smem(int kb) {
+    const int kbq = (kb + kTpv - 1) / kTpv * kTpv;
+    return (size_t)kbq * (kbq + 1) * sizeof(TC);
+}
 template <typename TS, typename TC>
 __global__ void __launch_bounds__(kTrsmThreads, 1) k_trsm_reg(TS *C, int64_t ldc, int64_t n, int64_t k0, int kb,
                                                               DevStatus *st) {
     extern __shared__ __align__(16) unsigned char smraw[];
     TC *T = reinterpret_cast<TC *>(smraw);
-    constexpr int ld = kTrsmLd;
+    const int nq = (kb + kTpv - 1) / kTpv, kbq = kTpv * nq, ld = kbq + 1;   // the block rounded up to 16
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int v = tid / kTpv, g = tid % kTpv;
     const int64_t c0 = k0 + kb + (int64_t)blockIdx.x * kTrsmW;
     const int w = (int)min((int64_t)kTrsmW, n - c0);
     if (w <= 0) return;
     const bool role_u = blockIdx.y == 0;
-    for (int r = warp; r < 128; r += kTrsmThreads / 32)
-        for (int c = lane; c < 128; c += 32)
+    for (int r = warp; r < kbq; r += kTrsmThreads / 32)
+        for (int c = lane; c < kbq; c += 32)
             T[r * ld + c] = (r < kb && c < kb) ? ld_as<TC>(C[(k0 + r) * ldc + k0 + c]) : TC(r == c ? 1.0 : 0.0);
+    __syncthreads();
+    // the L role divides by u_jj at every step: in FP64 and double-float by
+    // reciprocals formed once (an FP64 division is a sequence of operations
+    // that a whole warp issues for its one dividing lane, at 1/64 of the
+    // FP32 rate on this GPU); FP32 divides
+    constexpr bool kRcp = !std::is_same<TC, float>::value;
+    if (kRcp && !role_u && tid < kbq) {
+        const TC one(1.0);
+        T[tid * ld + tid] = one / T[tid * ld + tid];
+    }
     __syncthreads();
     const bool valid = v < w;
     const int base = lane & ~(kTpv - 1);
-    const int nq = (kb + kTpv - 1) / kTpv;
     TC x[kEpt];
     if (role_u) {
         // L11 x = c, L11 unit lower: x_r -= l_rk x_k for r > k
@@ -372,7 +388,8 @@ __global__ void __launch_bounds__(kTrsmThreads, 1) k_trsm_reg(TS *C, int64_t ldc
                 const TC xk = shfl_idx(x[b], base | kk);       // entry k, final
                 if (g > kk) x[b] = fms(x[b], T[(g + kTpv * b) * ld + k], xk);
 #pragma unroll
-                for (int m = b + 1; m < kEpt; ++m) x[m] = fms(x[m], T[(g + kTpv * m) * ld + k], xk);
+                for (int m = b + 1; m < kEpt; ++m)
+                    if (m < nq) x[m] = fms(x[m], T[(g + kTpv * m) * ld + k], xk);   // (uniform) past kb: padding
             }
         }
         using MT = decltype(mag(TC()));
@@ -404,11 +421,12 @@ __global__ void __launch_bounds__(kTrsmThreads, 1) k_trsm_reg(TS *C, int64_t ldc
 #pragma unroll 1
             for (int kk = 0; kk < kTpv; ++kk) {
                 const int j = kTpv * b + kk;
-                if (g == kk) x[b] = x[b] / T[j * ld + j];           // l_vj = x_vj / u_jj
+                if (g == kk) x[b] = kRcp ? x[b] * T[j * ld + j] : x[b] / T[j * ld + j];   // l_vj = x_vj / u_jj
                 const TC xj = shfl_idx(x[b], base | kk);
                 if (g > kk) x[b] = fms(x[b], xj, T[j * ld + g + kTpv * b]);
 #pragma unroll
-                for (int m = b + 1; m < kEpt; ++m) x[m] = fms(x[m], xj, T[j * ld + g + kTpv * m]);
+                for (int m = b + 1; m < kEpt; ++m)
+                    if (m < nq) x[m] = fms(x[m], xj, T[j * ld + g + kTpv * m]);
             }
         }
 #pragma unroll
@@ -424,13 +442,15 @@ __global__ void __launch_bounds__(kTrsmThreads, 1) k_trsm_reg(TS *C, int64_t ldc
 template <typename TS, typename TC>
 cudaError_t panel_and_trsm(TS *C, int64_t ldc, int64_t n, int64_t i0, int kb, DevStatus *st, cudaStream_t s) {
     static bool attr_done = false;
-    const size_t sm = (size_t)128 * kTrsmLd * sizeof(TC);
-    const size_t smp = panel_smem<TC>();
+    const size_t sm = trsm_smem<TC>(kb);
+    const size_t smp = panel_smem<TC>(kb);
     if (!attr_done) {
         cudaError_t e =
-            cudaFuncSetAttribute(k_trsm_reg<TS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaFuncSetAttribute(k_trsm_reg<TS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)trsm_smem<TC>(128));
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_panel_reg<TS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+            e = cudaFuncSetAttribute(k_panel_reg<TS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)panel_smem<TC>(128));
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
@@ -488,10 +508,10 @@ cudaError_t factor_tc(genp_factors *F, cudaStream_t s) {
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(k_trsm_reg<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             128 * kTrsmLd * (int)sizeof(float));
+                                             (int)trsm_smem<float>(128));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_panel_reg<float, dfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)panel_smem<dfloat>());
+                                     (int)panel_smem<dfloat>(128));
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
@@ -500,12 +520,12 @@ cudaError_t factor_tc(genp_factors *F, cudaStream_t s) {
     for (int64_t k0 = 0; k0 < n; k0 += nb) {
         const int kb = (int)(n - k0 < nb ? n - k0 : nb);
         note_launch();
-        k_panel_reg<float, dfloat><<<1, kPanelThreads, panel_smem<dfloat>(), s>>>(C, ldc, k0, kb, F->st);
+        k_panel_reg<float, dfloat><<<1, kPanelThreads, panel_smem<dfloat>(kb), s>>>(C, ldc, k0, kb, F->st);
         const int64_t rem = n - k0 - kb;
         if (rem <= 0) break;
         dim3 g((unsigned)cdiv(rem, kTrsmW), 2);
         note_launch();
-        k_trsm_reg<float, float><<<g, kTrsmThreads, (size_t)128 * kTrsmLd * sizeof(float), s>>>(C, ldc, n, k0, kb,
+        k_trsm_reg<float, float><<<g, kTrsmThreads, trsm_smem<float>(kb), s>>>(C, ldc, n, k0, kb,
                                                                                                F->st);
         float *L21 = C + (k0 + kb) * ldc + k0;
         float *U12 = C + k0 * ldc + k0 + kb;

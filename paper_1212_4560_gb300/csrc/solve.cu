@@ -956,20 +956,30 @@ __global__ void __launch_bounds__(TB) k_trtri_diag(const TS *C, int64_t ldc, int
     for (int r = 0; r < TB; ++r) t[r][c] = (r < bj && c < bj) ? (double)C[(j0 + r) * ldc + j0 + c] : 0.0;
     __syncthreads();
     for (int r = 0; r < TB; ++r) x[r][c] = 0.0;
+    // each row's sum in four interleaved partial sums (the FP64 units' latency
+    // made the single dependent chain the launch's cost)
     if (c < bj) {
         if (which == 0) {   // L x = e_c, unit diagonal
             x[c][c] = 1.0;
             for (int r = c + 1; r < bj; ++r) {
-                double sum = 0.0;
-                for (int k = c; k < r; ++k) sum = fma(t[r][k], x[k][c], sum);
-                x[r][c] = -sum;
+                double s4[4] = {0.0, 0.0, 0.0, 0.0};
+                int k = c;
+                for (; k + 3 < r; k += 4)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) s4[q] = fma(t[r][k + q], x[k + q][c], s4[q]);
+                for (; k < r; ++k) s4[0] = fma(t[r][k], x[k][c], s4[0]);
+                x[r][c] = -((s4[0] + s4[1]) + (s4[2] + s4[3]));
             }
         } else {            // U x = e_c
             x[c][c] = 1.0 / t[c][c];
             for (int r = c - 1; r >= 0; --r) {
-                double sum = 0.0;
-                for (int k = r + 1; k <= c; ++k) sum = fma(t[r][k], x[k][c], sum);
-                x[r][c] = -sum / t[r][r];
+                double s4[4] = {0.0, 0.0, 0.0, 0.0};
+                int k = r + 1;
+                for (; k + 3 <= c; k += 4)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) s4[q] = fma(t[r][k + q], x[k + q][c], s4[q]);
+                for (; k <= c; ++k) s4[0] = fma(t[r][k], x[k][c], s4[0]);
+                x[r][c] = -((s4[0] + s4[1]) + (s4[2] + s4[3])) / t[r][r];
             }
         }
     }

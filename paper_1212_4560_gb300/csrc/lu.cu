@@ -102,8 +102,9 @@ __device__ __forceinline__ void pivot_stats(DevStatus *st, int64_t step, double 
 // A12, 8 threads per column with the substitution carried by shuffles; (3)
 // the trailing block -= L21 U12 (K = 32), a register-tiled product over all
 // threads.  The pivot steps touch only the strip; most of the arithmetic is
-// in (3), without per-step barriers.  FP64 divides by the pivot, as in the
-// unblocked recurrence; double-float multiplies by its reciprocal.
+// in (3), without per-step barriers.  FP64 and double-float multiply by the
+// pivot's reciprocal (an FP64 division per row costs a warp-wide sequence of
+// FP64 operations each), FP32 divides.
 constexpr int kPanelThreads = 1024, kPanelLd = 129;
 
 // 1 / p in double-float by two Newton steps from the hardware's
@@ -193,8 +194,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_panel_reg(TS *C, int64_t l
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
                             if (j == (k >> 3)) p = sv[j];
-                        if constexpr (std::is_same<TC, dfloat>::value) prcp[buf] = TC(1.0) / p;
-                        else prcp[buf] = p;
+                        prcp[buf] = TC(1.0) / p;   // one reciprocal per pivot, not a division per row
                         if (pk < kb) pivot_stats(st, k0 + pk, (double)p);
                     }
                 }
@@ -204,8 +204,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_panel_reg(TS *C, int64_t l
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
                         if (j == (k >> 3)) {
-                            if constexpr (std::is_same<TC, dfloat>::value) sv[j] = sv[j] * prcp[buf];
-                            else sv[j] = sv[j] / prcp[buf];
+                            sv[j] = sv[j] * prcp[buf];
                             l = sv[j];
                         }
                 }

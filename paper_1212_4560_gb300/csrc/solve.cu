@@ -957,7 +957,11 @@ __global__ void __launch_bounds__(TB) k_trtri_diag(const TS *C, int64_t ldc, int
     __syncthreads();
     for (int r = 0; r < TB; ++r) x[r][c] = 0.0;
     // each row's sum in four interleaved partial sums (the FP64 units' latency
-    // made the single dependent chain the launch's cost)
+    // made the single dependent chain the launch's cost); U's diagonal by its
+    // reciprocals, formed once
+    __shared__ double rdiag[TB];
+    if (which == 1) rdiag[c] = c < bj ? 1.0 / t[c][c] : 0.0;
+    __syncthreads();
     if (c < bj) {
         if (which == 0) {   // L x = e_c, unit diagonal
             x[c][c] = 1.0;
@@ -971,7 +975,7 @@ __global__ void __launch_bounds__(TB) k_trtri_diag(const TS *C, int64_t ldc, int
                 x[r][c] = -((s4[0] + s4[1]) + (s4[2] + s4[3]));
             }
         } else {            // U x = e_c
-            x[c][c] = 1.0 / t[c][c];
+            x[c][c] = rdiag[c];
             for (int r = c - 1; r >= 0; --r) {
                 double s4[4] = {0.0, 0.0, 0.0, 0.0};
                 int k = r + 1;
@@ -979,7 +983,7 @@ __global__ void __launch_bounds__(TB) k_trtri_diag(const TS *C, int64_t ldc, int
 #pragma unroll
                     for (int q = 0; q < 4; ++q) s4[q] = fma(t[r][k + q], x[k + q][c], s4[q]);
                 for (; k <= c; ++k) s4[0] = fma(t[r][k], x[k][c], s4[0]);
-                x[r][c] = -((s4[0] + s4[1]) + (s4[2] + s4[3])) / t[r][r];
+                x[r][c] = -((s4[0] + s4[1]) + (s4[2] + s4[3])) * rdiag[r];
             }
         }
     }

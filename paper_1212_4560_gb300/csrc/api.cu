@@ -810,12 +810,15 @@ genp_status genp_refactor(genp_factors *F, void *C, int64_t ldc, void *cuda_stre
 
 void genp_factors_destroy(genp_factors *F) {
     if (!F) return;
-    bool any = F->rg_stream != nullptr;
+    bool any = F->rg_stream != nullptr || F->la_stream != nullptr;
     for (auto &g : F->rgraph) any = any || g.exec;
-    if (any) cudaDeviceSynchronize();   // graphs and their stream may still be in use
+    if (any) cudaDeviceSynchronize();   // graphs and their streams may still be in use
     for (auto &g : F->rgraph)
         if (g.exec) cudaGraphExecDestroy(g.exec);
     if (F->rg_stream) cudaStreamDestroy(F->rg_stream);
+    if (F->la_stream) cudaStreamDestroy(F->la_stream);
+    for (auto &ev : F->la_ev)
+        if (ev) cudaEventDestroy(ev);
     cudaFree(F->st);
     cudaFree(F->norms);
     cudaFree(F->work);

@@ -941,6 +941,10 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S_TMEM) : "memory");
 }
 
+// SMs the persistent sliced product leaves free (a concurrent one-CTA
+// kernel of the factorization's look-ahead runs there); per host thread.
+thread_local int tl_sliced_spare = 0;
+
 // Optional CUDA-event timing of every k_tc_sliced launch (genp_profile_*).
 struct TcProfile {
     bool on = false;
@@ -1010,7 +1014,8 @@ cudaError_t launch_sliced(const CUtensorMap &ma, const CUtensorMap &mb, int64_t 
     }
     const int64_t tiles = cdiv(m, BM) * cdiv(n, SBN);
     if (tiles > INT32_MAX) return cudaErrorInvalidValue;
-    const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
+    const int use = sms - tl_sliced_spare > 0 ? sms - tl_sliced_spare : 1;
+    const unsigned grid = (unsigned)(tiles < use ? tiles : use);
     auto *ev = profile_slot(2.0 * (double)m * (double)n * (double)kpad * Cfg::kPairs,
                             2.0 * (double)m * (double)n * (double)kpad);
     if (ev) cudaEventRecord(ev->first, s);
@@ -1034,6 +1039,12 @@ bool make_map_8b(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, 
     return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void *>(ptr), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int sliced_spare_sms(int k) {
+    const int prev = tl_sliced_spare;
+    tl_sliced_spare = k;
+    return prev;
 }
 
 cudaError_t tc_gemm_sliced(int nd, int64_t m, int64_t n, int64_t kpad, float alpha, const __nv_bfloat16 *Aq,

@@ -91,6 +91,8 @@ struct genp_factors {
     GenpRefineGraph rgraph[4];         // cached refinement graphs, round robin
     int rg_next = 0;
     cudaStream_t rg_stream = nullptr;  // private stream the graphs are recorded on
+    cudaStream_t la_stream = nullptr;  // the sliced factorization's look-ahead stream
+    cudaEvent_t la_ev[2] = {nullptr, nullptr};   // update done -> block factored
     void *C = nullptr;
     int64_t n = 0, ldc = 0, nb = 64;
     genp_prec prec = GENP_FP64;
@@ -284,6 +286,9 @@ cudaError_t tc_gemm_sliced2(int nda, int ndb, int64_t m, int64_t n, int64_t kpad
 cudaError_t tc_gemm_sliced(int nd, int64_t m, int64_t n, int64_t kpad, float alpha, const __nv_bfloat16 *Aq,
                            int64_t lda, const __nv_bfloat16 *Bq, int64_t ldb, const int *ea, const int *fb, dfloat *D,
                            int64_t ldd, cudaStream_t s);
+// SMs the persistent sliced product leaves free from now on in this host
+// thread (0: none); returns the previous value.
+int sliced_spare_sms(int k);
 
 // sliced.cu: exact 7-bit digit slicing of FP64 operands (Ozaki scheme).
 int64_t sliced_kpad(int64_t K);   // K rounded up to the k-tile

@@ -437,37 +437,51 @@ __global__ void __launch_bounds__(kTrsmThreads, 1) k_trsm_reg(TS *C, int64_t ldc
 }
 
 // one step of the blocked factorization's panel work: the diagonal block at
-// (i0, i0), then the block row and column beside it
+// (i0, i0) (panel_only), then the block row and column beside it (trsm_only)
 template <typename TS, typename TC>
-cudaError_t panel_and_trsm(TS *C, int64_t ldc, int64_t n, int64_t i0, int kb, DevStatus *st, cudaStream_t s) {
+cudaError_t panel_attrs() {
     static bool attr_done = false;
-    const size_t sm = trsm_smem<TC>(kb);
-    const size_t smp = panel_smem<TC>(kb);
     if (!attr_done) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_trsm_reg<TS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)trsm_smem<TC>(128));
+        cudaError_t e = cudaFuncSetAttribute(k_trsm_reg<TS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)trsm_smem<TC>(128));
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_panel_reg<TS, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)panel_smem<TC>(128));
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
+    return cudaSuccess;
+}
+template <typename TS, typename TC>
+cudaError_t panel_only(TS *C, int64_t ldc, int64_t i0, int kb, DevStatus *st, cudaStream_t s) {
+    cudaError_t e = panel_attrs<TS, TC>();
+    if (e != cudaSuccess) return e;
     auto *ev = profile_class_slot(kProfFactorAux, 2.0 / 3.0 * (double)kb * kb * kb);
     prof_begin(ev, s);
     note_launch();
-    k_panel_reg<TS, TC><<<1, kPanelThreads, smp, s>>>(C, ldc, i0, kb, st);
-    prof_end(ev, s);
-    const int64_t rem = n - i0 - kb;
-    if (rem <= 0) return cudaGetLastError();
-    dim3 g((unsigned)cdiv(rem, kTrsmW), 2);
-    // block row and block column: kb^2 flops per vector of length kb, 2 rem vectors
-    ev = profile_class_slot(kProfFactorAux, 2.0 * (double)kb * kb * (double)rem);
-    prof_begin(ev, s);
-    note_launch();
-    k_trsm_reg<TS, TC><<<g, kTrsmThreads, sm, s>>>(C, ldc, n, i0, kb, st);
+    k_panel_reg<TS, TC><<<1, kPanelThreads, panel_smem<TC>(kb), s>>>(C, ldc, i0, kb, st);
     prof_end(ev, s);
     return cudaGetLastError();
+}
+template <typename TS, typename TC>
+cudaError_t trsm_only(TS *C, int64_t ldc, int64_t n, int64_t i0, int kb, DevStatus *st, cudaStream_t s) {
+    const int64_t rem = n - i0 - kb;
+    if (rem <= 0) return cudaSuccess;
+    cudaError_t e = panel_attrs<TS, TC>();
+    if (e != cudaSuccess) return e;
+    dim3 g((unsigned)cdiv(rem, kTrsmW), 2);
+    // block row and block column: kb^2 flops per vector of length kb, 2 rem vectors
+    auto *ev = profile_class_slot(kProfFactorAux, 2.0 * (double)kb * kb * (double)rem);
+    prof_begin(ev, s);
+    note_launch();
+    k_trsm_reg<TS, TC><<<g, kTrsmThreads, trsm_smem<TC>(kb), s>>>(C, ldc, n, i0, kb, st);
+    prof_end(ev, s);
+    return cudaGetLastError();
+}
+template <typename TS, typename TC>
+cudaError_t panel_and_trsm(TS *C, int64_t ldc, int64_t n, int64_t i0, int kb, DevStatus *st, cudaStream_t s) {
+    cudaError_t e = panel_only<TS, TC>(C, ldc, i0, kb, st, s);
+    return e == cudaSuccess ? trsm_only<TS, TC>(C, ldc, n, i0, kb, st, s) : e;
 }
 
 template <typename TS, typename TC>
@@ -570,6 +584,44 @@ cudaError_t factor_sliced(genp_factors *F, cudaStream_t s) {
     // which the digit-pair groups stay exact in FP32, so the fewest TMEM
     // read-outs per MMA), inner steps of nb
     const int nb = (int)F->nb, nbo = 2 * nb > kSlicedOuter ? 2 * nb : kSlicedOuter;
+    // Look-ahead: each update that precedes a diagonal block first updates
+    // that block's columns; the block is then factored on a second stream (one
+    // SM, which the rest of the update leaves free) while the rest of the
+    // update runs, and the block solves wait for both.
+    // (the stream and events are made on the first factorization outside a
+    // stream capture; a captured one joins the second stream into its graph)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusActive;
+    }
+    if (cap == cudaStreamCaptureStatusNone) {
+        if (!F->la_stream && cudaStreamCreateWithFlags(&F->la_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            F->la_stream = nullptr;
+        }
+        for (auto &ev : F->la_ev)
+            if (!ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                ev = nullptr;
+            }
+    }
+    cudaStream_t s2 = F->la_stream;
+    const bool ahead = s2 && F->la_ev[0] && F->la_ev[1];
+    bool pending = false;   // the current block is being factored on s2
+    auto block_ahead = [&](int64_t p0, int pb) -> cudaError_t {
+        cudaError_t e = cudaEventRecord(F->la_ev[0], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, F->la_ev[0], 0);
+        if (e == cudaSuccess) e = panel_only<dfloat, dfloat>(W, ldw, p0, pb, F->st, s2);
+        if (e == cudaSuccess) e = cudaEventRecord(F->la_ev[1], s2);
+        pending = e == cudaSuccess;
+        return e;
+    };
+    // D[rows r0.., cols c0..c0+w) -= L U over the sliced operands' columns c0 - cb ..
+    auto update = [&](int64_t m, int64_t w, int64_t kpad, int64_t bcol, dfloat *D) {
+        return tc_gemm_sliced(F->nd, m, w, kpad, -1.0f, F->tcA, ldq, F->tcB + bcol * ldq, ldq, F->exps,
+                              F->exps + n + bcol, D, ldw, s);
+    };
     note_launch();
     k_maxabs<double><<<152 * 4, 256, 0, s>>>(C, n, ldc, &F->st->max_abs_c);
     cudaError_t e = df_from_f64(C, ldc, W, ldw, n, n, s);
@@ -580,7 +632,13 @@ cudaError_t factor_sliced(genp_factors *F, cudaStream_t s) {
         for (int64_t i0 = k0; i0 < e0; i0 += nb) {
             const int kb = (int)(e0 - i0 < nb ? e0 - i0 : nb);
             const int64_t j0 = i0 + kb, rem = n - j0;
-            e = panel_and_trsm<dfloat, dfloat>(W, ldw, n, i0, kb, F->st, s);
+            if (pending) {
+                e = cudaStreamWaitEvent(s, F->la_ev[1], 0);
+                pending = false;
+            } else {
+                e = panel_only<dfloat, dfloat>(W, ldw, i0, kb, F->st, s);
+            }
+            if (e == cudaSuccess) e = trsm_only<dfloat, dfloat>(W, ldw, n, i0, kb, F->st, s);
             if (e != cudaSuccess) return e;
             if (rem <= 0) break;
             if (j0 < e0) {
@@ -589,20 +647,27 @@ cudaError_t factor_sliced(genp_factors *F, cudaStream_t s) {
                 // (columns j0..n) are final, so they go to C in FP64 (exactly) and
                 // are sliced once for both updates
                 const int64_t w2 = e0 - j0;
+                const int nb2 = (int)(w2 < nb ? w2 : nb);   // the next inner block
                 double *Lc = C + j0 * ldc + i0;
                 double *Uc = C + i0 * ldc + j0;
                 unsigned long long *kk = reinterpret_cast<unsigned long long *>(F->exps + 2 * n);
+                const int64_t kp = sliced_kpad(kb);
                 e = df_to_f64(W + j0 * ldw + i0, ldw, Lc, ldc, rem, kb, s);
                 if (e == cudaSuccess) e = df_to_f64(W + i0 * ldw + j0, ldw, Uc, ldc, kb, rem, s);
                 if (e == cudaSuccess) e = sliced_inner_exps(Lc, ldc, rem, kb, kk, s);
                 if (e == cudaSuccess) e = slice_rows(F->nd, Lc, ldc, rem, kb, F->tcA, ldq, F->exps, s, kk);
                 if (e == cudaSuccess) e = slice_cols_T(F->nd, Uc, ldc, kb, rem, F->tcB, ldq, F->exps + n, s, kk);
-                if (e == cudaSuccess)
-                    e = tc_gemm_sliced(F->nd, rem, w2, sliced_kpad(kb), -1.0f, F->tcA, ldq, F->tcB, ldq, F->exps,
-                                       F->exps + n, W + j0 * ldw + j0, ldw, s);
-                if (e == cudaSuccess && remo > 0)
-                    e = tc_gemm_sliced(F->nd, w2, remo, sliced_kpad(kb), -1.0f, F->tcA, ldq, F->tcB + w2 * ldq, ldq,
-                                       F->exps, F->exps + n + w2, W + j0 * ldw + e0, ldw, s);
+                if (ahead) {
+                    if (e == cudaSuccess) e = update(rem, nb2, kp, 0, W + j0 * ldw + j0);
+                    if (e == cudaSuccess) e = block_ahead(j0, nb2);
+                    const int prev = sliced_spare_sms(1);
+                    if (e == cudaSuccess && w2 > nb2) e = update(rem, w2 - nb2, kp, nb2, W + j0 * ldw + j0 + nb2);
+                    if (e == cudaSuccess && remo > 0) e = update(w2, remo, kp, w2, W + j0 * ldw + e0);
+                    sliced_spare_sms(prev);
+                } else {
+                    if (e == cudaSuccess) e = update(rem, w2, kp, 0, W + j0 * ldw + j0);
+                    if (e == cudaSuccess && remo > 0) e = update(w2, remo, kp, w2, W + j0 * ldw + e0);
+                }
                 if (e != cudaSuccess) return e;
             }
         }
@@ -621,9 +686,21 @@ cudaError_t factor_sliced(genp_factors *F, cudaStream_t s) {
         e = sliced_inner_exps(L21, ldc, remo, kbo, kexp, s);
         if (e == cudaSuccess) e = slice_rows(F->nd, L21, ldc, remo, kbo, F->tcA, ldq, F->exps, s, kexp);
         if (e == cudaSuccess) e = slice_cols_T(F->nd, U12, ldc, kbo, remo, F->tcB, ldq, F->exps + n, s, kexp);
-        if (e == cudaSuccess)
-            e = tc_gemm_sliced(F->nd, remo, remo, sliced_kpad(kbo), -1.0f, F->tcA, ldq, F->tcB, ldq, F->exps,
-                               F->exps + n, W + e0 * ldw + e0, ldw, s);
+        const int64_t kp = sliced_kpad(kbo);
+        const int nb2 = (int)(remo < nb ? remo : nb);       // the next step's first block
+        if (ahead) {
+            if (e == cudaSuccess) e = update(remo, nb2, kp, 0, W + e0 * ldw + e0);
+            if (e == cudaSuccess) e = block_ahead(e0, nb2);
+            const int prev = sliced_spare_sms(1);
+            if (e == cudaSuccess && remo > nb2) e = update(remo, remo - nb2, kp, nb2, W + e0 * ldw + e0 + nb2);
+            sliced_spare_sms(prev);
+        } else if (e == cudaSuccess) {
+            e = update(remo, remo, kp, 0, W + e0 * ldw + e0);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    if (pending) {   // not reached (the last block is factored in place), kept for safety
+        e = cudaStreamWaitEvent(s, F->la_ev[1], 0);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();

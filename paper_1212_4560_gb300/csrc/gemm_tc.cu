@@ -641,6 +641,25 @@ __device__ bool mbar_wait_sleep(unsigned long long *b, uint32_t parity, volatile
     return true;
 }
 
+// One Horner step on two columns at once: (H, L) <- w (H, L) + p, w a power
+// of two, as double-float: TwoSum of w H and p by FMA (w H is exact, so each
+// FMA rounds once, as the plain sequence does), the error plus w L, then the
+// FastTwoSum renormalisation; ten packed FP32 instructions for two columns.
+__device__ __forceinline__ void horner2(float2 &H, float2 &L, float2 p, float2 w) {
+    const float2 mw = make_float2(-w.x, -w.y), m1 = make_float2(-1.0f, -1.0f);
+    const float2 s = __ffma2_rn(H, w, p);
+    const float2 bb = __ffma2_rn(H, mw, s);       // s - w H
+    const float2 t1 = __ffma2_rn(bb, m1, s);      // s - bb
+    const float2 t2n = __ffma2_rn(H, mw, t1);     // t1 - w H
+    const float2 t3 = __ffma2_rn(bb, m1, p);      // p - bb
+    float2 e = __ffma2_rn(t2n, m1, t3);           // (w H - t1) + (p - bb)
+    e = __ffma2_rn(L, w, e);                      // + w L
+    const float2 hn = __fadd2_rn(s, e);
+    const float2 u = __ffma2_rn(s, m1, hn);       // hn - s
+    H = hn;
+    L = __ffma2_rn(u, m1, e);                     // e - u
+}
+
 // NDA digits of the A operand, NDB of B (an operand whose entries are exact
 // in fewer digits, such as a multiplier on a fixed-point grid, takes fewer
 // and goes on the M side, so the wide operand's digits lie along N):
@@ -857,29 +876,37 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             if (r == 0) ctl->epi_go = *abort ? 0 : 1;
             epi_sync();
             if (!ctl->epi_go) break;
-            dfloat S[2][32];
+            // S as double-float, hi and lo parts of column pairs (2i, 2i + 1)
+            float2 SH[2][16], SL[2][16];
             uint32_t q[32];
+            const float2 w128 = make_float2(128.0f, 128.0f), w1 = make_float2(1.0f, 1.0f);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 // Horner over the groups, largest weight first: S = 2^7 S + P_g.  The
                 // P_g are integers below 2^24 and the partial sums integers below
-                // 2^60: exact as double-float up to 48 bits, all on the FP32 pipe.
+                // 2^60: exact as double-float up to 48 bits, all on the FP32 pipe,
+                // two columns per instruction.
                 tmem_ld32(lane_addr + (uint32_t)(32 * h), q);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) S[h][j] = dfloat(__uint_as_float(q[j]));
+                for (int i = 0; i < 16; ++i) {
+                    SH[h][i] = make_float2(__uint_as_float(q[2 * i]), __uint_as_float(q[2 * i + 1]));
+                    SL[h][i] = make_float2(0.0f, 0.0f);
+                }
 #pragma unroll 1
                 for (int g = 1; g < ND - 1; ++g) {
                     tmem_ld32(lane_addr + (uint32_t)(SBN * g + 32 * h), q);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        S[h][j].hi *= 128.0f;
-                        S[h][j].lo *= 128.0f;
-                        S[h][j] = S[h][j] + dfloat(__uint_as_float(q[j]));
-                    }
+                    for (int i = 0; i < 16; ++i)
+                        horner2(SH[h][i], SL[h][i],
+                                make_float2(__uint_as_float(q[2 * i]), __uint_as_float(q[2 * i + 1])), w128);
                 }
                 tmem_ld32(lane_addr + (uint32_t)(SBN * (ND - 1) + 32 * h), q);   // the last group: 2^-7
 #pragma unroll
-                for (int j = 0; j < 32; ++j) S[h][j] = S[h][j] + dfloat(__uint_as_float(q[j]) * 0.0078125f);
+                for (int i = 0; i < 16; ++i)
+                    horner2(SH[h][i], SL[h][i],
+                            make_float2(__uint_as_float(q[2 * i]) * 0.0078125f,
+                                        __uint_as_float(q[2 * i + 1]) * 0.0078125f),
+                            w1);
             }
             // TMEM is free for the next tile's MMAs
             fence_before();
@@ -892,11 +919,15 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             for (int h = 0; h < 2; ++h) {
                 epi_sync();                    // the staging area is free
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    dfloat a0;
-                    a0.hi = (S[h][j].hi * rs) * ctl->cs[32 * h + j];
-                    a0.lo = (S[h][j].lo * rs) * ctl->cs[32 * h + j];
-                    stage[r * kHalfLd + j] = a0;
+                for (int i = 0; i < 16; ++i) {
+                    const float c0 = ctl->cs[32 * h + 2 * i], c1 = ctl->cs[32 * h + 2 * i + 1];
+                    dfloat a0, a1;
+                    a0.hi = (SH[h][i].x * rs) * c0;
+                    a0.lo = (SL[h][i].x * rs) * c0;
+                    a1.hi = (SH[h][i].y * rs) * c1;
+                    a1.lo = (SL[h][i].y * rs) * c1;
+                    stage[r * kHalfLd + 2 * i] = a0;
+                    stage[r * kHalfLd + 2 * i + 1] = a1;
                 }
                 epi_sync();
                 const int col = n0 + 32 * h + lane;

@@ -60,6 +60,26 @@ __device__ __forceinline__ dfloat fms(dfloat x, dfloat l, dfloat u) {
     const float err = (x.hi - (s - bb)) - (p + bb);
     return df_norm(s, (err + x.lo) - pe);
 }
+// The same on two entries at once with packed FP32 operations (hi and lo
+// parts of the pair in float2 registers), the operations and roundings of
+// the scalar form in the same order: np is -l.hi u.hi, formed from the
+// negated leading part of the operand the pair shares, and a - b is an FMA
+// of b by -1 and a.
+__device__ __forceinline__ void fms2(float2 &xh, float2 &xl, float2 lh, float2 ll, float2 uh, float2 ul,
+                                     float2 np) {
+    const float2 m1 = make_float2(-1.0f, -1.0f);
+    const float2 e1 = __ffma2_rn(lh, uh, np);                         // l.hi u.hi - p
+    const float2 pe = __fadd2_rn(e1, __ffma2_rn(lh, ul, __fmul2_rn(ll, uh)));
+    const float2 sm = __fadd2_rn(xh, np);                             // x.hi - p
+    const float2 bb = __ffma2_rn(xh, m1, sm);                         // s - x.hi
+    const float2 q2 = __ffma2_rn(__ffma2_rn(bb, m1, sm), m1, xh);     // x.hi - (s - bb)
+    const float2 q3 = __ffma2_rn(np, m1, bb);                         // p + bb
+    const float2 er = __fadd2_rn(__ffma2_rn(q3, m1, q2), xl);         // err + x.lo
+    const float2 e = __ffma2_rn(pe, m1, er);                          // - pe
+    const float2 hn = __fadd2_rn(sm, e);
+    xh = hn;
+    xl = __ffma2_rn(__ffma2_rn(sm, m1, hn), m1, e);                   // e - (hn - s)
+}
 __device__ __forceinline__ double shfl_idx(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 __device__ __forceinline__ float shfl_idx(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 __device__ __forceinline__ dfloat shfl_idx(dfloat v, int src) {
@@ -337,15 +357,28 @@ __global__ void __launch_bounds__(kPanelThreads, 1) k_panel_reg(TS *C, int64_t l
 // dependent double-float operations.
 constexpr int kTrsmThreads = 1024, kTpv = 16, kEpt = 128 / kTpv;
 // dynamic shared memory of a block solve: the diagonal block rounded up to 16
+// (double-float: hi and lo planes of the block as the packed solve reads
+// it, [k][pair][thread][2], and the reciprocal pivots)
 template <typename TC>
 size_t trsm_smem(int kb) {
     const int kbq = (kb + kTpv - 1) / kTpv * kTpv;
+    if (std::is_same<TC, dfloat>::value) {
+        const int np = (kbq / kTpv + 1) / 2;
+        return (size_t)kbq * np * kTpv * 2 * sizeof(float2) + (size_t)kbq * sizeof(dfloat);
+    }
     return (size_t)kbq * (kbq + 1) * sizeof(TC);
 }
+template <typename TS>
+__device__ __forceinline__ void trsm_df(TS *C, int64_t ldc, int64_t n, int64_t k0, int kb, DevStatus *st,
+                                        unsigned char *smraw);
 template <typename TS, typename TC>
 __global__ void __launch_bounds__(kTrsmThreads, 1) k_trsm_reg(TS *C, int64_t ldc, int64_t n, int64_t k0, int kb,
                                                               DevStatus *st) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    if constexpr (std::is_same<TC, dfloat>::value) {
+        trsm_df<TS>(C, ldc, n, k0, kb, st, smraw);
+        return;
+    }
     TC *T = reinterpret_cast<TC *>(smraw);
     const int nq = (kb + kTpv - 1) / kTpv, kbq = kTpv * nq, ld = kbq + 1;   // the block rounded up to 16
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -433,6 +466,138 @@ __global__ void __launch_bounds__(kTrsmThreads, 1) k_trsm_reg(TS *C, int64_t ldc
             const int c = g + kTpv * m;
             if (valid && c < kb) C[(c0 + v) * ldc + k0 + c] = st_as<TS>(x[m]);
         }
+    }
+}
+
+// The double-float block solve on packed FP32 pairs: the same substitution
+// and roundings as the kernel above, each thread's eight entries held as four
+// pairs (2p, 2p + 1) of hi and lo parts, every update of a pair one packed
+// double-float multiply-subtract (half the FP32 instructions).  The block's
+// operand of entry c = g + 16 m at step k (L11[c][k] for the block row,
+// U11[k][c] for the block column) sits at [k][m / 2][g][m % 2] of a hi and a
+// lo plane, so a thread reads a pair with one 8-byte load and a half-warp's
+// loads are contiguous; past the block the planes hold the identity.
+template <typename TS>
+__device__ __forceinline__ void trsm_df(TS *C, int64_t ldc, int64_t n, int64_t k0, int kb, DevStatus *st,
+                                        unsigned char *smraw) {
+    const int nq = (kb + kTpv - 1) / kTpv, kbq = kTpv * nq, np = (nq + 1) / 2, span = 2 * kTpv * np;
+    float2 *Ph = reinterpret_cast<float2 *>(smraw);
+    float2 *Pl = Ph + (size_t)kbq * np * kTpv;
+    dfloat *rd = reinterpret_cast<dfloat *>(Pl + (size_t)kbq * np * kTpv);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int v = tid / kTpv, g = tid % kTpv;
+    const int64_t c0 = k0 + kb + (int64_t)blockIdx.x * kTrsmW;
+    const int w = (int)min((int64_t)kTrsmW, n - c0);
+    if (w <= 0) return;
+    const bool role_u = blockIdx.y == 0;
+    for (int idx = tid; idx < kbq * span; idx += kTrsmThreads) {
+        // the global reads run along a row of C: k fastest for the block row's
+        // operand (a column of L11), c fastest for the block column's (a row of U11)
+        const int k = role_u ? idx % kbq : idx / span, c = role_u ? idx / kbq : idx % span;
+        const int r = role_u ? c : k, cc = role_u ? k : c;
+        const dfloat t = (r < kb && cc < kb) ? ld_as<dfloat>(C[(k0 + r) * ldc + k0 + cc])
+                                             : dfloat(r == cc ? 1.0f : 0.0f);
+        const int m = c / kTpv, gg = c % kTpv;
+        const size_t at = ((size_t)k * np + (m >> 1)) * kTpv + gg;
+        reinterpret_cast<float *>(Ph + at)[m & 1] = t.hi;
+        reinterpret_cast<float *>(Pl + at)[m & 1] = t.lo;
+    }
+    if (!role_u && tid < kbq) {
+        const dfloat ujj = tid < kb ? ld_as<dfloat>(C[(k0 + tid) * ldc + k0 + tid]) : dfloat(1.0f);
+        rd[tid] = dfloat(1.0) / ujj;
+    }
+    __syncthreads();
+    const bool valid = v < w;
+    const int base = lane & ~(kTpv - 1);
+    float2 xh[kEpt / 2], xl[kEpt / 2];
+#pragma unroll
+    for (int p = 0; p < kEpt / 2; ++p) {
+        dfloat a[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = g + kTpv * (2 * p + h);
+            a[h] = (valid && e < kb) ? ld_as<dfloat>(role_u ? C[(k0 + e) * ldc + c0 + v] : C[(c0 + v) * ldc + k0 + e])
+                                     : dfloat(0.0f);
+        }
+        xh[p] = make_float2(a[0].hi, a[1].hi);
+        xl[p] = make_float2(a[0].lo, a[1].lo);
+    }
+#pragma unroll
+    for (int b = 0; b < kEpt; ++b) {
+        if (b >= nq) break;
+        const int pb = b >> 1;
+#pragma unroll 1
+        for (int kk = 0; kk < kTpv; ++kk) {
+            const int k = kTpv * b + kk;
+            if (!role_u && g == kk) {
+                // l_vk = x_vk / u_kk by the reciprocal pivot
+                dfloat xb((b & 1) ? xh[pb].y : xh[pb].x);
+                xb.lo = (b & 1) ? xl[pb].y : xl[pb].x;
+                xb = xb * rd[k];
+                if (b & 1) {
+                    xh[pb].y = xb.hi;
+                    xl[pb].y = xb.lo;
+                } else {
+                    xh[pb].x = xb.hi;
+                    xl[pb].x = xb.lo;
+                }
+            }
+            // entry k, final
+            const float kh = __shfl_sync(0xffffffffu, (b & 1) ? xh[pb].y : xh[pb].x, base | kk);
+            const float kl = __shfl_sync(0xffffffffu, (b & 1) ? xl[pb].y : xl[pb].x, base | kk);
+            const float2 bh = make_float2(kh, kh), bl = make_float2(kl, kl);
+            const float2 *ph = Ph + (size_t)k * np * kTpv + g, *pl = Pl + (size_t)k * np * kTpv + g;
+            // block row: x -= L11[.][k] x_k (l varies, u = x_k); block column:
+            // x -= x_k U11[k][.] (l = x_k, u varies)
+            auto upd = [&](float2 &h, float2 &l, int p) {
+                const float2 th = ph[p * kTpv], tl = pl[p * kTpv];
+                if (role_u) fms2(h, l, th, tl, bh, bl, __fmul2_rn(th, make_float2(-kh, -kh)));
+                else fms2(h, l, bh, bl, th, tl, __fmul2_rn(make_float2(-kh, -kh), th));
+            };
+            {
+                // the pair of entry b: b itself below the step's row only
+                float2 h = xh[pb], l = xl[pb];
+                upd(h, l, pb);
+                const bool below = g > kk;
+                if (b & 1) {
+                    xh[pb].y = below ? h.y : xh[pb].y;
+                    xl[pb].y = below ? l.y : xl[pb].y;
+                } else {
+                    xh[pb].x = below ? h.x : xh[pb].x;
+                    xl[pb].x = below ? l.x : xl[pb].x;
+                    xh[pb].y = h.y;
+                    xl[pb].y = l.y;
+                }
+            }
+#pragma unroll
+            for (int p = pb + 1; p < kEpt / 2; ++p)
+                if (p < np) upd(xh[p], xl[p], p);   // (uniform) past kb: padding
+        }
+    }
+    float xmax = 0.0f;
+#pragma unroll
+    for (int p = 0; p < kEpt / 2; ++p)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = g + kTpv * (2 * p + h);
+            if (valid && e < kb) {
+                dfloat a(h ? xh[p].y : xh[p].x);
+                a.lo = h ? xl[p].y : xl[p].x;
+                if (role_u) {
+                    C[(k0 + e) * ldc + c0 + v] = st_as<TS>(a);
+                    const float av = mag(a);
+                    xmax = (av > xmax || isnan(av)) ? av : xmax;
+                } else {
+                    C[(c0 + v) * ldc + k0 + e] = st_as<TS>(a);
+                }
+            }
+        }
+    if (role_u) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const float q = __shfl_xor_sync(0xffffffffu, xmax, o);
+            xmax = (q > xmax || isnan(q)) ? q : xmax;
+        }
+        if (lane == 0) atomic_max_nonneg(&st->max_abs_u, (double)xmax);
     }
 }
 

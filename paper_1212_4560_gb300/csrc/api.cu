@@ -10,13 +10,21 @@
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
 #include <new>
+#include <vector>
 
 using namespace genp;
 
 namespace {
 
 std::atomic<uint64_t> g_launches{0};
+// kernels of the conditional bodies that recorded refinement graphs ran: the
+// IF nodes' condition kernels add them up in pinned host memory (one thread
+// each, ordered by the graph), so the count needs no copy or synchronization
+unsigned long long *g_body_launches = nullptr;       // host view
+unsigned long long *g_body_launches_dev = nullptr;   // device view
+std::mutex g_body_launches_mu;
 
 cudaStream_t S(void *p) { return static_cast<cudaStream_t>(p); }
 
@@ -192,6 +200,91 @@ cudaError_t apply_multiplier(const genp_multiplier *G, bool trans, const double 
 
 }  // namespace genp
 
+namespace genp {
+
+// The recording state of a refinement graph's conditional bodies (nesting:
+// the graph, a residual check or correction, a Krylov step).
+struct CondRec {
+    static constexpr int kMaxBodies = (GENP_MAX_REFINE + 1) * (GENP_GMRES_RESTART + 2);
+    cudaStream_t chain[3] = {};          // the graph's stream, then the nested bodies'
+    int depth = 0;
+    int idx[3] = {};
+    uint64_t start[3] = {}, nested[3] = {};   // launch count at a body's start, its nested bodies' kernels
+    std::vector<int> counts;             // kernels of each body, not counting the bodies nested in it
+    int *dev_counts = nullptr;           // their device copy, read by the condition kernels
+};
+
+namespace {
+// Sets the condition of the IF node that follows: run the body while *done
+// is 0, and count its kernels.
+__global__ void k_cond_set(cudaGraphConditionalHandle h, const int *done, const int *counts, int idx,
+                           unsigned long long *launched) {
+    const bool go = *done == 0;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+    if (go) {
+        volatile unsigned long long *p = launched;
+        *p = *p + (unsigned long long)counts[idx];
+    }
+}
+}  // namespace
+
+cudaError_t cond_begin(CondRec *c, cudaStream_t &s, const int *done) {
+    if (!c) return cudaSuccess;
+    if (c->depth >= 2 || (int)c->counts.size() >= CondRec::kMaxBodies) return cudaErrorInvalidValue;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusActive || !g) return cudaErrorStreamCaptureInvalidated;
+    cudaGraphConditionalHandle h;
+    e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return e;
+    const int idx = (int)c->counts.size();
+    c->counts.push_back(0);
+    note_launch();
+    k_cond_set<<<1, 1, 0, s>>>(h, done, c->dev_counts, idx, g_body_launches_dev);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddNode(&node, g, deps, nullptr, nd, &p);
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) return e;
+    cudaStream_t child = c->chain[c->depth + 1];
+    e = cudaStreamBeginCaptureToGraph(child, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    ++c->depth;
+    c->idx[c->depth] = idx;
+    c->start[c->depth] = g_launches.load(std::memory_order_relaxed);
+    c->nested[c->depth] = 0;
+    s = child;
+    return cudaSuccess;
+}
+
+cudaError_t cond_end(CondRec *c, cudaStream_t &s) {
+    if (!c) return cudaSuccess;
+    const int d = c->depth;
+    if (d <= 0 || s != c->chain[d]) return cudaErrorInvalidValue;
+    cudaGraph_t body = nullptr;   // owned by its IF node
+    const cudaError_t e = cudaStreamEndCapture(s, &body);
+    const uint64_t total = g_launches.load(std::memory_order_relaxed) - c->start[d];
+    c->counts[c->idx[d]] = (int)(total - c->nested[d]);
+    c->nested[d - 1] += total;
+    c->depth = d - 1;
+    s = c->chain[d - 1];
+    return e;
+}
+
+}  // namespace genp
+
 extern "C" {
 
 const char *genp_version(void) { return "genp 0.1 sm_103a"; }
@@ -306,7 +399,10 @@ genp_status genp_redraw_multiplier(genp_multiplier *G, uint64_t seed, uint64_t s
     return GENP_OK;
 }
 
-uint64_t genp_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+uint64_t genp_launch_count(void) {
+    const volatile unsigned long long *b = g_body_launches;
+    return g_launches.load(std::memory_order_relaxed) + (b ? *b : 0ull);
+}
 
 genp_status genp_gemm_bf16(int64_t m, int64_t n, int64_t K, float alpha, const void *A, int64_t lda, const void *Bt,
                            int64_t ldb, float beta, const float *Cin, int64_t ldci, float *D, int64_t ldd,
@@ -813,9 +909,13 @@ void genp_factors_destroy(genp_factors *F) {
     bool any = F->rg_stream != nullptr || F->la_stream != nullptr;
     for (auto &g : F->rgraph) any = any || g.exec;
     if (any) cudaDeviceSynchronize();   // graphs and their streams may still be in use
-    for (auto &g : F->rgraph)
+    for (auto &g : F->rgraph) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
+        cudaFree(g.body_counts);
+    }
     if (F->rg_stream) cudaStreamDestroy(F->rg_stream);
+    for (auto &b : F->rg_body)
+        if (b) cudaStreamDestroy(b);
     if (F->la_stream) cudaStreamDestroy(F->la_stream);
     for (auto &ev : F->la_ev)
         if (ev) cudaEventDestroy(ev);
@@ -870,11 +970,11 @@ bool g_refine_graphs = true;
 // The launch sequence of genp_refine (workspace already in place).
 genp_status refine_enqueue(const double *A, int64_t lda, genp_factors *Fm, const genp_multiplier *G,
                            const double *B, int64_t ldb, int64_t nrhs, double *X, int64_t ldx, double tol,
-                           int max_iter, int method, cudaStream_t s) {
+                           int max_iter, int method, cudaStream_t s, CondRec *cr = nullptr) {
     const genp_factors *F = Fm;
     const int64_t n = F->n;
     if (method == 1) {
-        CU(refine_gmres(Fm, G, A, lda, B, ldb, nrhs, X, ldx, tol, max_iter, F->work, s));
+        CU(refine_gmres(Fm, G, A, lda, B, ldb, nrhs, X, ldx, tol, max_iter, F->work, s, cr));
         return GENP_OK;
     }
     const size_t rd = align256((size_t)n * nrhs * sizeof(double));
@@ -885,9 +985,14 @@ genp_status refine_enqueue(const double *A, int64_t lda, genp_factors *Fm, const
     const bool left = G->side == GENP_SIDE_LEFT;
     CU(refine_init(Fm, A, lda, n, s));
     for (int it = 0; it <= max_iter; ++it) {
+        // the residual and its check, then the correction: each skipped once
+        // the refinement has converged
+        if (it > 0) CU(cond_begin(cr, s, done));
         CU(gemm<double>(n, nrhs, n, -1.0, A, lda, false, X, ldx, 1.0, B, ldb, R, nrhs, done, s));
         CU(refine_check(Fm, R, nrhs, X, ldx, B, ldb, n, nrhs, it, tol, max_iter, 1, s));
+        if (it > 0) CU(cond_end(cr, s));
         if (it == max_iter) break;
+        CU(cond_begin(cr, s, done));
         double *D = R;
         if (left) {   // d = U^-1 L^-1 (G r)
             CU(apply_multiplier(G, false, R, nrhs, T, nrhs, nrhs, false, done, s));
@@ -902,6 +1007,7 @@ genp_status refine_enqueue(const double *A, int64_t lda, genp_factors *Fm, const
         }
         if (left) CU(add_into(D, nrhs, X, ldx, n, nrhs, done, s));
         else CU(apply_multiplier(G, false, R, nrhs, X, ldx, nrhs, true, done, s));
+        CU(cond_end(cr, s));
     }
     return GENP_OK;
 }
@@ -911,29 +1017,68 @@ genp_status refine_enqueue(const double *A, int64_t lda, genp_factors *Fm, const
 // holds in *launches.
 genp_status refine_record(const double *A, int64_t lda, genp_factors *F, const genp_multiplier *G, const double *B,
                           int64_t ldb, int64_t nrhs, double *X, int64_t ldx, double tol, int max_iter, int method,
-                          cudaGraphExec_t *exec, uint64_t *launches) {
+                          cudaGraphExec_t *exec, uint64_t *launches, int **body_counts) {
     if (!F->rg_stream && cudaStreamCreateWithFlags(&F->rg_stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         F->rg_stream = nullptr;
         return GENP_ERR_CUDA;
     }
+    for (auto &b : F->rg_body)
+        if (!b && cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            b = nullptr;
+            return GENP_ERR_CUDA;
+        }
+    {
+        std::lock_guard<std::mutex> lk(g_body_launches_mu);
+        if (!g_body_launches) {
+            void *h = nullptr, *d = nullptr;
+            if (cudaHostAlloc(&h, sizeof(unsigned long long), cudaHostAllocMapped) != cudaSuccess ||
+                cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+                if (h) cudaFreeHost(h);
+                cudaGetLastError();
+                return GENP_ERR_CUDA;
+            }
+            *static_cast<unsigned long long *>(h) = 0;
+            g_body_launches_dev = static_cast<unsigned long long *>(d);
+            g_body_launches = static_cast<unsigned long long *>(h);
+        }
+    }
+    if (!*body_counts) TRY(dalloc(body_counts, CondRec::kMaxBodies));
+    CondRec cr;
+    cr.chain[0] = F->rg_stream;
+    cr.chain[1] = F->rg_body[0];
+    cr.chain[2] = F->rg_body[1];
+    cr.dev_counts = *body_counts;
     cudaStream_t rs = F->rg_stream;
     if (cudaStreamBeginCapture(rs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         return GENP_ERR_CUDA;
     }
-    const uint64_t l0 = genp_launch_count();
+    const uint64_t l0 = g_launches.load(std::memory_order_relaxed);
     profile_suspend(true);
-    const genp_status st = refine_enqueue(A, lda, F, G, B, ldb, nrhs, X, ldx, tol, max_iter, method, rs);
+    genp_status st = refine_enqueue(A, lda, F, G, B, ldb, nrhs, X, ldx, tol, max_iter, method, rs, &cr);
     profile_suspend(false);
-    *launches = genp_launch_count() - l0;
-    g_launches.fetch_sub(*launches, std::memory_order_relaxed);   // counted when the graph runs
+    while (cr.depth > 0) {   // a body left open by an error
+        cudaGraph_t body = nullptr;
+        cudaStreamEndCapture(cr.chain[cr.depth--], &body);
+        if (st == GENP_OK) st = GENP_ERR_CUDA;
+    }
+    const uint64_t total = g_launches.load(std::memory_order_relaxed) - l0;
+    *launches = total - cr.nested[0];
+    g_launches.fetch_sub(total, std::memory_order_relaxed);   // counted when the graph runs
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(rs, &graph);
     if (st != GENP_OK || ec != cudaSuccess || !graph) {
         if (graph) cudaGraphDestroy(graph);
         cudaGetLastError();
         return st != GENP_OK ? st : GENP_ERR_CUDA;
+    }
+    if (!cr.counts.empty() && cudaMemcpy(*body_counts, cr.counts.data(), cr.counts.size() * sizeof(int),
+                                         cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return GENP_ERR_CUDA;
     }
     const cudaError_t ei = cudaGraphInstantiate(exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -1004,7 +1149,8 @@ genp_status genp_refine(const double *A, int64_t lda, const genp_factors *F, con
         }
         // the recording stream must see the caller's stream state (buffers
         // written by earlier calls): recording enqueues nothing, so no wait
-        TRY(refine_record(A, lda, Fm, G, B, ldb, nrhs, X, ldx, tol, max_iter, method, &slot.exec, &slot.launches));
+        TRY(refine_record(A, lda, Fm, G, B, ldb, nrhs, X, ldx, tol, max_iter, method, &slot.exec, &slot.launches,
+                          &slot.body_counts));
         memcpy(slot.key, key, sizeof(key));
         hit = &slot;
     }

@@ -84,13 +84,15 @@ struct genp_multiplier {
 struct GenpRefineGraph {
     uint64_t key[16] = {};
     cudaGraphExec_t exec = nullptr;
-    uint64_t launches = 0;             // kernels the graph holds (for genp_launch_count)
+    uint64_t launches = 0;             // kernels the graph always runs (for genp_launch_count)
+    int *body_counts = nullptr;        // device: kernels in each of its conditional bodies
 };
 
 struct genp_factors {
     GenpRefineGraph rgraph[4];         // cached refinement graphs, round robin
     int rg_next = 0;
     cudaStream_t rg_stream = nullptr;  // private stream the graphs are recorded on
+    cudaStream_t rg_body[2] = {nullptr, nullptr};   // streams their nested conditional bodies are recorded on
     cudaStream_t la_stream = nullptr;  // the sliced factorization's look-ahead stream
     cudaEvent_t la_ev[2] = {nullptr, nullptr};   // update done -> block factored
     void *C = nullptr;
@@ -462,11 +464,23 @@ cudaError_t maxabs_f64(const double *C, int64_t n, int64_t ldc, unsigned long lo
 cudaError_t outer_update(const double *Lam, int64_t ldl, const double *X, int64_t ldx, int64_t n,
                          int64_t nrhs, void *dA, int64_t ldda, bool dA_f32, cudaStream_t s);
 
+// Conditional bodies of a recorded refinement graph.  A step that a
+// converged refinement no longer needs (a residual check, a correction, a
+// Krylov step) is recorded as the body of an IF node, whose condition a
+// one-thread kernel sets from the step's done flag just before it, so the
+// replayed graph skips it instead of launching kernels that return at once.
+// cond_begin opens a body (s then names the stream it is recorded on) and
+// cond_end closes it; both do nothing when c is null (launches enqueued as
+// they are).  api.cu.
+struct CondRec;
+cudaError_t cond_begin(CondRec *c, cudaStream_t &s, const int *done);
+cudaError_t cond_end(CondRec *c, cudaStream_t &s);
+
 // gmres.cu: GMRES-IR (genp_refine method 1); work holds gmres_work_bytes(n, nrhs)
 size_t gmres_work_bytes(int64_t n, int64_t nrhs);
 cudaError_t refine_gmres(genp_factors *F, const genp_multiplier *G, const double *A, int64_t lda, const double *B,
                          int64_t ldb, int64_t nrhs, double *X, int64_t ldx, double tol, int max_iter, void *work,
-                         cudaStream_t s);
+                         cudaStream_t s, CondRec *cr = nullptr);
 
 // api.cu helpers
 // X[r][c] += Y[r][c] (n x nr), skipped when *skip != 0

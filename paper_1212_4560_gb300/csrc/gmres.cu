@@ -246,7 +246,7 @@ size_t gmres_work_bytes(int64_t n, int64_t nrhs) {
 
 cudaError_t refine_gmres(genp_factors *F, const genp_multiplier *G, const double *A, int64_t lda, const double *B,
                          int64_t ldb, int64_t nrhs, double *X, int64_t ldx, double tol, int max_iter, void *work,
-                         cudaStream_t s) {
+                         cudaStream_t s, CondRec *cr) {
     const int64_t n = F->n;
     const int nr = (int)nrhs;
     const size_t vec = ((size_t)n * nrhs * sizeof(double) + 255) & ~(size_t)255;
@@ -267,9 +267,16 @@ cudaError_t refine_gmres(genp_factors *F, const genp_multiplier *G, const double
     const bool left = G->side == GENP_SIDE_LEFT;
     cudaError_t e = refine_init(F, A, lda, n, s);
     for (int it = 0; it <= max_iter && e == cudaSuccess; ++it) {
-        e = gemm<double>(n, nrhs, n, -1.0, A, lda, false, X, ldx, 1.0, B, ldb, R, nrhs, outer_done, s);
+        // the residual and its check, then one restarted cycle: each skipped
+        // once the refinement has converged
+        if (it > 0) e = cond_begin(cr, s, outer_done);
+        if (e == cudaSuccess)
+            e = gemm<double>(n, nrhs, n, -1.0, A, lda, false, X, ldx, 1.0, B, ldb, R, nrhs, outer_done, s);
         if (e == cudaSuccess) e = refine_check(F, R, nrhs, X, ldx, B, ldb, n, nrhs, it, tol, max_iter, 1, s);
+        if (e == cudaSuccess && it > 0) e = cond_end(cr, s);
         if (e != cudaSuccess || it == max_iter) break;
+        e = cond_begin(cr, s, outer_done);
+        if (e != cudaSuccess) break;
         note_launch();
         k_gm_begin<<<1, 32, 0, s>>>(st, nr, outer_done);
         // V_0 = M^{-1} r / ||M^{-1} r||  (left multiplier: M^{-1} G r)
@@ -282,6 +289,9 @@ cudaError_t refine_gmres(genp_factors *F, const genp_multiplier *G, const double
         note_launch();
         k_gm_scale<<<vb, 256, 0, s>>>(V, V, n, nr, st, inner);
         for (int k = 0; k < kM && e == cudaSuccess; ++k) {
+            // a Krylov step, skipped once the cycle has converged
+            e = cond_begin(cr, s, inner);
+            if (e != cudaSuccess) break;
             double *Vk = V + (int64_t)k * vstride;
             // W = M^{-1} A (G V_k)  (left multiplier: M^{-1} G (A V_k))
             if (left) {
@@ -306,7 +316,9 @@ cudaError_t refine_gmres(genp_factors *F, const genp_multiplier *G, const double
                 note_launch();
                 k_gm_scale<<<vb, 256, 0, s>>>(W, V + (int64_t)(k + 1) * vstride, n, nr, st, inner);
             }
+            if (e == cudaSuccess) e = cond_end(cr, s);
         }
+        if (e != cudaSuccess) break;
         // d = V y;  x += G d
         note_launch();
         k_gm_finish<<<1, 32, 0, s>>>(st, nr, outer_done);
@@ -316,6 +328,7 @@ cudaError_t refine_gmres(genp_factors *F, const genp_multiplier *G, const double
             e = left ? add_into(T, nrhs, X, ldx, n, nrhs, outer_done, s)
                      : apply_multiplier(G, false, T, nrhs, X, ldx, nrhs, true, outer_done, s);
         if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cond_end(cr, s);
     }
     return e;
 }

@@ -565,7 +565,8 @@ def run_ours(a, emit=True):
                     # once), scaled by the n^2 output tiles to this size's chunk launches
                     "traffic": 282.0e6 * (n / 4096) ** 2 if (nd == 7 and pd == 5) else None,
                     "traffic_basis": "A G chunk launch (K = 1024) of k_tc_sliced<2, 5>; ncu at n = 4096 scaled by "
-                                     "n^2; Schur-update launches (K = 256) move about a quarter of it per tile"}
+                                     "n^2; Schur-update launches (K = 512) read and write the same accumulator "
+                                     "per tile over half the depth"}
     elif a.prec == "fp8" and tc_launches:
         # per launch: the A G product (K = n, k_tc_e4m3, tensor-bound) and the
         # Schur updates (K = nb <= 128, k_tc_gemm<true>, HBM-bound: C read and

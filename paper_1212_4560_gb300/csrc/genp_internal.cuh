@@ -314,6 +314,14 @@ cudaError_t slice_cols_T(int nd, const double *src, int64_t lds, int64_t K, int6
 // inversely, the rows of U) before slicing
 cudaError_t sliced_inner_exps(const double *L, int64_t ldl, int64_t m, int64_t K, unsigned long long *keys,
                               cudaStream_t s);
+// the same three from the double-float trailing matrix (each entry taken
+// exactly as FP64), so a block needs no FP64 copy before it is sliced
+cudaError_t slice_rows(int nd, const dfloat *src, int64_t lds, int64_t m, int64_t K, __nv_bfloat16 *dst, int64_t ldq,
+                       int *exps, cudaStream_t s, const unsigned long long *kkey);
+cudaError_t slice_cols_T(int nd, const dfloat *src, int64_t lds, int64_t K, int64_t n, __nv_bfloat16 *dst,
+                         int64_t ldq, int *exps, cudaStream_t s, const unsigned long long *kkey);
+cudaError_t sliced_inner_exps(const dfloat *L, int64_t ldl, int64_t m, int64_t K, unsigned long long *keys,
+                              cudaStream_t s);
 // double <-> double-float copies of an m x n block
 cudaError_t df_from_f64(const double *src, int64_t lds, dfloat *dst, int64_t ldd, int64_t m, int64_t n,
                         cudaStream_t s);

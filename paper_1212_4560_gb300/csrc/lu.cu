@@ -809,19 +809,18 @@ cudaError_t factor_sliced(genp_factors *F, cudaStream_t s) {
             if (j0 < e0) {
                 // the rest of the outer block column, and its block row beyond it,
                 // by the sliced product too: this inner step's L (rows j0..n) and U
-                // (columns j0..n) are final, so they go to C in FP64 (exactly) and
-                // are sliced once for both updates
+                // (columns j0..n) are final, and are sliced once for both updates
+                // straight from the double-float matrix (each entry exactly as
+                // FP64; their FP64 copy in C is made at the end of the outer step)
                 const int64_t w2 = e0 - j0;
                 const int nb2 = (int)(w2 < nb ? w2 : nb);   // the next inner block
-                double *Lc = C + j0 * ldc + i0;
-                double *Uc = C + i0 * ldc + j0;
+                const dfloat *Lw = W + j0 * ldw + i0;
+                const dfloat *Uw = W + i0 * ldw + j0;
                 unsigned long long *kk = reinterpret_cast<unsigned long long *>(F->exps + 2 * n);
                 const int64_t kp = sliced_kpad(kb);
-                e = df_to_f64(W + j0 * ldw + i0, ldw, Lc, ldc, rem, kb, s);
-                if (e == cudaSuccess) e = df_to_f64(W + i0 * ldw + j0, ldw, Uc, ldc, kb, rem, s);
-                if (e == cudaSuccess) e = sliced_inner_exps(Lc, ldc, rem, kb, kk, s);
-                if (e == cudaSuccess) e = slice_rows(F->nd, Lc, ldc, rem, kb, F->tcA, ldq, F->exps, s, kk);
-                if (e == cudaSuccess) e = slice_cols_T(F->nd, Uc, ldc, kb, rem, F->tcB, ldq, F->exps + n, s, kk);
+                e = sliced_inner_exps(Lw, ldw, rem, kb, kk, s);
+                if (e == cudaSuccess) e = slice_rows(F->nd, Lw, ldw, rem, kb, F->tcA, ldq, F->exps, s, kk);
+                if (e == cudaSuccess) e = slice_cols_T(F->nd, Uw, ldw, kb, rem, F->tcB, ldq, F->exps + n, s, kk);
                 if (ahead) {
                     if (e == cudaSuccess) e = update(rem, nb2, kp, 0, W + j0 * ldw + j0);
                     if (e == cudaSuccess) e = block_ahead(j0, nb2);

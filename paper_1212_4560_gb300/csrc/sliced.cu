@@ -21,6 +21,11 @@ namespace {
 int g_default_digits = 7;
 int g_precond_digits = 7;
 
+// An operand entry in FP64: the double-float trailing matrix of the sliced
+// factorization converts exactly (48 significant bits).
+__device__ __forceinline__ double as_f64(double x) { return x; }
+__device__ __forceinline__ double as_f64(dfloat v) { return (double)v.hi + (double)v.lo; }
+
 // |x| as its IEEE bit pattern, NaN mapped to 0: the integer maximum of these
 // is the bit pattern of max|x| (no FP64 min/max on the scarce FP64 units)
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
@@ -104,26 +109,26 @@ __device__ __forceinline__ void put(__nv_bfloat16 *row, int64_t kpad, int64_t k,
     for (int t = 0; t < ND; ++t) row[t * kpad + k] = __float2bfloat16_rn(d[t]);
 }
 
-// A operand: rows of src (m x K, FP64, ld lds).  One warp per row.  With
-// kexp, entry k of every row is taken as x 2^-kexp[k] (an exact power-of-two
-// scaling of the inner dimension that the B operand undoes; see
-// slice_cols_T).
-template <int ND>
-__global__ void k_slice_rows(const double *src, int64_t lds, int64_t m, int64_t K, int64_t kpad,
+// A operand: rows of src (m x K, FP64 or double-float, ld lds).  One warp
+// per row.  With kexp, entry k of every row is taken as x 2^-kexp[k] (an
+// exact power-of-two scaling of the inner dimension that the B operand
+// undoes; see slice_cols_T).
+template <int ND, typename TS>
+__global__ void k_slice_rows(const TS *src, int64_t lds, int64_t m, int64_t K, int64_t kpad,
                              __nv_bfloat16 *dst, int64_t ldq, int *exps, const unsigned long long *kkey) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp; i < m; i += nw) {
-        const double *a = src + i * lds;
+        const TS *a = src + i * lds;
         int e;
         unsigned long long mb = 0ull;
         if (kkey) {
-            for (int64_t k = lane; k < K; k += 32) mb = max(mb, scaled_key(a[k], -key_exp(kkey[k])));
+            for (int64_t k = lane; k < K; k += 32) mb = max(mb, scaled_key(as_f64(a[k]), -key_exp(kkey[k])));
             for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
             e = key_exp(mb);
         } else {
-            for (int64_t k = lane; k < K; k += 32) mb = max(mb, abs_bits(a[k]));
+            for (int64_t k = lane; k < K; k += 32) mb = max(mb, abs_bits(as_f64(a[k])));
             for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
             e = scale_exp(__longlong_as_double((long long)mb));
         }
@@ -131,7 +136,7 @@ __global__ void k_slice_rows(const double *src, int64_t lds, int64_t m, int64_t 
         __nv_bfloat16 *row = dst + i * ldq;
         for (int64_t k = lane; k < kpad; k += 32) {
             float d[ND] = {};
-            if (k < K) digits<ND>(a[k], e, d, kkey ? -key_exp(kkey[k]) : 0);
+            if (k < K) digits<ND>(as_f64(a[k]), e, d, kkey ? -key_exp(kkey[k]) : 0);
             put<ND>(row, kpad, k, d);
         }
     }
@@ -142,7 +147,8 @@ __global__ void k_slice_rows(const double *src, int64_t lds, int64_t m, int64_t 
 // columns, its 8 warps split the rows (coalesced 256-byte rows per warp),
 // and the 8 partial maxima meet in shared memory.
 // With kkey, row k of src is taken as x 2^+q_k, q_k = key_exp(kkey[k]).
-__global__ void k_col_exps(const double *src, int64_t lds, int64_t K, int64_t n, int *exps,
+template <typename TS>
+__global__ void k_col_exps(const TS *src, int64_t lds, int64_t K, int64_t n, int *exps,
                            const unsigned long long *kkey) {
     __shared__ unsigned long long part[8][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -150,9 +156,9 @@ __global__ void k_col_exps(const double *src, int64_t lds, int64_t K, int64_t n,
     unsigned long long mb = 0ull;
     if (j < n) {
         if (kkey)
-            for (int64_t k = ty; k < K; k += 8) mb = max(mb, scaled_key(src[k * lds + j], key_exp(kkey[k])));
+            for (int64_t k = ty; k < K; k += 8) mb = max(mb, scaled_key(as_f64(src[k * lds + j]), key_exp(kkey[k])));
         else
-            for (int64_t k = ty; k < K; k += 8) mb = max(mb, abs_bits(src[k * lds + j]));
+            for (int64_t k = ty; k < K; k += 8) mb = max(mb, abs_bits(as_f64(src[k * lds + j])));
     }
     part[ty][tx] = mb;
     __syncthreads();
@@ -166,7 +172,8 @@ __global__ void k_col_exps(const double *src, int64_t lds, int64_t K, int64_t n,
 // sliced Schur update): a CTA takes 32 columns and a strip of rows, its 8
 // warps split the strip, and the strip's maximum goes to keys[k] by atomicMax
 // (keys cleared before).
-__global__ void k_col_keys(const double *src, int64_t lds, int64_t m, int64_t K, unsigned long long *keys) {
+template <typename TS>
+__global__ void k_col_keys(const TS *src, int64_t lds, int64_t m, int64_t K, unsigned long long *keys) {
     __shared__ unsigned long long part[8][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int64_t k = (int64_t)blockIdx.x * 32 + tx;
@@ -174,7 +181,7 @@ __global__ void k_col_keys(const double *src, int64_t lds, int64_t m, int64_t K,
     const int64_t r0 = (int64_t)blockIdx.y * rows, r1 = r0 + rows < m ? r0 + rows : m;
     unsigned long long mb = 0ull;
     if (k < K)
-        for (int64_t i = r0 + ty; i < r1; i += 8) mb = max(mb, scaled_key(src[i * lds + k], 0));
+        for (int64_t i = r0 + ty; i < r1; i += 8) mb = max(mb, scaled_key(as_f64(src[i * lds + k]), 0));
     part[ty][tx] = mb;
     __syncthreads();
     if (ty == 0 && k < K) {
@@ -184,15 +191,15 @@ __global__ void k_col_keys(const double *src, int64_t lds, int64_t m, int64_t K,
 }
 
 // Pass 2: 32 x 32 tiles through shared memory so both sides stay coalesced.
-template <int ND>
-__global__ void k_slice_cols_T(const double *src, int64_t lds, int64_t K, int64_t n, int64_t kpad,
+template <int ND, typename TS>
+__global__ void k_slice_cols_T(const TS *src, int64_t lds, int64_t K, int64_t n, int64_t kpad,
                                __nv_bfloat16 *dst, int64_t ldq, const int *exps, const unsigned long long *kkey) {
     __shared__ double tile[32][33];
     const int64_t k0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
     for (int r = ty; r < 32; r += 8) {
         const int64_t k = k0 + r, j = j0 + tx;
-        tile[r][tx] = (k < K && j < n) ? src[k * lds + j] : 0.0;
+        tile[r][tx] = (k < K && j < n) ? as_f64(src[k * lds + j]) : 0.0;
     }
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
@@ -201,6 +208,45 @@ __global__ void k_slice_cols_T(const double *src, int64_t lds, int64_t K, int64_
             float d[ND] = {};
             if (k < K) digits<ND>(tile[tx][r], exps[j], d, kkey ? key_exp(kkey[k]) : 0);
             put<ND>(dst + j * ldq, kpad, k, d);
+        }
+    }
+}
+
+// Both passes in one for a shallow operand (K <= 128, the inner blocks of
+// the sliced factorization): a CTA holds its 32 columns whole in shared
+// memory, takes their exponents, and slices them.
+constexpr int kColsSmallK = 128;
+template <int ND, typename TS>
+__global__ void k_slice_cols_T_small(const TS *src, int64_t lds, int64_t K, int64_t n, int64_t kpad,
+                                     __nv_bfloat16 *dst, int64_t ldq, int *exps, const unsigned long long *kkey) {
+    __shared__ double tile[kColsSmallK][33];
+    __shared__ unsigned long long part[8][33];
+    __shared__ int ej[32];
+    const int64_t j0 = (int64_t)blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    const int64_t j = j0 + tx;
+    unsigned long long mb = 0ull;
+    for (int k = ty; k < (int)K; k += 8) {
+        const double x = j < n ? as_f64(src[k * lds + j]) : 0.0;
+        tile[k][tx] = x;
+        mb = max(mb, kkey ? scaled_key(x, key_exp(kkey[k])) : abs_bits(x));
+    }
+    part[ty][tx] = mb;
+    __syncthreads();
+    if (ty == 0) {
+        for (int w = 1; w < 8; ++w) mb = max(mb, part[w][tx]);
+        const int e = kkey ? key_exp(mb) : scale_exp(__longlong_as_double((long long)mb));
+        ej[tx] = e;
+        if (j < n) exps[j] = e;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t jr = j0 + r;
+        if (jr >= n) break;
+        for (int k = tx; k < (int)kpad; k += 32) {
+            float d[ND] = {};
+            if (k < K) digits<ND>(tile[k][r], ej[r], d, kkey ? key_exp(kkey[k]) : 0);
+            put<ND>(dst + jr * ldq, kpad, k, d);
         }
     }
 }
@@ -268,8 +314,10 @@ int set_sliced_precond_digits(int nd) {
     return old;
 }
 
-cudaError_t slice_rows(int nd, const double *src, int64_t lds, int64_t m, int64_t K, __nv_bfloat16 *dst, int64_t ldq,
-                       int *exps, cudaStream_t s, const unsigned long long *kexp) {
+namespace {
+template <typename TS>
+cudaError_t slice_rows_t(int nd, const TS *src, int64_t lds, int64_t m, int64_t K, __nv_bfloat16 *dst, int64_t ldq,
+                         int *exps, cudaStream_t s, const unsigned long long *kexp) {
     if (m <= 0) return cudaSuccess;
     if (nd < 2 || nd > 7 || ldq < nd * sliced_kpad(K)) return cudaErrorInvalidValue;
     int blocks = (int)((m + 7) / 8);
@@ -277,39 +325,54 @@ cudaError_t slice_rows(int nd, const double *src, int64_t lds, int64_t m, int64_
     const int64_t kpad = sliced_kpad(K);
     note_launch();
     switch (nd) {
-        case 2: k_slice_rows<2><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
-        case 3: k_slice_rows<3><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
-        case 4: k_slice_rows<4><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
-        case 5: k_slice_rows<5><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
-        case 6: k_slice_rows<6><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
-        default: k_slice_rows<7><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
+        case 2: k_slice_rows<2, TS><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
+        case 3: k_slice_rows<3, TS><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
+        case 4: k_slice_rows<4, TS><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
+        case 5: k_slice_rows<5, TS><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
+        case 6: k_slice_rows<6, TS><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
+        default: k_slice_rows<7, TS><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
     }
     return cudaGetLastError();
 }
 
-cudaError_t slice_cols_T(int nd, const double *src, int64_t lds, int64_t K, int64_t n, __nv_bfloat16 *dst,
-                         int64_t ldq, int *exps, cudaStream_t s, const unsigned long long *kexp) {
+template <typename TS>
+cudaError_t slice_cols_T_t(int nd, const TS *src, int64_t lds, int64_t K, int64_t n, __nv_bfloat16 *dst,
+                           int64_t ldq, int *exps, cudaStream_t s, const unsigned long long *kexp) {
     if (n <= 0) return cudaSuccess;
     const int64_t kpad = sliced_kpad(K);
     if (nd < 2 || nd > 7 || ldq < nd * kpad) return cudaErrorInvalidValue;
+    if (kpad <= kColsSmallK) {
+        const unsigned gx = (unsigned)cdiv(n, 32);
+        note_launch();
+        switch (nd) {
+            case 2: k_slice_cols_T_small<2, TS><<<gx, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
+            case 3: k_slice_cols_T_small<3, TS><<<gx, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
+            case 4: k_slice_cols_T_small<4, TS><<<gx, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
+            case 5: k_slice_cols_T_small<5, TS><<<gx, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
+            case 6: k_slice_cols_T_small<6, TS><<<gx, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
+            default: k_slice_cols_T_small<7, TS><<<gx, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
+        }
+        return cudaGetLastError();
+    }
     note_launch();
-    k_col_exps<<<(unsigned)cdiv(n, 32), 256, 0, s>>>(src, lds, K, n, exps, kexp);
+    k_col_exps<TS><<<(unsigned)cdiv(n, 32), 256, 0, s>>>(src, lds, K, n, exps, kexp);
     dim3 g((unsigned)cdiv(n, 32), (unsigned)cdiv(kpad, 32));
     if (g.y > 65535u) return cudaErrorInvalidValue;
     note_launch();
     switch (nd) {
-        case 2: k_slice_cols_T<2><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
-        case 3: k_slice_cols_T<3><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
-        case 4: k_slice_cols_T<4><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
-        case 5: k_slice_cols_T<5><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
-        case 6: k_slice_cols_T<6><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
-        default: k_slice_cols_T<7><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
+        case 2: k_slice_cols_T<2, TS><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
+        case 3: k_slice_cols_T<3, TS><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
+        case 4: k_slice_cols_T<4, TS><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
+        case 5: k_slice_cols_T<5, TS><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
+        case 6: k_slice_cols_T<6, TS><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
+        default: k_slice_cols_T<7, TS><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
     }
     return cudaGetLastError();
 }
 
-cudaError_t sliced_inner_exps(const double *L, int64_t ldl, int64_t m, int64_t K, unsigned long long *keys,
-                              cudaStream_t s) {
+template <typename TS>
+cudaError_t sliced_inner_exps_t(const TS *L, int64_t ldl, int64_t m, int64_t K, unsigned long long *keys,
+                                cudaStream_t s) {
     if (K <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(keys, 0, (size_t)K * sizeof(unsigned long long), s);
     if (e != cudaSuccess || m <= 0) return e;
@@ -318,8 +381,34 @@ cudaError_t sliced_inner_exps(const double *L, int64_t ldl, int64_t m, int64_t K
     int64_t gy = (152 * 2 + gx - 1) / gx;
     gy = gy < cdiv(m, 64) ? gy : cdiv(m, 64);
     note_launch();
-    k_col_keys<<<dim3((unsigned)gx, (unsigned)(gy > 0 ? gy : 1)), 256, 0, s>>>(L, ldl, m, K, keys);
+    k_col_keys<TS><<<dim3((unsigned)gx, (unsigned)(gy > 0 ? gy : 1)), 256, 0, s>>>(L, ldl, m, K, keys);
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t slice_rows(int nd, const double *src, int64_t lds, int64_t m, int64_t K, __nv_bfloat16 *dst, int64_t ldq,
+                       int *exps, cudaStream_t s, const unsigned long long *kexp) {
+    return slice_rows_t(nd, src, lds, m, K, dst, ldq, exps, s, kexp);
+}
+cudaError_t slice_rows(int nd, const dfloat *src, int64_t lds, int64_t m, int64_t K, __nv_bfloat16 *dst, int64_t ldq,
+                       int *exps, cudaStream_t s, const unsigned long long *kexp) {
+    return slice_rows_t(nd, src, lds, m, K, dst, ldq, exps, s, kexp);
+}
+cudaError_t slice_cols_T(int nd, const double *src, int64_t lds, int64_t K, int64_t n, __nv_bfloat16 *dst,
+                         int64_t ldq, int *exps, cudaStream_t s, const unsigned long long *kexp) {
+    return slice_cols_T_t(nd, src, lds, K, n, dst, ldq, exps, s, kexp);
+}
+cudaError_t slice_cols_T(int nd, const dfloat *src, int64_t lds, int64_t K, int64_t n, __nv_bfloat16 *dst,
+                         int64_t ldq, int *exps, cudaStream_t s, const unsigned long long *kexp) {
+    return slice_cols_T_t(nd, src, lds, K, n, dst, ldq, exps, s, kexp);
+}
+cudaError_t sliced_inner_exps(const double *L, int64_t ldl, int64_t m, int64_t K, unsigned long long *keys,
+                              cudaStream_t s) {
+    return sliced_inner_exps_t(L, ldl, m, K, keys, s);
+}
+cudaError_t sliced_inner_exps(const dfloat *L, int64_t ldl, int64_t m, int64_t K, unsigned long long *keys,
+                              cudaStream_t s) {
+    return sliced_inner_exps_t(L, ldl, m, K, keys, s);
 }
 
 cudaError_t df_from_f64(const double *src, int64_t lds, dfloat *dst, int64_t ldd, int64_t m, int64_t n,

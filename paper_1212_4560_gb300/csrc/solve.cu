@@ -209,7 +209,8 @@ __global__ void __launch_bounds__(256) k_outer_rows(const double *Lam, int64_t l
 // 64 x 64 tiles and the diagonal blocks are taken one after the other (block
 // j(q) at step q: j = q forward, nblk-1-q backward).  The CTA that draws
 // ticket 0 walks the diagonal: for each block it applies the precomputed
-// inverse of the diagonal tile plus one refinement step, publishes y_j (into a
+// inverse of the diagonal tile plus one refinement step (the double-float
+// walker: the inverse alone, see kDdBlockRefine), publishes y_j (into a
 // buffer filled with an all-ones NaN before the launch, which no result
 // takes: a reader sees each value land without a fence or flag), and
 // subtracts op(T)[next][j] y_j from the next block itself, so the chain from
@@ -226,11 +227,18 @@ __global__ void __launch_bounds__(256) k_outer_rows(const double *Lam, int64_t l
 // cannot deadlock (it needs two or more CTAs).  Every wait is bounded: on
 // timeout the kernel sets a device flag (read by genp_device_check) and goes
 // on.  In double-float (the sliced path's factors) the walker's tiles (the
-// inverse, the masked diagonal block, the next block's tile) come by TMA a
-// step before they are needed, into shared memory: one SM's own loads of
-// three 32 KiB tiles per step were what set the pace.
+// inverse, the masked diagonal block when it refines, the next block's tile)
+// come by TMA a step before they are needed, into shared memory: one SM's
+// own loads of three 32 KiB tiles per step were what set the pace.
 // ---------------------------------------------------------------------------
 constexpr int TB = 64;          // tile
+// The double-float walker's diagonal blocks: y = T_jj^{-1} b by the inverse
+// alone, or followed by one refinement step y += T_jj^{-1} (b - T_jj y).
+// The inverses are FP64's held to 48 bits, so the inverse alone leaves a
+// block's solve within about cond(T_jj) 2^-48 (relative), the size of the
+// sliced factors' own error, which the FP64 refinement that follows every
+// sliced solve absorbs; the step doubled the chain's work per block.
+constexpr bool kDdBlockRefine = false;
 constexpr int kSeg = 16;        // tiles per work item
 constexpr int kTrsvThreads = 256;
 constexpr long long kSpinTicks = 4000000000LL;   // ~2 s at 2 GHz
@@ -685,7 +693,7 @@ __global__ void __launch_bounds__(kTrsvThreads, 1) k_trsv(const TS *C, int64_t l
             };
             fill_x(0);
             if (nblk > 1) fill_x(1);
-            fill_d(0);
+            if constexpr (kDdBlockRefine) fill_d(0);
             if (nblk > 1) fill_o(0);
             load_b(block_of(0));
             for (int q = 0; q < nblk; ++q) {
@@ -703,28 +711,30 @@ __global__ void __launch_bounds__(kTrsvThreads, 1) k_trsv(const TS *C, int64_t l
                 const dfloat(*X)[kDdLd] = sd.X[q & 1];
                 take(q & 1);
                 __syncthreads();
-                // y = X b;  y += X (b - T y)
+                // y = X b  (then, with kDdBlockRefine, y += X (b - T y))
                 dfloat part[NR];
                 if (tr) tile_gemv_dd<NR, true>(X, sd.acc, r, qq, part);
                 else tile_gemv_dd<NR, false>(X, sd.acc, r, qq, part);
+                if constexpr (kDdBlockRefine) {
 #pragma unroll
-                for (int c = 0; c < NR; ++c)
-                    if ((c & 3) == qq) sd.y[r][c] = part[c];
-                take(2);
-                __syncthreads();
-                if (tr) tile_gemv_dd<NR, true>(sd.D, sd.y, r, qq, part);
-                else tile_gemv_dd<NR, false>(sd.D, sd.y, r, qq, part);
+                    for (int c = 0; c < NR; ++c)
+                        if ((c & 3) == qq) sd.y[r][c] = part[c];
+                    take(2);
+                    __syncthreads();
+                    if (tr) tile_gemv_dd<NR, true>(sd.D, sd.y, r, qq, part);
+                    else tile_gemv_dd<NR, false>(sd.D, sd.y, r, qq, part);
 #pragma unroll
-                for (int c = 0; c < NR; ++c)
-                    if ((c & 3) == qq) sd.acc[r][c] = sd.acc[r][c] - part[c];
-                __syncthreads();
-                if (q + 1 < nblk) fill_d(q + 1);      // D is free
-                if (tr) tile_gemv_dd<NR, true>(X, sd.acc, r, qq, part);
-                else tile_gemv_dd<NR, false>(X, sd.acc, r, qq, part);
+                    for (int c = 0; c < NR; ++c)
+                        if ((c & 3) == qq) sd.acc[r][c] = sd.acc[r][c] - part[c];
+                    __syncthreads();
+                    if (q + 1 < nblk) fill_d(q + 1);      // D is free
+                    if (tr) tile_gemv_dd<NR, true>(X, sd.acc, r, qq, part);
+                    else tile_gemv_dd<NR, false>(X, sd.acc, r, qq, part);
+                }
 #pragma unroll
                 for (int c = 0; c < NR; ++c)
                     if ((c & 3) == qq) {
-                        const dfloat yv = sd.y[r][c] + part[c];
+                        const dfloat yv = kDdBlockRefine ? sd.y[r][c] + part[c] : part[c];
                         sd.y[r][c] = yv;
                         if (r < bj && c < nr) {
                             Y[((int64_t)j * TB + r) * ldy + c] = (T)(double)yv;

@@ -560,10 +560,10 @@ def run_ours(a, emit=True):
                     "tensor_pipe": {"achieved": pipe, "frac": pipe / peak, "unit": "TFLOP/s",
                                     "counted": "BF16 digit-pair products actually issued (2 m n Kpad per pair)"},
                     # dram read + write bytes of one n = 4096 A G chunk launch (k_tc_sliced<2, 5>,
-                    # K = 1024, column-major tile order) under ncu, 282.0 MB (the double-float
-                    # accumulator's read-modify-write 268 MB, the digit slices 59 MB read about
-                    # once), scaled by the n^2 output tiles to this size's chunk launches
-                    "traffic": 282.0e6 * (n / 4096) ** 2 if (nd == 7 and pd == 5) else None,
+                    # K = 1024, column-major tile order) under ncu on the current kernel, 281.7 MB
+                    # (the double-float accumulator's read-modify-write 268 MB, the digit slices
+                    # read about once), scaled by the n^2 output tiles to this size's chunk launches
+                    "traffic": 281.7e6 * (n / 4096) ** 2 if (nd == 7 and pd == 5) else None,
                     "traffic_basis": "A G chunk launch (K = 1024) of k_tc_sliced<2, 5>; ncu at n = 4096 scaled by "
                                      "n^2; Schur-update launches (K = 512) read and write the same accumulator "
                                      "per tile over half the depth"}

@@ -368,25 +368,45 @@ size_t trsm_smem(int kb) {
     }
     return (size_t)kbq * (kbq + 1) * sizeof(TC);
 }
+// The vectors a block-solve launch takes: rows [l_beg, l_end) of the block
+// column (L role) and columns [u_beg, u_end) of the block row (U role), 64
+// per CTA, the L role's CTAs first.
+struct TrsmRange {
+    int64_t l_beg, l_end, u_beg, u_end;
+};
+__host__ __device__ __forceinline__ int trsm_l_ctas(const TrsmRange &rg) {
+    return rg.l_end > rg.l_beg ? (int)((rg.l_end - rg.l_beg + kTrsmW - 1) / kTrsmW) : 0;
+}
+__host__ __device__ __forceinline__ int trsm_u_ctas(const TrsmRange &rg) {
+    return rg.u_end > rg.u_beg ? (int)((rg.u_end - rg.u_beg + kTrsmW - 1) / kTrsmW) : 0;
+}
+// this CTA's role, first vector and vector count
+__device__ __forceinline__ void trsm_cta(const TrsmRange &rg, bool &role_u, int64_t &c0, int &w) {
+    const int nbl = trsm_l_ctas(rg);
+    role_u = (int)blockIdx.x >= nbl;
+    c0 = role_u ? rg.u_beg + (int64_t)((int)blockIdx.x - nbl) * kTrsmW : rg.l_beg + (int64_t)blockIdx.x * kTrsmW;
+    w = (int)min((int64_t)kTrsmW, (role_u ? rg.u_end : rg.l_end) - c0);
+}
 template <typename TS>
-__device__ __forceinline__ void trsm_df(TS *C, int64_t ldc, int64_t n, int64_t k0, int kb, DevStatus *st,
+__device__ __forceinline__ void trsm_df(TS *C, int64_t ldc, TrsmRange rg, int64_t k0, int kb, DevStatus *st,
                                         unsigned char *smraw);
 template <typename TS, typename TC>
-__global__ void __launch_bounds__(kTrsmThreads, 1) k_trsm_reg(TS *C, int64_t ldc, int64_t n, int64_t k0, int kb,
+__global__ void __launch_bounds__(kTrsmThreads, 1) k_trsm_reg(TS *C, int64_t ldc, TrsmRange rg, int64_t k0, int kb,
                                                               DevStatus *st) {
     extern __shared__ __align__(16) unsigned char smraw[];
     if constexpr (std::is_same<TC, dfloat>::value) {
-        trsm_df<TS>(C, ldc, n, k0, kb, st, smraw);
+        trsm_df<TS>(C, ldc, rg, k0, kb, st, smraw);
         return;
     }
     TC *T = reinterpret_cast<TC *>(smraw);
     const int nq = (kb + kTpv - 1) / kTpv, kbq = kTpv * nq, ld = kbq + 1;   // the block rounded up to 16
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int v = tid / kTpv, g = tid % kTpv;
-    const int64_t c0 = k0 + kb + (int64_t)blockIdx.x * kTrsmW;
-    const int w = (int)min((int64_t)kTrsmW, n - c0);
+    bool role_u;
+    int64_t c0;
+    int w;
+    trsm_cta(rg, role_u, c0, w);
     if (w <= 0) return;
-    const bool role_u = blockIdx.y == 0;
     for (int r = warp; r < kbq; r += kTrsmThreads / 32)
         for (int c = lane; c < kbq; c += 32)
             T[r * ld + c] = (r < kb && c < kb) ? ld_as<TC>(C[(k0 + r) * ldc + k0 + c]) : TC(r == c ? 1.0 : 0.0);
@@ -478,7 +498,7 @@ __global__ void __launch_bounds__(kTrsmThreads, 1) k_trsm_reg(TS *C, int64_t ldc
 // lo plane, so a thread reads a pair with one 8-byte load and a half-warp's
 // loads are contiguous; past the block the planes hold the identity.
 template <typename TS>
-__device__ __forceinline__ void trsm_df(TS *C, int64_t ldc, int64_t n, int64_t k0, int kb, DevStatus *st,
+__device__ __forceinline__ void trsm_df(TS *C, int64_t ldc, TrsmRange rg, int64_t k0, int kb, DevStatus *st,
                                         unsigned char *smraw) {
     const int nq = (kb + kTpv - 1) / kTpv, kbq = kTpv * nq, np = (nq + 1) / 2, span = 2 * kTpv * np;
     float2 *Ph = reinterpret_cast<float2 *>(smraw);
@@ -486,10 +506,11 @@ __device__ __forceinline__ void trsm_df(TS *C, int64_t ldc, int64_t n, int64_t k
     dfloat *rd = reinterpret_cast<dfloat *>(Pl + (size_t)kbq * np * kTpv);
     const int tid = threadIdx.x, lane = tid & 31;
     const int v = tid / kTpv, g = tid % kTpv;
-    const int64_t c0 = k0 + kb + (int64_t)blockIdx.x * kTrsmW;
-    const int w = (int)min((int64_t)kTrsmW, n - c0);
+    bool role_u;
+    int64_t c0;
+    int w;
+    trsm_cta(rg, role_u, c0, w);
     if (w <= 0) return;
-    const bool role_u = blockIdx.y == 0;
     for (int idx = tid; idx < kbq * span; idx += kTrsmThreads) {
         // the global reads run along a row of C: k fastest for the block row's
         // operand (a column of L11), c fastest for the block column's (a row of U11)
@@ -629,19 +650,27 @@ cudaError_t panel_only(TS *C, int64_t ldc, int64_t i0, int kb, DevStatus *st, cu
     return cudaGetLastError();
 }
 template <typename TS, typename TC>
-cudaError_t trsm_only(TS *C, int64_t ldc, int64_t n, int64_t i0, int kb, DevStatus *st, cudaStream_t s) {
-    const int64_t rem = n - i0 - kb;
-    if (rem <= 0) return cudaSuccess;
+cudaError_t trsm_range(TS *C, int64_t ldc, TrsmRange rg, int64_t i0, int kb, DevStatus *st, cudaStream_t s) {
+    const int ctas = trsm_l_ctas(rg) + trsm_u_ctas(rg);
+    if (ctas <= 0) return cudaSuccess;
     cudaError_t e = panel_attrs<TS, TC>();
     if (e != cudaSuccess) return e;
-    dim3 g((unsigned)cdiv(rem, kTrsmW), 2);
-    // block row and block column: kb^2 flops per vector of length kb, 2 rem vectors
-    auto *ev = profile_class_slot(kProfFactorAux, 2.0 * (double)kb * kb * (double)rem);
+    const double vecs = (double)((rg.l_end > rg.l_beg ? rg.l_end - rg.l_beg : 0) +
+                                 (rg.u_end > rg.u_beg ? rg.u_end - rg.u_beg : 0));
+    // kb^2 flops per vector of length kb
+    auto *ev = profile_class_slot(kProfFactorAux, (double)kb * kb * vecs);
     prof_begin(ev, s);
     note_launch();
-    k_trsm_reg<TS, TC><<<g, kTrsmThreads, trsm_smem<TC>(kb), s>>>(C, ldc, n, i0, kb, st);
+    k_trsm_reg<TS, TC><<<ctas, kTrsmThreads, trsm_smem<TC>(kb), s>>>(C, ldc, rg, i0, kb, st);
     prof_end(ev, s);
     return cudaGetLastError();
+}
+// the whole block row and block column beside the diagonal block at i0
+template <typename TS, typename TC>
+cudaError_t trsm_only(TS *C, int64_t ldc, int64_t n, int64_t i0, int kb, DevStatus *st, cudaStream_t s) {
+    const int64_t j0 = i0 + kb;
+    if (n - j0 <= 0) return cudaSuccess;
+    return trsm_range<TS, TC>(C, ldc, TrsmRange{j0, n, j0, n}, i0, kb, st, s);
 }
 template <typename TS, typename TC>
 cudaError_t panel_and_trsm(TS *C, int64_t ldc, int64_t n, int64_t i0, int kb, DevStatus *st, cudaStream_t s) {
@@ -701,10 +730,10 @@ cudaError_t factor_tc(genp_factors *F, cudaStream_t s) {
         k_panel_reg<float, dfloat><<<1, kPanelThreads, panel_smem<dfloat>(kb), s>>>(C, ldc, k0, kb, F->st);
         const int64_t rem = n - k0 - kb;
         if (rem <= 0) break;
-        dim3 g((unsigned)cdiv(rem, kTrsmW), 2);
+        const TrsmRange rg{k0 + kb, n, k0 + kb, n};
         note_launch();
-        k_trsm_reg<float, float><<<g, kTrsmThreads, trsm_smem<float>(kb), s>>>(C, ldc, n, k0, kb,
-                                                                                               F->st);
+        k_trsm_reg<float, float><<<trsm_l_ctas(rg) + trsm_u_ctas(rg), kTrsmThreads, trsm_smem<float>(kb), s>>>(
+            C, ldc, rg, k0, kb, F->st);
         float *L21 = C + (k0 + kb) * ldc + k0;
         float *U12 = C + k0 * ldc + k0 + kb;
         float *A22 = C + (k0 + kb) * ldc + k0 + kb;
@@ -803,7 +832,15 @@ cudaError_t factor_sliced(genp_factors *F, cudaStream_t s) {
             } else {
                 e = panel_only<dfloat, dfloat>(W, ldw, i0, kb, F->st, s);
             }
-            if (e == cudaSuccess) e = trsm_only<dfloat, dfloat>(W, ldw, n, i0, kb, F->st, s);
+            // with the look-ahead, the block row beyond the next inner block is
+            // solved later, while that block is factored: the path from one
+            // diagonal block to the next takes only the block column and the
+            // next block's columns of the block row
+            const bool split = ahead && j0 < e0 && rem > 0;
+            const int64_t nbn = split ? (e0 - j0 < nb ? e0 - j0 : nb) : 0;
+            if (e == cudaSuccess)
+                e = split ? trsm_range<dfloat, dfloat>(W, ldw, TrsmRange{j0, n, j0, j0 + nbn}, i0, kb, F->st, s)
+                          : trsm_only<dfloat, dfloat>(W, ldw, n, i0, kb, F->st, s);
             if (e != cudaSuccess) return e;
             if (rem <= 0) break;
             if (j0 < e0) {
@@ -820,15 +857,22 @@ cudaError_t factor_sliced(genp_factors *F, cudaStream_t s) {
                 const int64_t kp = sliced_kpad(kb);
                 e = sliced_inner_exps(Lw, ldw, rem, kb, kk, s);
                 if (e == cudaSuccess) e = slice_rows(F->nd, Lw, ldw, rem, kb, F->tcA, ldq, F->exps, s, kk);
-                if (e == cudaSuccess) e = slice_cols_T(F->nd, Uw, ldw, kb, rem, F->tcB, ldq, F->exps + n, s, kk);
-                if (ahead) {
+                if (split) {
+                    if (e == cudaSuccess) e = slice_cols_T(F->nd, Uw, ldw, kb, nb2, F->tcB, ldq, F->exps + n, s, kk);
                     if (e == cudaSuccess) e = update(rem, nb2, kp, 0, W + j0 * ldw + j0);
                     if (e == cudaSuccess) e = block_ahead(j0, nb2);
                     const int prev = sliced_spare_sms(1);
+                    // the rest of the block row, solved and sliced beside the next block
+                    if (e == cudaSuccess)
+                        e = trsm_range<dfloat, dfloat>(W, ldw, TrsmRange{j0, j0, j0 + nb2, n}, i0, kb, F->st, s);
+                    if (e == cudaSuccess)
+                        e = slice_cols_T(F->nd, Uw + nb2, ldw, kb, rem - nb2, F->tcB + nb2 * ldq, ldq,
+                                         F->exps + n + nb2, s, kk);
                     if (e == cudaSuccess && w2 > nb2) e = update(rem, w2 - nb2, kp, nb2, W + j0 * ldw + j0 + nb2);
                     if (e == cudaSuccess && remo > 0) e = update(w2, remo, kp, w2, W + j0 * ldw + e0);
                     sliced_spare_sms(prev);
                 } else {
+                    if (e == cudaSuccess) e = slice_cols_T(F->nd, Uw, ldw, kb, rem, F->tcB, ldq, F->exps + n, s, kk);
                     if (e == cudaSuccess) e = update(rem, w2, kp, 0, W + j0 * ldw + j0);
                     if (e == cudaSuccess && remo > 0) e = update(w2, remo, kp, w2, W + j0 * ldw + e0);
                 }

@@ -323,8 +323,9 @@ cudaError_t slice_cols_T(int nd, const dfloat *src, int64_t lds, int64_t K, int6
 cudaError_t sliced_inner_exps(const dfloat *L, int64_t ldl, int64_t m, int64_t K, unsigned long long *keys,
                               cudaStream_t s);
 // double <-> double-float copies of an m x n block
+// (with amax: max |src| into that status word as well)
 cudaError_t df_from_f64(const double *src, int64_t lds, dfloat *dst, int64_t ldd, int64_t m, int64_t n,
-                        cudaStream_t s);
+                        cudaStream_t s, unsigned long long *amax = nullptr);
 cudaError_t df_to_f64(const dfloat *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int64_t n,
                       cudaStream_t s);
 // D = alpha * W + beta * D (W double-float, D double; beta == 0 ignores D)

@@ -816,9 +816,8 @@ cudaError_t factor_sliced(genp_factors *F, cudaStream_t s) {
         return tc_gemm_sliced(F->nd, m, w, kpad, -1.0f, F->tcA, ldq, F->tcB + bcol * ldq, ldq, F->exps,
                               F->exps + n + bcol, D, ldw, s);
     };
-    note_launch();
-    k_maxabs<double><<<152 * 4, 256, 0, s>>>(C, n, ldc, &F->st->max_abs_c);
-    cudaError_t e = df_from_f64(C, ldc, W, ldw, n, n, s);
+    // the double-float copy and max |c_ij| in one pass over C
+    cudaError_t e = df_from_f64(C, ldc, W, ldw, n, n, s, &F->st->max_abs_c);
     if (e != cudaSuccess) return e;
     for (int64_t k0 = 0; k0 < n; k0 += nbo) {
         const int kbo = (int)(n - k0 < nbo ? n - k0 : nbo);

@@ -252,10 +252,21 @@ __global__ void k_slice_cols_T_small(const TS *src, int64_t lds, int64_t K, int6
 }
 
 // Double-float <-> FP64 copies of a block (grid-stride over rows, coalesced columns).
-__global__ void k_df_from_f64(const double *src, int64_t lds, dfloat *dst, int64_t ldd, int64_t m, int64_t n) {
+// With amax, also max |src| into the status word *amax (the integer maximum
+// of the magnitudes' bit patterns: a NaN outranks every number).
+__global__ void k_df_from_f64(const double *src, int64_t lds, dfloat *dst, int64_t ldd, int64_t m, int64_t n,
+                              unsigned long long *amax) {
+    unsigned long long mb = 0ull;
     for (int64_t i = blockIdx.y; i < m; i += gridDim.y)
-        for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-            dst[i * ldd + j] = dfloat(src[i * lds + j]);
+        for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+            const double v = src[i * lds + j];
+            mb = max(mb, (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull);
+            dst[i * ldd + j] = dfloat(v);
+        }
+    if (amax) {
+        for (int o = 16; o > 0; o >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+        if ((threadIdx.x & 31) == 0 && mb) atomicMax(amax, mb);
+    }
 }
 __global__ void k_df_to_f64(const dfloat *src, int64_t lds, double *dst, int64_t ldd, int64_t m, int64_t n) {
     for (int64_t i = blockIdx.y; i < m; i += gridDim.y)
@@ -412,10 +423,10 @@ cudaError_t sliced_inner_exps(const dfloat *L, int64_t ldl, int64_t m, int64_t K
 }
 
 cudaError_t df_from_f64(const double *src, int64_t lds, dfloat *dst, int64_t ldd, int64_t m, int64_t n,
-                        cudaStream_t s) {
+                        cudaStream_t s, unsigned long long *amax) {
     if (m <= 0 || n <= 0) return cudaSuccess;
     note_launch();
-    k_df_from_f64<<<block_grid(m, n), 256, 0, s>>>(src, lds, dst, ldd, m, n);
+    k_df_from_f64<<<block_grid(m, n), 256, 0, s>>>(src, lds, dst, ldd, m, n, amax);
     return cudaGetLastError();
 }
 

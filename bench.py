@@ -82,6 +82,8 @@ def parse():
     p.add_argument("--precond-digits", type=int, default=None,
                    help="digits of A in the sliced C = A G (3 .. 7; 0: the library's setting, 7; default 5 with "
                         "GMRES-IR, which needs the product only as accurate as the factors it feeds)")
+    p.add_argument("--mult-digits", type=int, default=0, choices=[0, 1, 2],
+                   help="digits of the dense Gaussian multiplier's sliced grid (0: the library's setting, 1)")
     p.add_argument("--refine", default=None, choices=["classic", "gmres"],
                    help="refinement method (default: classic for fp64, GMRES-IR otherwise)")
     p.add_argument("--max-iter", type=int, default=None)
@@ -373,6 +375,8 @@ def run_ours(a, emit=True):
         a.precond_digits = 5 if (a.prec == "sliced" and method_name == "gmres") else 0
     old_pdigits = genp._lib.load().genp_sliced_precondition_digits(0)
     genp._lib.load().genp_sliced_precondition_digits(a.precond_digits or old_pdigits)
+    if a.mult_digits:
+        genp._lib.load().genp_sliced_multiplier_digits(a.mult_digits)
     cdt = torch.float64 if a.prec in F64_FACTORS else torch.float32
     method = {"classic": 0, "gmres": 1}[a.refine or ("classic" if a.prec == "fp64" else "gmres")]
     max_iter = a.max_iter if a.max_iter is not None else (10 if a.prec == "fp64" or method == 1 else 30)
@@ -666,7 +670,8 @@ def run_ours(a, emit=True):
             "data": "synthetic",
             "config": {"workload": workload_name(a), "n": n, "nrhs": nrhs, "multiplier": a.kind, "precision": a.prec,
                        "digits": {"factor": lib.genp_sliced_digits(0),
-                                  "precondition": lib.genp_sliced_precondition_digits(0)}
+                                  "precondition": lib.genp_sliced_precondition_digits(0),
+                                  "multiplier": lib.genp_sliced_multiplier_digits(0)}
                        if a.prec == "sliced" else None,
                        "A": ("J U diag(sigma) V^T, kappa=%g" % a.kappa) if a.workload == "svd"
                        else ("N(0,1) with leading 32x32 block of rank 16" if n <= 256

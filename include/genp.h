@@ -198,8 +198,13 @@ GENP_API const char *genp_status_string(genp_status s);
  *              products instead of 28 at the same accuracy, and
  *              x += G d uses that same G.  The rounding moves an entry by at
  *              most 2^(E - 14) < 1.6e-3 scale, a perturbed Gaussian that
- *              Thm. 4.1 covers (G = G' + U).  SPARSE,
- *              IDENTITY and HOUSEHOLDER_PM1 ignore it.
+ *              Thm. 4.1 covers (G = G' + U).  A dense Gaussian takes the
+ *              grid of genp_sliced_multiplier_digits at its creation: with
+ *              one digit (the default) the multiples are of 2^(E - 6), an
+ *              entry moves by at most 2^(E - 7) (about 0.1 to 0.2 of the
+ *              scale), and A G forms 5 digit products for five digits of A
+ *              (7 for seven).  SPARSE, IDENTITY and HOUSEHOLDER_PM1 ignore
+ *              it.
  *  out         receives the handle; the library owns G's device storage.
  * Errors: GENP_ERR_ARG, GENP_ERR_NOMEM, GENP_ERR_CUDA. */
 GENP_API genp_status genp_make_multiplier(genp_mult_kind kind, int64_t n, uint64_t seed, uint64_t stream_id,
@@ -602,6 +607,20 @@ GENP_API int genp_sliced_digits(int digits);
  * previous one, or -1 if digits is not supported.  Not synchronized with
  * concurrent calls. */
 GENP_API int genp_sliced_precondition_digits(int digits);
+
+/* Digits of the sliced grid (value_grid GENP_BF16_SLICED) of the dense
+ * Gaussian multipliers created afterwards: 1 (the default; multiples of
+ * 2^(E - 6)) or 2 (multiples of 2^(E - 13)); circulant and Toeplitz
+ * multipliers keep two.  Thm. 4.1's perturbed Gaussian G = G' + U covers
+ * either grid, and GENP of A G with the coarser one leaves the pivots'
+ * growth and the unrefined backward error at the two-digit grid's level on
+ * Gaussian test matrices; with one digit the sliced C = A G forms nd digit
+ * products per multiply-add (nd = genp_sliced_precondition_digits) instead
+ * of 2 nd - 1.  A multiplier keeps the grid it was created with (redraws
+ * included).  digits == 0 returns the current setting; 1 or 2 sets it and
+ * returns the previous one; anything else returns -1.  Not synchronized
+ * with concurrent calls. */
+GENP_API int genp_sliced_multiplier_digits(int digits);
 
 /* Measurement hook: while enabled, every launch of the sliced and the e4m3
  * tensor-core kernels is bracketed by two CUDA events on its stream.

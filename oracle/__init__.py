@@ -713,13 +713,18 @@ def sliced_grid_exponent(scale: float) -> int:
     return p - 1 if f == 0.5 else p
 
 
-def sliced_grid(G: np.ndarray, scale: float) -> np.ndarray:
-    """The multiplier rounded to the fixed-point grid of the sliced product:
-    the nearest integer multiple of 2^(E - 13), ties to even (Thm. 4.1's
-    perturbed Gaussian G = G' + U with |U| <= 2^(E - 14)).  The library
-    rounds its single precision draw (``multiplier(..., grid="fp32")``)."""
+def sliced_grid(G: np.ndarray, scale: float, digits: int = 2) -> np.ndarray:
+    """The multiplier rounded to the fixed-point grid of the sliced product
+    with ``digits`` balanced 7-bit digits: the nearest integer multiple of
+    2^(E - 7 digits + 1), ties to even (Thm. 4.1's perturbed Gaussian
+    G = G' + U with |U| <= 2^(E - 7 digits)): 2^(E - 13) for two digits,
+    2^(E - 6) for one.  The library rounds its single precision draw
+    (``multiplier(..., grid="fp32")``)."""
+    if digits not in (1, 2):
+        raise ValueError("digits: 1 or 2")
     E = sliced_grid_exponent(scale)
-    return np.ldexp(np.rint(np.ldexp(_c(G), 13 - E)), E - 13)
+    q = 7 * digits - 1
+    return np.ldexp(np.rint(np.ldexp(_c(G), q - E)), E - q)
 
 
 def det_leibniz(M) -> Fraction:

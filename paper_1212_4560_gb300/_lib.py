@@ -54,6 +54,7 @@ SIGNATURES = {
                             _vp, _vp]),
     "genp_sliced_digits": (_int, [_int]),
     "genp_sliced_precondition_digits": (_int, [_int]),
+    "genp_sliced_multiplier_digits": (_int, [_int]),
     "genp_profile_enable": (_int, [_int]),
     "genp_profile_read": (_int, [_vp, _vp, _vp]),
     "genp_profile_launches": (_int, [_vp, _vp, _int, _vp]),

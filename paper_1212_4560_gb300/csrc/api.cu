@@ -76,7 +76,7 @@ cudaError_t draw_multiplier(genp_multiplier *G, uint64_t seed, uint64_t stream_i
     switch (G->kind) {
         case GENP_MULT_GAUSSIAN:
             return launch_make_dense(G->dense, G->n, seed, stream_id, G->scale, G->grid, G->dense_f32, G->dense_bf16,
-                                     s);
+                                     s, G->grid_digits);
         case GENP_MULT_CIRCULANT: {
             cudaError_t e = G->pm1        ? launch_make_circulant_pm1(G->g, G->n, seed, stream_id, G->attempt, s)
                             : G->toeplitz ? launch_make_toeplitz(G->g, G->n, seed, stream_id, G->scale, G->grid, s)
@@ -338,6 +338,7 @@ genp_status genp_make_multiplier(genp_mult_kind kind, int64_t n, uint64_t seed, 
     G->n = n;
     G->nnz = kind == GENP_MULT_SPARSE_PM1 ? nnz_per_col : 0;
     G->grid = kind == GENP_MULT_SPARSE_PM1 ? GENP_FP64 : value_grid;
+    G->grid_digits = (kind == GENP_MULT_GAUSSIAN && value_grid == GENP_BF16_SLICED) ? sliced_mult_digits() : 2;
     G->scale = kind == GENP_MULT_SPARSE_PM1 ? 1.0 : scale;
     G->pm1 = pm1;
     G->toeplitz = toeplitz;
@@ -481,6 +482,11 @@ int genp_sliced_digits(int digits) {
 int genp_sliced_precondition_digits(int digits) {
     if (digits == 0) return sliced_precond_digits();
     return set_sliced_precond_digits(digits);
+}
+
+int genp_sliced_multiplier_digits(int digits) {
+    if (digits == 0) return sliced_mult_digits();
+    return set_sliced_mult_digits(digits);
 }
 
 genp_status genp_gemm_sliced(int64_t m, int64_t n, int64_t K, double alpha, const double *A, int64_t lda,
@@ -649,9 +655,10 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
         const double *a = static_cast<const double *>(A);
         if (c_prec == GENP_BF16_SLICED && G->kind == GENP_MULT_GAUSSIAN) {
             const int nd = sliced_precond_digits();
-            // G on the sliced grid is exact in two digits: 13 digit products instead of 28
-            const int ndg = (G->grid == GENP_BF16_SLICED && nd >= 5) ? 2 : nd;
-            const int64_t ldq = (int64_t)nd * (ndg == 2 ? kSlicedChunk2 : kSlicedChunk), ldd = round8(n);
+            // G on the sliced grid is exact in its one or two digits: nd or 2 nd - 1
+            // digit products instead of nd (nd + 1) / 2
+            const int ndg = (G->grid == GENP_BF16_SLICED && nd >= 5) ? G->grid_digits : nd;
+            const int64_t ldq = (int64_t)nd * (ndg <= 2 ? kSlicedChunk2 : kSlicedChunk), ldd = round8(n);
             char *buf = nullptr;
             const size_t dbytes = (size_t)n * ldd * 8, qbytes = (size_t)n * ldq * sizeof(__nv_bfloat16);
             CU(cudaMallocAsync((void **)&buf, dbytes + 2 * qbytes + (size_t)2 * n * sizeof(int) + 256, s));
@@ -680,9 +687,10 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
         // digits as genp_sliced_precondition_digits asks), summed in
         // double-float and rounded to FP64 once.
         const int nd = sliced_precond_digits();
-        // G on the sliced grid is exact in two digits: 13 digit products instead of 28
-        const int ndg = (G->grid == GENP_BF16_SLICED && nd >= 5) ? 2 : nd;
-        const int64_t ldq = (int64_t)nd * (ndg == 2 ? kSlicedChunk2 : kSlicedChunk), ldd = round8(n);
+        // G on the sliced grid is exact in its one or two digits: nd or 2 nd - 1
+        // digit products instead of nd (nd + 1) / 2
+        const int ndg = (G->grid == GENP_BF16_SLICED && nd >= 5) ? G->grid_digits : nd;
+        const int64_t ldq = (int64_t)nd * (ndg <= 2 ? kSlicedChunk2 : kSlicedChunk), ldd = round8(n);
         char *buf = nullptr;
         const size_t dbytes = (size_t)n * ldd * 8, qbytes = (size_t)n * ldq * sizeof(__nv_bfloat16);
         CU(cudaMallocAsync((void **)&buf, dbytes + 2 * qbytes + (size_t)2 * n * sizeof(int) + 256, s));
@@ -690,11 +698,11 @@ genp_status genp_precondition(const genp_multiplier *G, const void *A, int64_t l
         __nv_bfloat16 *Aq = reinterpret_cast<__nv_bfloat16 *>(buf + dbytes);
         __nv_bfloat16 *Bq = Aq + (size_t)n * ldq;
         int *ex = reinterpret_cast<int *>(Bq + (size_t)n * ldq);
-        if (ndg == 2) {
-            // G (two digits) on the M side, A's rows (nd digits) along N: the
-            // product comes out transposed and is turned around on the way to FP64
-            CU(sliced_matmul_t(nd, 2, n, n, n, static_cast<const double *>(A), lda, G->dense, n, D, ldd, Bq, Aq, ex,
-                               s));
+        if (ndg <= 2) {
+            // G (one or two digits) on the M side, A's rows (nd digits) along N:
+            // the product comes out transposed and is turned around on the way to FP64
+            CU(sliced_matmul_t(nd, ndg, n, n, n, static_cast<const double *>(A), lda, G->dense, n, D, ldd, Bq, Aq,
+                               ex, s));
             CU(df_to_f64_T(D, ldd, static_cast<double *>(C), ldc, n, n, s));
         } else {
             CU(sliced_matmul(nd, n, n, n, static_cast<const double *>(A), lda, G->dense, n, D, ldd, Aq, Bq, ex, s));

@@ -1089,9 +1089,10 @@ cudaError_t tc_gemm_sliced2(int nda, int ndb, int64_t m, int64_t n, int64_t kpad
                             const int *fb, dfloat *D, int64_t ldd, cudaStream_t s) {
     if (m <= 0 || n <= 0) return cudaSuccess;
     const bool sym = nda == ndb && sliced::supported(nda);
-    const bool twodigit = nda == 2 && ndb >= 5 && ndb <= 7;   // a two-digit M side, the wide operand along N
-    if (!sym && !twodigit) return cudaErrorInvalidValue;
-    const int64_t kmax = nda == 2 ? kSlicedChunk2 : kSlicedChunk;
+    // a one- or two-digit M side (a multiplier on the sliced grid), the wide operand along N
+    const bool narrow = (nda == 1 || nda == 2) && ndb >= 5 && ndb <= 7;
+    if (!sym && !narrow) return cudaErrorInvalidValue;
+    const int64_t kmax = nda <= 2 ? kSlicedChunk2 : kSlicedChunk;
     if (kpad <= 0 || kpad % BK || kpad > kmax || m > INT32_MAX || n > INT32_MAX) return cudaErrorInvalidValue;
     if ((lda % 8) || (ldb % 8) || ((uintptr_t)Aq % 16) || ((uintptr_t)Bq % 16)) return cudaErrorInvalidValue;
     const int64_t kqa = (int64_t)nda * kpad, kqb = (int64_t)ndb * kpad;
@@ -1104,6 +1105,9 @@ cudaError_t tc_gemm_sliced2(int nda, int ndb, int64_t m, int64_t n, int64_t kpad
         case 5 * 9: return launch_sliced<5, 5>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
         case 6 * 9: return launch_sliced<6, 6>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
         case 7 * 9: return launch_sliced<7, 7>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
+        case 1 * 8 + 5: return launch_sliced<1, 5>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
+        case 1 * 8 + 6: return launch_sliced<1, 6>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
+        case 1 * 8 + 7: return launch_sliced<1, 7>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
         case 2 * 8 + 5: return launch_sliced<2, 5>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
         case 2 * 8 + 6: return launch_sliced<2, 6>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);
         case 2 * 8 + 7: return launch_sliced<2, 7>(ma, mb, m, n, kpad, alpha, ea, fb, D, ldd, s);

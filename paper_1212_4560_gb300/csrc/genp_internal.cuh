@@ -71,6 +71,7 @@ struct genp_multiplier {
     int8_t *inv_signs = nullptr;
     int32_t *draws = nullptr;          // nnz x n Fisher-Yates draws (SPARSE)
     double scale = 1.0;
+    int grid_digits = 2;               // digits of the sliced grid (dense Gaussian, grid GENP_BF16_SLICED)
     bool pm1 = false;                  // CIRCULANT_PM1 (stored as a circulant)
     bool toeplitz = false;             // TOEPLITZ (stored as a circulant of order 2n)
     int side = GENP_SIDE_RIGHT;        // C = A G (right) or C = G A (left)
@@ -160,8 +161,9 @@ void note_launches(uint64_t count);
 void profile_suspend(bool on);
 
 // rng.cu
+// (grid GENP_BF16_SLICED: grid_digits balanced 7-bit digits, 1 or 2)
 cudaError_t launch_make_dense(double *G, int64_t n, uint64_t seed, uint64_t stream_id, double scale,
-                              genp_prec grid, float *G32, __nv_bfloat16 *Gbf, cudaStream_t s);
+                              genp_prec grid, float *G32, __nv_bfloat16 *Gbf, cudaStream_t s, int grid_digits = 2);
 cudaError_t launch_make_circulant(double *g, int64_t n, uint64_t seed, uint64_t stream_id,
                                   double scale, genp_prec grid, cudaStream_t s);
 // +-1 first column, redrawn until no DFT bin of power-of-two order vanishes
@@ -299,6 +301,8 @@ int sliced_digits();              // digits of the GENP_BF16_SLICED path
 int set_sliced_digits(int nd);    // returns the previous value, -1 if nd is unsupported
 int sliced_precond_digits();      // digits of the sliced C = A G
 int set_sliced_precond_digits(int nd);
+int sliced_mult_digits();         // digits of a new dense Gaussian's sliced grid (1 or 2)
+int set_sliced_mult_digits(int d);   // returns the previous value, -1 if d is not 1 or 2
 // rows of src (m x K): dst[i][p*kpad + k] = slice p of src[i][k] 2^-q_k
 // (kkey null: no scaling; else q_k from kkey[k], see sliced_inner_exps);
 // exps[i] = row exponent
@@ -352,8 +356,9 @@ cudaError_t sliced_matmul(int nd, int64_t m, int64_t n, int64_t K, const double 
 constexpr int kSlicedOuter = 512;       // outer step (Schur update K) of the sliced factorization
 constexpr int64_t kSlicedChunk = 512;   // keeps the digit groups of weight >= 2^-49 exact in FP32
 // With a two-digit M side (a multiplier on the sliced grid) a group holds at
-// most two pairs of |d_t d_u| <= 2^13 (one pair of 2^14 for group 0), so
-// every group but the last stays exact in FP32 up to K = 1024.
+// most two pairs of |d_t d_u| <= 2^13 (one pair of 2^14 for group 0), and
+// with a one-digit side one pair of at most 2^14, so every group but the
+// last stays exact in FP32 up to K = 1024.
 constexpr int64_t kSlicedChunk2 = 1024;
 constexpr int64_t kSlicedLdq = 7 * kSlicedChunk;    // operand width for up to 7 digits
 

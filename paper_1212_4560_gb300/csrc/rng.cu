@@ -175,7 +175,9 @@ __device__ __forceinline__ double round_to_fp8_grid(double v, int e) {
 // Fixed-point grid of the sliced product: integer multiples of 2^(E - 13)
 // with E the least integer such that 12.5 scale <= 2^E (12.5 standard
 // deviations bound every polar draw), so |entry| < 2^E holds 14 signed bits
-// at any column scale 2^f <= 2^E: two exact balanced base-128 digits.
+// at any column scale 2^f <= 2^E: two exact balanced base-128 digits.  The
+// one-digit grid (the dense Gaussian's, by genp_sliced_multiplier_digits):
+// multiples of 2^(E - 6), one exact digit.  qb below is 13 or 6.
 // Rounding to nearest, ties to even.
 __host__ __device__ inline int sliced_grid_exp(double scale) {
     const double amax = 12.5 * scale;
@@ -185,10 +187,10 @@ __host__ __device__ inline int sliced_grid_exp(double scale) {
     const int e = f == 0.5 ? p - 1 : p;
     return e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
 }
-__device__ __forceinline__ double round_to_sliced_grid(double v, int e) {
-    // v 2^(13 - e) and back: exact power-of-two scalings (|e| <= 1000)
-    const double down = __longlong_as_double((long long)(1023 + 13 - e) << 52);
-    const double up = __longlong_as_double((long long)(1023 - 13 + e) << 52);
+__device__ __forceinline__ double round_to_sliced_grid(double v, int e, int qb = 13) {
+    // v 2^(qb - e) and back: exact power-of-two scalings (|e| <= 1000)
+    const double down = __longlong_as_double((long long)(1023 + qb - e) << 52);
+    const double up = __longlong_as_double((long long)(1023 - qb + e) << 52);
     return rint(v * down) * up;
 }
 
@@ -197,9 +199,9 @@ __device__ __forceinline__ double round_to_sliced_grid(double v, int e) {
 // magnitude below 2^13, so rintf (ties to even) and both power-of-two
 // scalings are exact and give the FP64 rounding's value bit for bit, without
 // FP64 operations (a sixty-fourth of the FP32 rate on this GPU).
-__device__ __forceinline__ double round_to_sliced_grid_f32(float v, int e) {
-    const float down = __uint_as_float((uint32_t)(127 + 13 - e) << 23);
-    const float up = __uint_as_float((uint32_t)(127 - 13 + e) << 23);
+__device__ __forceinline__ double round_to_sliced_grid_f32(float v, int e, int qb = 13) {
+    const float down = __uint_as_float((uint32_t)(127 + qb - e) << 23);
+    const float up = __uint_as_float((uint32_t)(127 - qb + e) << 23);
     return (double)__fmul_rn(rintf(__fmul_rn(v, down)), up);
 }
 
@@ -226,7 +228,7 @@ __device__ __forceinline__ double draw_on_grid(uint64_t seed, uint64_t sid, uint
 }
 
 __global__ void k_dense(double *G, int64_t n, uint64_t seed, uint64_t sid, double scale, genp_prec grid,
-                        float *G32, __nv_bfloat16 *Gbf) {
+                        float *G32, __nv_bfloat16 *Gbf, int qb) {
     const int64_t total = n * n;
     // the sliced grid's exponent and the FP32 scale, once; the FP32 rounding
     // needs both scalings' exponents in the normal range
@@ -237,8 +239,13 @@ __global__ void k_dense(double *G, int64_t n, uint64_t seed, uint64_t sid, doubl
          idx += (int64_t)gridDim.x * blockDim.x) {
         const double v = grid == GENP_BF16_SLICED && sliced_f32_ok
                              ? round_to_sliced_grid_f32(__fmul_rn(polar_normal_f32(seed, sid, kTagDense + 4, (uint64_t)idx), sf),
-                                                        ge)
-                             : draw_on_grid(seed, sid, kTagDense, (uint64_t)idx, scale, grid);
+                                                        ge, qb)
+                             : grid == GENP_BF16_SLICED
+                                   ? round_to_sliced_grid((double)__fmul_rn(polar_normal_f32(seed, sid, kTagDense + 4,
+                                                                                             (uint64_t)idx),
+                                                                            sf),
+                                                          ge, qb)
+                                   : draw_on_grid(seed, sid, kTagDense, (uint64_t)idx, scale, grid);
         G[idx] = v;
         if (G32) G32[idx] = (float)v;
         if (Gbf) Gbf[(idx % n) * round8(n) + idx / n] = __float2bfloat16_rn((float)v);  // G^T, K-major
@@ -453,9 +460,10 @@ int grid_for(int64_t work, int threads) {
 }  // namespace
 
 cudaError_t launch_make_dense(double *G, int64_t n, uint64_t seed, uint64_t sid, double scale, genp_prec grid,
-                              float *G32, __nv_bfloat16 *Gbf, cudaStream_t s) {
+                              float *G32, __nv_bfloat16 *Gbf, cudaStream_t s, int grid_digits) {
+    if (grid_digits != 1 && grid_digits != 2) return cudaErrorInvalidValue;
     note_launch();
-    k_dense<<<grid_for(n * n, 256), 256, 0, s>>>(G, n, seed, sid, scale, grid, G32, Gbf);
+    k_dense<<<grid_for(n * n, 256), 256, 0, s>>>(G, n, seed, sid, scale, grid, G32, Gbf, 7 * grid_digits - 1);
     return cudaGetLastError();
 }
 

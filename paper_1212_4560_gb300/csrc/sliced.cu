@@ -20,6 +20,7 @@ namespace {
 
 int g_default_digits = 7;
 int g_precond_digits = 7;
+int g_mult_digits = 1;
 
 // An operand entry in FP64: the double-float trailing matrix of the sliced
 // factorization converts exactly (48 significant bits).
@@ -318,6 +319,13 @@ int set_sliced_digits(int nd) {
     return old;
 }
 int sliced_precond_digits() { return g_precond_digits; }
+int sliced_mult_digits() { return g_mult_digits; }
+int set_sliced_mult_digits(int d) {
+    if (d != 1 && d != 2) return -1;
+    const int old = g_mult_digits;
+    g_mult_digits = d;
+    return old;
+}
 int set_sliced_precond_digits(int nd) {
     if (!sliced::supported(nd)) return -1;
     const int old = g_precond_digits;
@@ -330,12 +338,13 @@ template <typename TS>
 cudaError_t slice_rows_t(int nd, const TS *src, int64_t lds, int64_t m, int64_t K, __nv_bfloat16 *dst, int64_t ldq,
                          int *exps, cudaStream_t s, const unsigned long long *kexp) {
     if (m <= 0) return cudaSuccess;
-    if (nd < 2 || nd > 7 || ldq < nd * sliced_kpad(K)) return cudaErrorInvalidValue;
+    if (nd < 1 || nd > 7 || ldq < nd * sliced_kpad(K)) return cudaErrorInvalidValue;
     int blocks = (int)((m + 7) / 8);
     if (blocks > 152 * 16) blocks = 152 * 16;
     const int64_t kpad = sliced_kpad(K);
     note_launch();
     switch (nd) {
+        case 1: k_slice_rows<1, TS><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
         case 2: k_slice_rows<2, TS><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
         case 3: k_slice_rows<3, TS><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
         case 4: k_slice_rows<4, TS><<<blocks, 256, 0, s>>>(src, lds, m, K, kpad, dst, ldq, exps, kexp); break;
@@ -351,11 +360,12 @@ cudaError_t slice_cols_T_t(int nd, const TS *src, int64_t lds, int64_t K, int64_
                            int64_t ldq, int *exps, cudaStream_t s, const unsigned long long *kexp) {
     if (n <= 0) return cudaSuccess;
     const int64_t kpad = sliced_kpad(K);
-    if (nd < 2 || nd > 7 || ldq < nd * kpad) return cudaErrorInvalidValue;
+    if (nd < 1 || nd > 7 || ldq < nd * kpad) return cudaErrorInvalidValue;
     if (kpad <= kColsSmallK) {
         const unsigned gx = (unsigned)cdiv(n, 32);
         note_launch();
         switch (nd) {
+            case 1: k_slice_cols_T_small<1, TS><<<gx, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
             case 2: k_slice_cols_T_small<2, TS><<<gx, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
             case 3: k_slice_cols_T_small<3, TS><<<gx, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
             case 4: k_slice_cols_T_small<4, TS><<<gx, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
@@ -371,6 +381,7 @@ cudaError_t slice_cols_T_t(int nd, const TS *src, int64_t lds, int64_t K, int64_
     if (g.y > 65535u) return cudaErrorInvalidValue;
     note_launch();
     switch (nd) {
+        case 1: k_slice_cols_T<1, TS><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
         case 2: k_slice_cols_T<2, TS><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
         case 3: k_slice_cols_T<3, TS><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
         case 4: k_slice_cols_T<4, TS><<<g, dim3(32, 8), 0, s>>>(src, lds, K, n, kpad, dst, ldq, exps, kexp); break;
@@ -463,7 +474,7 @@ cudaError_t sliced_matmul(int nd, int64_t m, int64_t n, int64_t K, const double 
     const int nda = nd;
     if (ndb <= 0) ndb = nd;
     cudaError_t e = cudaMemset2DAsync(D, (size_t)ldd * sizeof(dfloat), 0, (size_t)n * sizeof(dfloat), (size_t)m, s);
-    const int64_t chunk = nda == 2 ? kSlicedChunk2 : kSlicedChunk;
+    const int64_t chunk = nda <= 2 ? kSlicedChunk2 : kSlicedChunk;
     for (int64_t k0 = 0; k0 < K && e == cudaSuccess; k0 += chunk) {
         const int64_t kc = K - k0 < chunk ? K - k0 : chunk;
         const int64_t kpad = sliced_kpad(kc), lda_q = nda * kpad, ldb_q = ndb * kpad;
@@ -480,7 +491,7 @@ cudaError_t sliced_matmul_t(int nda, int ndb, int64_t m, int64_t n, int64_t K, c
                             __nv_bfloat16 *Aq, int *exps, cudaStream_t s) {
     if (m <= 0 || n <= 0) return cudaSuccess;
     cudaError_t e = cudaMemset2DAsync(Dt, (size_t)lddt * sizeof(dfloat), 0, (size_t)m * sizeof(dfloat), (size_t)n, s);
-    const int64_t chunk = ndb == 2 ? kSlicedChunk2 : kSlicedChunk;
+    const int64_t chunk = ndb <= 2 ? kSlicedChunk2 : kSlicedChunk;
     for (int64_t k0 = 0; k0 < K && e == cudaSuccess; k0 += chunk) {
         const int64_t kc = K - k0 < chunk ? K - k0 : chunk;
         const int64_t kpad = sliced_kpad(kc), ldq_b = ndb * kpad, ldq_a = nda * kpad;

@@ -324,16 +324,49 @@ def test_sliced_gmres_ir_short_precondition(g, digits, pdigits):
 
 # ------------------------------------------------ G on the sliced product's grid
 
+class _mult_digits:
+    """genp_sliced_multiplier_digits set for the multipliers made inside."""
+
+    def __init__(self, g, d):
+        self.lib, self.d = g._lib.load(), d
+
+    def __enter__(self):
+        self.prev = self.lib.genp_sliced_multiplier_digits(self.d)
+        assert self.prev in (1, 2)
+
+    def __exit__(self, *exc):
+        self.lib.genp_sliced_multiplier_digits(self.prev)
+
+
+def test_multiplier_digits_setting(g):
+    """genp_sliced_multiplier_digits: 1 by default, 1 or 2 accepted, anything
+    else refused with -1 and the setting kept."""
+    lib = g._lib.load()
+    assert lib.genp_sliced_multiplier_digits(0) == 1
+    assert lib.genp_sliced_multiplier_digits(3) == -1
+    assert lib.genp_sliced_multiplier_digits(-2) == -1
+    assert lib.genp_sliced_multiplier_digits(2) == 1
+    assert lib.genp_sliced_multiplier_digits(1) == 2
+    assert lib.genp_sliced_multiplier_digits(0) == 1
+
+
+@pytest.mark.parametrize("digits", [1, 2])
 @pytest.mark.parametrize("n", [64, 257, 1024])
-def test_sliced_grid_multiplier_bit_exact(g, n):
+def test_sliced_grid_multiplier_bit_exact(g, n, digits):
     """value_grid GENP_BF16_SLICED: the single precision draw rounded to
-    multiples of 2^(E - 13), bit for bit the oracle's (dense Gaussian and
-    circulant)."""
+    multiples of 2^(E - 7 digits + 1) for the dense Gaussian (2^(E - 13) for
+    the circulant), bit for bit the oracle's; a redraw keeps the grid."""
     s = 1.0 / np.sqrt(n)
-    G = g.make_multiplier(g.GAUSSIAN, n, seed=n, value_grid=g.BF16_SLICED)
+    with _mult_digits(g, digits):
+        G = g.make_multiplier(g.GAUSSIAN, n, seed=n, value_grid=g.BF16_SLICED)
     D = torch.empty((n, n), dtype=torch.float64, device=DEV)
     g.multiplier_export(G, dense=D)
-    ref = oracle.sliced_grid(oracle.multiplier(0, n, seed=n, grid="fp32")["G"], s)
+    ref = oracle.sliced_grid(oracle.multiplier(0, n, seed=n, grid="fp32")["G"], s, digits=digits)
+    assert np.array_equal(D.cpu().numpy(), ref)
+    with _mult_digits(g, 3 - digits):
+        g.redraw_multiplier(G, seed=n + 1)
+    g.multiplier_export(G, dense=D)
+    ref = oracle.sliced_grid(oracle.multiplier(0, n, seed=n + 1, grid="fp32")["G"], s, digits=digits)
     assert np.array_equal(D.cpu().numpy(), ref)
     Gc = g.make_multiplier(g.CIRCULANT, n, seed=n, value_grid=g.BF16_SLICED)
     col = torch.empty(n, dtype=torch.float64, device=DEV)
@@ -342,17 +375,20 @@ def test_sliced_grid_multiplier_bit_exact(g, n):
     assert np.array_equal(col.cpu().numpy(), ref_c)
 
 
+@pytest.mark.parametrize("mdigits", [1, 2])
 @pytest.mark.parametrize("pdigits", [5, 7], indirect=True)
 @pytest.mark.parametrize("side", [0, 1])
 @pytest.mark.parametrize("n", [300, 1100])
-def test_precondition_two_digit_multiplier(g, pdigits, side, n):
-    """With G on the sliced grid, A G (and G A) take G in two digits (13
-    digit products for 7 digits of A instead of 28): the same error bound as
-    the symmetric product, against the oracle's FP64 product of the same G."""
+def test_precondition_two_digit_multiplier(g, pdigits, side, n, mdigits):
+    """With G on the sliced grid, A G (and G A) take G in its one or two
+    digits (7 or 13 digit products for 7 digits of A instead of 28): the
+    same error bound as the symmetric product, against the oracle's FP64
+    product of the same G."""
     digits = pdigits
     A, _, _ = W.lead_deficient(n, 32, 16, 1, seed=n + 7)
     A = A.numpy()
-    G = g.make_multiplier(g.GAUSSIAN, n, seed=9, value_grid=g.BF16_SLICED, side=side)
+    with _mult_digits(g, mdigits):
+        G = g.make_multiplier(g.GAUSSIAN, n, seed=9, value_grid=g.BF16_SLICED, side=side)
     Gd = torch.empty((n, n), dtype=torch.float64, device=DEV)
     g.multiplier_export(G, dense=Gd)
     Gm = Gd.cpu().numpy()

@@ -784,6 +784,45 @@ def test_sliced_grid_exact_in_two_digits(n):
         assert np.array_equal(d[:, 0] * 128 + d[:, 1], X.astype(np.int64))
 
 
+@pytest.mark.parametrize("n", [64, 300, 1024])
+def test_sliced_grid_exact_in_one_digit(n):
+    """The one-digit grid: every column scaled by its own power of two 2^-f
+    (f the least with max |g| < 2^f) and by 2^7 is an integer below 2^7 in
+    magnitude, so one balanced digit (|d_1| <= 128) holds it exactly; the
+    grid is the two-digit grid's coarsening (every one-digit value is a
+    two-digit value) and moves an entry by at most 2^(E - 7)."""
+    s = 1.0 / math.sqrt(n)
+    G0 = oracle.multiplier(0, n, seed=n, grid="fp32")["G"]
+    G = oracle.sliced_grid(G0, s, digits=1)
+    E = oracle.sliced_grid_exponent(s)
+    assert np.abs(G - G0).max() <= 2.0 ** (E - 7)
+    assert np.array_equal(oracle.sliced_grid(G, s, digits=2), G)
+    for j in range(n):
+        col = G[:, j]
+        amax = float(np.abs(col).max())
+        if amax == 0.0:
+            continue
+        f = math.frexp(amax)[1]
+        X = np.ldexp(col, 7 - f)
+        assert np.array_equal(X, np.round(X))
+        assert np.abs(X).max() < 2**7
+
+
+def test_sliced_grid_one_digit_rounding():
+    """Nearest multiple of 2^(E - 6), ties to even, by hand; the coarser grid
+    keeps the Gaussian's first two moments within 1%."""
+    n = 512
+    s = 1.0 / math.sqrt(n)
+    q = 2.0 ** (oracle.sliced_grid_exponent(s) - 6)
+    T = np.array([[0.5 * q, 1.5 * q, 2.5 * q, -0.5 * q, -1.5 * q, 0.49 * q]])
+    assert np.array_equal(oracle.sliced_grid(T, s, digits=1) / q, [[0.0, 2.0, 2.0, -0.0, -2.0, 0.0]])
+    G = oracle.sliced_grid(oracle.multiplier(0, n, seed=3)["G"], s, digits=1)
+    assert np.array_equal(G / q, np.round(G / q))
+    assert abs(G.std() / s - 1) < 0.01 and abs(G.mean()) < 0.01 * s
+    with pytest.raises(ValueError):
+        oracle.sliced_grid(G, s, digits=3)
+
+
 def test_sliced_grid_rounding_and_exponent():
     """E is the least integer with 12.5 scale <= 2^E; entries move to the
     nearest multiple of 2^(E-13) (error <= 2^(E-14)), ties to even; the grid

@@ -563,13 +563,16 @@ def run_ours(a, emit=True):
                                    "Schur updates)",
                     "tensor_pipe": {"achieved": pipe, "frac": pipe / peak, "unit": "TFLOP/s",
                                     "counted": "BF16 digit-pair products actually issued (2 m n Kpad per pair)"},
-                    # dram read + write bytes of one n = 4096 A G chunk launch (k_tc_sliced<2, 5>,
-                    # K = 1024, column-major tile order) under ncu on the current kernel, 281.7 MB
-                    # (the double-float accumulator's read-modify-write 268 MB, the digit slices
-                    # read about once), scaled by the n^2 output tiles to this size's chunk launches
-                    "traffic": 281.7e6 * (n / 4096) ** 2 if (nd == 7 and pd == 5) else None,
-                    "traffic_basis": "A G chunk launch (K = 1024) of k_tc_sliced<2, 5>; ncu at n = 4096 scaled by "
-                                     "n^2; Schur-update launches (K = 512) read and write the same accumulator "
+                    # dram read + write bytes of one n = 4096 A G chunk launch (K = 1024,
+                    # column-major tile order) under ncu on the current kernel: 266.2 MB for
+                    # k_tc_sliced<1, 5> (the one-digit multiplier grid), 281.7 MB for
+                    # k_tc_sliced<2, 5> (two digits); the double-float accumulator's
+                    # read-modify-write is 268 MB of either, the digit slices are read about
+                    # once; scaled by the n^2 output tiles to this size's chunk launches
+                    "traffic": (266.2e6 if lib.genp_sliced_multiplier_digits(0) == 1 else 281.7e6) * (n / 4096) ** 2
+                    if (nd == 7 and pd == 5) else None,
+                    "traffic_basis": "A G chunk launch (K = 1024) of k_tc_sliced<1 or 2, 5>; ncu at n = 4096 scaled "
+                                     "by n^2; Schur-update launches (K = 512) read and write the same accumulator "
                                      "per tile over half the depth"}
     elif a.prec == "fp8" and tc_launches:
         # per launch: the A G product (K = n, k_tc_e4m3, tensor-bound) and the

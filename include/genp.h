@@ -712,7 +712,9 @@ GENP_API genp_status genp_make_sparse_noalloc(int64_t n, int nnz_per_col, uint64
  * steps of a recorded refinement graph that a converged refinement skips
  * launch nothing and are not counted; the kernels of the steps that ran are
  * added on the device, into pinned host memory, so the count is complete
- * once the caller has synchronized the stream. */
+ * once the caller has synchronized the stream.  That pinned word belongs to
+ * the device's context: after cudaDeviceReset in the process, do not call
+ * this function again. */
 GENP_API uint64_t genp_launch_count(void);
 
 /* Copies the device status of F to *out after synchronizing cuda_stream. */

@@ -194,8 +194,9 @@ def solve_system(A: torch.Tensor, B: torch.Tensor, kind: int = GAUSSIAN, seed: i
     n = A.size(0)
     f64 = prec in (FP64, BF16_SLICED)
     # FP32-grid draws for the FP32 factorization, BF16 / FP8 grids for the
-    # tensor-core ones, and the sliced product's two-digit fixed-point grid for
-    # the sliced one (A G then forms 13 digit products instead of 28)
+    # tensor-core ones, and the sliced product's fixed-point grid for the
+    # sliced one (one digit by default: A G then forms nd digit products
+    # instead of nd (nd + 1) / 2)
     grid = {FP64: FP64, BF16: BF16, BF16X3: BF16, FP8_E4M3: FP8_E4M3, BF16_SLICED: BF16_SLICED}.get(prec, FP32)
     G = make_multiplier(kind, n, seed, value_grid=grid, stream=stream, side=side)
     C = torch.empty((n, n), dtype=torch.float64 if f64 else torch.float32, device=A.device)

@@ -715,7 +715,7 @@ k_tc_sliced(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     const int ntm = (m + BM - 1) / BM, ntn = (n + SBN - 1) / SBN;
     const int ntiles = ntm * ntn;
     // Tile order: the CTAs in flight walk the M tiles of a few N columns when
-    // the M side is the narrow operand (a two-digit multiplier), so the wide
+    // the M side is the narrow operand (a one- or two-digit multiplier), so the wide
     // operand's digit slices of those columns are shared through L2 and the
     // narrow one is what gets re-read; otherwise the N tiles of a few M rows.
     auto tile_m = [&](int tile) { return NDA < NDB ? tile % ntm : tile / ntn; };

@@ -336,14 +336,14 @@ cudaError_t df_to_f64(const dfloat *src, int64_t lds, double *dst, int64_t ldd, 
 cudaError_t df_axpby(double alpha, const dfloat *W, int64_t ldw, double beta, double *D, int64_t ldd, int64_t m,
                      int64_t n, cudaStream_t s);
 // D (double-float, m x n) = A B, A m x K and B K x n FP64, K cut in chunks of
-// at most kSlicedChunk (kSlicedChunk2 for a two-digit A side); Aq, Bq hold
+// at most kSlicedChunk (kSlicedChunk2 for a one- or two-digit A side); Aq, Bq hold
 // (m or n) x nd chunk BF16, exps m + n ints.
 // Dt (double-float, n x m) = (A B)^T = B^T A^T, with B's columns (ndb
 // digits) on the M side and A's rows (nda digits) on the N side: for a B
 // exact in few digits (a multiplier on the sliced grid) the wide operand
 // then sits along N, where one MMA covers several of its digits.
 // Bq holds n x ndb chunk, Aq m x nda chunk BF16 (chunk kSlicedChunk2 for
-// ndb = 2, else kSlicedChunk); exps n + m ints.
+// ndb <= 2, else kSlicedChunk); exps n + m ints.
 cudaError_t sliced_matmul_t(int nda, int ndb, int64_t m, int64_t n, int64_t K, const double *A, int64_t lda,
                             const double *B, int64_t ldb, dfloat *Dt, int64_t lddt, __nv_bfloat16 *Bq,
                             __nv_bfloat16 *Aq, int *exps, cudaStream_t s);
